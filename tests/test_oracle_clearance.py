@@ -1,0 +1,76 @@
+"""Pins for the float64 clearance-cost oracle (Eq. 2's clearance term as a squared hinge).
+
+* closed form: obstacles on the plane x = 0 give D = x^2, so d = vs * x is linear and trilinear
+  interpolation reproduces it exactly; cost and gradient then have closed forms in p_x;
+* the same along y and z (catches transposed axes);
+* at a voxel centre d = vs * sqrt(D) of that voxel;
+* the analytic gradient against central finite differences (h = 1e-3 m) of the oracle's value
+  on a real transform, away from cell faces and hinge kinks.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+
+def plane_field(axis, shape=(12, 13, 14), dmax=8):
+    occ = np.zeros(shape, np.uint8)
+    sl = [slice(None)] * 3
+    sl[2 - axis] = 0  # axis 0 = x is array axis 2
+    occ[tuple(sl)] = 1
+    return occ, O.edt_factorised(occ, dmax)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_plane_closed_form(axis):
+    vs, tau, dmax = 0.1, 0.45, 8
+    occ, D = plane_field(axis, dmax=dmax)
+    rs = np.random.default_rng(axis)
+    nz, ny, nx = D.shape
+    hi = np.array([nx - 1, ny - 1, nz - 1]) * vs
+    pts = (rs.random((5, 40, 3)) * hi).astype(np.float32)
+    pts[..., axis] = np.minimum(pts[..., axis], np.float32((dmax - 1) * vs))  # stay below truncation
+    cost, grad, d = O.clearance(D, dmax, vs, tau, pts)
+    q = pts[..., axis].astype(np.float64)
+    np.testing.assert_allclose(d, q, rtol=0, atol=1e-6)
+    h = np.maximum(0.0, tau - q)
+    np.testing.assert_allclose(cost, (h * h).sum(-1), rtol=1e-6, atol=1e-7)  # u is taken in float32
+    expect = np.zeros_like(grad)
+    expect[..., axis] = -2.0 * h
+    np.testing.assert_allclose(grad, expect, rtol=1e-6, atol=1e-6)
+
+
+def test_voxel_centres():
+    occ = W.bernoulli_grid(5, (10, 11, 12), 0.03)
+    dmax, vs = 5, 0.2
+    D = O.edt_factorised(occ, dmax)
+    rs = np.random.default_rng(0)
+    ijk = np.stack([rs.integers(0, 11, 50), rs.integers(0, 10, 50), rs.integers(0, 9, 50)], 1)
+    pts = (ijk * vs).astype(np.float32)[None]
+    _, _, d = O.clearance(D, dmax, vs, 1.0, pts)
+    ref = vs * np.sqrt(D[ijk[:, 2], ijk[:, 1], ijk[:, 0]].astype(np.float64))
+    np.testing.assert_allclose(d[0], ref, rtol=1e-6, atol=1e-6)
+
+
+def test_gradient_vs_central_differences():
+    occ = W.bernoulli_grid(9, (24, 24, 24), 0.01)
+    dmax, vs, tau, h = 8, 0.1, 0.5, 1e-3
+    D = O.edt_factorised(occ, dmax)
+    pts = W.free_points(3, occ, vs, 400).reshape(1, 400, 3)
+    _, grad, d = O.clearance(D, dmax, vs, tau, pts)
+    u = pts[0].astype(np.float64) / vs
+    frac = u - np.floor(u)
+    keep = ((frac > 2 * h / vs) & (frac < 1 - 2 * h / vs)).all(1) & (np.abs(tau - d[0]) > 2 * h)
+    assert keep.sum() > 100
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        # finite differences in float64 on the oracle's own value, evaluated point by point
+        cp = [O.clearance(D, dmax, vs, tau, (pts[0, i] + e)[None, None].astype(np.float64).astype(np.float32))[0][0]
+              for i in np.flatnonzero(keep)]
+        cm = [O.clearance(D, dmax, vs, tau, (pts[0, i] - e)[None, None].astype(np.float64).astype(np.float32))[0][0]
+              for i in np.flatnonzero(keep)]
+        fd = (np.array(cp) - np.array(cm)) / (2 * h)
+        an = grad[0, keep, a]
+        np.testing.assert_allclose(an, fd, rtol=1e-3, atol=1e-4)
