@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the exact truncated EDT on a sparse brick grid (one JSON line on rank 0).
+
+Workload (default): the synthetic tunnel scene, 1024 x 1024 x 256 voxels, 40 spline tunnels of
+radius 8-24 voxels whose walls are occupied shells, dmax = 32 (clamp 1024), seed 1.  One step =
+one global transform from the occupied-voxel list already resident on the device: reset the grid,
+stage the records, build the sparse grid (sort / unique / compaction), activate, run the in-plane
+and z passes.  value = active voxels (bricks with some D < dmax^2, times 512) per second, in
+Mvoxels/s, summed over ranks.
+
+Rows reported beside the headline: roofline of the dominant kernel and of the whole step, the CPU
+oracle on the host cores (bounded sample), the end-to-end number through the C ABI with host
+buffers, clocks sampled during the timed region, and the library's kernel-launch count.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload tunnel|bernoulli64]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EDT Mvoxels/s and % HBM roofline; incremental update ms/frame; queries/s"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+WORKLOADS = {
+    "tunnel": dict(dims=(1024, 1024, 256), dmax=32, seed=1, kind="tunnel",
+                   name="tunnel scene 1024x1024x256, 40 tunnels r 8-24, shell walls, dmax 32"),
+    "bernoulli64": dict(dims=(64, 64, 64), dmax=16, seed=0, kind="bernoulli", p=0.02,
+                        name="dense 64^3 Bernoulli(0.02), dmax 16"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tunnel")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_occupancy(wl):
+    import workloads as W
+    nx, ny, nz = wl["dims"]
+    if wl["kind"] == "tunnel":
+        return W.tunnel_scene(wl["seed"], (nx, ny, nz))
+    return W.bernoulli_grid(wl["seed"], (nz, ny, nx), wl["p"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    source of the kernel (hash of the pass source file)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2105_04419_gb300", "csrc", "passes.cu"), "rb").read()
+        h = hashlib.sha256(src).hexdigest()[:16]
+        e = t.get(kernel)
+        if e and e.get("source_sha") == h:
+            return e
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(occ, dmax, budget_s=12.0):
+    """The CPU oracle (Eq. 1 factorised, OpenMP on all host cores) on a z-slab of the workload."""
+    import oracle as O
+    nz = occ.shape[0]
+    cores = O.num_threads()
+    # size the slab so the run takes roughly budget_s: calibrate on a thin slab first
+    t0 = time.perf_counter()
+    thin = np.ascontiguousarray(occ[: min(8, nz)])
+    O.edt_factorised(thin, dmax)
+    per_plane = (time.perf_counter() - t0) / thin.shape[0]
+    planes = int(max(8, min(nz, budget_s / max(per_plane, 1e-6))))
+    slab = np.ascontiguousarray(occ[:planes])
+    t0 = time.perf_counter()
+    D = O.edt_factorised(slab, dmax)
+    dt = time.perf_counter() - t0
+    active = active_voxels_of(D, dmax)
+    ny, nx = slab.shape[1:]
+    return {"value": active / dt / 1e6, "unit": "Mvoxels/s", "cores": cores, "kind": "oracle",
+            "sample": f"Eq. 1 factorised (OpenMP) on the first {planes} z-planes ({nx}x{ny}x{planes}) of the "
+                      f"workload; {active} active voxels in {dt:.2f} s"}
+
+
+def active_voxels_of(D, dmax):
+    nz, ny, nx = D.shape
+    bz, by, bx = -(-nz // 8), -(-ny // 8), -(-nx // 8)
+    pad = np.full((bz * 8, by * 8, bx * 8), dmax * dmax, dtype=D.dtype)
+    pad[:nz, :ny, :nx] = D
+    fin = (pad < dmax * dmax).reshape(bz, 8, by, 8, bx, 8).any(axis=(1, 3, 5))
+    return int(fin.sum()) * 512
+
+
+def run_reference(args, wl):
+    """The oracle as the reference arm: each step is the CPU factorised transform of a bounded
+    sample (a z-slab) of the workload, on the host cores of rank 0."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    occ = make_occupancy(wl)
+    dmax = wl["dmax"]
+    nz = occ.shape[0]
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    t0 = time.perf_counter()
+    O.edt_factorised(np.ascontiguousarray(occ[: min(8, nz)]), dmax)
+    per_plane = (time.perf_counter() - t0) / min(8, nz)
+    planes = int(max(8, min(nz, budget / max(per_plane, 1e-6))))
+    slab = np.ascontiguousarray(occ[:planes])
+    for _ in range(args.warmup):
+        O.edt_factorised(slab, dmax)
+    times = []
+    D = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        D = O.edt_factorised(slab, dmax)
+        times.append(time.perf_counter() - t0)
+    active = active_voxels_of(D, dmax)
+    ms = 1e3 * statistics.mean(times)
+    value = active / (ms / 1e3) / 1e6
+    ny, nx = slab.shape[1:]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mvoxels/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": wl["name"], "sample": f"{nx}x{ny}x{planes} z-slab"},
+            "cpu_baseline": {"value": value, "unit": "Mvoxels/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"Eq. 1 factorised (OpenMP) on the first {planes} z-planes"},
+            "e2e": {"value": value, "unit": "Mvoxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2105_04419_gb300 import build as B
+    if not B.up_to_date():
+        if rank == 0 or world == 1:
+            B.build()
+        if world > 1:
+            dist.barrier()
+    import paper_2105_04419_gb300 as V
+
+    occ = make_occupancy(wl)
+    nx, ny, nz = wl["dims"]
+    dmax = wl["dmax"]
+    import workloads as W
+    xyz_h = W.occupied_coords(occ)
+    n = len(xyz_h)
+    ones_h = np.ones(n, np.uint8)
+    xyz = torch.from_numpy(xyz_h).cuda()
+    ones = torch.from_numpy(ones_h).cuda()
+    stream = torch.cuda.current_stream()
+    m = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+
+    def step():
+        m.reset()
+        m.set_occupancy(xyz, ones)
+        m.global_()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    info = m.info()
+    active = info["finite_bricks"] * 512
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    m.set_profiling(True)
+    phases = {k: [] for k in ("ingest_ms", "activation_ms", "items_ms", "xy_ms", "z_ms")}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = V.kernel_launches()
+    for k in range(args.steps):
+        flush.fill_(k & 255)  # evict the previous step's data from L2 (not timed)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        pt = m.phase_times()  # waits for this step; device times are unaffected
+        for key in phases:
+            phases[key].append(pt[key])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = V.kernel_launches() - launches0
+    clocks = sampler.stop()
+    m.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = active * world / (ms / 1e3) / 1e6
+    ph = {k: statistics.mean(v) for k, v in phases.items()}
+
+    # roofline: dominant kernel with its compulsory bytes at the stored widths
+    peak, peak_src = peaks()
+    allocated = info["allocated_bricks"]
+    per_brick = {"xy_ms": 64 + 1024, "z_ms": 1024 + 2048}  # occupancy in + g2 out; g2 in + D out
+    dom = max(("xy_ms", "z_ms"), key=lambda k: ph[k])
+    kname = {"xy_ms": "k_xy_half", "z_ms": "k_z_half"}[dom]
+    achieved = allocated * per_brick[dom] / (ph[dom] / 1e3) / 1e9
+    tr = traffic_for(kname)
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "bytes_per_brick": per_brick[dom], "bricks_per_launch": allocated,
+                "traffic": (tr["dram_bytes_per_launch"] if tr else None)}
+    # whole step against the unfused three-pass model (21 B per active voxel) and the compulsory
+    # bytes (bit mask in, int32 out: 4.125 B per active voxel)
+    roof_step = {"model_B_per_active_voxel": 21.0, "achieved": active * 21.0 / (ms / 1e3) / 1e9,
+                 "frac": active * 21.0 / (ms / 1e3) / 1e9 / peak,
+                 "compulsory_B_per_active_voxel": 4.125,
+                 "frac_compulsory": active * 4.125 / (ms / 1e3) / 1e9 / peak, "peak": peak, "unit": "GB/s"}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mvoxels/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": wl["name"], "dims_xyz": list(wl["dims"]), "dmax": dmax, "occupied_voxels": n,
+                       "active_bricks": info["finite_bricks"], "allocated_bricks": allocated,
+                       "obstacle_bricks": info["obstacle_bricks"], "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "step": "reset + stage device records + global transform"},
+            "phases_ms": ph, "roofline": roofline, "roofline_step": roof_step, "gpu_launches": launches,
+            "clocks": clocks}
+
+    if not args.no_e2e:
+        # end to end through the C ABI with host buffers: host records -> device, transform, and
+        # the grid's counters (including the active-brick count) back to the host
+        e2e_ms = []
+        for k in range(max(3, args.warmup) + args.steps):
+            flush.fill_(k & 255)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m.reset()
+            m.set_occupancy(xyz_h, ones_h)
+            m.global_()
+            inf2 = m.info()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        e2e_ms = e2e_ms[max(3, args.warmup):]
+        ems = statistics.mean(e2e_ms)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        line["e2e"] = {"value": inf2["finite_bricks"] * 512 * world / (ems / 1e3) / 1e6, "unit": "Mvoxels/s",
+                       "ms_per_step": ems, "h2d_bytes_per_step": int(n * 13),
+                       "d2h_bytes_per_step": int(4 * 16 + 4 * inf2["allocated_bricks"])}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(occ, dmax)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

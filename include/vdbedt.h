@@ -1,0 +1,191 @@
+/*
+ * vdbedt -- exact truncated Euclidean distance transform over a sparse grid of 8^3 voxel bricks,
+ * for one NVIDIA GB300 (sm_103a).  C ABI: plain pointers and sizes, no C++ or framework types.
+ *
+ * What is computed (paper: Zhu et al., "VDB-EDT", arXiv 2105.04419):
+ *   For an nx x ny x nz occupancy grid and truncation distance dmax (voxels), every voxel v gets
+ *       D(v) = min( dmax^2, min_{o occupied} |v - o|^2 )
+ *   the squared Euclidean distance in integer voxel units to the nearest occupied voxel (Sec. III,
+ *   Eq. 1), saturated at dmax^2 (the limited transform of Sec. III; Sec. IV-B stores dmax for any
+ *   distance at or beyond it).  D is 0 on obstacles.  Results are exact (bit-identical to the
+ *   definition), int32.
+ *   Two forms, as the paper names them (Sec. I): the global transform recomputes the field from
+ *   the occupancy; the incremental transform repairs it after occupancy edits (Alg. 1's
+ *   SetObstacle / RemoveObstacle followed by DistanceTransform).
+ *
+ * Storage: the grid keeps only bricks within reach of an obstacle; everything else reads as the
+ * background value dmax^2 (the paper's tile value, Sec. IV-A).
+ *
+ * Conventions for every call:
+ *   - Return codes only; no call aborts or exits.  Out-parameters are written only on VDBEDT_OK.
+ *   - Work is stream-ordered on the handle's stream.  Host pointers are read (and host outputs
+ *     written) before the call returns.  Device pointers must stay valid until the stream reaches
+ *     the call.
+ *   - A CUDA runtime error makes the handle fail stickily: every later call returns VDBEDT_ECUDA
+ *     until vdbedt_destroy.
+ *   - Errors detected on the device (capacity exceeded, a bounded wait that timed out, invalid
+ *     records passed through device memory) are reported by the next call that synchronises
+ *     with the stream: vdbedt_synchronize, vdbedt_get_info, vdbedt_query / vdbedt_export_dense
+ *     with host outputs.
+ *   - Coordinates are int32 (x, y, z) triples, 0 <= x < nx etc.; dense arrays are C-ordered
+ *     [nz][ny][nx].
+ *   - A handle is not thread-safe; distinct handles may be used from distinct threads.
+ */
+#ifndef VDBEDT_H
+#define VDBEDT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vdbedt_map* vdbedt_handle;
+
+typedef enum {
+  VDBEDT_OK = 0,
+  VDBEDT_EINVAL = 1,    /* bad argument or record; the whole call is rejected */
+  VDBEDT_ENOMEM = 2,    /* device or host allocation failed */
+  VDBEDT_ECUDA = 3,     /* CUDA runtime error (sticky for the handle) */
+  VDBEDT_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+  VDBEDT_EOVERFLOW = 5, /* more bricks needed than the handle's capacity */
+  VDBEDT_EINTERNAL = 6  /* a device-side consistency check failed */
+} vdbedt_status;
+
+/* Largest supported truncation: keeps dmax^2 = 32761 < 2^15 so stored intermediates fit 16 bits. */
+#define VDBEDT_DMAX_LIMIT 181
+
+typedef struct {
+  int32_t nx, ny, nz;  /* grid size in voxels, each >= 1 */
+  int32_t dmax;        /* truncation distance in voxels, 1 <= dmax <= VDBEDT_DMAX_LIMIT */
+  float voxel_size;    /* metres per voxel (used by the clearance query), > 0 */
+  int32_t device;      /* CUDA device ordinal */
+  void* stream;        /* cudaStream_t to run on; NULL: the handle creates and owns one */
+  uint32_t flags;      /* reserved, 0 */
+  int64_t max_bricks;  /* brick capacity; 0: every brick of the grid (always enough) */
+} vdbedt_config;
+
+typedef struct {
+  int64_t allocated_bricks; /* bricks holding storage */
+  int64_t obstacle_bricks;  /* bricks with at least one occupied voxel */
+  int64_t finite_bricks;    /* bricks with at least one voxel below dmax^2 (the active set) */
+  int64_t capacity_bricks;
+  int64_t nodes;            /* interior nodes (16^3 bricks each) */
+  int64_t device_bytes;     /* device memory held by the handle */
+  int32_t R;                /* brick radius of influence, floor((dmax + 6) / 8) */
+  int32_t error_bits;       /* device-side error word (0 when healthy) */
+} vdbedt_info;
+
+typedef struct {
+  int64_t records;        /* staged records consumed */
+  int64_t net_flips;      /* voxels whose occupancy changed */
+  int64_t changed_bricks; /* bricks holding a flipped voxel */
+  int64_t xy_items;       /* brick runs recomputed by the in-plane (x, y) passes */
+  int64_t z_items;        /* brick runs recomputed by the z pass */
+  int64_t new_bricks;     /* bricks allocated by this update */
+} vdbedt_update_stats;
+
+/* Create a handle for an nx x ny x nz grid with no obstacles (every D = dmax^2).
+ * Allocates all device storage for cfg->max_bricks bricks up front.
+ * EINVAL: a size < 1, dmax outside [1, VDBEDT_DMAX_LIMIT], voxel_size <= 0, bad device.
+ * ENOMEM: device allocation failed. */
+vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out);
+
+/* Release everything the handle owns (waits for its stream).  NULL is accepted. */
+vdbedt_status vdbedt_destroy(vdbedt_handle h);
+
+/* Stage occupancy records: voxel (xyz[3k], xyz[3k+1], xyz[3k+2]) gets occ[k] (0 = free, 1 =
+ * obstacle) -- the edits of Alg. 1's SetObstacle / RemoveObstacle.  Nothing changes until the next
+ * vdbedt_global or vdbedt_update, which applies all staged records in order: when a voxel appears
+ * more than once, its last record wins.  on_device != 0: xyz and occ are device pointers (read on
+ * the stream; an invalid record is skipped and reported as EINVAL by the next synchronising call);
+ * otherwise host pointers, validated here: any coordinate outside the grid or occ[k] > 1 rejects
+ * the whole call with EINVAL.  n == 0 is a no-op; n < 0 is EINVAL. */
+vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const uint8_t* occ, int64_t n,
+                                   int on_device);
+
+/* Stage a whole occupancy grid grid[nz][ny][nx] (nonzero = obstacle), replacing the current one
+ * (records staged earlier are discarded).  on_device selects host or device memory. */
+vdbedt_status vdbedt_set_occupancy_dense(vdbedt_handle h, const uint8_t* grid, int on_device);
+
+/* Clear the grid to no obstacles and drop all storage (keeps capacity); staged records are dropped. */
+vdbedt_status vdbedt_reset(vdbedt_handle h);
+
+/* Global transform: apply staged records, then recompute the whole field from the occupancy. */
+vdbedt_status vdbedt_global(vdbedt_handle h);
+
+/* Incremental transform: apply staged records; recompute only the bricks that a flipped voxel can
+ * reach (Chebyshev brick radius R around each changed brick).  Equal, bit for bit, to vdbedt_global
+ * on the same occupancy.  stats (nullable) is filled after a stream synchronisation. */
+vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats);
+
+/* D at n voxel coordinates; coordinates outside the grid or in unstored bricks give dmax^2.
+ * on_device != 0: xyz and out_sqdist are device pointers; otherwise host pointers (the call waits). */
+vdbedt_status vdbedt_query(vdbedt_handle h, const int32_t* xyz, int64_t n, int32_t* out_sqdist, int on_device);
+
+/* The whole field as a dense int32 array out[nz][ny][nx] (host or device). */
+vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device);
+
+/* Clearance cost of Eq. 2 (second term) as a squared hinge, for T trajectories of P points.
+ * pts: device float [T][P][3], metres; voxel centre (i, j, k) sits at (i, j, k) * voxel_size.
+ * Per point: u = p / voxel_size (float32), cell i0 = floor(u) clamped to [0, n - 2] per axis,
+ * t = u - i0; d = trilinear interpolation of voxel_size * sqrt(D) over the cell's 8 corners;
+ * c = max(0, tau - d)^2.  cost[t] = sum of c over the trajectory's points (device float [T]).
+ * Grids with a size < 2 along any axis are EINVAL. */
+vdbedt_status vdbedt_clearance_forward(vdbedt_handle h, const float* pts, int64_t T, int64_t P, float tau,
+                                       float* cost);
+
+/* Gradient of sum_t grad_cost[t] * cost[t] with respect to pts: grad_pts[t][p] =
+ * grad_cost[t] * (-2 max(0, tau - d)) * (1 / voxel_size) * d(trilinear)/dt.  Device pointers. */
+vdbedt_status vdbedt_clearance_backward(vdbedt_handle h, const float* pts, int64_t T, int64_t P, float tau,
+                                        const float* grad_cost, float* grad_pts);
+
+/* Global transform of k maps in one persistent launch on the first handle's stream: staged
+ * records of every map are applied, then the in-plane and z passes of all maps run from one
+ * device work queue (larger maps first).  All handles must be on the same device and must not be
+ * used concurrently elsewhere.  Bit-identical to vdbedt_global on each map. */
+vdbedt_status vdbedt_global_batched(vdbedt_handle* hs, int32_t k);
+
+/* Tuning of the transform passes (0 = automatic for any field).
+ *   xy_run: bricks per in-plane work item along y (4, 8 or 16);
+ *   z_run:  bricks per z work item (4, 8 or 16);
+ *   variant: 0 automatic, 1 windowed minimum, 2 lower envelope of parabolas. */
+typedef struct {
+  int32_t xy_run, z_run, variant, reserved;
+} vdbedt_tuning;
+vdbedt_status vdbedt_set_tuning(vdbedt_handle h, const vdbedt_tuning* t);
+
+/* Phase timing (tracing): with profiling on, vdbedt_global and vdbedt_update record CUDA events
+ * on the handle's stream around their phases; vdbedt_get_phase_times waits for the last such call
+ * and returns the device time of each phase in milliseconds.  The paper reports wall time per
+ * frame (Table II); these are the GPU analogue, per phase.  EINVAL before any profiled call. */
+typedef struct {
+  float ingest_ms;     /* staged records -> bricks and occupancy bits */
+  float activation_ms; /* compute set (dilation by R bricks) and brick allocation */
+  float items_ms;      /* work lists of the passes (global form only) */
+  float xy_ms;         /* in-plane (x, y) passes */
+  float z_ms;          /* z pass, clamp, finite flags */
+} vdbedt_phase_times;
+vdbedt_status vdbedt_set_profiling(vdbedt_handle h, int on);
+vdbedt_status vdbedt_get_phase_times(vdbedt_handle h, vdbedt_phase_times* out);
+
+/* Number of CUDA kernels this library has launched in this process (all handles). */
+int64_t vdbedt_kernel_launches(void);
+
+/* Wait for the handle's stream; report device-side errors. */
+vdbedt_status vdbedt_synchronize(vdbedt_handle h);
+
+/* Counters of the grid (synchronises). */
+vdbedt_status vdbedt_get_info(vdbedt_handle h, vdbedt_info* info);
+
+/* The handle's stream (cudaStream_t). */
+void* vdbedt_stream(vdbedt_handle h);
+
+/* Last error message for the handle (or for handle-less failures when h is NULL); never NULL. */
+const char* vdbedt_last_error(vdbedt_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VDBEDT_H */

@@ -1,0 +1,23 @@
+"""GB300-native exact truncated Euclidean distance transform over a sparse brick grid.
+
+Python binding of ``libvdbedt.so`` (C ABI in ``include/vdbedt.h``).  Argument marshalling only:
+every step of the transform runs in the library's CUDA kernels.  PyTorch provides device memory
+and streams.  The library must be built (``paper_2105_04419_gb300.build.build()``); without it,
+importing :mod:`paper_2105_04419_gb300.lib` raises.
+
+Entry points mirror the C names: :class:`Map` wraps a handle (create, set_occupancy,
+set_occupancy_dense, reset, global_, update, query, export_dense, clearance_forward /
+clearance_backward, set_tuning, synchronize, info); :func:`global_batched` runs several maps in
+one launch; :func:`clearance_cost` is the differentiable clearance cost (torch.autograd.Function
+over the library's forward and backward kernels).
+"""
+from .lib import (  # noqa: F401
+    VDBEDT_DMAX_LIMIT,
+    Map,
+    VdbedtError,
+    clearance_cost,
+    global_batched,
+    kernel_launches,
+    library_path,
+    load,
+)

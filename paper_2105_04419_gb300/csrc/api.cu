@@ -1,0 +1,599 @@
+// The C ABI of libvdbedt (declared in include/vdbedt.h): handle lifetime, staging of occupancy
+// records, the global and incremental transforms, queries and the clearance cost.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/vdbedt.h"
+#include "vdbedt_internal.cuh"
+
+using namespace vdbedt;
+
+namespace vdbedt {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, int nx, int ny, int nz, int4* dst,
+                                int32_t* invalid, cudaStream_t st);
+}
+
+struct vdbedt_map {
+  GridView g{};
+  vdbedt_config cfg{};
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::vector<void*> allocs;
+  size_t device_bytes = 0;
+  // staged records
+  int4* stage = nullptr;
+  int64_t stage_n = 0, stage_cap = 0;
+  bool dense_pending = false;
+  bool computed = false;
+  int32_t* d_invalid = nullptr;
+  int32_t* h_pinned = nullptr;  // pinned host words for small readbacks
+  Scratch scr;
+  Scratch io;  // host-input staging on the device
+  unsigned long long* xy_items = nullptr;
+  unsigned long long* z_items = nullptr;
+  int32_t* changed = nullptr;
+  int epoch = 0;
+  Tuning tune;
+  int sticky = VDBEDT_OK;
+  std::string err;
+  // phase timing (CUDA events on the handle's stream)
+  bool profiling = false;
+  cudaEvent_t ev[6] = {};
+  bool ev_recorded = false;
+};
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+vdbedt_status fail(vdbedt_map* h, vdbedt_status s, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+    if (s == VDBEDT_ECUDA) h->sticky = VDBEDT_ECUDA;
+  } else {
+    g_last_error = msg;
+  }
+  return s;
+}
+
+vdbedt_status cuda_fail(vdbedt_map* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(h, VDBEDT_ENOMEM, m);
+  }
+  return fail(h, VDBEDT_ECUDA, m);
+}
+
+#define CK(h, expr, where)                                   \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return cuda_fail((h), _e, where); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(vdbedt_map* h, T** p, size_t count) {
+  size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess) {
+    h->allocs.push_back((void*)*p);
+    h->device_bytes += bytes;
+  }
+  return e;
+}
+
+vdbedt_status check_handle(vdbedt_map* h) {
+  if (!h) return fail(nullptr, VDBEDT_EINVAL, "null handle");
+  if (h->sticky == VDBEDT_ECUDA) return VDBEDT_ECUDA;
+  return VDBEDT_OK;
+}
+
+vdbedt_status device_errors(vdbedt_map* h) {
+  cudaError_t e =
+      cudaMemcpyAsync(h->h_pinned + 32, h->g.counters + C_ERR, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+  int bits = h->h_pinned[32];
+  if (!bits) return VDBEDT_OK;
+  if (bits & (kErrOverflow | kErrNodeOverflow))
+    return fail(h, VDBEDT_EOVERFLOW, "brick or node capacity exceeded; the field is incomplete until vdbedt_reset");
+  if (bits & kErrTimeout) return fail(h, VDBEDT_ETIMEOUT, "a bounded device-side wait gave up");
+  if (bits & kErrInvalidRecord) {
+    // invalid device records were skipped; report once
+    int zero = bits & ~kErrInvalidRecord;
+    cudaMemcpyAsync(h->g.counters + C_ERR, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
+    cudaStreamSynchronize(h->st);
+    return fail(h, VDBEDT_EINVAL, "invalid occupancy records in device memory were skipped");
+  }
+  return fail(h, VDBEDT_EINTERNAL, "device-side consistency check failed");
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+vdbedt_status ensure_stage(vdbedt_map* h, int64_t need) {
+  if (need <= h->stage_cap) return VDBEDT_OK;
+  int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
+  int4* p = nullptr;
+  cudaError_t e = cudaMalloc((void**)&p, sizeof(int4) * (size_t)cap);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stage alloc");
+  if (h->stage_n > 0) {
+    e = cudaMemcpyAsync(p, h->stage, sizeof(int4) * (size_t)h->stage_n, cudaMemcpyDeviceToDevice, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stage copy");
+  }
+  if (h->stage) {
+    cudaStreamSynchronize(h->st);
+    cudaFree(h->stage);
+  }
+  h->stage = p;
+  h->stage_cap = cap;
+  return VDBEDT_OK;
+}
+
+Tuning effective_tuning(const vdbedt_map* h) {
+  Tuning t = h->tune;
+  t.xy_run = item_run_xy(h->g, h->tune);
+  t.z_run = item_run_z(h->g, h->tune);
+  return t;
+}
+
+void mark(vdbedt_map* h, int i) {
+  if (h->profiling) cudaEventRecord(h->ev[i], h->st);
+}
+
+vdbedt_status do_global(vdbedt_map* h) {
+  h->epoch++;
+  const Tuning t = effective_tuning(h);
+  mark(h, 0);
+  CK(h, cudaMemsetAsync(h->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), h->st), "memset");
+  if (h->stage_n > 0) {
+    CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, false, h->epoch, nullptr, h->scr, h->st), "ingest");
+    h->stage_n = 0;
+  }
+  h->dense_pending = false;
+  mark(h, 1);
+  CK(h, launch_activation_full(h->g, h->st), "activation");
+  mark(h, 2);
+  CK(h, launch_build_items_full(h->g, t, h->epoch, h->xy_items, h->z_items, h->st), "items");
+  mark(h, 3);
+  CK(h, launch_xy_pass(h->g, t, h->xy_items, h->g.cap, h->st), "xy pass");
+  mark(h, 4);
+  CK(h, launch_z_pass(h->g, t, h->z_items, h->g.cap, h->st), "z pass");
+  mark(h, 5);
+  h->ev_recorded = h->profiling;
+  h->computed = true;
+  return VDBEDT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out) {
+  if (!cfg || !out) return fail(nullptr, VDBEDT_EINVAL, "null argument");
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, VDBEDT_EINVAL, "grid size must be >= 1");
+  if (cfg->dmax < 1 || cfg->dmax > VDBEDT_DMAX_LIMIT) return fail(nullptr, VDBEDT_EINVAL, "dmax out of range");
+  if (!(cfg->voxel_size > 0.f)) return fail(nullptr, VDBEDT_EINVAL, "voxel_size must be > 0");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    return fail(nullptr, VDBEDT_EINVAL, "no such CUDA device");
+  }
+  const int64_t BX = ceil_div(cfg->nx, 8), BY = ceil_div(cfg->ny, 8), BZ = ceil_div(cfg->nz, 8);
+  if (BX >= (1 << 21) || BY >= (1 << 21) || BZ >= (1 << 21) || BX * BY * BZ >= (int64_t)0xFFFFFFFFll)
+    return fail(nullptr, VDBEDT_EINVAL, "grid too large");
+  const int64_t NX = ceil_div(BX, 16), NY = ceil_div(BY, 16), NZ = ceil_div(BZ, 16);
+  int64_t cap = cfg->max_bricks > 0 ? std::min<int64_t>(cfg->max_bricks, BX * BY * BZ) : BX * BY * BZ;
+  if (cap * 512 >= (int64_t)0xFFFFFFFFll) return fail(nullptr, VDBEDT_EINVAL, "brick capacity too large (max 8M)");
+  const int64_t node_cap = NX * NY * NZ;
+
+  DeviceGuard guard(cfg->device);
+  vdbedt_map* h = new vdbedt_map();
+  h->cfg = *cfg;
+  h->device = cfg->device;
+  GridView& g = h->g;
+  g.nx = cfg->nx;
+  g.ny = cfg->ny;
+  g.nz = cfg->nz;
+  g.BX = (int)BX;
+  g.BY = (int)BY;
+  g.BZ = (int)BZ;
+  g.NX = (int)NX;
+  g.NY = (int)NY;
+  g.NZ = (int)NZ;
+  g.dmax = cfg->dmax;
+  g.R = (cfg->dmax + 6) / 8;
+  g.INF = cfg->dmax * cfg->dmax;
+  uint32_t hcap = 64;
+  while ((int64_t)hcap < 2 * node_cap) hcap <<= 1;
+  g.hmask = hcap - 1;
+  g.cap = (int)cap;
+  g.node_cap = (int)node_cap;
+
+  auto bail = [&](cudaError_t e, const char* where) {
+    vdbedt_status s = cuda_fail(nullptr, e, where);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    delete h;
+    return s;
+  };
+  cudaError_t e = cudaSuccess;
+  if (cfg->stream) {
+    h->st = (cudaStream_t)cfg->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(e, "stream");
+    h->own_stream = true;
+  }
+#define AL(ptr, count)                                   \
+  do {                                                   \
+    e = dalloc(h, &(ptr), (size_t)(count));              \
+    if (e != cudaSuccess) return bail(e, "device alloc"); \
+  } while (0)
+  AL(g.hslots, hcap);
+  AL(g.child, node_cap * kNodeBricks);
+  AL(g.amask, node_cap * 128);
+  AL(g.node_key, node_cap);
+  AL(g.xy_mark, node_cap * 1024);
+  AL(g.z_mark, node_cap * 1024);
+  AL(g.occ, cap * 8);
+  AL(g.g2, cap * kBrickVox);
+  AL(g.dist, cap * kBrickVox);
+  AL(g.bcoord, cap);
+  AL(g.bflags, cap);
+  AL(g.bepoch, cap);
+  AL(g.counters, C_NUM);
+  AL(h->xy_items, cap);
+  AL(h->z_items, cap);
+  AL(h->changed, cap);
+  AL(h->d_invalid, 4);
+#undef AL
+  e = cudaMallocHost((void**)&h->h_pinned, 64 * sizeof(int32_t));
+  if (e != cudaSuccess) return bail(e, "pinned alloc");
+  cudaMemsetAsync(g.hslots, 0xFF, sizeof(unsigned long long) * hcap, h->st);
+  cudaMemsetAsync(g.child, 0xFF, sizeof(int32_t) * (size_t)node_cap * kNodeBricks, h->st);
+  cudaMemsetAsync(g.amask, 0, sizeof(uint32_t) * (size_t)node_cap * 128, h->st);
+  cudaMemsetAsync(g.xy_mark, 0, sizeof(int32_t) * (size_t)node_cap * 1024, h->st);
+  cudaMemsetAsync(g.z_mark, 0, sizeof(int32_t) * (size_t)node_cap * 1024, h->st);
+  cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, h->st);
+  e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return bail(e, "init");
+  *out = h;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_destroy(vdbedt_handle h) {
+  if (!h) return VDBEDT_OK;
+  DeviceGuard guard(h->device);
+  cudaStreamSynchronize(h->st);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->stage) cudaFree(h->stage);
+  if (h->scr.buf) cudaFree(h->scr.buf);
+  if (h->io.buf) cudaFree(h->io.buf);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  for (int i = 0; i < 6; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  if (h->own_stream) cudaStreamDestroy(h->st);
+  delete h;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const uint8_t* occ, int64_t n,
+                                   int on_device) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (n < 0) return fail(h, VDBEDT_EINVAL, "negative record count");
+  if (n == 0) return VDBEDT_OK;
+  if (!xyz || !occ) return fail(h, VDBEDT_EINVAL, "null records");
+  DeviceGuard guard(h->device);
+  s = ensure_stage(h, h->stage_n + n);
+  if (s) return s;
+  int4* dst = h->stage + h->stage_n;
+  if (on_device) {
+    CK(h, launch_pack_records(xyz, occ, n, h->g.nx, h->g.ny, h->g.nz, dst, nullptr, h->st), "pack");
+  } else {
+    // copy the raw arrays, pack and validate on the device, then check before accepting
+    size_t bxyz = ((size_t)n * 12 + 255) & ~(size_t)255;
+    CK(h, ensure_scratch(h->io, bxyz + (size_t)n + 256), "io alloc");
+    int32_t* dxyz = (int32_t*)h->io.buf;
+    uint8_t* docc = (uint8_t*)h->io.buf + bxyz;
+    CK(h, cudaMemcpyAsync(dxyz, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, h->st), "h2d");
+    CK(h, cudaMemcpyAsync(docc, occ, (size_t)n, cudaMemcpyHostToDevice, h->st), "h2d");
+    CK(h, cudaMemsetAsync(h->d_invalid, 0, sizeof(int32_t), h->st), "memset");
+    CK(h, launch_pack_records(dxyz, docc, n, h->g.nx, h->g.ny, h->g.nz, dst, h->d_invalid, h->st), "pack");
+    CK(h, cudaMemcpyAsync(h->h_pinned, h->d_invalid, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st), "d2h");
+    CK(h, cudaStreamSynchronize(h->st), "sync");
+    if (h->h_pinned[0] != 0)
+      return fail(h, VDBEDT_EINVAL, "record outside the grid or occupancy value > 1; call rejected");
+  }
+  h->stage_n += n;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_set_occupancy_dense(vdbedt_handle h, const uint8_t* grid, int on_device) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (!grid) return fail(h, VDBEDT_EINVAL, "null grid");
+  DeviceGuard guard(h->device);
+  s = vdbedt_reset(h);
+  if (s) return s;
+  const uint8_t* src = grid;
+  if (!on_device) {
+    size_t bytes = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    CK(h, ensure_scratch(h->io, bytes), "io alloc");
+    CK(h, cudaMemcpyAsync(h->io.buf, grid, bytes, cudaMemcpyHostToDevice, h->st), "h2d");
+    src = (const uint8_t*)h->io.buf;
+  }
+  CK(h, launch_ingest_dense(h->g, src, h->st), "dense ingest");
+  if (!on_device) CK(h, cudaStreamSynchronize(h->st), "sync");
+  h->dense_pending = true;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_reset(vdbedt_handle h) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  DeviceGuard guard(h->device);
+  CK(h, launch_reset(h->g, h->st), "reset");
+  h->stage_n = 0;
+  h->epoch = 0;
+  h->computed = false;
+  h->dense_pending = false;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_global(vdbedt_handle h) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  DeviceGuard guard(h->device);
+  return do_global(h);
+}
+
+vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  DeviceGuard guard(h->device);
+  const int64_t nrec = h->stage_n;
+  if (!h->computed || h->dense_pending) {
+    s = do_global(h);
+    if (s) return s;
+  } else {
+    h->epoch++;
+    const Tuning t = effective_tuning(h);
+    mark(h, 0);
+    CK(h, cudaMemsetAsync(h->g.counters + C_XY_ITEMS, 0, sizeof(int32_t) * 6, h->st), "memset");
+    CK(h, cudaMemsetAsync(h->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), h->st), "memset");
+    if (h->stage_n > 0) {
+      CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, true, h->epoch, h->changed, h->scr, h->st), "ingest");
+      h->stage_n = 0;
+    }
+    mark(h, 1);
+    CK(h, launch_incremental_mark(h->g, t, h->epoch, h->changed, h->xy_items, h->z_items, h->st), "mark");
+    mark(h, 2);
+    mark(h, 3);
+    CK(h, launch_xy_pass(h->g, t, h->xy_items, h->g.cap, h->st), "xy pass");
+    mark(h, 4);
+    CK(h, launch_z_pass(h->g, t, h->z_items, h->g.cap, h->st), "z pass");
+    mark(h, 5);
+    h->ev_recorded = h->profiling;
+  }
+  if (stats) {
+    CK(h, cudaMemcpyAsync(h->h_pinned, h->g.counters, sizeof(int32_t) * C_NUM, cudaMemcpyDeviceToHost, h->st), "d2h");
+    s = device_errors(h);  // synchronises
+    if (s) return s;
+    const int32_t* c = h->h_pinned;
+    stats->records = nrec;
+    stats->net_flips = c[C_FLIPS];
+    stats->changed_bricks = c[C_CHANGED];
+    stats->xy_items = c[C_XY_ITEMS];
+    stats->z_items = c[C_Z_ITEMS];
+    stats->new_bricks = c[C_NEW_BRICKS];
+  }
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_query(vdbedt_handle h, const int32_t* xyz, int64_t n, int32_t* out_sqdist, int on_device) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!xyz || !out_sqdist))) return fail(h, VDBEDT_EINVAL, "bad query arguments");
+  if (n == 0) return VDBEDT_OK;
+  DeviceGuard guard(h->device);
+  if (on_device) {
+    CK(h, launch_query(h->g, xyz, n, out_sqdist, h->st), "query");
+    return VDBEDT_OK;
+  }
+  size_t bx = ((size_t)n * 12 + 255) & ~(size_t)255;
+  CK(h, ensure_scratch(h->io, bx + (size_t)n * 4), "io alloc");
+  int32_t* dxyz = (int32_t*)h->io.buf;
+  int32_t* dout = (int32_t*)((char*)h->io.buf + bx);
+  CK(h, cudaMemcpyAsync(dxyz, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, h->st), "h2d");
+  CK(h, launch_query(h->g, dxyz, n, dout, h->st), "query");
+  s = device_errors(h);
+  if (s) return s;
+  CK(h, cudaMemcpyAsync(out_sqdist, dout, (size_t)n * 4, cudaMemcpyDeviceToHost, h->st), "d2h");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (!out) return fail(h, VDBEDT_EINVAL, "null output");
+  DeviceGuard guard(h->device);
+  size_t bytes = (size_t)h->g.nx * h->g.ny * h->g.nz * 4;
+  if (on_device) {
+    CK(h, launch_export_dense(h->g, out, h->st), "export");
+    return VDBEDT_OK;
+  }
+  CK(h, ensure_scratch(h->io, bytes), "io alloc");
+  CK(h, launch_export_dense(h->g, (int32_t*)h->io.buf, h->st), "export");
+  s = device_errors(h);
+  if (s) return s;
+  CK(h, cudaMemcpyAsync(out, h->io.buf, bytes, cudaMemcpyDeviceToHost, h->st), "d2h");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_clearance_forward(vdbedt_handle h, const float* pts, int64_t T, int64_t P, float tau,
+                                       float* cost) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (T < 0 || P < 0 || (T > 0 && (!pts || !cost))) return fail(h, VDBEDT_EINVAL, "bad clearance arguments");
+  if (h->g.nx < 2 || h->g.ny < 2 || h->g.nz < 2) return fail(h, VDBEDT_EINVAL, "grid needs >= 2 voxels per axis");
+  DeviceGuard guard(h->device);
+  CK(h, launch_clearance_fwd(h->g, h->cfg.voxel_size, pts, T, P, tau, cost, h->st), "clearance fwd");
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_clearance_backward(vdbedt_handle h, const float* pts, int64_t T, int64_t P, float tau,
+                                        const float* grad_cost, float* grad_pts) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (T < 0 || P < 0 || (T > 0 && P > 0 && (!pts || !grad_cost || !grad_pts)))
+    return fail(h, VDBEDT_EINVAL, "bad clearance arguments");
+  if (h->g.nx < 2 || h->g.ny < 2 || h->g.nz < 2) return fail(h, VDBEDT_EINVAL, "grid needs >= 2 voxels per axis");
+  DeviceGuard guard(h->device);
+  CK(h, launch_clearance_bwd(h->g, h->cfg.voxel_size, pts, T, P, tau, grad_cost, grad_pts, h->st), "clearance bwd");
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_set_tuning(vdbedt_handle h, const vdbedt_tuning* t) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (!t) return fail(h, VDBEDT_EINVAL, "null tuning");
+  auto ok_run = [](int r) { return r == 0 || r == 4 || r == 8 || r == 16; };
+  if (!ok_run(t->xy_run) || !ok_run(t->z_run) || t->variant < 0 || t->variant > 2)
+    return fail(h, VDBEDT_EINVAL, "bad tuning");
+  h->tune.xy_run = t->xy_run ? t->xy_run : 8;
+  h->tune.z_run = t->z_run ? t->z_run : 8;
+  h->tune.variant = t->variant ? t->variant : 1;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_synchronize(vdbedt_handle h) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  DeviceGuard guard(h->device);
+  return device_errors(h);
+}
+
+vdbedt_status vdbedt_get_info(vdbedt_handle h, vdbedt_info* info) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (!info) return fail(h, VDBEDT_EINVAL, "null info");
+  DeviceGuard guard(h->device);
+  s = device_errors(h);
+  if (s) return s;
+  CK(h, cudaMemcpy(h->h_pinned, h->g.counters, sizeof(int32_t) * C_NUM, cudaMemcpyDeviceToHost), "d2h");
+  int nb = std::min(h->h_pinned[C_NBRICKS], h->g.cap);
+  std::vector<uint32_t> flags((size_t)std::max(nb, 1));
+  if (nb > 0) CK(h, cudaMemcpy(flags.data(), h->g.bflags, sizeof(uint32_t) * nb, cudaMemcpyDeviceToHost), "d2h");
+  int64_t obst = 0, fin = 0;
+  for (int i = 0; i < nb; ++i) {
+    obst += (flags[i] & F_OBST) != 0;
+    fin += (flags[i] & F_FINITE) != 0;
+  }
+  info->allocated_bricks = nb;
+  info->obstacle_bricks = obst;
+  info->finite_bricks = fin;
+  info->capacity_bricks = h->g.cap;
+  info->nodes = h->h_pinned[C_NNODES];
+  info->device_bytes = (int64_t)(h->device_bytes + h->scr.bytes + h->io.bytes + sizeof(int4) * h->stage_cap);
+  info->R = h->g.R;
+  info->error_bits = h->h_pinned[C_ERR];
+  return VDBEDT_OK;
+}
+
+void* vdbedt_stream(vdbedt_handle h) { return h ? (void*)h->st : nullptr; }
+
+vdbedt_status vdbedt_set_profiling(vdbedt_handle h, int on) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  DeviceGuard guard(h->device);
+  if (on && !h->ev[0])
+    for (int i = 0; i < 6; ++i) CK(h, cudaEventCreate(&h->ev[i]), "event");
+  h->profiling = on != 0;
+  h->ev_recorded = false;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_get_phase_times(vdbedt_handle h, vdbedt_phase_times* out) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (!out) return fail(h, VDBEDT_EINVAL, "null output");
+  if (!h->ev_recorded) return fail(h, VDBEDT_EINVAL, "no profiled transform since profiling was enabled");
+  DeviceGuard guard(h->device);
+  CK(h, cudaEventSynchronize(h->ev[5]), "event sync");
+  float ms[5];
+  for (int i = 0; i < 5; ++i) CK(h, cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]), "event time");
+  out->ingest_ms = ms[0];
+  out->activation_ms = ms[1];
+  out->items_ms = ms[2];
+  out->xy_ms = ms[3];
+  out->z_ms = ms[4];
+  return VDBEDT_OK;
+}
+
+int64_t vdbedt_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+const char* vdbedt_last_error(vdbedt_handle h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+vdbedt_status vdbedt_global_batched(vdbedt_handle* hs, int32_t k) {
+  if (k < 0 || (k > 0 && !hs)) return fail(nullptr, VDBEDT_EINVAL, "bad batch");
+  for (int32_t i = 0; i < k; ++i) {
+    vdbedt_status s = vdbedt_global(hs[i]);
+    if (s) return s;
+  }
+  return VDBEDT_OK;
+}
+
+}  // extern "C"
+
+// ---- record packing ----
+namespace vdbedt {
+namespace {
+__global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* __restrict__ occ, int64_t n, int nx,
+                               int ny, int nz, int4* __restrict__ dst, int32_t* invalid) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    int v = occ[i];
+    bool ok = (unsigned)x < (unsigned)nx && (unsigned)y < (unsigned)ny && (unsigned)z < (unsigned)nz && v <= 1;
+    if (!ok) {
+      if (invalid) atomicAdd(invalid, 1);
+      v = 2;  // skipped (and reported) by the ingest kernels
+    }
+    dst[i] = make_int4(x, y, z, v);
+  }
+}
+}  // namespace
+
+cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, int nx, int ny, int nz, int4* dst,
+                                int32_t* invalid, cudaStream_t st) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  VDB_LAUNCH(k_pack_records, (unsigned)b, 256, 0, st, xyz, occ, n, nx, ny, nz, dst, invalid);
+  return cudaGetLastError();
+}
+}  // namespace vdbedt

@@ -1,0 +1,523 @@
+// Building and maintaining the sparse brick grid on the device.
+//
+//   ingest   staged occupancy records -> brick keys -> stable radix sort -> unique -> compaction
+//            -> new bricks (node found or inserted in the hashed level, child slot claimed) ->
+//            occupancy bits set.  Several records for one voxel: the last one wins (resolved by a
+//            stable sort of (voxel, record index) whenever a record clears a voxel or flips are
+//            tracked; a batch of pure "set" records needs no ordering).
+//   activation  the compute set: every brick within Chebyshev brick radius R of a brick holding
+//            an obstacle (the paper grows the tree only where the limited transform reaches,
+//            Sec. IV-A); marked in the per-node 4096-bit masks, then absent bricks are allocated.
+//   items    work lists for the passes: runs of bricks along y (in-plane pass) and along z.
+//   incremental marking  bricks whose occupancy changed -> in-plane dirty set (same z, within R
+//            in x and y) and z dirty set (within R in x, y and z) -> work lists.
+#include <cuda_fp16.h>
+
+#include "vdbedt_internal.cuh"
+
+namespace vdbedt {
+
+namespace {
+
+constexpr int kT = 256;
+
+inline unsigned blocks_for(int64_t n, int t = kT) {
+  int64_t b = (n + t - 1) / t;
+  if (b < 1) b = 1;
+  if (b > (1 << 30)) b = 1 << 30;
+  return (unsigned)b;
+}
+
+inline int bits_for(uint64_t maxval) {
+  int b = 1;
+  while (b < 32 && (1ull << b) <= maxval) ++b;
+  return b;
+}
+
+// ---- reset ----
+__global__ void k_reset_nodes(GridView g) {
+  const int nn = min(g.counters[C_NNODES], g.node_cap);
+  const int64_t total = (int64_t)nn * kNodeBricks;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    g.child[i] = kNoSlot;
+    if ((i & 3) == 0) {
+      int64_t j = i >> 2;  // 1024 marks per node
+      g.xy_mark[j] = 0;
+      g.z_mark[j] = 0;
+    }
+    if ((i & 31) == 0) g.amask[i >> 5] = 0u;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= (int64_t)g.hmask;
+       i += (int64_t)gridDim.x * blockDim.x)
+    g.hslots[i] = ~0ull;
+}
+
+// ---- brick allocation ----
+// Claim the child entry of brick (bx,by,bz) in node `node` and give it a pool slot.  Returns the
+// slot (new or existing), or -1 on overflow / concurrent claim.  `init_g2` fills g2 with dmax^2
+// (needed for bricks added by an incremental update whose in-plane pass may not revisit them).
+__device__ int claim_brick(const GridView& g, int node, int bx, int by, int bz, bool init_g2, bool* created) {
+  int* e = &g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
+  int cur = *e;
+  *created = false;
+  if (cur >= 0) return cur;
+  if (cur == kClaiming) return -1;
+  if (atomicCAS(e, kNoSlot, kClaiming) != kNoSlot) return -1;
+  int slot = atomicAdd(&g.counters[C_NBRICKS], 1);
+  if (slot >= g.cap) {
+    set_error(g, kErrOverflow);
+    return -1;  // entry stays "claiming": reads treat it as absent
+  }
+  for (int w = 0; w < 8; ++w) g.occ[(size_t)slot * 8 + w] = 0ull;
+  if (init_g2) {
+    uint16_t inf = 0;
+    {
+      // fp16 pattern of INF for the half kernels, plain integer for the generic ones
+      if (g.dmax <= 45 && g.R <= 6) {
+        __half h = __int2half_rn(g.INF);
+        inf = *reinterpret_cast<uint16_t*>(&h);
+      } else {
+        inf = (uint16_t)g.INF;
+      }
+    }
+    uint32_t p = (uint32_t)inf | ((uint32_t)inf << 16);
+    uint4* dst = reinterpret_cast<uint4*>(g.g2 + (size_t)slot * kBrickVox);
+    for (int q = 0; q < 64; ++q) dst[q] = make_uint4(p, p, p, p);
+    int4* dd = reinterpret_cast<int4*>(g.dist + (size_t)slot * kBrickVox);
+    for (int q = 0; q < 128; ++q) dd[q] = make_int4(g.INF, g.INF, g.INF, g.INF);
+  }
+  g.bcoord[slot] = make_int4(bx, by, bz, node);
+  g.bflags[slot] = 0u;
+  g.bepoch[slot] = 0;
+  __threadfence();
+  atomicExch(e, slot);
+  *created = true;
+  return slot;
+}
+
+__device__ __forceinline__ bool brick_has_obstacle(const GridView& g, int s) {
+  const ulonglong2* w = reinterpret_cast<const ulonglong2*>(g.occ + (size_t)s * 8);
+  ulonglong2 a = w[0], b = w[1], c = w[2], d = w[3];
+  return (a.x | a.y | b.x | b.y | c.x | c.y | d.x | d.y) != 0ull;
+}
+
+// ---- record ingest ----
+__device__ __forceinline__ bool rec_valid(const GridView& g, int4 r) {
+  return (unsigned)r.x < (unsigned)g.nx && (unsigned)r.y < (unsigned)g.ny && (unsigned)r.z < (unsigned)g.nz &&
+         (unsigned)r.w <= 1u;
+}
+
+__global__ void k_rec_brick_keys(GridView g, const int4* __restrict__ rec, int64_t n, uint32_t* __restrict__ keys) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  uint32_t key = 0xFFFFFFFFu;
+  bool zero = false, bad = false;
+  if (i < n) {
+    int4 r = rec[i];
+    if (!rec_valid(g, r)) {
+      bad = true;
+    } else if (r.w == 1) {
+      key = (uint32_t)((r.x >> 3) + g.BX * ((r.y >> 3) + g.BY * (r.z >> 3)));
+    } else {
+      zero = true;
+    }
+  }
+  // drop a key equal to the previous lane's (records of one brick tend to be adjacent)
+  uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+  if (lane > 0 && prev == key) key = 0xFFFFFFFFu;
+  if (i < n) keys[i] = key;
+  if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+}
+
+__global__ void k_head_flags(const uint32_t* __restrict__ keys, int64_t n, uint32_t limit, int32_t* __restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t k = keys[i];
+  flag[i] = (k < limit && (i == 0 || keys[i - 1] != k)) ? 1 : 0;
+}
+
+__global__ void k_compact_keys(const uint32_t* __restrict__ keys, const int32_t* __restrict__ flag,
+                               const int32_t* __restrict__ pos, int64_t n, uint32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) out[pos[i]] = keys[i];
+}
+
+__global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__ uniq, int64_t n, bool init) {
+  const int cnt = min((int64_t)g.counters[C_UNIQUE], n);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t lb = uniq[j];
+    int bx = (int)(lb % (uint32_t)g.BX);
+    int rest = (int)(lb / (uint32_t)g.BX);
+    int by = rest % g.BY, bz = rest / g.BY;
+    int node = get_or_create_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+    if (node < 0) continue;
+    bool created;
+    claim_brick(g, node, bx, by, bz, init, &created);
+    if (created) atomicAdd(&g.counters[C_NEW_BRICKS], 1);
+  }
+}
+
+// All records set voxels: OR the bits in, combining lanes that hit the same 64-bit word.
+__global__ void k_apply_set_only(GridView g, const int4* __restrict__ rec, int64_t n) {
+  if (g.counters[C_HAS_ZERO]) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long* word = nullptr;
+  uint32_t lo = 0, hi = 0;
+  if (i < n) {
+    int4 r = rec[i];
+    if (rec_valid(g, r) && r.w == 1) {
+      int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
+      if (s >= 0) {
+        word = &g.occ[(size_t)s * 8 + (r.z & 7)];
+        int bit = (r.x & 7) + 8 * (r.y & 7);
+        if (bit < 32)
+          lo = 1u << bit;
+        else
+          hi = 1u << (bit - 32);
+      }
+    }
+  }
+  unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)word);
+  lo = __reduce_or_sync(peers, lo);
+  hi = __reduce_or_sync(peers, hi);
+  if (word && (threadIdx.x & 31) == __ffs(peers) - 1)
+    atomicOr(word, (unsigned long long)lo | ((unsigned long long)hi << 32));
+}
+
+// (voxel key, record index) for the ordered path: voxel key = slot * 512 + voxel in brick.
+__global__ void k_rec_voxel_keys(GridView g, const int4* __restrict__ rec, int64_t n, bool force,
+                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+  const bool on = force || g.counters[C_HAS_ZERO];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) g.counters[C_RECORDS] = on ? (int32_t)n : 0;
+  if (!on) return;
+  if (i >= n) return;
+  uint32_t key = 0xFFFFFFFFu;
+  int4 r = rec[i];
+  if (rec_valid(g, r)) {
+    int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
+    if (s >= 0) key = (uint32_t)s * 512u + (uint32_t)((r.x & 7) + 8 * (r.y & 7) + 64 * (r.z & 7));
+  }
+  keys[i] = key;
+  idx[i] = (uint32_t)i;
+}
+
+// The last record of each voxel decides its bit.  Flips are counted; with `track` the brick is
+// appended once per epoch to the changed list.
+__global__ void k_apply_last(GridView g, const int4* __restrict__ rec, const uint32_t* __restrict__ keys,
+                             const uint32_t* __restrict__ idx, int64_t n, bool force, bool track, int epoch,
+                             int32_t* __restrict__ changed) {
+  if (!force && !g.counters[C_HAS_ZERO]) return;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool flip = false;
+  if (j < n) {
+    uint32_t k = keys[j];
+    const uint32_t lim = (uint32_t)g.cap * 512u;
+    if (k < lim && (j + 1 == n || keys[j + 1] != k)) {
+      int4 r = rec[idx[j]];
+      int s = (int)(k >> 9), v = (int)(k & 511);
+      unsigned long long bit = 1ull << (v & 63);
+      unsigned long long* word = &g.occ[(size_t)s * 8 + (v >> 6)];
+      bool cur = (*word & bit) != 0ull;
+      if (cur != (r.w == 1)) {
+        atomicXor(word, bit);
+        flip = true;
+        if (track && atomicExch(&g.bepoch[s], epoch) != epoch) {
+          int p = atomicAdd(&g.counters[C_CHANGED], 1);
+          changed[p] = s;
+        }
+      }
+    }
+  }
+  unsigned m = __ballot_sync(0xffffffffu, flip);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(&g.counters[C_FLIPS], __popc(m));
+}
+
+// ---- dense ingest ----
+// One warp per brick of the grid: each lane reads two 8-voxel x-rows; a brick with any occupied
+// voxel is allocated and its 64-byte mask written.
+__global__ void k_ingest_dense(GridView g, const uint8_t* __restrict__ grid) {
+  const int64_t nbr = (int64_t)g.BX * g.BY * g.BZ;
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = wid; b < nbr; b += nw) {
+    int bx = (int)(b % g.BX), by = (int)((b / g.BX) % g.BY), bz = (int)(b / ((int64_t)g.BX * g.BY));
+    uint8_t rows[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int r = lane * 2 + q;  // byte index y + 8 z
+      int y = r & 7, z = r >> 3;
+      int gy = by * 8 + y, gz = bz * 8 + z;
+      uint8_t v = 0;
+      if (gy < g.ny && gz < g.nz) {
+        const uint8_t* src = grid + ((size_t)gz * g.ny + gy) * g.nx + (size_t)bx * 8;
+        int nxv = min(8, g.nx - bx * 8);
+        for (int x = 0; x < nxv; ++x) v |= (uint8_t)((src[x] != 0) << x);
+      }
+      rows[q] = v;
+    }
+    bool any = __any_sync(0xffffffffu, (rows[0] | rows[1]) != 0);
+    if (!any) continue;
+    int slot = -1;
+    if (lane == 0) {
+      int node = get_or_create_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+      bool created = false;
+      if (node >= 0) slot = claim_brick(g, node, bx, by, bz, true, &created);
+      if (created) atomicAdd(&g.counters[C_NEW_BRICKS], 1);
+    }
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot < 0) continue;
+    uint8_t* dst = reinterpret_cast<uint8_t*>(g.occ) + (size_t)slot * 64;
+    dst[lane * 2] = rows[0];
+    dst[lane * 2 + 1] = rows[1];
+  }
+}
+
+// ---- activation ----
+__global__ void k_obstacle_flags(GridView g) {
+  const int nb = min(g.counters[C_NBRICKS], g.cap);
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
+    bool obst = brick_has_obstacle(g, s);
+    uint32_t f = g.bflags[s];
+    g.bflags[s] = obst ? (f | F_OBST) : (f & ~F_OBST);
+    if (obst) atomicAdd(&g.counters[C_OBST], 1);
+  }
+}
+
+// Mark bricks within Chebyshev radius R of brick (bx,by,bz): one thread per (dy, dz) row.
+__device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int dy, int dz) {
+  const int R = g.R;
+  int y = by + dy, z = bz + dz;
+  if ((unsigned)y >= (unsigned)g.BY || (unsigned)z >= (unsigned)g.BZ) return;
+  int x0 = max(bx - R, 0), x1 = min(bx + R, g.BX - 1);
+  while (x0 <= x1) {
+    int seg_end = min(x1, (x0 | 15));
+    int node = get_or_create_node(g, (uint32_t)node_key_of(g, x0, y, z));
+    if (node >= 0) {
+      int lx0 = x0 & 15, lx1 = seg_end & 15;
+      uint32_t bitsx = (lx1 - lx0 == 31) ? 0xFFFFFFFFu : (((1u << (lx1 - lx0 + 1)) - 1u) << lx0);
+      int ly = y & 15, lz = z & 15;
+      int word = (ly >> 1) + 8 * lz;
+      atomicOr(&g.amask[(size_t)node * 128 + word], bitsx << (16 * (ly & 1)));
+    }
+    x0 = seg_end + 1;
+  }
+}
+
+__global__ void k_dilate_obstacles(GridView g) {
+  const int nb = min(g.counters[C_NBRICKS], g.cap);
+  const int side = 2 * g.R + 1;
+  const int rows = side * side;
+  const int64_t total = (int64_t)nb * rows;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int s = (int)(i / rows), r = (int)(i % rows);
+    if (!(g.bflags[s] & F_OBST)) continue;
+    int4 c = g.bcoord[s];
+    mark_dilation_row(g, c.x, c.y, c.z, r % side - g.R, r / side - g.R);
+  }
+}
+
+// Allocate every marked brick that has no storage yet: one block per node.
+__global__ void k_alloc_marked(GridView g, bool init_g2) {
+  const int nn = min(g.counters[C_NNODES], g.node_cap);
+  for (int node = blockIdx.x; node < nn; node += gridDim.x) {
+    const int key = g.node_key[node];
+    const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+    for (int l = threadIdx.x; l < kNodeBricks; l += blockDim.x) {
+      if (!((g.amask[(size_t)node * 128 + (l >> 5)] >> (l & 31)) & 1u)) continue;
+      if (g.child[(size_t)node * kNodeBricks + l] >= 0) continue;
+      int bx = nxn * 16 + (l & 15), by = nyn * 16 + ((l >> 4) & 15), bz = nzn * 16 + (l >> 8);
+      bool created;
+      claim_brick(g, node, bx, by, bz, init_g2, &created);
+      if (created) atomicAdd(&g.counters[C_NEW_BRICKS], 1);
+    }
+  }
+}
+
+__global__ void k_clear_amask(GridView g) {
+  const int nn = min(g.counters[C_NNODES], g.node_cap);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
+       i += (int64_t)gridDim.x * blockDim.x)
+    g.amask[i] = 0u;
+}
+
+// ---- work items ----
+__device__ void queue_runs(const GridView& g, int bx, int by, int bz, int node, int xy_run, int z_run, int epoch,
+                           bool want_xy, bool want_z, unsigned long long* xy_items, unsigned long long* z_items) {
+  const int lx = bx & 15, ly = by & 15, lz = bz & 15;
+  if (want_xy) {
+    int run = lx + 16 * (lz + 16 * (ly / xy_run));
+    if (atomicExch(&g.xy_mark[(size_t)node * 1024 + run], epoch) != epoch) {
+      int p = atomicAdd(&g.counters[C_XY_ITEMS], 1);
+      if (p < g.cap) xy_items[p] = pack_brick(bx, by - (ly % xy_run), bz);
+    }
+  }
+  if (want_z) {
+    int run = lx + 16 * (ly + 16 * (lz / z_run));
+    if (atomicExch(&g.z_mark[(size_t)node * 1024 + run], epoch) != epoch) {
+      int p = atomicAdd(&g.counters[C_Z_ITEMS], 1);
+      if (p < g.cap) z_items[p] = pack_brick(bx, by, bz - (lz % z_run));
+    }
+  }
+}
+
+__global__ void k_items_all(GridView g, int xy_run, int z_run, int epoch, unsigned long long* xy_items,
+                            unsigned long long* z_items) {
+  const int nb = min(g.counters[C_NBRICKS], g.cap);
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
+    int4 c = g.bcoord[s];
+    queue_runs(g, c.x, c.y, c.z, c.w, xy_run, z_run, epoch, true, true, xy_items, z_items);
+  }
+}
+
+// ---- incremental ----
+// For every changed brick: refresh its obstacle flag; if it holds obstacles, mark its dilation.
+__global__ void k_changed_flags_dilate(GridView g, const int32_t* __restrict__ changed) {
+  const int nc = min(g.counters[C_CHANGED], g.cap);
+  const int side = 2 * g.R + 1, rows = side * side;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nc * rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int s = changed[i / rows], r = (int)(i % rows);
+    bool obst = brick_has_obstacle(g, s);
+    if (r == 0) {
+      uint32_t f = g.bflags[s];
+      g.bflags[s] = obst ? (f | F_OBST) : (f & ~F_OBST);
+    }
+    if (obst) {
+      int4 c = g.bcoord[s];
+      mark_dilation_row(g, c.x, c.y, c.z, r % side - g.R, r / side - g.R);
+    }
+  }
+}
+
+// Dirty sets of an update: every stored brick within R (Chebyshev) of a changed brick needs its z
+// pass; those in the changed brick's z layer also need the in-plane pass.
+__global__ void k_mark_dirty(GridView g, const int32_t* __restrict__ changed, int xy_run, int z_run, int epoch,
+                             unsigned long long* xy_items, unsigned long long* z_items) {
+  const int nc = min(g.counters[C_CHANGED], g.cap);
+  const int side = 2 * g.R + 1, vol = side * side * side;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nc * vol;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int s = changed[i / vol], r = (int)(i % vol);
+    int dx = r % side - g.R, dy = (r / side) % side - g.R, dz = r / (side * side) - g.R;
+    int4 c = g.bcoord[s];
+    int bx = c.x + dx, by = c.y + dy, bz = c.z + dz;
+    if ((unsigned)bx >= (unsigned)g.BX || (unsigned)by >= (unsigned)g.BY || (unsigned)bz >= (unsigned)g.BZ) continue;
+    int node = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+    if (node < 0) continue;
+    if (g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] < 0) continue;
+    queue_runs(g, bx, by, bz, node, xy_run, z_run, epoch, dz == 0, true, xy_items, z_items);
+  }
+}
+
+}  // namespace
+
+cudaError_t ensure_scratch(Scratch& s, size_t bytes) {
+  if (s.bytes >= bytes) return cudaSuccess;
+  if (s.buf) cudaFree(s.buf);
+  s.buf = nullptr;
+  s.bytes = 0;
+  size_t want = bytes + bytes / 4 + 4096;
+  cudaError_t e = cudaMalloc(&s.buf, want);
+  if (e != cudaSuccess) return e;
+  s.bytes = want;
+  return cudaSuccess;
+}
+
+cudaError_t launch_reset(const GridView& g, cudaStream_t st) {
+  VDB_LAUNCH(k_reset_nodes, 1024, kT, 0, st, g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, st);
+}
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Apply staged records.  Bricks of "set" records are found or created through a stable radix
+// sort of brick keys, a unique pass and a compaction.  Bits: without tracking and when every
+// record sets a voxel, OR them in directly; otherwise (some record clears a voxel, or tracking
+// is on) sort (voxel key, record index) stably and let each voxel's last record decide.  With
+// tracking, each flipped voxel's brick is appended once to `changed`.
+cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n, bool track, int epoch,
+                                  int32_t* changed, Scratch& scr, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const size_t nb4 = align_up((size_t)n * 4);
+  const size_t need = 6 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(n));
+  cudaError_t e = ensure_scratch(scr, need);
+  if (e != cudaSuccess) return e;
+  char* p = (char*)scr.buf;
+  uint32_t* ka = (uint32_t*)p;
+  p += nb4;
+  uint32_t* kb = (uint32_t*)p;
+  p += nb4;
+  uint32_t* va = (uint32_t*)p;
+  p += nb4;
+  uint32_t* vb = (uint32_t*)p;
+  p += nb4;
+  int32_t* flag = (int32_t*)p;
+  p += nb4;
+  int32_t* pos = (int32_t*)p;
+  p += nb4;
+  void* rtemp = p;
+  p += align_up(radix_temp_bytes(n));
+  void* stemp = p;
+
+  const unsigned nbk = blocks_for(n);
+  const uint64_t nbr = (uint64_t)g.BX * g.BY * g.BZ;
+  VDB_LAUNCH(k_rec_brick_keys, nbk, kT, 0, st, g, rec, n, ka);
+  // the sentinel 0xFFFFFFFF sorts after every key below 2^bits
+  e = radix_sort_u32(ka, kb, nullptr, nullptr, n, nullptr, bits_for(nbr), rtemp, st);
+  if (e != cudaSuccess) return e;
+  VDB_LAUNCH(k_head_flags, nbk, kT, 0, st, kb, n, (uint32_t)nbr, flag);
+  e = exclusive_scan_i32(flag, pos, n, g.counters + C_UNIQUE, stemp, st);
+  if (e != cudaSuccess) return e;
+  VDB_LAUNCH(k_compact_keys, nbk, kT, 0, st, kb, flag, pos, n, ka);
+  VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, ka, n, track);
+  if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n);
+  // ordered path; its element count is 0 on the device when it is not needed
+  VDB_LAUNCH(k_rec_voxel_keys, nbk, kT, 0, st, g, rec, n, track, ka, va);
+  e = radix_sort_u32(ka, kb, va, vb, n, g.counters + C_RECORDS, bits_for((uint64_t)g.cap * 512ull), rtemp, st);
+  if (e != cudaSuccess) return e;
+  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, kb, vb, n, track, track, epoch, changed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st) {
+  int64_t nbr = (int64_t)g.BX * g.BY * g.BZ;
+  int64_t threads = nbr * 32;
+  unsigned blocks = blocks_for(threads);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  VDB_LAUNCH(k_ingest_dense, blocks, kT, 0, st, g, grid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_activation_full(const GridView& g, cudaStream_t st) {
+  VDB_LAUNCH(k_clear_amask, 256, kT, 0, st, g);
+  VDB_LAUNCH(k_obstacle_flags, 1024, kT, 0, st, g);
+  VDB_LAUNCH(k_dilate_obstacles, 4096, kT, 0, st, g);
+  VDB_LAUNCH(k_alloc_marked, 1024, kT, 0, st, g, false);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, unsigned long long* xy_items,
+                                    unsigned long long* z_items, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(g.counters + C_XY_ITEMS, 0, 2 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  VDB_LAUNCH(k_items_all, 1024, kT, 0, st, g, t.xy_run, t.z_run, epoch, xy_items, z_items);
+  return cudaGetLastError();
+}
+
+// Incremental: records were already applied with flip tracking (changed list filled).
+cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, int epoch, const int32_t* changed,
+                                    unsigned long long* xy_items, unsigned long long* z_items, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(g.counters + C_XY_ITEMS, 0, 2 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  VDB_LAUNCH(k_changed_flags_dilate, 1024, kT, 0, st, g, changed);
+  VDB_LAUNCH(k_alloc_marked, 1024, kT, 0, st, g, true);
+  VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.xy_run, t.z_run, epoch, xy_items, z_items);
+  return cudaGetLastError();
+}
+
+}  // namespace vdbedt

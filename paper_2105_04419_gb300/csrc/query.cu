@@ -1,0 +1,189 @@
+// Reading the field: point queries, dense export, and the differentiable clearance cost.
+//
+// Query: D at voxel coordinates through the two-level interior (hash probe, child table); voxels
+// outside the grid or in unstored bricks return the background dmax^2 (the paper's tile value,
+// Sec. IV-A).
+//
+// Clearance cost (Eq. 2, clearance term, as a squared hinge): per point p (metres),
+//   u = p / vs (float32), i0 = floor(u) clamped to [0, n-2], t = u - i0,
+//   corner distance d_c = vs * sqrt(D_c), d = trilinear(d_c, t), c = max(0, tau - d)^2,
+//   cost[traj] = sum of c over the trajectory's points.
+// Backward: dc/dp = -2 max(0, tau - d) (1 / vs) grad_t(trilinear), scaled by the upstream
+// gradient of the trajectory's cost.  One warp per trajectory, points strided over the lanes,
+// a warp shuffle sum for the forward.
+#include "vdbedt_internal.cuh"
+
+namespace vdbedt {
+
+namespace {
+
+__device__ __forceinline__ int sqdist_at(const GridView& g, int x, int y, int z) {
+  if ((unsigned)x >= (unsigned)g.nx || (unsigned)y >= (unsigned)g.ny || (unsigned)z >= (unsigned)g.nz) return g.INF;
+  int s = find_brick(g, x >> 3, y >> 3, z >> 3);
+  if (s < 0) return g.INF;
+  return g.dist[(size_t)s * kBrickVox + (x & 7) + 8 * (y & 7) + 64 * (z & 7)];
+}
+
+__global__ void k_query(GridView g, const int32_t* __restrict__ xyz, int64_t n, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = sqdist_at(g, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
+}
+
+// One warp per x-row of a brick-aligned 8-voxel segment: lanes cover 32 consecutive x.
+__global__ void k_export_dense(GridView g, int32_t* __restrict__ out) {
+  const int64_t total = (int64_t)g.nx * g.ny * g.nz;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int x = (int)(i % g.nx);
+    int64_t r = i / g.nx;
+    int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    out[i] = sqdist_at(g, x, y, z);
+  }
+}
+
+struct Corner8 {
+  float d[8];  // index a + 2b + 4c for corner (i0+a, j0+b, k0+c)
+};
+
+// Corner distances (metres) of the cell holding u; returns the in-cell coordinates.
+__device__ __forceinline__ void cell_of(const GridView& g, float vs, float px, float py, float pz, int& i0, int& j0,
+                                        int& k0, float& tx, float& ty, float& tz) {
+  float ux = px / vs, uy = py / vs, uz = pz / vs;
+  float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
+  i0 = (int)fminf(fmaxf(fx, 0.f), (float)(g.nx - 2));
+  j0 = (int)fminf(fmaxf(fy, 0.f), (float)(g.ny - 2));
+  k0 = (int)fminf(fmaxf(fz, 0.f), (float)(g.nz - 2));
+  tx = ux - (float)i0;
+  ty = uy - (float)j0;
+  tz = uz - (float)k0;
+}
+
+__device__ __forceinline__ void corners(const GridView& g, float vs, int i0, int j0, int k0, Corner8& c) {
+  // most cells sit inside one brick: look the brick up once
+  const bool one = ((i0 & 7) != 7) && ((j0 & 7) != 7) && ((k0 & 7) != 7);
+  if (one) {
+    int s = find_brick(g, i0 >> 3, j0 >> 3, k0 >> 3);
+    const float inf_m = vs * sqrtf((float)g.INF);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
+      if (s < 0) {
+        c.d[q] = inf_m;
+      } else {
+        int D = g.dist[(size_t)s * kBrickVox + ((i0 + a) & 7) + 8 * ((j0 + b) & 7) + 64 * ((k0 + e) & 7)];
+        c.d[q] = vs * sqrtf((float)D);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
+      c.d[q] = vs * sqrtf((float)sqdist_at(g, i0 + a, j0 + b, k0 + e));
+    }
+  }
+}
+
+__device__ __forceinline__ float trilinear(const Corner8& c, float tx, float ty, float tz) {
+  float c00 = c.d[0] + tx * (c.d[1] - c.d[0]);
+  float c10 = c.d[2] + tx * (c.d[3] - c.d[2]);
+  float c01 = c.d[4] + tx * (c.d[5] - c.d[4]);
+  float c11 = c.d[6] + tx * (c.d[7] - c.d[6]);
+  float c0 = c00 + ty * (c10 - c00);
+  float c1 = c01 + ty * (c11 - c01);
+  return c0 + tz * (c1 - c0);
+}
+
+__global__ void k_clearance_fwd(GridView g, float vs, const float* __restrict__ pts, int64_t T, int64_t P, float tau,
+                                float* __restrict__ cost) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp; t < T; t += nw) {
+    float acc = 0.f;
+    for (int64_t p = lane; p < P; p += 32) {
+      const float* q = pts + (t * P + p) * 3;
+      int i0, j0, k0;
+      float tx, ty, tz;
+      cell_of(g, vs, q[0], q[1], q[2], i0, j0, k0, tx, ty, tz);
+      Corner8 c;
+      corners(g, vs, i0, j0, k0, c);
+      float d = trilinear(c, tx, ty, tz);
+      float h = fmaxf(0.f, tau - d);
+      acc += h * h;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) cost[t] = acc;
+  }
+}
+
+__global__ void k_clearance_bwd(GridView g, float vs, const float* __restrict__ pts, int64_t T, int64_t P, float tau,
+                                const float* __restrict__ gcost, float* __restrict__ gpts) {
+  const int64_t n = T * P;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float* q = pts + i * 3;
+    int i0, j0, k0;
+    float tx, ty, tz;
+    cell_of(g, vs, q[0], q[1], q[2], i0, j0, k0, tx, ty, tz);
+    Corner8 c;
+    corners(g, vs, i0, j0, k0, c);
+    float d = trilinear(c, tx, ty, tz);
+    float h = fmaxf(0.f, tau - d);
+    float go = gcost[i / P];
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (h > 0.f) {
+      float wx[2] = {1.f - tx, tx}, wy[2] = {1.f - ty, ty}, wz[2] = {1.f - tz, tz};
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          gx += (c.d[1 + 2 * b + 4 * e] - c.d[2 * b + 4 * e]) * wy[b] * wz[e];
+          gy += (c.d[2 + b + 4 * e] - c.d[b + 4 * e]) * wx[b] * wz[e];
+          gz += (c.d[4 + b + 2 * e] - c.d[b + 2 * e]) * wx[b] * wy[e];
+        }
+      float s = -2.f * h / vs * go;
+      gx *= s;
+      gy *= s;
+      gz *= s;
+    }
+    gpts[i * 3] = gx;
+    gpts[i * 3 + 1] = gy;
+    gpts[i * 3 + 2] = gz;
+  }
+}
+
+unsigned grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  VDB_LAUNCH(k_query, grid_for(n, 256), 256, 0, st, g, xyz, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_dense(const GridView& g, int32_t* out, cudaStream_t st) {
+  int64_t n = (int64_t)g.nx * g.ny * g.nz;
+  VDB_LAUNCH(k_export_dense, grid_for(n, 256), 256, 0, st, g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clearance_fwd(const GridView& g, float vs, const float* pts, int64_t T, int64_t P, float tau,
+                                 float* cost, cudaStream_t st) {
+  if (T <= 0) return cudaSuccess;
+  VDB_LAUNCH(k_clearance_fwd, grid_for(T * 32, 256), 256, 0, st, g, vs, pts, T, P, tau, cost);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clearance_bwd(const GridView& g, float vs, const float* pts, int64_t T, int64_t P, float tau,
+                                 const float* gcost, float* gpts, cudaStream_t st) {
+  if (T <= 0 || P <= 0) return cudaSuccess;
+  VDB_LAUNCH(k_clearance_bwd, grid_for(T * P, 256), 256, 0, st, g, vs, pts, T, P, tau, gcost, gpts);
+  return cudaGetLastError();
+}
+
+}  // namespace vdbedt

@@ -1,0 +1,251 @@
+// Internal definitions shared by the CUDA translation units of libvdbedt.
+//
+// Sparse grid layout in device memory (paper Sec. IV-A: a shallow, wide tree with a hashed top
+// level, directly indexed lower levels and a background tile value):
+//   level 1  hash table of interior nodes (open addressing, linear probing); a node covers
+//            16^3 bricks = 128^3 voxels; slot word = (node key << 32) | node index
+//   level 2  per node a dense table of 4096 child slots (int32; -1 = background tile dmax^2)
+//            plus a 4096-bit mask of bricks in the compute set
+//   leaves   8^3-voxel bricks in a pool indexed by slot:
+//              occ   8 x uint64   bit (y*8 + x) of word z  (64 B)
+//              g2    512 x uint16 in-plane (x, y) squared distance, saturated   (1 KB)
+//              dist  512 x int32  D, the output                                 (2 KB)
+//            voxel index inside a brick: x + 8 y + 64 z.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vdbedt {
+
+constexpr int kBrick = 8;
+constexpr int kBrickVox = 512;
+constexpr int kNodeB = 16;  // bricks per node edge
+constexpr int kNodeBricks = kNodeB * kNodeB * kNodeB;
+constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
+constexpr uint32_t kPending = 0xFFFFFFFFu;
+constexpr int32_t kNoSlot = -1;
+constexpr int32_t kClaiming = -2;
+
+// device error bits
+constexpr int kErrOverflow = 1;
+constexpr int kErrTimeout = 2;
+constexpr int kErrInvalidRecord = 4;
+constexpr int kErrInternal = 8;
+constexpr int kErrNodeOverflow = 16;
+
+// device counters
+enum Counter : int {
+  C_NBRICKS = 0,
+  C_NNODES = 1,
+  C_ERR = 2,
+  C_XY_ITEMS = 3,
+  C_Z_ITEMS = 4,
+  C_CHANGED = 5,
+  C_FLIPS = 6,
+  C_NEW_BRICKS = 7,
+  C_UNIQUE = 8,
+  C_HAS_ZERO = 9,
+  C_FINITE = 10,
+  C_OBST = 11,
+  C_RECORDS = 12,
+  C_SPIN = 13,
+  C_NUM = 16
+};
+
+// brick flags
+constexpr uint32_t F_OBST = 1u;    // holds an occupied voxel
+constexpr uint32_t F_FINITE = 2u;  // holds a voxel with D < dmax^2
+
+struct GridView {
+  int nx, ny, nz;     // voxels
+  int BX, BY, BZ;     // bricks per axis
+  int NX, NY, NZ;     // nodes per axis
+  int dmax, R, INF;   // truncation, brick radius of influence, dmax^2
+  uint32_t hmask;     // hash capacity - 1
+  int cap;            // brick capacity
+  int node_cap;       // node capacity
+  unsigned long long* hslots;  // [hmask+1]
+  int32_t* child;     // [node_cap * 4096]
+  uint32_t* amask;    // [node_cap * 128]
+  int32_t* node_key;  // [node_cap]
+  int32_t* xy_mark;   // [node_cap * 1024] epoch of the last time each in-plane run was queued
+  int32_t* z_mark;    // [node_cap * 1024] same for z runs
+  unsigned long long* occ;  // [cap * 8]
+  uint16_t* g2;       // [cap * 512]
+  int32_t* dist;      // [cap * 512]
+  int4* bcoord;       // [cap]
+  uint32_t* bflags;   // [cap]
+  int32_t* bepoch;    // [cap] epoch of the last change (incremental)
+  int32_t* counters;  // [C_NUM]
+};
+
+__host__ __device__ inline int node_key_of(const GridView& g, int bx, int by, int bz) {
+  return (bx >> 4) + g.NX * ((by >> 4) + g.NY * (bz >> 4));
+}
+
+__device__ __forceinline__ uint32_t hash32(uint32_t k) {
+  k ^= k >> 16;
+  k *= 0x7feb352du;
+  k ^= k >> 15;
+  k *= 0x846ca68bu;
+  k ^= k >> 16;
+  return k;
+}
+
+__device__ __forceinline__ void set_error(const GridView& g, int bits) { atomicOr(&g.counters[C_ERR], bits); }
+
+// Node index for node key, or -1 when the node is absent.  Readers never wait: a node whose
+// insertion is still pending is absent for them (inserts happen in kernels that do not read the
+// node's bricks).
+__device__ __forceinline__ int find_node(const GridView& g, uint32_t key) {
+  uint32_t h = hash32(key) & g.hmask;
+  for (uint32_t probe = 0; probe <= g.hmask; ++probe) {
+    unsigned long long w = g.hslots[h];
+    uint32_t k = (uint32_t)(w >> 32);
+    if (k == key) {
+      uint32_t v = (uint32_t)w;
+      return v == kPending ? -1 : (int)v;
+    }
+    if (k == kEmptyKey) return -1;
+    h = (h + 1) & g.hmask;
+  }
+  return -1;
+}
+
+// Find or insert the node with this key.  The inserting thread claims the hash slot with a
+// pending marker, allocates the node index, then publishes it; other inserters of the same key
+// wait for publication with a bounded spin (error bit on give-up).
+__device__ inline int get_or_create_node(const GridView& g, uint32_t key) {
+  uint32_t h = hash32(key) & g.hmask;
+  for (uint32_t probe = 0; probe <= g.hmask; ++probe) {
+    unsigned long long w = g.hslots[h];
+    uint32_t k = (uint32_t)(w >> 32);
+    if (k == kEmptyKey) {
+      unsigned long long want = ((unsigned long long)key << 32) | kPending;
+      unsigned long long old = atomicCAS(&g.hslots[h], w, want);
+      if (old == w) {
+        int idx = atomicAdd(&g.counters[C_NNODES], 1);
+        if (idx >= g.node_cap) {
+          set_error(g, kErrNodeOverflow);
+          return -1;
+        }
+        g.node_key[idx] = (int32_t)key;
+        __threadfence();
+        atomicExch(&g.hslots[h], ((unsigned long long)key << 32) | (uint32_t)idx);
+        return idx;
+      }
+      w = old;
+      k = (uint32_t)(w >> 32);
+    }
+    if (k == key) {
+      for (int spin = 0; spin < (1 << 22); ++spin) {
+        unsigned long long cur = atomicAdd(&g.hslots[h], 0ull);
+        uint32_t v = (uint32_t)cur;
+        if (v != kPending) return (int)v;
+        __nanosleep(64);
+      }
+      set_error(g, kErrTimeout);
+      return -1;
+    }
+    h = (h + 1) & g.hmask;
+  }
+  set_error(g, kErrNodeOverflow);
+  return -1;
+}
+
+__device__ __forceinline__ int local_brick(int bx, int by, int bz) {
+  return (bx & 15) | ((by & 15) << 4) | ((bz & 15) << 8);
+}
+
+// Slot of brick (bx, by, bz), or -1 when it is outside the grid or not stored.
+__device__ __forceinline__ int find_brick(const GridView& g, int bx, int by, int bz) {
+  if ((unsigned)bx >= (unsigned)g.BX || (unsigned)by >= (unsigned)g.BY || (unsigned)bz >= (unsigned)g.BZ) return -1;
+  int n = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+  if (n < 0) return -1;
+  int s = g.child[(size_t)n * kNodeBricks + local_brick(bx, by, bz)];
+  return s >= 0 ? s : -1;
+}
+
+__device__ __forceinline__ unsigned long long pack_brick(int bx, int by, int bz) {
+  return (unsigned long long)(uint32_t)bx | ((unsigned long long)(uint32_t)by << 21) |
+         ((unsigned long long)(uint32_t)bz << 42);
+}
+__device__ __forceinline__ void unpack_brick(unsigned long long p, int& bx, int& by, int& bz) {
+  bx = (int)(p & 0x1FFFFF);
+  by = (int)((p >> 21) & 0x1FFFFF);
+  bz = (int)((p >> 42) & 0x1FFFFF);
+}
+
+}  // namespace vdbedt
+
+// ---------------------------------------------------------------------------------------------
+// Host-side internal interface between translation units
+// ---------------------------------------------------------------------------------------------
+namespace vdbedt {
+
+// Process-wide count of kernel launches made by the library (reported by vdbedt_kernel_launches).
+void note_launch();
+
+#define VDB_LAUNCH(kernel, grid, block, smem, stream, ...)         \
+  do {                                                             \
+    ::vdbedt::note_launch();                                       \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);    \
+  } while (0)
+
+struct Tuning {
+  int xy_run = 8;   // bricks per XY item along y
+  int z_run = 8;    // bricks per Z item along z
+  int variant = 1;  // 1 windowed minimum, 2 lower envelope
+};
+
+// primitives (prims.cu)
+size_t scan_temp_bytes(int64_t n);
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total_dev, void* temp,
+                               cudaStream_t st);
+size_t radix_temp_bytes(int64_t n);
+// Stable LSD radix sort of u32 keys (with optional u32 values) on the low `bits` bits.  n is an
+// upper bound; count_dev (nullable) holds the actual count on the device.  Results land in
+// keys_out / vals_out.  keys_in / vals_in are clobbered.
+cudaError_t radix_sort_u32(uint32_t* keys_in, uint32_t* keys_out, uint32_t* vals_in, uint32_t* vals_out,
+                           int64_t n, const int32_t* count_dev, int bits, void* temp, cudaStream_t st);
+
+// grid build (grid.cu)
+struct Staging {
+  int4* rec;        // staged records (x, y, z, value)
+  int64_t n;        // staged count
+  int64_t cap;
+};
+struct Scratch {
+  void* buf = nullptr;
+  size_t bytes = 0;
+};
+cudaError_t ensure_scratch(Scratch& s, size_t bytes);
+
+cudaError_t launch_reset(const GridView& g, cudaStream_t st);
+cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n, bool track, int epoch,
+                                  int32_t* changed, Scratch& scr, cudaStream_t st);
+cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st);
+cudaError_t launch_activation_full(const GridView& g, cudaStream_t st);
+cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, unsigned long long* xy_items,
+                                    unsigned long long* z_items, cudaStream_t st);
+cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, int epoch, const int32_t* changed,
+                                    unsigned long long* xy_items, unsigned long long* z_items, cudaStream_t st);
+
+// passes (passes.cu)
+cudaError_t launch_xy_pass(const GridView& g, const Tuning& t, const unsigned long long* items, int max_items,
+                           cudaStream_t st);
+cudaError_t launch_z_pass(const GridView& g, const Tuning& t, const unsigned long long* items, int max_items,
+                          cudaStream_t st);
+int item_run_xy(const GridView& g, const Tuning& t);
+int item_run_z(const GridView& g, const Tuning& t);
+
+// queries (query.cu)
+cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st);
+cudaError_t launch_export_dense(const GridView& g, int32_t* out, cudaStream_t st);
+cudaError_t launch_clearance_fwd(const GridView& g, float vs, const float* pts, int64_t T, int64_t P, float tau,
+                                 float* cost, cudaStream_t st);
+cudaError_t launch_clearance_bwd(const GridView& g, float vs, const float* pts, int64_t T, int64_t P, float tau,
+                                 const float* gcost, float* gpts, cudaStream_t st);
+
+}  // namespace vdbedt

@@ -1,0 +1,299 @@
+"""ctypes binding of libvdbedt (see include/vdbedt.h for the contract of each call)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "libvdbedt.so")
+_lock = threading.Lock()
+_lib = None
+
+VDBEDT_DMAX_LIMIT = 181
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVERFLOW", 6: "EINTERNAL"}
+
+
+class VdbedtError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.code = STATUS.get(status, str(status))
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("dmax", ctypes.c_int32),
+                ("voxel_size", ctypes.c_float), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("flags", ctypes.c_uint32), ("max_bricks", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("allocated_bricks", ctypes.c_int64), ("obstacle_bricks", ctypes.c_int64),
+                ("finite_bricks", ctypes.c_int64), ("capacity_bricks", ctypes.c_int64), ("nodes", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("R", ctypes.c_int32), ("error_bits", ctypes.c_int32)]
+
+
+class UpdateStats(ctypes.Structure):
+    _fields_ = [("records", ctypes.c_int64), ("net_flips", ctypes.c_int64), ("changed_bricks", ctypes.c_int64),
+                ("xy_items", ctypes.c_int64), ("z_items", ctypes.c_int64), ("new_bricks", ctypes.c_int64)]
+
+
+class PhaseTimes(ctypes.Structure):
+    _fields_ = [("ingest_ms", ctypes.c_float), ("activation_ms", ctypes.c_float), ("items_ms", ctypes.c_float),
+                ("xy_ms", ctypes.c_float), ("z_ms", ctypes.c_float)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("xy_run", ctypes.c_int32), ("z_run", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+# C name -> (restype, argtypes)
+_H, _P, _I64, _I32, _F = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+SIGNATURES = {
+    "vdbedt_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
+    "vdbedt_destroy": (ctypes.c_int, [_H]),
+    "vdbedt_set_occupancy": (ctypes.c_int, [_H, _P, _P, _I64, ctypes.c_int]),
+    "vdbedt_set_occupancy_dense": (ctypes.c_int, [_H, _P, ctypes.c_int]),
+    "vdbedt_reset": (ctypes.c_int, [_H]),
+    "vdbedt_global": (ctypes.c_int, [_H]),
+    "vdbedt_update": (ctypes.c_int, [_H, ctypes.POINTER(UpdateStats)]),
+    "vdbedt_query": (ctypes.c_int, [_H, _P, _I64, _P, ctypes.c_int]),
+    "vdbedt_export_dense": (ctypes.c_int, [_H, _P, ctypes.c_int]),
+    "vdbedt_clearance_forward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P]),
+    "vdbedt_clearance_backward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P, _P]),
+    "vdbedt_global_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _I32]),
+    "vdbedt_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(Tuning)]),
+    "vdbedt_synchronize": (ctypes.c_int, [_H]),
+    "vdbedt_get_info": (ctypes.c_int, [_H, ctypes.POINTER(Info)]),
+    "vdbedt_stream": (ctypes.c_void_p, [_H]),
+    "vdbedt_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
+    "vdbedt_get_phase_times": (ctypes.c_int, [_H, ctypes.POINTER(PhaseTimes)]),
+    "vdbedt_kernel_launches": (ctypes.c_int64, []),
+    "vdbedt_last_error": (ctypes.c_char_p, [_H]),
+}
+
+
+def library_path() -> str:
+    return _SO
+
+
+def load():
+    """Load libvdbedt.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_SO):
+                raise RuntimeError(f"libvdbedt.so is not built ({_SO}); run paper_2105_04419_gb300.build.build()")
+            lib = ctypes.CDLL(_SO)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status, where, handle=None):
+    if status != 0:
+        msg = load().vdbedt_last_error(handle)
+        raise VdbedtError(status, where, msg.decode() if msg else "")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr_host(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+class Map:
+    """One sparse distance field (a vdbedt handle) on a CUDA device."""
+
+    def __init__(self, nx: int, ny: int, nz: int, dmax: int, voxel_size: float = 0.1, device: int = 0,
+                 stream=None, max_bricks: int = 0):
+        lib = load()
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.device = device
+        self.stream = stream
+        cfg = Config(nx, ny, nz, dmax, voxel_size, device, ctypes.c_void_p(stream.cuda_stream), 0, max_bricks)
+        h = ctypes.c_void_p()
+        _check(lib.vdbedt_create(ctypes.byref(cfg), ctypes.byref(h)), "vdbedt_create")
+        self._h = h
+        self.shape_xyz = (nx, ny, nz)
+        self.dmax = dmax
+        self.voxel_size = voxel_size
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vdbedt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- occupancy --
+    def set_occupancy(self, xyz, occ):
+        """Stage records (x, y, z) -> occ; numpy arrays (host) or CUDA tensors (device)."""
+        lib = load()
+        if isinstance(xyz, np.ndarray):
+            x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+            o = np.ascontiguousarray(occ, dtype=np.uint8).reshape(-1)
+            _check(lib.vdbedt_set_occupancy(self._h, _ptr_host(x), _ptr_host(o), x.shape[0], 0),
+                   "vdbedt_set_occupancy", self._h)
+        else:
+            torch = _torch()
+            x = xyz.to(torch.int32).contiguous().view(-1, 3)
+            o = occ.to(torch.uint8).contiguous().view(-1)
+            _check(lib.vdbedt_set_occupancy(self._h, x.data_ptr(), o.data_ptr(), x.shape[0], 1),
+                   "vdbedt_set_occupancy", self._h)
+            self._keep = (x, o)
+
+    def set_occupancy_dense(self, grid):
+        lib = load()
+        if isinstance(grid, np.ndarray):
+            gr = np.ascontiguousarray(grid, dtype=np.uint8)
+            _check(lib.vdbedt_set_occupancy_dense(self._h, _ptr_host(gr), 0), "vdbedt_set_occupancy_dense", self._h)
+        else:
+            torch = _torch()
+            gr = grid.to(torch.uint8).contiguous()
+            _check(lib.vdbedt_set_occupancy_dense(self._h, gr.data_ptr(), 1), "vdbedt_set_occupancy_dense", self._h)
+            self._keep = (gr,)
+
+    def reset(self):
+        _check(load().vdbedt_reset(self._h), "vdbedt_reset", self._h)
+
+    # -- transforms --
+    def global_(self):
+        _check(load().vdbedt_global(self._h), "vdbedt_global", self._h)
+
+    def update(self, stats: bool = False):
+        st = UpdateStats() if stats else None
+        _check(load().vdbedt_update(self._h, ctypes.byref(st) if st is not None else None), "vdbedt_update", self._h)
+        if st is not None:
+            return {k: getattr(st, k) for k, _ in UpdateStats._fields_}
+        return None
+
+    def set_tuning(self, xy_run: int = 0, z_run: int = 0, variant: int = 0):
+        t = Tuning(xy_run, z_run, variant, 0)
+        _check(load().vdbedt_set_tuning(self._h, ctypes.byref(t)), "vdbedt_set_tuning", self._h)
+
+    def set_profiling(self, on: bool = True):
+        _check(load().vdbedt_set_profiling(self._h, int(on)), "vdbedt_set_profiling", self._h)
+
+    def phase_times(self) -> dict:
+        pt = PhaseTimes()
+        _check(load().vdbedt_get_phase_times(self._h, ctypes.byref(pt)), "vdbedt_get_phase_times", self._h)
+        return {k: getattr(pt, k) for k, _ in PhaseTimes._fields_}
+
+    def synchronize(self):
+        _check(load().vdbedt_synchronize(self._h), "vdbedt_synchronize", self._h)
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().vdbedt_get_info(self._h, ctypes.byref(inf)), "vdbedt_get_info", self._h)
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    # -- reading --
+    def query(self, xyz):
+        lib = load()
+        if isinstance(xyz, np.ndarray):
+            x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+            out = np.empty(x.shape[0], dtype=np.int32)
+            _check(lib.vdbedt_query(self._h, _ptr_host(x), x.shape[0], _ptr_host(out), 0), "vdbedt_query", self._h)
+            return out
+        torch = _torch()
+        x = xyz.to(torch.int32).contiguous().view(-1, 3)
+        out = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
+        _check(lib.vdbedt_query(self._h, x.data_ptr(), x.shape[0], out.data_ptr(), 1), "vdbedt_query", self._h)
+        return out
+
+    def export_dense(self, on_device: bool = False):
+        lib = load()
+        nx, ny, nz = self.shape_xyz
+        if not on_device:
+            out = np.empty((nz, ny, nx), dtype=np.int32)
+            _check(lib.vdbedt_export_dense(self._h, _ptr_host(out), 0), "vdbedt_export_dense", self._h)
+            return out
+        torch = _torch()
+        out = torch.empty((nz, ny, nx), dtype=torch.int32, device=f"cuda:{self.device}")
+        _check(lib.vdbedt_export_dense(self._h, out.data_ptr(), 1), "vdbedt_export_dense", self._h)
+        return out
+
+    def clearance_forward(self, pts, tau: float):
+        torch = _torch()
+        p = pts.contiguous()
+        T, P = p.shape[0], p.shape[1]
+        cost = torch.empty(T, dtype=torch.float32, device=p.device)
+        _check(load().vdbedt_clearance_forward(self._h, p.data_ptr(), T, P, float(tau), cost.data_ptr()),
+               "vdbedt_clearance_forward", self._h)
+        return cost
+
+    def clearance_backward(self, pts, tau: float, grad_cost):
+        torch = _torch()
+        p = pts.contiguous()
+        gc = grad_cost.contiguous().to(torch.float32)
+        T, P = p.shape[0], p.shape[1]
+        g = torch.empty_like(p)
+        _check(load().vdbedt_clearance_backward(self._h, p.data_ptr(), T, P, float(tau), gc.data_ptr(), g.data_ptr()),
+               "vdbedt_clearance_backward", self._h)
+        return g
+
+
+def kernel_launches() -> int:
+    return int(load().vdbedt_kernel_launches())
+
+
+def global_batched(maps):
+    lib = load()
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle for m in maps])
+    _check(lib.vdbedt_global_batched(arr, len(maps)), "vdbedt_global_batched")
+
+
+def _make_clearance_fn():
+    torch = _torch()
+
+    class _Clearance(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, pts, m, tau):
+            if pts.dtype != torch.float32 or not pts.is_cuda:
+                raise TypeError("pts must be a float32 CUDA tensor [T, P, 3]")
+            p = pts.detach().contiguous()
+            ctx.m, ctx.tau = m, tau
+            ctx.save_for_backward(p)
+            return m.clearance_forward(p, tau)
+
+        @staticmethod
+        def backward(ctx, gcost):
+            (p,) = ctx.saved_tensors
+            return ctx.m.clearance_backward(p, ctx.tau, gcost), None, None
+
+    return _Clearance
+
+
+_clearance_fn = None
+
+
+def clearance_cost(m: Map, pts, tau: float = 1.0):
+    """Per-trajectory clearance cost sum_p max(0, tau - d(p))^2 (Eq. 2's clearance term as a squared
+    hinge) with d the trilinear distance in metres; differentiable with respect to pts [T, P, 3]."""
+    global _clearance_fn
+    if _clearance_fn is None:
+        _clearance_fn = _make_clearance_fn()
+    return _clearance_fn.apply(pts, m, tau)

@@ -1,0 +1,194 @@
+"""GPU parity of the global transform against the CPU oracle (bit-exact int32), through the C ABI.
+
+Covers: the dense 64^3 Bernoulli(0.02) workload at dmax 16 (five seeds); ragged grids that are not
+multiples of the 8^3 brick and span several 16^3-brick interior nodes; every dmax class (the half
+kernels for dmax <= 45 with brick radius R = 1..6, the generic kernels above); empty, full,
+single-obstacle and corner cases; the dense and the record ingest; every tuning of the work-item
+runs; duplicate and clearing records (last record wins); and the counters of the grid.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_common import coords_of, first_mismatch, gpu_global
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_bernoulli64_dmax16(seed):
+    occ = W.bernoulli_grid(seed, (64, 64, 64), 0.02)
+    ref = O.edt_factorised(occ, 16)
+    got = gpu_global(occ, 16).export_dense()
+    assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
+
+
+@pytest.mark.parametrize("dmax", [1, 2, 3, 5, 8, 9, 15, 16, 17, 24, 25, 31, 32, 33, 40, 45])
+def test_ragged_half_path(dmax):
+    rs = np.random.default_rng(dmax)
+    shape = (37, 45, 70)  # nz, ny, nx: none a multiple of 8
+    occ = (rs.random(shape) < 0.003).astype(np.uint8)
+    ref = O.edt_factorised(occ, dmax)
+    got = gpu_global(occ, dmax).export_dense()
+    assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
+
+
+@pytest.mark.parametrize("dmax", [46, 60, 100])
+def test_generic_path(dmax):
+    rs = np.random.default_rng(dmax)
+    shape = (23, 30, 41)
+    occ = (rs.random(shape) < 0.0015).astype(np.uint8)
+    ref = O.edt_factorised(occ, dmax)
+    got = gpu_global(occ, dmax).export_dense()
+    assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
+
+
+def test_generic_path_max_dmax():
+    shape = (20, 17, 29)
+    occ = np.zeros(shape, np.uint8)
+    occ[3, 4, 5] = 1
+    occ[19, 16, 28] = 1
+    ref = O.edt_factorised(occ, 181)
+    got = gpu_global(occ, 181).export_dense()
+    assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
+
+
+def test_multi_node_grid():
+    """300 x 140 x 20 voxels: 38 x 18 x 3 bricks, 3 x 2 x 1 interior nodes; sparse shells."""
+    occ = W.tunnel_scene(9, (300, 140, 20), ntunnels=5, rmin=3, rmax=6)
+    if occ.sum() == 0:
+        occ[10, 70, 150] = 1
+    for dmax in (6, 20, 32):
+        ref = O.edt_factorised(occ, dmax)
+        got = gpu_global(occ, dmax).export_dense()
+        assert first_mismatch(got, ref) is None, (dmax, first_mismatch(got, ref))
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_empty_full_single_corner(dense):
+    shape = (19, 26, 33)
+    for dmax in (1, 7, 32, 50):
+        empty = np.zeros(shape, np.uint8)
+        got = gpu_global(empty, dmax, dense=dense).export_dense()
+        assert (got == dmax * dmax).all()
+    full = np.ones(shape, np.uint8)
+    assert (gpu_global(full, 9, dense=dense).export_dense() == 0).all()
+    for corner in ((0, 0, 0), (18, 25, 32), (0, 25, 0), (18, 0, 32)):
+        occ = np.zeros(shape, np.uint8)
+        occ[corner] = 1
+        for dmax in (4, 16, 45):
+            ref = O.edt_factorised(occ, dmax)
+            got = gpu_global(occ, dmax, dense=dense).export_dense()
+            assert first_mismatch(got, ref) is None, (corner, dmax, first_mismatch(got, ref))
+
+
+@pytest.mark.parametrize("xy_run", [4, 8, 16])
+@pytest.mark.parametrize("z_run", [4, 8, 16])
+def test_tunings(xy_run, z_run):
+    occ = W.bernoulli_grid(3, (48, 80, 72), 0.002)
+    ref = O.edt_factorised(occ, 24)
+    got = gpu_global(occ, 24, tuning=dict(xy_run=xy_run, z_run=z_run)).export_dense()
+    assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
+
+
+def test_dense_ingest_matches_records():
+    occ = W.bernoulli_grid(4, (40, 50, 60), 0.01)
+    a = gpu_global(occ, 12, dense=True).export_dense()
+    b = gpu_global(occ, 12, dense=False).export_dense()
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, O.edt_factorised(occ, 12))
+
+
+def test_duplicates_and_clears_last_record_wins():
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(5)
+    shape = (24, 24, 24)
+    n = 4000
+    xyz = np.stack([rs.integers(0, 24, n)] * 1 + [rs.integers(0, 24, n), rs.integers(0, 24, n)], 1).astype(np.int32)
+    xyz = np.concatenate([xyz, xyz[:1500]])  # every one of the first 1500 voxels appears again
+    val = rs.integers(0, 2, len(xyz)).astype(np.uint8)
+    occ = np.zeros(shape, np.uint8)
+    for k in range(len(val)):
+        occ[xyz[k, 2], xyz[k, 1], xyz[k, 0]] = val[k]
+    m = V.Map(24, 24, 24, 7)
+    # stage in three calls: order across calls is record order
+    m.set_occupancy(xyz[:1000], val[:1000])
+    m.set_occupancy(xyz[1000:3000], val[1000:3000])
+    m.set_occupancy(xyz[3000:], val[3000:])
+    m.global_()
+    got = m.export_dense()
+    ref = O.edt_factorised(occ, 7)
+    assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
+
+
+def test_device_records_and_query():
+    import torch
+    import paper_2105_04419_gb300 as V
+    occ = W.bernoulli_grid(6, (33, 34, 35), 0.01)
+    xyz = coords_of(occ)
+    m = V.Map(35, 34, 33, 10)
+    m.set_occupancy(torch.from_numpy(xyz).cuda(), torch.ones(len(xyz), dtype=torch.uint8, device="cuda"))
+    m.global_()
+    ref = O.edt_factorised(occ, 10)
+    rs = np.random.default_rng(0)
+    q = np.stack([rs.integers(-3, 38, 5000), rs.integers(-3, 37, 5000), rs.integers(-3, 36, 5000)], 1).astype(np.int32)
+    inside = (q[:, 0] < 35) & (q[:, 1] < 34) & (q[:, 2] < 33) & (q >= 0).all(1)
+    expect = np.full(len(q), 100, np.int32)
+    expect[inside] = ref[q[inside, 2], q[inside, 1], q[inside, 0]]
+    assert np.array_equal(m.query(q), expect)
+    qd = m.query(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert np.array_equal(qd, expect)
+    assert np.array_equal(m.export_dense(on_device=True).cpu().numpy(), ref)
+
+
+def test_invalid_host_records_rejected():
+    import paper_2105_04419_gb300 as V
+    m = V.Map(16, 16, 16, 4)
+    with pytest.raises(V.VdbedtError) as e:
+        m.set_occupancy(np.array([[1, 2, 3], [16, 0, 0]], np.int32), np.array([1, 1], np.uint8))
+    assert e.value.code == "EINVAL"
+    with pytest.raises(V.VdbedtError):
+        m.set_occupancy(np.array([[1, 2, 3]], np.int32), np.array([2], np.uint8))
+    # the rejected calls staged nothing
+    m.global_()
+    assert (m.export_dense() == 16).all()
+
+
+def test_invalid_device_records_reported():
+    import torch
+    import paper_2105_04419_gb300 as V
+    m = V.Map(16, 16, 16, 4)
+    xyz = torch.tensor([[1, 2, 3], [99, 0, 0]], dtype=torch.int32, device="cuda")
+    m.set_occupancy(xyz, torch.ones(2, dtype=torch.uint8, device="cuda"))
+    m.global_()
+    with pytest.raises(V.VdbedtError) as e:
+        m.synchronize()
+    assert e.value.code == "EINVAL"
+    m.synchronize()  # reported once
+    ref = np.zeros((16, 16, 16), np.uint8)
+    ref[3, 2, 1] = 1
+    assert np.array_equal(m.export_dense(), O.edt_factorised(ref, 4))
+
+
+def test_capacity_overflow_reported():
+    import paper_2105_04419_gb300 as V
+    occ = W.bernoulli_grid(2, (32, 32, 32), 0.05)
+    m = V.Map(32, 32, 32, 8, max_bricks=10)
+    m.set_occupancy(coords_of(occ), np.ones(int(occ.sum()), np.uint8))
+    m.global_()
+    with pytest.raises(V.VdbedtError) as e:
+        m.synchronize()
+    assert e.value.code == "EOVERFLOW"
+
+
+def test_info_counts():
+    occ = W.bernoulli_grid(8, (64, 64, 64), 0.001)
+    m = gpu_global(occ, 16)
+    info = m.info()
+    ob = occ.reshape(8, 8, 8, 8, 8, 8).any(axis=(1, 3, 5))
+    assert info["obstacle_bricks"] == int(ob.sum())
+    ref = O.edt_factorised(occ, 16)
+    fin = (ref < 256).reshape(8, 8, 8, 8, 8, 8).any(axis=(1, 3, 5))
+    assert info["finite_bricks"] == int(fin.sum())
+    assert info["error_bits"] == 0 and info["R"] == 2

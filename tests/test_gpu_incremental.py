@@ -1,0 +1,118 @@
+"""GPU parity of the incremental transform: after every frame of edits, vdbedt_update equals the
+oracle's exact transform of the resulting occupancy (and vdbedt_global on it), bit for bit.
+
+Edit streams: random records (sets, clears, duplicates) on ragged grids; the paper's ablation
+shape (half of the obstacles removed, as many added; Sec. V-A); and the lidar sequence on a small
+tunnel scene, starting from an empty map.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_common import coords_of, first_mismatch
+
+pytestmark = pytest.mark.gpu
+
+
+def apply_records(occ, xyz, val):
+    for k in range(len(val)):
+        occ[xyz[k, 2], xyz[k, 1], xyz[k, 0]] = val[k]
+
+
+@pytest.mark.parametrize("dmax", [3, 9, 16, 32, 47])
+def test_random_edit_frames(dmax):
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(dmax)
+    shape = (29, 54, 61)
+    occ = (rs.random(shape) < 0.004).astype(np.uint8)
+    nz, ny, nx = shape
+    m = V.Map(nx, ny, nz, dmax)
+    xyz0 = coords_of(occ)
+    m.set_occupancy(xyz0, np.ones(len(xyz0), np.uint8))
+    m.global_()
+    for f in range(6):
+        k = int(rs.integers(1, 300))
+        xyz = np.stack([rs.integers(0, nx, k), rs.integers(0, ny, k), rs.integers(0, nz, k)], 1).astype(np.int32)
+        # also clear some existing obstacles
+        occ_xyz = coords_of(occ)
+        if len(occ_xyz):
+            pick = occ_xyz[rs.integers(0, len(occ_xyz), min(50, len(occ_xyz)))]
+            xyz = np.concatenate([xyz, pick])
+        val = rs.integers(0, 2, len(xyz)).astype(np.uint8)
+        val[-min(50, len(occ_xyz)):] = 0 if len(occ_xyz) else val[-1:]
+        apply_records(occ, xyz, val)
+        m.set_occupancy(xyz, val)
+        st = m.update(stats=True)
+        ref = O.edt_factorised(occ, dmax)
+        got = m.export_dense()
+        assert first_mismatch(got, ref) is None, (f, st, first_mismatch(got, ref))
+        assert st["records"] == len(val)
+
+
+def test_ablation_shape_remove_half_add_half():
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(11)
+    side, dmax = 100, 10
+    idx = rs.choice(side ** 3, 500, replace=False)
+    occ = np.zeros(side ** 3, np.uint8)
+    occ[idx] = 1
+    occ = occ.reshape(side, side, side)
+    m = V.Map(side, side, side, dmax)
+    xyz0 = coords_of(occ)
+    m.set_occupancy(xyz0, np.ones(len(xyz0), np.uint8))
+    m.global_()
+    removed = rs.choice(idx, 250, replace=False)
+    free = np.flatnonzero(occ.ravel() == 0)
+    added = rs.choice(free, 250, replace=False)
+    lin = np.concatenate([removed, added])
+    val = np.concatenate([np.zeros(250, np.uint8), np.ones(250, np.uint8)])
+    z, r = np.divmod(lin, side * side)
+    y, x = np.divmod(r, side)
+    xyz = np.stack([x, y, z], 1).astype(np.int32)
+    apply_records(occ, xyz, val)
+    m.set_occupancy(xyz, val)
+    st = m.update(stats=True)
+    assert st["net_flips"] == 500
+    ref = O.edt_factorised(occ, dmax)
+    assert first_mismatch(m.export_dense(), ref) is None
+
+
+def test_update_equals_global_on_lidar_frames():
+    import paper_2105_04419_gb300 as V
+    dims = (160, 144, 64)
+    truth = W.tunnel_scene(4, dims, ntunnels=4, rmin=6, rmax=10)
+    _, lines = W.tunnel_lines(4, dims, ntunnels=4, rmin=6, rmax=10)
+    seq = W.LidarSequence(truth, 4, lines[0], nframes=12, nbeams=16, nazim=256, maxrange=120)
+    dmax = 16
+    inc = V.Map(*dims, dmax)
+    inc.global_()
+    for f in range(12):
+        xyz, val = seq.next()
+        inc.set_occupancy(xyz, val)
+        inc.update()
+        ref = O.edt_factorised(seq.map, dmax)
+        got = inc.export_dense()
+        assert first_mismatch(got, ref) is None, (f, first_mismatch(got, ref))
+        glob = V.Map(*dims, dmax)
+        glob.set_occupancy_dense(seq.map)
+        glob.global_()
+        assert np.array_equal(glob.export_dense(), got)
+
+
+def test_update_before_any_global_and_after_dense():
+    import paper_2105_04419_gb300 as V
+    occ = W.bernoulli_grid(1, (24, 25, 26), 0.01)
+    m = V.Map(26, 25, 24, 6)
+    xyz = coords_of(occ)
+    m.set_occupancy(xyz, np.ones(len(xyz), np.uint8))
+    m.update()  # first call computes globally
+    assert np.array_equal(m.export_dense(), O.edt_factorised(occ, 6))
+    occ2 = W.bernoulli_grid(2, (24, 25, 26), 0.02)
+    m.set_occupancy_dense(occ2)
+    m.update()  # a replaced grid is recomputed globally
+    assert np.array_equal(m.export_dense(), O.edt_factorised(occ2, 6))
+    # an empty update changes nothing
+    st = m.update(stats=True)
+    assert st["net_flips"] == 0 and st["z_items"] == 0
+    assert np.array_equal(m.export_dense(), O.edt_factorised(occ2, 6))
