@@ -37,6 +37,8 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 WORKLOADS = {
     "tunnel": dict(dims=(1024, 1024, 256), dmax=32, seed=1, kind="tunnel",
                    name="tunnel scene 1024x1024x256, 40 tunnels r 8-24, shell walls, dmax 32"),
+    "tunnel512": dict(dims=(512, 512, 256), dmax=32, seed=1, kind="tunnel", ntunnels=20,
+                      name="tunnel scene 512x512x256, 20 tunnels r 8-24, shell walls, dmax 32 (profiling size)"),
     "bernoulli64": dict(dims=(64, 64, 64), dmax=16, seed=0, kind="bernoulli", p=0.02,
                         name="dense 64^3 Bernoulli(0.02), dmax 16"),
 }
@@ -51,6 +53,10 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tunnel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", type=int, default=0, help="pass variant (0 automatic; see vdbedt_set_tuning)")
+    ap.add_argument("--x-run", type=int, default=0)
+    ap.add_argument("--y-run", type=int, default=0)
+    ap.add_argument("--z-run", type=int, default=0)
     return ap.parse_args()
 
 
@@ -58,7 +64,7 @@ def make_occupancy(wl):
     import workloads as W
     nx, ny, nz = wl["dims"]
     if wl["kind"] == "tunnel":
-        return W.tunnel_scene(wl["seed"], (nx, ny, nz))
+        return W.tunnel_scene(wl["seed"], (nx, ny, nz), ntunnels=wl.get("ntunnels", 40))
     return W.bernoulli_grid(wl["seed"], (nz, ny, nx), wl["p"])
 
 
@@ -237,10 +243,13 @@ def main():
     xyz_h = W.occupied_coords(occ)
     n = len(xyz_h)
     ones_h = np.ones(n, np.uint8)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # everything below (torch and the library) runs on this stream
     xyz = torch.from_numpy(xyz_h).cuda()
     ones = torch.from_numpy(ones_h).cuda()
-    stream = torch.cuda.current_stream()
     m = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    if args.variant or args.x_run or args.y_run or args.z_run:
+        m.set_tuning(args.x_run, args.y_run, args.z_run, args.variant)
 
     def step():
         m.reset()
@@ -255,7 +264,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     m.set_profiling(True)
-    phases = {k: [] for k in ("ingest_ms", "activation_ms", "items_ms", "xy_ms", "z_ms")}
+    phases = {k: [] for k in ("ingest_ms", "activation_ms", "items_ms", "x_ms", "y_ms", "z_ms")}
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sampler = ClockSampler(local)
     sampler.start()
@@ -290,9 +299,10 @@ def main():
     # roofline: dominant kernel with its compulsory bytes at the stored widths
     peak, peak_src = peaks()
     allocated = info["allocated_bricks"]
-    per_brick = {"xy_ms": 64 + 1024, "z_ms": 1024 + 2048}  # occupancy in + g2 out; g2 in + D out
-    dom = max(("xy_ms", "z_ms"), key=lambda k: ph[k])
-    kname = {"xy_ms": "k_xy_half", "z_ms": "k_z_half"}[dom]
+    # compulsory bytes per brick: x pass mask in + g1 out; y pass g1 in + g2 out; z pass g2 in + D out
+    per_brick = {"x_ms": 64 + 1024, "y_ms": 1024 + 1024, "z_ms": 1024 + 2048}
+    dom = max(per_brick, key=lambda k: ph[k])
+    kname = {"x_ms": "k_pass<x>", "y_ms": "k_pass<y>", "z_ms": "k_pass<z>"}[dom]
     achieved = allocated * per_brick[dom] / (ph[dom] / 1e3) / 1e9
     tr = traffic_for(kname)
     roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -80,7 +80,8 @@ typedef struct {
   int64_t records;        /* staged records consumed */
   int64_t net_flips;      /* voxels whose occupancy changed */
   int64_t changed_bricks; /* bricks holding a flipped voxel */
-  int64_t xy_items;       /* brick runs recomputed by the in-plane (x, y) passes */
+  int64_t x_items;        /* brick runs recomputed by the x pass */
+  int64_t y_items;        /* brick runs recomputed by the y pass */
   int64_t z_items;        /* brick runs recomputed by the z pass */
   int64_t new_bricks;     /* bricks allocated by this update */
 } vdbedt_update_stats;
@@ -147,11 +148,11 @@ vdbedt_status vdbedt_clearance_backward(vdbedt_handle h, const float* pts, int64
 vdbedt_status vdbedt_global_batched(vdbedt_handle* hs, int32_t k);
 
 /* Tuning of the transform passes (0 = automatic for any field).
- *   xy_run: bricks per in-plane work item along y (4, 8 or 16);
- *   z_run:  bricks per z work item (4, 8 or 16);
- *   variant: 0 automatic, 1 windowed minimum, 2 lower envelope of parabolas. */
+ *   x_run, y_run, z_run: bricks per work item of the pass along that axis (4, 8 or 16);
+ *   variant: 0 automatic, 1 full windowed minimum, 3 windowed minimum with early exit and skips
+ *            (the default; both exact).  Other values are EINVAL. */
 typedef struct {
-  int32_t xy_run, z_run, variant, reserved;
+  int32_t x_run, y_run, z_run, variant;
 } vdbedt_tuning;
 vdbedt_status vdbedt_set_tuning(vdbedt_handle h, const vdbedt_tuning* t);
 
@@ -163,7 +164,8 @@ typedef struct {
   float ingest_ms;     /* staged records -> bricks and occupancy bits */
   float activation_ms; /* compute set (dilation by R bricks) and brick allocation */
   float items_ms;      /* work lists of the passes (global form only) */
-  float xy_ms;         /* in-plane (x, y) passes */
+  float x_ms;          /* x pass (nearest obstacle along each x-line) */
+  float y_ms;          /* y pass (in-plane squared distance) */
   float z_ms;          /* z pass, clamp, finite flags */
 } vdbedt_phase_times;
 vdbedt_status vdbedt_set_profiling(vdbedt_handle h, int on);

@@ -38,8 +38,7 @@ struct vdbedt_map {
   int32_t* h_pinned = nullptr;  // pinned host words for small readbacks
   Scratch scr;
   Scratch io;  // host-input staging on the device
-  unsigned long long* xy_items = nullptr;
-  unsigned long long* z_items = nullptr;
+  Items items{};
   int32_t* changed = nullptr;
   int epoch = 0;
   Tuning tune;
@@ -47,7 +46,7 @@ struct vdbedt_map {
   std::string err;
   // phase timing (CUDA events on the handle's stream)
   bool profiling = false;
-  cudaEvent_t ev[6] = {};
+  cudaEvent_t ev[7] = {};
   bool ev_recorded = false;
 };
 
@@ -151,15 +150,27 @@ vdbedt_status ensure_stage(vdbedt_map* h, int64_t need) {
   return VDBEDT_OK;
 }
 
+void mark(vdbedt_map* h, int i) {
+  if (h->profiling) cudaEventRecord(h->ev[i], h->st);
+}
+
 Tuning effective_tuning(const vdbedt_map* h) {
   Tuning t = h->tune;
-  t.xy_run = item_run_xy(h->g, h->tune);
-  t.z_run = item_run_z(h->g, h->tune);
+  for (int a = 0; a < 3; ++a) t.run[a] = effective_run(h->g, h->tune, a);
   return t;
 }
 
-void mark(vdbedt_map* h, int i) {
-  if (h->profiling) cudaEventRecord(h->ev[i], h->st);
+vdbedt_status run_passes(vdbedt_map* h, const Tuning& t) {
+  if (half_path(h->g)) CK(h, launch_item_slots(h->g, t, h->items, h->st), "item slots");
+  mark(h, 3);
+  CK(h, launch_pass(h->g, t, 0, h->items, h->st), "x pass");
+  mark(h, 4);
+  CK(h, launch_pass(h->g, t, 1, h->items, h->st), "y pass");
+  mark(h, 5);
+  CK(h, launch_pass(h->g, t, 2, h->items, h->st), "z pass");
+  mark(h, 6);
+  h->ev_recorded = h->profiling;
+  return VDBEDT_OK;
 }
 
 vdbedt_status do_global(vdbedt_map* h) {
@@ -175,13 +186,9 @@ vdbedt_status do_global(vdbedt_map* h) {
   mark(h, 1);
   CK(h, launch_activation_full(h->g, h->st), "activation");
   mark(h, 2);
-  CK(h, launch_build_items_full(h->g, t, h->epoch, h->xy_items, h->z_items, h->st), "items");
-  mark(h, 3);
-  CK(h, launch_xy_pass(h->g, t, h->xy_items, h->g.cap, h->st), "xy pass");
-  mark(h, 4);
-  CK(h, launch_z_pass(h->g, t, h->z_items, h->g.cap, h->st), "z pass");
-  mark(h, 5);
-  h->ev_recorded = h->profiling;
+  CK(h, launch_build_items_full(h->g, t, h->epoch, h->items, h->st), "items");
+  vdbedt_status s = run_passes(h, t);
+  if (s) return s;
   h->computed = true;
   return VDBEDT_OK;
 }
@@ -254,18 +261,21 @@ vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out) {
   AL(g.hslots, hcap);
   AL(g.child, node_cap * kNodeBricks);
   AL(g.amask, node_cap * 128);
+  AL(g.mwork, node_cap * 384);
   AL(g.node_key, node_cap);
-  AL(g.xy_mark, node_cap * 1024);
-  AL(g.z_mark, node_cap * 1024);
+  AL(g.mark, node_cap * 3 * 1024);
   AL(g.occ, cap * 8);
+  AL(g.g1, cap * kBrickVox);
   AL(g.g2, cap * kBrickVox);
   AL(g.dist, cap * kBrickVox);
   AL(g.bcoord, cap);
   AL(g.bflags, cap);
   AL(g.bepoch, cap);
   AL(g.counters, C_NUM);
-  AL(h->xy_items, cap);
-  AL(h->z_items, cap);
+  for (int a = 0; a < 3; ++a) {
+    AL(h->items.run[a], cap);
+    AL(h->items.slots[a], cap * kItemSlots);
+  }
   AL(h->changed, cap);
   AL(h->d_invalid, 4);
 #undef AL
@@ -274,8 +284,8 @@ vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out) {
   cudaMemsetAsync(g.hslots, 0xFF, sizeof(unsigned long long) * hcap, h->st);
   cudaMemsetAsync(g.child, 0xFF, sizeof(int32_t) * (size_t)node_cap * kNodeBricks, h->st);
   cudaMemsetAsync(g.amask, 0, sizeof(uint32_t) * (size_t)node_cap * 128, h->st);
-  cudaMemsetAsync(g.xy_mark, 0, sizeof(int32_t) * (size_t)node_cap * 1024, h->st);
-  cudaMemsetAsync(g.z_mark, 0, sizeof(int32_t) * (size_t)node_cap * 1024, h->st);
+  cudaMemsetAsync(g.mwork, 0, sizeof(uint32_t) * (size_t)node_cap * 384, h->st);
+  cudaMemsetAsync(g.mark, 0, sizeof(int32_t) * (size_t)node_cap * 3 * 1024, h->st);
   cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, h->st);
   e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return bail(e, "init");
@@ -292,7 +302,7 @@ vdbedt_status vdbedt_destroy(vdbedt_handle h) {
   if (h->scr.buf) cudaFree(h->scr.buf);
   if (h->io.buf) cudaFree(h->io.buf);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 7; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
@@ -382,21 +392,17 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     h->epoch++;
     const Tuning t = effective_tuning(h);
     mark(h, 0);
-    CK(h, cudaMemsetAsync(h->g.counters + C_XY_ITEMS, 0, sizeof(int32_t) * 6, h->st), "memset");
+    CK(h, cudaMemsetAsync(h->g.counters + C_Y_ITEMS, 0, sizeof(int32_t) * 6, h->st), "memset");
     CK(h, cudaMemsetAsync(h->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), h->st), "memset");
     if (h->stage_n > 0) {
       CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, true, h->epoch, h->changed, h->scr, h->st), "ingest");
       h->stage_n = 0;
     }
     mark(h, 1);
-    CK(h, launch_incremental_mark(h->g, t, h->epoch, h->changed, h->xy_items, h->z_items, h->st), "mark");
+    CK(h, launch_incremental_mark(h->g, t, h->epoch, h->changed, h->items, h->st), "mark");
     mark(h, 2);
-    mark(h, 3);
-    CK(h, launch_xy_pass(h->g, t, h->xy_items, h->g.cap, h->st), "xy pass");
-    mark(h, 4);
-    CK(h, launch_z_pass(h->g, t, h->z_items, h->g.cap, h->st), "z pass");
-    mark(h, 5);
-    h->ev_recorded = h->profiling;
+    s = run_passes(h, t);
+    if (s) return s;
   }
   if (stats) {
     CK(h, cudaMemcpyAsync(h->h_pinned, h->g.counters, sizeof(int32_t) * C_NUM, cudaMemcpyDeviceToHost, h->st), "d2h");
@@ -406,7 +412,8 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     stats->records = nrec;
     stats->net_flips = c[C_FLIPS];
     stats->changed_bricks = c[C_CHANGED];
-    stats->xy_items = c[C_XY_ITEMS];
+    stats->x_items = c[C_X_ITEMS];
+    stats->y_items = c[C_Y_ITEMS];
     stats->z_items = c[C_Z_ITEMS];
     stats->new_bricks = c[C_NEW_BRICKS];
   }
@@ -483,11 +490,14 @@ vdbedt_status vdbedt_set_tuning(vdbedt_handle h, const vdbedt_tuning* t) {
   if (s) return s;
   if (!t) return fail(h, VDBEDT_EINVAL, "null tuning");
   auto ok_run = [](int r) { return r == 0 || r == 4 || r == 8 || r == 16; };
-  if (!ok_run(t->xy_run) || !ok_run(t->z_run) || t->variant < 0 || t->variant > 2)
+  if (!ok_run(t->x_run) || !ok_run(t->y_run) || !ok_run(t->z_run) ||
+      !(t->variant == 0 || t->variant == 1 || t->variant == 3))
     return fail(h, VDBEDT_EINVAL, "bad tuning");
-  h->tune.xy_run = t->xy_run ? t->xy_run : 8;
-  h->tune.z_run = t->z_run ? t->z_run : 8;
-  h->tune.variant = t->variant ? t->variant : 1;
+  const Tuning d;
+  h->tune.run[0] = t->x_run ? t->x_run : d.run[0];
+  h->tune.run[1] = t->y_run ? t->y_run : d.run[1];
+  h->tune.run[2] = t->z_run ? t->z_run : d.run[2];
+  h->tune.variant = t->variant ? t->variant : d.variant;
   return VDBEDT_OK;
 }
 
@@ -532,7 +542,7 @@ vdbedt_status vdbedt_set_profiling(vdbedt_handle h, int on) {
   if (s) return s;
   DeviceGuard guard(h->device);
   if (on && !h->ev[0])
-    for (int i = 0; i < 6; ++i) CK(h, cudaEventCreate(&h->ev[i]), "event");
+    for (int i = 0; i < 7; ++i) CK(h, cudaEventCreate(&h->ev[i]), "event");
   h->profiling = on != 0;
   h->ev_recorded = false;
   return VDBEDT_OK;
@@ -544,14 +554,15 @@ vdbedt_status vdbedt_get_phase_times(vdbedt_handle h, vdbedt_phase_times* out) {
   if (!out) return fail(h, VDBEDT_EINVAL, "null output");
   if (!h->ev_recorded) return fail(h, VDBEDT_EINVAL, "no profiled transform since profiling was enabled");
   DeviceGuard guard(h->device);
-  CK(h, cudaEventSynchronize(h->ev[5]), "event sync");
-  float ms[5];
-  for (int i = 0; i < 5; ++i) CK(h, cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]), "event time");
+  CK(h, cudaEventSynchronize(h->ev[6]), "event sync");
+  float ms[6];
+  for (int i = 0; i < 6; ++i) CK(h, cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]), "event time");
   out->ingest_ms = ms[0];
   out->activation_ms = ms[1];
   out->items_ms = ms[2];
-  out->xy_ms = ms[3];
-  out->z_ms = ms[4];
+  out->x_ms = ms[3];
+  out->y_ms = ms[4];
+  out->z_ms = ms[5];
   return VDBEDT_OK;
 }
 

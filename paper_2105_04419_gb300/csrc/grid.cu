@@ -41,11 +41,13 @@ __global__ void k_reset_nodes(GridView g) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     g.child[i] = kNoSlot;
     if ((i & 3) == 0) {
-      int64_t j = i >> 2;  // 1024 marks per node
-      g.xy_mark[j] = 0;
-      g.z_mark[j] = 0;
+      int64_t j = i >> 2;  // 3 x 1024 marks per node
+      g.mark[3 * j] = 0;
+      g.mark[3 * j + 1] = 0;
+      g.mark[3 * j + 2] = 0;
     }
     if ((i & 31) == 0) g.amask[i >> 5] = 0u;
+    if ((i & 31) < 3) g.mwork[(i >> 5) * 3 + (i & 31)] = 0u;
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= (int64_t)g.hmask;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -53,10 +55,45 @@ __global__ void k_reset_nodes(GridView g) {
 }
 
 // ---- brick allocation ----
-// Claim the child entry of brick (bx,by,bz) in node `node` and give it a pool slot.  Returns the
-// slot (new or existing), or -1 on overflow / concurrent claim.  `init_g2` fills g2 with dmax^2
-// (needed for bricks added by an incremental update whose in-plane pass may not revisit them).
-__device__ int claim_brick(const GridView& g, int node, int bx, int by, int bz, bool init_g2, bool* created) {
+__device__ __forceinline__ int warp_agg_add(int* ctr, bool pred) {
+  const unsigned act = __activemask();
+  const unsigned m = __ballot_sync(act, pred);
+  if (!m) return -1;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(ctr, __popc(m));
+  base = __shfl_sync(act, base, leader);
+  return pred ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
+// Fill a freshly allocated brick: empty occupancy, coordinates, flags; with `init_fields` also
+// g2 and D at dmax^2 (bricks added by an incremental update may be read before a pass writes them).
+__device__ void init_brick(const GridView& g, int slot, int node, int bx, int by, int bz, bool init_fields) {
+  for (int w = 0; w < 8; ++w) g.occ[(size_t)slot * 8 + w] = 0ull;
+  if (init_fields) {
+    uint16_t inf;
+    if (g.dmax <= 45 && g.R <= 6) {
+      __half h = __int2half_rn(g.INF);
+      inf = *reinterpret_cast<uint16_t*>(&h);
+    } else {
+      inf = (uint16_t)g.INF;
+    }
+    uint32_t p = (uint32_t)inf | ((uint32_t)inf << 16);
+    uint4* dst = reinterpret_cast<uint4*>(g.g2 + (size_t)slot * kBrickVox);
+    for (int q = 0; q < 64; ++q) dst[q] = make_uint4(p, p, p, p);
+    uint4* d1 = reinterpret_cast<uint4*>(g.g1 + (size_t)slot * kBrickVox);
+    for (int q = 0; q < 64; ++q) d1[q] = make_uint4(p, p, p, p);
+    int4* dd = reinterpret_cast<int4*>(g.dist + (size_t)slot * kBrickVox);
+    for (int q = 0; q < 128; ++q) dd[q] = make_int4(g.INF, g.INF, g.INF, g.INF);
+  }
+  g.bcoord[slot] = make_int4(bx, by, bz, node);
+  g.bflags[slot] = 0u;
+  g.bepoch[slot] = 0;
+}
+
+// Claim the child entry of brick (bx,by,bz) in `node` and give it a pool slot (concurrent
+// callers may race for the same brick: one wins).  Returns the slot, or -1 on overflow / lost race.
+__device__ int claim_brick(const GridView& g, int node, int bx, int by, int bz, bool init_fields, bool* created) {
   int* e = &g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
   int cur = *e;
   *created = false;
@@ -68,27 +105,7 @@ __device__ int claim_brick(const GridView& g, int node, int bx, int by, int bz, 
     set_error(g, kErrOverflow);
     return -1;  // entry stays "claiming": reads treat it as absent
   }
-  for (int w = 0; w < 8; ++w) g.occ[(size_t)slot * 8 + w] = 0ull;
-  if (init_g2) {
-    uint16_t inf = 0;
-    {
-      // fp16 pattern of INF for the half kernels, plain integer for the generic ones
-      if (g.dmax <= 45 && g.R <= 6) {
-        __half h = __int2half_rn(g.INF);
-        inf = *reinterpret_cast<uint16_t*>(&h);
-      } else {
-        inf = (uint16_t)g.INF;
-      }
-    }
-    uint32_t p = (uint32_t)inf | ((uint32_t)inf << 16);
-    uint4* dst = reinterpret_cast<uint4*>(g.g2 + (size_t)slot * kBrickVox);
-    for (int q = 0; q < 64; ++q) dst[q] = make_uint4(p, p, p, p);
-    int4* dd = reinterpret_cast<int4*>(g.dist + (size_t)slot * kBrickVox);
-    for (int q = 0; q < 128; ++q) dd[q] = make_int4(g.INF, g.INF, g.INF, g.INF);
-  }
-  g.bcoord[slot] = make_int4(bx, by, bz, node);
-  g.bflags[slot] = 0u;
-  g.bepoch[slot] = 0;
+  init_brick(g, slot, node, bx, by, bz, init_fields);
   __threadfence();
   atomicExch(e, slot);
   *created = true;
@@ -130,6 +147,33 @@ __global__ void k_rec_brick_keys(GridView g, const int4* __restrict__ rec, int64
   if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
 }
 
+// Many records: bucket the brick keys of "set" records through one flag per brick of the grid
+// (a counting sort on the brick key); the compaction of the flags is the sorted unique key list.
+__global__ void k_mark_record_bricks(GridView g, const int4* __restrict__ rec, int64_t n, int32_t* __restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  bool zero = false, bad = false;
+  if (i < n) {
+    int4 r = rec[i];
+    if (!rec_valid(g, r)) {
+      bad = true;
+    } else if (r.w == 1) {
+      int64_t lb = (r.x >> 3) + (int64_t)g.BX * ((r.y >> 3) + (int64_t)g.BY * (r.z >> 3));
+      if (!flag[lb]) flag[lb] = 1;
+    } else {
+      zero = true;
+    }
+  }
+  if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+}
+
+__global__ void k_compact_flag_index(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t n,
+                                     uint32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) out[pos[i]] = (uint32_t)i;
+}
+
 __global__ void k_head_flags(const uint32_t* __restrict__ keys, int64_t n, uint32_t limit, int32_t* __restrict__ flag) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -144,17 +188,38 @@ __global__ void k_compact_keys(const uint32_t* __restrict__ keys, const int32_t*
 }
 
 __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__ uniq, int64_t n, bool init) {
-  const int cnt = min((int64_t)g.counters[C_UNIQUE], n);
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t lb = uniq[j];
-    int bx = (int)(lb % (uint32_t)g.BX);
-    int rest = (int)(lb / (uint32_t)g.BX);
-    int by = rest % g.BY, bz = rest / g.BY;
-    int node = get_or_create_node(g, (uint32_t)node_key_of(g, bx, by, bz));
-    if (node < 0) continue;
-    bool created;
-    claim_brick(g, node, bx, by, bz, init, &created);
-    if (created) atomicAdd(&g.counters[C_NEW_BRICKS], 1);
+  const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t rounds = (cnt + stride - 1) / stride;
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t j = r * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int bx = 0, by = 0, bz = 0, node = -1;
+    int* e = nullptr;
+    bool need = false;
+    if (j < cnt) {
+      uint32_t lb = uniq[j];
+      bx = (int)(lb % (uint32_t)g.BX);
+      int rest = (int)(lb / (uint32_t)g.BX);
+      by = rest % g.BY;
+      bz = rest / g.BY;
+      node = get_or_create_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+      if (node >= 0) {
+        e = &g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
+        need = *e == kNoSlot;
+      }
+    }
+    int slot = warp_agg_add(&g.counters[C_NBRICKS], need);
+    if (need) {
+      if (slot >= g.cap) {
+        set_error(g, kErrOverflow);
+      } else {
+        init_brick(g, slot, node, bx, by, bz, init);
+        __threadfence();
+        *e = slot;
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, need && slot < g.cap);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&g.counters[C_NEW_BRICKS], __popc(m));
   }
 }
 
@@ -276,17 +341,133 @@ __global__ void k_ingest_dense(GridView g, const uint8_t* __restrict__ grid) {
 }
 
 // ---- activation ----
+// Compute set = bricks within Chebyshev brick radius R of an obstacle brick.  Global form: per-node
+// 4096-bit masks, obstacle bits first, then a separable dilation (x, then y, then z), each stage a
+// pure gather over neighbouring nodes' rows (no atomics).  A mask word holds two 16-brick x-rows:
+// word (y >> 1) + 8 z, bits 16 (y & 1) + x.
+
+__global__ void k_clear_masks(GridView g) {
+  const int nn = min(g.counters[C_NNODES], g.node_cap);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    g.amask[i] = 0u;
+    int64_t node = i >> 7, w = i & 127;
+    g.mwork[node * 384 + w] = 0u;
+    g.mwork[node * 384 + 128 + w] = 0u;
+    g.mwork[node * 384 + 256 + w] = 0u;
+  }
+}
+
 __global__ void k_obstacle_flags(GridView g) {
   const int nb = min(g.counters[C_NBRICKS], g.cap);
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
     bool obst = brick_has_obstacle(g, s);
     uint32_t f = g.bflags[s];
     g.bflags[s] = obst ? (f | F_OBST) : (f & ~F_OBST);
-    if (obst) atomicAdd(&g.counters[C_OBST], 1);
+    if (obst) {
+      int4 c = g.bcoord[s];
+      int l = local_brick(c.x, c.y, c.z);
+      atomicOr(&g.mwork[(size_t)c.w * 384 + (l >> 5)], 1u << (l & 31));
+    }
   }
 }
 
-// Mark bricks within Chebyshev radius R of brick (bx,by,bz): one thread per (dy, dz) row.
+// One warp per node holding obstacle bricks: create the nodes within ceil(R / 16) nodes of it.
+__global__ void k_node_halo(GridView g) {
+  const int nn = min(g.counters[C_NNODES], g.node_cap);
+  const int lane = threadIdx.x & 31;
+  const int NR = (g.R + 15) / 16, side = 2 * NR + 1;
+  for (int node = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; node < nn; node += (gridDim.x * blockDim.x) >> 5) {
+    const uint32_t* om = g.mwork + (size_t)node * 384;
+    uint32_t any = om[lane] | om[lane + 32] | om[lane + 64] | om[lane + 96];
+    if (!__any_sync(0xffffffffu, any != 0u)) continue;
+    const int key = g.node_key[node];
+    const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+    for (int o = lane; o < side * side * side; o += 32) {
+      int x = nxn + o % side - NR, y = nyn + (o / side) % side - NR, z = nzn + o / (side * side) - NR;
+      if (x < 0 || y < 0 || z < 0 || x >= g.NX || y >= g.NY || z >= g.NZ) continue;
+      get_or_create_node(g, (uint32_t)(x + g.NX * (y + g.NY * z)));
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t row16(const uint32_t* m, int y, int z) {
+  return (m[(y >> 1) + 8 * z] >> (16 * (y & 1))) & 0xFFFFu;
+}
+
+__device__ __forceinline__ int node_at(const GridView& g, int x, int y, int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= g.NX || y >= g.NY || z >= g.NZ) return -1;
+  return find_node(g, (uint32_t)(x + g.NX * (y + g.NY * z)));
+}
+
+// Stage 0 -> 1: dilate each x-row by R across the neighbouring nodes along x.
+// Stage 1 -> 2: OR of the rows y - R .. y + R; stage 2 -> amask: rows z - R .. z + R, then clipped
+// to the grid.  One thread per (node, mask word), i.e. two rows.
+template <int AXIS>
+__global__ void k_dilate_stage(GridView g) {
+  const int nn = min(g.counters[C_NNODES], g.node_cap);
+  const int R = g.R;
+  const int src_off = AXIS * 128;  // obstacle bits, then stage 1, then stage 2
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int node = (int)(i >> 7), w = (int)(i & 127);
+    const int key = g.node_key[node];
+    const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+    const int z = w >> 3;
+    uint32_t out = 0u;
+    for (int half = 0; half < 2; ++half) {
+      const int y = 2 * (w & 7) + half;
+      uint32_t r = 0u;
+      if (AXIS == 0) {
+        // absolute brick x of bit j of chunk c: 16 (nxn + c) + j
+        const int NR = (R + 15) / 16;
+        for (int c = -NR; c <= NR; ++c) {
+          int nb = c == 0 ? node : node_at(g, nxn + c, nyn, nzn);
+          if (nb < 0) continue;
+          uint32_t v = row16(g.mwork + (size_t)nb * 384 + src_off, y, z);
+          if (!v) continue;
+          for (int x = 0; x < 16; ++x) {
+            int lo = x - R - 16 * c, hi = x + R - 16 * c;  // chunk-local bit range
+            if (hi < 0 || lo > 15) continue;
+            lo = max(lo, 0);
+            hi = min(hi, 15);
+            uint32_t msk = ((hi - lo == 31) ? 0xFFFFFFFFu : ((1u << (hi - lo + 1)) - 1u)) << lo;
+            if (v & msk) r |= 1u << x;
+          }
+        }
+      } else if (AXIS == 1) {
+        for (int d = -R; d <= R; ++d) {
+          int yy = y + d;
+          int q = (yy >= 0) ? (yy >> 4) : -((15 - yy) >> 4);
+          int nb = q == 0 ? node : node_at(g, nxn, nyn + q, nzn);
+          if (nb < 0) continue;
+          r |= row16(g.mwork + (size_t)nb * 384 + src_off, yy - 16 * q, z);
+        }
+      } else {
+        for (int d = -R; d <= R; ++d) {
+          int zz = z + d;
+          int q = (zz >= 0) ? (zz >> 4) : -((15 - zz) >> 4);
+          int nb = q == 0 ? node : node_at(g, nxn, nyn, nzn + q);
+          if (nb < 0) continue;
+          r |= row16(g.mwork + (size_t)nb * 384 + src_off, y, zz - 16 * q);
+        }
+        // clip to the grid
+        const int gy = nyn * 16 + y, gz = nzn * 16 + z;
+        if (gy >= g.BY || gz >= g.BZ) r = 0u;
+        const int xs = g.BX - nxn * 16;
+        if (xs < 16) r &= (xs <= 0) ? 0u : ((1u << xs) - 1u);
+      }
+      out |= r << (16 * half);
+    }
+    if (AXIS < 2)
+      g.mwork[(size_t)node * 384 + (AXIS + 1) * 128 + w] = out;
+    else
+      g.amask[(size_t)node * 128 + w] = out;
+  }
+}
+
+// Mark bricks within Chebyshev radius R of brick (bx,by,bz) in amask: one (dy, dz) row (used by the
+// incremental form, where few bricks change).
 __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int dy, int dz) {
   const int R = g.R;
   int y = by + dy, z = bz + dz;
@@ -297,7 +478,7 @@ __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int
     int node = get_or_create_node(g, (uint32_t)node_key_of(g, x0, y, z));
     if (node >= 0) {
       int lx0 = x0 & 15, lx1 = seg_end & 15;
-      uint32_t bitsx = (lx1 - lx0 == 31) ? 0xFFFFFFFFu : (((1u << (lx1 - lx0 + 1)) - 1u) << lx0);
+      uint32_t bitsx = ((1u << (lx1 - lx0 + 1)) - 1u) << lx0;
       int ly = y & 15, lz = z & 15;
       int word = (ly >> 1) + 8 * lz;
       atomicOr(&g.amask[(size_t)node * 128 + word], bitsx << (16 * (ly & 1)));
@@ -306,69 +487,112 @@ __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int
   }
 }
 
-__global__ void k_dilate_obstacles(GridView g) {
-  const int nb = min(g.counters[C_NBRICKS], g.cap);
-  const int side = 2 * g.R + 1;
-  const int rows = side * side;
-  const int64_t total = (int64_t)nb * rows;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    int s = (int)(i / rows), r = (int)(i % rows);
-    if (!(g.bflags[s] & F_OBST)) continue;
-    int4 c = g.bcoord[s];
-    mark_dilation_row(g, c.x, c.y, c.z, r % side - g.R, r / side - g.R);
-  }
-}
-
-// Allocate every marked brick that has no storage yet: one block per node.
-__global__ void k_alloc_marked(GridView g, bool init_g2) {
+// Allocate every marked brick without storage: one block per node, 16 bricks per thread, one
+// atomic per block for the slot range (block scan of the per-thread counts).
+__global__ void __launch_bounds__(256) k_alloc_marked(GridView g, bool init_fields) {
+  __shared__ int wsum[8];
+  __shared__ int base_sh;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int node = blockIdx.x; node < nn; node += gridDim.x) {
-    const int key = g.node_key[node];
-    const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
-    for (int l = threadIdx.x; l < kNodeBricks; l += blockDim.x) {
-      if (!((g.amask[(size_t)node * 128 + (l >> 5)] >> (l & 31)) & 1u)) continue;
-      if (g.child[(size_t)node * kNodeBricks + l] >= 0) continue;
-      int bx = nxn * 16 + (l & 15), by = nyn * 16 + ((l >> 4) & 15), bz = nzn * 16 + (l >> 8);
-      bool created;
-      claim_brick(g, node, bx, by, bz, init_g2, &created);
-      if (created) atomicAdd(&g.counters[C_NEW_BRICKS], 1);
+    const int l0 = threadIdx.x * 16;
+    const uint32_t bits = (g.amask[(size_t)node * 128 + (threadIdx.x >> 1)] >> (16 * (threadIdx.x & 1))) & 0xFFFFu;
+    uint32_t need = 0u;
+    if (bits) {
+      const int4* ch = reinterpret_cast<const int4*>(g.child + (size_t)node * kNodeBricks + l0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int4 c = ch[q];
+        int cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (((bits >> (4 * q + k)) & 1u) && cc[k] == kNoSlot) need |= 1u << (4 * q + k);
+      }
     }
+    int cnt = __popc(need);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < 8; ++w) {
+        int t = wsum[w];
+        wsum[w] = tot;
+        tot += t;
+      }
+      base_sh = tot ? atomicAdd(&g.counters[C_NBRICKS], tot) : 0;
+      if (tot) atomicAdd(&g.counters[C_NEW_BRICKS], tot);
+    }
+    __syncthreads();
+    int slot = base_sh + wsum[warp] + incl - cnt;
+    if (need) {
+      const int key = g.node_key[node];
+      const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+      for (int k = 0; k < 16; ++k) {
+        if (!((need >> k) & 1u)) continue;
+        const int l = l0 + k;
+        if (slot >= g.cap) {
+          set_error(g, kErrOverflow);
+        } else {
+          init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8),
+                     init_fields);
+          __threadfence();
+          g.child[(size_t)node * kNodeBricks + l] = slot;
+        }
+        ++slot;
+      }
+    }
+    __syncthreads();
   }
-}
-
-__global__ void k_clear_amask(GridView g) {
-  const int nn = min(g.counters[C_NNODES], g.node_cap);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
-       i += (int64_t)gridDim.x * blockDim.x)
-    g.amask[i] = 0u;
 }
 
 // ---- work items ----
-__device__ void queue_runs(const GridView& g, int bx, int by, int bz, int node, int xy_run, int z_run, int epoch,
-                           bool want_xy, bool want_z, unsigned long long* xy_items, unsigned long long* z_items) {
-  const int lx = bx & 15, ly = by & 15, lz = bz & 15;
-  if (want_xy) {
-    int run = lx + 16 * (lz + 16 * (ly / xy_run));
-    if (atomicExch(&g.xy_mark[(size_t)node * 1024 + run], epoch) != epoch) {
-      int p = atomicAdd(&g.counters[C_XY_ITEMS], 1);
-      if (p < g.cap) xy_items[p] = pack_brick(bx, by - (ly % xy_run), bz);
-    }
-  }
-  if (want_z) {
-    int run = lx + 16 * (ly + 16 * (lz / z_run));
-    if (atomicExch(&g.z_mark[(size_t)node * 1024 + run], epoch) != epoch) {
-      int p = atomicAdd(&g.counters[C_Z_ITEMS], 1);
-      if (p < g.cap) z_items[p] = pack_brick(bx, by, bz - (lz % z_run));
-    }
+// Queue the run along `axis` that holds brick (bx, by, bz) (runs are aligned to `run` bricks
+// inside the node), once per epoch.
+__device__ __forceinline__ void queue_run(const GridView& g, int axis, int bx, int by, int bz, int node, int run,
+                                          int epoch, unsigned long long* items) {
+  const int l[3] = {bx & 15, by & 15, bz & 15};
+  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+  const int id = l[a1] + 16 * (l[a2] + 16 * (l[axis] / run));
+  if (atomicExch(&g.mark[((size_t)node * 3 + axis) * 1024 + id], epoch) != epoch) {
+    const int p = atomicAdd(&g.counters[items_counter(axis)], 1);
+    const int back = l[axis] % run;
+    if (p < g.cap)
+      items[p] = pack_brick(bx - (axis == 0 ? back : 0), by - (axis == 1 ? back : 0), bz - (axis == 2 ? back : 0));
   }
 }
 
-__global__ void k_items_all(GridView g, int xy_run, int z_run, int epoch, unsigned long long* xy_items,
-                            unsigned long long* z_items) {
+__global__ void k_items_all(GridView g, int rx, int ry, int rz, int epoch, Items it) {
   const int nb = min(g.counters[C_NBRICKS], g.cap);
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
     int4 c = g.bcoord[s];
-    queue_runs(g, c.x, c.y, c.z, c.w, xy_run, z_run, epoch, true, true, xy_items, z_items);
+    queue_run(g, 0, c.x, c.y, c.z, c.w, rx, epoch, it.run[0]);
+    queue_run(g, 1, c.x, c.y, c.z, c.w, ry, epoch, it.run[1]);
+    queue_run(g, 2, c.x, c.y, c.z, c.w, rz, epoch, it.run[2]);
+  }
+}
+
+// Slots of each queued run's bricks with R bricks of halo on both sides along the axis.
+__global__ void k_item_slots(GridView g, int axis, int run, const unsigned long long* __restrict__ items,
+                             int32_t* __restrict__ out) {
+  const int n = min(g.counters[items_counter(axis)], g.cap);
+  const int nb = run + 2 * g.R;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n * kItemSlots;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int item = (int)(i / kItemSlots), j = (int)(i % kItemSlots);
+    int s = -1;
+    if (j < nb) {
+      int bx, by, bz;
+      unpack_brick(items[item], bx, by, bz);
+      const int off = j - g.R;
+      s = find_brick(g, bx + (axis == 0 ? off : 0), by + (axis == 1 ? off : 0), bz + (axis == 2 ? off : 0));
+    }
+    out[i] = s;
   }
 }
 
@@ -394,8 +618,8 @@ __global__ void k_changed_flags_dilate(GridView g, const int32_t* __restrict__ c
 
 // Dirty sets of an update: every stored brick within R (Chebyshev) of a changed brick needs its z
 // pass; those in the changed brick's z layer also need the in-plane pass.
-__global__ void k_mark_dirty(GridView g, const int32_t* __restrict__ changed, int xy_run, int z_run, int epoch,
-                             unsigned long long* xy_items, unsigned long long* z_items) {
+__global__ void k_mark_dirty(GridView g, const int32_t* __restrict__ changed, int rx, int ry, int rz, int epoch,
+                             Items it) {
   const int nc = min(g.counters[C_CHANGED], g.cap);
   const int side = 2 * g.R + 1, vol = side * side * side;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nc * vol;
@@ -407,8 +631,13 @@ __global__ void k_mark_dirty(GridView g, const int32_t* __restrict__ changed, in
     if ((unsigned)bx >= (unsigned)g.BX || (unsigned)by >= (unsigned)g.BY || (unsigned)bz >= (unsigned)g.BZ) continue;
     int node = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
     if (node < 0) continue;
-    if (g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] < 0) continue;
-    queue_runs(g, bx, by, bz, node, xy_run, z_run, epoch, dz == 0, true, xy_items, z_items);
+    const int slot = g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
+    if (slot < 0) continue;
+    // x-lines change only within R bricks along x of a changed brick, in-plane values within R in
+    // x and y, D within R in all three
+    if (dy == 0 && dz == 0) queue_run(g, 0, bx, by, bz, node, rx, epoch, it.run[0]);
+    if (dz == 0) queue_run(g, 1, bx, by, bz, node, ry, epoch, it.run[1]);
+    queue_run(g, 2, bx, by, bz, node, rz, epoch, it.run[2]);
   }
 }
 
@@ -443,8 +672,10 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n, bool track, int epoch,
                                   int32_t* changed, Scratch& scr, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const size_t nb4 = align_up((size_t)n * 4);
-  const size_t need = 6 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(n));
+  const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
+  const int64_t m = n > nbr_all ? n : nbr_all;
+  const size_t nb4 = align_up((size_t)m * 4);
+  const size_t need = 6 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(m));
   cudaError_t e = ensure_scratch(scr, need);
   if (e != cudaSuccess) return e;
   char* p = (char*)scr.buf;
@@ -466,15 +697,27 @@ cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n,
 
   const unsigned nbk = blocks_for(n);
   const uint64_t nbr = (uint64_t)g.BX * g.BY * g.BZ;
-  VDB_LAUNCH(k_rec_brick_keys, nbk, kT, 0, st, g, rec, n, ka);
-  // the sentinel 0xFFFFFFFF sorts after every key below 2^bits
-  e = radix_sort_u32(ka, kb, nullptr, nullptr, n, nullptr, bits_for(nbr), rtemp, st);
-  if (e != cudaSuccess) return e;
-  VDB_LAUNCH(k_head_flags, nbk, kT, 0, st, kb, n, (uint32_t)nbr, flag);
-  e = exclusive_scan_i32(flag, pos, n, g.counters + C_UNIQUE, stemp, st);
-  if (e != cudaSuccess) return e;
-  VDB_LAUNCH(k_compact_keys, nbk, kT, 0, st, kb, flag, pos, n, ka);
-  VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, ka, n, track);
+  if ((uint64_t)n >= nbr / 4) {
+    // counting sort of brick keys over the grid's bricks, then compaction
+    e = cudaMemsetAsync(flag, 0, sizeof(int32_t) * nbr, st);
+    if (e != cudaSuccess) return e;
+    VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, flag);
+    e = exclusive_scan_i32(flag, pos, (int64_t)nbr, g.counters + C_UNIQUE, stemp, st);
+    if (e != cudaSuccess) return e;
+    VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, flag, pos, (int64_t)nbr, ka);
+    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for((int64_t)nbr), kT, 0, st, g, ka, (int64_t)nbr, track);
+  } else {
+    // LSD radix sort of the brick keys, unique, compaction
+    VDB_LAUNCH(k_rec_brick_keys, nbk, kT, 0, st, g, rec, n, ka);
+    // the sentinel 0xFFFFFFFF sorts after every key below 2^bits
+    e = radix_sort_u32(ka, kb, nullptr, nullptr, n, nullptr, bits_for(nbr), rtemp, st);
+    if (e != cudaSuccess) return e;
+    VDB_LAUNCH(k_head_flags, nbk, kT, 0, st, kb, n, (uint32_t)nbr, flag);
+    e = exclusive_scan_i32(flag, pos, n, g.counters + C_UNIQUE, stemp, st);
+    if (e != cudaSuccess) return e;
+    VDB_LAUNCH(k_compact_keys, nbk, kT, 0, st, kb, flag, pos, n, ka);
+    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, ka, n, track);
+  }
   if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n);
   // ordered path; its element count is 0 on the device when it is not needed
   VDB_LAUNCH(k_rec_voxel_keys, nbk, kT, 0, st, g, rec, n, track, ka, va);
@@ -494,29 +737,42 @@ cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStre
 }
 
 cudaError_t launch_activation_full(const GridView& g, cudaStream_t st) {
-  VDB_LAUNCH(k_clear_amask, 256, kT, 0, st, g);
+  VDB_LAUNCH(k_clear_masks, 256, kT, 0, st, g);
   VDB_LAUNCH(k_obstacle_flags, 1024, kT, 0, st, g);
-  VDB_LAUNCH(k_dilate_obstacles, 4096, kT, 0, st, g);
+  VDB_LAUNCH(k_node_halo, 64, kT, 0, st, g);
+  VDB_LAUNCH(k_dilate_stage<0>, 256, kT, 0, st, g);
+  VDB_LAUNCH(k_dilate_stage<1>, 256, kT, 0, st, g);
+  VDB_LAUNCH(k_dilate_stage<2>, 256, kT, 0, st, g);
   VDB_LAUNCH(k_alloc_marked, 1024, kT, 0, st, g, false);
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, unsigned long long* xy_items,
-                                    unsigned long long* z_items, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(g.counters + C_XY_ITEMS, 0, 2 * sizeof(int32_t), st);
+static cudaError_t clear_item_counters(const GridView& g, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(g.counters + C_Y_ITEMS, 0, 2 * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  VDB_LAUNCH(k_items_all, 1024, kT, 0, st, g, t.xy_run, t.z_run, epoch, xy_items, z_items);
+  return cudaMemsetAsync(g.counters + C_X_ITEMS, 0, sizeof(int32_t), st);
+}
+
+cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, const Items& it, cudaStream_t st) {
+  cudaError_t e = clear_item_counters(g, st);
+  if (e != cudaSuccess) return e;
+  VDB_LAUNCH(k_items_all, 1024, kT, 0, st, g, t.run[0], t.run[1], t.run[2], epoch, it);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st) {
+  for (int a = 0; a < 3; ++a) VDB_LAUNCH(k_item_slots, 2048, kT, 0, st, g, a, t.run[a], it.run[a], it.slots[a]);
   return cudaGetLastError();
 }
 
 // Incremental: records were already applied with flip tracking (changed list filled).
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, int epoch, const int32_t* changed,
-                                    unsigned long long* xy_items, unsigned long long* z_items, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(g.counters + C_XY_ITEMS, 0, 2 * sizeof(int32_t), st);
+                                    const Items& it, cudaStream_t st) {
+  cudaError_t e = clear_item_counters(g, st);
   if (e != cudaSuccess) return e;
   VDB_LAUNCH(k_changed_flags_dilate, 1024, kT, 0, st, g, changed);
   VDB_LAUNCH(k_alloc_marked, 1024, kT, 0, st, g, true);
-  VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.xy_run, t.z_run, epoch, xy_items, z_items);
+  VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.run[0], t.run[1], t.run[2], epoch, it);
   return cudaGetLastError();
 }
 

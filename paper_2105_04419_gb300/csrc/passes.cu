@@ -7,27 +7,36 @@
 //   D(x,y,z)  = min over |d| <= W of d^2 + g2(x,y,z+d)         (z pass)
 // with any window W >= dmax - 1 (offsets of dmax or more cost at least dmax^2 and can never beat
 // the d = 0 term, which is already saturated).  Here W = 8R, R = floor((dmax + 6) / 8): exactly the
-// halo of R bricks that each pass stages.
+// halo of R bricks a pass reads on each side.  A brick that is not stored has no obstacle within
+// R bricks, so every intermediate value in it is dmax^2: absent bricks read as dmax^2.
 //
-// Kernel "xy": one work item = a run of RUN bricks along y at fixed (bx, bz).  It stages the
-// occupancy bits of bricks bx-R..bx+R and by-R..by+RUN-1+R (64 B each) in shared memory, expands
-// every x-line into g1 with a find-nearest-set-bit per voxel (clz / ffs on a 64-bit window), then
-// evaluates the y pass for the run and stores g2 (16 bit) into the run's bricks.
-//
-// Kernel "z": one work item = a run of RUN bricks along z at fixed (bx, by).  It stages g2 of
-// bricks bz-R..bz+RUN-1+R (1 KB each, contiguous, vectorised 16-byte loads; an absent brick reads
-// as dmax^2) and evaluates the z pass, writing D (int32) and the brick's finite flag.
+// All three passes run in one warp-specialised kernel, k_pass<R, RUN, AXIS>.  A work item is a run
+// of RUN bricks along the pass axis; its slot list (the run plus R bricks of halo on each side) is
+// prepared when the item is queued.  A producer warp streams each item's brick inputs into a
+// three-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk global -> shared,
+// completion counted in bytes on a "full" mbarrier per stage) and fills absent bricks itself;
+// RUN consumer warps each own one output brick of the item, wait on the stage's full barrier,
+// compute, write, and release the stage on its "empty" barrier.  No block-wide barrier sits on
+// the main path, so warps whose windows exit early run ahead.
+//   x (AXIS 0): inputs are the 64-byte occupancy masks.  Each lane expands two x-lines: the line's
+//     occupancy is gathered from the masks of bricks bx-R..bx+R (one byte each) and the nearest
+//     set bit on either side of each voxel is found with clz / ffs on a 64-bit window.  g1 is
+//     stored y-major so that the y pass reads it as planes.
+//   y, z (AXIS 1, 2): inputs are 1 KB bricks of g1 / g2.  In the staged column a plane along the
+//     pass axis is 32 words (two voxels per word) and a lane's line is one word per plane, so the
+//     32 lanes of a consumer read 32 consecutive words.
 //
 // Arithmetic of the windowed minimum: packed half2, two voxels per 32-bit lane.  Every operand is
 // an integer in [0, 2048] (values are saturated at dmax^2 <= 2025 for dmax <= 45 before they enter
-// a window, and d^2 <= (8R)^2 <= 2304 only ever adds to them): fp16 represents each such integer
-// exactly, the sum of two is exact whenever it is below 2048 and rounds to a value >= 2048
-// otherwise, and min is exact, so every minimum below dmax^2 is computed exactly and every
-// candidate at or above it stays at or above it.  Each thread owns 8 consecutive outputs of two
-// neighbouring lines and keeps the 8 + 2W inputs in registers (fully unrolled), pairing offsets
-// +d and -d: acc = min(acc, min(v[k-d], v[k+d]) + d^2).
+// a window, and offsets whose square exceeds 2048 are represented by 2048): fp16 represents each
+// such integer exactly, the sum of two is exact whenever it is below 2048 and rounds to a value
+// >= 2048 otherwise, and min is exact, so every minimum below dmax^2 is computed exactly and every
+// candidate at or above it stays at or above it.  Each lane owns 8 consecutive outputs of two
+// neighbouring lines, pairing offsets +d and -d: acc = min(acc, min(v[k-d], v[k+d]) + d^2).  The
+// pruned form stops when (d + 1)^2 reaches every output's current minimum in the warp, and skips
+// windows whose input bricks hold no value below dmax^2.
 //
-// Grids larger than dmax 45 (up to 181) take the generic kernels at the end of the file: int32
+// Grids with dmax above 45 (up to 181) take the generic kernels at the end of the file: int32
 // arithmetic read from shared memory with a runtime window.
 #include <cuda_fp16.h>
 
@@ -52,199 +61,303 @@ __host__ __device__ constexpr uint32_t half_bits(int n) {
 }
 __host__ __device__ constexpr uint32_t half2_bits(int n) { return half_bits(n) | (half_bits(n) << 16); }
 
+// ---- asynchronous bulk copies and mbarriers (inline PTX) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Ordering between this thread's earlier generic-proxy accesses to shared memory and async-proxy
+// writes issued after it.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait for a phase of an mbarrier: gives up after ~2^22 polls (seconds), sets the
+// device error word and reports failure; the caller's whole block agrees before acting.
+__device__ __forceinline__ bool mbar_wait_bounded(const GridView& g, uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < (1 << 22); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 16) __nanosleep(64);
+  }
+  set_error(g, kErrTimeout);
+  return false;
+}
+
 // One 8-output window minimum on packed half2 registers:
-// out[k] = min over |d| <= W of v[k + W + d] + d^2, pairing +d and -d.
+//   out[k] = min over |d| <= W of v[k + W + d] + d^2, pairing +d and -d.
+// With `prune`, the offsets stop once (d + 1)^2 is at least every output's current minimum in the
+// warp (a farther candidate costs at least (d + 1)^2, so none can lower any output); the test runs
+// every 4 offsets and is warp-uniform.
 template <int W>
-__device__ __forceinline__ void window_min8(const uint32_t (&v)[8 + 2 * W], uint32_t (&out)[8]) {
+__device__ __forceinline__ void window_min8(const uint32_t (&v)[8 + 2 * W], uint32_t (&out)[8], bool prune) {
+  static_assert(W % 4 == 0, "window is a multiple of 4 offsets");
+  __half2 acc[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    __half2 acc = u2h(v[k + W]);
+  for (int k = 0; k < 8; ++k) acc[k] = u2h(v[k + W]);
+  bool live = true;  // warp-uniform
 #pragma unroll
-    for (int d = 1; d <= W; ++d) {
-      __half2 m = __hmin2(u2h(v[k + W - d]), u2h(v[k + W + d]));
-      acc = __hmin2(acc, __hadd2(m, u2h(half2_bits(d * d))));
-    }
-    out[k] = h2u(acc);
-  }
-}
-
-template <int R, int RUN>
-struct XYShape {
-  static constexpr int W = 8 * R;
-  static constexpr int NBX = 2 * R + 1;                  // bricks across x
-  static constexpr int NBY = RUN + 2 * R;                // bricks along y
-  static constexpr int NYR = 8 * NBY;                    // rows along y
-  static constexpr int BITS_BYTES = 8 * NYR * NBX;       // [z][row][bxi]
-  static constexpr int G1_STRIDE_Z = (NYR + 1) * 4;      // words per z plane (padded by one row)
-  static constexpr int G1_WORDS = 8 * G1_STRIDE_Z;       // [z][row][xpair]
-  static constexpr int THREADS = 32 * RUN;               // warp per brick of the run
-  static constexpr int SLOTS = NBX * NBY;
-  static constexpr size_t SMEM = (size_t)BITS_BYTES + (size_t)G1_WORDS * 4 + (size_t)SLOTS * 4 + 16;
-};
-
-template <int R, int RUN>
-__global__ void __launch_bounds__(32 * RUN) k_xy_half(GridView g, const unsigned long long* __restrict__ items,
-                                                      int max_items) {
-  using S = XYShape<R, RUN>;
-  constexpr int W = S::W;
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint8_t* bits = smem;                                          // [z][row][bxi]
-  uint32_t* g1 = reinterpret_cast<uint32_t*>(smem + S::BITS_BYTES);  // [z][row(+pad)][xpair]
-  int* slots = reinterpret_cast<int*>(smem + S::BITS_BYTES + (size_t)S::G1_WORDS * 4);
-  const int nitems = min(g.counters[C_XY_ITEMS], max_items);
-  const int tid = threadIdx.x;
-  const __half hinf = __int2half_rn(g.INF);
-
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    int bx, by0, bz;
-    unpack_brick(items[it], bx, by0, bz);
-    // 1. slots of the staged bricks
-    for (int i = tid; i < S::SLOTS; i += S::THREADS) {
-      int bxi = i % S::NBX, byi = i / S::NBX;
-      slots[i] = find_brick(g, bx - R + bxi, by0 - R + byi, bz);
-    }
-    __syncthreads();
-    // 2. occupancy bytes: row (y, z) of brick (bxi, byi) is byte y + 8 z of its 64-byte mask
-    for (int i = tid; i < S::SLOTS * 64; i += S::THREADS) {
-      int b = i >> 6, byte = i & 63;
-      int s = slots[b];
-      uint8_t v = 0;
-      if (s >= 0) v = reinterpret_cast<const uint8_t*>(g.occ)[(size_t)s * 64 + byte];
-      int bxi = b % S::NBX, byi = b / S::NBX;
-      int y = byte & 7, z = byte >> 3;
-      bits[(z * S::NYR + byi * 8 + y) * S::NBX + bxi] = v;
-    }
-    __syncthreads();
-    // 3. x pass: g1 for every (z, row), 8 voxels of the centre brick
-    for (int i = tid; i < 8 * S::NYR; i += S::THREADS) {
-      const uint8_t* line = bits + i * S::NBX;
-      unsigned long long lo = 0, hi = 0;
+  for (int c = 0; c < W / 4; ++c) {
+    if (live) {
 #pragma unroll
-      for (int b = 0; b < S::NBX; ++b) {
-        unsigned long long byte = line[b];
-        if (b < 8)
-          lo |= byte << (8 * b);
-        else
-          hi |= byte << (8 * (b - 8));
-      }
-      uint32_t w[4];
-      if ((lo | hi) == 0ull) {
-        uint32_t p = h2u(__halves2half2(hinf, hinf));
-        w[0] = w[1] = w[2] = w[3] = p;
-      } else {
-        __half hv[8];
+      for (int dd = 1; dd <= 4; ++dd) {
+        const int d = 4 * c + dd;
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          const int p = 8 * R + x;  // position of voxel x in the line (p < 64 for R <= 6)
-          int best = g.INF;
-          unsigned long long L = lo & ((2ull << p) - 1ull);
-          if (L) {
-            int dl = p - (63 - __clzll((long long)L));
-            best = min(best, dl * dl);
-          }
-          unsigned long long Rm = (lo >> p) | (p ? (hi << (64 - p)) : 0ull);
-          if (Rm) {
-            int dr = __ffsll((long long)Rm) - 1;
-            best = min(best, dr * dr);
-          }
-          hv[x] = __int2half_rn(best);
+        for (int k = 0; k < 8; ++k) {
+          __half2 m = __hmin2(u2h(v[k + W - d]), u2h(v[k + W + d]));
+          acc[k] = __hmin2(acc[k], __hadd2(m, u2h(half2_bits(d * d))));
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = h2u(__halves2half2(hv[2 * q], hv[2 * q + 1]));
       }
-      int z = i / S::NYR, row = i % S::NYR;
-      uint32_t* dst = g1 + z * S::G1_STRIDE_Z + row * 4;
-      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    __syncthreads();
-    // 4. y pass: warp = brick of the run; lane = (xpair, z); 8 outputs along y
-    {
-      const int warp = tid >> 5, lane = tid & 31;
-      const int xp = lane & 3, z = lane >> 2;
-      const int s = slots[(warp + R) * S::NBX + R];
-      if (s >= 0) {
-        uint32_t v[8 + 2 * W];
-        const uint32_t* col = g1 + z * S::G1_STRIDE_Z + xp;
-        const int r0 = warp * 8;  // row of output y = 0 minus W, i.e. (warp + R) * 8 - W
-#pragma unroll
-        for (int j = 0; j < 8 + 2 * W; ++j) v[j] = col[(r0 + j) * 4];
-        uint32_t out[8];
-        window_min8<W>(v, out);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(g.g2 + (size_t)s * kBrickVox) + z * 32 + xp;
-#pragma unroll
-        for (int y = 0; y < 8; ++y) dst[y * 4] = out[y];
+      if (prune && c + 1 < W / 4) {
+        const int d1 = 4 * c + 5;  // the next offset
+        __half2 mx = __hmax2(__hmax2(__hmax2(acc[0], acc[1]), __hmax2(acc[2], acc[3])),
+                             __hmax2(__hmax2(acc[4], acc[5]), __hmax2(acc[6], acc[7])));
+        const bool done = __hbge2(u2h(half2_bits(d1 * d1)), mx);
+        live = !__all_sync(0xffffffffu, done);
       }
     }
-    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) out[k] = h2u(acc[k]);
+}
+
+__device__ __forceinline__ int floor16(int v) { return v >= 0 ? (v >> 4) : -((15 - v) >> 4); }
+
+// ================================================================================================
+// The three passes: warp-specialised kernel with a bulk-copy ring
+// ================================================================================================
+template <int R, int RUN, int AXIS>
+struct ColShape {
+  static constexpr int W = 8 * R;
+  static constexpr int NB = RUN + 2 * R;                     // staged bricks per item
+  static constexpr int NS = 3;                               // ring stages
+  static constexpr int UNIT = AXIS == 0 ? 64 : 1024;         // bytes staged per brick
+  static constexpr int STAGE_BYTES = NB * UNIT;
+  static constexpr int META = 2 * NB;                        // slots, then input flags
+  static constexpr int THREADS = 32 * (RUN + 1);
+  static constexpr size_t DATA_BYTES = (size_t)NS * STAGE_BYTES;
+  static constexpr size_t META_BYTES = (size_t)NS * META * 4;
+  static constexpr size_t SMEM = DATA_BYTES + ((META_BYTES + 15) & ~(size_t)15) + 2 * NS * 8 + 16;
+};
+
+// x pass of one brick from the staged masks of bricks w .. w + 2R (64 B each; byte y + 8 z is the
+// x-row (y, z)).  Lane: z = lane & 7, rows y0 = 2 (lane >> 3) and y0 + 1.  g1 is stored y-major.
+template <int R>
+__device__ __forceinline__ void x_compute(const GridView& g, const uint8_t* masks, int slot, uint32_t inf2) {
+  constexpr int NBX = 2 * R + 1;
+  const int lane = threadIdx.x & 31;
+  const int z = lane & 7, y0 = (lane >> 3) * 2;
+  unsigned long long lo[2] = {0ull, 0ull}, hi[2] = {0ull, 0ull};
+#pragma unroll
+  for (int b = 0; b < NBX; ++b) {
+    const uint32_t two = *reinterpret_cast<const uint16_t*>(masks + b * 64 + y0 + 8 * z);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const unsigned long long byte = (two >> (8 * r)) & 0xFFu;
+      if (b < 8)
+        lo[r] |= byte << (8 * b);
+      else
+        hi[r] |= byte << (8 * (b - 8));
+    }
+  }
+  bool fin = false;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    uint32_t w[4];
+    if ((lo[r] | hi[r]) == 0ull) {
+      w[0] = w[1] = w[2] = w[3] = inf2;
+    } else {
+      __half hv[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const int p = 8 * R + x;  // position of voxel x in the line (8 <= p < 64 for 1 <= R <= 6)
+        int best = g.INF;
+        const unsigned long long L = lo[r] & ((2ull << p) - 1ull);
+        if (L) {
+          const int dl = p - (63 - __clzll((long long)L));
+          best = min(best, dl * dl);
+        }
+        const unsigned long long Rm = (lo[r] >> p) | (hi[r] << (64 - p));
+        if (Rm) {
+          const int dr = __ffsll((long long)Rm) - 1;
+          best = min(best, dr * dr);
+        }
+        fin |= best < g.INF;
+        hv[x] = __int2half_rn(best);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[q] = h2u(__halves2half2(hv[2 * q], hv[2 * q + 1]));
+    }
+    *reinterpret_cast<uint4*>(g.g1 + (size_t)slot * kBrickVox + (y0 + r) * 64 + z * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  const unsigned anyfin = __any_sync(0xffffffffu, fin);
+  if (lane == 0) g.bflags[slot] = anyfin ? (g.bflags[slot] | F_G1FIN) : (g.bflags[slot] & ~F_G1FIN);
+}
+
+// y or z pass of one brick: the staged column holds planes along the pass axis, 32 words each
+// (two voxels per word); lane (xpair, a) reads one word per plane.
+//   AXIS 1: g1 (y-major) -> g2 (z-major) + F_G2FIN;   AXIS 2: g2 -> D + F_FINITE.
+template <int R, int AXIS>
+__device__ __forceinline__ void window_compute(const GridView& g, const uint32_t* col, const int* fin_flags, int slot,
+                                               int w, bool prune, uint32_t inf2) {
+  constexpr int W = 8 * R;
+  const int lane = threadIdx.x & 31;
+  const int xp = lane & 3, a = lane >> 2;
+  const __half2 hinf2 = u2h(inf2);
+  bool any_fin = !prune;
+#pragma unroll
+  for (int b = 0; b <= 2 * R; ++b) any_fin |= fin_flags[w + b] != 0;
+  uint32_t out[8];
+  if (any_fin) {
+    uint32_t v[8 + 2 * W];
+    const uint32_t* c = col + a * 4 + xp;
+    const int p0 = w * 8;  // plane of output 0 minus W
+#pragma unroll
+    for (int j = 0; j < 8 + 2 * W; ++j) v[j] = c[(p0 + j) * 32];
+    window_min8<W>(v, out, prune);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[q] = inf2;
+  }
+  bool fin = false;
+  if (AXIS == 1) {
+    // g2, z-major: word z * 32 + y * 4 + xpair, here z = a and y = q
+    uint32_t* dst = reinterpret_cast<uint32_t*>(g.g2 + (size_t)slot * kBrickVox) + a * 32 + xp;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      dst[q * 4] = out[q];
+      fin |= !__hbge2(u2h(out[q]), hinf2);
+    }
+  } else {
+    // D, z-major int32: pair index z * 32 + y * 4 + xpair, here y = a and z = q
+    int2* dst = reinterpret_cast<int2*>(g.dist + (size_t)slot * kBrickVox) + a * 4 + xp;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const __half2 h = u2h(out[q]);
+      const int lo = __half2int_rn(__low2half(h)), hi = __half2int_rn(__high2half(h));
+      fin |= (lo < g.INF) | (hi < g.INF);
+      dst[q * 32] = make_int2(lo, hi);
+    }
+  }
+  const unsigned anyfin = __any_sync(0xffffffffu, fin);
+  if (lane == 0) {
+    const uint32_t bit = AXIS == 1 ? F_G2FIN : F_FINITE;
+    g.bflags[slot] = anyfin ? (g.bflags[slot] | bit) : (g.bflags[slot] & ~bit);
   }
 }
 
-template <int R, int RUN>
-struct ZShape {
-  static constexpr int W = 8 * R;
-  static constexpr int NB = RUN + 2 * R;
-  static constexpr int WORDS = NB * 256;  // 512 half values per brick
-  static constexpr int THREADS = 32 * RUN;
-  static constexpr size_t SMEM = (size_t)WORDS * 4 + (size_t)NB * 4 + 16;
-};
-
-template <int R, int RUN>
-__global__ void __launch_bounds__(32 * RUN) k_z_half(GridView g, const unsigned long long* __restrict__ items,
-                                                     int max_items) {
-  using S = ZShape<R, RUN>;
-  constexpr int W = S::W;
+// One work item = a run of RUN bricks along AXIS.  Warp 0 produces: it reads the item's slot list
+// (prefetched two items ahead, with the input flags one item ahead), fills absent bricks of the
+// stage, and starts one bulk copy per present brick (64 B masks for x, 1 KB g1 / g2 for y / z).
+// Warps 1..RUN consume: warp w computes output brick w of the item from the stage, then
+// releases it.  Every wait is bounded; on a timeout the error word is set and the block drains.
+template <int R, int RUN, int AXIS>
+__global__ void __launch_bounds__(32 * (RUN + 1)) k_pass(GridView g, const int32_t* __restrict__ islots, int max_items,
+                                                         bool prune) {
+  using S = ColShape<R, RUN, AXIS>;
+  constexpr int NB = S::NB, NS = S::NS;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* col = reinterpret_cast<uint32_t*>(smem);  // [brick][z][y][xpair]
-  int* slots = reinterpret_cast<int*>(smem + (size_t)S::WORDS * 4);
-  const int nitems = min(g.counters[C_Z_ITEMS], max_items);
-  const int tid = threadIdx.x;
+  unsigned char* data = smem;
+  int* meta = reinterpret_cast<int*>(smem + S::DATA_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::DATA_BYTES + ((S::META_BYTES + 15) & ~(size_t)15));
+  uint64_t* empty = full + NS;
+  const int nitems = min(g.counters[items_counter(AXIS)], max_items);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const __half hinf = __int2half_rn(g.INF);
   const uint32_t inf2 = h2u(__halves2half2(hinf, hinf));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], RUN);
+    }
+  }
+  __syncthreads();
 
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    int bx, by, bz0;
-    unpack_brick(items[it], bx, by, bz0);
-    for (int i = tid; i < S::NB; i += S::THREADS) slots[i] = find_brick(g, bx, by, bz0 - R + i);
-    __syncthreads();
-    // stage g2 of the column, 16 bytes per thread per step
-    for (int i = tid; i < S::NB * 64; i += S::THREADS) {
-      int b = i >> 6, q = i & 63;
-      int s = slots[b];
-      uint4 v = make_uint4(inf2, inf2, inf2, inf2);
-      if (s >= 0) v = reinterpret_cast<const uint4*>(g.g2 + (size_t)s * kBrickVox)[q];
-      reinterpret_cast<uint4*>(col)[i] = v;
-    }
-    __syncthreads();
-    {
-      const int warp = tid >> 5, lane = tid & 31;
-      const int xp = lane & 3, y = lane >> 2;
-      const int s = slots[warp + R];
-      if (s >= 0) {
-        uint32_t v[8 + 2 * W];
-        const uint32_t* c = col + y * 4 + xp;
-        const int p0 = warp * 8;  // plane of output z = 0 minus W
-#pragma unroll
-        for (int j = 0; j < 8 + 2 * W; ++j) v[j] = c[(p0 + j) * 32];
-        uint32_t out[8];
-        window_min8<W>(v, out);
-        int2* dst = reinterpret_cast<int2*>(g.dist + (size_t)s * kBrickVox) + y * 4 + xp;
-        bool finite = false;
-#pragma unroll
-        for (int z = 0; z < 8; ++z) {
-          __half2 h = u2h(out[z]);
-          int a = __half2int_rn(__low2half(h)), b = __half2int_rn(__high2half(h));
-          finite |= (a < g.INF) | (b < g.INF);
-          dst[z * 32] = make_int2(a, b);
-        }
-        unsigned any = __any_sync(0xffffffffu, finite);
-        if (lane == 0) {
-          uint32_t f = g.bflags[s];
-          f = any ? (f | F_FINITE) : (f & ~F_FINITE);
-          g.bflags[s] = f;
-        }
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    const void* src_base = AXIS == 0 ? (const void*)g.occ : (AXIS == 1 ? (const void*)g.g1 : (const void*)g.g2);
+    const uint32_t in_fin = AXIS == 1 ? F_G1FIN : F_G2FIN;
+    auto slot_of = [&](int item) -> int {
+      return (item < nitems && lane < NB) ? islots[(size_t)item * kItemSlots + lane] : -1;
+    };
+    auto flag_of = [&](int slot) -> int { return (AXIS == 0 || slot < 0) ? 0 : ((g.bflags[slot] & in_fin) != 0); };
+    int it = blockIdx.x;
+    int sl_cur = slot_of(it), sl_nxt = slot_of(it + (int)gridDim.x);
+    int fl_cur = flag_of(sl_cur);
+    int k = 0;
+    for (; it < nitems; it += gridDim.x, ++k) {
+      const int sl_nn = slot_of(it + 2 * (int)gridDim.x);  // prefetch two items ahead
+      const int fl_nxt = flag_of(sl_nxt);                  // and the next item's flags
+      const int s = k % NS, u = k / NS;
+      if (u > 0 && !mbar_wait_bounded(g, &empty[s], (u - 1) & 1)) break;
+      if (lane < NB) {
+        meta[s * S::META + lane] = sl_cur;
+        meta[s * S::META + NB + lane] = fl_cur;
       }
+      const unsigned present = __ballot_sync(0xffffffffu, lane < NB && sl_cur >= 0);
+      unsigned absent = __ballot_sync(0xffffffffu, lane < NB && sl_cur < 0);
+      uint4* stage = reinterpret_cast<uint4*>(data + (size_t)s * S::STAGE_BYTES);
+      constexpr int U16 = S::UNIT / 16;  // 16-byte words per staged brick
+      while (absent) {
+        const int b = __ffs(absent) - 1;
+        absent &= absent - 1;
+        const uint32_t fill = AXIS == 0 ? 0u : inf2;
+        for (int q = lane; q < U16; q += 32) stage[b * U16 + q] = make_uint4(fill, fill, fill, fill);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&full[s], (uint32_t)__popc(present) * (uint32_t)S::UNIT);
+      }
+      __syncwarp();
+      if ((present >> lane) & 1u)
+        bulk_copy_g2s(data + (size_t)s * S::STAGE_BYTES + lane * S::UNIT,
+                      reinterpret_cast<const unsigned char*>(src_base) + (size_t)sl_cur * S::UNIT, (uint32_t)S::UNIT,
+                      &full[s]);
+      sl_cur = sl_nxt;
+      fl_cur = fl_nxt;
+      sl_nxt = sl_nn;
     }
-    __syncthreads();
+    // after a timeout, let copies already issued land before the block can exit
+    if (it < nitems)
+      for (int j = max(0, k - NS); j < k; ++j) mbar_wait_bounded(g, &full[j % NS], (j / NS) & 1);
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  const int w = warp - 1;  // output brick of the item
+  int k = 0;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++k) {
+    const int s = k % NS, u = k / NS;
+    if (!mbar_wait_bounded(g, &full[s], u & 1)) break;
+    const int* m = meta + s * S::META;
+    const int slot = m[w + R];
+    if (slot >= 0) {
+      const unsigned char* stage = data + (size_t)s * S::STAGE_BYTES;
+      if (AXIS == 0)
+        x_compute<R>(g, stage + w * 64, slot, inf2);
+      else
+        window_compute<R, AXIS>(g, reinterpret_cast<const uint32_t*>(stage), m + NB, slot, w, prune, inf2);
+    }
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
   }
 }
 
@@ -260,7 +373,7 @@ __global__ void __launch_bounds__(kGenThreads) k_xy_generic(GridView g, const un
   extern __shared__ __align__(16) unsigned char smem[];
   int* slots = reinterpret_cast<int*>(smem);                        // [NBY][NBX]
   int* g1 = slots + NBX * NBY;                                      // [z][row][x]
-  const int nitems = min(g.counters[C_XY_ITEMS], max_items);
+  const int nitems = min(g.counters[C_Y_ITEMS], max_items);
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     int bx, by0, bz;
     unpack_brick(items[it], bx, by0, bz);
@@ -297,6 +410,15 @@ __global__ void __launch_bounds__(kGenThreads) k_xy_generic(GridView g, const un
       g.g2[(size_t)s * kBrickVox + v] = (uint16_t)best;
     }
     __syncthreads();
+    // in-plane finite flags of the run's bricks
+    for (int b = 0; b < kGenRun; ++b) {
+      int s = slots[(b + R) * NBX + R];
+      if (s < 0) continue;
+      bool fin = false;
+      for (int v = threadIdx.x; v < 512; v += blockDim.x) fin |= g.g2[(size_t)s * kBrickVox + v] < (uint16_t)g.INF;
+      int any = __syncthreads_or(fin);
+      if (threadIdx.x == 0) g.bflags[s] = any ? (g.bflags[s] | F_G2FIN) : (g.bflags[s] & ~F_G2FIN);
+    }
   }
 }
 
@@ -347,9 +469,9 @@ int num_sms() {
   return g_num_sms;
 }
 
-template <typename K>
+template <typename K, typename... Extra>
 cudaError_t launch_persistent(K kernel, int threads, size_t smem, const GridView& g, const unsigned long long* items,
-                              int max_items, cudaStream_t st) {
+                              int max_items, cudaStream_t st, Extra... extra) {
   if (max_items <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -359,81 +481,73 @@ cudaError_t launch_persistent(K kernel, int threads, size_t smem, const GridView
   if (per_sm < 1) per_sm = 1;
   int grid = num_sms() * per_sm;
   if (grid > max_items) grid = max_items;
-  VDB_LAUNCH(kernel, grid, threads, smem, st, g, items, max_items);
+  VDB_LAUNCH(kernel, grid, threads, smem, st, g, items, max_items, extra...);
   return cudaGetLastError();
 }
 
-template <int R, int RUN>
-cudaError_t xy_half(const GridView& g, const unsigned long long* items, int max_items, cudaStream_t st) {
-  using S = XYShape<R, RUN>;
-  return launch_persistent(k_xy_half<R, RUN>, S::THREADS, S::SMEM, g, items, max_items, st);
-}
-template <int R, int RUN>
-cudaError_t z_half(const GridView& g, const unsigned long long* items, int max_items, cudaStream_t st) {
-  using S = ZShape<R, RUN>;
-  return launch_persistent(k_z_half<R, RUN>, S::THREADS, S::SMEM, g, items, max_items, st);
+template <int R, int RUN, int AXIS>
+cudaError_t pass_half(const GridView& g, const int32_t* islots, int max_items, cudaStream_t st, bool prune) {
+  using S = ColShape<R, RUN, AXIS>;
+  auto kernel = k_pass<R, RUN, AXIS>;
+  if (max_items <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, S::THREADS, S::SMEM);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int grid = num_sms() * per_sm;
+  if (grid > max_items) grid = max_items;
+  VDB_LAUNCH(kernel, grid, S::THREADS, S::SMEM, st, g, islots, max_items, prune);
+  return cudaGetLastError();
 }
 
-template <int RUN>
-cudaError_t xy_half_r(const GridView& g, const unsigned long long* items, int max_items, cudaStream_t st) {
+template <int RUN, int AXIS>
+cudaError_t pass_half_r(const GridView& g, const int32_t* islots, int max_items, cudaStream_t st, bool prune) {
   switch (g.R) {
-    case 1: return xy_half<1, RUN>(g, items, max_items, st);
-    case 2: return xy_half<2, RUN>(g, items, max_items, st);
-    case 3: return xy_half<3, RUN>(g, items, max_items, st);
-    case 4: return xy_half<4, RUN>(g, items, max_items, st);
-    case 5: return xy_half<5, RUN>(g, items, max_items, st);
-    case 6: return xy_half<6, RUN>(g, items, max_items, st);
-  }
-  return cudaErrorInvalidValue;
-}
-template <int RUN>
-cudaError_t z_half_r(const GridView& g, const unsigned long long* items, int max_items, cudaStream_t st) {
-  switch (g.R) {
-    case 1: return z_half<1, RUN>(g, items, max_items, st);
-    case 2: return z_half<2, RUN>(g, items, max_items, st);
-    case 3: return z_half<3, RUN>(g, items, max_items, st);
-    case 4: return z_half<4, RUN>(g, items, max_items, st);
-    case 5: return z_half<5, RUN>(g, items, max_items, st);
-    case 6: return z_half<6, RUN>(g, items, max_items, st);
+    case 1: return pass_half<1, RUN, AXIS>(g, islots, max_items, st, prune);
+    case 2: return pass_half<2, RUN, AXIS>(g, islots, max_items, st, prune);
+    case 3: return pass_half<3, RUN, AXIS>(g, islots, max_items, st, prune);
+    case 4: return pass_half<4, RUN, AXIS>(g, islots, max_items, st, prune);
+    case 5: return pass_half<5, RUN, AXIS>(g, islots, max_items, st, prune);
+    case 6: return pass_half<6, RUN, AXIS>(g, islots, max_items, st, prune);
   }
   return cudaErrorInvalidValue;
 }
 
-bool use_half(const GridView& g) { return g.dmax <= 45 && g.R >= 1 && g.R <= 6; }
+template <int AXIS>
+cudaError_t pass_half_run(const GridView& g, int run, const int32_t* islots, int max_items, cudaStream_t st,
+                          bool prune) {
+  switch (run) {
+    case 4: return pass_half_r<4, AXIS>(g, islots, max_items, st, prune);
+    case 8: return pass_half_r<8, AXIS>(g, islots, max_items, st, prune);
+    case 16: return pass_half_r<16, AXIS>(g, islots, max_items, st, prune);
+  }
+  return cudaErrorInvalidValue;
+}
 
 }  // namespace
 
-int item_run_xy(const GridView& g, const Tuning& t) { return use_half(g) ? t.xy_run : kGenRun; }
-int item_run_z(const GridView& g, const Tuning& t) { return use_half(g) ? t.z_run : kGenRun; }
+bool half_path(const GridView& g) { return g.dmax <= 45 && g.R >= 1 && g.R <= 6; }
 
-cudaError_t launch_xy_pass(const GridView& g, const Tuning& t, const unsigned long long* items, int max_items,
-                           cudaStream_t st) {
-  if (use_half(g)) {
-    switch (t.xy_run) {
-      case 4: return xy_half_r<4>(g, items, max_items, st);
-      case 8: return xy_half_r<8>(g, items, max_items, st);
-      case 16: return xy_half_r<16>(g, items, max_items, st);
-    }
-    return cudaErrorInvalidValue;
+int effective_run(const GridView& g, const Tuning& t, int axis) { return half_path(g) ? t.run[axis] : kGenRun; }
+
+cudaError_t launch_pass(const GridView& g, const Tuning& t, int axis, const Items& it, cudaStream_t st) {
+  const bool prune = t.variant != 1;
+  if (half_path(g)) {
+    if (axis == 0) return pass_half_run<0>(g, t.run[0], it.slots[0], g.cap, st, prune);
+    if (axis == 1) return pass_half_run<1>(g, t.run[1], it.slots[1], g.cap, st, prune);
+    return pass_half_run<2>(g, t.run[2], it.slots[2], g.cap, st, prune);
   }
-  const int R = g.R, NBX = 2 * R + 1, NBY = kGenRun + 2 * R;
-  size_t smem = (size_t)NBX * NBY * 4 + (size_t)8 * 8 * NBY * 8 * 4 + 64;
-  return launch_persistent(k_xy_generic, kGenThreads, smem, g, items, max_items, st);
-}
-
-cudaError_t launch_z_pass(const GridView& g, const Tuning& t, const unsigned long long* items, int max_items,
-                          cudaStream_t st) {
-  if (use_half(g)) {
-    switch (t.z_run) {
-      case 4: return z_half_r<4>(g, items, max_items, st);
-      case 8: return z_half_r<8>(g, items, max_items, st);
-      case 16: return z_half_r<16>(g, items, max_items, st);
-    }
-    return cudaErrorInvalidValue;
+  if (axis == 0) return cudaSuccess;  // the generic in-plane kernel reads the masks itself
+  if (axis == 1) {
+    const int R = g.R, NBX = 2 * R + 1, NBY = kGenRun + 2 * R;
+    size_t smem = (size_t)NBX * NBY * 4 + (size_t)8 * 8 * NBY * 8 * 4 + 64;
+    return launch_persistent(k_xy_generic, kGenThreads, smem, g, it.run[1], g.cap, st);
   }
   const int NB = kGenRun + 2 * g.R;
   size_t smem = (size_t)(NB + 3) * 4 + (size_t)NB * 512 * 2 + 64;
-  return launch_persistent(k_z_generic, kGenThreads, smem, g, items, max_items, st);
+  return launch_persistent(k_z_generic, kGenThreads, smem, g, it.run[2], g.cap, st);
 }
 
 }  // namespace vdbedt

@@ -8,9 +8,10 @@
 //            plus a 4096-bit mask of bricks in the compute set
 //   leaves   8^3-voxel bricks in a pool indexed by slot:
 //              occ   8 x uint64   bit (y*8 + x) of word z  (64 B)
+//              g1    512 x uint16 x-line squared distance, saturated, y-major  (1 KB)
 //              g2    512 x uint16 in-plane (x, y) squared distance, saturated   (1 KB)
 //              dist  512 x int32  D, the output                                 (2 KB)
-//            voxel index inside a brick: x + 8 y + 64 z.
+//            voxel index inside a brick: x + 8 y + 64 z (g1: x + 8 z + 64 y).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -39,7 +40,7 @@ enum Counter : int {
   C_NBRICKS = 0,
   C_NNODES = 1,
   C_ERR = 2,
-  C_XY_ITEMS = 3,
+  C_Y_ITEMS = 3,
   C_Z_ITEMS = 4,
   C_CHANGED = 5,
   C_FLIPS = 6,
@@ -50,12 +51,15 @@ enum Counter : int {
   C_OBST = 11,
   C_RECORDS = 12,
   C_SPIN = 13,
+  C_X_ITEMS = 14,
   C_NUM = 16
 };
 
 // brick flags
 constexpr uint32_t F_OBST = 1u;    // holds an occupied voxel
 constexpr uint32_t F_FINITE = 2u;  // holds a voxel with D < dmax^2
+constexpr uint32_t F_G2FIN = 4u;   // holds a voxel with in-plane value g2 < dmax^2
+constexpr uint32_t F_G1FIN = 8u;   // holds a voxel with x-line value g1 < dmax^2
 
 struct GridView {
   int nx, ny, nz;     // voxels
@@ -67,11 +71,12 @@ struct GridView {
   int node_cap;       // node capacity
   unsigned long long* hslots;  // [hmask+1]
   int32_t* child;     // [node_cap * 4096]
-  uint32_t* amask;    // [node_cap * 128]
+  uint32_t* amask;    // [node_cap * 128] compute-set bits: bit l = bx + 16 by + 256 bz (local)
+  uint32_t* mwork;    // [node_cap * 384] obstacle bits and two dilation stages, same layout
   int32_t* node_key;  // [node_cap]
-  int32_t* xy_mark;   // [node_cap * 1024] epoch of the last time each in-plane run was queued
-  int32_t* z_mark;    // [node_cap * 1024] same for z runs
+  int32_t* mark;      // [node_cap * 3 * 1024] epoch of the last time each run along axis a was queued
   unsigned long long* occ;  // [cap * 8]
+  uint16_t* g1;       // [cap * 512]
   uint16_t* g2;       // [cap * 512]
   int32_t* dist;      // [cap * 512]
   int4* bcoord;       // [cap]
@@ -193,10 +198,20 @@ void note_launch();
     kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);    \
   } while (0)
 
+constexpr int kItemSlots = 32;  // slot list entries per work item (run + 2R <= 28 on the half path)
+
+__host__ __device__ inline int items_counter(int axis) { return axis == 0 ? C_X_ITEMS : (axis == 1 ? C_Y_ITEMS : C_Z_ITEMS); }
+
 struct Tuning {
-  int xy_run = 8;   // bricks per XY item along y
-  int z_run = 8;    // bricks per Z item along z
-  int variant = 1;  // 1 windowed minimum, 2 lower envelope
+  int run[3] = {4, 4, 4};  // bricks per work item along x, y, z
+  int variant = 3;         // 1 full windowed minimum, 3 windowed minimum with early exit and skips
+};
+
+// Work lists of the passes: runs of bricks along each axis, and (half path) the slots of each
+// run's bricks with their halo of R bricks on both sides.
+struct Items {
+  unsigned long long* run[3];  // packed brick coordinates of the first brick of each run
+  int32_t* slots[3];           // [cap * kItemSlots]
 };
 
 // primitives (prims.cu)
@@ -227,18 +242,17 @@ cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n,
                                   int32_t* changed, Scratch& scr, cudaStream_t st);
 cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st);
 cudaError_t launch_activation_full(const GridView& g, cudaStream_t st);
-cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, unsigned long long* xy_items,
-                                    unsigned long long* z_items, cudaStream_t st);
+cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, const Items& it, cudaStream_t st);
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, int epoch, const int32_t* changed,
-                                    unsigned long long* xy_items, unsigned long long* z_items, cudaStream_t st);
+                                    const Items& it, cudaStream_t st);
+// slot lists of every queued run (half path)
+cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st);
 
 // passes (passes.cu)
-cudaError_t launch_xy_pass(const GridView& g, const Tuning& t, const unsigned long long* items, int max_items,
-                           cudaStream_t st);
-cudaError_t launch_z_pass(const GridView& g, const Tuning& t, const unsigned long long* items, int max_items,
-                          cudaStream_t st);
-int item_run_xy(const GridView& g, const Tuning& t);
-int item_run_z(const GridView& g, const Tuning& t);
+bool half_path(const GridView& g);
+// pass along `axis` (0 x, 1 y, 2 z) over the queued runs
+cudaError_t launch_pass(const GridView& g, const Tuning& t, int axis, const Items& it, cudaStream_t st);
+int effective_run(const GridView& g, const Tuning& t, int axis);
 
 // queries (query.cu)
 cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st);

@@ -38,17 +38,18 @@ class Info(ctypes.Structure):
 
 class UpdateStats(ctypes.Structure):
     _fields_ = [("records", ctypes.c_int64), ("net_flips", ctypes.c_int64), ("changed_bricks", ctypes.c_int64),
-                ("xy_items", ctypes.c_int64), ("z_items", ctypes.c_int64), ("new_bricks", ctypes.c_int64)]
+                ("x_items", ctypes.c_int64), ("y_items", ctypes.c_int64), ("z_items", ctypes.c_int64),
+                ("new_bricks", ctypes.c_int64)]
 
 
 class PhaseTimes(ctypes.Structure):
     _fields_ = [("ingest_ms", ctypes.c_float), ("activation_ms", ctypes.c_float), ("items_ms", ctypes.c_float),
-                ("xy_ms", ctypes.c_float), ("z_ms", ctypes.c_float)]
+                ("x_ms", ctypes.c_float), ("y_ms", ctypes.c_float), ("z_ms", ctypes.c_float)]
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("xy_run", ctypes.c_int32), ("z_run", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+    _fields_ = [("x_run", ctypes.c_int32), ("y_run", ctypes.c_int32), ("z_run", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
 
 
 # C name -> (restype, argtypes)
@@ -121,7 +122,8 @@ class Map:
         lib = load()
         torch = _torch()
         if stream is None:
-            stream = torch.cuda.current_stream(device)
+            # a stream of its own: the library would otherwise create one that torch cannot see
+            stream = torch.cuda.Stream(device)
         self.device = device
         self.stream = stream
         cfg = Config(nx, ny, nz, dmax, voxel_size, device, ctypes.c_void_p(stream.cuda_stream), 0, max_bricks)
@@ -148,6 +150,21 @@ class Map:
     def handle(self):
         return self._h
 
+    # stream ordering between the caller's current torch stream and the handle's stream
+    def _enter(self, *tensors):
+        torch = _torch()
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+        for t in tensors:
+            t.record_stream(self.stream)
+
+    def _leave(self):
+        torch = _torch()
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+
     # -- occupancy --
     def set_occupancy(self, xyz, occ):
         """Stage records (x, y, z) -> occ; numpy arrays (host) or CUDA tensors (device)."""
@@ -161,9 +178,9 @@ class Map:
             torch = _torch()
             x = xyz.to(torch.int32).contiguous().view(-1, 3)
             o = occ.to(torch.uint8).contiguous().view(-1)
+            self._enter(x, o)
             _check(lib.vdbedt_set_occupancy(self._h, x.data_ptr(), o.data_ptr(), x.shape[0], 1),
                    "vdbedt_set_occupancy", self._h)
-            self._keep = (x, o)
 
     def set_occupancy_dense(self, grid):
         lib = load()
@@ -173,8 +190,8 @@ class Map:
         else:
             torch = _torch()
             gr = grid.to(torch.uint8).contiguous()
+            self._enter(gr)
             _check(lib.vdbedt_set_occupancy_dense(self._h, gr.data_ptr(), 1), "vdbedt_set_occupancy_dense", self._h)
-            self._keep = (gr,)
 
     def reset(self):
         _check(load().vdbedt_reset(self._h), "vdbedt_reset", self._h)
@@ -190,8 +207,8 @@ class Map:
             return {k: getattr(st, k) for k, _ in UpdateStats._fields_}
         return None
 
-    def set_tuning(self, xy_run: int = 0, z_run: int = 0, variant: int = 0):
-        t = Tuning(xy_run, z_run, variant, 0)
+    def set_tuning(self, x_run: int = 0, y_run: int = 0, z_run: int = 0, variant: int = 0):
+        t = Tuning(x_run, y_run, z_run, variant)
         _check(load().vdbedt_set_tuning(self._h, ctypes.byref(t)), "vdbedt_set_tuning", self._h)
 
     def set_profiling(self, on: bool = True):
@@ -221,7 +238,9 @@ class Map:
         torch = _torch()
         x = xyz.to(torch.int32).contiguous().view(-1, 3)
         out = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
+        self._enter(x, out)
         _check(lib.vdbedt_query(self._h, x.data_ptr(), x.shape[0], out.data_ptr(), 1), "vdbedt_query", self._h)
+        self._leave()
         return out
 
     def export_dense(self, on_device: bool = False):
@@ -233,7 +252,9 @@ class Map:
             return out
         torch = _torch()
         out = torch.empty((nz, ny, nx), dtype=torch.int32, device=f"cuda:{self.device}")
+        self._enter(out)
         _check(lib.vdbedt_export_dense(self._h, out.data_ptr(), 1), "vdbedt_export_dense", self._h)
+        self._leave()
         return out
 
     def clearance_forward(self, pts, tau: float):
@@ -241,8 +262,10 @@ class Map:
         p = pts.contiguous()
         T, P = p.shape[0], p.shape[1]
         cost = torch.empty(T, dtype=torch.float32, device=p.device)
+        self._enter(p, cost)
         _check(load().vdbedt_clearance_forward(self._h, p.data_ptr(), T, P, float(tau), cost.data_ptr()),
                "vdbedt_clearance_forward", self._h)
+        self._leave()
         return cost
 
     def clearance_backward(self, pts, tau: float, grad_cost):
@@ -251,8 +274,10 @@ class Map:
         gc = grad_cost.contiguous().to(torch.float32)
         T, P = p.shape[0], p.shape[1]
         g = torch.empty_like(p)
+        self._enter(p, gc, g)
         _check(load().vdbedt_clearance_backward(self._h, p.data_ptr(), T, P, float(tau), gc.data_ptr(), g.data_ptr()),
                "vdbedt_clearance_backward", self._h)
+        self._leave()
         return g
 
 

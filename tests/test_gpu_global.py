@@ -83,12 +83,25 @@ def test_empty_full_single_corner(dense):
             assert first_mismatch(got, ref) is None, (corner, dmax, first_mismatch(got, ref))
 
 
-@pytest.mark.parametrize("xy_run", [4, 8, 16])
-@pytest.mark.parametrize("z_run", [4, 8, 16])
-def test_tunings(xy_run, z_run):
+@pytest.mark.parametrize("runs", [(4, 4, 4), (16, 4, 16), (8, 8, 8), (4, 16, 4), (16, 16, 16)])
+@pytest.mark.parametrize("variant", [1, 3])
+def test_tunings(runs, variant):
+    """Work-item runs and pass variants: 1 full window, 3 window with early exit and skips."""
+    x_run, y_run, z_run = runs
     occ = W.bernoulli_grid(3, (48, 80, 72), 0.002)
     ref = O.edt_factorised(occ, 24)
-    got = gpu_global(occ, 24, tuning=dict(xy_run=xy_run, z_run=z_run)).export_dense()
+    got = gpu_global(occ, 24, tuning=dict(x_run=x_run, y_run=y_run, z_run=z_run, variant=variant)).export_dense()
+    assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
+
+
+@pytest.mark.parametrize("variant", [1, 3])
+@pytest.mark.parametrize("dmax", [2, 12, 20, 28, 36, 44])
+def test_variants_every_radius(variant, dmax):
+    """Brick radius R = 1..6 for both window variants."""
+    rs = np.random.default_rng(100 + dmax)
+    occ = (rs.random((44, 57, 66)) < 0.002).astype(np.uint8)
+    ref = O.edt_factorised(occ, dmax)
+    got = gpu_global(occ, dmax, tuning=dict(variant=variant)).export_dense()
     assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
 
 
@@ -192,3 +205,29 @@ def test_info_counts():
     fin = (ref < 256).reshape(8, 8, 8, 8, 8, 8).any(axis=(1, 3, 5))
     assert info["finite_bricks"] == int(fin.sum())
     assert info["error_bits"] == 0 and info["R"] == 2
+
+
+def test_sparse_records_take_the_radix_path():
+    """Few records in a large grid (fewer than a quarter of its bricks): brick keys go through the
+    LSD radix sort / unique / compaction path; includes duplicates and clears."""
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(21)
+    nx, ny, nz = 300, 260, 90  # 38 x 33 x 12 = 15048 bricks
+    n = 1500
+    xyz = np.stack([rs.integers(0, nx, n), rs.integers(0, ny, n), rs.integers(0, nz, n)], 1).astype(np.int32)
+    xyz = np.concatenate([xyz, xyz[:300]])
+    val = np.ones(len(xyz), np.uint8)
+    val[1500:1400 + 300] = 0  # later clears of earlier sets
+    occ = np.zeros((nz, ny, nx), np.uint8)
+    for k in range(len(val)):
+        occ[xyz[k, 2], xyz[k, 1], xyz[k, 0]] = val[k]
+    m = V.Map(nx, ny, nz, 11)
+    m.set_occupancy(xyz, val)
+    m.global_()
+    ref = O.edt_factorised(occ, 11)
+    got = m.export_dense()
+    assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
+    single = np.zeros((nz, ny, nx), np.uint8)
+    single[45, 130, 150] = 1
+    got = gpu_global(single, 40).export_dense()
+    assert first_mismatch(got, O.edt_factorised(single, 40)) is None

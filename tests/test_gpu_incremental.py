@@ -116,3 +116,28 @@ def test_update_before_any_global_and_after_dense():
     st = m.update(stats=True)
     assert st["net_flips"] == 0 and st["z_items"] == 0
     assert np.array_equal(m.export_dense(), O.edt_factorised(occ2, 6))
+
+
+def test_small_frames_in_large_grid():
+    """Frames of a few hundred records in a 320 x 300 x 96 grid: the incremental ingest takes the
+    radix-sort path and touches few bricks."""
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(3)
+    nx, ny, nz = 320, 300, 96
+    dmax = 24
+    occ = (rs.random((nz, ny, nx)) < 0.0005).astype(np.uint8)
+    m = V.Map(nx, ny, nz, dmax)
+    m.set_occupancy_dense(occ)
+    m.global_()
+    for f in range(5):
+        k = 200
+        xyz = np.stack([rs.integers(0, nx, k), rs.integers(0, ny, k), rs.integers(0, nz, k)], 1).astype(np.int32)
+        occ_xyz = coords_of(occ)
+        pick = occ_xyz[rs.integers(0, len(occ_xyz), 100)]
+        xyz = np.concatenate([xyz, pick])
+        val = np.concatenate([np.ones(k, np.uint8), np.zeros(100, np.uint8)])
+        apply_records(occ, xyz, val)
+        m.set_occupancy(xyz, val)
+        st = m.update(stats=True)
+        ref = O.edt_factorised(occ, dmax)
+        assert first_mismatch(m.export_dense(), ref) is None, (f, st)
