@@ -160,8 +160,8 @@ Tuning effective_tuning(const vdbedt_map* h) {
   return t;
 }
 
-vdbedt_status run_passes(vdbedt_map* h, const Tuning& t) {
-  if (half_path(h->g)) CK(h, launch_item_slots(h->g, t, h->items, h->st), "item slots");
+vdbedt_status run_passes(vdbedt_map* h, const Tuning& t, bool need_slots) {
+  if (need_slots && half_path(h->g)) CK(h, launch_item_slots(h->g, t, h->items, h->st), "item slots");
   mark(h, 3);
   CK(h, launch_pass(h->g, t, 0, h->items, h->st), "x pass");
   mark(h, 4);
@@ -186,8 +186,8 @@ vdbedt_status do_global(vdbedt_map* h) {
   mark(h, 1);
   CK(h, launch_activation_full(h->g, h->st), "activation");
   mark(h, 2);
-  CK(h, launch_build_items_full(h->g, t, h->epoch, h->items, h->st), "items");
-  vdbedt_status s = run_passes(h, t);
+  CK(h, launch_build_items_full(h->g, t, h->epoch, h->items, half_path(h->g), h->st), "items");
+  vdbedt_status s = run_passes(h, t, false);
   if (s) return s;
   h->computed = true;
   return VDBEDT_OK;
@@ -401,7 +401,7 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     mark(h, 1);
     CK(h, launch_incremental_mark(h->g, t, h->epoch, h->changed, h->items, h->st), "mark");
     mark(h, 2);
-    s = run_passes(h, t);
+    s = run_passes(h, t, true);
     if (s) return s;
   }
   if (stats) {
@@ -602,7 +602,7 @@ __global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* _
 cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, int nx, int ny, int nz, int4* dst,
                                 int32_t* invalid, cudaStream_t st) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * 64) b = 152 * 64;
+  if (b > 152 * 16) b = 152 * 16;
   if (b < 1) b = 1;
   VDB_LAUNCH(k_pack_records, (unsigned)b, 256, 0, st, xyz, occ, n, nx, ny, nz, dst, invalid);
   return cudaGetLastError();

@@ -21,10 +21,11 @@ namespace {
 
 constexpr int kT = 256;
 
+// Grid of a grid-stride kernel over n items: enough blocks to fill the GPU a few times over.
 inline unsigned blocks_for(int64_t n, int t = kT) {
   int64_t b = (n + t - 1) / t;
   if (b < 1) b = 1;
-  if (b > (1 << 30)) b = 1 << 30;
+  if (b > 152 * 16) b = 152 * 16;
   return (unsigned)b;
 }
 
@@ -55,17 +56,6 @@ __global__ void k_reset_nodes(GridView g) {
 }
 
 // ---- brick allocation ----
-__device__ __forceinline__ int warp_agg_add(int* ctr, bool pred) {
-  const unsigned act = __activemask();
-  const unsigned m = __ballot_sync(act, pred);
-  if (!m) return -1;
-  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(ctr, __popc(m));
-  base = __shfl_sync(act, base, leader);
-  return pred ? base + __popc(m & ((1u << lane) - 1u)) : -1;
-}
-
 // Fill a freshly allocated brick: empty occupancy, coordinates, flags; with `init_fields` also
 // g2 and D at dmax^2 (bricks added by an incremental update may be read before a pass writes them).
 __device__ void init_brick(const GridView& g, int slot, int node, int bx, int by, int bz, bool init_fields) {
@@ -106,8 +96,7 @@ __device__ int claim_brick(const GridView& g, int node, int bx, int by, int bz, 
     return -1;  // entry stays "claiming": reads treat it as absent
   }
   init_brick(g, slot, node, bx, by, bz, init_fields);
-  __threadfence();
-  atomicExch(e, slot);
+  atomicExch(e, slot);  // brick data is read by later kernels only: the kernel boundary orders it
   *created = true;
   return slot;
 }
@@ -124,75 +113,111 @@ __device__ __forceinline__ bool rec_valid(const GridView& g, int4 r) {
          (unsigned)r.w <= 1u;
 }
 
-__global__ void k_rec_brick_keys(GridView g, const int4* __restrict__ rec, int64_t n, uint32_t* __restrict__ keys) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  uint32_t key = 0xFFFFFFFFu;
-  bool zero = false, bad = false;
-  if (i < n) {
-    int4 r = rec[i];
-    if (!rec_valid(g, r)) {
-      bad = true;
-    } else if (r.w == 1) {
-      key = (uint32_t)((r.x >> 3) + g.BX * ((r.y >> 3) + g.BY * (r.z >> 3)));
-    } else {
-      zero = true;
+// Block-wide aggregation: every thread of the block calls it; returns base + the thread's rank
+// among the threads with `pred` (-1 without), after one atomicAdd of the block's total on ctr.
+__device__ int block_agg_add(int* ctr, bool pred, int* block_total) {
+  __shared__ int wsum[32];
+  __shared__ int base_sh, tot_sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, pred);
+  if (lane == 0) wsum[warp] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int c = wsum[w];
+      wsum[w] = t;
+      t += c;
     }
+    tot_sh = t;
+    base_sh = t ? atomicAdd(ctr, t) : 0;
   }
-  // drop a key equal to the previous lane's (records of one brick tend to be adjacent)
-  uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-  if (lane > 0 && prev == key) key = 0xFFFFFFFFu;
-  if (i < n) keys[i] = key;
-  if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
-  if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+  __syncthreads();
+  const int r = pred ? base_sh + wsum[warp] + __popc(bal & ((1u << lane) - 1u)) : -1;
+  if (block_total) *block_total = tot_sh;
+  __syncthreads();
+  return r;
+}
+
+// Grid-stride loops below keep every warp iterating together (the index base is block-uniform),
+// so warp-wide votes and shuffles inside the loop see all 32 lanes.
+#define GRID_STRIDE(i, n)                                                                              \
+  for (int64_t i##_base = (int64_t)blockIdx.x * blockDim.x, i = i##_base + threadIdx.x; i##_base < (n); \
+       i##_base += (int64_t)gridDim.x * blockDim.x, i = i##_base + threadIdx.x)
+
+__global__ void k_rec_brick_keys(GridView g, const int4* __restrict__ rec, int64_t n, uint32_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  GRID_STRIDE(i, n) {
+    uint32_t key = 0xFFFFFFFFu;
+    bool zero = false, bad = false;
+    if (i < n) {
+      int4 r = rec[i];
+      if (!rec_valid(g, r)) {
+        bad = true;
+      } else if (r.w == 1) {
+        key = (uint32_t)((r.x >> 3) + g.BX * ((r.y >> 3) + g.BY * (r.z >> 3)));
+      } else {
+        zero = true;
+      }
+    }
+    // drop a key equal to the previous lane's (records of one brick tend to be adjacent)
+    uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    if (lane > 0 && prev == key) key = 0xFFFFFFFFu;
+    if (i < n) keys[i] = key;
+    if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+  }
 }
 
 // Many records: bucket the brick keys of "set" records through one flag per brick of the grid
 // (a counting sort on the brick key); the compaction of the flags is the sorted unique key list.
 __global__ void k_mark_record_bricks(GridView g, const int4* __restrict__ rec, int64_t n, int32_t* __restrict__ flag) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  bool zero = false, bad = false;
-  if (i < n) {
-    int4 r = rec[i];
-    if (!rec_valid(g, r)) {
-      bad = true;
-    } else if (r.w == 1) {
-      int64_t lb = (r.x >> 3) + (int64_t)g.BX * ((r.y >> 3) + (int64_t)g.BY * (r.z >> 3));
-      if (!flag[lb]) flag[lb] = 1;
-    } else {
-      zero = true;
+  GRID_STRIDE(i, n) {
+    bool zero = false, bad = false;
+    if (i < n) {
+      int4 r = rec[i];
+      if (!rec_valid(g, r)) {
+        bad = true;
+      } else if (r.w == 1) {
+        int64_t lb = (r.x >> 3) + (int64_t)g.BX * ((r.y >> 3) + (int64_t)g.BY * (r.z >> 3));
+        if (!flag[lb]) flag[lb] = 1;
+      } else {
+        zero = true;
+      }
     }
+    if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
   }
-  if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
-  if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
 }
 
 __global__ void k_compact_flag_index(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t n,
                                      uint32_t* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && flag[i]) out[pos[i]] = (uint32_t)i;
+  GRID_STRIDE(i, n) {
+    if (i < n && flag[i]) out[pos[i]] = (uint32_t)i;
+  }
 }
 
 __global__ void k_head_flags(const uint32_t* __restrict__ keys, int64_t n, uint32_t limit, int32_t* __restrict__ flag) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t k = keys[i];
-  flag[i] = (k < limit && (i == 0 || keys[i - 1] != k)) ? 1 : 0;
+  GRID_STRIDE(i, n) {
+    if (i < n) {
+      uint32_t k = keys[i];
+      flag[i] = (k < limit && (i == 0 || keys[i - 1] != k)) ? 1 : 0;
+    }
+  }
 }
 
 __global__ void k_compact_keys(const uint32_t* __restrict__ keys, const int32_t* __restrict__ flag,
                                const int32_t* __restrict__ pos, int64_t n, uint32_t* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && flag[i]) out[pos[i]] = keys[i];
+  GRID_STRIDE(i, n) {
+    if (i < n && flag[i]) out[pos[i]] = keys[i];
+  }
 }
 
+// Bricks of the unique keys: node found or inserted, slot reserved with one atomic per block.
 __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__ uniq, int64_t n, bool init) {
   const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], n);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t rounds = (cnt + stride - 1) / stride;
-  for (int64_t r = 0; r < rounds; ++r) {
-    const int64_t j = r * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  GRID_STRIDE(j, cnt) {
     int bx = 0, by = 0, bz = 0, node = -1;
     int* e = nullptr;
     bool need = false;
@@ -208,64 +233,68 @@ __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__
         need = *e == kNoSlot;
       }
     }
-    int slot = warp_agg_add(&g.counters[C_NBRICKS], need);
+    int total = 0;
+    const int slot = block_agg_add(&g.counters[C_NBRICKS], need, &total);
     if (need) {
       if (slot >= g.cap) {
         set_error(g, kErrOverflow);
       } else {
         init_brick(g, slot, node, bx, by, bz, init);
-        __threadfence();
         *e = slot;
       }
     }
-    unsigned m = __ballot_sync(0xffffffffu, need && slot < g.cap);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&g.counters[C_NEW_BRICKS], __popc(m));
+    if (threadIdx.x == 0 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
   }
 }
 
-// All records set voxels: OR the bits in, combining lanes that hit the same 64-bit word.
+// All records set voxels: OR the bits in.  Adjacent lanes that hit the same 64-bit word (records
+// of one x-row usually sit next to each other) are merged by a segmented OR over the warp, and the
+// last lane of each segment issues the atomic.
 __global__ void k_apply_set_only(GridView g, const int4* __restrict__ rec, int64_t n) {
   if (g.counters[C_HAS_ZERO]) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long* word = nullptr;
-  uint32_t lo = 0, hi = 0;
-  if (i < n) {
-    int4 r = rec[i];
-    if (rec_valid(g, r) && r.w == 1) {
-      int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
-      if (s >= 0) {
-        word = &g.occ[(size_t)s * 8 + (r.z & 7)];
-        int bit = (r.x & 7) + 8 * (r.y & 7);
-        if (bit < 32)
-          lo = 1u << bit;
-        else
-          hi = 1u << (bit - 32);
+  const int lane = threadIdx.x & 31;
+  GRID_STRIDE(i, n) {
+    unsigned long long word = 0ull;  // address of the target word, 0 for none
+    unsigned long long bits = 0ull;
+    if (i < n) {
+      int4 r = rec[i];
+      if (rec_valid(g, r) && r.w == 1) {
+        int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
+        if (s >= 0) {
+          word = (unsigned long long)(&g.occ[(size_t)s * 8 + (r.z & 7)]);
+          bits = 1ull << ((r.x & 7) + 8 * (r.y & 7));
+        }
       }
     }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long wp = __shfl_up_sync(0xffffffffu, word, o);
+      const unsigned long long bp = __shfl_up_sync(0xffffffffu, bits, o);
+      if (lane >= o && wp == word) bits |= bp;
+    }
+    const unsigned long long wn = __shfl_down_sync(0xffffffffu, word, 1);
+    if (word && (lane == 31 || wn != word)) atomicOr(reinterpret_cast<unsigned long long*>(word), bits);
   }
-  unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)word);
-  lo = __reduce_or_sync(peers, lo);
-  hi = __reduce_or_sync(peers, hi);
-  if (word && (threadIdx.x & 31) == __ffs(peers) - 1)
-    atomicOr(word, (unsigned long long)lo | ((unsigned long long)hi << 32));
 }
 
 // (voxel key, record index) for the ordered path: voxel key = slot * 512 + voxel in brick.
 __global__ void k_rec_voxel_keys(GridView g, const int4* __restrict__ rec, int64_t n, bool force,
                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   const bool on = force || g.counters[C_HAS_ZERO];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) g.counters[C_RECORDS] = on ? (int32_t)n : 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_RECORDS] = on ? (int32_t)n : 0;
   if (!on) return;
-  if (i >= n) return;
-  uint32_t key = 0xFFFFFFFFu;
-  int4 r = rec[i];
-  if (rec_valid(g, r)) {
-    int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
-    if (s >= 0) key = (uint32_t)s * 512u + (uint32_t)((r.x & 7) + 8 * (r.y & 7) + 64 * (r.z & 7));
+  GRID_STRIDE(i, n) {
+    if (i < n) {
+      uint32_t key = 0xFFFFFFFFu;
+      int4 r = rec[i];
+      if (rec_valid(g, r)) {
+        int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
+        if (s >= 0) key = (uint32_t)s * 512u + (uint32_t)((r.x & 7) + 8 * (r.y & 7) + 64 * (r.z & 7));
+      }
+      keys[i] = key;
+      idx[i] = (uint32_t)i;
+    }
   }
-  keys[i] = key;
-  idx[i] = (uint32_t)i;
 }
 
 // The last record of each voxel decides its bit.  Flips are counted; with `track` the brick is
@@ -274,29 +303,30 @@ __global__ void k_apply_last(GridView g, const int4* __restrict__ rec, const uin
                              const uint32_t* __restrict__ idx, int64_t n, bool force, bool track, int epoch,
                              int32_t* __restrict__ changed) {
   if (!force && !g.counters[C_HAS_ZERO]) return;
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool flip = false;
-  if (j < n) {
-    uint32_t k = keys[j];
-    const uint32_t lim = (uint32_t)g.cap * 512u;
-    if (k < lim && (j + 1 == n || keys[j + 1] != k)) {
-      int4 r = rec[idx[j]];
-      int s = (int)(k >> 9), v = (int)(k & 511);
-      unsigned long long bit = 1ull << (v & 63);
-      unsigned long long* word = &g.occ[(size_t)s * 8 + (v >> 6)];
-      bool cur = (*word & bit) != 0ull;
-      if (cur != (r.w == 1)) {
-        atomicXor(word, bit);
-        flip = true;
-        if (track && atomicExch(&g.bepoch[s], epoch) != epoch) {
-          int p = atomicAdd(&g.counters[C_CHANGED], 1);
-          changed[p] = s;
+  GRID_STRIDE(j, n) {
+    bool flip = false;
+    if (j < n) {
+      uint32_t k = keys[j];
+      const uint32_t lim = (uint32_t)g.cap * 512u;
+      if (k < lim && (j + 1 == n || keys[j + 1] != k)) {
+        int4 r = rec[idx[j]];
+        int s = (int)(k >> 9), v = (int)(k & 511);
+        unsigned long long bit = 1ull << (v & 63);
+        unsigned long long* word = &g.occ[(size_t)s * 8 + (v >> 6)];
+        bool cur = (*word & bit) != 0ull;
+        if (cur != (r.w == 1)) {
+          atomicXor(word, bit);
+          flip = true;
+          if (track && atomicExch(&g.bepoch[s], epoch) != epoch) {
+            int p = atomicAdd(&g.counters[C_CHANGED], 1);
+            changed[p] = s;
+          }
         }
       }
     }
+    unsigned m = __ballot_sync(0xffffffffu, flip);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&g.counters[C_FLIPS], __popc(m));
   }
-  unsigned m = __ballot_sync(0xffffffffu, flip);
-  if ((threadIdx.x & 31) == 0 && m) atomicAdd(&g.counters[C_FLIPS], __popc(m));
 }
 
 // ---- dense ingest ----
@@ -487,67 +517,42 @@ __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int
   }
 }
 
-// Allocate every marked brick without storage: one block per node, 16 bricks per thread, one
-// atomic per block for the slot range (block scan of the per-thread counts).
+// Allocate every marked brick without storage: a block per (node, 512-brick chunk), two bricks
+// per thread, one atomic per block for the slot range (block scan of the per-thread counts).
 __global__ void __launch_bounds__(256) k_alloc_marked(GridView g, bool init_fields) {
-  __shared__ int wsum[8];
-  __shared__ int base_sh;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int node = blockIdx.x; node < nn; node += gridDim.x) {
-    const int l0 = threadIdx.x * 16;
-    const uint32_t bits = (g.amask[(size_t)node * 128 + (threadIdx.x >> 1)] >> (16 * (threadIdx.x & 1))) & 0xFFFFu;
-    uint32_t need = 0u;
-    if (bits) {
-      const int4* ch = reinterpret_cast<const int4*>(g.child + (size_t)node * kNodeBricks + l0);
+  for (int b = blockIdx.x; b < nn * 8; b += gridDim.x) {
+    const int node = b >> 3, chunk = b & 7;
+    const int l0 = chunk * 512 + threadIdx.x * 2;
+    const uint32_t word = g.amask[(size_t)node * 128 + (l0 >> 5)];
+    bool need[2];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int4 c = ch[q];
-        int cc[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (((bits >> (4 * q + k)) & 1u) && cc[k] == kNoSlot) need |= 1u << (4 * q + k);
-      }
-    }
-    int cnt = __popc(need);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int tot = 0;
-      for (int w = 0; w < 8; ++w) {
-        int t = wsum[w];
-        wsum[w] = tot;
-        tot += t;
-      }
-      base_sh = tot ? atomicAdd(&g.counters[C_NBRICKS], tot) : 0;
-      if (tot) atomicAdd(&g.counters[C_NEW_BRICKS], tot);
-    }
-    __syncthreads();
-    int slot = base_sh + wsum[warp] + incl - cnt;
-    if (need) {
+    for (int k = 0; k < 2; ++k)
+      need[k] = ((word >> ((l0 + k) & 31)) & 1u) && g.child[(size_t)node * kNodeBricks + l0 + k] == kNoSlot;
+    const int cnt = (int)need[0] + (int)need[1];
+    // block scan of cnt (0..2): two predicates in sequence keep block_agg_add's contract
+    int total0 = 0, total1 = 0;
+    const int s0 = block_agg_add(&g.counters[C_NBRICKS], need[0], &total0);
+    const int s1 = block_agg_add(&g.counters[C_NBRICKS], need[1], &total1);
+    (void)cnt;
+    if (threadIdx.x == 0 && total0 + total1) atomicAdd(&g.counters[C_NEW_BRICKS], total0 + total1);
+    if (need[0] || need[1]) {
       const int key = g.node_key[node];
       const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
-      for (int k = 0; k < 16; ++k) {
-        if (!((need >> k) & 1u)) continue;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (!need[k]) continue;
+        const int slot = k ? s1 : s0;
         const int l = l0 + k;
         if (slot >= g.cap) {
           set_error(g, kErrOverflow);
         } else {
           init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8),
                      init_fields);
-          __threadfence();
           g.child[(size_t)node * kNodeBricks + l] = slot;
         }
-        ++slot;
       }
     }
-    __syncthreads();
   }
 }
 
@@ -567,13 +572,100 @@ __device__ __forceinline__ void queue_run(const GridView& g, int axis, int bx, i
   }
 }
 
-__global__ void k_items_all(GridView g, int rx, int ry, int rz, int epoch, Items it) {
-  const int nb = min(g.counters[C_NBRICKS], g.cap);
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
-    int4 c = g.bcoord[s];
-    queue_run(g, 0, c.x, c.y, c.z, c.w, rx, epoch, it.run[0]);
-    queue_run(g, 1, c.x, c.y, c.z, c.w, ry, epoch, it.run[1]);
-    queue_run(g, 2, c.x, c.y, c.z, c.w, rz, epoch, it.run[2]);
+// Global form: every run that holds a stored brick, found node by node.  Block = (node, axis, run
+// index along the axis); its 256 threads cover the 16 x 16 lines of the node across the axis.  A
+// block-wide scan compacts the runs and one atomic reserves their places; the run slot lists are
+// then read straight from the child tables of the node and of its neighbour along the axis
+// (R <= 6 < 16, so the halo reaches at most one node each way), one slot per thread.
+__global__ void __launch_bounds__(256) k_items_nodes(GridView g, int rx, int ry, int rz, Items it, bool with_slots) {
+  __shared__ int wsum[8];
+  __shared__ int base_sh, count_sh;
+  __shared__ int nbr_sh[2];
+  __shared__ unsigned char lines[256];
+  const int nn = min(g.counters[C_NNODES], g.node_cap);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int R = g.R;
+  for (int b = blockIdx.x; b < nn * 12; b += gridDim.x) {
+    const int node = b / 12, axis = (b % 12) / 4, qrun = b % 4;
+    const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
+    if (qrun >= 16 / run) continue;  // block-uniform
+    const int key = g.node_key[node];
+    const int q[3] = {key % g.NX, (key / g.NX) % g.NY, key / (g.NX * g.NY)};
+    const int32_t* ch = g.child + (size_t)node * kNodeBricks;
+    const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+    const int r0 = qrun * run, nb = run + 2 * R;
+    if (threadIdx.x < 2) {
+      int qq[3] = {q[0], q[1], q[2]};
+      qq[axis] += threadIdx.x == 0 ? -1 : 1;
+      int n2 = -1;
+      if (qq[0] >= 0 && qq[1] >= 0 && qq[2] >= 0 && qq[0] < g.NX && qq[1] < g.NY && qq[2] < g.NZ)
+        n2 = find_node(g, (uint32_t)(qq[0] + g.NX * (qq[1] + g.NY * qq[2])));
+      nbr_sh[threadIdx.x] = n2;
+    }
+    const int o1 = threadIdx.x & 15, o2 = threadIdx.x >> 4;
+    bool any = false;
+    for (int j = 0; j < run; ++j) {
+      int l[3];
+      l[axis] = r0 + j;
+      l[a1] = o1;
+      l[a2] = o2;
+      any |= ch[local_brick(l[0], l[1], l[2])] >= 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, any);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < 8; ++w) {
+        const int t = wsum[w];
+        wsum[w] = tot;
+        tot += t;
+      }
+      count_sh = tot;
+      base_sh = tot ? atomicAdd(&g.counters[items_counter(axis)], tot) : 0;
+    }
+    __syncthreads();
+    const int base = base_sh, cnt = count_sh;
+    if (any) {
+      const int pos = wsum[warp] + __popc(bal & ((1u << lane) - 1u));
+      lines[pos] = (unsigned char)threadIdx.x;
+      const int p = base + pos;
+      if (p < g.cap) {
+        int l0[3];
+        l0[axis] = r0;
+        l0[a1] = o1;
+        l0[a2] = o2;
+        it.run[axis][p] = pack_brick(q[0] * 16 + l0[0], q[1] * 16 + l0[1], q[2] * 16 + l0[2]);
+      }
+    }
+    __syncthreads();
+    if (with_slots) {
+      for (int idx = threadIdx.x; idx < cnt * nb; idx += 256) {
+        const int i = idx / nb, j = idx % nb;
+        const int p = base + i;
+        if (p >= g.cap) continue;
+        const int line = lines[i];
+        int l[3];
+        l[a1] = line & 15;
+        l[a2] = line >> 4;
+        int c = r0 + j - R, src = node;
+        if (c < 0) {
+          c += 16;
+          src = nbr_sh[0];
+        } else if (c >= 16) {
+          c -= 16;
+          src = nbr_sh[1];
+        }
+        l[axis] = c;
+        int sv = -1;
+        if (src >= 0) {
+          sv = g.child[(size_t)src * kNodeBricks + local_brick(l[0], l[1], l[2])];
+          if (sv < 0) sv = -1;
+        }
+        it.slots[axis][(size_t)p * kItemSlots + j] = sv;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -710,20 +802,25 @@ cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n,
     // LSD radix sort of the brick keys, unique, compaction
     VDB_LAUNCH(k_rec_brick_keys, nbk, kT, 0, st, g, rec, n, ka);
     // the sentinel 0xFFFFFFFF sorts after every key below 2^bits
-    e = radix_sort_u32(ka, kb, nullptr, nullptr, n, nullptr, bits_for(nbr), rtemp, st);
+    bool in_b = false;
+    e = radix_sort_u32(ka, kb, nullptr, nullptr, n, nullptr, bits_for(nbr), rtemp, st, &in_b);
     if (e != cudaSuccess) return e;
-    VDB_LAUNCH(k_head_flags, nbk, kT, 0, st, kb, n, (uint32_t)nbr, flag);
+    uint32_t* sorted = in_b ? kb : ka;
+    uint32_t* uniq = in_b ? ka : kb;
+    VDB_LAUNCH(k_head_flags, nbk, kT, 0, st, sorted, n, (uint32_t)nbr, flag);
     e = exclusive_scan_i32(flag, pos, n, g.counters + C_UNIQUE, stemp, st);
     if (e != cudaSuccess) return e;
-    VDB_LAUNCH(k_compact_keys, nbk, kT, 0, st, kb, flag, pos, n, ka);
-    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, ka, n, track);
+    VDB_LAUNCH(k_compact_keys, nbk, kT, 0, st, sorted, flag, pos, n, uniq);
+    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, uniq, n, track);
   }
   if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n);
   // ordered path; its element count is 0 on the device when it is not needed
   VDB_LAUNCH(k_rec_voxel_keys, nbk, kT, 0, st, g, rec, n, track, ka, va);
-  e = radix_sort_u32(ka, kb, va, vb, n, g.counters + C_RECORDS, bits_for((uint64_t)g.cap * 512ull), rtemp, st);
+  bool in_b = false;
+  e = radix_sort_u32(ka, kb, va, vb, n, g.counters + C_RECORDS, bits_for((uint64_t)g.cap * 512ull), rtemp, st,
+                     &in_b);
   if (e != cudaSuccess) return e;
-  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, kb, vb, n, track, track, epoch, changed);
+  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, in_b ? kb : ka, in_b ? vb : va, n, track, track, epoch, changed);
   return cudaGetLastError();
 }
 
@@ -743,7 +840,7 @@ cudaError_t launch_activation_full(const GridView& g, cudaStream_t st) {
   VDB_LAUNCH(k_dilate_stage<0>, 256, kT, 0, st, g);
   VDB_LAUNCH(k_dilate_stage<1>, 256, kT, 0, st, g);
   VDB_LAUNCH(k_dilate_stage<2>, 256, kT, 0, st, g);
-  VDB_LAUNCH(k_alloc_marked, 1024, kT, 0, st, g, false);
+  VDB_LAUNCH(k_alloc_marked, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, g, false);
   return cudaGetLastError();
 }
 
@@ -753,10 +850,13 @@ static cudaError_t clear_item_counters(const GridView& g, cudaStream_t st) {
   return cudaMemsetAsync(g.counters + C_X_ITEMS, 0, sizeof(int32_t), st);
 }
 
-cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, const Items& it, cudaStream_t st) {
+cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, const Items& it, bool with_slots,
+                                    cudaStream_t st) {
+  (void)epoch;
   cudaError_t e = clear_item_counters(g, st);
   if (e != cudaSuccess) return e;
-  VDB_LAUNCH(k_items_all, 1024, kT, 0, st, g, t.run[0], t.run[1], t.run[2], epoch, it);
+  VDB_LAUNCH(k_items_nodes, g.node_cap * 12 < 8192 ? g.node_cap * 12 : 8192, kT, 0, st, g, t.run[0], t.run[1],
+             t.run[2], it, with_slots);
   return cudaGetLastError();
 }
 
@@ -771,7 +871,7 @@ cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, int epoc
   cudaError_t e = clear_item_counters(g, st);
   if (e != cudaSuccess) return e;
   VDB_LAUNCH(k_changed_flags_dilate, 1024, kT, 0, st, g, changed);
-  VDB_LAUNCH(k_alloc_marked, 1024, kT, 0, st, g, true);
+  VDB_LAUNCH(k_alloc_marked, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, g, true);
   VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.run[0], t.run[1], t.run[2], epoch, it);
   return cudaGetLastError();
 }

@@ -138,14 +138,11 @@ __device__ __forceinline__ void window_min8(const uint32_t (&v)[8 + 2 * W], uint
   for (int k = 0; k < 8; ++k) out[k] = h2u(acc[k]);
 }
 
-__device__ __forceinline__ int floor16(int v) { return v >= 0 ? (v >> 4) : -((15 - v) >> 4); }
-
 // ================================================================================================
 // The three passes: warp-specialised kernel with a bulk-copy ring
 // ================================================================================================
 template <int R, int RUN, int AXIS>
 struct ColShape {
-  static constexpr int W = 8 * R;
   static constexpr int NB = RUN + 2 * R;                     // staged bricks per item
   static constexpr int NS = 3;                               // ring stages
   static constexpr int UNIT = AXIS == 0 ? 64 : 1024;         // bytes staged per brick
@@ -159,54 +156,98 @@ struct ColShape {
 
 // x pass of one brick from the staged masks of bricks w .. w + 2R (64 B each; byte y + 8 z is the
 // x-row (y, z)).  Lane: z = lane & 7, rows y0 = 2 (lane >> 3) and y0 + 1.  g1 is stored y-major.
+// For dmax <= 32 (and R <= 4) a distance of 32 or more is already saturated, so each voxel needs
+// only the 32 line bits on either side: two funnel shifts of 32-bit words and a count of leading
+// zeros (left) and of trailing zeros (right).  Otherwise the 64-bit form covers the whole line.
 template <int R>
 __device__ __forceinline__ void x_compute(const GridView& g, const uint8_t* masks, int slot, uint32_t inf2) {
   constexpr int NBX = 2 * R + 1;
   const int lane = threadIdx.x & 31;
   const int z = lane & 7, y0 = (lane >> 3) * 2;
-  unsigned long long lo[2] = {0ull, 0ull}, hi[2] = {0ull, 0ull};
+  bool fin = false;
+  uint32_t w[2][4];
+  bool done = false;
+  if constexpr (R <= 4) {
+    if (g.dmax <= 32) {
+      // E[r][1 + k] holds line bits 32k .. 32k + 31; E[r][0] = 0 stands for positions -32 .. -1
+      uint32_t E[2][5] = {{0u, 0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u, 0u}};
 #pragma unroll
-  for (int b = 0; b < NBX; ++b) {
-    const uint32_t two = *reinterpret_cast<const uint16_t*>(masks + b * 64 + y0 + 8 * z);
+      for (int b = 0; b < NBX; ++b) {
+        const uint32_t two = *reinterpret_cast<const uint16_t*>(masks + b * 64 + y0 + 8 * z);
+        E[0][1 + b / 4] |= (two & 0xFFu) << (8 * (b % 4));
+        E[1][1 + b / 4] |= (two >> 8) << (8 * (b % 4));
+      }
+      const int inf = g.INF;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if ((E[r][1] | E[r][2] | E[r][3]) == 0u) {
+          w[r][0] = w[r][1] = w[r][2] = w[r][3] = inf2;
+          continue;
+        }
+        __half hv[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          const int P = 8 * R + x + 32;  // position in E
+          const int s0 = P - 31;
+          const uint32_t Lw = __funnelshift_r(E[r][s0 >> 5], E[r][(s0 >> 5) + 1], s0 & 31);  // bit 31 = P
+          const uint32_t Rw = __funnelshift_r(E[r][P >> 5], E[r][(P >> 5) + 1], P & 31);      // bit 0 = P
+          const int d = min(__clz(Lw), __clz(__brev(Rw)));  // 32 when the side is empty
+          const int best = min(d * d, inf);
+          fin |= best < inf;
+          hv[x] = __int2half_rn(best);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[r][q] = h2u(__halves2half2(hv[2 * q], hv[2 * q + 1]));
+      }
+      done = true;
+    }
+  }
+  if (!done) {
+    unsigned long long lo[2] = {0ull, 0ull}, hi[2] = {0ull, 0ull};
+#pragma unroll
+    for (int b = 0; b < NBX; ++b) {
+      const uint32_t two = *reinterpret_cast<const uint16_t*>(masks + b * 64 + y0 + 8 * z);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const unsigned long long byte = (two >> (8 * r)) & 0xFFu;
+        if (b < 8)
+          lo[r] |= byte << (8 * b);
+        else
+          hi[r] |= byte << (8 * (b - 8));
+      }
+    }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      const unsigned long long byte = (two >> (8 * r)) & 0xFFu;
-      if (b < 8)
-        lo[r] |= byte << (8 * b);
-      else
-        hi[r] |= byte << (8 * (b - 8));
-    }
-  }
-  bool fin = false;
+      if ((lo[r] | hi[r]) == 0ull) {
+        w[r][0] = w[r][1] = w[r][2] = w[r][3] = inf2;
+      } else {
+        __half hv[8];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    uint32_t w[4];
-    if ((lo[r] | hi[r]) == 0ull) {
-      w[0] = w[1] = w[2] = w[3] = inf2;
-    } else {
-      __half hv[8];
+        for (int x = 0; x < 8; ++x) {
+          const int p = 8 * R + x;  // position of voxel x in the line (8 <= p < 64 for 1 <= R <= 6)
+          int best = g.INF;
+          const unsigned long long L = lo[r] & ((2ull << p) - 1ull);
+          if (L) {
+            const int dl = p - (63 - __clzll((long long)L));
+            best = min(best, dl * dl);
+          }
+          const unsigned long long Rm = (lo[r] >> p) | (hi[r] << (64 - p));
+          if (Rm) {
+            const int dr = __ffsll((long long)Rm) - 1;
+            best = min(best, dr * dr);
+          }
+          fin |= best < g.INF;
+          hv[x] = __int2half_rn(best);
+        }
 #pragma unroll
-      for (int x = 0; x < 8; ++x) {
-        const int p = 8 * R + x;  // position of voxel x in the line (8 <= p < 64 for 1 <= R <= 6)
-        int best = g.INF;
-        const unsigned long long L = lo[r] & ((2ull << p) - 1ull);
-        if (L) {
-          const int dl = p - (63 - __clzll((long long)L));
-          best = min(best, dl * dl);
-        }
-        const unsigned long long Rm = (lo[r] >> p) | (hi[r] << (64 - p));
-        if (Rm) {
-          const int dr = __ffsll((long long)Rm) - 1;
-          best = min(best, dr * dr);
-        }
-        fin |= best < g.INF;
-        hv[x] = __int2half_rn(best);
+        for (int q = 0; q < 4; ++q) w[r][q] = h2u(__halves2half2(hv[2 * q], hv[2 * q + 1]));
       }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) w[q] = h2u(__halves2half2(hv[2 * q], hv[2 * q + 1]));
     }
-    *reinterpret_cast<uint4*>(g.g1 + (size_t)slot * kBrickVox + (y0 + r) * 64 + z * 8) = make_uint4(w[0], w[1], w[2], w[3]);
   }
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+    *reinterpret_cast<uint4*>(g.g1 + (size_t)slot * kBrickVox + (y0 + r) * 64 + z * 8) =
+        make_uint4(w[r][0], w[r][1], w[r][2], w[r][3]);
   const unsigned anyfin = __any_sync(0xffffffffu, fin);
   if (lane == 0) g.bflags[slot] = anyfin ? (g.bflags[slot] | F_G1FIN) : (g.bflags[slot] & ~F_G1FIN);
 }

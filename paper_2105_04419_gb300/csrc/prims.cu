@@ -45,7 +45,9 @@ __device__ int block_excl_scan(int v, int* total) {
   return r;
 }
 
-__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ part) {
+__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ part,
+                              const int32_t* gate) {
+  if (gate && *gate == 0) return;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
   int s = 0;
 #pragma unroll
@@ -56,7 +58,8 @@ __global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int32_t
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_partials(int32_t* part, int64_t nb, int32_t* total) {
+__global__ void k_scan_partials(int32_t* part, int64_t nb, int32_t* total, const int32_t* gate) {
+  if (gate && *gate == 0) return;
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
@@ -74,7 +77,8 @@ __global__ void k_scan_partials(int32_t* part, int64_t nb, int32_t* total) {
 }
 
 __global__ void k_scan_down(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
-                            const int32_t* __restrict__ part) {
+                            const int32_t* __restrict__ part, const int32_t* gate) {
+  if (gate && *gate == 0) return;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
   int v[kScanPer];
   int s = 0;
@@ -106,11 +110,16 @@ __device__ __forceinline__ int64_t actual_count(int64_t n, const int32_t* count_
 
 __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, const int32_t* count_dev, int shift,
                              int32_t* __restrict__ hist, int nblocks) {
+  const int64_t cnt = actual_count(n, count_dev);
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (cnt == 0) return;  // the whole sort is idle (the scan and scatter check the same count)
+  if (base >= cnt) {
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = 0;
+    return;
+  }
   __shared__ int sh[256];
   sh[threadIdx.x] = 0;
   __syncthreads();
-  const int64_t cnt = actual_count(n, count_dev);
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
   for (int j = threadIdx.x; j < kSortTile; j += kSortThreads) {
     int64_t i = base + j;
     if (i < cnt) atomicAdd(&sh[(keys[i] >> shift) & 255], 1);
@@ -122,11 +131,12 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, const
 __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, uint32_t* __restrict__ kout,
                                 const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout, int64_t n,
                                 const int32_t* count_dev, int shift, const int32_t* __restrict__ offs, int nblocks) {
+  const int64_t total = actual_count(n, count_dev);
+  if ((int64_t)blockIdx.x * kSortTile >= total) return;  // block-uniform
   __shared__ int cnt[kSortWarps][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = threadIdx.x; j < kSortWarps * 256; j += kSortThreads) (&cnt[0][0])[j] = 0;
   __syncthreads();
-  const int64_t total = actual_count(n, count_dev);
   const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kSubTile;
   // phase A: per-warp digit counts
   for (int r = 0; r < kSubTile / 32; ++r) {
@@ -180,16 +190,16 @@ size_t scan_temp_bytes(int64_t n) {
 }
 
 cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total_dev, void* temp,
-                               cudaStream_t st) {
+                               cudaStream_t st, const int32_t* gate) {
   if (n <= 0) {
     if (total_dev) return cudaMemsetAsync(total_dev, 0, sizeof(int32_t), st);
     return cudaSuccess;
   }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   int32_t* part = (int32_t*)temp;
-  VDB_LAUNCH(k_scan_reduce, (unsigned)nb, kScanThreads, 0, st, in, n, part);
-  VDB_LAUNCH(k_scan_partials, 1, kScanThreads, 0, st, part, nb, total_dev);
-  VDB_LAUNCH(k_scan_down, (unsigned)nb, kScanThreads, 0, st, in, out, n, part);
+  VDB_LAUNCH(k_scan_reduce, (unsigned)nb, kScanThreads, 0, st, in, n, part, gate);
+  VDB_LAUNCH(k_scan_partials, 1, kScanThreads, 0, st, part, nb, total_dev, gate);
+  VDB_LAUNCH(k_scan_down, (unsigned)nb, kScanThreads, 0, st, in, out, n, part, gate);
   return cudaGetLastError();
 }
 
@@ -200,8 +210,9 @@ size_t radix_temp_bytes(int64_t n) {
   return 2 * hist + scan_temp_bytes(256 * nb) + 512;
 }
 
-cudaError_t radix_sort_u32(uint32_t* keys_in, uint32_t* keys_out, uint32_t* vals_in, uint32_t* vals_out, int64_t n,
-                           const int32_t* count_dev, int bits, void* temp, cudaStream_t st) {
+cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
+                           const int32_t* count_dev, int bits, void* temp, cudaStream_t st, bool* result_in_b) {
+  *result_in_b = false;
   if (n <= 0) return cudaSuccess;
   int64_t nb = (n + kSortTile - 1) / kSortTile;
   int32_t* hist = (int32_t*)temp;
@@ -209,23 +220,11 @@ cudaError_t radix_sort_u32(uint32_t* keys_in, uint32_t* keys_out, uint32_t* vals
   void* stemp = (void*)(offs + 256 * nb);
   int passes = (bits + 7) / 8;
   if (passes < 1) passes = 1;
-  // Ping-pong so that the final pass writes keys_out: with an even number of passes the first
-  // pass goes in -> out -> in ... ; copy in -> out first so the parity works out.
-  uint32_t *ka = keys_in, *kb = keys_out, *va = vals_in, *vb = vals_out;
-  if (passes % 2 == 0) {
-    cudaMemcpyAsync(kb, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
-    if (va) cudaMemcpyAsync(vb, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
-    uint32_t* t = ka;
-    ka = kb;
-    kb = t;
-    t = va;
-    va = vb;
-    vb = t;
-  }
+  uint32_t *ka = keys_a, *kb = keys_b, *va = vals_a, *vb = vals_b;
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
     VDB_LAUNCH(k_radix_hist, (unsigned)nb, kSortThreads, 0, st, ka, n, count_dev, shift, hist, (int)nb);
-    cudaError_t e = exclusive_scan_i32(hist, offs, 256 * nb, nullptr, stemp, st);
+    cudaError_t e = exclusive_scan_i32(hist, offs, 256 * nb, nullptr, stemp, st, count_dev);
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_radix_scatter, (unsigned)nb, kSortThreads, 0, st, ka, kb, va, vb, n, count_dev, shift, offs, (int)nb);
     uint32_t* t = ka;
@@ -235,6 +234,7 @@ cudaError_t radix_sort_u32(uint32_t* keys_in, uint32_t* keys_out, uint32_t* vals
     va = vb;
     vb = t;
   }
+  *result_in_b = (passes & 1) != 0;
   return cudaGetLastError();
 }
 

@@ -216,14 +216,16 @@ struct Items {
 
 // primitives (prims.cu)
 size_t scan_temp_bytes(int64_t n);
+// gate (nullable): a device count; when it is 0 the scan does nothing
 cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total_dev, void* temp,
-                               cudaStream_t st);
+                               cudaStream_t st, const int32_t* gate = nullptr);
 size_t radix_temp_bytes(int64_t n);
-// Stable LSD radix sort of u32 keys (with optional u32 values) on the low `bits` bits.  n is an
-// upper bound; count_dev (nullable) holds the actual count on the device.  Results land in
-// keys_out / vals_out.  keys_in / vals_in are clobbered.
-cudaError_t radix_sort_u32(uint32_t* keys_in, uint32_t* keys_out, uint32_t* vals_in, uint32_t* vals_out,
-                           int64_t n, const int32_t* count_dev, int bits, void* temp, cudaStream_t st);
+// Stable LSD radix sort of u32 keys (with optional u32 values) on the low `bits` bits, ping-ponging
+// between the a and b buffers (input in a).  n is an upper bound; count_dev (nullable) holds the
+// actual count on the device (0: every kernel of the sort returns at once).  *result_in_b tells
+// which buffer holds the sorted data.
+cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
+                           const int32_t* count_dev, int bits, void* temp, cudaStream_t st, bool* result_in_b);
 
 // grid build (grid.cu)
 struct Staging {
@@ -242,7 +244,9 @@ cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n,
                                   int32_t* changed, Scratch& scr, cudaStream_t st);
 cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st);
 cudaError_t launch_activation_full(const GridView& g, cudaStream_t st);
-cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, const Items& it, cudaStream_t st);
+// every run holding a stored brick, with slot lists when with_slots (half path)
+cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, const Items& it, bool with_slots,
+                                    cudaStream_t st);
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, int epoch, const int32_t* changed,
                                     const Items& it, cudaStream_t st);
 // slot lists of every queued run (half path)
