@@ -17,7 +17,7 @@ using namespace vdbedt;
 namespace vdbedt {
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, int nx, int ny, int nz, int4* dst,
+cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, int nx, int ny, int nz, rec_t* dst,
                                 int32_t* invalid, cudaStream_t st);
 }
 
@@ -30,7 +30,7 @@ struct vdbedt_map {
   std::vector<void*> allocs;
   size_t device_bytes = 0;
   // staged records
-  int4* stage = nullptr;
+  rec_t* stage = nullptr;
   int64_t stage_n = 0, stage_cap = 0;
   bool dense_pending = false;
   bool computed = false;
@@ -134,11 +134,11 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 vdbedt_status ensure_stage(vdbedt_map* h, int64_t need) {
   if (need <= h->stage_cap) return VDBEDT_OK;
   int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
-  int4* p = nullptr;
-  cudaError_t e = cudaMalloc((void**)&p, sizeof(int4) * (size_t)cap);
+  rec_t* p = nullptr;
+  cudaError_t e = cudaMalloc((void**)&p, sizeof(rec_t) * (size_t)cap);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage alloc");
   if (h->stage_n > 0) {
-    e = cudaMemcpyAsync(p, h->stage, sizeof(int4) * (size_t)h->stage_n, cudaMemcpyDeviceToDevice, h->st);
+    e = cudaMemcpyAsync(p, h->stage, sizeof(rec_t) * (size_t)h->stage_n, cudaMemcpyDeviceToDevice, h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "stage copy");
   }
   if (h->stage) {
@@ -208,7 +208,7 @@ vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out) {
     return fail(nullptr, VDBEDT_EINVAL, "no such CUDA device");
   }
   const int64_t BX = ceil_div(cfg->nx, 8), BY = ceil_div(cfg->ny, 8), BZ = ceil_div(cfg->nz, 8);
-  if (BX >= (1 << 21) || BY >= (1 << 21) || BZ >= (1 << 21) || BX * BY * BZ >= (int64_t)0xFFFFFFFFll)
+  if (cfg->nx >= kBadCoord || cfg->ny >= kBadCoord || cfg->nz >= kBadCoord || BX * BY * BZ >= (int64_t)0xFFFFFFFFll)
     return fail(nullptr, VDBEDT_EINVAL, "grid too large");
   const int64_t NX = ceil_div(BX, 16), NY = ceil_div(BY, 16), NZ = ceil_div(BZ, 16);
   int64_t cap = cfg->max_bricks > 0 ? std::min<int64_t>(cfg->max_bricks, BX * BY * BZ) : BX * BY * BZ;
@@ -319,7 +319,7 @@ vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const ui
   DeviceGuard guard(h->device);
   s = ensure_stage(h, h->stage_n + n);
   if (s) return s;
-  int4* dst = h->stage + h->stage_n;
+  rec_t* dst = h->stage + h->stage_n;
   if (on_device) {
     CK(h, launch_pack_records(xyz, occ, n, h->g.nx, h->g.ny, h->g.nz, dst, nullptr, h->st), "pack");
   } else {
@@ -529,7 +529,7 @@ vdbedt_status vdbedt_get_info(vdbedt_handle h, vdbedt_info* info) {
   info->finite_bricks = fin;
   info->capacity_bricks = h->g.cap;
   info->nodes = h->h_pinned[C_NNODES];
-  info->device_bytes = (int64_t)(h->device_bytes + h->scr.bytes + h->io.bytes + sizeof(int4) * h->stage_cap);
+  info->device_bytes = (int64_t)(h->device_bytes + h->scr.bytes + h->io.bytes + sizeof(rec_t) * h->stage_cap);
   info->R = h->g.R;
   info->error_bits = h->h_pinned[C_ERR];
   return VDBEDT_OK;
@@ -585,21 +585,22 @@ vdbedt_status vdbedt_global_batched(vdbedt_handle* hs, int32_t k) {
 namespace vdbedt {
 namespace {
 __global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* __restrict__ occ, int64_t n, int nx,
-                               int ny, int nz, int4* __restrict__ dst, int32_t* invalid) {
+                               int ny, int nz, rec_t* __restrict__ dst, int32_t* invalid) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
     int v = occ[i];
     bool ok = (unsigned)x < (unsigned)nx && (unsigned)y < (unsigned)ny && (unsigned)z < (unsigned)nz && v <= 1;
     if (!ok) {
       if (invalid) atomicAdd(invalid, 1);
-      v = 2;  // skipped (and reported) by the ingest kernels
+      dst[i] = pack_rec(kBadCoord, 0, 0, 0);  // skipped (and reported) by the ingest kernels
+    } else {
+      dst[i] = pack_rec(x, y, z, v);
     }
-    dst[i] = make_int4(x, y, z, v);
   }
 }
 }  // namespace
 
-cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, int nx, int ny, int nz, int4* dst,
+cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, int nx, int ny, int nz, rec_t* dst,
                                 int32_t* invalid, cudaStream_t st) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;

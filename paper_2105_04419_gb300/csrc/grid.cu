@@ -145,13 +145,13 @@ __device__ int block_agg_add(int* ctr, bool pred, int* block_total) {
   for (int64_t i##_base = (int64_t)blockIdx.x * blockDim.x, i = i##_base + threadIdx.x; i##_base < (n); \
        i##_base += (int64_t)gridDim.x * blockDim.x, i = i##_base + threadIdx.x)
 
-__global__ void k_rec_brick_keys(GridView g, const int4* __restrict__ rec, int64_t n, uint32_t* __restrict__ keys) {
+__global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int64_t n, uint32_t* __restrict__ keys) {
   const int lane = threadIdx.x & 31;
   GRID_STRIDE(i, n) {
     uint32_t key = 0xFFFFFFFFu;
     bool zero = false, bad = false;
     if (i < n) {
-      int4 r = rec[i];
+      int4 r = unpack_rec(rec[i]);
       if (!rec_valid(g, r)) {
         bad = true;
       } else if (r.w == 1) {
@@ -171,20 +171,40 @@ __global__ void k_rec_brick_keys(GridView g, const int4* __restrict__ rec, int64
 
 // Many records: bucket the brick keys of "set" records through one flag per brick of the grid
 // (a counting sort on the brick key); the compaction of the flags is the sorted unique key list.
-__global__ void k_mark_record_bricks(GridView g, const int4* __restrict__ rec, int64_t n, int32_t* __restrict__ flag) {
+// With `dbits` (global form), the records' bits are also OR-ed into a dense mask of every brick of
+// the grid (64 B per brick; lanes of one x-row merged by a segmented OR), so that allocation can copy
+// each new brick's mask whole instead of a second pass over the records.
+__global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, int64_t n, int32_t* __restrict__ flag,
+                                     unsigned long long* __restrict__ dbits) {
   const int lane = threadIdx.x & 31;
   GRID_STRIDE(i, n) {
     bool zero = false, bad = false;
+    unsigned long long* word = nullptr;
+    unsigned long long bits = 0ull;
     if (i < n) {
-      int4 r = rec[i];
+      int4 r = unpack_rec(rec[i]);
       if (!rec_valid(g, r)) {
         bad = true;
       } else if (r.w == 1) {
         int64_t lb = (r.x >> 3) + (int64_t)g.BX * ((r.y >> 3) + (int64_t)g.BY * (r.z >> 3));
         if (!flag[lb]) flag[lb] = 1;
+        if (dbits) {
+          word = dbits + lb * 8 + (r.z & 7);
+          bits = 1ull << ((r.x & 7) + 8 * (r.y & 7));
+        }
       } else {
         zero = true;
       }
+    }
+    if (dbits) {
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long wp = __shfl_up_sync(0xffffffffu, (unsigned long long)word, o);
+        const unsigned long long bp = __shfl_up_sync(0xffffffffu, bits, o);
+        if (lane >= o && wp == (unsigned long long)word) bits |= bp;
+      }
+      const unsigned long long wn = __shfl_down_sync(0xffffffffu, (unsigned long long)word, 1);
+      if (word && (lane == 31 || wn != (unsigned long long)word)) atomicOr(word, bits);
     }
     if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
     if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
@@ -215,14 +235,16 @@ __global__ void k_compact_keys(const uint32_t* __restrict__ keys, const int32_t*
 }
 
 // Bricks of the unique keys: node found or inserted, slot reserved with one atomic per block.
-__global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__ uniq, int64_t n, bool init) {
+__global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__ uniq, int64_t n, bool init,
+                                        const unsigned long long* __restrict__ dbits) {
   const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], n);
   GRID_STRIDE(j, cnt) {
     int bx = 0, by = 0, bz = 0, node = -1;
     int* e = nullptr;
     bool need = false;
+    uint32_t lb = 0;
     if (j < cnt) {
-      uint32_t lb = uniq[j];
+      lb = uniq[j];
       bx = (int)(lb % (uint32_t)g.BX);
       int rest = (int)(lb / (uint32_t)g.BX);
       by = rest % g.BY;
@@ -243,6 +265,18 @@ __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__
         *e = slot;
       }
     }
+    if (dbits && j < cnt && e) {
+      const int sl = need ? slot : *e;
+      if (sl >= 0 && sl < g.cap) {
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(dbits + (size_t)lb * 8);
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(g.occ + (size_t)sl * 8);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ulonglong2 a = src[q], b = dst[q];
+          dst[q] = make_ulonglong2(a.x | b.x, a.y | b.y);
+        }
+      }
+    }
     if (threadIdx.x == 0 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
   }
 }
@@ -250,14 +284,14 @@ __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__
 // All records set voxels: OR the bits in.  Adjacent lanes that hit the same 64-bit word (records
 // of one x-row usually sit next to each other) are merged by a segmented OR over the warp, and the
 // last lane of each segment issues the atomic.
-__global__ void k_apply_set_only(GridView g, const int4* __restrict__ rec, int64_t n) {
+__global__ void k_apply_set_only(GridView g, const rec_t* __restrict__ rec, int64_t n) {
   if (g.counters[C_HAS_ZERO]) return;
   const int lane = threadIdx.x & 31;
   GRID_STRIDE(i, n) {
     unsigned long long word = 0ull;  // address of the target word, 0 for none
     unsigned long long bits = 0ull;
     if (i < n) {
-      int4 r = rec[i];
+      int4 r = unpack_rec(rec[i]);
       if (rec_valid(g, r) && r.w == 1) {
         int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
         if (s >= 0) {
@@ -278,7 +312,7 @@ __global__ void k_apply_set_only(GridView g, const int4* __restrict__ rec, int64
 }
 
 // (voxel key, record index) for the ordered path: voxel key = slot * 512 + voxel in brick.
-__global__ void k_rec_voxel_keys(GridView g, const int4* __restrict__ rec, int64_t n, bool force,
+__global__ void k_rec_voxel_keys(GridView g, const rec_t* __restrict__ rec, int64_t n, bool force,
                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   const bool on = force || g.counters[C_HAS_ZERO];
   if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_RECORDS] = on ? (int32_t)n : 0;
@@ -286,7 +320,7 @@ __global__ void k_rec_voxel_keys(GridView g, const int4* __restrict__ rec, int64
   GRID_STRIDE(i, n) {
     if (i < n) {
       uint32_t key = 0xFFFFFFFFu;
-      int4 r = rec[i];
+      int4 r = unpack_rec(rec[i]);
       if (rec_valid(g, r)) {
         int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
         if (s >= 0) key = (uint32_t)s * 512u + (uint32_t)((r.x & 7) + 8 * (r.y & 7) + 64 * (r.z & 7));
@@ -299,7 +333,7 @@ __global__ void k_rec_voxel_keys(GridView g, const int4* __restrict__ rec, int64
 
 // The last record of each voxel decides its bit.  Flips are counted; with `track` the brick is
 // appended once per epoch to the changed list.
-__global__ void k_apply_last(GridView g, const int4* __restrict__ rec, const uint32_t* __restrict__ keys,
+__global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, const uint32_t* __restrict__ keys,
                              const uint32_t* __restrict__ idx, int64_t n, bool force, bool track, int epoch,
                              int32_t* __restrict__ changed) {
   if (!force && !g.counters[C_HAS_ZERO]) return;
@@ -309,7 +343,7 @@ __global__ void k_apply_last(GridView g, const int4* __restrict__ rec, const uin
       uint32_t k = keys[j];
       const uint32_t lim = (uint32_t)g.cap * 512u;
       if (k < lim && (j + 1 == n || keys[j + 1] != k)) {
-        int4 r = rec[idx[j]];
+        int4 r = unpack_rec(rec[idx[j]]);
         int s = (int)(k >> 9), v = (int)(k & 511);
         unsigned long long bit = 1ull << (v & 63);
         unsigned long long* word = &g.occ[(size_t)s * 8 + (v >> 6)];
@@ -761,13 +795,23 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 // record sets a voxel, OR them in directly; otherwise (some record clears a voxel, or tracking
 // is on) sort (voxel key, record index) stably and let each voxel's last record decide.  With
 // tracking, each flipped voxel's brick is appended once to `changed`.
-cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n, bool track, int epoch,
+// Apply staged records.  Bricks of "set" records are found or created through a stable radix
+// sort of brick keys, a unique pass and a compaction (few records), or a counting sort through one
+// flag per brick of the grid (many records).  Bits: in the global form the records' bits go to the
+// bricks directly (few records: OR-ed per record; many records: OR-ed into a dense scratch mask in
+// the counting pass and copied whole at allocation); whenever a record clears a voxel, or flips are
+// tracked, a stable sort of (voxel key, record index) lets each voxel's last record decide.  With
+// tracking, each flipped voxel's brick is appended once to `changed`.
+cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, bool track, int epoch,
                                   int32_t* changed, Scratch& scr, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
+  const bool counting = n >= nbr_all / 4;
+  const bool dense_bits = counting && !track;
   const int64_t m = n > nbr_all ? n : nbr_all;
   const size_t nb4 = align_up((size_t)m * 4);
-  const size_t need = 6 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(m));
+  const size_t dbytes = dense_bits ? align_up((size_t)nbr_all * 64) : 0;
+  const size_t need = 6 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(m)) + dbytes;
   cudaError_t e = ensure_scratch(scr, need);
   if (e != cudaSuccess) return e;
   char* p = (char*)scr.buf;
@@ -786,18 +830,24 @@ cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n,
   void* rtemp = p;
   p += align_up(radix_temp_bytes(n));
   void* stemp = p;
+  p += align_up(scan_temp_bytes(m));
+  unsigned long long* dbits = dense_bits ? (unsigned long long*)p : nullptr;
 
   const unsigned nbk = blocks_for(n);
-  const uint64_t nbr = (uint64_t)g.BX * g.BY * g.BZ;
-  if ((uint64_t)n >= nbr / 4) {
+  const uint64_t nbr = (uint64_t)nbr_all;
+  if (counting) {
     // counting sort of brick keys over the grid's bricks, then compaction
     e = cudaMemsetAsync(flag, 0, sizeof(int32_t) * nbr, st);
     if (e != cudaSuccess) return e;
-    VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, flag);
+    if (dbits) {
+      e = cudaMemsetAsync(dbits, 0, (size_t)nbr * 64, st);
+      if (e != cudaSuccess) return e;
+    }
+    VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, flag, dbits);
     e = exclusive_scan_i32(flag, pos, (int64_t)nbr, g.counters + C_UNIQUE, stemp, st);
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, flag, pos, (int64_t)nbr, ka);
-    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for((int64_t)nbr), kT, 0, st, g, ka, (int64_t)nbr, track);
+    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for((int64_t)nbr), kT, 0, st, g, ka, (int64_t)nbr, track, dbits);
   } else {
     // LSD radix sort of the brick keys, unique, compaction
     VDB_LAUNCH(k_rec_brick_keys, nbk, kT, 0, st, g, rec, n, ka);
@@ -811,9 +861,9 @@ cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n,
     e = exclusive_scan_i32(flag, pos, n, g.counters + C_UNIQUE, stemp, st);
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_compact_keys, nbk, kT, 0, st, sorted, flag, pos, n, uniq);
-    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, uniq, n, track);
+    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, uniq, n, track, nullptr);
+    if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n);
   }
-  if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n);
   // ordered path; its element count is 0 on the device when it is not needed
   VDB_LAUNCH(k_rec_voxel_keys, nbk, kT, 0, st, g, rec, n, track, ka, va);
   bool in_b = false;

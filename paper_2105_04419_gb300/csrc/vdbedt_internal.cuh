@@ -228,11 +228,16 @@ cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a,
                            const int32_t* count_dev, int bits, void* temp, cudaStream_t st, bool* result_in_b);
 
 // grid build (grid.cu)
-struct Staging {
-  int4* rec;        // staged records (x, y, z, value)
-  int64_t n;        // staged count
-  int64_t cap;
-};
+// A staged occupancy record in 64 bits: x | y << 21 | z << 42 | value << 63.  A record that failed
+// validation carries x = kBadCoord (never inside a grid) and is skipped (and reported).
+typedef unsigned long long rec_t;
+constexpr int kBadCoord = 0x1FFFFF;
+__host__ __device__ inline rec_t pack_rec(int x, int y, int z, int v) {
+  return (rec_t)(uint32_t)x | ((rec_t)(uint32_t)y << 21) | ((rec_t)(uint32_t)z << 42) | ((rec_t)(v & 1) << 63);
+}
+__host__ __device__ inline int4 unpack_rec(rec_t r) {
+  return make_int4((int)(r & 0x1FFFFF), (int)((r >> 21) & 0x1FFFFF), (int)((r >> 42) & 0x1FFFFF), (int)(r >> 63));
+}
 struct Scratch {
   void* buf = nullptr;
   size_t bytes = 0;
@@ -240,7 +245,7 @@ struct Scratch {
 cudaError_t ensure_scratch(Scratch& s, size_t bytes);
 
 cudaError_t launch_reset(const GridView& g, cudaStream_t st);
-cudaError_t launch_ingest_records(const GridView& g, const int4* rec, int64_t n, bool track, int epoch,
+cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, bool track, int epoch,
                                   int32_t* changed, Scratch& scr, cudaStream_t st);
 cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st);
 cudaError_t launch_activation_full(const GridView& g, cudaStream_t st);
