@@ -174,6 +174,24 @@ vdbedt_status vdbedt_get_phase_times(vdbedt_handle h, vdbedt_phase_times* out);
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 int64_t vdbedt_kernel_launches(void);
 
+/* Dense transform without any allocation (no paper counterpart: this is a deployment feature).
+ * For callers that cannot call cudaMalloc -- code running while the application holds a stream
+ * capture open, real-time loops that must stay out of the allocator, hosts whose device memory
+ * budget is fixed at load time.  Computes D (int32, out[nz][ny][nx]) of the dense occupancy
+ * occ[nz][ny][nx] (nonzero = obstacle), exactly as a handle's vdbedt_global would, on the current
+ * device and `stream` (cudaStream_t, NULL = legacy default stream).  occ and out are device
+ * pointers, owned by the caller.
+ * Its two intermediate fields live in a fixed device array of the library (2 x 16 bit x
+ * VDBEDT_NOALLOC_MAX_VOXELS = 8 MiB) that every GPU loading the library holds until exit.  The
+ * first call on a device looks that array's address up (cudaGetSymbolAddress) while the device is
+ * current: make that first call before any stream capture.  All calls on a device share the array:
+ * calls whose work overlaps on the GPU race.
+ * EINVAL: a null pointer, a size < 1, nx * ny * nz > VDBEDT_NOALLOC_MAX_VOXELS, or dmax outside
+ * [1, VDBEDT_DMAX_LIMIT].  ECUDA: the address lookup or a launch failed. */
+#define VDBEDT_NOALLOC_MAX_VOXELS (1 << 21)
+vdbedt_status vdbedt_edt_dense_noalloc(const uint8_t* occ, int32_t nx, int32_t ny, int32_t nz, int32_t dmax,
+                                       int32_t* out, void* stream);
+
 /* Wait for the handle's stream; report device-side errors. */
 vdbedt_status vdbedt_synchronize(vdbedt_handle h);
 

@@ -16,6 +16,7 @@ from .lib import (  # noqa: F401
     Map,
     VdbedtError,
     clearance_cost,
+    edt_dense_noalloc,
     global_batched,
     kernel_launches,
     library_path,

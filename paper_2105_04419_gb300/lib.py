@@ -74,6 +74,7 @@ SIGNATURES = {
     "vdbedt_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
     "vdbedt_get_phase_times": (ctypes.c_int, [_H, ctypes.POINTER(PhaseTimes)]),
     "vdbedt_kernel_launches": (ctypes.c_int64, []),
+    "vdbedt_edt_dense_noalloc": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _P, ctypes.c_void_p]),
     "vdbedt_last_error": (ctypes.c_char_p, [_H]),
 }
 
@@ -279,6 +280,24 @@ class Map:
                "vdbedt_clearance_backward", self._h)
         self._leave()
         return g
+
+
+NOALLOC_MAX_VOXELS = 1 << 21
+
+
+def edt_dense_noalloc(occ, dmax: int, out=None):
+    """D of a small dense grid occ [nz, ny, nx] (CUDA tensor) through vdbedt_edt_dense_noalloc, which
+    allocates nothing on the device (its scratch is a fixed array of the library); returns int32
+    [nz, ny, nx] on the current torch stream.  `out` (int32 CUDA tensor) may be given preallocated."""
+    torch = _torch()
+    o = occ.to(torch.uint8).contiguous()
+    nz, ny, nx = o.shape
+    if out is None:
+        out = torch.empty((nz, ny, nx), dtype=torch.int32, device=o.device)
+    st = torch.cuda.current_stream(o.device).cuda_stream
+    _check(load().vdbedt_edt_dense_noalloc(o.data_ptr(), nx, ny, nz, int(dmax), out.data_ptr(), st),
+           "vdbedt_edt_dense_noalloc")
+    return out
 
 
 def kernel_launches() -> int:
