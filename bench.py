@@ -10,7 +10,10 @@ Mvoxels/s, summed over ranks.
 
 Rows reported beside the headline: roofline of the dominant kernel and of the whole step, the CPU
 oracle on the host cores (bounded sample), the end-to-end number through the C ABI with host
-buffers, clocks sampled during the timed region, and the library's kernel-launch count.
+buffers, clocks sampled during the timed region, and the library's kernel-launch count; then the
+clearance cost (queries/s, forward and forward + backward, 8192 x 128 points in free space) on
+the same field, and the incremental update along 300 lidar frames (ms/frame of the CUDA-graph
+replay and of the eager calls, against the global transform of the final occupancy).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload tunnel|bernoulli64]
 """
@@ -53,6 +56,9 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tunnel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-incremental", action="store_true")
+    ap.add_argument("--no-clearance", action="store_true")
+    ap.add_argument("--frames", type=int, default=300, help="lidar frames of the incremental measurement")
     ap.add_argument("--variant", type=int, default=0, help="pass variant (0 automatic; see vdbedt_set_tuning)")
     ap.add_argument("--x-run", type=int, default=0)
     ap.add_argument("--y-run", type=int, default=0)
@@ -143,6 +149,145 @@ def traffic_for(kernel: str):
     except Exception:
         pass
     return None
+
+
+def dist_summary(v):
+    v = sorted(v)
+    if not v:
+        return None
+    return {"median": statistics.median(v), "p95": v[min(len(v) - 1, int(round(0.95 * (len(v) - 1))))],
+            "max": v[-1], "min": v[0], "mean": statistics.mean(v)}
+
+
+def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
+    """Per-frame incremental update along the lidar sequence (map starts empty): eager calls and
+    the CUDA-graph replay, each frame event-timed on the map's stream with L2 flushed before it,
+    against the global transform of the final occupancy."""
+    import workloads as W
+    nx, ny, nz = wl["dims"]
+    dmax = wl["dmax"]
+    _, lines = W.tunnel_lines(wl["seed"], (nx, ny, nz), ntunnels=wl.get("ntunnels", 40))
+    seq = W.LidarSequence(truth, wl["seed"], lines[0], nframes=nframes)
+    frames = [seq.next() for _ in range(nframes)]
+    final_occ = seq.map
+    counts = [len(v) for _, v in frames]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    xyz_d = torch.from_numpy(np.concatenate([x for x, _ in frames])).cuda()
+    val_d = torch.from_numpy(np.concatenate([v for _, v in frames])).cuda()
+    sl = [(xyz_d[offs[k]:offs[k + 1]], val_d[offs[k]:offs[k + 1]]) for k in range(nframes)]
+
+    # untimed pass with statistics (records, net flips, dirty runs per frame)
+    ms = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    ms.global_()
+    stats = []
+    for x, v in sl:
+        ms.set_occupancy(x, v)
+        stats.append(ms.update(stats=True))
+    info_final = ms.info()
+    ms.close()
+
+    def timed(run_frame):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nframes)]
+        for k in range(nframes):
+            flush.fill_(k & 255)
+            ev[k][0].record(stream)
+            run_frame(k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    me = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    me.global_()
+    launches0 = V.kernel_launches()
+
+    def eager(k):
+        me.set_occupancy(*sl[k])
+        me.update()
+
+    eager_ms = timed(eager)
+    eager_launches = (V.kernel_launches() - launches0) / nframes
+    D_eager = me.export_dense(on_device=True)
+    me.close()
+
+    mg = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    mg.global_()
+    graph = V.UpdateGraph(mg, max(counts))
+    graph_ms = timed(lambda k: graph.run(*sl[k]))
+    D_graph = mg.export_dense(on_device=True)
+    same = bool(torch.equal(D_eager, D_graph))
+    del D_eager, D_graph
+    mg.close()
+
+    # global transform of the final occupancy (same step as the headline: reset + records + global)
+    fx = torch.from_numpy(W.occupied_coords(final_occ)).cuda()
+    fo = torch.ones(fx.shape[0], dtype=torch.uint8, device="cuda")
+    mf = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    gms = []
+    for k in range(8):
+        flush.fill_(k & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mf.reset()
+        mf.set_occupancy(fx, fo)
+        mf.global_()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            gms.append(a.elapsed_time(b))
+    mf.close()
+    glob = statistics.median(gms)
+    g = dist_summary(graph_ms)
+    return {"frames": nframes, "workload": "lidar sequence along tunnel 0 of the scene, 64 beams x 1024 azimuths, "
+                                           "range 400 voxels, 1 % noise; map starts empty",
+            "records_per_frame": dist_summary([s["records"] for s in stats]),
+            "net_flips_per_frame": dist_summary([s["net_flips"] for s in stats]),
+            "changed_bricks_per_frame": dist_summary([s["changed_bricks"] for s in stats]),
+            "z_runs_per_frame": dist_summary([s["z_items"] for s in stats]),
+            "graph_ms_per_frame": g, "eager_ms_per_frame": dist_summary(eager_ms),
+            "eager_launches_per_frame": eager_launches,
+            "global_ms_final_occupancy": glob, "global_over_graph_median": glob / g["median"],
+            "final_map": {"occupied_voxels": int(final_occ.sum()), "allocated_bricks": info_final["allocated_bricks"]},
+            "graph_equals_eager": same, "l2": "flushed before every frame (untimed)"}
+
+
+def bench_clearance(V, torch, m, occ, stream, reps=20):
+    """Clearance cost of 8192 trajectories x 128 points in free space on the field of the headline
+    workload: raw forward, raw forward + backward and the autograd path, event-timed."""
+    import workloads as W
+    T, P, tau = 8192, 128, 1.0
+    pts = torch.from_numpy(W.free_points(11, occ, 0.1, T * P).reshape(T, P, 3)).cuda()
+    ones = torch.ones(T, dtype=torch.float32, device="cuda")
+
+    def time_it(fn):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    fwd = time_it(lambda: m.clearance_forward(pts, tau))
+    fb = time_it(lambda: (m.clearance_forward(pts, tau), m.clearance_backward(pts, tau, ones)))
+
+    def autograd():
+        p = pts.detach().requires_grad_(True)
+        V.clearance_cost(m, p, tau).sum().backward()
+        return p.grad
+
+    ag = time_it(autograd)
+    gr = m.clearance_backward(pts, tau, ones)
+    active = float((gr.abs().sum(-1) > 0).float().mean().item())
+    q = T * P
+    return {"trajectories": T, "points_per_trajectory": P, "tau_m": tau, "voxel_m": 0.1,
+            "fwd_ms": fwd, "fwd_queries_per_s": q / (fwd / 1e3),
+            "fwd_bwd_ms": fb, "fwd_bwd_queries_per_s": q / (fb / 1e3),
+            "autograd_fwd_bwd_ms": ag, "autograd_overhead_ms": ag - fb,
+            "hinge_active_fraction": active,
+            "hinge_active_rule": "points with a nonzero gradient (d < tau and a nonzero distance gradient)"}
 
 
 def cpu_baseline(occ, dmax, budget_s=12.0):
@@ -352,6 +497,10 @@ def main():
                        "ms_per_step": ems, "host_buffers": "pinned", "h2d_bytes_per_step": int(n * 13),
                        "d2h_bytes_per_step": int(4 * 16 + 4 * inf2["allocated_bricks"])}
 
+    if wl["kind"] == "tunnel" and not args.no_clearance:
+        line["clearance"] = bench_clearance(V, torch, m, occ, stream)
+    if wl["kind"] == "tunnel" and not args.no_incremental:
+        line["incremental"] = bench_incremental(V, torch, wl, occ, stream, flush, args.frames)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(occ, dmax)
     if rank == 0:

@@ -105,6 +105,19 @@ vdbedt_status vdbedt_destroy(vdbedt_handle h);
 vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const uint8_t* occ, int64_t n,
                                    int on_device);
 
+/* Stage up to n_max occupancy records in device memory whose actual count is the int32 at n_dev
+ * (device memory), read when the stream reaches the call -- the same edits as vdbedt_set_occupancy
+ * with on_device = 1, in a form whose launches do not depend on the count, so that a staging call
+ * followed by vdbedt_update can be captured once into a CUDA graph and replayed for frames of
+ * different sizes (write the frame into xyz / occ and its count into *n_dev before each replay).
+ * The stage must be empty (EINVAL otherwise), and no other records may be staged until the next
+ * transform applies these.  The call reserves the stage and the ingest scratch for n_max records,
+ * so a capture taken after one uncaptured call with the same n_max allocates nothing.  A count
+ * below 0 or above n_max is clamped to [0, n_max] and reported as EINVAL by the next synchronising
+ * call, as are invalid records (which are skipped).  n_max must lie in [1, 2^31). */
+vdbedt_status vdbedt_set_occupancy_counted(vdbedt_handle h, const int32_t* xyz, const uint8_t* occ,
+                                           const int32_t* n_dev, int64_t n_max);
+
 /* Stage a whole occupancy grid grid[nz][ny][nx] (nonzero = obstacle), replacing the current one
  * (records staged earlier are discarded).  on_device selects host or device memory. */
 vdbedt_status vdbedt_set_occupancy_dense(vdbedt_handle h, const uint8_t* grid, int on_device);

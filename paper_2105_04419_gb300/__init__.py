@@ -6,14 +6,16 @@ and streams.  The library must be built (``paper_2105_04419_gb300.build.build()`
 importing :mod:`paper_2105_04419_gb300.lib` raises.
 
 Entry points mirror the C names: :class:`Map` wraps a handle (create, set_occupancy,
-set_occupancy_dense, reset, global_, update, query, export_dense, clearance_forward /
-clearance_backward, set_tuning, synchronize, info); :func:`global_batched` runs several maps in
-one launch; :func:`clearance_cost` is the differentiable clearance cost (torch.autograd.Function
+set_occupancy_counted, set_occupancy_dense, reset, global_, update, query, export_dense, clearance_forward /
+clearance_backward, set_tuning, synchronize, info); :class:`UpdateGraph` captures one
+incremental update into a CUDA graph and replays it per frame; :func:`global_batched` runs
+several maps in one launch; :func:`clearance_cost` is the differentiable clearance cost (torch.autograd.Function
 over the library's forward and backward kernels).
 """
 from .lib import (  # noqa: F401
     VDBEDT_DMAX_LIMIT,
     Map,
+    UpdateGraph,
     VdbedtError,
     clearance_cost,
     edt_dense_noalloc,

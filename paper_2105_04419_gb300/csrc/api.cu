@@ -17,8 +17,9 @@ using namespace vdbedt;
 namespace vdbedt {
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, int nx, int ny, int nz, rec_t* dst,
-                                int32_t* invalid, cudaStream_t st);
+cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, const int32_t* n_dev,
+                                int32_t* count_out, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
+                                int32_t* counters, cudaStream_t st);
 }
 
 struct vdbedt_map {
@@ -32,6 +33,8 @@ struct vdbedt_map {
   // staged records
   rec_t* stage = nullptr;
   int64_t stage_n = 0, stage_cap = 0;
+  bool stage_counted = false;  // the stage holds up to stage_n records, *d_count of them valid
+  int32_t* d_count = nullptr;
   bool dense_pending = false;
   bool computed = false;
   int32_t* d_invalid = nullptr;
@@ -40,7 +43,6 @@ struct vdbedt_map {
   Scratch io;  // host-input staging on the device
   Items items{};
   int32_t* changed = nullptr;
-  int epoch = 0;
   Tuning tune;
   int sticky = VDBEDT_OK;
   std::string err;
@@ -150,8 +152,14 @@ vdbedt_status ensure_stage(vdbedt_map* h, int64_t need) {
   return VDBEDT_OK;
 }
 
+bool capturing(const vdbedt_map* h) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(h->st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// phase events are not recorded while the stream is being captured into a graph
 void mark(vdbedt_map* h, int i) {
-  if (h->profiling) cudaEventRecord(h->ev[i], h->st);
+  if (h->profiling && !capturing(h)) cudaEventRecord(h->ev[i], h->st);
 }
 
 Tuning effective_tuning(const vdbedt_map* h) {
@@ -169,24 +177,31 @@ vdbedt_status run_passes(vdbedt_map* h, const Tuning& t, bool need_slots) {
   mark(h, 5);
   CK(h, launch_pass(h->g, t, 2, h->items, h->st), "z pass");
   mark(h, 6);
-  h->ev_recorded = h->profiling;
+  h->ev_recorded = h->profiling && !capturing(h);
   return VDBEDT_OK;
 }
 
+const int32_t* stage_count(const vdbedt_map* h) { return h->stage_counted ? h->d_count : nullptr; }
+
+void clear_stage(vdbedt_map* h) {
+  h->stage_n = 0;
+  h->stage_counted = false;
+}
+
 vdbedt_status do_global(vdbedt_map* h) {
-  h->epoch++;
   const Tuning t = effective_tuning(h);
   mark(h, 0);
   CK(h, cudaMemsetAsync(h->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), h->st), "memset");
   if (h->stage_n > 0) {
-    CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, false, h->epoch, nullptr, h->scr, h->st), "ingest");
-    h->stage_n = 0;
+    CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, nullptr, h->scr, h->st),
+       "ingest");
+    clear_stage(h);
   }
   h->dense_pending = false;
   mark(h, 1);
   CK(h, launch_activation_full(h->g, h->st), "activation");
   mark(h, 2);
-  CK(h, launch_build_items_full(h->g, t, h->epoch, h->items, half_path(h->g), h->st), "items");
+  CK(h, launch_build_items_full(h->g, t, h->items, half_path(h->g), h->st), "items");
   vdbedt_status s = run_passes(h, t, false);
   if (s) return s;
   h->computed = true;
@@ -278,6 +293,7 @@ vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out) {
   }
   AL(h->changed, cap);
   AL(h->d_invalid, 4);
+  h->d_count = h->d_invalid + 1;
 #undef AL
   e = cudaMallocHost((void**)&h->h_pinned, 64 * sizeof(int32_t));
   if (e != cudaSuccess) return bail(e, "pinned alloc");
@@ -316,12 +332,14 @@ vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const ui
   if (n < 0) return fail(h, VDBEDT_EINVAL, "negative record count");
   if (n == 0) return VDBEDT_OK;
   if (!xyz || !occ) return fail(h, VDBEDT_EINVAL, "null records");
+  if (h->stage_counted) return fail(h, VDBEDT_EINVAL, "records staged with a device count must be applied first");
   DeviceGuard guard(h->device);
   s = ensure_stage(h, h->stage_n + n);
   if (s) return s;
   rec_t* dst = h->stage + h->stage_n;
   if (on_device) {
-    CK(h, launch_pack_records(xyz, occ, n, h->g.nx, h->g.ny, h->g.nz, dst, nullptr, h->st), "pack");
+    CK(h, launch_pack_records(xyz, occ, n, nullptr, nullptr, h->g.nx, h->g.ny, h->g.nz, dst, nullptr, h->g.counters,
+                              h->st), "pack");
   } else {
     // copy the raw arrays, pack and validate on the device, then check before accepting
     size_t bxyz = ((size_t)n * 12 + 255) & ~(size_t)255;
@@ -331,13 +349,34 @@ vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const ui
     CK(h, cudaMemcpyAsync(dxyz, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, h->st), "h2d");
     CK(h, cudaMemcpyAsync(docc, occ, (size_t)n, cudaMemcpyHostToDevice, h->st), "h2d");
     CK(h, cudaMemsetAsync(h->d_invalid, 0, sizeof(int32_t), h->st), "memset");
-    CK(h, launch_pack_records(dxyz, docc, n, h->g.nx, h->g.ny, h->g.nz, dst, h->d_invalid, h->st), "pack");
+    CK(h, launch_pack_records(dxyz, docc, n, nullptr, nullptr, h->g.nx, h->g.ny, h->g.nz, dst, h->d_invalid,
+                              h->g.counters, h->st),
+       "pack");
     CK(h, cudaMemcpyAsync(h->h_pinned, h->d_invalid, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st), "d2h");
     CK(h, cudaStreamSynchronize(h->st), "sync");
     if (h->h_pinned[0] != 0)
       return fail(h, VDBEDT_EINVAL, "record outside the grid or occupancy value > 1; call rejected");
   }
   h->stage_n += n;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_set_occupancy_counted(vdbedt_handle h, const int32_t* xyz, const uint8_t* occ,
+                                           const int32_t* n_dev, int64_t n_max) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (n_max < 1 || n_max > INT32_MAX || !xyz || !occ || !n_dev)
+    return fail(h, VDBEDT_EINVAL, "bad counted records (need n_max in [1, 2^31) and device pointers)");
+  if (h->stage_n > 0) return fail(h, VDBEDT_EINVAL, "counted records need an empty stage");
+  DeviceGuard guard(h->device);
+  s = ensure_stage(h, n_max);
+  if (s) return s;
+  CK(h, reserve_ingest(h->g, n_max, h->scr), "ingest scratch");
+  CK(h, launch_pack_records(xyz, occ, n_max, n_dev, h->d_count, h->g.nx, h->g.ny, h->g.nz, h->stage, nullptr,
+                              h->g.counters, h->st),
+     "pack");
+  h->stage_n = n_max;
+  h->stage_counted = true;
   return VDBEDT_OK;
 }
 
@@ -366,8 +405,7 @@ vdbedt_status vdbedt_reset(vdbedt_handle h) {
   if (s) return s;
   DeviceGuard guard(h->device);
   CK(h, launch_reset(h->g, h->st), "reset");
-  h->stage_n = 0;
-  h->epoch = 0;
+  clear_stage(h);
   h->computed = false;
   h->dense_pending = false;
   return VDBEDT_OK;
@@ -385,31 +423,33 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
   if (s) return s;
   DeviceGuard guard(h->device);
   const int64_t nrec = h->stage_n;
+  const bool counted = h->stage_counted;
   if (!h->computed || h->dense_pending) {
     s = do_global(h);
     if (s) return s;
   } else {
-    h->epoch++;
     const Tuning t = effective_tuning(h);
     mark(h, 0);
-    CK(h, cudaMemsetAsync(h->g.counters + C_Y_ITEMS, 0, sizeof(int32_t) * 6, h->st), "memset");
-    CK(h, cudaMemsetAsync(h->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), h->st), "memset");
+    CK(h, launch_begin_update(h->g, h->st), "begin update");
     if (h->stage_n > 0) {
-      CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, true, h->epoch, h->changed, h->scr, h->st), "ingest");
-      h->stage_n = 0;
+      CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->scr, h->st),
+         "ingest");
+      clear_stage(h);
     }
     mark(h, 1);
-    CK(h, launch_incremental_mark(h->g, t, h->epoch, h->changed, h->items, h->st), "mark");
+    CK(h, launch_incremental_mark(h->g, t, h->changed, h->items, h->st), "mark");
     mark(h, 2);
     s = run_passes(h, t, true);
     if (s) return s;
   }
   if (stats) {
     CK(h, cudaMemcpyAsync(h->h_pinned, h->g.counters, sizeof(int32_t) * C_NUM, cudaMemcpyDeviceToHost, h->st), "d2h");
+    if (counted)
+      CK(h, cudaMemcpyAsync(h->h_pinned + 40, h->d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st), "d2h");
     s = device_errors(h);  // synchronises
     if (s) return s;
     const int32_t* c = h->h_pinned;
-    stats->records = nrec;
+    stats->records = counted ? h->h_pinned[40] : nrec;
     stats->net_flips = c[C_FLIPS];
     stats->changed_bricks = c[C_CHANGED];
     stats->x_items = c[C_X_ITEMS];
@@ -584,8 +624,21 @@ vdbedt_status vdbedt_global_batched(vdbedt_handle* hs, int32_t k) {
 // ---- record packing ----
 namespace vdbedt {
 namespace {
-__global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* __restrict__ occ, int64_t n, int nx,
-                               int ny, int nz, rec_t* __restrict__ dst, int32_t* invalid) {
+// Validate and pack records.  With n_dev, only the first *n_dev of the n records are read; the
+// count, clamped to [0, n], is copied to count_out for the ingest kernels, and a count outside that
+// range sets the invalid-record error bit.
+__global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* __restrict__ occ, int64_t n_max,
+                               const int32_t* n_dev, int32_t* count_out, int nx, int ny, int nz,
+                               rec_t* __restrict__ dst, int32_t* invalid, int32_t* counters) {
+  int64_t n = n_max;
+  if (n_dev) {
+    const int64_t c = *n_dev;
+    n = c < 0 ? 0 : (c < n_max ? c : n_max);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      *count_out = (int32_t)n;
+      if (c < 0 || c > n_max) atomicOr(&counters[C_ERR], kErrInvalidRecord);
+    }
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
     int v = occ[i];
@@ -600,12 +653,14 @@ __global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* _
 }
 }  // namespace
 
-cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, int nx, int ny, int nz, rec_t* dst,
-                                int32_t* invalid, cudaStream_t st) {
+cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, const int32_t* n_dev,
+                                int32_t* count_out, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
+                                int32_t* counters, cudaStream_t st) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
   if (b < 1) b = 1;
-  VDB_LAUNCH(k_pack_records, (unsigned)b, 256, 0, st, xyz, occ, n, nx, ny, nz, dst, invalid);
+  VDB_LAUNCH(k_pack_records, (unsigned)b, 256, 0, st, xyz, occ, n, n_dev, count_out, nx, ny, nz, dst, invalid,
+             counters);
   return cudaGetLastError();
 }
 }  // namespace vdbedt

@@ -55,6 +55,22 @@ __global__ void k_reset_nodes(GridView g) {
     g.hslots[i] = ~0ull;
 }
 
+// Start of an incremental update: clear the per-update counters and advance the update epoch
+// (kept on the device, so that a captured update replays with a fresh epoch each time).
+__global__ void k_begin_update(GridView g) {
+  if (threadIdx.x == 0) {
+    g.counters[C_Y_ITEMS] = 0;
+    g.counters[C_Z_ITEMS] = 0;
+    g.counters[C_X_ITEMS] = 0;
+    g.counters[C_CHANGED] = 0;
+    g.counters[C_FLIPS] = 0;
+    g.counters[C_NEW_BRICKS] = 0;
+    g.counters[C_UNIQUE] = 0;
+    g.counters[C_HAS_ZERO] = 0;
+    g.counters[C_EPOCH] += 1;
+  }
+}
+
 // ---- brick allocation ----
 // Fill a freshly allocated brick: empty occupancy, coordinates, flags; with `init_fields` also
 // g2 and D at dmax^2 (bricks added by an incremental update may be read before a pass writes them).
@@ -139,18 +155,28 @@ __device__ int block_agg_add(int* ctr, bool pred, int* block_total) {
   return r;
 }
 
+// Number of staged records to apply: n, or the count in device memory (clamped to n) when the
+// records were staged with a device-side count.
+__device__ __forceinline__ int64_t rec_count(int64_t n, const int32_t* n_dev) {
+  if (!n_dev) return n;
+  const int64_t c = *n_dev;
+  return c < 0 ? 0 : (c < n ? c : n);
+}
+
 // Grid-stride loops below keep every warp iterating together (the index base is block-uniform),
 // so warp-wide votes and shuffles inside the loop see all 32 lanes.
 #define GRID_STRIDE(i, n)                                                                              \
   for (int64_t i##_base = (int64_t)blockIdx.x * blockDim.x, i = i##_base + threadIdx.x; i##_base < (n); \
        i##_base += (int64_t)gridDim.x * blockDim.x, i = i##_base + threadIdx.x)
 
-__global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int64_t n, uint32_t* __restrict__ keys) {
+__global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int64_t n, const int32_t* n_dev,
+                                 uint32_t* __restrict__ keys) {
   const int lane = threadIdx.x & 31;
+  const int64_t ne = rec_count(n, n_dev);  // keys past the count are the sentinel
   GRID_STRIDE(i, n) {
     uint32_t key = 0xFFFFFFFFu;
     bool zero = false, bad = false;
-    if (i < n) {
+    if (i < ne) {
       int4 r = unpack_rec(rec[i]);
       if (!rec_valid(g, r)) {
         bad = true;
@@ -174,9 +200,10 @@ __global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int6
 // With `dbits` (global form), the records' bits are also OR-ed into a dense mask of every brick of
 // the grid (64 B per brick; lanes of one x-row merged by a segmented OR), so that allocation can copy
 // each new brick's mask whole instead of a second pass over the records.
-__global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, int64_t n, int32_t* __restrict__ flag,
-                                     unsigned long long* __restrict__ dbits) {
+__global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
+                                     int32_t* __restrict__ flag, unsigned long long* __restrict__ dbits) {
   const int lane = threadIdx.x & 31;
+  const int64_t n = rec_count(n_max, n_dev);
   GRID_STRIDE(i, n) {
     bool zero = false, bad = false;
     unsigned long long* word = nullptr;
@@ -284,9 +311,10 @@ __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__
 // All records set voxels: OR the bits in.  Adjacent lanes that hit the same 64-bit word (records
 // of one x-row usually sit next to each other) are merged by a segmented OR over the warp, and the
 // last lane of each segment issues the atomic.
-__global__ void k_apply_set_only(GridView g, const rec_t* __restrict__ rec, int64_t n) {
+__global__ void k_apply_set_only(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev) {
   if (g.counters[C_HAS_ZERO]) return;
   const int lane = threadIdx.x & 31;
+  const int64_t n = rec_count(n_max, n_dev);
   GRID_STRIDE(i, n) {
     unsigned long long word = 0ull;  // address of the target word, 0 for none
     unsigned long long bits = 0ull;
@@ -312,9 +340,10 @@ __global__ void k_apply_set_only(GridView g, const rec_t* __restrict__ rec, int6
 }
 
 // (voxel key, record index) for the ordered path: voxel key = slot * 512 + voxel in brick.
-__global__ void k_rec_voxel_keys(GridView g, const rec_t* __restrict__ rec, int64_t n, bool force,
-                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+__global__ void k_rec_voxel_keys(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
+                                 bool force, uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   const bool on = force || g.counters[C_HAS_ZERO];
+  const int64_t n = rec_count(n_max, n_dev);
   if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_RECORDS] = on ? (int32_t)n : 0;
   if (!on) return;
   GRID_STRIDE(i, n) {
@@ -334,9 +363,11 @@ __global__ void k_rec_voxel_keys(GridView g, const rec_t* __restrict__ rec, int6
 // The last record of each voxel decides its bit.  Flips are counted; with `track` the brick is
 // appended once per epoch to the changed list.
 __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, const uint32_t* __restrict__ keys,
-                             const uint32_t* __restrict__ idx, int64_t n, bool force, bool track, int epoch,
+                             const uint32_t* __restrict__ idx, int64_t n_max, bool force, bool track,
                              int32_t* __restrict__ changed) {
   if (!force && !g.counters[C_HAS_ZERO]) return;
+  const int64_t n = min(n_max, (int64_t)g.counters[C_RECORDS]);  // set by k_rec_voxel_keys
+  const int epoch = g.counters[C_EPOCH];
   GRID_STRIDE(j, n) {
     bool flip = false;
     if (j < n) {
@@ -744,9 +775,9 @@ __global__ void k_changed_flags_dilate(GridView g, const int32_t* __restrict__ c
 
 // Dirty sets of an update: every stored brick within R (Chebyshev) of a changed brick needs its z
 // pass; those in the changed brick's z layer also need the in-plane pass.
-__global__ void k_mark_dirty(GridView g, const int32_t* __restrict__ changed, int rx, int ry, int rz, int epoch,
-                             Items it) {
+__global__ void k_mark_dirty(GridView g, const int32_t* __restrict__ changed, int rx, int ry, int rz, Items it) {
   const int nc = min(g.counters[C_CHANGED], g.cap);
+  const int epoch = g.counters[C_EPOCH];
   const int side = 2 * g.R + 1, vol = side * side * side;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nc * vol;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -802,7 +833,28 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 // the counting pass and copied whole at allocation); whenever a record clears a voxel, or flips are
 // tracked, a stable sort of (voxel key, record index) lets each voxel's last record decide.  With
 // tracking, each flipped voxel's brick is appended once to `changed`.
-cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, bool track, int epoch,
+static size_t ingest_scratch_bytes(const GridView& g, int64_t n, bool track) {
+  const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
+  const bool counting = n >= nbr_all / 4;
+  const bool dense_bits = counting && !track;
+  const int64_t m = n > nbr_all ? n : nbr_all;
+  const size_t nb4 = align_up((size_t)m * 4);
+  const size_t dbytes = dense_bits ? align_up((size_t)nbr_all * 64) : 0;
+  return 6 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(m)) + dbytes;
+}
+
+cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr) {
+  if (n <= 0) return cudaSuccess;
+  const size_t a = ingest_scratch_bytes(g, n, false), b = ingest_scratch_bytes(g, n, true);
+  return ensure_scratch(scr, a > b ? a : b);
+}
+
+cudaError_t launch_begin_update(const GridView& g, cudaStream_t st) {
+  VDB_LAUNCH(k_begin_update, 1, 32, 0, st, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
                                   int32_t* changed, Scratch& scr, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
@@ -810,9 +862,7 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
   const bool dense_bits = counting && !track;
   const int64_t m = n > nbr_all ? n : nbr_all;
   const size_t nb4 = align_up((size_t)m * 4);
-  const size_t dbytes = dense_bits ? align_up((size_t)nbr_all * 64) : 0;
-  const size_t need = 6 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(m)) + dbytes;
-  cudaError_t e = ensure_scratch(scr, need);
+  cudaError_t e = ensure_scratch(scr, ingest_scratch_bytes(g, n, track));
   if (e != cudaSuccess) return e;
   char* p = (char*)scr.buf;
   uint32_t* ka = (uint32_t*)p;
@@ -843,14 +893,14 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
       e = cudaMemsetAsync(dbits, 0, (size_t)nbr * 64, st);
       if (e != cudaSuccess) return e;
     }
-    VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, flag, dbits);
+    VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, n_dev, flag, dbits);
     e = exclusive_scan_i32(flag, pos, (int64_t)nbr, g.counters + C_UNIQUE, stemp, st);
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, flag, pos, (int64_t)nbr, ka);
     VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for((int64_t)nbr), kT, 0, st, g, ka, (int64_t)nbr, track, dbits);
   } else {
     // LSD radix sort of the brick keys, unique, compaction
-    VDB_LAUNCH(k_rec_brick_keys, nbk, kT, 0, st, g, rec, n, ka);
+    VDB_LAUNCH(k_rec_brick_keys, nbk, kT, 0, st, g, rec, n, n_dev, ka);
     // the sentinel 0xFFFFFFFF sorts after every key below 2^bits
     bool in_b = false;
     e = radix_sort_u32(ka, kb, nullptr, nullptr, n, nullptr, bits_for(nbr), rtemp, st, &in_b);
@@ -862,15 +912,15 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_compact_keys, nbk, kT, 0, st, sorted, flag, pos, n, uniq);
     VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, uniq, n, track, nullptr);
-    if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n);
+    if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
   }
   // ordered path; its element count is 0 on the device when it is not needed
-  VDB_LAUNCH(k_rec_voxel_keys, nbk, kT, 0, st, g, rec, n, track, ka, va);
+  VDB_LAUNCH(k_rec_voxel_keys, nbk, kT, 0, st, g, rec, n, n_dev, track, ka, va);
   bool in_b = false;
   e = radix_sort_u32(ka, kb, va, vb, n, g.counters + C_RECORDS, bits_for((uint64_t)g.cap * 512ull), rtemp, st,
                      &in_b);
   if (e != cudaSuccess) return e;
-  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, in_b ? kb : ka, in_b ? vb : va, n, track, track, epoch, changed);
+  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, in_b ? kb : ka, in_b ? vb : va, n, track, track, changed);
   return cudaGetLastError();
 }
 
@@ -900,9 +950,8 @@ static cudaError_t clear_item_counters(const GridView& g, cudaStream_t st) {
   return cudaMemsetAsync(g.counters + C_X_ITEMS, 0, sizeof(int32_t), st);
 }
 
-cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, const Items& it, bool with_slots,
+cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, const Items& it, bool with_slots,
                                     cudaStream_t st) {
-  (void)epoch;
   cudaError_t e = clear_item_counters(g, st);
   if (e != cudaSuccess) return e;
   VDB_LAUNCH(k_items_nodes, g.node_cap * 12 < 8192 ? g.node_cap * 12 : 8192, kT, 0, st, g, t.run[0], t.run[1],
@@ -916,13 +965,13 @@ cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& i
 }
 
 // Incremental: records were already applied with flip tracking (changed list filled).
-cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, int epoch, const int32_t* changed,
-                                    const Items& it, cudaStream_t st) {
+cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const int32_t* changed, const Items& it,
+                                    cudaStream_t st) {
   cudaError_t e = clear_item_counters(g, st);
   if (e != cudaSuccess) return e;
   VDB_LAUNCH(k_changed_flags_dilate, 1024, kT, 0, st, g, changed);
   VDB_LAUNCH(k_alloc_marked, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, g, true);
-  VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.run[0], t.run[1], t.run[2], epoch, it);
+  VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }
 

@@ -52,6 +52,7 @@ enum Counter : int {
   C_RECORDS = 12,
   C_SPIN = 13,
   C_X_ITEMS = 14,
+  C_EPOCH = 15,  // incremental update epoch (run and brick dedupe marks)
   C_NUM = 16
 };
 
@@ -144,6 +145,7 @@ __device__ inline int get_or_create_node(const GridView& g, uint32_t key) {
       k = (uint32_t)(w >> 32);
     }
     if (k == key) {
+      if ((uint32_t)w != kPending) return (int)(uint32_t)w;  // published: no atomic needed
       for (int spin = 0; spin < (1 << 22); ++spin) {
         unsigned long long cur = atomicAdd(&g.hslots[h], 0ull);
         uint32_t v = (uint32_t)cur;
@@ -245,15 +247,20 @@ struct Scratch {
 cudaError_t ensure_scratch(Scratch& s, size_t bytes);
 
 cudaError_t launch_reset(const GridView& g, cudaStream_t st);
-cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, bool track, int epoch,
+// n records at rec; with n_dev (nullable) only the first *n_dev of them (clamped to [0, n]).
+cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
                                   int32_t* changed, Scratch& scr, cudaStream_t st);
+// size the ingest scratch for up to n records, either form
+cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr);
+// clear the per-update counters and advance the device-side update epoch
+cudaError_t launch_begin_update(const GridView& g, cudaStream_t st);
 cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st);
 cudaError_t launch_activation_full(const GridView& g, cudaStream_t st);
 // every run holding a stored brick, with slot lists when with_slots (half path)
-cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, int epoch, const Items& it, bool with_slots,
+cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, const Items& it, bool with_slots,
                                     cudaStream_t st);
-cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, int epoch, const int32_t* changed,
-                                    const Items& it, cudaStream_t st);
+cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const int32_t* changed, const Items& it,
+                                    cudaStream_t st);
 // slot lists of every queued run (half path)
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st);
 

@@ -58,6 +58,7 @@ SIGNATURES = {
     "vdbedt_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
     "vdbedt_destroy": (ctypes.c_int, [_H]),
     "vdbedt_set_occupancy": (ctypes.c_int, [_H, _P, _P, _I64, ctypes.c_int]),
+    "vdbedt_set_occupancy_counted": (ctypes.c_int, [_H, _P, _P, _P, _I64]),
     "vdbedt_set_occupancy_dense": (ctypes.c_int, [_H, _P, ctypes.c_int]),
     "vdbedt_reset": (ctypes.c_int, [_H]),
     "vdbedt_global": (ctypes.c_int, [_H]),
@@ -183,6 +184,17 @@ class Map:
             _check(lib.vdbedt_set_occupancy(self._h, x.data_ptr(), o.data_ptr(), x.shape[0], 1),
                    "vdbedt_set_occupancy", self._h)
 
+    def set_occupancy_counted(self, xyz, occ, count, n_max: int):
+        """Stage up to n_max device records whose count is the int32 CUDA tensor `count` (read on
+        the stream); see UpdateGraph for the captured form."""
+        torch = _torch()
+        assert xyz.is_cuda and occ.is_cuda and count.is_cuda and count.dtype == torch.int32
+        assert xyz.dtype == torch.int32 and occ.dtype == torch.uint8 and xyz.is_contiguous() and occ.is_contiguous()
+        assert xyz.shape[0] >= n_max and occ.shape[0] >= n_max
+        self._enter(xyz, occ, count)
+        _check(load().vdbedt_set_occupancy_counted(self._h, xyz.data_ptr(), occ.data_ptr(), count.data_ptr(),
+                                                   int(n_max)), "vdbedt_set_occupancy_counted", self._h)
+
     def set_occupancy_dense(self, grid):
         lib = load()
         if isinstance(grid, np.ndarray):
@@ -280,6 +292,59 @@ class Map:
                "vdbedt_clearance_backward", self._h)
         self._leave()
         return g
+
+
+class UpdateGraph:
+    """One incremental update of a Map -- staging of up to max_records device records with a
+    device-side count, then vdbedt_update -- captured once into a CUDA graph.  run(xyz, occ)
+    writes a frame's records into the graph's fixed input buffers and replays the graph on the
+    map's stream; the result equals set_occupancy(xyz, occ) + update() bit for bit.  The map must
+    not be reset, given a dense grid or retuned while the graph is in use (the graph holds the
+    launches of the incremental form with the tuning of capture time)."""
+
+    def __init__(self, m: Map, max_records: int):
+        torch = _torch()
+        self.m = m
+        self.max_records = int(max_records)
+        dev = f"cuda:{m.device}"
+        self.xyz = torch.zeros((self.max_records, 3), dtype=torch.int32, device=dev)
+        self.occ = torch.zeros(self.max_records, dtype=torch.uint8, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int32, device=dev)
+        m._enter()
+        with torch.cuda.stream(m.stream):
+            # one uncaptured update with an empty frame: reserves the stage and the ingest scratch,
+            # and runs the global transform first if the map has none yet
+            self._body()
+            m.stream.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=m.stream):
+                self._body()
+        m.synchronize()
+
+    def _body(self):
+        lib = load()
+        h = self.m._h
+        _check(lib.vdbedt_set_occupancy_counted(h, self.xyz.data_ptr(), self.occ.data_ptr(), self.count.data_ptr(),
+                                                self.max_records), "vdbedt_set_occupancy_counted", h)
+        _check(lib.vdbedt_update(h, None), "vdbedt_update", h)
+
+    def run(self, xyz, occ):
+        """Replay for one frame; xyz [n, 3] int32 and occ [n] uint8, CUDA tensors or numpy arrays."""
+        torch = _torch()
+        n = int(occ.shape[0])
+        if n > self.max_records:
+            raise ValueError(f"{n} records exceed the captured maximum {self.max_records}")
+        if isinstance(xyz, np.ndarray):
+            xyz = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3))
+            occ = torch.from_numpy(np.ascontiguousarray(occ, dtype=np.uint8).reshape(-1))
+        self.m._enter()
+        with torch.cuda.stream(self.m.stream):
+            if n:
+                self.xyz[:n].copy_(xyz.view(-1, 3), non_blocking=True)
+                self.occ[:n].copy_(occ.view(-1), non_blocking=True)
+            self.count.fill_(n)
+            self.graph.replay()
+        self.m._leave()
 
 
 NOALLOC_MAX_VOXELS = 1 << 21
