@@ -154,11 +154,6 @@ vdbedt_status vdbedt_clearance_forward(vdbedt_handle h, const float* pts, int64_
 vdbedt_status vdbedt_clearance_backward(vdbedt_handle h, const float* pts, int64_t T, int64_t P, float tau,
                                         const float* grad_cost, float* grad_pts);
 
-/* Global transform of k maps in one persistent launch on the first handle's stream: staged
- * records of every map are applied, then the in-plane and z passes of all maps run from one
- * device work queue (larger maps first).  All handles must be on the same device and must not be
- * used concurrently elsewhere.  Bit-identical to vdbedt_global on each map. */
-vdbedt_status vdbedt_global_batched(vdbedt_handle* hs, int32_t k);
 
 /* Tuning of the transform passes (0 = automatic for any field).
  *   x_run, y_run, z_run: bricks per work item of the pass along that axis (4, 8 or 16);
@@ -183,6 +178,51 @@ typedef struct {
 } vdbedt_phase_times;
 vdbedt_status vdbedt_set_profiling(vdbedt_handle h, int on);
 vdbedt_status vdbedt_get_phase_times(vdbedt_handle h, vdbedt_phase_times* out);
+
+/* ---- Batches: many grids of uneven size transformed together (no paper counterpart: the paper
+ * transforms one map at a time; this is the batched form of its global transform, Sec. IV). ----
+ *
+ * A batch owns k grids created together.  Their bricks live in one pool, so that each step of
+ * the global transform is one launch for all k grids: the per-grid steps (reset, dense ingest,
+ * activation, work-list build) launch a block row per grid, and the three passes run as one
+ * persistent launch each over a single work queue holding every grid's brick runs.  Each grid is
+ * also an ordinary handle (vdbedt_batch_map): records, queries, export, incremental updates and
+ * single-grid transforms work on it as on any handle; it is released with the batch (vdbedt_destroy
+ * of a batch grid is EINVAL).  Operations on the grids of one batch must not overlap (they share
+ * the work lists and run on the batch's stream). */
+typedef struct vdbedt_batch* vdbedt_batch_handle;
+#define VDBEDT_BATCH_MAX 1024
+
+/* Create k grids (cfgs[i], 1 <= k <= VDBEDT_BATCH_MAX) that share dmax, voxel_size, device and
+ * stream (NULL: the batch creates and owns one); sizes and max_bricks may differ.  EINVAL on a
+ * bad or inconsistent configuration; ENOMEM when the pool does not fit. */
+vdbedt_status vdbedt_batch_create(const vdbedt_config* cfgs, int32_t k, vdbedt_batch_handle* out);
+/* Release the batch and its grids (waits for its stream).  NULL is accepted. */
+vdbedt_status vdbedt_batch_destroy(vdbedt_batch_handle b);
+/* Handle of grid i (owned by the batch). */
+vdbedt_status vdbedt_batch_map(vdbedt_batch_handle b, int32_t i, vdbedt_handle* out);
+/* Replace the occupancy of every grid: grids[i] is grid i's [nz][ny][nx] uint8 array (nonzero =
+ * obstacle), device pointers when on_device != 0 (read on the stream), else host pointers (copied
+ * before return).  grids itself is a host array of k pointers. */
+vdbedt_status vdbedt_batch_set_occupancy_dense(vdbedt_batch_handle b, const uint8_t* const* grids, int on_device);
+/* Global transform of every grid of the batch (records staged on a grid are applied first).
+ * Bit-identical to vdbedt_global on each grid.  Grids with dmax above 45 are transformed one
+ * after the other. */
+vdbedt_status vdbedt_batch_global(vdbedt_batch_handle b);
+/* vdbedt_set_tuning on every grid of the batch. */
+vdbedt_status vdbedt_batch_set_tuning(vdbedt_batch_handle b, const vdbedt_tuning* t);
+/* Report device-side errors of any grid (vdbedt_synchronize on each). */
+vdbedt_status vdbedt_batch_synchronize(vdbedt_batch_handle b);
+/* Phase timing of vdbedt_batch_global (CUDA events on the batch's stream); in the result, ingest_ms
+ * is the staged-record ingest, z_ms covers the y and z passes together and y_ms is 0. */
+vdbedt_status vdbedt_batch_set_profiling(vdbedt_batch_handle b, int on);
+vdbedt_status vdbedt_batch_get_phase_times(vdbedt_batch_handle b, vdbedt_phase_times* out);
+const char* vdbedt_batch_last_error(vdbedt_batch_handle b);
+
+/* Global transform of k handles in one call.  When they are exactly the grids of one batch (in
+ * any order) this is vdbedt_batch_global; otherwise each handle is transformed in turn on its
+ * own stream.  Bit-identical to vdbedt_global on each. */
+vdbedt_status vdbedt_global_batched(vdbedt_handle* hs, int32_t k);
 
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 int64_t vdbedt_kernel_launches(void);

@@ -22,8 +22,11 @@ cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t 
                                 int32_t* counters, cudaStream_t st);
 }
 
+struct vdbedt_batch;
+
 struct vdbedt_map {
   GridView g{};
+  vdbedt_batch* batch = nullptr;  // owning batch of a batch grid (its bricks live in the batch's pool)
   vdbedt_config cfg{};
   int device = 0;
   cudaStream_t st = nullptr;
@@ -111,12 +114,17 @@ vdbedt_status check_handle(vdbedt_map* h) {
   return VDBEDT_OK;
 }
 
+int32_t* batch_error_word(const vdbedt_map* h);
+
 vdbedt_status device_errors(vdbedt_map* h) {
   cudaError_t e =
       cudaMemcpyAsync(h->h_pinned + 32, h->g.counters + C_ERR, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+  h->h_pinned[33] = 0;
+  if (e == cudaSuccess && h->batch)
+    e = cudaMemcpyAsync(h->h_pinned + 33, batch_error_word(h), sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
-  int bits = h->h_pinned[32];
+  int bits = h->h_pinned[32] | h->h_pinned[33];
   if (!bits) return VDBEDT_OK;
   if (bits & (kErrOverflow | kErrNodeOverflow))
     return fail(h, VDBEDT_EOVERFLOW, "brick or node capacity exceeded; the field is incomplete until vdbedt_reset");
@@ -208,11 +216,29 @@ vdbedt_status do_global(vdbedt_map* h) {
   return VDBEDT_OK;
 }
 
-}  // namespace
+// Per-brick storage and work lists of a batch grid, carved from the batch's pool.
+struct PoolSlice {
+  unsigned long long* occ;
+  uint16_t* g1;
+  uint16_t* g2;
+  int32_t* dist;
+  int4* bcoord;
+  uint32_t* bflags;
+  int32_t* bepoch;
+  int32_t* counters;
+  int32_t* items_ctr;
+  Items items;
+  int slot_base;
+  int item_cap;
+};
 
-extern "C" {
+// Brick capacity of a configuration (after validation).
+int64_t config_cap(const vdbedt_config* cfg) {
+  const int64_t nbr = ceil_div(cfg->nx, 8) * ceil_div(cfg->ny, 8) * ceil_div(cfg->nz, 8);
+  return cfg->max_bricks > 0 ? std::min<int64_t>(cfg->max_bricks, nbr) : nbr;
+}
 
-vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out) {
+vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbedt_map** out) {
   if (!cfg || !out) return fail(nullptr, VDBEDT_EINVAL, "null argument");
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, VDBEDT_EINVAL, "grid size must be >= 1");
   if (cfg->dmax < 1 || cfg->dmax > VDBEDT_DMAX_LIMIT) return fail(nullptr, VDBEDT_EINVAL, "dmax out of range");
@@ -279,17 +305,35 @@ vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out) {
   AL(g.mwork, node_cap * 384);
   AL(g.node_key, node_cap);
   AL(g.mark, node_cap * 3 * 1024);
-  AL(g.occ, cap * 8);
-  AL(g.g1, cap * kBrickVox);
-  AL(g.g2, cap * kBrickVox);
-  AL(g.dist, cap * kBrickVox);
-  AL(g.bcoord, cap);
-  AL(g.bflags, cap);
-  AL(g.bepoch, cap);
-  AL(g.counters, C_NUM);
-  for (int a = 0; a < 3; ++a) {
-    AL(h->items.run[a], cap);
-    AL(h->items.slots[a], cap * kItemSlots);
+  if (slice) {
+    g.occ = slice->occ;
+    g.g1 = slice->g1;
+    g.g2 = slice->g2;
+    g.dist = slice->dist;
+    g.bcoord = slice->bcoord;
+    g.bflags = slice->bflags;
+    g.bepoch = slice->bepoch;
+    g.counters = slice->counters;
+    g.items_ctr = slice->items_ctr;
+    g.slot_base = slice->slot_base;
+    g.item_cap = slice->item_cap;
+    h->items = slice->items;
+  } else {
+    AL(g.occ, cap * 8);
+    AL(g.g1, cap * kBrickVox);
+    AL(g.g2, cap * kBrickVox);
+    AL(g.dist, cap * kBrickVox);
+    AL(g.bcoord, cap);
+    AL(g.bflags, cap);
+    AL(g.bepoch, cap);
+    AL(g.counters, C_NUM);
+    for (int a = 0; a < 3; ++a) {
+      AL(h->items.run[a], cap);
+      AL(h->items.slots[a], cap * kItemSlots);
+    }
+    g.items_ctr = g.counters + C_X_ITEMS;
+    g.slot_base = 0;
+    g.item_cap = (int)cap;
   }
   AL(h->changed, cap);
   AL(h->d_invalid, 4);
@@ -302,15 +346,28 @@ vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out) {
   cudaMemsetAsync(g.amask, 0, sizeof(uint32_t) * (size_t)node_cap * 128, h->st);
   cudaMemsetAsync(g.mwork, 0, sizeof(uint32_t) * (size_t)node_cap * 384, h->st);
   cudaMemsetAsync(g.mark, 0, sizeof(int32_t) * (size_t)node_cap * 3 * 1024, h->st);
-  cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, h->st);
+  if (!slice) cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, h->st);
   e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return bail(e, "init");
   *out = h;
   return VDBEDT_OK;
 }
 
-vdbedt_status vdbedt_destroy(vdbedt_handle h) {
-  if (!h) return VDBEDT_OK;
+}  // namespace
+
+extern "C" {
+
+vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out) {
+  vdbedt_map* h = nullptr;
+  vdbedt_status s = create_impl(cfg, nullptr, &h);
+  if (s == VDBEDT_OK) *out = h;
+  return s;
+}
+
+}  // extern "C"
+
+namespace {
+void destroy_impl(vdbedt_map* h) {
   DeviceGuard guard(h->device);
   cudaStreamSynchronize(h->st);
   for (void* p : h->allocs) cudaFree(p);
@@ -322,6 +379,15 @@ vdbedt_status vdbedt_destroy(vdbedt_handle h) {
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
+}
+}  // namespace
+
+extern "C" {
+
+vdbedt_status vdbedt_destroy(vdbedt_handle h) {
+  if (!h) return VDBEDT_OK;
+  if (h->batch) return fail(h, VDBEDT_EINVAL, "a batch grid is released with its batch");
+  destroy_impl(h);
   return VDBEDT_OK;
 }
 
@@ -444,6 +510,7 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
   }
   if (stats) {
     CK(h, cudaMemcpyAsync(h->h_pinned, h->g.counters, sizeof(int32_t) * C_NUM, cudaMemcpyDeviceToHost, h->st), "d2h");
+    CK(h, cudaMemcpyAsync(h->h_pinned + 44, h->g.items_ctr, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, h->st), "d2h");
     if (counted)
       CK(h, cudaMemcpyAsync(h->h_pinned + 40, h->d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st), "d2h");
     s = device_errors(h);  // synchronises
@@ -452,9 +519,9 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     stats->records = counted ? h->h_pinned[40] : nrec;
     stats->net_flips = c[C_FLIPS];
     stats->changed_bricks = c[C_CHANGED];
-    stats->x_items = c[C_X_ITEMS];
-    stats->y_items = c[C_Y_ITEMS];
-    stats->z_items = c[C_Z_ITEMS];
+    stats->x_items = c[44];
+    stats->y_items = c[45];
+    stats->z_items = c[46];
     stats->new_bricks = c[C_NEW_BRICKS];
   }
   return VDBEDT_OK;
@@ -610,8 +677,361 @@ int64_t vdbedt_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 const char* vdbedt_last_error(vdbedt_handle h) { return h ? h->err.c_str() : g_last_error.c_str(); }
 
+}  // extern "C"
+
+// ---- batches of grids ----
+struct vdbedt_batch {
+  int k = 0;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::vector<vdbedt_map*> maps;
+  std::vector<void*> allocs;
+  size_t device_bytes = 0;
+  GridView pool{};               // pass view over the shared pool (the batch's counters and work lists)
+  Items items{};                 // work lists of every grid of the batch
+  int32_t* counters = nullptr;   // (k + 1) * C_NUM words: grid i at i * C_NUM, the batch at k * C_NUM
+  GridView* d_views = nullptr;   // the k grids' views in device memory
+  BatchShape shape{};
+  Scratch io;
+  Tuning tune;
+  std::string err;
+  bool profiling = false;
+  cudaEvent_t ev[6] = {};
+  bool ev_recorded = false;
+};
+
+namespace {
+
+int32_t* batch_error_word(const vdbedt_map* h) { return h->batch->counters + (size_t)h->batch->k * C_NUM + C_ERR; }
+
+vdbedt_status bfail(vdbedt_batch* b, vdbedt_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  g_last_error = msg;
+  return s;
+}
+
+void destroy_batch(vdbedt_batch* b) {
+  DeviceGuard guard(b->device);
+  if (b->st) cudaStreamSynchronize(b->st);
+  for (vdbedt_map* m : b->maps) destroy_impl(m);
+  for (void* p : b->allocs) cudaFree(p);
+  if (b->io.buf) cudaFree(b->io.buf);
+  for (int i = 0; i < 6; ++i)
+    if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+void bmark(vdbedt_batch* b, int i) {
+  if (b->profiling) cudaEventRecord(b->ev[i], b->st);
+}
+
+vdbedt_status batch_members_ok(vdbedt_batch* b) {
+  for (vdbedt_map* m : b->maps)
+    if (m->sticky == VDBEDT_ECUDA) return bfail(b, VDBEDT_ECUDA, "a grid of the batch hit a CUDA error");
+  return VDBEDT_OK;
+}
+
+#define BCK(b, expr, where)                                                                          \
+  do {                                                                                             \
+    cudaError_t _e = (expr);                                                                       \
+    if (_e != cudaSuccess) {                                                                       \
+      for (vdbedt_map* _m : (b)->maps) _m->sticky = VDBEDT_ECUDA;                                  \
+      return bfail((b), _e == cudaErrorMemoryAllocation ? VDBEDT_ENOMEM : VDBEDT_ECUDA,            \
+                   std::string(where) + ": " + cudaGetErrorString(_e));                            \
+    }                                                                                              \
+  } while (0)
+
+vdbedt_status batch_global(vdbedt_batch* b) {
+  vdbedt_status s = batch_members_ok(b);
+  if (s) return s;
+  DeviceGuard guard(b->device);
+  const GridView& g0 = b->maps[0]->g;
+  if (!half_path(g0)) {
+    // dmax above 45: the generic kernels find bricks through each grid's own tables; grid by grid
+    for (vdbedt_map* m : b->maps) {
+      s = do_global(m);
+      if (s) return bfail(b, s, m->err);
+    }
+    return VDBEDT_OK;
+  }
+  Tuning t = b->tune;
+  for (int a = 0; a < 3; ++a) t.run[a] = effective_run(g0, b->tune, a);
+  bmark(b, 0);
+  // staged records: applied grid by grid (the sort-based ingest keeps per-grid scratch)
+  for (vdbedt_map* m : b->maps) {
+    if (m->stage_n <= 0) continue;
+    BCK(b, cudaMemsetAsync(m->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), b->st), "memset");
+    BCK(b, launch_ingest_records(m->g, m->stage, m->stage_n, stage_count(m), false, nullptr, m->scr, b->st), "ingest");
+    clear_stage(m);
+  }
+  bmark(b, 1);
+  BCK(b, launch_activation_batch(b->d_views, b->shape, b->st), "activation");
+  bmark(b, 2);
+  BCK(b, launch_build_items_batch(b->d_views, b->shape, t, b->items, b->pool.items_ctr, b->st), "items");
+  bmark(b, 3);
+  BCK(b, launch_pass(b->pool, t, 0, b->items, b->st), "x pass");
+  bmark(b, 4);
+  BCK(b, launch_pass(b->pool, t, 1, b->items, b->st), "y pass");
+  BCK(b, launch_pass(b->pool, t, 2, b->items, b->st), "z pass");
+  bmark(b, 5);
+  b->ev_recorded = b->profiling;
+  for (vdbedt_map* m : b->maps) {
+    m->computed = true;
+    m->dense_pending = false;
+  }
+  return VDBEDT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vdbedt_status vdbedt_batch_create(const vdbedt_config* cfgs, int32_t k, vdbedt_batch_handle* out) {
+  if (!cfgs || !out || k < 1 || k > kBatchMax) return bfail(nullptr, VDBEDT_EINVAL, "need 1 <= k <= VDBEDT_BATCH_MAX configs");
+  int64_t total = 0;
+  for (int i = 0; i < k; ++i) {
+    const vdbedt_config& c = cfgs[i];
+    if (c.dmax != cfgs[0].dmax || c.device != cfgs[0].device || c.stream != cfgs[0].stream ||
+        c.voxel_size != cfgs[0].voxel_size)
+      return bfail(nullptr, VDBEDT_EINVAL, "the grids of a batch share dmax, voxel_size, device and stream");
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.nx >= kBadCoord || c.ny >= kBadCoord || c.nz >= kBadCoord)
+      return bfail(nullptr, VDBEDT_EINVAL, "grid size out of range");
+    total += config_cap(&c);
+  }
+  if (total * kItemSlots >= (int64_t)INT32_MAX) return bfail(nullptr, VDBEDT_EINVAL, "batch too large");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfgs[0].device < 0 || cfgs[0].device >= ndev) {
+    cudaGetLastError();
+    return bfail(nullptr, VDBEDT_EINVAL, "no such CUDA device");
+  }
+  DeviceGuard guard(cfgs[0].device);
+  vdbedt_batch* b = new vdbedt_batch();
+  b->k = k;
+  b->device = cfgs[0].device;
+  cudaError_t e = cudaSuccess;
+  auto bail = [&](cudaError_t err, const char* where) {
+    vdbedt_status st = err == cudaErrorMemoryAllocation ? VDBEDT_ENOMEM : VDBEDT_ECUDA;
+    cudaGetLastError();
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(err);
+    destroy_batch(b);
+    return st;
+  };
+  if (cfgs[0].stream) {
+    b->st = (cudaStream_t)cfgs[0].stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(e, "stream");
+    b->own_stream = true;
+  }
+  GridView& p = b->pool;
+#define BAL(ptr, count)                                                        \
+  do {                                                                         \
+    size_t bytes_ = std::max<size_t>((size_t)(count) * sizeof(*(ptr)), 256);   \
+    e = cudaMalloc((void**)&(ptr), bytes_);                                    \
+    if (e != cudaSuccess) return bail(e, "device alloc");                      \
+    b->allocs.push_back((void*)(ptr));                                         \
+    b->device_bytes += bytes_;                                                 \
+  } while (0)
+  BAL(p.occ, total * 8);
+  BAL(p.g1, total * kBrickVox);
+  BAL(p.g2, total * kBrickVox);
+  BAL(p.dist, total * kBrickVox);
+  BAL(p.bcoord, total);
+  BAL(p.bflags, total);
+  BAL(p.bepoch, total);
+  BAL(b->counters, (size_t)(k + 1) * C_NUM);
+  for (int a = 0; a < 3; ++a) {
+    BAL(b->items.run[a], total);
+    BAL(b->items.slots[a], total * kItemSlots);
+  }
+  BAL(b->d_views, k);
+#undef BAL
+  e = cudaMemsetAsync(b->counters, 0, sizeof(int32_t) * (size_t)(k + 1) * C_NUM, b->st);
+  if (e != cudaSuccess) return bail(e, "memset");
+  int32_t* bctr = b->counters + (size_t)k * C_NUM;
+  int64_t off = 0;
+  std::vector<GridView> views((size_t)k);
+  for (int i = 0; i < k; ++i) {
+    vdbedt_config c = cfgs[i];
+    c.stream = (void*)b->st;
+    PoolSlice sl;
+    sl.occ = p.occ + (size_t)off * 8;
+    sl.g1 = p.g1 + (size_t)off * kBrickVox;
+    sl.g2 = p.g2 + (size_t)off * kBrickVox;
+    sl.dist = p.dist + (size_t)off * kBrickVox;
+    sl.bcoord = p.bcoord + off;
+    sl.bflags = p.bflags + off;
+    sl.bepoch = p.bepoch + off;
+    sl.counters = b->counters + (size_t)i * C_NUM;
+    sl.items_ctr = bctr + C_X_ITEMS;
+    sl.items = b->items;
+    sl.slot_base = (int)off;
+    sl.item_cap = (int)total;
+    vdbedt_map* m = nullptr;
+    vdbedt_status st = create_impl(&c, &sl, &m);
+    if (st) {
+      destroy_batch(b);
+      return st;
+    }
+    m->batch = b;
+    b->maps.push_back(m);
+    views[(size_t)i] = m->g;
+    b->shape.max_node_cap = std::max(b->shape.max_node_cap, m->g.node_cap);
+    b->shape.max_cap = std::max(b->shape.max_cap, m->g.cap);
+    b->shape.max_grid_bricks = std::max<int64_t>(b->shape.max_grid_bricks, (int64_t)m->g.BX * m->g.BY * m->g.BZ);
+    off += m->g.cap;
+  }
+  b->shape.k = k;
+  // the pool view: shape fields of grid 0 (dmax, R, INF are common), the batch's words and lists
+  {
+    const GridView& g0 = b->maps[0]->g;
+    GridView pv = g0;
+    pv.occ = p.occ;
+    pv.g1 = p.g1;
+    pv.g2 = p.g2;
+    pv.dist = p.dist;
+    pv.bcoord = p.bcoord;
+    pv.bflags = p.bflags;
+    pv.bepoch = p.bepoch;
+    pv.counters = bctr;
+    pv.items_ctr = bctr + C_X_ITEMS;
+    pv.slot_base = 0;
+    pv.cap = (int)total;
+    pv.item_cap = (int)total;
+    b->pool = pv;
+  }
+  e = cudaMemcpy(b->d_views, views.data(), sizeof(GridView) * (size_t)k, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(e, "views");
+  e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return bail(e, "init");
+  *out = b;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_batch_destroy(vdbedt_batch_handle b) {
+  if (b) destroy_batch(b);
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_batch_map(vdbedt_batch_handle b, int32_t i, vdbedt_handle* out) {
+  if (!b || !out || i < 0 || i >= b->k) return bfail(b, VDBEDT_EINVAL, "bad batch index");
+  *out = b->maps[(size_t)i];
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_batch_set_occupancy_dense(vdbedt_batch_handle b, const uint8_t* const* grids, int on_device) {
+  if (!b || !grids) return bfail(b, VDBEDT_EINVAL, "null argument");
+  for (int i = 0; i < b->k; ++i)
+    if (!grids[i]) return bfail(b, VDBEDT_EINVAL, "null grid");
+  vdbedt_status s = batch_members_ok(b);
+  if (s) return s;
+  DeviceGuard guard(b->device);
+  for (vdbedt_map* m : b->maps) {
+    clear_stage(m);
+    m->computed = false;
+    m->dense_pending = true;
+  }
+  BCK(b, launch_reset_batch(b->d_views, b->shape, b->counters, (size_t)(b->k + 1) * C_NUM, b->st), "reset");
+  std::vector<const uint8_t*> src((size_t)b->k);
+  if (on_device) {
+    for (int i = 0; i < b->k; ++i) src[(size_t)i] = grids[i];
+  } else {
+    size_t total = 0;
+    for (vdbedt_map* m : b->maps) total += ((size_t)m->g.nx * m->g.ny * m->g.nz + 255) & ~(size_t)255;
+    BCK(b, ensure_scratch(b->io, total), "io alloc");
+    size_t off = 0;
+    for (int i = 0; i < b->k; ++i) {
+      const GridView& g = b->maps[(size_t)i]->g;
+      const size_t bytes = (size_t)g.nx * g.ny * g.nz;
+      BCK(b, cudaMemcpyAsync((uint8_t*)b->io.buf + off, grids[i], bytes, cudaMemcpyHostToDevice, b->st), "h2d");
+      src[(size_t)i] = (const uint8_t*)b->io.buf + off;
+      off += (bytes + 255) & ~(size_t)255;
+    }
+  }
+  BCK(b, launch_ingest_dense_batch(b->d_views, b->shape, src.data(), b->st), "dense ingest");
+  if (!on_device) BCK(b, cudaStreamSynchronize(b->st), "sync");
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_batch_global(vdbedt_batch_handle b) {
+  if (!b) return bfail(nullptr, VDBEDT_EINVAL, "null batch");
+  return batch_global(b);
+}
+
+vdbedt_status vdbedt_batch_set_tuning(vdbedt_batch_handle b, const vdbedt_tuning* t) {
+  if (!b) return bfail(nullptr, VDBEDT_EINVAL, "null batch");
+  for (vdbedt_map* m : b->maps) {
+    vdbedt_status s = vdbedt_set_tuning(m, t);
+    if (s) return bfail(b, s, m->err);
+  }
+  b->tune = b->maps[0]->tune;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_batch_synchronize(vdbedt_batch_handle b) {
+  if (!b) return bfail(nullptr, VDBEDT_EINVAL, "null batch");
+  for (vdbedt_map* m : b->maps) {
+    vdbedt_status s = vdbedt_synchronize(m);
+    if (s) return bfail(b, s, m->err);
+  }
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_batch_set_profiling(vdbedt_batch_handle b, int on) {
+  if (!b) return bfail(nullptr, VDBEDT_EINVAL, "null batch");
+  DeviceGuard guard(b->device);
+  if (on && !b->ev[0])
+    for (int i = 0; i < 6; ++i) BCK(b, cudaEventCreate(&b->ev[i]), "event");
+  b->profiling = on != 0;
+  b->ev_recorded = false;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_batch_get_phase_times(vdbedt_batch_handle b, vdbedt_phase_times* out) {
+  if (!b || !out) return bfail(b, VDBEDT_EINVAL, "null argument");
+  if (!b->ev_recorded) return bfail(b, VDBEDT_EINVAL, "no profiled batch transform since profiling was enabled");
+  DeviceGuard guard(b->device);
+  BCK(b, cudaEventSynchronize(b->ev[5]), "event sync");
+  float ms[5];
+  for (int i = 0; i < 5; ++i) BCK(b, cudaEventElapsedTime(&ms[i], b->ev[i], b->ev[i + 1]), "event time");
+  out->ingest_ms = ms[0];
+  out->activation_ms = ms[1];
+  out->items_ms = ms[2];
+  out->x_ms = ms[3];
+  out->y_ms = 0.f;  // the y and z passes are timed together
+  out->z_ms = ms[4];
+  return VDBEDT_OK;
+}
+
+const char* vdbedt_batch_last_error(vdbedt_batch_handle b) { return b ? b->err.c_str() : g_last_error.c_str(); }
+
+// Several grids in one call.  When the handles are exactly the grids of one batch (any order),
+// each step runs once for all of them (vdbedt_batch_global); otherwise grid by grid.
 vdbedt_status vdbedt_global_batched(vdbedt_handle* hs, int32_t k) {
   if (k < 0 || (k > 0 && !hs)) return fail(nullptr, VDBEDT_EINVAL, "bad batch");
+  if (k == 0) return VDBEDT_OK;
+  for (int32_t i = 0; i < k; ++i)
+    if (!hs[i]) return fail(nullptr, VDBEDT_EINVAL, "null handle in batch");
+  vdbedt_batch* b = hs[0]->batch;
+  bool whole = b && b->k == k;
+  if (whole) {
+    std::vector<char> seen((size_t)k, 0);
+    for (int32_t i = 0; i < k && whole; ++i) {
+      int idx = -1;
+      if (hs[i]->batch == b)
+        for (int j = 0; j < k; ++j)
+          if (b->maps[(size_t)j] == hs[i]) idx = j;
+      if (idx < 0 || seen[(size_t)idx]) whole = false;
+      else seen[(size_t)idx] = 1;
+    }
+  }
+  if (whole) {
+    vdbedt_status s = batch_global(b);
+    if (s) g_last_error = b->err;
+    return s;
+  }
   for (int32_t i = 0; i < k; ++i) {
     vdbedt_status s = vdbedt_global(hs[i]);
     if (s) return s;

@@ -35,8 +35,29 @@ inline int bits_for(uint64_t maxval) {
   return b;
 }
 
+// View sources of the kernels that run once per grid: a single grid (the view is a kernel
+// parameter), or every grid of a batch (views in device memory, grid = blockIdx.y).
+struct OneView {
+  GridView g;
+  __device__ __forceinline__ GridView get() const { return g; }
+};
+struct BatchViews {
+  const GridView* v;
+  __device__ __forceinline__ GridView get() const { return v[blockIdx.y]; }
+};
+struct OneSrc {
+  const uint8_t* p;
+  __device__ __forceinline__ const uint8_t* get() const { return p; }
+};
+struct BatchSrc {
+  const uint8_t* p[kBatchMax];
+  __device__ __forceinline__ const uint8_t* get() const { return p[blockIdx.y]; }
+};
+
 // ---- reset ----
-__global__ void k_reset_nodes(GridView g) {
+template <class VS>
+__global__ void k_reset_nodes(VS vs) {
+  const GridView g = vs.get();
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int64_t total = (int64_t)nn * kNodeBricks;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -59,9 +80,9 @@ __global__ void k_reset_nodes(GridView g) {
 // (kept on the device, so that a captured update replays with a fresh epoch each time).
 __global__ void k_begin_update(GridView g) {
   if (threadIdx.x == 0) {
-    g.counters[C_Y_ITEMS] = 0;
-    g.counters[C_Z_ITEMS] = 0;
-    g.counters[C_X_ITEMS] = 0;
+    g.items_ctr[0] = 0;
+    g.items_ctr[1] = 0;
+    g.items_ctr[2] = 0;
     g.counters[C_CHANGED] = 0;
     g.counters[C_FLIPS] = 0;
     g.counters[C_NEW_BRICKS] = 0;
@@ -397,7 +418,10 @@ __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, const ui
 // ---- dense ingest ----
 // One warp per brick of the grid: each lane reads two 8-voxel x-rows; a brick with any occupied
 // voxel is allocated and its 64-byte mask written.
-__global__ void k_ingest_dense(GridView g, const uint8_t* __restrict__ grid) {
+template <class VS, class SRC>
+__global__ void k_ingest_dense(VS vs, SRC src) {
+  const GridView g = vs.get();
+  const uint8_t* __restrict__ grid = src.get();
   const int64_t nbr = (int64_t)g.BX * g.BY * g.BZ;
   const int lane = threadIdx.x & 31;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -441,7 +465,9 @@ __global__ void k_ingest_dense(GridView g, const uint8_t* __restrict__ grid) {
 // pure gather over neighbouring nodes' rows (no atomics).  A mask word holds two 16-brick x-rows:
 // word (y >> 1) + 8 z, bits 16 (y & 1) + x.
 
-__global__ void k_clear_masks(GridView g) {
+template <class VS>
+__global__ void k_clear_masks(VS vs) {
+  const GridView g = vs.get();
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -453,7 +479,9 @@ __global__ void k_clear_masks(GridView g) {
   }
 }
 
-__global__ void k_obstacle_flags(GridView g) {
+template <class VS>
+__global__ void k_obstacle_flags(VS vs) {
+  const GridView g = vs.get();
   const int nb = min(g.counters[C_NBRICKS], g.cap);
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
     bool obst = brick_has_obstacle(g, s);
@@ -468,7 +496,9 @@ __global__ void k_obstacle_flags(GridView g) {
 }
 
 // One warp per node holding obstacle bricks: create the nodes within ceil(R / 16) nodes of it.
-__global__ void k_node_halo(GridView g) {
+template <class VS>
+__global__ void k_node_halo(VS vs) {
+  const GridView g = vs.get();
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int lane = threadIdx.x & 31;
   const int NR = (g.R + 15) / 16, side = 2 * NR + 1;
@@ -498,8 +528,9 @@ __device__ __forceinline__ int node_at(const GridView& g, int x, int y, int z) {
 // Stage 0 -> 1: dilate each x-row by R across the neighbouring nodes along x.
 // Stage 1 -> 2: OR of the rows y - R .. y + R; stage 2 -> amask: rows z - R .. z + R, then clipped
 // to the grid.  One thread per (node, mask word), i.e. two rows.
-template <int AXIS>
-__global__ void k_dilate_stage(GridView g) {
+template <int AXIS, class VS>
+__global__ void k_dilate_stage(VS vs) {
+  const GridView g = vs.get();
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int R = g.R;
   const int src_off = AXIS * 128;  // obstacle bits, then stage 1, then stage 2
@@ -584,7 +615,9 @@ __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int
 
 // Allocate every marked brick without storage: a block per (node, 512-brick chunk), two bricks
 // per thread, one atomic per block for the slot range (block scan of the per-thread counts).
-__global__ void __launch_bounds__(256) k_alloc_marked(GridView g, bool init_fields) {
+template <class VS>
+__global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
+  const GridView g = vs.get();
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   for (int b = blockIdx.x; b < nn * 8; b += gridDim.x) {
     const int node = b >> 3, chunk = b & 7;
@@ -630,9 +663,9 @@ __device__ __forceinline__ void queue_run(const GridView& g, int axis, int bx, i
   const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
   const int id = l[a1] + 16 * (l[a2] + 16 * (l[axis] / run));
   if (atomicExch(&g.mark[((size_t)node * 3 + axis) * 1024 + id], epoch) != epoch) {
-    const int p = atomicAdd(&g.counters[items_counter(axis)], 1);
+    const int p = atomicAdd(&g.items_ctr[axis], 1);
     const int back = l[axis] % run;
-    if (p < g.cap)
+    if (p < g.item_cap)
       items[p] = pack_brick(bx - (axis == 0 ? back : 0), by - (axis == 1 ? back : 0), bz - (axis == 2 ? back : 0));
   }
 }
@@ -642,7 +675,9 @@ __device__ __forceinline__ void queue_run(const GridView& g, int axis, int bx, i
 // block-wide scan compacts the runs and one atomic reserves their places; the run slot lists are
 // then read straight from the child tables of the node and of its neighbour along the axis
 // (R <= 6 < 16, so the halo reaches at most one node each way), one slot per thread.
-__global__ void __launch_bounds__(256) k_items_nodes(GridView g, int rx, int ry, int rz, Items it, bool with_slots) {
+template <class VS>
+__global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int rz, Items it, bool with_slots) {
+  const GridView g = vs.get();
   __shared__ int wsum[8];
   __shared__ int base_sh, count_sh;
   __shared__ int nbr_sh[2];
@@ -687,7 +722,7 @@ __global__ void __launch_bounds__(256) k_items_nodes(GridView g, int rx, int ry,
         tot += t;
       }
       count_sh = tot;
-      base_sh = tot ? atomicAdd(&g.counters[items_counter(axis)], tot) : 0;
+      base_sh = tot ? atomicAdd(&g.items_ctr[axis], tot) : 0;
     }
     __syncthreads();
     const int base = base_sh, cnt = count_sh;
@@ -695,7 +730,7 @@ __global__ void __launch_bounds__(256) k_items_nodes(GridView g, int rx, int ry,
       const int pos = wsum[warp] + __popc(bal & ((1u << lane) - 1u));
       lines[pos] = (unsigned char)threadIdx.x;
       const int p = base + pos;
-      if (p < g.cap) {
+      if (p < g.item_cap) {
         int l0[3];
         l0[axis] = r0;
         l0[a1] = o1;
@@ -708,7 +743,7 @@ __global__ void __launch_bounds__(256) k_items_nodes(GridView g, int rx, int ry,
       for (int idx = threadIdx.x; idx < cnt * nb; idx += 256) {
         const int i = idx / nb, j = idx % nb;
         const int p = base + i;
-        if (p >= g.cap) continue;
+        if (p >= g.item_cap) continue;
         const int line = lines[i];
         int l[3];
         l[a1] = line & 15;
@@ -725,7 +760,7 @@ __global__ void __launch_bounds__(256) k_items_nodes(GridView g, int rx, int ry,
         int sv = -1;
         if (src >= 0) {
           sv = g.child[(size_t)src * kNodeBricks + local_brick(l[0], l[1], l[2])];
-          if (sv < 0) sv = -1;
+          sv = sv >= 0 ? sv + g.slot_base : -1;
         }
         it.slots[axis][(size_t)p * kItemSlots + j] = sv;
       }
@@ -737,7 +772,7 @@ __global__ void __launch_bounds__(256) k_items_nodes(GridView g, int rx, int ry,
 // Slots of each queued run's bricks with R bricks of halo on both sides along the axis.
 __global__ void k_item_slots(GridView g, int axis, int run, const unsigned long long* __restrict__ items,
                              int32_t* __restrict__ out) {
-  const int n = min(g.counters[items_counter(axis)], g.cap);
+  const int n = min(g.items_ctr[axis], g.item_cap);
   const int nb = run + 2 * g.R;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n * kItemSlots;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -748,6 +783,7 @@ __global__ void k_item_slots(GridView g, int axis, int run, const unsigned long 
       unpack_brick(items[item], bx, by, bz);
       const int off = j - g.R;
       s = find_brick(g, bx + (axis == 0 ? off : 0), by + (axis == 1 ? off : 0), bz + (axis == 2 ? off : 0));
+      if (s >= 0) s += g.slot_base;
     }
     out[i] = s;
   }
@@ -813,7 +849,7 @@ cudaError_t ensure_scratch(Scratch& s, size_t bytes) {
 }
 
 cudaError_t launch_reset(const GridView& g, cudaStream_t st) {
-  VDB_LAUNCH(k_reset_nodes, 1024, kT, 0, st, g);
+  VDB_LAUNCH(k_reset_nodes<OneView>, 1024, kT, 0, st, OneView{g});
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, st);
@@ -929,38 +965,89 @@ cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStre
   int64_t threads = nbr * 32;
   unsigned blocks = blocks_for(threads);
   if (blocks > 152 * 64) blocks = 152 * 64;
-  VDB_LAUNCH(k_ingest_dense, blocks, kT, 0, st, g, grid);
+  VDB_LAUNCH((k_ingest_dense<OneView, OneSrc>), blocks, kT, 0, st, OneView{g}, OneSrc{grid});
   return cudaGetLastError();
 }
 
 cudaError_t launch_activation_full(const GridView& g, cudaStream_t st) {
-  VDB_LAUNCH(k_clear_masks, 256, kT, 0, st, g);
-  VDB_LAUNCH(k_obstacle_flags, 1024, kT, 0, st, g);
-  VDB_LAUNCH(k_node_halo, 64, kT, 0, st, g);
-  VDB_LAUNCH(k_dilate_stage<0>, 256, kT, 0, st, g);
-  VDB_LAUNCH(k_dilate_stage<1>, 256, kT, 0, st, g);
-  VDB_LAUNCH(k_dilate_stage<2>, 256, kT, 0, st, g);
-  VDB_LAUNCH(k_alloc_marked, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, g, false);
+  const OneView v{g};
+  VDB_LAUNCH(k_clear_masks<OneView>, 256, kT, 0, st, v);
+  VDB_LAUNCH(k_obstacle_flags<OneView>, 1024, kT, 0, st, v);
+  VDB_LAUNCH(k_node_halo<OneView>, 64, kT, 0, st, v);
+  VDB_LAUNCH((k_dilate_stage<0, OneView>), 256, kT, 0, st, v);
+  VDB_LAUNCH((k_dilate_stage<1, OneView>), 256, kT, 0, st, v);
+  VDB_LAUNCH((k_dilate_stage<2, OneView>), 256, kT, 0, st, v);
+  VDB_LAUNCH(k_alloc_marked<OneView>, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, v, false);
   return cudaGetLastError();
 }
 
 static cudaError_t clear_item_counters(const GridView& g, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(g.counters + C_Y_ITEMS, 0, 2 * sizeof(int32_t), st);
-  if (e != cudaSuccess) return e;
-  return cudaMemsetAsync(g.counters + C_X_ITEMS, 0, sizeof(int32_t), st);
+  return cudaMemsetAsync(g.items_ctr, 0, 3 * sizeof(int32_t), st);
 }
 
 cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, const Items& it, bool with_slots,
                                     cudaStream_t st) {
   cudaError_t e = clear_item_counters(g, st);
   if (e != cudaSuccess) return e;
-  VDB_LAUNCH(k_items_nodes, g.node_cap * 12 < 8192 ? g.node_cap * 12 : 8192, kT, 0, st, g, t.run[0], t.run[1],
-             t.run[2], it, with_slots);
+  VDB_LAUNCH(k_items_nodes<OneView>, g.node_cap * 12 < 8192 ? g.node_cap * 12 : 8192, kT, 0, st, OneView{g}, t.run[0],
+             t.run[1], t.run[2], it, with_slots);
   return cudaGetLastError();
 }
 
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st) {
   for (int a = 0; a < 3; ++a) VDB_LAUNCH(k_item_slots, 2048, kT, 0, st, g, a, t.run[a], it.run[a], it.slots[a]);
+  return cudaGetLastError();
+}
+
+// ---- batches ----
+cudaError_t launch_reset_batch(const GridView* views, const BatchShape& b, int32_t* counters_all, size_t n_counters,
+                               cudaStream_t st) {
+  if (b.k <= 0) return cudaSuccess;
+  const BatchViews v{views};
+  VDB_LAUNCH(k_reset_nodes<BatchViews>, dim3(1024, b.k), kT, 0, st, v);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(counters_all, 0, sizeof(int32_t) * n_counters, st);
+}
+
+cudaError_t launch_ingest_dense_batch(const GridView* views, const BatchShape& b, const uint8_t* const* srcs,
+                                      cudaStream_t st) {
+  if (b.k <= 0) return cudaSuccess;
+  if (b.k > kBatchMax) return cudaErrorInvalidValue;
+  BatchSrc src;
+  for (int i = 0; i < kBatchMax; ++i) src.p[i] = i < b.k ? srcs[i] : nullptr;
+  unsigned blocks = blocks_for(b.max_grid_bricks * 32);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  VDB_LAUNCH((k_ingest_dense<BatchViews, BatchSrc>), dim3(blocks, b.k), kT, 0, st, BatchViews{views}, src);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_activation_batch(const GridView* views, const BatchShape& b, cudaStream_t st) {
+  if (b.k <= 0) return cudaSuccess;
+  const BatchViews v{views};
+  const unsigned node_words = blocks_for((int64_t)b.max_node_cap * 128);
+  const unsigned bricks = blocks_for(b.max_cap);
+  const unsigned halo = blocks_for((int64_t)b.max_node_cap * 32);
+  const unsigned c256 = node_words < 256 ? node_words : 256;
+  VDB_LAUNCH(k_clear_masks<BatchViews>, dim3(c256, b.k), kT, 0, st, v);
+  VDB_LAUNCH(k_obstacle_flags<BatchViews>, dim3(bricks < 1024 ? bricks : 1024, b.k), kT, 0, st, v);
+  VDB_LAUNCH(k_node_halo<BatchViews>, dim3(halo < 64 ? halo : 64, b.k), kT, 0, st, v);
+  VDB_LAUNCH((k_dilate_stage<0, BatchViews>), dim3(c256, b.k), kT, 0, st, v);
+  VDB_LAUNCH((k_dilate_stage<1, BatchViews>), dim3(c256, b.k), kT, 0, st, v);
+  VDB_LAUNCH((k_dilate_stage<2, BatchViews>), dim3(c256, b.k), kT, 0, st, v);
+  const int chunks = b.max_node_cap * 8 < 8192 ? b.max_node_cap * 8 : 8192;
+  VDB_LAUNCH(k_alloc_marked<BatchViews>, dim3(chunks, b.k), kT, 0, st, v, false);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_items_batch(const GridView* views, const BatchShape& b, const Tuning& t, const Items& it,
+                                     int32_t* items_ctr, cudaStream_t st) {
+  if (b.k <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(items_ctr, 0, 3 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  const int blocks = b.max_node_cap * 12 < 8192 ? b.max_node_cap * 12 : 8192;
+  VDB_LAUNCH(k_items_nodes<BatchViews>, dim3(blocks, b.k), kT, 0, st, BatchViews{views}, t.run[0], t.run[1], t.run[2],
+             it, true);
   return cudaGetLastError();
 }
 
@@ -970,7 +1057,7 @@ cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const in
   cudaError_t e = clear_item_counters(g, st);
   if (e != cudaSuccess) return e;
   VDB_LAUNCH(k_changed_flags_dilate, 1024, kT, 0, st, g, changed);
-  VDB_LAUNCH(k_alloc_marked, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, g, true);
+  VDB_LAUNCH(k_alloc_marked<OneView>, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, OneView{g}, true);
   VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }

@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(32 * (RUN + 1)) k_pass(GridView g, const int32
   int* meta = reinterpret_cast<int*>(smem + S::DATA_BYTES);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::DATA_BYTES + ((S::META_BYTES + 15) & ~(size_t)15));
   uint64_t* empty = full + NS;
-  const int nitems = min(g.counters[items_counter(AXIS)], max_items);
+  const int nitems = min(g.items_ctr[AXIS], max_items);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const __half hinf = __int2half_rn(g.INF);
   const uint32_t inf2 = h2u(__halves2half2(hinf, hinf));
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kGenThreads) k_xy_generic(GridView g, const un
   extern __shared__ __align__(16) unsigned char smem[];
   int* slots = reinterpret_cast<int*>(smem);                        // [NBY][NBX]
   int* g1 = slots + NBX * NBY;                                      // [z][row][x]
-  const int nitems = min(g.counters[C_Y_ITEMS], max_items);
+  const int nitems = min(g.items_ctr[1], max_items);
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     int bx, by0, bz;
     unpack_brick(items[it], bx, by0, bz);
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(kGenThreads) k_z_generic(GridView g, const uns
   extern __shared__ __align__(16) unsigned char smem[];
   int* slots = reinterpret_cast<int*>(smem);
   uint16_t* col = reinterpret_cast<uint16_t*>(slots + NB + 3);  // [brick][512]
-  const int nitems = min(g.counters[C_Z_ITEMS], max_items);
+  const int nitems = min(g.items_ctr[2], max_items);
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     int bx, by, bz0;
     unpack_brick(items[it], bx, by, bz0);
@@ -573,22 +573,40 @@ bool half_path(const GridView& g) { return g.dmax <= 45 && g.R >= 1 && g.R <= 6;
 
 int effective_run(const GridView& g, const Tuning& t, int axis) { return half_path(g) ? t.run[axis] : kGenRun; }
 
+// The half kernels address bricks by pool slot (the slot lists hold local slot + slot_base):
+// their view has the per-brick pointers moved back to the first slot of the pool.
+GridView pool_view(const GridView& g) {
+  GridView p = g;
+  const size_t b = (size_t)g.slot_base;
+  p.occ = g.occ - b * 8;
+  p.g1 = g.g1 - b * kBrickVox;
+  p.g2 = g.g2 - b * kBrickVox;
+  p.dist = g.dist - b * kBrickVox;
+  p.bcoord = g.bcoord - b;
+  p.bflags = g.bflags - b;
+  p.bepoch = g.bepoch - b;
+  p.slot_base = 0;
+  return p;
+}
+
 cudaError_t launch_pass(const GridView& g, const Tuning& t, int axis, const Items& it, cudaStream_t st) {
   const bool prune = t.variant != 1;
   if (half_path(g)) {
-    if (axis == 0) return pass_half_run<0>(g, t.run[0], it.slots[0], g.cap, st, prune);
-    if (axis == 1) return pass_half_run<1>(g, t.run[1], it.slots[1], g.cap, st, prune);
-    return pass_half_run<2>(g, t.run[2], it.slots[2], g.cap, st, prune);
+    const GridView p = pool_view(g);
+    if (axis == 0) return pass_half_run<0>(p, t.run[0], it.slots[0], g.item_cap, st, prune);
+    if (axis == 1) return pass_half_run<1>(p, t.run[1], it.slots[1], g.item_cap, st, prune);
+    return pass_half_run<2>(p, t.run[2], it.slots[2], g.item_cap, st, prune);
   }
+  // the generic kernels find bricks through the grid's own tables (local slots)
   if (axis == 0) return cudaSuccess;  // the generic in-plane kernel reads the masks itself
   if (axis == 1) {
     const int R = g.R, NBX = 2 * R + 1, NBY = kGenRun + 2 * R;
     size_t smem = (size_t)NBX * NBY * 4 + (size_t)8 * 8 * NBY * 8 * 4 + 64;
-    return launch_persistent(k_xy_generic, kGenThreads, smem, g, it.run[1], g.cap, st);
+    return launch_persistent(k_xy_generic, kGenThreads, smem, g, it.run[1], g.item_cap, st);
   }
   const int NB = kGenRun + 2 * g.R;
   size_t smem = (size_t)(NB + 3) * 4 + (size_t)NB * 512 * 2 + 64;
-  return launch_persistent(k_z_generic, kGenThreads, smem, g, it.run[2], g.cap, st);
+  return launch_persistent(k_z_generic, kGenThreads, smem, g, it.run[2], g.item_cap, st);
 }
 
 }  // namespace vdbedt

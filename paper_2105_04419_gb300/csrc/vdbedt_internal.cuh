@@ -40,19 +40,19 @@ enum Counter : int {
   C_NBRICKS = 0,
   C_NNODES = 1,
   C_ERR = 2,
-  C_Y_ITEMS = 3,
-  C_Z_ITEMS = 4,
-  C_CHANGED = 5,
-  C_FLIPS = 6,
-  C_NEW_BRICKS = 7,
-  C_UNIQUE = 8,
-  C_HAS_ZERO = 9,
-  C_FINITE = 10,
-  C_OBST = 11,
-  C_RECORDS = 12,
-  C_SPIN = 13,
-  C_X_ITEMS = 14,
-  C_EPOCH = 15,  // incremental update epoch (run and brick dedupe marks)
+  C_X_ITEMS = 3,  // work items queued per axis (x, y, z: three consecutive words)
+  C_Y_ITEMS = 4,
+  C_Z_ITEMS = 5,
+  C_CHANGED = 6,
+  C_FLIPS = 7,
+  C_NEW_BRICKS = 8,
+  C_UNIQUE = 9,
+  C_HAS_ZERO = 10,
+  C_FINITE = 11,
+  C_OBST = 12,
+  C_RECORDS = 13,
+  C_EPOCH = 14,  // incremental update epoch (run and brick dedupe marks)
+  C_SPARE = 15,
   C_NUM = 16
 };
 
@@ -84,6 +84,13 @@ struct GridView {
   uint32_t* bflags;   // [cap]
   int32_t* bepoch;    // [cap] epoch of the last change (incremental)
   int32_t* counters;  // [C_NUM]
+  // Work lists.  A grid of a batch keeps its bricks in a pool shared by the batch, at slots
+  // slot_base .. slot_base + cap - 1 of the pool; the per-brick pointers above already point at
+  // its first slot.  Work-item slot lists hold pool slots (local slot + slot_base), so that one
+  // pass launch can serve every grid of the batch.  Single grids: slot_base = 0.
+  int slot_base;
+  int item_cap;       // capacity of the work lists (items per axis)
+  int32_t* items_ctr; // [3] items queued along x, y, z (the grid's counters, or the batch's)
 };
 
 __host__ __device__ inline int node_key_of(const GridView& g, int bx, int by, int bz) {
@@ -201,8 +208,7 @@ void note_launch();
   } while (0)
 
 constexpr int kItemSlots = 32;  // slot list entries per work item (run + 2R <= 28 on the half path)
-
-__host__ __device__ inline int items_counter(int axis) { return axis == 0 ? C_X_ITEMS : (axis == 1 ? C_Y_ITEMS : C_Z_ITEMS); }
+constexpr int kBatchMax = 1024;  // grids per batch (the dense-ingest source table is a kernel parameter)
 
 struct Tuning {
   int run[3] = {4, 4, 4};  // bricks per work item along x, y, z
@@ -263,6 +269,23 @@ cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const in
                                     cudaStream_t st);
 // slot lists of every queued run (half path)
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st);
+
+// The same steps for every grid of a batch at once (one launch per step; views: device array of
+// the k grids' views; the grid of a block is blockIdx.y).  `big` is a view with the largest
+// node and brick capacities of the batch (it sizes the launches).
+struct BatchShape {
+  int k;
+  int max_node_cap;
+  int max_cap;
+  int64_t max_grid_bricks;  // largest BX * BY * BZ
+};
+cudaError_t launch_reset_batch(const GridView* views, const BatchShape& b, int32_t* counters_all, size_t n_counters,
+                               cudaStream_t st);
+cudaError_t launch_ingest_dense_batch(const GridView* views, const BatchShape& b, const uint8_t* const* srcs,
+                                      cudaStream_t st);
+cudaError_t launch_activation_batch(const GridView* views, const BatchShape& b, cudaStream_t st);
+cudaError_t launch_build_items_batch(const GridView* views, const BatchShape& b, const Tuning& t, const Items& it,
+                                     int32_t* items_ctr, cudaStream_t st);
 
 // passes (passes.cu)
 bool half_path(const GridView& g);

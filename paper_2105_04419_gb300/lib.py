@@ -68,6 +68,16 @@ SIGNATURES = {
     "vdbedt_clearance_forward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P]),
     "vdbedt_clearance_backward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P, _P]),
     "vdbedt_global_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _I32]),
+    "vdbedt_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), _I32, ctypes.POINTER(ctypes.c_void_p)]),
+    "vdbedt_batch_destroy": (ctypes.c_int, [_H]),
+    "vdbedt_batch_map": (ctypes.c_int, [_H, _I32, ctypes.POINTER(ctypes.c_void_p)]),
+    "vdbedt_batch_set_occupancy_dense": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+    "vdbedt_batch_global": (ctypes.c_int, [_H]),
+    "vdbedt_batch_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(Tuning)]),
+    "vdbedt_batch_synchronize": (ctypes.c_int, [_H]),
+    "vdbedt_batch_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
+    "vdbedt_batch_get_phase_times": (ctypes.c_int, [_H, ctypes.POINTER(PhaseTimes)]),
+    "vdbedt_batch_last_error": (ctypes.c_char_p, [_H]),
     "vdbedt_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(Tuning)]),
     "vdbedt_synchronize": (ctypes.c_int, [_H]),
     "vdbedt_get_info": (ctypes.c_int, [_H, ctypes.POINTER(Info)]),
@@ -120,9 +130,15 @@ class Map:
     """One sparse distance field (a vdbedt handle) on a CUDA device."""
 
     def __init__(self, nx: int, ny: int, nz: int, dmax: int, voxel_size: float = 0.1, device: int = 0,
-                 stream=None, max_bricks: int = 0):
+                 stream=None, max_bricks: int = 0, _borrow=None):
         lib = load()
         torch = _torch()
+        if _borrow is not None:
+            # a grid of a Batch: the batch owns the handle and the stream
+            self._h, self.stream, self._owned = _borrow, stream, False
+            self.device, self.shape_xyz, self.dmax, self.voxel_size = device, (nx, ny, nz), dmax, voxel_size
+            return
+        self._owned = True
         if stream is None:
             # a stream of its own: the library would otherwise create one that torch cannot see
             stream = torch.cuda.Stream(device)
@@ -139,7 +155,8 @@ class Map:
     # -- lifetime --
     def close(self):
         if getattr(self, "_h", None):
-            load().vdbedt_destroy(self._h)
+            if getattr(self, "_owned", True):
+                load().vdbedt_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -370,9 +387,89 @@ def kernel_launches() -> int:
 
 
 def global_batched(maps):
+    """vdbedt_global_batched over Map objects (one launch per step when they are one Batch's grids)."""
     lib = load()
     arr = (ctypes.c_void_p * len(maps))(*[m.handle for m in maps])
     _check(lib.vdbedt_global_batched(arr, len(maps)), "vdbedt_global_batched")
+
+
+class Batch:
+    """k grids of uneven size created together (vdbedt_batch_create); maps[i] is grid i as a Map.
+    set_occupancy_dense(grids) and global_() run each step once for all grids."""
+
+    def __init__(self, dims_xyz, dmax: int, voxel_size: float = 0.1, device: int = 0, stream=None):
+        lib = load()
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.Stream(device)
+        self.device, self.stream, self.dmax = device, stream, dmax
+        k = len(dims_xyz)
+        cfgs = (Config * k)(*[Config(int(nx), int(ny), int(nz), int(dmax), voxel_size, device,
+                                     ctypes.c_void_p(stream.cuda_stream), 0, 0) for nx, ny, nz in dims_xyz])
+        b = ctypes.c_void_p()
+        st = lib.vdbedt_batch_create(cfgs, k, ctypes.byref(b))
+        if st != 0:
+            raise VdbedtError(st, "vdbedt_batch_create", (lib.vdbedt_batch_last_error(None) or b"").decode())
+        self._b = b
+        self.maps = []
+        for i, (nx, ny, nz) in enumerate(dims_xyz):
+            h = ctypes.c_void_p()
+            self._chk(lib.vdbedt_batch_map(b, i, ctypes.byref(h)), "vdbedt_batch_map")
+            self.maps.append(Map(int(nx), int(ny), int(nz), dmax, voxel_size, device, stream, _borrow=h))
+
+    def _chk(self, status, where):
+        if status != 0:
+            msg = load().vdbedt_batch_last_error(self._b)
+            raise VdbedtError(status, where, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            for m in self.maps:
+                m._h = None
+            load().vdbedt_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.maps)
+
+    def set_occupancy_dense(self, grids):
+        """grids[i]: grid i's occupancy [nz, ny, nx]; all numpy arrays (host) or all CUDA tensors."""
+        lib = load()
+        k = len(self.maps)
+        if all(isinstance(g, np.ndarray) for g in grids):
+            keep = [np.ascontiguousarray(g, dtype=np.uint8) for g in grids]
+            arr = (ctypes.c_void_p * k)(*[_ptr_host(g) for g in keep])
+            self._chk(lib.vdbedt_batch_set_occupancy_dense(self._b, arr, 0), "vdbedt_batch_set_occupancy_dense")
+            return
+        torch = _torch()
+        keep = [g.to(torch.uint8).contiguous() for g in grids]
+        self.maps[0]._enter(*keep)
+        arr = (ctypes.c_void_p * k)(*[g.data_ptr() for g in keep])
+        self._chk(lib.vdbedt_batch_set_occupancy_dense(self._b, arr, 1), "vdbedt_batch_set_occupancy_dense")
+
+    def global_(self):
+        self._chk(load().vdbedt_batch_global(self._b), "vdbedt_batch_global")
+
+    def set_tuning(self, x_run: int = 0, y_run: int = 0, z_run: int = 0, variant: int = 0):
+        t = Tuning(x_run, y_run, z_run, variant)
+        self._chk(load().vdbedt_batch_set_tuning(self._b, ctypes.byref(t)), "vdbedt_batch_set_tuning")
+
+    def synchronize(self):
+        self._chk(load().vdbedt_batch_synchronize(self._b), "vdbedt_batch_synchronize")
+
+    def set_profiling(self, on: bool = True):
+        self._chk(load().vdbedt_batch_set_profiling(self._b, int(on)), "vdbedt_batch_set_profiling")
+
+    def phase_times(self) -> dict:
+        pt = PhaseTimes()
+        self._chk(load().vdbedt_batch_get_phase_times(self._b, ctypes.byref(pt)), "vdbedt_batch_get_phase_times")
+        return {k: getattr(pt, k) for k, _ in PhaseTimes._fields_}
 
 
 def _make_clearance_fn():
