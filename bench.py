@@ -12,8 +12,9 @@ Rows reported beside the headline: roofline of the dominant kernel and of the wh
 oracle on the host cores (bounded sample), the end-to-end number through the C ABI with host
 buffers, clocks sampled during the timed region, and the library's kernel-launch count; then the
 clearance cost (queries/s, forward and forward + backward, 8192 x 128 points in free space) on
-the same field, and the incremental update along 300 lidar frames (ms/frame of the CUDA-graph
-replay and of the eager calls, against the global transform of the final occupancy).
+the same field; the incremental update along 300 lidar frames (ms/frame of the CUDA-graph
+replay and of the eager calls, against the global transform of the final occupancy); and the
+batched transform of 96 maps of uneven size (one batch against 96 single handles).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload tunnel|bernoulli64]
 """
@@ -58,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-incremental", action="store_true")
     ap.add_argument("--no-clearance", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--frames", type=int, default=300, help="lidar frames of the incremental measurement")
     ap.add_argument("--variant", type=int, default=0, help="pass variant (0 automatic; see vdbedt_set_tuning)")
     ap.add_argument("--x-run", type=int, default=0)
@@ -290,6 +292,78 @@ def bench_clearance(V, torch, m, occ, stream, reps=20):
             "hinge_active_rule": "points with a nonzero gradient (d < tau and a nonzero distance gradient)"}
 
 
+def bench_batched(V, torch, stream, flush, steps=5, warmup=3):
+    """96 maps of uneven size (cubes of log-uniform side 32..512, Bernoulli(0.01..0.05) plus up to
+    20 solid boxes, dmax 24, seed 7) from dense device grids: the batch (each step launched once
+    for all maps) against the same maps as 96 single handles (every step launched per map)."""
+    import workloads as W
+    k, dmax, seed = 96, 24, 7
+    grids_h = [W.batched_map(seed, i) for i in range(k)]
+    dims = [(g.shape[2], g.shape[1], g.shape[0]) for g in grids_h]
+    grids = [torch.from_numpy(g).cuda() for g in grids_h]
+    del grids_h
+    voxels = sum(int(g.numel()) for g in grids)
+    b = V.Batch(dims, dmax, stream=stream)
+    singles = [V.Map(nx, ny, nz, dmax, stream=stream) for nx, ny, nz in dims]
+
+    def run_batch():
+        b.set_occupancy_dense(grids)
+        b.global_()
+
+    def run_singles():
+        for m, g in zip(singles, grids):
+            m.set_occupancy_dense(g)
+            m.global_()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        ms = []
+        l0 = V.kernel_launches()
+        for i in range(steps):
+            flush.fill_(i & 255)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            e.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(e))
+        return statistics.median(ms), (V.kernel_launches() - l0) / steps
+
+    batch_ms, batch_launches = timed(run_batch)
+    single_ms, single_launches = timed(run_singles)
+    b.set_profiling(True)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    b.set_occupancy_dense(grids)
+    a1.record(stream)
+    b.global_()
+    phases = b.phase_times()
+    dense_ms = a0.elapsed_time(a1)
+    b.set_profiling(False)
+    same = True
+    active = 0
+    for i in range(k):
+        a = b.maps[i].export_dense(on_device=True)
+        c = singles[i].export_dense(on_device=True)
+        same &= bool(torch.equal(a, c))
+        active += b.maps[i].info()["finite_bricks"] * 512
+        del a, c
+    for m in singles:
+        m.close()
+    b.close()
+    return {"maps": k, "dmax": dmax, "seed": seed, "domain_voxels": voxels, "active_voxels": active,
+            "sides": {"min": min(d[0] for d in dims), "max": max(d[0] for d in dims)},
+            "step": "dense occupancy from device grids + global transform of every map",
+            "batch_ms": batch_ms, "batch_mvoxels_per_s": active / (batch_ms / 1e3) / 1e6,
+            "batch_domain_mvoxels_per_s": voxels / (batch_ms / 1e3) / 1e6, "batch_launches": batch_launches,
+            "single_handles_ms": single_ms, "single_handles_mvoxels_per_s": active / (single_ms / 1e3) / 1e6,
+            "single_handles_launches": single_launches, "single_over_batch": single_ms / batch_ms,
+            "batch_phases_ms": {"reset_and_dense_ingest": dense_ms, "activation": phases["activation_ms"], "items": phases["items_ms"],
+                                "x": phases["x_ms"], "y_and_z": phases["z_ms"]},
+            "batch_equals_single_handles": same, "l2": "flushed between timed steps (untimed)"}
+
+
 def cpu_baseline(occ, dmax, budget_s=12.0):
     """The CPU oracle (Eq. 1 factorised, OpenMP on all host cores) on a z-slab of the workload."""
     import oracle as O
@@ -499,6 +573,8 @@ def main():
 
     if wl["kind"] == "tunnel" and not args.no_clearance:
         line["clearance"] = bench_clearance(V, torch, m, occ, stream)
+    if wl["kind"] == "tunnel" and not args.no_batched:
+        line["batched"] = bench_batched(V, torch, stream, flush)
     if wl["kind"] == "tunnel" and not args.no_incremental:
         line["incremental"] = bench_incremental(V, torch, wl, occ, stream, flush, args.frames)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -43,6 +43,7 @@ struct vdbedt_map {
   int32_t* d_invalid = nullptr;
   int32_t* h_pinned = nullptr;  // pinned host words for small readbacks
   Scratch scr;
+  Scratch vlast;  // per-voxel last-record table of the ordered ingest
   Scratch io;  // host-input staging on the device
   Items items{};
   int32_t* changed = nullptr;
@@ -201,7 +202,7 @@ vdbedt_status do_global(vdbedt_map* h) {
   mark(h, 0);
   CK(h, cudaMemsetAsync(h->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), h->st), "memset");
   if (h->stage_n > 0) {
-    CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, nullptr, h->scr, h->st),
+    CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, nullptr, h->scr, h->vlast, h->st),
        "ingest");
     clear_stage(h);
   }
@@ -373,6 +374,7 @@ void destroy_impl(vdbedt_map* h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->stage) cudaFree(h->stage);
   if (h->scr.buf) cudaFree(h->scr.buf);
+  if (h->vlast.buf) cudaFree(h->vlast.buf);
   if (h->io.buf) cudaFree(h->io.buf);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (int i = 0; i < 7; ++i)
@@ -437,7 +439,7 @@ vdbedt_status vdbedt_set_occupancy_counted(vdbedt_handle h, const int32_t* xyz, 
   DeviceGuard guard(h->device);
   s = ensure_stage(h, n_max);
   if (s) return s;
-  CK(h, reserve_ingest(h->g, n_max, h->scr), "ingest scratch");
+  CK(h, reserve_ingest(h->g, n_max, h->scr, h->vlast, h->st), "ingest scratch");
   CK(h, launch_pack_records(xyz, occ, n_max, n_dev, h->d_count, h->g.nx, h->g.ny, h->g.nz, h->stage, nullptr,
                               h->g.counters, h->st),
      "pack");
@@ -498,7 +500,7 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     mark(h, 0);
     CK(h, launch_begin_update(h->g, h->st), "begin update");
     if (h->stage_n > 0) {
-      CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->scr, h->st),
+      CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->scr, h->vlast, h->st),
          "ingest");
       clear_stage(h);
     }
@@ -636,7 +638,8 @@ vdbedt_status vdbedt_get_info(vdbedt_handle h, vdbedt_info* info) {
   info->finite_bricks = fin;
   info->capacity_bricks = h->g.cap;
   info->nodes = h->h_pinned[C_NNODES];
-  info->device_bytes = (int64_t)(h->device_bytes + h->scr.bytes + h->io.bytes + sizeof(rec_t) * h->stage_cap);
+  info->device_bytes =
+      (int64_t)(h->device_bytes + h->scr.bytes + h->vlast.bytes + h->io.bytes + sizeof(rec_t) * h->stage_cap);
   info->R = h->g.R;
   info->error_bits = h->h_pinned[C_ERR];
   return VDBEDT_OK;
@@ -763,7 +766,7 @@ vdbedt_status batch_global(vdbedt_batch* b) {
   for (vdbedt_map* m : b->maps) {
     if (m->stage_n <= 0) continue;
     BCK(b, cudaMemsetAsync(m->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), b->st), "memset");
-    BCK(b, launch_ingest_records(m->g, m->stage, m->stage_n, stage_count(m), false, nullptr, m->scr, b->st), "ingest");
+    BCK(b, launch_ingest_records(m->g, m->stage, m->stage_n, stage_count(m), false, nullptr, m->scr, m->vlast, b->st), "ingest");
     clear_stage(m);
   }
   bmark(b, 1);

@@ -118,26 +118,6 @@ __device__ void init_brick(const GridView& g, int slot, int node, int bx, int by
   g.bepoch[slot] = 0;
 }
 
-// Claim the child entry of brick (bx,by,bz) in `node` and give it a pool slot (concurrent
-// callers may race for the same brick: one wins).  Returns the slot, or -1 on overflow / lost race.
-__device__ int claim_brick(const GridView& g, int node, int bx, int by, int bz, bool init_fields, bool* created) {
-  int* e = &g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
-  int cur = *e;
-  *created = false;
-  if (cur >= 0) return cur;
-  if (cur == kClaiming) return -1;
-  if (atomicCAS(e, kNoSlot, kClaiming) != kNoSlot) return -1;
-  int slot = atomicAdd(&g.counters[C_NBRICKS], 1);
-  if (slot >= g.cap) {
-    set_error(g, kErrOverflow);
-    return -1;  // entry stays "claiming": reads treat it as absent
-  }
-  init_brick(g, slot, node, bx, by, bz, init_fields);
-  atomicExch(e, slot);  // brick data is read by later kernels only: the kernel boundary orders it
-  *created = true;
-  return slot;
-}
-
 __device__ __forceinline__ bool brick_has_obstacle(const GridView& g, int s) {
   const ulonglong2* w = reinterpret_cast<const ulonglong2*>(g.occ + (size_t)s * 8);
   ulonglong2 a = w[0], b = w[1], c = w[2], d = w[3];
@@ -360,47 +340,49 @@ __global__ void k_apply_set_only(GridView g, const rec_t* __restrict__ rec, int6
   }
 }
 
-// (voxel key, record index) for the ordered path: voxel key = slot * 512 + voxel in brick.
-__global__ void k_rec_voxel_keys(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
-                                 bool force, uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
-  const bool on = force || g.counters[C_HAS_ZERO];
+// Ordered path: the last record of each voxel decides its bit.  vlast holds, per voxel of the
+// pool (slot * 512 + voxel in brick), the highest index of a record for it (-1 when none): the
+// first kernel raises it with atomicMax, the second applies each voxel's winning record and puts
+// the entry back to -1, so vlast is all -1 between ingests.  Both run only when some record
+// clears a voxel, or when flips are tracked.
+__device__ __forceinline__ int64_t rec_voxel(const GridView& g, rec_t packed) {
+  const int4 r = unpack_rec(packed);
+  if (!rec_valid(g, r)) return -1;
+  const int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
+  if (s < 0) return -1;
+  return (int64_t)s * 512 + ((r.x & 7) + 8 * (r.y & 7) + 64 * (r.z & 7));
+}
+
+__global__ void k_rec_last(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev, bool force,
+                           int32_t* __restrict__ vlast) {
+  if (!force && !g.counters[C_HAS_ZERO]) return;
   const int64_t n = rec_count(n_max, n_dev);
-  if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_RECORDS] = on ? (int32_t)n : 0;
-  if (!on) return;
   GRID_STRIDE(i, n) {
     if (i < n) {
-      uint32_t key = 0xFFFFFFFFu;
-      int4 r = unpack_rec(rec[i]);
-      if (rec_valid(g, r)) {
-        int s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
-        if (s >= 0) key = (uint32_t)s * 512u + (uint32_t)((r.x & 7) + 8 * (r.y & 7) + 64 * (r.z & 7));
-      }
-      keys[i] = key;
-      idx[i] = (uint32_t)i;
+      const int64_t key = rec_voxel(g, rec[i]);
+      if (key >= 0) atomicMax(&vlast[key], (int)i);
     }
   }
 }
 
-// The last record of each voxel decides its bit.  Flips are counted; with `track` the brick is
-// appended once per epoch to the changed list.
-__global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, const uint32_t* __restrict__ keys,
-                             const uint32_t* __restrict__ idx, int64_t n_max, bool force, bool track,
-                             int32_t* __restrict__ changed) {
+// Flips are counted; with `track` the brick is appended once per epoch to the changed list.
+__global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
+                             bool force, bool track, int32_t* __restrict__ vlast, int32_t* __restrict__ changed) {
   if (!force && !g.counters[C_HAS_ZERO]) return;
-  const int64_t n = min(n_max, (int64_t)g.counters[C_RECORDS]);  // set by k_rec_voxel_keys
+  const int64_t n = rec_count(n_max, n_dev);
   const int epoch = g.counters[C_EPOCH];
   GRID_STRIDE(j, n) {
     bool flip = false;
     if (j < n) {
-      uint32_t k = keys[j];
-      const uint32_t lim = (uint32_t)g.cap * 512u;
-      if (k < lim && (j + 1 == n || keys[j + 1] != k)) {
-        int4 r = unpack_rec(rec[idx[j]]);
-        int s = (int)(k >> 9), v = (int)(k & 511);
-        unsigned long long bit = 1ull << (v & 63);
+      const rec_t packed = rec[j];
+      const int64_t key = rec_voxel(g, packed);
+      if (key >= 0 && vlast[key] == (int)j) {
+        vlast[key] = -1;
+        const int s = (int)(key >> 9), v = (int)(key & 511);
+        const unsigned long long bit = 1ull << (v & 63);
         unsigned long long* word = &g.occ[(size_t)s * 8 + (v >> 6)];
-        bool cur = (*word & bit) != 0ull;
-        if (cur != (r.w == 1)) {
+        const bool cur = (*word & bit) != 0ull;
+        if (cur != ((packed >> 63) != 0ull)) {
           atomicXor(word, bit);
           flip = true;
           if (track && atomicExch(&g.bepoch[s], epoch) != epoch) {
@@ -416,46 +398,68 @@ __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, const ui
 }
 
 // ---- dense ingest ----
-// One warp per brick of the grid: each lane reads two 8-voxel x-rows; a brick with any occupied
-// voxel is allocated and its 64-byte mask written.
+// One warp per brick of the grid: each lane builds two 8-voxel x-rows of the brick's mask (one
+// 8-byte load per row when rows are 8-byte aligned).  The grid was reset just before, so every
+// brick is claimed by exactly one warp: slots come from one atomic per block (block scan), and
+// the brick's fields are left for the global transform that always follows a dense ingest.
 template <class VS, class SRC>
-__global__ void k_ingest_dense(VS vs, SRC src) {
+__global__ void __launch_bounds__(256) k_ingest_dense(VS vs, SRC src) {
   const GridView g = vs.get();
   const uint8_t* __restrict__ grid = src.get();
   const int64_t nbr = (int64_t)g.BX * g.BY * g.BZ;
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t b = wid; b < nbr; b += nw) {
-    int bx = (int)(b % g.BX), by = (int)((b / g.BX) % g.BY), bz = (int)(b / ((int64_t)g.BX * g.BY));
-    uint8_t rows[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const bool vec = (g.nx % 8) == 0 && (reinterpret_cast<uintptr_t>(grid) & 7u) == 0;
+  for (int64_t base = (int64_t)blockIdx.x * nwarps; base < nbr; base += (int64_t)gridDim.x * nwarps) {
+    const int64_t b = base + warp;
+    int bx = 0, by = 0, bz = 0;
+    uint32_t rows[2] = {0u, 0u};
+    if (b < nbr) {
+      bx = (int)(b % g.BX);
+      by = (int)((b / g.BX) % g.BY);
+      bz = (int)(b / ((int64_t)g.BX * g.BY));
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      int r = lane * 2 + q;  // byte index y + 8 z
-      int y = r & 7, z = r >> 3;
-      int gy = by * 8 + y, gz = bz * 8 + z;
-      uint8_t v = 0;
-      if (gy < g.ny && gz < g.nz) {
-        const uint8_t* src = grid + ((size_t)gz * g.ny + gy) * g.nx + (size_t)bx * 8;
-        int nxv = min(8, g.nx - bx * 8);
-        for (int x = 0; x < nxv; ++x) v |= (uint8_t)((src[x] != 0) << x);
+      for (int q = 0; q < 2; ++q) {
+        const int r = lane * 2 + q;  // byte index y + 8 z
+        const int gy = by * 8 + (r & 7), gz = bz * 8 + (r >> 3);
+        if (gy < g.ny && gz < g.nz) {
+          const uint8_t* row = grid + ((size_t)gz * g.ny + gy) * g.nx + (size_t)bx * 8;
+          if (vec) {
+            // bit i of the result = byte i nonzero (fold each byte onto its low bit, then gather)
+            unsigned long long w = __ldg(reinterpret_cast<const unsigned long long*>(row));
+            w |= w >> 4;
+            w |= w >> 2;
+            w |= w >> 1;
+            w &= 0x0101010101010101ull;
+            rows[q] = (uint32_t)((w * 0x0102040810204080ull) >> 56);
+          } else {
+            const int nxv = min(8, g.nx - bx * 8);
+            uint32_t v = 0u;
+            for (int x = 0; x < nxv; ++x) v |= (uint32_t)(row[x] != 0) << x;
+            rows[q] = v;
+          }
+        }
       }
-      rows[q] = v;
     }
-    bool any = __any_sync(0xffffffffu, (rows[0] | rows[1]) != 0);
-    if (!any) continue;
-    int slot = -1;
-    if (lane == 0) {
-      int node = get_or_create_node(g, (uint32_t)node_key_of(g, bx, by, bz));
-      bool created = false;
-      if (node >= 0) slot = claim_brick(g, node, bx, by, bz, true, &created);
-      if (created) atomicAdd(&g.counters[C_NEW_BRICKS], 1);
+    const bool any = __any_sync(0xffffffffu, (rows[0] | rows[1]) != 0u);  // false past the grid
+    int node = -1;
+    if (any && lane == 0) node = get_or_create_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+    node = __shfl_sync(0xffffffffu, node, 0);
+    int total = 0;
+    const int mine = block_agg_add(&g.counters[C_NBRICKS], lane == 0 && node >= 0, &total);
+    const int slot = __shfl_sync(0xffffffffu, mine, 0);
+    if (node >= 0) {
+      if (slot >= g.cap) {
+        if (lane == 0) set_error(g, kErrOverflow);
+      } else {
+        if (lane == 0) {
+          init_brick(g, slot, node, bx, by, bz, false);
+          g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] = slot;
+        }
+        __syncwarp();
+        reinterpret_cast<uint16_t*>(g.occ + (size_t)slot * 8)[lane] = (uint16_t)(rows[0] | (rows[1] << 8));
+      }
     }
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-    if (slot < 0) continue;
-    uint8_t* dst = reinterpret_cast<uint8_t*>(g.occ) + (size_t)slot * 64;
-    dst[lane * 2] = rows[0];
-    dst[lane * 2 + 1] = rows[1];
+    if (threadIdx.x == 0 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
   }
 }
 
@@ -876,13 +880,24 @@ static size_t ingest_scratch_bytes(const GridView& g, int64_t n, bool track) {
   const int64_t m = n > nbr_all ? n : nbr_all;
   const size_t nb4 = align_up((size_t)m * 4);
   const size_t dbytes = dense_bits ? align_up((size_t)nbr_all * 64) : 0;
-  return 6 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(m)) + dbytes;
+  return 4 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(m)) + dbytes;
 }
 
-cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr) {
+// The per-voxel last-record table of the ordered path: cap * 512 words, all -1 between ingests.
+static cudaError_t ensure_vlast(const GridView& g, Scratch& vl, cudaStream_t st) {
+  const size_t want = (size_t)g.cap * 512 * sizeof(int32_t);
+  if (vl.bytes >= want) return cudaSuccess;
+  cudaError_t e = ensure_scratch(vl, want);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(vl.buf, 0xFF, want, st);
+}
+
+cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const size_t a = ingest_scratch_bytes(g, n, false), b = ingest_scratch_bytes(g, n, true);
-  return ensure_scratch(scr, a > b ? a : b);
+  cudaError_t e = ensure_scratch(scr, a > b ? a : b);
+  if (e != cudaSuccess) return e;
+  return ensure_vlast(g, vl, st);
 }
 
 cudaError_t launch_begin_update(const GridView& g, cudaStream_t st) {
@@ -891,7 +906,7 @@ cudaError_t launch_begin_update(const GridView& g, cudaStream_t st) {
 }
 
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
-                                  int32_t* changed, Scratch& scr, cudaStream_t st) {
+                                  int32_t* changed, Scratch& scr, Scratch& vl, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
   const bool counting = n >= nbr_all / 4;
@@ -900,14 +915,13 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
   const size_t nb4 = align_up((size_t)m * 4);
   cudaError_t e = ensure_scratch(scr, ingest_scratch_bytes(g, n, track));
   if (e != cudaSuccess) return e;
+  e = ensure_vlast(g, vl, st);
+  if (e != cudaSuccess) return e;
+  int32_t* vlast = (int32_t*)vl.buf;
   char* p = (char*)scr.buf;
   uint32_t* ka = (uint32_t*)p;
   p += nb4;
   uint32_t* kb = (uint32_t*)p;
-  p += nb4;
-  uint32_t* va = (uint32_t*)p;
-  p += nb4;
-  uint32_t* vb = (uint32_t*)p;
   p += nb4;
   int32_t* flag = (int32_t*)p;
   p += nb4;
@@ -950,13 +964,9 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
     VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, uniq, n, track, nullptr);
     if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
   }
-  // ordered path; its element count is 0 on the device when it is not needed
-  VDB_LAUNCH(k_rec_voxel_keys, nbk, kT, 0, st, g, rec, n, n_dev, track, ka, va);
-  bool in_b = false;
-  e = radix_sort_u32(ka, kb, va, vb, n, g.counters + C_RECORDS, bits_for((uint64_t)g.cap * 512ull), rtemp, st,
-                     &in_b);
-  if (e != cudaSuccess) return e;
-  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, in_b ? kb : ka, in_b ? vb : va, n, track, track, changed);
+  // ordered path (its kernels return at once when no record clears a voxel and flips are untracked)
+  VDB_LAUNCH(k_rec_last, nbk, kT, 0, st, g, rec, n, n_dev, track, vlast);
+  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, n, n_dev, track, track, vlast, changed);
   return cudaGetLastError();
 }
 

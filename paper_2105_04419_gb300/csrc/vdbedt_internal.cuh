@@ -26,7 +26,6 @@ constexpr int kNodeBricks = kNodeB * kNodeB * kNodeB;
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 constexpr uint32_t kPending = 0xFFFFFFFFu;
 constexpr int32_t kNoSlot = -1;
-constexpr int32_t kClaiming = -2;
 
 // device error bits
 constexpr int kErrOverflow = 1;
@@ -50,7 +49,7 @@ enum Counter : int {
   C_HAS_ZERO = 10,
   C_FINITE = 11,
   C_OBST = 12,
-  C_RECORDS = 13,
+  C_SPARE13 = 13,
   C_EPOCH = 14,  // incremental update epoch (run and brick dedupe marks)
   C_SPARE = 15,
   C_NUM = 16
@@ -254,10 +253,12 @@ cudaError_t ensure_scratch(Scratch& s, size_t bytes);
 
 cudaError_t launch_reset(const GridView& g, cudaStream_t st);
 // n records at rec; with n_dev (nullable) only the first *n_dev of them (clamped to [0, n]).
+// scr: sort / scan scratch; vl: the per-voxel last-record table (allocated and set to -1 on first
+// use, cap * 512 words).
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
-                                  int32_t* changed, Scratch& scr, cudaStream_t st);
-// size the ingest scratch for up to n records, either form
-cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr);
+                                  int32_t* changed, Scratch& scr, Scratch& vl, cudaStream_t st);
+// size the ingest scratch and the last-record table for up to n records, either form
+cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, cudaStream_t st);
 // clear the per-update counters and advance the device-side update epoch
 cudaError_t launch_begin_update(const GridView& g, cudaStream_t st);
 cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st);
