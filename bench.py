@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-incremental", action="store_true")
     ap.add_argument("--no-clearance", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default work-item tuning")
     ap.add_argument("--frames", type=int, default=300, help="lidar frames of the incremental measurement")
     ap.add_argument("--variant", type=int, default=0, help="pass variant (0 automatic; see vdbedt_set_tuning)")
     ap.add_argument("--x-run", type=int, default=0)
@@ -151,6 +152,18 @@ def traffic_for(kernel: str):
     except Exception:
         pass
     return None
+
+
+def max_over_ranks(x: float) -> float:
+    """Largest value of x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_summary(v):
@@ -292,7 +305,7 @@ def bench_clearance(V, torch, m, occ, stream, reps=20):
             "hinge_active_rule": "points with a nonzero gradient (d < tau and a nonzero distance gradient)"}
 
 
-def bench_batched(V, torch, stream, flush, steps=5, warmup=3):
+def bench_batched(V, torch, stream, flush, autotuned=True, steps=5, warmup=3):
     """96 maps of uneven size (cubes of log-uniform side 32..512, Bernoulli(0.01..0.05) plus up to
     20 solid boxes, dmax 24, seed 7) from dense device grids: the batch (each step launched once
     for all maps) against the same maps as 96 single handles (every step launched per map)."""
@@ -305,6 +318,13 @@ def bench_batched(V, torch, stream, flush, steps=5, warmup=3):
     voxels = sum(int(g.numel()) for g in grids)
     b = V.Batch(dims, dmax, stream=stream)
     singles = [V.Map(nx, ny, nz, dmax, stream=stream) for nx, ny, nz in dims]
+    b.set_occupancy_dense(grids)
+    tuning = {"source": "default"}
+    if autotuned:
+        from paper_2105_04419_gb300.autotune import autotune
+        tuning = autotune(b)  # untimed
+        for m in singles:
+            m.set_tuning(tuning["x_run"], tuning["y_run"], tuning["z_run"], tuning["variant"])
 
     def run_batch():
         b.set_occupancy_dense(grids)
@@ -361,7 +381,8 @@ def bench_batched(V, torch, stream, flush, steps=5, warmup=3):
             "single_handles_launches": single_launches, "single_over_batch": single_ms / batch_ms,
             "batch_phases_ms": {"reset_and_dense_ingest": dense_ms, "activation": phases["activation_ms"], "items": phases["items_ms"],
                                 "x": phases["x_ms"], "y_and_z": phases["z_ms"]},
-            "batch_equals_single_handles": same, "l2": "flushed between timed steps (untimed)"}
+            "batch_equals_single_handles": same, "l2": "flushed between timed steps (untimed)",
+            "tuning": {k: v for k, v in tuning.items() if k != "key"}}
 
 
 def cpu_baseline(occ, dmax, budget_s=12.0):
@@ -467,8 +488,15 @@ def main():
     xyz = torch.from_numpy(xyz_h).cuda()
     ones = torch.from_numpy(ones_h).cuda()
     m = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    tuning = {"source": "default"}
     if args.variant or args.x_run or args.y_run or args.z_run:
         m.set_tuning(args.x_run, args.y_run, args.z_run, args.variant)
+        tuning = {"source": "command line", "x_run": args.x_run, "y_run": args.y_run, "z_run": args.z_run,
+                  "variant": args.variant}
+    elif not args.no_autotune:
+        from paper_2105_04419_gb300.autotune import autotune
+        m.set_occupancy(xyz, ones)
+        tuning = autotune(m)  # untimed; leaves the chosen tuning set
 
     def step():
         m.reset()
@@ -507,11 +535,7 @@ def main():
     clocks = sampler.stop()
     m.set_profiling(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms))
     value = active * world / (ms / 1e3) / 1e6
     ph = {k: statistics.mean(v) for k, v in phases.items()}
 
@@ -542,7 +566,8 @@ def main():
                        "active_bricks": info["finite_bricks"], "allocated_bricks": allocated,
                        "obstacle_bricks": info["obstacle_bricks"], "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
-                       "step": "reset + stage device records + global transform"},
+                       "step": "reset + stage device records + global transform",
+                       "tuning": {k: v for k, v in tuning.items() if k != "key"}},
             "phases_ms": ph, "roofline": roofline, "roofline_step": roof_step, "gpu_launches": launches,
             "clocks": clocks}
 
@@ -562,11 +587,7 @@ def main():
             inf2 = m.info()
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
         e2e_ms = e2e_ms[max(3, args.warmup):]
-        ems = statistics.mean(e2e_ms)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(statistics.mean(e2e_ms))
         line["e2e"] = {"value": inf2["finite_bricks"] * 512 * world / (ems / 1e3) / 1e6, "unit": "Mvoxels/s",
                        "ms_per_step": ems, "host_buffers": "pinned", "h2d_bytes_per_step": int(n * 13),
                        "d2h_bytes_per_step": int(4 * 16 + 4 * inf2["allocated_bricks"])}
@@ -574,7 +595,7 @@ def main():
     if wl["kind"] == "tunnel" and not args.no_clearance:
         line["clearance"] = bench_clearance(V, torch, m, occ, stream)
     if wl["kind"] == "tunnel" and not args.no_batched:
-        line["batched"] = bench_batched(V, torch, stream, flush)
+        line["batched"] = bench_batched(V, torch, stream, flush, autotuned=not args.no_autotune)
     if wl["kind"] == "tunnel" and not args.no_incremental:
         line["incremental"] = bench_incremental(V, torch, wl, occ, stream, flush, args.frames)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,0 +1,131 @@
+"""Autotuner of the transform passes' work-item shapes.
+
+The brick is fixed at 8^3 voxels (the storage layout); what is tuned is the tile each pass works
+on -- the run of bricks one work item covers along the pass axis (4, 8 or 16 bricks: longer runs
+re-read less halo per output brick but give fewer, larger items) -- and the window variant of the
+in-plane and z passes (1: full window; 3: window with early exit and skips of windows without
+finite input).  Every choice computes the same exact field; only the time differs.
+
+The tuner times the map's (or batch's) own global transform under each candidate with the
+library's phase events, picks per axis the fastest run, and stores the choice in a JSON cache keyed
+by GPU, brick radius and workload size, so that later maps of the same kind reuse it without
+timing.  The passes are independent per axis, so 2 variants x 3 runs = 6 timed configurations
+cover the 54 combinations.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+import threading
+
+RUNS = (4, 8, 16)
+VARIANTS = (1, 3)
+_lock = threading.Lock()
+
+
+def default_cache_path() -> str:
+    base = os.environ.get("VDBEDT_TUNING_CACHE")
+    if base:
+        return base
+    root = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(root, "vdbedt", "tuning.json")
+
+
+def _round_sig(v: int, digits: int = 2) -> int:
+    if v <= 0:
+        return 0
+    s = len(str(int(v)))
+    q = 10 ** max(0, s - digits)
+    return int(round(v / q) * q)
+
+
+def signature(target) -> str:
+    """Cache key: GPU name, brick radius R, grid count and allocated bricks (2 significant
+    digits) of a Map or Batch after a transform."""
+    import torch
+    maps = getattr(target, "maps", None) or [target]
+    dev = torch.cuda.get_device_name(maps[0].device)
+    infos = [m.info() for m in maps]
+    bricks = sum(i["allocated_bricks"] for i in infos)
+    return f"{dev}|R={infos[0]['R']}|grids={len(maps)}|bricks~{_round_sig(bricks)}"
+
+
+def choose(table: dict, joint_yz: bool = False) -> dict:
+    """Pick the tuning from timed phases.  table[(variant, run)] = {"x_ms", "y_ms", "z_ms"}
+    (medians).  x does not depend on the variant; the variant is the one whose best y + z is
+    lowest; then y and z each take their fastest run under it (jointly when the phases are timed
+    together, as for batches)."""
+    x_run = min(RUNS, key=lambda r: min(table[(v, r)]["x_ms"] for v in VARIANTS))
+
+    def yz_best(v):
+        if joint_yz:
+            r = min(RUNS, key=lambda r: table[(v, r)]["z_ms"])
+            return table[(v, r)]["z_ms"], r, r
+        ry = min(RUNS, key=lambda r: table[(v, r)]["y_ms"])
+        rz = min(RUNS, key=lambda r: table[(v, r)]["z_ms"])
+        return table[(v, ry)]["y_ms"] + table[(v, rz)]["z_ms"], ry, rz
+
+    variant = min(VARIANTS, key=lambda v: yz_best(v)[0])
+    _, y_run, z_run = yz_best(variant)
+    return {"x_run": x_run, "y_run": y_run, "z_run": z_run, "variant": variant}
+
+
+def _load(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path: str, key: str, value: dict) -> None:
+    with _lock:
+        data = _load(path)
+        data[key] = value
+        os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
+def measure(target, reps: int = 5) -> dict:
+    """Median phase times of target.global_() under each (variant, run) candidate."""
+    table = {}
+    target.set_profiling(True)
+    try:
+        for v in VARIANTS:
+            for r in RUNS:
+                target.set_tuning(r, r, r, v)
+                target.global_()  # warm-up (also applies any staged records)
+                samples = []
+                for _ in range(reps):
+                    target.global_()
+                    samples.append(target.phase_times())
+                table[(v, r)] = {k: statistics.median(s[k] for s in samples) for k in ("x_ms", "y_ms", "z_ms")}
+    finally:
+        target.set_profiling(False)
+    return table
+
+
+def autotune(target, reps: int = 5, cache_path: str | None = None, use_cache: bool = True) -> dict:
+    """Tune a Map or Batch on its current occupancy; applies and returns the tuning
+    {"x_run", "y_run", "z_run", "variant", "source": "cache" | "measured"}.  The field is left
+    recomputed (global transform) under the chosen tuning."""
+    path = cache_path or default_cache_path()
+    target.global_()
+    key = signature(target)
+    if use_cache:
+        hit = _load(path).get(key)
+        if hit:
+            t = {k: int(hit[k]) for k in ("x_run", "y_run", "z_run", "variant")}
+            target.set_tuning(**t)
+            target.global_()
+            return dict(t, source="cache", key=key)
+    table = measure(target, reps)
+    t = choose(table, joint_yz=hasattr(target, "maps"))
+    target.set_tuning(**t)
+    target.global_()
+    _store(path, key, dict(t, table={f"v{v}_r{r}": ms for (v, r), ms in table.items()}))
+    return dict(t, source="measured", key=key)
