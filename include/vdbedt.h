@@ -158,7 +158,8 @@ vdbedt_status vdbedt_clearance_backward(vdbedt_handle h, const float* pts, int64
 /* Tuning of the transform passes (0 = automatic for any field).
  *   x_run, y_run, z_run: bricks per work item of the pass along that axis (4, 8 or 16);
  *   variant: 0 automatic, 1 full windowed minimum, 3 windowed minimum with early exit and skips
- *            (the default; both exact).  Other values are EINVAL. */
+ *            (the default; both exact); adding 4 (5 or 7) runs the x pass with plain loads instead
+ *            of the bulk-copy ring.  Other values are EINVAL. */
 typedef struct {
   int32_t x_run, y_run, z_run, variant;
 } vdbedt_tuning;

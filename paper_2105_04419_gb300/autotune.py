@@ -9,8 +9,8 @@ finite input).  Every choice computes the same exact field; only the time differ
 The tuner times the map's (or batch's) own global transform under each candidate with the
 library's phase events, picks per axis the fastest run, and stores the choice in a JSON cache keyed
 by GPU, brick radius and workload size, so that later maps of the same kind reuse it without
-timing.  The passes are independent per axis, so 2 variants x 3 runs = 6 timed configurations
-cover the 54 combinations.
+timing.  The passes are independent per axis, so 3 variants x 3 runs = 9 timed configurations
+cover every combination (the x pass also has two kernels: the bulk-copy ring and plain loads).
 """
 from __future__ import annotations
 
@@ -20,7 +20,9 @@ import statistics
 import threading
 
 RUNS = (4, 8, 16)
-VARIANTS = (1, 3)
+# 1: full window; 3: pruned window; 7: pruned window with the x pass on plain loads (+4)
+VARIANTS = (1, 3, 7)
+X_DIRECT = 4
 _lock = threading.Lock()
 
 
@@ -53,10 +55,11 @@ def signature(target) -> str:
 
 def choose(table: dict, joint_yz: bool = False) -> dict:
     """Pick the tuning from timed phases.  table[(variant, run)] = {"x_ms", "y_ms", "z_ms"}
-    (medians).  x does not depend on the variant; the variant is the one whose best y + z is
-    lowest; then y and z each take their fastest run under it (jointly when the phases are timed
-    together, as for batches)."""
-    x_run = min(RUNS, key=lambda r: min(table[(v, r)]["x_ms"] for v in VARIANTS))
+    (medians).  The x pass takes its fastest (kernel, run) over every candidate (its time depends
+    only on the X_DIRECT bit of the variant and the run); the window variant is the one whose best
+    y + z is lowest; then y and z each take their fastest run under it (jointly when the phases are
+    timed together, as for batches)."""
+    xv, x_run = min(((v, r) for v in VARIANTS for r in RUNS), key=lambda vr: table[vr]["x_ms"])
 
     def yz_best(v):
         if joint_yz:
@@ -66,8 +69,9 @@ def choose(table: dict, joint_yz: bool = False) -> dict:
         rz = min(RUNS, key=lambda r: table[(v, r)]["z_ms"])
         return table[(v, ry)]["y_ms"] + table[(v, rz)]["z_ms"], ry, rz
 
-    variant = min(VARIANTS, key=lambda v: yz_best(v)[0])
-    _, y_run, z_run = yz_best(variant)
+    window = min(VARIANTS, key=lambda v: yz_best(v)[0])
+    _, y_run, z_run = yz_best(window)
+    variant = (window & 3) | (xv & X_DIRECT)
     return {"x_run": x_run, "y_run": y_run, "z_run": z_run, "variant": variant}
 
 

@@ -600,7 +600,7 @@ vdbedt_status vdbedt_set_tuning(vdbedt_handle h, const vdbedt_tuning* t) {
   if (!t) return fail(h, VDBEDT_EINVAL, "null tuning");
   auto ok_run = [](int r) { return r == 0 || r == 4 || r == 8 || r == 16; };
   if (!ok_run(t->x_run) || !ok_run(t->y_run) || !ok_run(t->z_run) ||
-      !(t->variant == 0 || t->variant == 1 || t->variant == 3))
+      !(t->variant == 0 || t->variant == 1 || t->variant == 3 || t->variant == 5 || t->variant == 7))
     return fail(h, VDBEDT_EINVAL, "bad tuning");
   const Tuning d;
   h->tune.run[0] = t->x_run ? t->x_run : d.run[0];

@@ -202,7 +202,8 @@ __global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int6
 // the grid (64 B per brick; lanes of one x-row merged by a segmented OR), so that allocation can copy
 // each new brick's mask whole instead of a second pass over the records.
 __global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
-                                     int32_t* __restrict__ flag, unsigned long long* __restrict__ dbits) {
+                                     int32_t* __restrict__ flag, unsigned long long* __restrict__ dbits,
+                                     int32_t* __restrict__ nflag) {
   const int lane = threadIdx.x & 31;
   const int64_t n = rec_count(n_max, n_dev);
   GRID_STRIDE(i, n) {
@@ -215,7 +216,11 @@ __global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, 
         bad = true;
       } else if (r.w == 1) {
         int64_t lb = (r.x >> 3) + (int64_t)g.BX * ((r.y >> 3) + (int64_t)g.BY * (r.z >> 3));
-        if (!flag[lb]) flag[lb] = 1;
+        if (!flag[lb]) {
+          flag[lb] = 1;
+          const int nk = node_key_of(g, r.x >> 3, r.y >> 3, r.z >> 3);
+          if (!nflag[nk]) nflag[nk] = 1;
+        }
         if (dbits) {
           word = dbits + lb * 8 + (r.z & 7);
           bits = 1ull << ((r.x & 7) + 8 * (r.y & 7));
@@ -236,6 +241,46 @@ __global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, 
     }
     if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
     if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+  }
+}
+
+// Nodes of the obstacle bricks, created before the bricks so that no brick allocation waits on a
+// node insertion in progress: one thread per flagged node key absent from the table; indices come
+// from one atomic per block, and each key (inserted by exactly one thread) claims an empty hash
+// slot with its final word.  Later kernels read the nodes (the kernel boundary orders them).
+__global__ void k_create_flagged_nodes(GridView g, int32_t* __restrict__ nflag, int64_t nkeys) {
+  GRID_STRIDE(k, nkeys) {
+    bool need = false;
+    if (k < nkeys && nflag[k]) {
+      nflag[k] = 0;
+      need = find_node(g, (uint32_t)k) < 0;
+    }
+    const int idx = block_agg_add(&g.counters[C_NNODES], need, nullptr);
+    if (need) {
+      if (idx >= g.node_cap) {
+        set_error(g, kErrNodeOverflow);
+      } else {
+        g.node_key[idx] = (int32_t)k;
+        const unsigned long long word = ((unsigned long long)(uint32_t)k << 32) | (uint32_t)idx;
+        uint32_t h = hash32((uint32_t)k) & g.hmask;
+        bool placed = false;
+        for (uint32_t probe = 0; probe <= g.hmask && !placed; ++probe) {
+          placed = atomicCAS(&g.hslots[h], ~0ull, word) == ~0ull;
+          h = (h + 1) & g.hmask;
+        }
+        if (!placed) set_error(g, kErrNodeOverflow);
+      }
+    }
+  }
+}
+
+// Node flags of the unique brick keys (radix path).
+__global__ void k_flag_key_nodes(GridView g, const uint32_t* __restrict__ uniq, int64_t n, int32_t* __restrict__ nflag) {
+  const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], n);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t lb = uniq[j];
+    const int bx = (int)(lb % (uint32_t)g.BX), rest = (int)(lb / (uint32_t)g.BX);
+    nflag[node_key_of(g, bx, rest % g.BY, rest / g.BY)] = 1;
   }
 }
 
@@ -879,8 +924,10 @@ static size_t ingest_scratch_bytes(const GridView& g, int64_t n, bool track) {
   const bool dense_bits = counting && !track;
   const int64_t m = n > nbr_all ? n : nbr_all;
   const size_t nb4 = align_up((size_t)m * 4);
+  const size_t nkeys_al = ((size_t)g.NX * g.NY * g.NZ + 63) & ~(size_t)63;
+  const size_t flags = align_up(((size_t)m + nkeys_al) * 4);  // node flags, then brick flags
   const size_t dbytes = dense_bits ? align_up((size_t)nbr_all * 64) : 0;
-  return 4 * nb4 + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(m)) + dbytes;
+  return 3 * nb4 + flags + align_up(radix_temp_bytes(n)) + align_up(scan_temp_bytes(m)) + dbytes;
 }
 
 // The per-voxel last-record table of the ordered path: cap * 512 words, all -1 between ingests.
@@ -923,8 +970,12 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
   p += nb4;
   uint32_t* kb = (uint32_t*)p;
   p += nb4;
-  int32_t* flag = (int32_t*)p;
-  p += nb4;
+  // one flag per node key (nodes are created before their bricks), then one per brick or record
+  const int64_t nkeys = (int64_t)g.NX * g.NY * g.NZ;
+  const int64_t nkeys_al = (nkeys + 63) & ~(int64_t)63;
+  int32_t* nflag = (int32_t*)p;
+  int32_t* flag = nflag + nkeys_al;
+  p += align_up(((size_t)m + (size_t)nkeys_al) * 4);
   int32_t* pos = (int32_t*)p;
   p += nb4;
   void* rtemp = p;
@@ -937,13 +988,14 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
   const uint64_t nbr = (uint64_t)nbr_all;
   if (counting) {
     // counting sort of brick keys over the grid's bricks, then compaction
-    e = cudaMemsetAsync(flag, 0, sizeof(int32_t) * nbr, st);
+    e = cudaMemsetAsync(nflag, 0, sizeof(int32_t) * (size_t)(nkeys_al + (int64_t)nbr), st);
     if (e != cudaSuccess) return e;
     if (dbits) {
       e = cudaMemsetAsync(dbits, 0, (size_t)nbr * 64, st);
       if (e != cudaSuccess) return e;
     }
-    VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, n_dev, flag, dbits);
+    VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, n_dev, flag, dbits, nflag);
+    VDB_LAUNCH(k_create_flagged_nodes, blocks_for(nkeys), kT, 0, st, g, nflag, nkeys);
     e = exclusive_scan_i32(flag, pos, (int64_t)nbr, g.counters + C_UNIQUE, stemp, st);
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, flag, pos, (int64_t)nbr, ka);
@@ -961,6 +1013,10 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
     e = exclusive_scan_i32(flag, pos, n, g.counters + C_UNIQUE, stemp, st);
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_compact_keys, nbk, kT, 0, st, sorted, flag, pos, n, uniq);
+    e = cudaMemsetAsync(nflag, 0, sizeof(int32_t) * (size_t)nkeys, st);
+    if (e != cudaSuccess) return e;
+    VDB_LAUNCH(k_flag_key_nodes, blocks_for(n), kT, 0, st, g, uniq, n, nflag);
+    VDB_LAUNCH(k_create_flagged_nodes, blocks_for(nkeys), kT, 0, st, g, nflag, nkeys);
     VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, uniq, n, track, nullptr);
     if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
   }

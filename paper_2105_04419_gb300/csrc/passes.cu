@@ -160,7 +160,25 @@ struct ColShape {
 // only the 32 line bits on either side: two funnel shifts of 32-bit words and a count of leading
 // zeros (left) and of trailing zeros (right).  Otherwise the 64-bit form covers the whole line.
 template <int R>
+__device__ __forceinline__ void x_compute_rows(const GridView& g, const uint32_t (&rows2)[2 * R + 1], int slot,
+                                               uint32_t inf2);
+
+template <int R>
 __device__ __forceinline__ void x_compute(const GridView& g, const uint8_t* masks, int slot, uint32_t inf2) {
+  constexpr int NBX = 2 * R + 1;
+  const int lane = threadIdx.x & 31;
+  const int z = lane & 7, y0 = (lane >> 3) * 2;
+  uint32_t rows2[NBX];
+#pragma unroll
+  for (int b = 0; b < NBX; ++b) rows2[b] = *reinterpret_cast<const uint16_t*>(masks + b * 64 + y0 + 8 * z);
+  x_compute_rows<R>(g, rows2, slot, inf2);
+}
+
+// The x-line computation of one brick from the lane's two mask bytes of each brick of the window
+// (rows2[b]: bits of x-rows y0 (low byte) and y0 + 1 (high byte) at z, brick bx - R + b).
+template <int R>
+__device__ __forceinline__ void x_compute_rows(const GridView& g, const uint32_t (&rows2)[2 * R + 1], int slot,
+                                               uint32_t inf2) {
   constexpr int NBX = 2 * R + 1;
   const int lane = threadIdx.x & 31;
   const int z = lane & 7, y0 = (lane >> 3) * 2;
@@ -173,7 +191,7 @@ __device__ __forceinline__ void x_compute(const GridView& g, const uint8_t* mask
       uint32_t E[2][5] = {{0u, 0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u, 0u}};
 #pragma unroll
       for (int b = 0; b < NBX; ++b) {
-        const uint32_t two = *reinterpret_cast<const uint16_t*>(masks + b * 64 + y0 + 8 * z);
+        const uint32_t two = rows2[b];
         E[0][1 + b / 4] |= (two & 0xFFu) << (8 * (b % 4));
         E[1][1 + b / 4] |= (two >> 8) << (8 * (b % 4));
       }
@@ -206,7 +224,7 @@ __device__ __forceinline__ void x_compute(const GridView& g, const uint8_t* mask
     unsigned long long lo[2] = {0ull, 0ull}, hi[2] = {0ull, 0ull};
 #pragma unroll
     for (int b = 0; b < NBX; ++b) {
-      const uint32_t two = *reinterpret_cast<const uint16_t*>(masks + b * 64 + y0 + 8 * z);
+      const uint32_t two = rows2[b];
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const unsigned long long byte = (two >> (8 * r)) & 0xFFu;
@@ -402,6 +420,37 @@ __global__ void __launch_bounds__(32 * (RUN + 1)) k_pass(GridView g, const int32
   }
 }
 
+// x pass with plain loads: one warp per output brick of the queued runs; each lane reads its two
+// mask bytes of the 2R + 1 bricks of the window straight from global memory (the masks of
+// neighbouring bricks are shared through L1 / L2) and writes its 32 bytes of g1.
+template <int R>
+__global__ void __launch_bounds__(256) k_x_direct(GridView g, const int32_t* __restrict__ islots, int max_items,
+                                                  int run) {
+  constexpr int NBX = 2 * R + 1;
+  const int nitems = min(g.items_ctr[0], max_items);
+  const int lane = threadIdx.x & 31;
+  const int z = lane & 7, y0 = (lane >> 3) * 2;
+  const __half hinf = __int2half_rn(g.INF);
+  const uint32_t inf2 = h2u(__halves2half2(hinf, hinf));
+  const int64_t total = (int64_t)nitems * run;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned char* occ = reinterpret_cast<const unsigned char*>(g.occ);
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+    const int item = (int)(w / run), j = (int)(w % run);
+    const int32_t* sl = islots + (size_t)item * kItemSlots + j;
+    const int s = lane < NBX ? __ldg(sl + lane) : -1;
+    const int slot = __shfl_sync(0xffffffffu, s, R);
+    if (slot < 0) continue;  // warp-uniform
+    uint32_t rows2[NBX];
+#pragma unroll
+    for (int b = 0; b < NBX; ++b) {
+      const int sb = __shfl_sync(0xffffffffu, s, b);
+      rows2[b] = sb >= 0 ? (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(occ + (size_t)sb * 64 + y0 + 8 * z)) : 0u;
+    }
+    x_compute_rows<R>(g, rows2, slot, inf2);
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Generic kernels (any dmax up to 181): int32 from shared memory, runtime window W = 8R.
 // ------------------------------------------------------------------------------------------------
@@ -567,6 +616,30 @@ cudaError_t pass_half_run(const GridView& g, int run, const int32_t* islots, int
   return cudaErrorInvalidValue;
 }
 
+template <int R>
+cudaError_t x_direct_r(const GridView& g, const int32_t* islots, int max_items, int run, cudaStream_t st) {
+  auto kernel = k_x_direct<R>;
+  if (max_items <= 0) return cudaSuccess;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  VDB_LAUNCH(kernel, num_sms() * per_sm, 256, 0, st, g, islots, max_items, run);
+  return cudaGetLastError();
+}
+
+cudaError_t x_direct(const GridView& g, const int32_t* islots, int max_items, int run, cudaStream_t st) {
+  switch (g.R) {
+    case 1: return x_direct_r<1>(g, islots, max_items, run, st);
+    case 2: return x_direct_r<2>(g, islots, max_items, run, st);
+    case 3: return x_direct_r<3>(g, islots, max_items, run, st);
+    case 4: return x_direct_r<4>(g, islots, max_items, run, st);
+    case 5: return x_direct_r<5>(g, islots, max_items, run, st);
+    case 6: return x_direct_r<6>(g, islots, max_items, run, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 bool half_path(const GridView& g) { return g.dmax <= 45 && g.R >= 1 && g.R <= 6; }
@@ -590,9 +663,10 @@ GridView pool_view(const GridView& g) {
 }
 
 cudaError_t launch_pass(const GridView& g, const Tuning& t, int axis, const Items& it, cudaStream_t st) {
-  const bool prune = t.variant != 1;
+  const bool prune = (t.variant & 3) != 1;
   if (half_path(g)) {
     const GridView p = pool_view(g);
+    if (axis == 0 && (t.variant & kVariantXDirect)) return x_direct(p, it.slots[0], g.item_cap, t.run[0], st);
     if (axis == 0) return pass_half_run<0>(p, t.run[0], it.slots[0], g.item_cap, st, prune);
     if (axis == 1) return pass_half_run<1>(p, t.run[1], it.slots[1], g.item_cap, st, prune);
     return pass_half_run<2>(p, t.run[2], it.slots[2], g.item_cap, st, prune);

@@ -153,7 +153,8 @@ __device__ inline int get_or_create_node(const GridView& g, uint32_t key) {
     if (k == key) {
       if ((uint32_t)w != kPending) return (int)(uint32_t)w;  // published: no atomic needed
       for (int spin = 0; spin < (1 << 22); ++spin) {
-        unsigned long long cur = atomicAdd(&g.hslots[h], 0ull);
+        // plain (volatile) reads while waiting: they do not queue behind the publishing exchange
+        unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&g.hslots[h]);
         uint32_t v = (uint32_t)cur;
         if (v != kPending) return (int)v;
         __nanosleep(64);
@@ -209,9 +210,12 @@ void note_launch();
 constexpr int kItemSlots = 32;  // slot list entries per work item (run + 2R <= 28 on the half path)
 constexpr int kBatchMax = 1024;  // grids per batch (the dense-ingest source table is a kernel parameter)
 
+// Tuning.variant: low bits 1 = full windowed minimum, 3 = windowed minimum with early exit and
+// skips (y and z passes); + kVariantXDirect = x pass with plain loads instead of the copy ring.
+constexpr int kVariantXDirect = 4;
 struct Tuning {
   int run[3] = {4, 4, 4};  // bricks per work item along x, y, z
-  int variant = 3;         // 1 full windowed minimum, 3 windowed minimum with early exit and skips
+  int variant = 3;
 };
 
 // Work lists of the passes: runs of bricks along each axis, and (half path) the slots of each

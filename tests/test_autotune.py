@@ -13,18 +13,26 @@ def table_from(fn):
 
 
 def test_choose_per_axis_minimum():
-    # x best at run 16 (any variant), y best at 8, z best at 4; variant 3 faster for y and z
+    # x best at run 16 with the ring kernel, y best at 8, z best at 4; pruned windows faster
     def t(v, r):
-        return {"x_ms": {4: 3.0, 8: 2.0, 16: 1.0}[r] + (0.5 if v == 1 else 0.0),
+        return {"x_ms": {4: 3.0, 8: 2.0, 16: 1.0}[r] + (0.5 if v & 4 else 0.0),
                 "y_ms": {4: 5.0, 8: 4.0, 16: 6.0}[r] * (2.0 if v == 1 else 1.0),
                 "z_ms": {4: 4.0, 8: 5.0, 16: 7.0}[r] * (2.0 if v == 1 else 1.0)}
     assert A.choose(table_from(t)) == {"x_run": 16, "y_run": 8, "z_run": 4, "variant": 3}
 
 
+def test_choose_x_direct_bit():
+    # the plain-load x kernel wins at run 8; the window variant stays the full one
+    def t(v, r):
+        return {"x_ms": 1.0 if (v & 4 and r == 8) else 2.0,
+                "y_ms": 1.0 if v == 1 else 3.0, "z_ms": 1.0 if v == 1 else 3.0}
+    assert A.choose(table_from(t)) == {"x_run": 8, "y_run": 4, "z_run": 4, "variant": 5}
+
+
 def test_choose_variant_by_best_yz_sum():
     # variant 1 wins on y + z at its best runs even though variant 3 wins y alone at run 4
     def t(v, r):
-        if v == 3:
+        if v & 3 == 3:
             return {"x_ms": 1.0, "y_ms": {4: 1.0, 8: 9.0, 16: 9.0}[r], "z_ms": 9.0}
         return {"x_ms": 1.0, "y_ms": 2.0, "z_ms": {4: 3.0, 8: 2.5, 16: 4.0}[r]}
     got = A.choose(table_from(t))
@@ -33,7 +41,7 @@ def test_choose_variant_by_best_yz_sum():
 
 def test_choose_joint_yz():
     def t(v, r):
-        return {"x_ms": 1.0, "y_ms": 0.0, "z_ms": {4: 3.0, 8: 1.0, 16: 2.0}[r] + (v == 1)}
+        return {"x_ms": 1.0 + (v & 4), "y_ms": 0.0, "z_ms": {4: 3.0, 8: 1.0, 16: 2.0}[r] + (v == 1)}
     got = A.choose(table_from(t), joint_yz=True)
     assert got["y_run"] == got["z_run"] == 8 and got["variant"] == 3
 
@@ -60,7 +68,7 @@ class FakeTarget:
     def phase_times(self):
         x, y, z, v = self.tuning
         cost = {4: 2.0, 8: 1.0, 16: 3.0}
-        return {"x_ms": cost[x], "y_ms": cost[y] + (v == 1), "z_ms": cost[z] + (v == 1)}
+        return {"x_ms": cost[x] + (v & 4), "y_ms": cost[y] + (v == 1), "z_ms": cost[z] + (v == 1)}
 
 
 def test_autotune_measures_then_uses_cache(tmp_path, monkeypatch):
@@ -92,7 +100,7 @@ def test_autotuned_map_is_exact(tmp_path):
     m = V.Map(192, 160, 64, 20)
     m.set_occupancy_dense(occ)
     got = A.autotune(m, reps=2, cache_path=str(tmp_path / "t.json"))
-    assert got["source"] == "measured" and got["variant"] in (1, 3)
+    assert got["source"] == "measured" and got["variant"] in (1, 3, 5, 7)
     assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 20)) is None
     again = A.autotune(m, reps=2, cache_path=str(tmp_path / "t.json"))
     assert again["source"] == "cache"

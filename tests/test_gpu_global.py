@@ -84,9 +84,10 @@ def test_empty_full_single_corner(dense):
 
 
 @pytest.mark.parametrize("runs", [(4, 4, 4), (16, 4, 16), (8, 8, 8), (4, 16, 4), (16, 16, 16)])
-@pytest.mark.parametrize("variant", [1, 3])
+@pytest.mark.parametrize("variant", [1, 3, 5, 7])
 def test_tunings(runs, variant):
-    """Work-item runs and pass variants: 1 full window, 3 window with early exit and skips."""
+    """Work-item runs and pass variants: 1 full window, 3 window with early exit and skips; 5 and 7
+    the same with the x pass on plain loads."""
     x_run, y_run, z_run = runs
     occ = W.bernoulli_grid(3, (48, 80, 72), 0.002)
     ref = O.edt_factorised(occ, 24)
@@ -94,7 +95,7 @@ def test_tunings(runs, variant):
     assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
 
 
-@pytest.mark.parametrize("variant", [1, 3])
+@pytest.mark.parametrize("variant", [1, 3, 7])
 @pytest.mark.parametrize("dmax", [2, 12, 20, 28, 36, 44])
 def test_variants_every_radius(variant, dmax):
     """Brick radius R = 1..6 for both window variants."""
