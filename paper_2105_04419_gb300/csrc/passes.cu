@@ -102,31 +102,40 @@ __device__ __forceinline__ bool mbar_wait_bounded(const GridView& g, uint64_t* b
 }
 
 // One 8-output window minimum on packed half2 registers:
-//   out[k] = min over |d| <= W of v[k + W + d] + d^2, pairing +d and -d.
+//   out[k] = min over |d| <= W of v[k + W + d] + d^2, pairing +d and -d,
+// where v[j] is plane j of the lane's staged column (c[j * 32]).  Planes are loaded when first
+// needed: the 8 centre planes, then at offset d the two planes that enter the window (W - d and
+// W + 7 + d), so only about 16 planes are live at a time and the early exit also skips the loads.
 // With `prune`, the offsets stop once (d + 1)^2 is at least every output's current minimum in the
 // warp (a farther candidate costs at least (d + 1)^2, so none can lower any output); the test runs
 // every 4 offsets and is warp-uniform.
 template <int W>
-__device__ __forceinline__ void window_min8(const uint32_t (&v)[8 + 2 * W], uint32_t (&out)[8], bool prune) {
+__device__ __forceinline__ void window_min8(const uint32_t* __restrict__ c, uint32_t (&out)[8], bool prune) {
   static_assert(W % 4 == 0, "window is a multiple of 4 offsets");
+  uint32_t v[8 + 2 * W];
   __half2 acc[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) acc[k] = u2h(v[k + W]);
+  for (int k = 0; k < 8; ++k) {
+    v[k + W] = c[(k + W) * 32];
+    acc[k] = u2h(v[k + W]);
+  }
   bool live = true;  // warp-uniform
 #pragma unroll
-  for (int c = 0; c < W / 4; ++c) {
+  for (int ch = 0; ch < W / 4; ++ch) {
     if (live) {
 #pragma unroll
       for (int dd = 1; dd <= 4; ++dd) {
-        const int d = 4 * c + dd;
+        const int d = 4 * ch + dd;
+        v[W - d] = c[(W - d) * 32];
+        v[W + 7 + d] = c[(W + 7 + d) * 32];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           __half2 m = __hmin2(u2h(v[k + W - d]), u2h(v[k + W + d]));
           acc[k] = __hmin2(acc[k], __hadd2(m, u2h(half2_bits(d * d))));
         }
       }
-      if (prune && c + 1 < W / 4) {
-        const int d1 = 4 * c + 5;  // the next offset
+      if (prune && ch + 1 < W / 4) {
+        const int d1 = 4 * ch + 5;  // the next offset
         __half2 mx = __hmax2(__hmax2(__hmax2(acc[0], acc[1]), __hmax2(acc[2], acc[3])),
                              __hmax2(__hmax2(acc[4], acc[5]), __hmax2(acc[6], acc[7])));
         const bool done = __hbge2(u2h(half2_bits(d1 * d1)), mx);
@@ -285,12 +294,8 @@ __device__ __forceinline__ void window_compute(const GridView& g, const uint32_t
   for (int b = 0; b <= 2 * R; ++b) any_fin |= fin_flags[w + b] != 0;
   uint32_t out[8];
   if (any_fin) {
-    uint32_t v[8 + 2 * W];
-    const uint32_t* c = col + a * 4 + xp;
-    const int p0 = w * 8;  // plane of output 0 minus W
-#pragma unroll
-    for (int j = 0; j < 8 + 2 * W; ++j) v[j] = c[(p0 + j) * 32];
-    window_min8<W>(v, out, prune);
+    // plane w * 8 of the stage is plane 0 of this output brick's window (output 0 minus W)
+    window_min8<W>(col + a * 4 + xp + (size_t)w * 8 * 32, out, prune);
   } else {
 #pragma unroll
     for (int q = 0; q < 8; ++q) out[q] = inf2;
@@ -327,9 +332,15 @@ __device__ __forceinline__ void window_compute(const GridView& g, const uint32_t
 // stage, and starts one bulk copy per present brick (64 B masks for x, 1 KB g1 / g2 for y / z).
 // Warps 1..RUN consume: warp w computes output brick w of the item from the stage, then
 // releases it.  Every wait is bounded; on a timeout the error word is set and the block drains.
+// Resident blocks per SM the window passes ask the register allocator for (at most 80 registers
+// for RUN 4, 72 for RUN 8): enough warps to keep the packed-min pipe busy.
+__host__ __device__ constexpr int pass_min_blocks(int run, int axis) {
+  return axis == 0 ? 1 : (run == 4 ? 5 : (run == 8 ? 3 : 1));
+}
+
 template <int R, int RUN, int AXIS>
-__global__ void __launch_bounds__(32 * (RUN + 1)) k_pass(GridView g, const int32_t* __restrict__ islots, int max_items,
-                                                         bool prune) {
+__global__ void __launch_bounds__(32 * (RUN + 1), pass_min_blocks(RUN, AXIS))
+    k_pass(GridView g, const int32_t* __restrict__ islots, int max_items, bool prune) {
   using S = ColShape<R, RUN, AXIS>;
   constexpr int NB = S::NB, NS = S::NS;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -581,6 +592,8 @@ cudaError_t pass_half(const GridView& g, const int32_t* islots, int max_items, c
   auto kernel = k_pass<R, RUN, AXIS>;
   if (max_items <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, S::THREADS, S::SMEM);
