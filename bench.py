@@ -138,16 +138,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel: str):
+def traffic_for(kernel: str, tuning: dict):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
-    source of the kernel (hash of the pass source file)."""
+    source of the kernel (hash of the pass source file) with the same work-item runs."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         src = open(os.path.join(ROOT, "paper_2105_04419_gb300", "csrc", "passes.cu"), "rb").read()
         h = hashlib.sha256(src).hexdigest()[:16]
         e = t.get(kernel)
-        if e and e.get("source_sha") == h:
+        runs = "x_run {x_run}, y_run {y_run}, z_run {z_run}, variant {variant}".format(
+            **{k: tuning.get(k) for k in ("x_run", "y_run", "z_run", "variant")})
+        if e and e.get("source_sha") == h and runs in t.get("_note", ""):
             return e
     except Exception:
         pass
@@ -547,7 +549,7 @@ def main():
     dom = max(per_brick, key=lambda k: ph[k])
     kname = {"x_ms": "k_pass<x>", "y_ms": "k_pass<y>", "z_ms": "k_pass<z>"}[dom]
     achieved = allocated * per_brick[dom] / (ph[dom] / 1e3) / 1e9
-    tr = traffic_for(kname)
+    tr = traffic_for(kname, tuning)
     roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
                 "bytes_per_brick": per_brick[dom], "bricks_per_launch": allocated,
