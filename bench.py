@@ -196,12 +196,17 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
     # untimed pass with statistics (records, net flips, dirty runs per frame)
     ms = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
     ms.global_()
-    stats = []
+    ms.set_profiling(True)
+    stats, phases = [], []
     for x, v in sl:
         ms.set_occupancy(x, v)
         stats.append(ms.update(stats=True))
+        phases.append(ms.phase_times())
     info_final = ms.info()
     ms.close()
+    # update phases: ingest = records applied with flip tracking, activation = changed bricks, their
+    # dilation and the dirty runs, items = slot lists of the dirty runs
+    phase_med = {k: statistics.median(p[k] for p in phases) for k in phases[0]}
 
     def timed(run_frame):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nframes)]
@@ -261,6 +266,7 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
             "changed_bricks_per_frame": dist_summary([s["changed_bricks"] for s in stats]),
             "z_runs_per_frame": dist_summary([s["z_items"] for s in stats]),
             "graph_ms_per_frame": g, "eager_ms_per_frame": dist_summary(eager_ms),
+            "eager_phase_ms_median": phase_med,
             "eager_launches_per_frame": eager_launches,
             "global_ms_final_occupancy": glob, "global_over_graph_median": glob / g["median"],
             "final_map": {"occupied_voxels": int(final_occ.sum()), "allocated_bricks": info_final["allocated_bricks"]},
@@ -561,6 +567,25 @@ def main():
                  "compulsory_B_per_active_voxel": 4.125,
                  "frac_compulsory": active * 4.125 / (ms / 1e3) / 1e9 / peak, "peak": peak, "unit": "GB/s"}
 
+    # the same step captured once into a CUDA graph (reset + counted staging + global) and replayed
+    graph = V.GlobalGraph(m, n)
+    graph.xyz.copy_(xyz)
+    graph.occ.copy_(ones)
+    graph.count.fill_(n)
+    for _ in range(max(3, args.warmup)):
+        graph.replay()
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches_g0 = V.kernel_launches()
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        gev[k][0].record(stream)
+        graph.replay()
+        gev[k][1].record(stream)
+    torch.cuda.synchronize()
+    graph_ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in gev))
+    graph_launches = V.kernel_launches() - launches_g0  # host launches inside the graph replays: 0
+    del graph
+
     line = {"metric": METRIC, "value": value, "unit": "Mvoxels/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -571,11 +596,16 @@ def main():
                        "step": "reset + stage device records + global transform",
                        "tuning": {k: v for k, v in tuning.items() if k != "key"}},
             "phases_ms": ph, "roofline": roofline, "roofline_step": roof_step, "gpu_launches": launches,
-            "clocks": clocks}
+            "clocks": clocks,
+            "graph_replay": {"ms_per_step": graph_ms, "value": active * world / (graph_ms / 1e3) / 1e6,
+                             "unit": "Mvoxels/s", "library_launches_per_step": launches / args.steps,
+                             "host_launches_during_replay": graph_launches,
+                             "step": "the same step captured once into a CUDA graph and replayed"}}
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers (pinned): host records -> device,
-        # transform, and the grid's counters (including the active-brick count) back to the host
+        # transform, and the grid's counters (including the active-brick count, reduced on the
+        # device) back to the host
         xyz_h = torch.from_numpy(xyz_h).pin_memory().numpy()
         ones_h = torch.from_numpy(ones_h).pin_memory().numpy()
         e2e_ms = []
@@ -592,7 +622,7 @@ def main():
         ems = max_over_ranks(statistics.mean(e2e_ms))
         line["e2e"] = {"value": inf2["finite_bricks"] * 512 * world / (ems / 1e3) / 1e6, "unit": "Mvoxels/s",
                        "ms_per_step": ems, "host_buffers": "pinned", "h2d_bytes_per_step": int(n * 13),
-                       "d2h_bytes_per_step": int(4 * 16 + 4 * inf2["allocated_bricks"])}
+                       "d2h_bytes_per_step": 4 * 16}
 
     if wl["kind"] == "tunnel" and not args.no_clearance:
         line["clearance"] = bench_clearance(V, torch, m, occ, stream)

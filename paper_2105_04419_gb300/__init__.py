@@ -8,13 +8,15 @@ importing :mod:`paper_2105_04419_gb300.lib` raises.
 Entry points mirror the C names: :class:`Map` wraps a handle (create, set_occupancy,
 set_occupancy_counted, set_occupancy_dense, reset, global_, update, query, export_dense, clearance_forward /
 clearance_backward, set_tuning, synchronize, info); :class:`UpdateGraph` captures one
-incremental update into a CUDA graph and replays it per frame; :class:`Batch` holds grids
+incremental update into a CUDA graph and replays it per frame (:class:`GlobalGraph` the same for
+the global transform from fresh records); :class:`Batch` holds grids
 of uneven size whose transform steps run once for all of them; :func:`global_batched` runs
 several maps in one call; :func:`clearance_cost` is the differentiable clearance cost (torch.autograd.Function
 over the library's forward and backward kernels).
 """
 from .lib import (  # noqa: F401
     Batch,
+    GlobalGraph,
     VDBEDT_DMAX_LIMIT,
     Map,
     UpdateGraph,

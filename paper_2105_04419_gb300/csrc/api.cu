@@ -622,20 +622,14 @@ vdbedt_status vdbedt_get_info(vdbedt_handle h, vdbedt_info* info) {
   if (s) return s;
   if (!info) return fail(h, VDBEDT_EINVAL, "null info");
   DeviceGuard guard(h->device);
-  s = device_errors(h);
+  CK(h, launch_count_flags(h->g, h->st), "count");
+  s = device_errors(h);  // synchronises
   if (s) return s;
-  CK(h, cudaMemcpy(h->h_pinned, h->g.counters, sizeof(int32_t) * C_NUM, cudaMemcpyDeviceToHost), "d2h");
-  int nb = std::min(h->h_pinned[C_NBRICKS], h->g.cap);
-  std::vector<uint32_t> flags((size_t)std::max(nb, 1));
-  if (nb > 0) CK(h, cudaMemcpy(flags.data(), h->g.bflags, sizeof(uint32_t) * nb, cudaMemcpyDeviceToHost), "d2h");
-  int64_t obst = 0, fin = 0;
-  for (int i = 0; i < nb; ++i) {
-    obst += (flags[i] & F_OBST) != 0;
-    fin += (flags[i] & F_FINITE) != 0;
-  }
-  info->allocated_bricks = nb;
-  info->obstacle_bricks = obst;
-  info->finite_bricks = fin;
+  CK(h, cudaMemcpyAsync(h->h_pinned, h->g.counters, sizeof(int32_t) * C_NUM, cudaMemcpyDeviceToHost, h->st), "d2h");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  info->allocated_bricks = std::min(h->h_pinned[C_NBRICKS], h->g.cap);
+  info->obstacle_bricks = h->h_pinned[C_OBST];
+  info->finite_bricks = h->h_pinned[C_FINITE];
   info->capacity_bricks = h->g.cap;
   info->nodes = h->h_pinned[C_NNODES];
   info->device_bytes =

@@ -153,7 +153,7 @@ __device__ __forceinline__ void window_min8(const uint32_t* __restrict__ c, uint
 template <int R, int RUN, int AXIS>
 struct ColShape {
   static constexpr int NB = RUN + 2 * R;                     // staged bricks per item
-  static constexpr int NS = 3;                               // ring stages
+  static constexpr int NS = AXIS == 0 ? 8 : 3;               // ring stages (x stages are 64 B per brick)
   static constexpr int UNIT = AXIS == 0 ? 64 : 1024;         // bytes staged per brick
   static constexpr int STAGE_BYTES = NB * UNIT;
   static constexpr int META = 2 * NB;                        // slots, then input flags

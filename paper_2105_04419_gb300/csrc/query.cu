@@ -166,6 +166,30 @@ cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32
   return cudaGetLastError();
 }
 
+// Bricks holding an obstacle and bricks holding a finite D, counted on the device (counters
+// C_OBST and C_FINITE, cleared by the caller): one atomic per warp and flag.
+__global__ void k_count_flags(GridView g) {
+  const int nb = min(g.counters[C_NBRICKS], g.cap);
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x; base < nb; base += gridDim.x * blockDim.x) {
+    const int s = base + threadIdx.x;
+    const uint32_t f = s < nb ? g.bflags[s] : 0u;
+    const int obst = __popc(__ballot_sync(0xffffffffu, (f & F_OBST) != 0u));
+    const int fin = __popc(__ballot_sync(0xffffffffu, (f & F_FINITE) != 0u));
+    if (lane == 0) {
+      if (obst) atomicAdd(&g.counters[C_OBST], obst);
+      if (fin) atomicAdd(&g.counters[C_FINITE], fin);
+    }
+  }
+}
+
+cudaError_t launch_count_flags(const GridView& g, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(g.counters + C_FINITE, 0, 2 * sizeof(int32_t), st);  // C_FINITE, C_OBST
+  if (e != cudaSuccess) return e;
+  VDB_LAUNCH(k_count_flags, 1024, 256, 0, st, g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_export_dense(const GridView& g, int32_t* out, cudaStream_t st) {
   int64_t n = (int64_t)g.nx * g.ny * g.nz;
   VDB_LAUNCH(k_export_dense, grid_for(n, 256), 256, 0, st, g, out);

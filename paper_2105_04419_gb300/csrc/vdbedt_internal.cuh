@@ -301,6 +301,8 @@ int effective_run(const GridView& g, const Tuning& t, int axis);
 // queries (query.cu)
 cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st);
 cudaError_t launch_export_dense(const GridView& g, int32_t* out, cudaStream_t st);
+// obstacle and finite brick counts into counters C_OBST and C_FINITE
+cudaError_t launch_count_flags(const GridView& g, cudaStream_t st);
 cudaError_t launch_clearance_fwd(const GridView& g, float vs, const float* pts, int64_t T, int64_t P, float tau,
                                  float* cost, cudaStream_t st);
 cudaError_t launch_clearance_bwd(const GridView& g, float vs, const float* pts, int64_t T, int64_t P, float tau,

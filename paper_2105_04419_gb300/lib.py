@@ -311,13 +311,9 @@ class Map:
         return g
 
 
-class UpdateGraph:
-    """One incremental update of a Map -- staging of up to max_records device records with a
-    device-side count, then vdbedt_update -- captured once into a CUDA graph.  run(xyz, occ)
-    writes a frame's records into the graph's fixed input buffers and replays the graph on the
-    map's stream; the result equals set_occupancy(xyz, occ) + update() bit for bit.  The map must
-    not be reset, given a dense grid or retuned while the graph is in use (the graph holds the
-    launches of the incremental form with the tuning of capture time)."""
+class _CapturedStep:
+    """Shared machinery of the captured forms: fixed device input buffers (records and their
+    count) and one CUDA graph of the library calls of `_body`, replayed on the map's stream."""
 
     def __init__(self, m: Map, max_records: int):
         torch = _torch()
@@ -329,8 +325,7 @@ class UpdateGraph:
         self.count = torch.zeros(1, dtype=torch.int32, device=dev)
         m._enter()
         with torch.cuda.stream(m.stream):
-            # one uncaptured update with an empty frame: reserves the stage and the ingest scratch,
-            # and runs the global transform first if the map has none yet
+            # one uncaptured run with an empty frame: reserves the stage and the ingest scratch
             self._body()
             m.stream.synchronize()
             self.graph = torch.cuda.CUDAGraph()
@@ -338,15 +333,14 @@ class UpdateGraph:
                 self._body()
         m.synchronize()
 
-    def _body(self):
+    def _stage(self):
         lib = load()
         h = self.m._h
         _check(lib.vdbedt_set_occupancy_counted(h, self.xyz.data_ptr(), self.occ.data_ptr(), self.count.data_ptr(),
                                                 self.max_records), "vdbedt_set_occupancy_counted", h)
-        _check(lib.vdbedt_update(h, None), "vdbedt_update", h)
 
     def run(self, xyz, occ):
-        """Replay for one frame; xyz [n, 3] int32 and occ [n] uint8, CUDA tensors or numpy arrays."""
+        """Replay for one set of records; xyz [n, 3] int32 and occ [n] uint8, CUDA tensors or numpy."""
         torch = _torch()
         n = int(occ.shape[0])
         if n > self.max_records:
@@ -362,6 +356,43 @@ class UpdateGraph:
             self.count.fill_(n)
             self.graph.replay()
         self.m._leave()
+
+    def replay(self):
+        """Replay with the records already in the input buffers (xyz, occ, count)."""
+        torch = _torch()
+        self.m._enter()
+        with torch.cuda.stream(self.m.stream):
+            self.graph.replay()
+        self.m._leave()
+
+
+class GlobalGraph(_CapturedStep):
+    """The global transform from a fresh occupancy -- vdbedt_reset, staging of up to max_records
+    device records with a device-side count, vdbedt_global -- captured once into a CUDA graph.
+    run(xyz, occ) equals reset() + set_occupancy(xyz, occ) + global_() bit for bit."""
+
+    def _body(self):
+        lib = load()
+        h = self.m._h
+        _check(lib.vdbedt_reset(h), "vdbedt_reset", h)
+        self._stage()
+        _check(lib.vdbedt_global(h), "vdbedt_global", h)
+
+
+class UpdateGraph(_CapturedStep):
+    """One incremental update of a Map -- staging of up to max_records device records with a
+    device-side count, then vdbedt_update -- captured once into a CUDA graph.  run(xyz, occ)
+    writes a frame's records into the graph's fixed input buffers and replays the graph on the
+    map's stream; the result equals set_occupancy(xyz, occ) + update() bit for bit.  The map must
+    not be reset, given a dense grid or retuned while the graph is in use (the graph holds the
+    launches of the incremental form with the tuning of capture time); the first, uncaptured call
+    runs the global transform if the map has none yet."""
+
+    def _body(self):
+        lib = load()
+        h = self.m._h
+        self._stage()
+        _check(lib.vdbedt_update(h, None), "vdbedt_update", h)
 
 
 NOALLOC_MAX_VOXELS = 1 << 21

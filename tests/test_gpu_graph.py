@@ -146,3 +146,21 @@ def test_counted_stage_must_be_alone():
     ref = np.zeros((16, 16, 16), np.uint8)
     ref[3, 2, 1] = 1
     assert np.array_equal(m.export_dense(), O.edt_factorised(ref, 4))
+
+
+def test_global_graph_replay():
+    import torch
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(12)
+    shape = (40, 50, 60)
+    nz, ny, nx = shape
+    m = V.Map(nx, ny, nz, 14)
+    g = V.GlobalGraph(m, 20000)
+    for f in range(3):
+        occ = (rs.random(shape) < 0.003 * (f + 1)).astype(np.uint8)
+        xyz = coords_of(occ)
+        g.run(torch.from_numpy(xyz).cuda(), torch.ones(len(xyz), dtype=torch.uint8, device="cuda"))
+        assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 14)) is None, f
+    # replay with the buffers as they are gives the same field again
+    g.replay()
+    assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 14)) is None
