@@ -228,6 +228,15 @@ vdbedt_status vdbedt_global_batched(vdbedt_handle* hs, int32_t k);
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 int64_t vdbedt_kernel_launches(void);
 
+/* Self-test of the device-side bounded waits (no paper counterpart: it lets a test exercise the
+ * timeout path without a GPU fault).  which = 0: one thread waits on an mbarrier phase that never
+ * completes (the wait of the pass kernels); which = 1: one thread looks up a node whose insertion
+ * is left pending (the wait of node creation; the planted claim leaves the grid's node table
+ * invalid until vdbedt_reset).  Each wait gives up after one second, sets the handle's error word
+ * and returns, so the context stays usable; the next synchronising call reports VDBEDT_ETIMEOUT
+ * until vdbedt_reset.  Other values of which are EINVAL. */
+vdbedt_status vdbedt_selftest_wait_timeout(vdbedt_handle h, int32_t which);
+
 /* Dense transform without any allocation (no paper counterpart: this is a deployment feature).
  * For callers that cannot call cudaMalloc -- code running while the application holds a stream
  * capture open, real-time loops that must stay out of the allocator, hosts whose device memory

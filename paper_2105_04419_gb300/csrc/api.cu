@@ -672,6 +672,15 @@ vdbedt_status vdbedt_get_phase_times(vdbedt_handle h, vdbedt_phase_times* out) {
 
 int64_t vdbedt_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+vdbedt_status vdbedt_selftest_wait_timeout(vdbedt_handle h, int32_t which) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (which != 0 && which != 1) return fail(h, VDBEDT_EINVAL, "which must be 0 or 1");
+  DeviceGuard guard(h->device);
+  CK(h, launch_wait_selftest(h->g, which, h->st), "wait self-test");
+  return VDBEDT_OK;
+}
+
 const char* vdbedt_last_error(vdbedt_handle h) { return h ? h->err.c_str() : g_last_error.c_str(); }
 
 }  // extern "C"

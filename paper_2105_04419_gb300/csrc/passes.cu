@@ -90,11 +90,13 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// Bounded wait for a phase of an mbarrier: gives up after ~2^22 polls (seconds), sets the
-// device error word and reports failure; the caller's whole block agrees before acting.
+// Bounded wait for a phase of an mbarrier: gives up after one second of global time (or
+// kWaitMaxPolls polls), sets the device error word and reports failure.
 __device__ __forceinline__ bool mbar_wait_bounded(const GridView& g, uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < (1 << 22); ++i) {
+  const unsigned long long t0 = global_ns();
+  for (uint32_t i = 0; i < kWaitMaxPolls; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && global_ns() - t0 > kWaitLimitNs) break;
     if (i > 16) __nanosleep(64);
   }
   set_error(g, kErrTimeout);
@@ -629,6 +631,23 @@ cudaError_t pass_half_run(const GridView& g, int run, const int32_t* islots, int
   return cudaErrorInvalidValue;
 }
 
+// Self-test of the bounded waits: one thread waits on a phase that never completes (which = 0: an
+// mbarrier with no arrivals, the wait of the pass kernels) or looks up a node whose insertion was
+// left pending (which = 1: the wait of node creation).  Each gives up after its poll limit, sets
+// the error word and returns.
+__global__ void k_wait_selftest(GridView g, int which) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  if (which == 0) {
+    mbar_init(&bar, 1);
+    mbar_wait_bounded(g, &bar, 0);
+  } else {
+    const uint32_t key = 0;
+    g.hslots[hash32(key) & g.hmask] = ((unsigned long long)key << 32) | kPending;
+    get_or_create_node(g, key);
+  }
+}
+
 template <int R>
 cudaError_t x_direct_r(const GridView& g, const int32_t* islots, int max_items, int run, cudaStream_t st) {
   auto kernel = k_x_direct<R>;
@@ -654,6 +673,11 @@ cudaError_t x_direct(const GridView& g, const int32_t* islots, int max_items, in
 }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(const GridView& g, int which, cudaStream_t st) {
+  VDB_LAUNCH(k_wait_selftest, 1, 32, 0, st, g, which);
+  return cudaGetLastError();
+}
 
 bool half_path(const GridView& g) { return g.dmax <= 45 && g.R >= 1 && g.R <= 6; }
 

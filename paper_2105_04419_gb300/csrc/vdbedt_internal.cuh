@@ -107,6 +107,16 @@ __device__ __forceinline__ uint32_t hash32(uint32_t k) {
 
 __device__ __forceinline__ void set_error(const GridView& g, int bits) { atomicOr(&g.counters[C_ERR], bits); }
 
+// Device-side waits give up after kWaitLimitNs of global time (or kWaitMaxPolls polls, whichever
+// comes first), set the error word and let the kernel return.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // one second
+constexpr uint32_t kWaitMaxPolls = 1u << 28;
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Node index for node key, or -1 when the node is absent.  Readers never wait: a node whose
 // insertion is still pending is absent for them (inserts happen in kernels that do not read the
 // node's bricks).
@@ -152,11 +162,13 @@ __device__ inline int get_or_create_node(const GridView& g, uint32_t key) {
     }
     if (k == key) {
       if ((uint32_t)w != kPending) return (int)(uint32_t)w;  // published: no atomic needed
-      for (int spin = 0; spin < (1 << 22); ++spin) {
+      const unsigned long long t0 = global_ns();
+      for (uint32_t spin = 0; spin < kWaitMaxPolls; ++spin) {
         // plain (volatile) reads while waiting: they do not queue behind the publishing exchange
         unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&g.hslots[h]);
         uint32_t v = (uint32_t)cur;
         if (v != kPending) return (int)v;
+        if ((spin & 63u) == 63u && global_ns() - t0 > kWaitLimitNs) break;
         __nanosleep(64);
       }
       set_error(g, kErrTimeout);
@@ -297,6 +309,8 @@ bool half_path(const GridView& g);
 // pass along `axis` (0 x, 1 y, 2 z) over the queued runs
 cudaError_t launch_pass(const GridView& g, const Tuning& t, int axis, const Items& it, cudaStream_t st);
 int effective_run(const GridView& g, const Tuning& t, int axis);
+// a bounded device wait that runs out (0: mbarrier phase, 1: pending node), for tests
+cudaError_t launch_wait_selftest(const GridView& g, int which, cudaStream_t st);
 
 // queries (query.cu)
 cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st);

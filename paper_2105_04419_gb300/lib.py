@@ -85,6 +85,7 @@ SIGNATURES = {
     "vdbedt_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
     "vdbedt_get_phase_times": (ctypes.c_int, [_H, ctypes.POINTER(PhaseTimes)]),
     "vdbedt_kernel_launches": (ctypes.c_int64, []),
+    "vdbedt_selftest_wait_timeout": (ctypes.c_int, [_H, _I32]),
     "vdbedt_edt_dense_noalloc": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _P, ctypes.c_void_p]),
     "vdbedt_last_error": (ctypes.c_char_p, [_H]),
 }
