@@ -890,6 +890,27 @@ vdbedt_status vdbedt_batch_create(const vdbedt_config* cfgs, int32_t k, vdbedt_b
     off += m->g.cap;
   }
   b->shape.k = k;
+  b->shape.R = b->maps[0]->g.R;
+  {
+    // block shares of the per-grid kernels (one launch each, shares end to end)
+    std::vector<int> first((size_t)BK_NUM * (k + 1));
+    for (int kind = 0; kind < BK_NUM; ++kind) {
+      int acc = 0;
+      for (int i = 0; i < k; ++i) {
+        first[(size_t)kind * (k + 1) + i] = acc;
+        acc += batch_blocks(views[(size_t)i], kind);
+      }
+      first[(size_t)kind * (k + 1) + k] = acc;
+      b->shape.total[kind] = acc;
+    }
+    int* d_first = nullptr;
+    e = cudaMalloc((void**)&d_first, sizeof(int) * first.size());
+    if (e != cudaSuccess) return bail(e, "device alloc");
+    b->allocs.push_back(d_first);
+    e = cudaMemcpy(d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(e, "block shares");
+    for (int kind = 0; kind < BK_NUM; ++kind) b->shape.first[kind] = d_first + (size_t)kind * (k + 1);
+  }
   // the pool view: shape fields of grid 0 (dmax, R, INF are common), the batch's words and lists
   {
     const GridView& g0 = b->maps[0]->g;

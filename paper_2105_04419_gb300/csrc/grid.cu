@@ -35,32 +35,55 @@ inline int bits_for(uint64_t maxval) {
   return b;
 }
 
-// View sources of the kernels that run once per grid: a single grid (the view is a kernel
-// parameter), or every grid of a batch (views in device memory, grid = blockIdx.y).
+// View sources of the kernels that run once per grid.  get() returns the grid of the calling block
+// and the block's index and count within that grid's share of the launch: a single grid (the view
+// is a kernel parameter, the whole launch is its share), or every grid of a batch (views in device
+// memory; grid i owns blocks first[i] .. first[i + 1] - 1 of a one-dimensional launch, shares sized
+// to each grid's work, found by binary search).
 struct OneView {
   GridView g;
-  __device__ __forceinline__ GridView get() const { return g; }
+  __device__ __forceinline__ GridView get(int& bid, int& nblk, int& grid) const {
+    bid = blockIdx.x;
+    nblk = gridDim.x;
+    grid = 0;
+    return g;
+  }
 };
 struct BatchViews {
   const GridView* v;
-  __device__ __forceinline__ GridView get() const { return v[blockIdx.y]; }
+  const int* first;  // [k + 1], first[k] = blocks of the launch
+  int k;
+  __device__ __forceinline__ GridView get(int& bid, int& nblk, int& grid) const {
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = k;  // first[lo] <= b < first[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (first[mid] <= b) lo = mid; else hi = mid;
+    }
+    bid = b - first[lo];
+    nblk = first[lo + 1] - first[lo];
+    grid = lo;
+    return v[lo];
+  }
 };
 struct OneSrc {
   const uint8_t* p;
-  __device__ __forceinline__ const uint8_t* get() const { return p; }
+  __device__ __forceinline__ const uint8_t* get(int) const { return p; }
 };
 struct BatchSrc {
   const uint8_t* p[kBatchMax];
-  __device__ __forceinline__ const uint8_t* get() const { return p[blockIdx.y]; }
+  __device__ __forceinline__ const uint8_t* get(int grid) const { return p[grid]; }
 };
 
 // ---- reset ----
 template <class VS>
 __global__ void k_reset_nodes(VS vs) {
-  const GridView g = vs.get();
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int64_t total = (int64_t)nn * kNodeBricks;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < total; i += (int64_t)nblk * blockDim.x) {
     g.child[i] = kNoSlot;
     if ((i & 3) == 0) {
       int64_t j = i >> 2;  // 3 x 1024 marks per node
@@ -71,8 +94,8 @@ __global__ void k_reset_nodes(VS vs) {
     if ((i & 31) == 0) g.amask[i >> 5] = 0u;
     if ((i & 31) < 3) g.mwork[(i >> 5) * 3 + (i & 31)] = 0u;
   }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= (int64_t)g.hmask;
-       i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i <= (int64_t)g.hmask;
+       i += (int64_t)nblk * blockDim.x)
     g.hslots[i] = ~0ull;
 }
 
@@ -443,68 +466,110 @@ __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t 
 }
 
 // ---- dense ingest ----
-// One warp per brick of the grid: each lane builds two 8-voxel x-rows of the brick's mask (one
-// 8-byte load per row when rows are 8-byte aligned).  The grid was reset just before, so every
-// brick is claimed by exactly one warp: slots come from one atomic per block (block scan), and
-// the brick's fields are left for the global transform that always follows a dense ingest.
+// One warp per segment of kSeg consecutive bricks along x: each lane builds two x-rows (y, z) of
+// the segment's masks, loading each row's 8 * kSeg bytes as 8-byte words when rows are 8-byte
+// aligned (so the warp's loads cover whole 32-byte sectors).  The grid was reset just before, so
+// every brick is claimed by exactly one warp: the block counts its warps' occupied bricks and
+// reserves their slots with one atomic; brick fields are left for the global transform that
+// always follows a dense ingest.
+constexpr int kSeg = 4;
+
+__device__ __forceinline__ uint32_t nonzero_bytes(unsigned long long w) {
+  // bit i = byte i nonzero: fold each byte onto its low bit, then gather the eight low bits
+  w |= w >> 4;
+  w |= w >> 2;
+  w |= w >> 1;
+  w &= 0x0101010101010101ull;
+  return (uint32_t)((w * 0x0102040810204080ull) >> 56);
+}
+
 template <class VS, class SRC>
 __global__ void __launch_bounds__(256) k_ingest_dense(VS vs, SRC src) {
-  const GridView g = vs.get();
-  const uint8_t* __restrict__ grid = src.get();
-  const int64_t nbr = (int64_t)g.BX * g.BY * g.BZ;
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  const uint8_t* __restrict__ grid = src.get(gi);
+  const int SX = (g.BX + kSeg - 1) / kSeg;  // segments per brick row
+  const int64_t nseg = (int64_t)SX * g.BY * g.BZ;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool vec = (g.nx % 8) == 0 && (reinterpret_cast<uintptr_t>(grid) & 7u) == 0;
-  for (int64_t base = (int64_t)blockIdx.x * nwarps; base < nbr; base += (int64_t)gridDim.x * nwarps) {
-    const int64_t b = base + warp;
-    int bx = 0, by = 0, bz = 0;
-    uint32_t rows[2] = {0u, 0u};
-    if (b < nbr) {
-      bx = (int)(b % g.BX);
-      by = (int)((b / g.BX) % g.BY);
-      bz = (int)(b / ((int64_t)g.BX * g.BY));
+  __shared__ int wcount[32];
+  __shared__ int wbase[32];
+  for (int64_t base = (int64_t)bid * nwarps; base < nseg; base += (int64_t)nblk * nwarps) {
+    const int64_t sg = base + warp;
+    int bx0 = 0, by = 0, bz = 0;
+    uint32_t rows[kSeg][2];
+#pragma unroll
+    for (int j = 0; j < kSeg; ++j) rows[j][0] = rows[j][1] = 0u;
+    if (sg < nseg) {
+      bx0 = (int)(sg % SX) * kSeg;
+      by = (int)((sg / SX) % g.BY);
+      bz = (int)(sg / ((int64_t)SX * g.BY));
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int r = lane * 2 + q;  // byte index y + 8 z
+        const int r = lane * 2 + q;  // byte index y + 8 z within a brick
         const int gy = by * 8 + (r & 7), gz = bz * 8 + (r >> 3);
         if (gy < g.ny && gz < g.nz) {
-          const uint8_t* row = grid + ((size_t)gz * g.ny + gy) * g.nx + (size_t)bx * 8;
-          if (vec) {
-            // bit i of the result = byte i nonzero (fold each byte onto its low bit, then gather)
-            unsigned long long w = __ldg(reinterpret_cast<const unsigned long long*>(row));
-            w |= w >> 4;
-            w |= w >> 2;
-            w |= w >> 1;
-            w &= 0x0101010101010101ull;
-            rows[q] = (uint32_t)((w * 0x0102040810204080ull) >> 56);
-          } else {
-            const int nxv = min(8, g.nx - bx * 8);
-            uint32_t v = 0u;
-            for (int x = 0; x < nxv; ++x) v |= (uint32_t)(row[x] != 0) << x;
-            rows[q] = v;
+          const uint8_t* row = grid + ((size_t)gz * g.ny + gy) * g.nx + (size_t)bx0 * 8;
+#pragma unroll
+          for (int j = 0; j < kSeg; ++j) {
+            const int x0 = (bx0 + j) * 8;
+            if (x0 < g.nx) {
+              if (vec) {
+                rows[j][q] = nonzero_bytes(__ldg(reinterpret_cast<const unsigned long long*>(row + 8 * j)));
+              } else {
+                const int nxv = min(8, g.nx - x0);
+                uint32_t v = 0u;
+                for (int x = 0; x < nxv; ++x) v |= (uint32_t)(row[8 * j + x] != 0) << x;
+                rows[j][q] = v;
+              }
+            }
           }
         }
       }
     }
-    const bool any = __any_sync(0xffffffffu, (rows[0] | rows[1]) != 0u);  // false past the grid
+    // bricks of the segment holding an obstacle (false past the grid)
+    uint32_t occupied = 0u;
+#pragma unroll
+    for (int j = 0; j < kSeg; ++j)
+      occupied |= (__any_sync(0xffffffffu, (rows[j][0] | rows[j][1]) != 0u) ? 1u : 0u) << j;
+    // lane j finds brick j's node (nodes are shared, so look-ups mostly hit published entries)
     int node = -1;
-    if (any && lane == 0) node = get_or_create_node(g, (uint32_t)node_key_of(g, bx, by, bz));
-    node = __shfl_sync(0xffffffffu, node, 0);
-    int total = 0;
-    const int mine = block_agg_add(&g.counters[C_NBRICKS], lane == 0 && node >= 0, &total);
-    const int slot = __shfl_sync(0xffffffffu, mine, 0);
-    if (node >= 0) {
+    if (lane < kSeg && ((occupied >> lane) & 1u))
+      node = get_or_create_node(g, (uint32_t)node_key_of(g, bx0 + lane, by, bz));
+    const unsigned have = __ballot_sync(0xffffffffu, node >= 0) & ((1u << kSeg) - 1u);
+    if (lane == 0) wcount[warp] = __popc(have);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < nwarps; ++w) {
+        const int c = wcount[w];
+        wbase[w] = t;
+        t += c;
+      }
+      const int b0 = t ? atomicAdd(&g.counters[C_NBRICKS], t) : 0;
+      for (int w = 0; w < nwarps; ++w) wbase[w] += b0;
+      if (t) atomicAdd(&g.counters[C_NEW_BRICKS], t);
+    }
+    __syncthreads();
+    const int first = wbase[warp];
+    if (lane < kSeg && node >= 0) {
+      const int slot = first + __popc(have & ((1u << lane) - 1u));
       if (slot >= g.cap) {
-        if (lane == 0) set_error(g, kErrOverflow);
+        set_error(g, kErrOverflow);
       } else {
-        if (lane == 0) {
-          init_brick(g, slot, node, bx, by, bz, false);
-          g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] = slot;
-        }
-        __syncwarp();
-        reinterpret_cast<uint16_t*>(g.occ + (size_t)slot * 8)[lane] = (uint16_t)(rows[0] | (rows[1] << 8));
+        init_brick(g, slot, node, bx0 + lane, by, bz, false);
+        g.child[(size_t)node * kNodeBricks + local_brick(bx0 + lane, by, bz)] = slot;
       }
     }
-    if (threadIdx.x == 0 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < kSeg; ++j) {
+      if (!((have >> j) & 1u)) continue;  // warp-uniform
+      const int slot = first + __popc(have & ((1u << j) - 1u));
+      if (slot < g.cap)
+        reinterpret_cast<uint16_t*>(g.occ + (size_t)slot * 8)[lane] = (uint16_t)(rows[j][0] | (rows[j][1] << 8));
+    }
+    __syncthreads();  // wcount / wbase are reused by the next iteration
   }
 }
 
@@ -516,10 +581,12 @@ __global__ void __launch_bounds__(256) k_ingest_dense(VS vs, SRC src) {
 
 template <class VS>
 __global__ void k_clear_masks(VS vs) {
-  const GridView g = vs.get();
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
+       i += (int64_t)nblk * blockDim.x) {
     g.amask[i] = 0u;
     int64_t node = i >> 7, w = i & 127;
     g.mwork[node * 384 + w] = 0u;
@@ -530,9 +597,11 @@ __global__ void k_clear_masks(VS vs) {
 
 template <class VS>
 __global__ void k_obstacle_flags(VS vs) {
-  const GridView g = vs.get();
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  (void)gi;
   const int nb = min(g.counters[C_NBRICKS], g.cap);
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
+  for (int s = bid * blockDim.x + threadIdx.x; s < nb; s += nblk * blockDim.x) {
     bool obst = brick_has_obstacle(g, s);
     uint32_t f = g.bflags[s];
     g.bflags[s] = obst ? (f | F_OBST) : (f & ~F_OBST);
@@ -547,11 +616,13 @@ __global__ void k_obstacle_flags(VS vs) {
 // One warp per node holding obstacle bricks: create the nodes within ceil(R / 16) nodes of it.
 template <class VS>
 __global__ void k_node_halo(VS vs) {
-  const GridView g = vs.get();
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int lane = threadIdx.x & 31;
   const int NR = (g.R + 15) / 16, side = 2 * NR + 1;
-  for (int node = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; node < nn; node += (gridDim.x * blockDim.x) >> 5) {
+  for (int node = (bid * blockDim.x + threadIdx.x) >> 5; node < nn; node += (nblk * blockDim.x) >> 5) {
     const uint32_t* om = g.mwork + (size_t)node * 384;
     uint32_t any = om[lane] | om[lane + 32] | om[lane + 64] | om[lane + 96];
     if (!__any_sync(0xffffffffu, any != 0u)) continue;
@@ -579,12 +650,14 @@ __device__ __forceinline__ int node_at(const GridView& g, int x, int y, int z) {
 // to the grid.  One thread per (node, mask word), i.e. two rows.
 template <int AXIS, class VS>
 __global__ void k_dilate_stage(VS vs) {
-  const GridView g = vs.get();
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int R = g.R;
   const int src_off = AXIS * 128;  // obstacle bits, then stage 1, then stage 2
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
+       i += (int64_t)nblk * blockDim.x) {
     const int node = (int)(i >> 7), w = (int)(i & 127);
     const int key = g.node_key[node];
     const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
@@ -641,6 +714,70 @@ __global__ void k_dilate_stage(VS vs) {
   }
 }
 
+// The whole dilation of one node in one block (R <= 16, so the neighbourhood is the 3 x 3 x 3 nodes
+// around it): the obstacle rows of the 3 x 3 node columns along y and z are dilated along x
+// (48-bit rows across the three nodes along x), then along y, then along z, in shared memory, and
+// the node's own 16 x 16 rows are clipped to the grid and written.  Replaces the three separable
+// stage launches.
+template <class VS>
+__global__ void __launch_bounds__(256) k_dilate_nodes(VS vs) {
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  (void)gi;
+  __shared__ int nbr[27];
+  __shared__ uint16_t X[48][48];  // [z' + 16][y' + 16]: rows dilated along x
+  __shared__ uint16_t Y[48][16];  // [z' + 16][y]: then along y
+  const int nn = min(g.counters[C_NNODES], g.node_cap);
+  const int R = g.R;
+  for (int node = bid; node < nn; node += nblk) {
+    const int key = g.node_key[node];
+    const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+    if (threadIdx.x < 27) {
+      const int t = threadIdx.x, dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+      nbr[t] = (dx | dy | dz) == 0 ? node : node_at(g, nxn + dx, nyn + dy, nzn + dz);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < 48 * 48; r += blockDim.x) {
+      const int zq = r / 48 - 16, yq = r % 48 - 16;
+      const int dy = yq < 0 ? -1 : (yq >= 16 ? 1 : 0), dz = zq < 0 ? -1 : (zq >= 16 ? 1 : 0);
+      const int y = yq - 16 * dy, z = zq - 16 * dz;
+      unsigned long long w = 0ull;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int nb = nbr[(dx + 1) + 3 * ((dy + 1) + 3 * (dz + 1))];
+        if (nb >= 0) w |= (unsigned long long)row16(g.mwork + (size_t)nb * 384, y, z) << (16 * (dx + 1));
+      }
+      unsigned long long d = w;
+      for (int sft = 1; sft <= R; ++sft) d |= (w << sft) | (w >> sft);
+      X[zq + 16][yq + 16] = (uint16_t)(d >> 16);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < 48 * 16; r += blockDim.x) {
+      const int zi = r / 16, y = r % 16;
+      uint32_t o = 0u;
+      for (int d = -R; d <= R; ++d) o |= X[zi][y + d + 16];
+      Y[zi][y] = (uint16_t)o;
+    }
+    __syncthreads();
+    if (threadIdx.x < 128) {
+      const int w = threadIdx.x, z = w >> 3;
+      uint32_t out = 0u;
+      for (int half = 0; half < 2; ++half) {
+        const int y = 2 * (w & 7) + half;
+        uint32_t r = 0u;
+        for (int d = -R; d <= R; ++d) r |= Y[z + d + 16][y];
+        const int gy = nyn * 16 + y, gz = nzn * 16 + z;
+        if (gy >= g.BY || gz >= g.BZ) r = 0u;
+        const int xs = g.BX - nxn * 16;
+        if (xs < 16) r &= (xs <= 0) ? 0u : ((1u << xs) - 1u);
+        out |= r << (16 * half);
+      }
+      g.amask[(size_t)node * 128 + w] = out;
+    }
+    __syncthreads();
+  }
+}
+
 // Mark bricks within Chebyshev radius R of brick (bx,by,bz) in amask: one (dy, dz) row (used by the
 // incremental form, where few bricks change).
 __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int dy, int dz) {
@@ -666,9 +803,11 @@ __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int
 // per thread, one atomic per block for the slot range (block scan of the per-thread counts).
 template <class VS>
 __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
-  const GridView g = vs.get();
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
-  for (int b = blockIdx.x; b < nn * 8; b += gridDim.x) {
+  for (int b = bid; b < nn * 8; b += nblk) {
     const int node = b >> 3, chunk = b & 7;
     const int l0 = chunk * 512 + threadIdx.x * 2;
     const uint32_t word = g.amask[(size_t)node * 128 + (l0 >> 5)];
@@ -726,7 +865,9 @@ __device__ __forceinline__ void queue_run(const GridView& g, int axis, int bx, i
 // (R <= 6 < 16, so the halo reaches at most one node each way), one slot per thread.
 template <class VS>
 __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int rz, Items it, bool with_slots) {
-  const GridView g = vs.get();
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  (void)gi;
   __shared__ int wsum[8];
   __shared__ int base_sh, count_sh;
   __shared__ int nbr_sh[2];
@@ -734,7 +875,7 @@ __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int 
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int R = g.R;
-  for (int b = blockIdx.x; b < nn * 12; b += gridDim.x) {
+  for (int b = bid; b < nn * 12; b += nblk) {
     const int node = b / 12, axis = (b % 12) / 4, qrun = b % 4;
     const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
     if (qrun >= 16 / run) continue;  // block-uniform
@@ -1027,11 +1168,7 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
 }
 
 cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st) {
-  int64_t nbr = (int64_t)g.BX * g.BY * g.BZ;
-  int64_t threads = nbr * 32;
-  unsigned blocks = blocks_for(threads);
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  VDB_LAUNCH((k_ingest_dense<OneView, OneSrc>), blocks, kT, 0, st, OneView{g}, OneSrc{grid});
+  VDB_LAUNCH((k_ingest_dense<OneView, OneSrc>), batch_blocks(g, BK_DENSE), kT, 0, st, OneView{g}, OneSrc{grid});
   return cudaGetLastError();
 }
 
@@ -1040,9 +1177,13 @@ cudaError_t launch_activation_full(const GridView& g, cudaStream_t st) {
   VDB_LAUNCH(k_clear_masks<OneView>, 256, kT, 0, st, v);
   VDB_LAUNCH(k_obstacle_flags<OneView>, 1024, kT, 0, st, v);
   VDB_LAUNCH(k_node_halo<OneView>, 64, kT, 0, st, v);
-  VDB_LAUNCH((k_dilate_stage<0, OneView>), 256, kT, 0, st, v);
-  VDB_LAUNCH((k_dilate_stage<1, OneView>), 256, kT, 0, st, v);
-  VDB_LAUNCH((k_dilate_stage<2, OneView>), 256, kT, 0, st, v);
+  if (g.R <= 16) {
+    VDB_LAUNCH(k_dilate_nodes<OneView>, g.node_cap < 1024 ? g.node_cap : 1024, 256, 0, st, v);
+  } else {
+    VDB_LAUNCH((k_dilate_stage<0, OneView>), 256, kT, 0, st, v);
+    VDB_LAUNCH((k_dilate_stage<1, OneView>), 256, kT, 0, st, v);
+    VDB_LAUNCH((k_dilate_stage<2, OneView>), 256, kT, 0, st, v);
+  }
   VDB_LAUNCH(k_alloc_marked<OneView>, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, v, false);
   return cudaGetLastError();
 }
@@ -1066,11 +1207,30 @@ cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& i
 }
 
 // ---- batches ----
+static int clamp_blocks(int64_t n, int hi) { return (int)(n < 1 ? 1 : (n > hi ? hi : n)); }
+
+int batch_blocks(const GridView& g, int kind) {
+  const int64_t t = kT;
+  switch (kind) {
+    case BK_RESET: return clamp_blocks(((int64_t)g.node_cap * kNodeBricks + g.hmask + t) / t, 1024);
+    case BK_DENSE: {
+      const int64_t nseg = (int64_t)((g.BX + kSeg - 1) / kSeg) * g.BY * g.BZ;
+      return clamp_blocks((nseg * 32 + t - 1) / t, 152 * 64);
+    }
+    case BK_CLEAR: return clamp_blocks(((int64_t)g.node_cap * 128 + t - 1) / t, 256);
+    case BK_OBST: return clamp_blocks(((int64_t)g.cap + t - 1) / t, 1024);
+    case BK_HALO: return clamp_blocks(((int64_t)g.node_cap * 32 + t - 1) / t, 64);
+    case BK_DILATE: return clamp_blocks(g.node_cap, 1024);
+    case BK_ALLOC: return clamp_blocks((int64_t)g.node_cap * 8, 8192);
+    case BK_ITEMS: return clamp_blocks((int64_t)g.node_cap * 12, 8192);
+  }
+  return 1;
+}
+
 cudaError_t launch_reset_batch(const GridView* views, const BatchShape& b, int32_t* counters_all, size_t n_counters,
                                cudaStream_t st) {
   if (b.k <= 0) return cudaSuccess;
-  const BatchViews v{views};
-  VDB_LAUNCH(k_reset_nodes<BatchViews>, dim3(1024, b.k), kT, 0, st, v);
+  VDB_LAUNCH(k_reset_nodes<BatchViews>, b.total[BK_RESET], kT, 0, st, BatchViews{views, b.first[BK_RESET], b.k});
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaMemsetAsync(counters_all, 0, sizeof(int32_t) * n_counters, st);
@@ -1082,27 +1242,26 @@ cudaError_t launch_ingest_dense_batch(const GridView* views, const BatchShape& b
   if (b.k > kBatchMax) return cudaErrorInvalidValue;
   BatchSrc src;
   for (int i = 0; i < kBatchMax; ++i) src.p[i] = i < b.k ? srcs[i] : nullptr;
-  unsigned blocks = blocks_for(b.max_grid_bricks * 32);
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  VDB_LAUNCH((k_ingest_dense<BatchViews, BatchSrc>), dim3(blocks, b.k), kT, 0, st, BatchViews{views}, src);
+  VDB_LAUNCH((k_ingest_dense<BatchViews, BatchSrc>), b.total[BK_DENSE], kT, 0, st,
+             BatchViews{views, b.first[BK_DENSE], b.k}, src);
   return cudaGetLastError();
 }
 
 cudaError_t launch_activation_batch(const GridView* views, const BatchShape& b, cudaStream_t st) {
   if (b.k <= 0) return cudaSuccess;
-  const BatchViews v{views};
-  const unsigned node_words = blocks_for((int64_t)b.max_node_cap * 128);
-  const unsigned bricks = blocks_for(b.max_cap);
-  const unsigned halo = blocks_for((int64_t)b.max_node_cap * 32);
-  const unsigned c256 = node_words < 256 ? node_words : 256;
-  VDB_LAUNCH(k_clear_masks<BatchViews>, dim3(c256, b.k), kT, 0, st, v);
-  VDB_LAUNCH(k_obstacle_flags<BatchViews>, dim3(bricks < 1024 ? bricks : 1024, b.k), kT, 0, st, v);
-  VDB_LAUNCH(k_node_halo<BatchViews>, dim3(halo < 64 ? halo : 64, b.k), kT, 0, st, v);
-  VDB_LAUNCH((k_dilate_stage<0, BatchViews>), dim3(c256, b.k), kT, 0, st, v);
-  VDB_LAUNCH((k_dilate_stage<1, BatchViews>), dim3(c256, b.k), kT, 0, st, v);
-  VDB_LAUNCH((k_dilate_stage<2, BatchViews>), dim3(c256, b.k), kT, 0, st, v);
-  const int chunks = b.max_node_cap * 8 < 8192 ? b.max_node_cap * 8 : 8192;
-  VDB_LAUNCH(k_alloc_marked<BatchViews>, dim3(chunks, b.k), kT, 0, st, v, false);
+  VDB_LAUNCH(k_clear_masks<BatchViews>, b.total[BK_CLEAR], kT, 0, st, BatchViews{views, b.first[BK_CLEAR], b.k});
+  VDB_LAUNCH(k_obstacle_flags<BatchViews>, b.total[BK_OBST], kT, 0, st, BatchViews{views, b.first[BK_OBST], b.k});
+  VDB_LAUNCH(k_node_halo<BatchViews>, b.total[BK_HALO], kT, 0, st, BatchViews{views, b.first[BK_HALO], b.k});
+  const BatchViews dv{views, b.first[BK_DILATE], b.k};
+  if (b.R <= 16) {
+    VDB_LAUNCH(k_dilate_nodes<BatchViews>, b.total[BK_DILATE], 256, 0, st, dv);
+  } else {
+    VDB_LAUNCH((k_dilate_stage<0, BatchViews>), b.total[BK_DILATE], kT, 0, st, dv);
+    VDB_LAUNCH((k_dilate_stage<1, BatchViews>), b.total[BK_DILATE], kT, 0, st, dv);
+    VDB_LAUNCH((k_dilate_stage<2, BatchViews>), b.total[BK_DILATE], kT, 0, st, dv);
+  }
+  VDB_LAUNCH(k_alloc_marked<BatchViews>, b.total[BK_ALLOC], kT, 0, st, BatchViews{views, b.first[BK_ALLOC], b.k},
+             false);
   return cudaGetLastError();
 }
 
@@ -1111,9 +1270,8 @@ cudaError_t launch_build_items_batch(const GridView* views, const BatchShape& b,
   if (b.k <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(items_ctr, 0, 3 * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  const int blocks = b.max_node_cap * 12 < 8192 ? b.max_node_cap * 12 : 8192;
-  VDB_LAUNCH(k_items_nodes<BatchViews>, dim3(blocks, b.k), kT, 0, st, BatchViews{views}, t.run[0], t.run[1], t.run[2],
-             it, true);
+  VDB_LAUNCH(k_items_nodes<BatchViews>, b.total[BK_ITEMS], kT, 0, st, BatchViews{views, b.first[BK_ITEMS], b.k},
+             t.run[0], t.run[1], t.run[2], it, true);
   return cudaGetLastError();
 }
 

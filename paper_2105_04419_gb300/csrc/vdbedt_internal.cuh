@@ -290,11 +290,18 @@ cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& i
 // The same steps for every grid of a batch at once (one launch per step; views: device array of
 // the k grids' views; the grid of a block is blockIdx.y).  `big` is a view with the largest
 // node and brick capacities of the batch (it sizes the launches).
+// Kernels that run once per grid: in a batch each grid gets a share of one launch sized to its
+// work (batch_blocks), the shares laid end to end (first[kind][i] = first block of grid i).
+enum BatchKind { BK_RESET = 0, BK_DENSE, BK_CLEAR, BK_OBST, BK_HALO, BK_DILATE, BK_ALLOC, BK_ITEMS, BK_NUM };
+int batch_blocks(const GridView& g, int kind);
 struct BatchShape {
   int k;
+  int R;  // brick radius (common to the batch)
   int max_node_cap;
   int max_cap;
   int64_t max_grid_bricks;  // largest BX * BY * BZ
+  const int* first[BK_NUM];  // device arrays of k + 1 block offsets per kind
+  int total[BK_NUM];         // blocks of the launch per kind
 };
 cudaError_t launch_reset_batch(const GridView* views, const BatchShape& b, int32_t* counters_all, size_t n_counters,
                                cudaStream_t st);
