@@ -462,7 +462,7 @@ vdbedt_status vdbedt_set_occupancy_dense(vdbedt_handle h, const uint8_t* grid, i
     CK(h, cudaMemcpyAsync(h->io.buf, grid, bytes, cudaMemcpyHostToDevice, h->st), "h2d");
     src = (const uint8_t*)h->io.buf;
   }
-  CK(h, launch_ingest_dense(h->g, src, h->st), "dense ingest");
+  CK(h, launch_ingest_dense(h->g, src, h->scr, h->st), "dense ingest");
   if (!on_device) CK(h, cudaStreamSynchronize(h->st), "sync");
   h->dense_pending = true;
   return VDBEDT_OK;
@@ -700,6 +700,10 @@ struct vdbedt_batch {
   GridView* d_views = nullptr;   // the k grids' views in device memory
   BatchShape shape{};
   Scratch io;
+  Scratch scr;                     // dense-ingest scratch (all grids)
+  size_t dense_bytes = 0;          // its size
+  int64_t* d_dense_off = nullptr;  // per grid: mask, brick-flag, node-flag element offsets
+  size_t dense_nflag_byte = 0, dense_nflag_words = 0;
   Tuning tune;
   std::string err;
   bool profiling = false;
@@ -723,6 +727,7 @@ void destroy_batch(vdbedt_batch* b) {
   for (vdbedt_map* m : b->maps) destroy_impl(m);
   for (void* p : b->allocs) cudaFree(p);
   if (b->io.buf) cudaFree(b->io.buf);
+  if (b->scr.buf) cudaFree(b->scr.buf);
   for (int i = 0; i < 6; ++i)
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   if (b->own_stream && b->st) cudaStreamDestroy(b->st);
@@ -910,6 +915,31 @@ vdbedt_status vdbedt_batch_create(const vdbedt_config* cfgs, int32_t k, vdbedt_b
     e = cudaMemcpy(d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(e, "block shares");
     for (int kind = 0; kind < BK_NUM; ++kind) b->shape.first[kind] = d_first + (size_t)kind * (k + 1);
+    // dense-ingest scratch layout: every grid's masks, then brick flags, then node flags
+    size_t nbr_all = 0, nkeys_all = 0;
+    for (const GridView& v : views) {
+      nbr_all += (size_t)v.BX * v.BY * v.BZ;
+      nkeys_all += (size_t)v.NX * v.NY * v.NZ;
+    }
+    const size_t dbytes = (nbr_all * 64 + 255) & ~(size_t)255, fbytes = (nbr_all * 4 + 255) & ~(size_t)255;
+    std::vector<int64_t> off((size_t)3 * k);
+    size_t nb = 0, nk = 0;
+    for (int i = 0; i < k; ++i) {
+      const GridView& v = views[(size_t)i];
+      off[(size_t)3 * i] = (int64_t)(nb * 8);                     // u64 elements
+      off[(size_t)3 * i + 1] = (int64_t)((dbytes + nb * 4) / 4);  // int32 elements
+      off[(size_t)3 * i + 2] = (int64_t)((dbytes + fbytes + nk * 4) / 4);
+      nb += (size_t)v.BX * v.BY * v.BZ;
+      nk += (size_t)v.NX * v.NY * v.NZ;
+    }
+    b->dense_nflag_byte = dbytes + fbytes;
+    b->dense_nflag_words = nkeys_all;
+    b->dense_bytes = dbytes + fbytes + ((nkeys_all * 4 + 255) & ~(size_t)255);
+    e = cudaMalloc((void**)&b->d_dense_off, sizeof(int64_t) * off.size());
+    if (e != cudaSuccess) return bail(e, "device alloc");
+    b->allocs.push_back(b->d_dense_off);
+    e = cudaMemcpy(b->d_dense_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(e, "dense offsets");
   }
   // the pool view: shape fields of grid 0 (dmax, R, INF are common), the batch's words and lists
   {
@@ -977,7 +1007,10 @@ vdbedt_status vdbedt_batch_set_occupancy_dense(vdbedt_batch_handle b, const uint
       off += (bytes + 255) & ~(size_t)255;
     }
   }
-  BCK(b, launch_ingest_dense_batch(b->d_views, b->shape, src.data(), b->st), "dense ingest");
+  BCK(b, ensure_scratch(b->scr, b->dense_bytes), "dense scratch");
+  BCK(b, launch_ingest_dense_batch(b->d_views, b->shape, src.data(), b->scr.buf, b->d_dense_off, b->dense_nflag_words,
+                                   (int32_t*)((char*)b->scr.buf + b->dense_nflag_byte), b->st),
+      "dense ingest");
   if (!on_device) BCK(b, cudaStreamSynchronize(b->st), "sync");
   return VDBEDT_OK;
 }

@@ -466,14 +466,14 @@ __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t 
 }
 
 // ---- dense ingest ----
-// One warp per segment of kSeg consecutive bricks along x: each lane builds two x-rows (y, z) of
-// the segment's masks, loading each row's 8 * kSeg bytes as 8-byte words when rows are 8-byte
-// aligned (so the warp's loads cover whole 32-byte sectors).  The grid was reset just before, so
-// every brick is claimed by exactly one warp: the block counts its warps' occupied bricks and
-// reserves their slots with one atomic; brick fields are left for the global transform that
-// always follows a dense ingest.
-constexpr int kSeg = 4;
-
+// Two streaming passes.  (1) Masks: one warp per 4 consecutive bricks along x; lane (b, z) reads the
+// 8 x-rows (y = 0..7) of brick b at depth z, 8 bytes each (one 8-byte load when rows are 8-byte
+// aligned), so every load instruction covers whole 32-byte sectors and the warp writes its
+// bricks' 64-byte masks as 256 contiguous bytes of a dense per-brick scratch, with one flag per
+// brick and one per node key.  (2) After the flagged nodes are created, one thread per brick of
+// the grid allocates the occupied bricks (slots reserved with one atomic per block) and copies
+// their masks in.  The grid was reset just before, so every brick is new; brick fields are left
+// for the global transform that always follows a dense ingest.
 __device__ __forceinline__ uint32_t nonzero_bytes(unsigned long long w) {
   // bit i = byte i nonzero: fold each byte onto its low bit, then gather the eight low bits
   w |= w >> 4;
@@ -483,93 +483,145 @@ __device__ __forceinline__ uint32_t nonzero_bytes(unsigned long long w) {
   return (uint32_t)((w * 0x0102040810204080ull) >> 56);
 }
 
+// Scratch of the dense ingest: masks (8 words per brick of the grid), brick flags, node-key flags.
+// A single grid's pointers are its own; grid i of a batch adds off[3i], off[3i + 1], off[3i + 2].
+struct DenseScratch {
+  unsigned long long* dbits;
+  int32_t* flag;
+  int32_t* nflag;
+  const int64_t* off;  // nullptr for a single grid
+  __device__ __forceinline__ void at(int gi, unsigned long long*& d, int32_t*& f, int32_t*& nf) const {
+    d = dbits;
+    f = flag;
+    nf = nflag;
+    if (off) {
+      d += off[3 * gi];
+      f += off[3 * gi + 1];
+      nf += off[3 * gi + 2];
+    }
+  }
+};
+
 template <class VS, class SRC>
-__global__ void __launch_bounds__(256) k_ingest_dense(VS vs, SRC src) {
+__global__ void __launch_bounds__(256) k_dense_masks(VS vs, SRC src, DenseScratch ds) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   const uint8_t* __restrict__ grid = src.get(gi);
-  const int SX = (g.BX + kSeg - 1) / kSeg;  // segments per brick row
-  const int64_t nseg = (int64_t)SX * g.BY * g.BZ;
+  unsigned long long* dbits;
+  int32_t* flag;
+  int32_t* nflag;
+  ds.at(gi, dbits, flag, nflag);
+  const int SX = (g.BX + 3) / 4;
+  const int64_t nunits = (int64_t)SX * g.BY * g.BZ;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int b = lane >> 3, z = lane & 7;
   const bool vec = (g.nx % 8) == 0 && (reinterpret_cast<uintptr_t>(grid) & 7u) == 0;
-  __shared__ int wcount[32];
-  __shared__ int wbase[32];
-  for (int64_t base = (int64_t)bid * nwarps; base < nseg; base += (int64_t)nblk * nwarps) {
-    const int64_t sg = base + warp;
-    int bx0 = 0, by = 0, bz = 0;
-    uint32_t rows[kSeg][2];
+  for (int64_t u = (int64_t)bid * nwarps + warp; u < nunits; u += (int64_t)nblk * nwarps) {
+    const int bx = (int)(u % SX) * 4 + b;
+    const int by = (int)((u / SX) % g.BY), bz = (int)(u / ((int64_t)SX * g.BY));
+    const int gz = bz * 8 + z, x0 = bx * 8;
+    unsigned long long word = 0ull;  // bits x + 8 y of depth z
+    if (bx < g.BX && gz < g.nz) {
+      const int nxv = min(8, g.nx - x0);
 #pragma unroll
-    for (int j = 0; j < kSeg; ++j) rows[j][0] = rows[j][1] = 0u;
-    if (sg < nseg) {
-      bx0 = (int)(sg % SX) * kSeg;
-      by = (int)((sg / SX) % g.BY);
-      bz = (int)(sg / ((int64_t)SX * g.BY));
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int r = lane * 2 + q;  // byte index y + 8 z within a brick
-        const int gy = by * 8 + (r & 7), gz = bz * 8 + (r >> 3);
-        if (gy < g.ny && gz < g.nz) {
-          const uint8_t* row = grid + ((size_t)gz * g.ny + gy) * g.nx + (size_t)bx0 * 8;
-#pragma unroll
-          for (int j = 0; j < kSeg; ++j) {
-            const int x0 = (bx0 + j) * 8;
-            if (x0 < g.nx) {
-              if (vec) {
-                rows[j][q] = nonzero_bytes(__ldg(reinterpret_cast<const unsigned long long*>(row + 8 * j)));
-              } else {
-                const int nxv = min(8, g.nx - x0);
-                uint32_t v = 0u;
-                for (int x = 0; x < nxv; ++x) v |= (uint32_t)(row[8 * j + x] != 0) << x;
-                rows[j][q] = v;
-              }
-            }
+      for (int y = 0; y < 8; ++y) {
+        const int gy = by * 8 + y;
+        if (gy < g.ny) {
+          const uint8_t* row = grid + ((size_t)gz * g.ny + gy) * g.nx + x0;
+          uint32_t bits;
+          if (vec) {
+            bits = nonzero_bytes(__ldg(reinterpret_cast<const unsigned long long*>(row)));
+          } else {
+            bits = 0u;
+            for (int x = 0; x < nxv; ++x) bits |= (uint32_t)(row[x] != 0) << x;
           }
+          word |= (unsigned long long)bits << (8 * y);
         }
       }
     }
-    // bricks of the segment holding an obstacle (false past the grid)
-    uint32_t occupied = 0u;
-#pragma unroll
-    for (int j = 0; j < kSeg; ++j)
-      occupied |= (__any_sync(0xffffffffu, (rows[j][0] | rows[j][1]) != 0u) ? 1u : 0u) << j;
-    // lane j finds brick j's node (nodes are shared, so look-ups mostly hit published entries)
-    int node = -1;
-    if (lane < kSeg && ((occupied >> lane) & 1u))
-      node = get_or_create_node(g, (uint32_t)node_key_of(g, bx0 + lane, by, bz));
-    const unsigned have = __ballot_sync(0xffffffffu, node >= 0) & ((1u << kSeg) - 1u);
-    if (lane == 0) wcount[warp] = __popc(have);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int t = 0;
-      for (int w = 0; w < nwarps; ++w) {
-        const int c = wcount[w];
-        wbase[w] = t;
-        t += c;
+    const int64_t lb = bx + (int64_t)g.BX * (by + (int64_t)g.BY * bz);
+    if (bx < g.BX) dbits[lb * 8 + z] = word;
+    const unsigned nz8 = (__ballot_sync(0xffffffffu, word != 0ull) >> (8 * b)) & 0xFFu;
+    if (z == 0 && bx < g.BX) {
+      flag[lb] = nz8 ? 1 : 0;
+      if (nz8) {
+        const int nk = node_key_of(g, bx, by, bz);
+        if (!nflag[nk]) nflag[nk] = 1;
       }
-      const int b0 = t ? atomicAdd(&g.counters[C_NBRICKS], t) : 0;
-      for (int w = 0; w < nwarps; ++w) wbase[w] += b0;
-      if (t) atomicAdd(&g.counters[C_NEW_BRICKS], t);
     }
-    __syncthreads();
-    const int first = wbase[warp];
-    if (lane < kSeg && node >= 0) {
-      const int slot = first + __popc(have & ((1u << lane) - 1u));
+  }
+}
+
+// Nodes of flagged keys, one thread per key (each key inserted by exactly one thread; indices come
+// from one atomic per block): no insertion ever waits on another.
+template <class VS>
+__global__ void __launch_bounds__(256) k_dense_nodes(VS vs, DenseScratch ds) {
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  unsigned long long* dbits;
+  int32_t* flag;
+  int32_t* nflag;
+  ds.at(gi, dbits, flag, nflag);
+  const int64_t nkeys = (int64_t)g.NX * g.NY * g.NZ;
+  for (int64_t base = (int64_t)bid * blockDim.x; base < nkeys; base += (int64_t)nblk * blockDim.x) {
+    const int64_t k = base + threadIdx.x;
+    bool need = false;
+    if (k < nkeys && nflag[k]) {
+      nflag[k] = 0;
+      need = find_node(g, (uint32_t)k) < 0;
+    }
+    const int idx = block_agg_add(&g.counters[C_NNODES], need, nullptr);
+    if (need) {
+      if (idx >= g.node_cap) {
+        set_error(g, kErrNodeOverflow);
+      } else {
+        g.node_key[idx] = (int32_t)k;
+        const unsigned long long word = ((unsigned long long)(uint32_t)k << 32) | (uint32_t)idx;
+        uint32_t h = hash32((uint32_t)k) & g.hmask;
+        bool placed = false;
+        for (uint32_t probe = 0; probe <= g.hmask && !placed; ++probe) {
+          placed = atomicCAS(&g.hslots[h], ~0ull, word) == ~0ull;
+          h = (h + 1) & g.hmask;
+        }
+        if (!placed) set_error(g, kErrNodeOverflow);
+      }
+    }
+  }
+}
+
+template <class VS>
+__global__ void __launch_bounds__(256) k_dense_alloc(VS vs, DenseScratch ds) {
+  int bid, nblk, gi;
+  const GridView g = vs.get(bid, nblk, gi);
+  unsigned long long* dbits;
+  int32_t* flag;
+  int32_t* nflag;
+  ds.at(gi, dbits, flag, nflag);
+  const int64_t nbr = (int64_t)g.BX * g.BY * g.BZ;
+  for (int64_t base = (int64_t)bid * blockDim.x; base < nbr; base += (int64_t)nblk * blockDim.x) {
+    const int64_t lb = base + threadIdx.x;
+    int node = -1, bx = 0, by = 0, bz = 0;
+    if (lb < nbr && flag[lb]) {
+      bx = (int)(lb % g.BX);
+      by = (int)((lb / g.BX) % g.BY);
+      bz = (int)(lb / ((int64_t)g.BX * g.BY));
+      node = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+    }
+    int total = 0;
+    const int slot = block_agg_add(&g.counters[C_NBRICKS], node >= 0, &total);
+    if (node >= 0) {
       if (slot >= g.cap) {
         set_error(g, kErrOverflow);
       } else {
-        init_brick(g, slot, node, bx0 + lane, by, bz, false);
-        g.child[(size_t)node * kNodeBricks + local_brick(bx0 + lane, by, bz)] = slot;
+        init_brick(g, slot, node, bx, by, bz, false);
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(dbits + lb * 8);
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(g.occ + (size_t)slot * 8);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = src[q];
+        g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] = slot;
       }
     }
-    __syncwarp();
-#pragma unroll
-    for (int j = 0; j < kSeg; ++j) {
-      if (!((have >> j) & 1u)) continue;  // warp-uniform
-      const int slot = first + __popc(have & ((1u << j) - 1u));
-      if (slot < g.cap)
-        reinterpret_cast<uint16_t*>(g.occ + (size_t)slot * 8)[lane] = (uint16_t)(rows[j][0] | (rows[j][1] << 8));
-    }
-    __syncthreads();  // wcount / wbase are reused by the next iteration
+    if (threadIdx.x == 0 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
   }
 }
 
@@ -1167,8 +1219,24 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
   return cudaGetLastError();
 }
 
-cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st) {
-  VDB_LAUNCH((k_ingest_dense<OneView, OneSrc>), batch_blocks(g, BK_DENSE), kT, 0, st, OneView{g}, OneSrc{grid});
+size_t dense_scratch_bytes(const GridView& g) {
+  const size_t nbr = (size_t)g.BX * g.BY * g.BZ, nkeys = (size_t)g.NX * g.NY * g.NZ;
+  return align_up(nbr * 64) + align_up(nbr * 4) + align_up(nkeys * 4);
+}
+
+cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, Scratch& scr, cudaStream_t st) {
+  cudaError_t e = ensure_scratch(scr, dense_scratch_bytes(g));
+  if (e != cudaSuccess) return e;
+  const size_t nbr = (size_t)g.BX * g.BY * g.BZ, nkeys = (size_t)g.NX * g.NY * g.NZ;
+  char* p = (char*)scr.buf;
+  DenseScratch ds{(unsigned long long*)p, (int32_t*)(p + align_up(nbr * 64)),
+                  (int32_t*)(p + align_up(nbr * 64) + align_up(nbr * 4)), nullptr};
+  e = cudaMemsetAsync(ds.nflag, 0, nkeys * 4, st);
+  if (e != cudaSuccess) return e;
+  const OneView v{g};
+  VDB_LAUNCH((k_dense_masks<OneView, OneSrc>), batch_blocks(g, BK_DENSE), kT, 0, st, v, OneSrc{grid}, ds);
+  VDB_LAUNCH(k_dense_nodes<OneView>, batch_blocks(g, BK_DNODES), kT, 0, st, v, ds);
+  VDB_LAUNCH(k_dense_alloc<OneView>, batch_blocks(g, BK_DALLOC), kT, 0, st, v, ds);
   return cudaGetLastError();
 }
 
@@ -1214,9 +1282,11 @@ int batch_blocks(const GridView& g, int kind) {
   switch (kind) {
     case BK_RESET: return clamp_blocks(((int64_t)g.node_cap * kNodeBricks + g.hmask + t) / t, 1024);
     case BK_DENSE: {
-      const int64_t nseg = (int64_t)((g.BX + kSeg - 1) / kSeg) * g.BY * g.BZ;
-      return clamp_blocks((nseg * 32 + t - 1) / t, 152 * 64);
+      const int64_t units = (int64_t)((g.BX + 3) / 4) * g.BY * g.BZ;  // a warp each
+      return clamp_blocks((units * 32 + t - 1) / t, 152 * 64);
     }
+    case BK_DNODES: return clamp_blocks(((int64_t)g.NX * g.NY * g.NZ + t - 1) / t, 1024);
+    case BK_DALLOC: return clamp_blocks(((int64_t)g.BX * g.BY * g.BZ + t - 1) / t, 152 * 64);
     case BK_CLEAR: return clamp_blocks(((int64_t)g.node_cap * 128 + t - 1) / t, 256);
     case BK_OBST: return clamp_blocks(((int64_t)g.cap + t - 1) / t, 1024);
     case BK_HALO: return clamp_blocks(((int64_t)g.node_cap * 32 + t - 1) / t, 64);
@@ -1237,13 +1307,20 @@ cudaError_t launch_reset_batch(const GridView* views, const BatchShape& b, int32
 }
 
 cudaError_t launch_ingest_dense_batch(const GridView* views, const BatchShape& b, const uint8_t* const* srcs,
+                                      void* scratch, const int64_t* offsets, size_t nflag_words, int32_t* nflag0,
                                       cudaStream_t st) {
   if (b.k <= 0) return cudaSuccess;
   if (b.k > kBatchMax) return cudaErrorInvalidValue;
   BatchSrc src;
   for (int i = 0; i < kBatchMax; ++i) src.p[i] = i < b.k ? srcs[i] : nullptr;
-  VDB_LAUNCH((k_ingest_dense<BatchViews, BatchSrc>), b.total[BK_DENSE], kT, 0, st,
-             BatchViews{views, b.first[BK_DENSE], b.k}, src);
+  cudaError_t e = cudaMemsetAsync(nflag0, 0, nflag_words * 4, st);
+  if (e != cudaSuccess) return e;
+  char* p = (char*)scratch;
+  DenseScratch ds{(unsigned long long*)p, (int32_t*)p, (int32_t*)p, offsets};
+  VDB_LAUNCH((k_dense_masks<BatchViews, BatchSrc>), b.total[BK_DENSE], kT, 0, st,
+             BatchViews{views, b.first[BK_DENSE], b.k}, src, ds);
+  VDB_LAUNCH(k_dense_nodes<BatchViews>, b.total[BK_DNODES], kT, 0, st, BatchViews{views, b.first[BK_DNODES], b.k}, ds);
+  VDB_LAUNCH(k_dense_alloc<BatchViews>, b.total[BK_DALLOC], kT, 0, st, BatchViews{views, b.first[BK_DALLOC], b.k}, ds);
   return cudaGetLastError();
 }
 

@@ -277,7 +277,9 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
 cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, cudaStream_t st);
 // clear the per-update counters and advance the device-side update epoch
 cudaError_t launch_begin_update(const GridView& g, cudaStream_t st);
-cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, cudaStream_t st);
+// dense grid -> bricks (scratch: dense_scratch_bytes(g))
+size_t dense_scratch_bytes(const GridView& g);
+cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, Scratch& scr, cudaStream_t st);
 cudaError_t launch_activation_full(const GridView& g, cudaStream_t st);
 // every run holding a stored brick, with slot lists when with_slots (half path)
 cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, const Items& it, bool with_slots,
@@ -292,7 +294,9 @@ cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& i
 // node and brick capacities of the batch (it sizes the launches).
 // Kernels that run once per grid: in a batch each grid gets a share of one launch sized to its
 // work (batch_blocks), the shares laid end to end (first[kind][i] = first block of grid i).
-enum BatchKind { BK_RESET = 0, BK_DENSE, BK_CLEAR, BK_OBST, BK_HALO, BK_DILATE, BK_ALLOC, BK_ITEMS, BK_NUM };
+enum BatchKind {
+  BK_RESET = 0, BK_DENSE, BK_DNODES, BK_DALLOC, BK_CLEAR, BK_OBST, BK_HALO, BK_DILATE, BK_ALLOC, BK_ITEMS, BK_NUM
+};
 int batch_blocks(const GridView& g, int kind);
 struct BatchShape {
   int k;
@@ -305,7 +309,11 @@ struct BatchShape {
 };
 cudaError_t launch_reset_batch(const GridView* views, const BatchShape& b, int32_t* counters_all, size_t n_counters,
                                cudaStream_t st);
+// scratch: grid i's masks, brick flags and node flags start offsets[3i], offsets[3i + 1] and
+// offsets[3i + 2] elements (u64, int32, int32) from the scratch base; nflag0 .. nflag0 +
+// nflag_words covers every grid's node flags
 cudaError_t launch_ingest_dense_batch(const GridView* views, const BatchShape& b, const uint8_t* const* srcs,
+                                      void* scratch, const int64_t* offsets, size_t nflag_words, int32_t* nflag0,
                                       cudaStream_t st);
 cudaError_t launch_activation_batch(const GridView* views, const BatchShape& b, cudaStream_t st);
 cudaError_t launch_build_items_batch(const GridView* views, const BatchShape& b, const Tuning& t, const Items& it,
