@@ -162,7 +162,8 @@ struct ColShape {
   static constexpr int THREADS = 32 * (RUN + 1);
   static constexpr size_t DATA_BYTES = (size_t)NS * STAGE_BYTES;
   static constexpr size_t META_BYTES = (size_t)NS * META * 4;
-  static constexpr size_t SMEM = DATA_BYTES + ((META_BYTES + 15) & ~(size_t)15) + 2 * NS * 8 + 16;
+  static constexpr size_t LUT_BYTES = 80;  // x pass: fp16 bits of min(d^2, dmax^2), d = 0..32
+  static constexpr size_t SMEM = DATA_BYTES + ((META_BYTES + 15) & ~(size_t)15) + 2 * NS * 8 + LUT_BYTES + 16;
 };
 
 // x pass of one brick from the staged masks of bricks w .. w + 2R (64 B each; byte y + 8 z is the
@@ -172,24 +173,25 @@ struct ColShape {
 // zeros (left) and of trailing zeros (right).  Otherwise the 64-bit form covers the whole line.
 template <int R>
 __device__ __forceinline__ void x_compute_rows(const GridView& g, const uint32_t (&rows2)[2 * R + 1], int slot,
-                                               uint32_t inf2);
+                                               uint32_t inf2, const uint16_t* lut);
 
 template <int R>
-__device__ __forceinline__ void x_compute(const GridView& g, const uint8_t* masks, int slot, uint32_t inf2) {
+__device__ __forceinline__ void x_compute(const GridView& g, const uint8_t* masks, int slot, uint32_t inf2,
+                                          const uint16_t* lut) {
   constexpr int NBX = 2 * R + 1;
   const int lane = threadIdx.x & 31;
   const int z = lane & 7, y0 = (lane >> 3) * 2;
   uint32_t rows2[NBX];
 #pragma unroll
   for (int b = 0; b < NBX; ++b) rows2[b] = *reinterpret_cast<const uint16_t*>(masks + b * 64 + y0 + 8 * z);
-  x_compute_rows<R>(g, rows2, slot, inf2);
+  x_compute_rows<R>(g, rows2, slot, inf2, lut);
 }
 
 // The x-line computation of one brick from the lane's two mask bytes of each brick of the window
 // (rows2[b]: bits of x-rows y0 (low byte) and y0 + 1 (high byte) at z, brick bx - R + b).
 template <int R>
 __device__ __forceinline__ void x_compute_rows(const GridView& g, const uint32_t (&rows2)[2 * R + 1], int slot,
-                                               uint32_t inf2) {
+                                               uint32_t inf2, const uint16_t* lut) {
   constexpr int NBX = 2 * R + 1;
   const int lane = threadIdx.x & 31;
   const int z = lane & 7, y0 = (lane >> 3) * 2;
@@ -198,22 +200,28 @@ __device__ __forceinline__ void x_compute_rows(const GridView& g, const uint32_t
   bool done = false;
   if constexpr (R <= 4) {
     if (g.dmax <= 32) {
-      // E[r][1 + k] holds line bits 32k .. 32k + 31; E[r][0] = 0 stands for positions -32 .. -1
+      // E[r][1 + k] holds line bits 32k .. 32k + 31; E[r][0] = 0 stands for positions -32 .. -1.
+      // Byte b of the line is brick b's row: gathered with byte permutes (rows y0 and y0 + 1 are
+      // the low and high bytes of rows2[b]).
       uint32_t E[2][5] = {{0u, 0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u, 0u}};
 #pragma unroll
-      for (int b = 0; b < NBX; ++b) {
-        const uint32_t two = rows2[b];
-        E[0][1 + b / 4] |= (two & 0xFFu) << (8 * (b % 4));
-        E[1][1 + b / 4] |= (two >> 8) << (8 * (b % 4));
+      for (int k = 1; k <= 3; ++k) {
+        const int b0 = 4 * (k - 1);
+        if (b0 < NBX) {
+          const uint32_t a = rows2[b0], b = b0 + 1 < NBX ? rows2[b0 + 1] : 0u;
+          const uint32_t c = b0 + 2 < NBX ? rows2[b0 + 2] : 0u, d = b0 + 3 < NBX ? rows2[b0 + 3] : 0u;
+          const uint32_t t01 = __byte_perm(a, b, 0x5140), t23 = __byte_perm(c, d, 0x5140);
+          E[0][k] = __byte_perm(t01, t23, 0x5410);
+          E[1][k] = __byte_perm(t01, t23, 0x7632);
+        }
       }
-      const int inf = g.INF;
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         if ((E[r][1] | E[r][2] | E[r][3]) == 0u) {
           w[r][0] = w[r][1] = w[r][2] = w[r][3] = inf2;
           continue;
         }
-        __half hv[8];
+        uint32_t hv[8];
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
           const int P = 8 * R + x + 32;  // position in E
@@ -221,12 +229,11 @@ __device__ __forceinline__ void x_compute_rows(const GridView& g, const uint32_t
           const uint32_t Lw = __funnelshift_r(E[r][s0 >> 5], E[r][(s0 >> 5) + 1], s0 & 31);  // bit 31 = P
           const uint32_t Rw = __funnelshift_r(E[r][P >> 5], E[r][(P >> 5) + 1], P & 31);      // bit 0 = P
           const int d = min(__clz(Lw), __clz(__brev(Rw)));  // 32 when the side is empty
-          const int best = min(d * d, inf);
-          fin |= best < inf;
-          hv[x] = __int2half_rn(best);
+          fin |= d < g.dmax;                                  // d^2 < dmax^2
+          hv[x] = lut[d];                                     // fp16 bits of min(d^2, dmax^2)
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[r][q] = h2u(__halves2half2(hv[2 * q], hv[2 * q + 1]));
+        for (int q = 0; q < 4; ++q) w[r][q] = hv[2 * q] | (hv[2 * q + 1] << 16);
       }
       done = true;
     }
@@ -350,6 +357,7 @@ __global__ void __launch_bounds__(32 * (RUN + 1), pass_min_blocks(RUN, AXIS))
   int* meta = reinterpret_cast<int*>(smem + S::DATA_BYTES);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::DATA_BYTES + ((S::META_BYTES + 15) & ~(size_t)15));
   uint64_t* empty = full + NS;
+  uint16_t* lut = reinterpret_cast<uint16_t*>(empty + NS);
   const int nitems = min(g.items_ctr[AXIS], max_items);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const __half hinf = __int2half_rn(g.INF);
@@ -359,6 +367,10 @@ __global__ void __launch_bounds__(32 * (RUN + 1), pass_min_blocks(RUN, AXIS))
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], RUN);
     }
+  }
+  if (AXIS == 0 && threadIdx.x <= 32) {
+    const __half h = __int2half_rn(min((int)(threadIdx.x * threadIdx.x), g.INF));
+    lut[threadIdx.x] = *reinterpret_cast<const uint16_t*>(&h);
   }
   __syncthreads();
 
@@ -424,7 +436,7 @@ __global__ void __launch_bounds__(32 * (RUN + 1), pass_min_blocks(RUN, AXIS))
     if (slot >= 0) {
       const unsigned char* stage = data + (size_t)s * S::STAGE_BYTES;
       if (AXIS == 0)
-        x_compute<R>(g, stage + w * 64, slot, inf2);
+        x_compute<R>(g, stage + w * 64, slot, inf2, lut);
       else
         window_compute<R, AXIS>(g, reinterpret_cast<const uint32_t*>(stage), m + NB, slot, w, prune, inf2);
     }
@@ -448,6 +460,12 @@ __global__ void __launch_bounds__(256) k_x_direct(GridView g, const int32_t* __r
   const int64_t total = (int64_t)nitems * run;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned char* occ = reinterpret_cast<const unsigned char*>(g.occ);
+  __shared__ uint16_t lut[33];
+  if (threadIdx.x <= 32) {
+    const __half h = __int2half_rn(min((int)(threadIdx.x * threadIdx.x), g.INF));
+    lut[threadIdx.x] = *reinterpret_cast<const uint16_t*>(&h);
+  }
+  __syncthreads();
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
     const int item = (int)(w / run), j = (int)(w % run);
     const int32_t* sl = islots + (size_t)item * kItemSlots + j;
@@ -460,7 +478,7 @@ __global__ void __launch_bounds__(256) k_x_direct(GridView g, const int32_t* __r
       const int sb = __shfl_sync(0xffffffffu, s, b);
       rows2[b] = sb >= 0 ? (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(occ + (size_t)sb * 64 + y0 + 8 * z)) : 0u;
     }
-    x_compute_rows<R>(g, rows2, slot, inf2);
+    x_compute_rows<R>(g, rows2, slot, inf2, lut);
   }
 }
 
