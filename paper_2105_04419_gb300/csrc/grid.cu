@@ -231,8 +231,8 @@ __global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, 
   const int64_t n = rec_count(n_max, n_dev);
   GRID_STRIDE(i, n) {
     bool zero = false, bad = false;
-    unsigned long long* word = nullptr;
-    unsigned long long bits = 0ull;
+    uint32_t widx = 0xFFFFFFFFu;  // mask word index lb * 8 + z, or none
+    uint32_t blo = 0u, bhi = 0u;  // bit x + 8 y of that word, as two halves
     if (i < n) {
       int4 r = unpack_rec(rec[i]);
       if (!rec_valid(g, r)) {
@@ -245,22 +245,36 @@ __global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, 
           if (!nflag[nk]) nflag[nk] = 1;
         }
         if (dbits) {
-          word = dbits + lb * 8 + (r.z & 7);
-          bits = 1ull << ((r.x & 7) + 8 * (r.y & 7));
+          widx = (uint32_t)(lb * 8 + (r.z & 7));
+          const int bit = (r.x & 7) + 8 * (r.y & 7);
+          if (bit < 32) blo = 1u << bit; else bhi = 1u << (bit - 32);
         }
       } else {
         zero = true;
       }
     }
     if (dbits) {
+      // lanes hitting the same word OR their bits over up to 8 lanes back (runs of equal words are
+      // short: records of one x-row are adjacent); the last lane of each run, and every 8th lane of
+      // a longer run, issues the atomic
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long wp = __shfl_up_sync(0xffffffffu, (unsigned long long)word, o);
-        const unsigned long long bp = __shfl_up_sync(0xffffffffu, bits, o);
-        if (lane >= o && wp == (unsigned long long)word) bits |= bp;
+      for (int o = 1; o < 8; o <<= 1) {
+        const uint32_t wp = __shfl_up_sync(0xffffffffu, widx, o);
+        const uint32_t lp = __shfl_up_sync(0xffffffffu, blo, o);
+        const uint32_t hp = __shfl_up_sync(0xffffffffu, bhi, o);
+        if (lane >= o && wp == widx) {
+          blo |= lp;
+          bhi |= hp;
+        }
       }
-      const unsigned long long wn = __shfl_down_sync(0xffffffffu, (unsigned long long)word, 1);
-      if (word && (lane == 31 || wn != (unsigned long long)word)) atomicOr(word, bits);
+      const uint32_t wprev = __shfl_up_sync(0xffffffffu, widx, 1);
+      const uint32_t wnext = __shfl_down_sync(0xffffffffu, widx, 1);
+      const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || wprev != widx);
+      const unsigned upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+      const int start = 31 - __clz(heads & upto);
+      const bool run_end = lane == 31 || wnext != widx;
+      if (widx != 0xFFFFFFFFu && (run_end || ((lane - start) & 7) == 7))
+        atomicOr(dbits + widx, ((unsigned long long)bhi << 32) | blo);
     }
     if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
     if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
@@ -1114,7 +1128,7 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 static size_t ingest_scratch_bytes(const GridView& g, int64_t n, bool track) {
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
   const bool counting = n >= nbr_all / 4;
-  const bool dense_bits = counting && !track;
+  const bool dense_bits = counting && !track && nbr_all * 8 < (int64_t)0xFFFFFFFFll;
   const int64_t m = n > nbr_all ? n : nbr_all;
   const size_t nb4 = align_up((size_t)m * 4);
   const size_t nkeys_al = ((size_t)g.NX * g.NY * g.NZ + 63) & ~(size_t)63;
@@ -1150,7 +1164,8 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
   if (n <= 0) return cudaSuccess;
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
   const bool counting = n >= nbr_all / 4;
-  const bool dense_bits = counting && !track;
+  // the dense mask is indexed by a 32-bit word number (8 words per brick)
+  const bool dense_bits = counting && !track && nbr_all * 8 < (int64_t)0xFFFFFFFFll;
   const int64_t m = n > nbr_all ? n : nbr_all;
   const size_t nb4 = align_up((size_t)m * 4);
   cudaError_t e = ensure_scratch(scr, ingest_scratch_bytes(g, n, track));
@@ -1193,6 +1208,7 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, flag, pos, (int64_t)nbr, ka);
     VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for((int64_t)nbr), kT, 0, st, g, ka, (int64_t)nbr, track, dbits);
+    if (!track && !dbits) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
   } else {
     // LSD radix sort of the brick keys, unique, compaction
     VDB_LAUNCH(k_rec_brick_keys, nbk, kT, 0, st, g, rec, n, n_dev, ka);
