@@ -889,9 +889,6 @@ vdbedt_status vdbedt_batch_create(const vdbedt_config* cfgs, int32_t k, vdbedt_b
     m->batch = b;
     b->maps.push_back(m);
     views[(size_t)i] = m->g;
-    b->shape.max_node_cap = std::max(b->shape.max_node_cap, m->g.node_cap);
-    b->shape.max_cap = std::max(b->shape.max_cap, m->g.cap);
-    b->shape.max_grid_bricks = std::max<int64_t>(b->shape.max_grid_bricks, (int64_t)m->g.BX * m->g.BY * m->g.BZ);
     off += m->g.cap;
   }
   b->shape.k = k;

@@ -289,9 +289,8 @@ cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const in
 // slot lists of every queued run (half path)
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st);
 
-// The same steps for every grid of a batch at once (one launch per step; views: device array of
-// the k grids' views; the grid of a block is blockIdx.y).  `big` is a view with the largest
-// node and brick capacities of the batch (it sizes the launches).
+// The same steps for every grid of a batch at once: one launch per step (views: device array of
+// the k grids' views; each block finds its grid through the shape's block shares).
 // Kernels that run once per grid: in a batch each grid gets a share of one launch sized to its
 // work (batch_blocks), the shares laid end to end (first[kind][i] = first block of grid i).
 enum BatchKind {
@@ -301,9 +300,6 @@ int batch_blocks(const GridView& g, int kind);
 struct BatchShape {
   int k;
   int R;  // brick radius (common to the batch)
-  int max_node_cap;
-  int max_cap;
-  int64_t max_grid_bricks;  // largest BX * BY * BZ
   const int* first[BK_NUM];  // device arrays of k + 1 block offsets per kind
   int total[BK_NUM];         // blocks of the launch per kind
 };
