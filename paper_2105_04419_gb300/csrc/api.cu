@@ -44,6 +44,7 @@ struct vdbedt_map {
   int32_t* h_pinned = nullptr;  // pinned host words for small readbacks
   Scratch scr;
   Scratch vlast;  // per-voxel last-record table of the ordered ingest
+  Scratch miss;   // flags and missing-brick list of the tracked (incremental) ingest
   Scratch io;  // host-input staging on the device
   Items items{};
   int32_t* changed = nullptr;
@@ -202,7 +203,9 @@ vdbedt_status do_global(vdbedt_map* h) {
   mark(h, 0);
   CK(h, cudaMemsetAsync(h->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), h->st), "memset");
   if (h->stage_n > 0) {
-    CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, nullptr, h->scr, h->vlast, h->st),
+    CK(h,
+       launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, nullptr, h->scr, h->vlast, h->miss,
+                             h->st),
        "ingest");
     clear_stage(h);
   }
@@ -375,6 +378,7 @@ void destroy_impl(vdbedt_map* h) {
   if (h->stage) cudaFree(h->stage);
   if (h->scr.buf) cudaFree(h->scr.buf);
   if (h->vlast.buf) cudaFree(h->vlast.buf);
+  if (h->miss.buf) cudaFree(h->miss.buf);
   if (h->io.buf) cudaFree(h->io.buf);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (int i = 0; i < 7; ++i)
@@ -439,7 +443,7 @@ vdbedt_status vdbedt_set_occupancy_counted(vdbedt_handle h, const int32_t* xyz, 
   DeviceGuard guard(h->device);
   s = ensure_stage(h, n_max);
   if (s) return s;
-  CK(h, reserve_ingest(h->g, n_max, h->scr, h->vlast, h->st), "ingest scratch");
+  CK(h, reserve_ingest(h->g, n_max, h->scr, h->vlast, h->miss, h->st), "ingest scratch");
   CK(h, launch_pack_records(xyz, occ, n_max, n_dev, h->d_count, h->g.nx, h->g.ny, h->g.nz, h->stage, nullptr,
                               h->g.counters, h->st),
      "pack");
@@ -500,7 +504,9 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     mark(h, 0);
     CK(h, launch_begin_update(h->g, h->st), "begin update");
     if (h->stage_n > 0) {
-      CK(h, launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->scr, h->vlast, h->st),
+      CK(h,
+         launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->scr, h->vlast,
+                               h->miss, h->st),
          "ingest");
       clear_stage(h);
     }
@@ -633,7 +639,8 @@ vdbedt_status vdbedt_get_info(vdbedt_handle h, vdbedt_info* info) {
   info->capacity_bricks = h->g.cap;
   info->nodes = h->h_pinned[C_NNODES];
   info->device_bytes =
-      (int64_t)(h->device_bytes + h->scr.bytes + h->vlast.bytes + h->io.bytes + sizeof(rec_t) * h->stage_cap);
+      (int64_t)(h->device_bytes + h->scr.bytes + h->vlast.bytes + h->miss.bytes + h->io.bytes +
+                sizeof(rec_t) * h->stage_cap);
   info->R = h->g.R;
   info->error_bits = h->h_pinned[C_ERR];
   return VDBEDT_OK;
@@ -774,7 +781,10 @@ vdbedt_status batch_global(vdbedt_batch* b) {
   for (vdbedt_map* m : b->maps) {
     if (m->stage_n <= 0) continue;
     BCK(b, cudaMemsetAsync(m->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), b->st), "memset");
-    BCK(b, launch_ingest_records(m->g, m->stage, m->stage_n, stage_count(m), false, nullptr, m->scr, m->vlast, b->st), "ingest");
+    BCK(b,
+        launch_ingest_records(m->g, m->stage, m->stage_n, stage_count(m), false, nullptr, m->scr, m->vlast, m->miss,
+                              b->st),
+        "ingest");
     clear_stage(m);
   }
   bmark(b, 1);

@@ -422,6 +422,72 @@ __global__ void k_apply_set_only(GridView g, const rec_t* __restrict__ rec, int6
   }
 }
 
+// Tracked ingest (incremental form): the bricks of "set" records that are not stored yet are
+// appended once each to a list (brick flags dedupe; count in C_UNIQUE, cleared when the update
+// begins), with flags on their node keys; after the nodes are created, the listed bricks are
+// allocated with their fields at dmax^2 and their flags cleared again, so the flag arrays stay
+// zero between updates.  Records of stored bricks need no brick work at all.
+__global__ void k_rec_missing(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
+                              int32_t* __restrict__ flag, int32_t* __restrict__ nflag, int32_t* __restrict__ list) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = rec_count(n_max, n_dev);
+  GRID_STRIDE(i, n) {
+    bool zero = false, bad = false;
+    if (i < n) {
+      int4 r = unpack_rec(rec[i]);
+      if (!rec_valid(g, r)) {
+        bad = true;
+      } else if (r.w == 1) {
+        const int bx = r.x >> 3, by = r.y >> 3, bz = r.z >> 3;
+        if (find_brick(g, bx, by, bz) < 0) {
+          const int64_t lb = bx + (int64_t)g.BX * (by + (int64_t)g.BY * bz);
+          if (atomicCAS(&flag[lb], 0, 1) == 0) {
+            list[atomicAdd(&g.counters[C_UNIQUE], 1)] = (int32_t)lb;
+            const int nk = node_key_of(g, bx, by, bz);
+            if (!nflag[nk]) nflag[nk] = 1;
+          }
+        }
+      } else {
+        zero = true;
+      }
+    }
+    if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+  }
+}
+
+__global__ void k_alloc_listed(GridView g, const int32_t* __restrict__ list, int32_t* __restrict__ flag, int64_t max) {
+  const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], max);
+  GRID_STRIDE(j, cnt) {
+    int node = -1, bx = 0, by = 0, bz = 0;
+    int* e = nullptr;
+    bool need = false;
+    if (j < cnt) {
+      const int64_t lb = list[j];
+      flag[lb] = 0;
+      bx = (int)(lb % g.BX);
+      by = (int)((lb / g.BX) % g.BY);
+      bz = (int)(lb / ((int64_t)g.BX * g.BY));
+      node = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+      if (node >= 0) {
+        e = &g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
+        need = *e == kNoSlot;
+      }
+    }
+    int total = 0;
+    const int slot = block_agg_add(&g.counters[C_NBRICKS], need, &total);
+    if (need) {
+      if (slot >= g.cap) {
+        set_error(g, kErrOverflow);
+      } else {
+        init_brick(g, slot, node, bx, by, bz, true);
+        *e = slot;
+      }
+    }
+    if (threadIdx.x == 0 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
+  }
+}
+
 // Ordered path: the last record of each voxel decides its bit.  vlast holds, per voxel of the
 // pool (slot * 512 + voxel in brick), the highest index of a record for it (-1 when none): the
 // first kernel raises it with atomicMax, the second applies each voxel's winning record and puts
@@ -1146,10 +1212,25 @@ static cudaError_t ensure_vlast(const GridView& g, Scratch& vl, cudaStream_t st)
   return cudaMemsetAsync(vl.buf, 0xFF, want, st);
 }
 
-cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, cudaStream_t st) {
+// The tracked ingest's zeroed arrays: brick flags, node-key flags, the list of missing bricks.
+static size_t tracked_bytes(const GridView& g) {
+  const size_t nbr = (size_t)g.BX * g.BY * g.BZ, nkeys = (size_t)g.NX * g.NY * g.NZ;
+  return align_up(nbr * 4) + align_up(nkeys * 4) + align_up(nbr * 4);
+}
+
+static cudaError_t ensure_tracked(const GridView& g, Scratch& miss, cudaStream_t st) {
+  const size_t want = tracked_bytes(g);
+  if (miss.bytes >= want) return cudaSuccess;
+  cudaError_t e = ensure_scratch(miss, want);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(miss.buf, 0, miss.bytes, st);
+}
+
+cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const size_t a = ingest_scratch_bytes(g, n, false), b = ingest_scratch_bytes(g, n, true);
-  cudaError_t e = ensure_scratch(scr, a > b ? a : b);
+  cudaError_t e = ensure_scratch(scr, ingest_scratch_bytes(g, n, false));
+  if (e != cudaSuccess) return e;
+  e = ensure_tracked(g, miss, st);
   if (e != cudaSuccess) return e;
   return ensure_vlast(g, vl, st);
 }
@@ -1159,9 +1240,32 @@ cudaError_t launch_begin_update(const GridView& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev,
+                                         int32_t* changed, Scratch& vl, Scratch& miss, cudaStream_t st) {
+  cudaError_t e = ensure_tracked(g, miss, st);
+  if (e != cudaSuccess) return e;
+  e = ensure_vlast(g, vl, st);
+  if (e != cudaSuccess) return e;
+  const size_t nbr = (size_t)g.BX * g.BY * g.BZ, nkeys = (size_t)g.NX * g.NY * g.NZ;
+  char* p = (char*)miss.buf;
+  int32_t* flag = (int32_t*)p;
+  int32_t* nflag = (int32_t*)(p + align_up(nbr * 4));
+  int32_t* list = (int32_t*)(p + align_up(nbr * 4) + align_up(nkeys * 4));
+  int32_t* vlast = (int32_t*)vl.buf;
+  const unsigned nbk = blocks_for(n);
+  VDB_LAUNCH(k_rec_missing, nbk, kT, 0, st, g, rec, n, n_dev, flag, nflag, list);
+  VDB_LAUNCH(k_create_flagged_nodes, blocks_for((int64_t)nkeys), kT, 0, st, g, nflag, (int64_t)nkeys);
+  VDB_LAUNCH(k_alloc_listed, blocks_for(n < (int64_t)nbr ? n : (int64_t)nbr), kT, 0, st, g, list, flag,
+             n < (int64_t)nbr ? n : (int64_t)nbr);
+  VDB_LAUNCH(k_rec_last, nbk, kT, 0, st, g, rec, n, n_dev, true, vlast);
+  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, n, n_dev, true, true, vlast, changed);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
-                                  int32_t* changed, Scratch& scr, Scratch& vl, cudaStream_t st) {
+                                  int32_t* changed, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  if (track) return launch_ingest_tracked(g, rec, n, n_dev, changed, vl, miss, st);
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
   const bool counting = n >= nbr_all / 4;
   // the dense mask is indexed by a 32-bit word number (8 words per brick)
@@ -1369,10 +1473,9 @@ cudaError_t launch_build_items_batch(const GridView* views, const BatchShape& b,
 }
 
 // Incremental: records were already applied with flip tracking (changed list filled).
+// (the item counters were cleared when the update began)
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const int32_t* changed, const Items& it,
                                     cudaStream_t st) {
-  cudaError_t e = clear_item_counters(g, st);
-  if (e != cudaSuccess) return e;
   VDB_LAUNCH(k_changed_flags_dilate, 1024, kT, 0, st, g, changed);
   VDB_LAUNCH(k_alloc_marked<OneView>, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, OneView{g}, true);
   VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.run[0], t.run[1], t.run[2], it);

@@ -269,12 +269,13 @@ cudaError_t ensure_scratch(Scratch& s, size_t bytes);
 
 cudaError_t launch_reset(const GridView& g, cudaStream_t st);
 // n records at rec; with n_dev (nullable) only the first *n_dev of them (clamped to [0, n]).
-// scr: sort / scan scratch; vl: the per-voxel last-record table (allocated and set to -1 on first
-// use, cap * 512 words).
+// scr: sort / scan scratch of the global form; vl: the per-voxel last-record table (allocated and
+// set to -1 on first use, cap * 512 words); miss: the tracked form's flag and list arrays
+// (allocated zeroed on first use and kept zero).
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
-                                  int32_t* changed, Scratch& scr, Scratch& vl, cudaStream_t st);
-// size the ingest scratch and the last-record table for up to n records, either form
-cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, cudaStream_t st);
+                                  int32_t* changed, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st);
+// size the ingest scratch, the tracked arrays and the last-record table for up to n records
+cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st);
 // clear the per-update counters and advance the device-side update epoch
 cudaError_t launch_begin_update(const GridView& g, cudaStream_t st);
 // dense grid -> bricks (scratch: dense_scratch_bytes(g))
