@@ -87,7 +87,8 @@ typedef struct {
 } vdbedt_update_stats;
 
 /* Create a handle for an nx x ny x nz grid with no obstacles (every D = dmax^2).
- * Allocates all device storage for cfg->max_bricks bricks up front.
+ * Allocates the grid's storage for cfg->max_bricks bricks up front; the record stage and the
+ * ingest scratch grow on demand (vdbedt_set_occupancy_counted reserves them ahead).
  * EINVAL: a size < 1, dmax outside [1, VDBEDT_DMAX_LIMIT], voxel_size <= 0, bad device.
  * ENOMEM: device allocation failed. */
 vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out);
