@@ -143,6 +143,16 @@ vdbedt_status device_errors(vdbedt_map* h) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Device address of page-locked (pinned or registered) host memory, or nullptr for pageable memory.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 vdbedt_status ensure_stage(vdbedt_map* h, int64_t need) {
   if (need <= h->stage_cap) return VDBEDT_OK;
   int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
@@ -413,13 +423,20 @@ vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const ui
     CK(h, launch_pack_records(xyz, occ, n, nullptr, nullptr, h->g.nx, h->g.ny, h->g.nz, dst, nullptr, h->g.counters,
                               h->st), "pack");
   } else {
-    // copy the raw arrays, pack and validate on the device, then check before accepting
-    size_t bxyz = ((size_t)n * 12 + 255) & ~(size_t)255;
-    CK(h, ensure_scratch(h->io, bxyz + (size_t)n + 256), "io alloc");
-    int32_t* dxyz = (int32_t*)h->io.buf;
-    uint8_t* docc = (uint8_t*)h->io.buf + bxyz;
-    CK(h, cudaMemcpyAsync(dxyz, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, h->st), "h2d");
-    CK(h, cudaMemcpyAsync(docc, occ, (size_t)n, cudaMemcpyHostToDevice, h->st), "h2d");
+    // pack and validate on the device, then check before accepting.  Page-locked host arrays are
+    // read by the pack kernel in place (mapped host memory); other host arrays are copied first.
+    const int32_t* dxyz = static_cast<const int32_t*>(mapped_host(xyz));
+    const uint8_t* docc = static_cast<const uint8_t*>(mapped_host(occ));
+    if (!dxyz || !docc) {
+      size_t bxyz = ((size_t)n * 12 + 255) & ~(size_t)255;
+      CK(h, ensure_scratch(h->io, bxyz + (size_t)n + 256), "io alloc");
+      int32_t* cxyz = (int32_t*)h->io.buf;
+      uint8_t* cocc = (uint8_t*)h->io.buf + bxyz;
+      CK(h, cudaMemcpyAsync(cxyz, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, h->st), "h2d");
+      CK(h, cudaMemcpyAsync(cocc, occ, (size_t)n, cudaMemcpyHostToDevice, h->st), "h2d");
+      dxyz = cxyz;
+      docc = cocc;
+    }
     CK(h, cudaMemsetAsync(h->d_invalid, 0, sizeof(int32_t), h->st), "memset");
     CK(h, launch_pack_records(dxyz, docc, n, nullptr, nullptr, h->g.nx, h->g.ny, h->g.nz, dst, h->d_invalid,
                               h->g.counters, h->st),

@@ -232,3 +232,27 @@ def test_sparse_records_take_the_radix_path():
     single[45, 130, 150] = 1
     got = gpu_global(single, 40).export_dense()
     assert first_mismatch(got, O.edt_factorised(single, 40)) is None
+
+
+def test_pinned_host_records_read_in_place():
+    """Page-locked host records are read by the pack kernel in place; results and validation are
+    those of pageable records."""
+    import torch
+    import paper_2105_04419_gb300 as V
+    occ = W.bernoulli_grid(11, (40, 44, 52), 0.01)
+    xyz = coords_of(occ)
+    val = np.ones(len(xyz), np.uint8)
+    xyz_p = torch.from_numpy(xyz).pin_memory().numpy()
+    val_p = torch.from_numpy(val).pin_memory().numpy()
+    m = V.Map(52, 44, 40, 13)
+    m.set_occupancy(xyz_p, val_p)
+    m.global_()
+    assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 13)) is None
+    bad = xyz_p.copy()
+    bad_p = torch.from_numpy(bad).pin_memory().numpy()
+    bad_p[5] = (52, 0, 0)  # outside the grid: the whole call is rejected
+    with pytest.raises(V.VdbedtError) as e:
+        m.set_occupancy(bad_p, val_p)
+    assert e.value.code == "EINVAL"
+    m.global_()
+    assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 13)) is None
