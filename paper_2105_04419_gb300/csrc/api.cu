@@ -1,5 +1,7 @@
 // The C ABI of libvdbedt (declared in include/vdbedt.h): handle lifetime, staging of occupancy
-// records, the global and incremental transforms, queries and the clearance cost.
+// records (host, device, device-counted, dense), the global and incremental transforms, queries,
+// the clearance cost, tuning and phase events, batches of grids sharing one brick pool, and the
+// self-test of the bounded device waits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>

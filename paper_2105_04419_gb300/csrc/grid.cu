@@ -1,16 +1,27 @@
 // Building and maintaining the sparse brick grid on the device.
 //
-//   ingest   staged occupancy records -> brick keys -> stable radix sort -> unique -> compaction
-//            -> new bricks (node found or inserted in the hashed level, child slot claimed) ->
-//            occupancy bits set.  Several records for one voxel: the last one wins (resolved by a
-//            stable sort of (voxel, record index) whenever a record clears a voxel or flips are
-//            tracked; a batch of pure "set" records needs no ordering).
+//   ingest (global form)  staged occupancy records -> brick keys of "set" records -> sorted unique
+//            list (a counting sort through one flag per brick of the grid when records are many,
+//            an LSD radix sort + unique + compaction when they are few) -> nodes created first
+//            (one thread per flagged node key) -> bricks allocated (slots reserved with one
+//            atomic per block) -> occupancy bits set (OR-ed into a dense mask during the count, or
+//            per record).  Several records for one voxel: the last one wins -- a per-voxel
+//            last-record table (atomicMax of the record index) picks it whenever a record clears a
+//            voxel.
+//   ingest (incremental form)  only the bricks of "set" records that are not stored yet are
+//            appended to a list and allocated; every voxel's last record is applied through the
+//            last-record table and each flip's brick joins the changed list once.
+//   dense ingest  a whole occupancy grid -> per-brick masks in a scratch (sector-complete loads),
+//            then nodes, then the occupied bricks.
 //   activation  the compute set: every brick within Chebyshev brick radius R of a brick holding
 //            an obstacle (the paper grows the tree only where the limited transform reaches,
-//            Sec. IV-A); marked in the per-node 4096-bit masks, then absent bricks are allocated.
-//   items    work lists for the passes: runs of bricks along y (in-plane pass) and along z.
-//   incremental marking  bricks whose occupancy changed -> in-plane dirty set (same z, within R
-//            in x and y) and z dirty set (within R in x, y and z) -> work lists.
+//            Sec. IV-A): obstacle bits in per-node 4096-bit masks, halo nodes created, each node's
+//            dilation computed from its 3 x 3 x 3 node neighbourhood, absent bricks allocated.
+//   items    work lists for the passes: runs of bricks along x, y and z with their slot lists.
+//   incremental marking  bricks whose occupancy changed -> their dilation (allocated) -> dirty
+//            runs: x within R along x, in-plane within R in x and y, z within R in x, y and z.
+//   batches  the per-grid kernels take a view source: one grid, or every grid of a batch with
+//            block shares of one launch.
 #include <cuda_fp16.h>
 
 #include "vdbedt_internal.cuh"
