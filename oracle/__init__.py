@@ -13,6 +13,8 @@ Functions (each cites the passage it follows; the exact rules are in the C heade
                             global (Lower only, Sec. V-A) and incremental.
 * :func:`clearance`       -- the clearance term of Eq. 2 as a squared hinge on a trilinear
                             distance, its sum per trajectory and its gradient, in float64.
+* :func:`nearest_obstacle` -- the nearest occupied voxel of sampled voxels (the obstacle a cell
+                            records with its distance, Sec. IV-B), ties to the smallest (z, y, x).
 
 Arrays are C-ordered ``[nz, ny, nx]``; coordinates are ``(x, y, z)``.
 """
@@ -112,6 +114,31 @@ def edt_at(occ_zyx: np.ndarray, dmax: int, xyz: np.ndarray, threads: int = 0) ->
                             out.ctypes.data, threads)
     if rc:
         raise ValueError(f"oracle_edt_at failed ({rc})")
+    return out
+
+
+def nearest_obstacle(occ_zyx: np.ndarray, dmax: int, xyz: np.ndarray) -> np.ndarray:
+    """The nearest occupied voxel of each query voxel ``xyz`` [m, 3] (x, y, z) -- the obstacle a
+    cell keeps beside its distance in the paper's map (Sec. IV-B) -- written out by brute force over
+    every occupied voxel: among the occupied o with |v - o|^2 < dmax^2, the one with the least
+    |v - o|^2, ties broken by the smallest (z, y, x).  Returns [m, 3] int32 (x, y, z), or
+    (-1, -1, -1) when no obstacle lies closer than dmax or v is outside the grid.  Small grids."""
+    occ = np.asarray(occ_zyx)
+    nz, ny, nx = occ.shape
+    oz, oy, ox = np.nonzero(occ)  # C order: sorted by (z, y, x)
+    obs = np.stack([ox, oy, oz], 1).astype(np.int64)
+    pts = np.asarray(xyz, dtype=np.int64).reshape(-1, 3)
+    out = np.full((len(pts), 3), -1, dtype=np.int32)
+    if len(obs) == 0:
+        return out
+    lim = int(dmax) * int(dmax)
+    for i, (x, y, z) in enumerate(pts):
+        if not (0 <= x < nx and 0 <= y < ny and 0 <= z < nz):
+            continue
+        d2 = ((obs - np.array([x, y, z])) ** 2).sum(axis=1)
+        j = int(np.argmin(d2))  # the first of the minima: the smallest (z, y, x)
+        if d2[j] < lim:
+            out[i] = obs[j]
     return out
 
 
