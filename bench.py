@@ -393,6 +393,29 @@ def bench_batched(V, torch, stream, flush, autotuned=True, steps=5, warmup=3):
             "tuning": {k: v for k, v in tuning.items() if k != "key"}}
 
 
+def bench_nearest(V, torch, m, dims, stream, reps=20):
+    """Nearest-obstacle query of 2^20 voxels uniform in the grid, device in and out, event-timed."""
+    nx, ny, nz = dims
+    g = torch.Generator(device="cuda").manual_seed(5)
+    n = 1 << 20
+    q = torch.stack([torch.randint(0, nx, (n,), generator=g, device="cuda"),
+                     torch.randint(0, ny, (n,), generator=g, device="cuda"),
+                     torch.randint(0, nz, (n,), generator=g, device="cuda")], 1).to(torch.int32).contiguous()
+    for _ in range(3):
+        out = m.query_nearest(q)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        out = m.query_nearest(q)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    found = float((out[:, 0] >= 0).float().mean().item())
+    return {"queries": n, "ms": ms, "queries_per_s": n / (ms / 1e3), "with_obstacle_fraction": found,
+            "rule": "nearest occupied voxel, ties to the smallest (z, y, x); voxels uniform in the grid"}
+
+
 def cpu_baseline(occ, dmax, budget_s=12.0):
     """The CPU oracle (Eq. 1 factorised, OpenMP on all host cores) on a z-slab of the workload."""
     import oracle as O
@@ -626,6 +649,7 @@ def main():
 
     if wl["kind"] == "tunnel" and not args.no_clearance:
         line["clearance"] = bench_clearance(V, torch, m, occ, stream)
+        line["nearest"] = bench_nearest(V, torch, m, wl["dims"], stream)
     if wl["kind"] == "tunnel" and not args.no_batched:
         line["batched"] = bench_batched(V, torch, stream, flush, autotuned=not args.no_autotune)
     if wl["kind"] == "tunnel" and not args.no_incremental:

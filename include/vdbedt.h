@@ -138,6 +138,14 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats);
  * on_device != 0: xyz and out_sqdist are device pointers; otherwise host pointers (the call waits). */
 vdbedt_status vdbedt_query(vdbedt_handle h, const int32_t* xyz, int64_t n, int32_t* out_sqdist, int on_device);
 
+/* Nearest obstacle of n voxels: out_xyz[3k .. 3k + 2] is the occupied voxel o that D(v) measures
+ * to -- the obstacle the paper's map keeps beside each cell's distance (Sec. IV-B) -- found among
+ * the lattice points with |o - v|^2 = D(v) in increasing (z, y, x) order, so ties go to the
+ * smallest (z, y, x).  (-1, -1, -1) for voxels outside the grid or with D = dmax^2 (no obstacle
+ * closer than dmax).  Reads the current field (after vdbedt_global / vdbedt_update).  on_device
+ * as for vdbedt_query. */
+vdbedt_status vdbedt_query_nearest(vdbedt_handle h, const int32_t* xyz, int64_t n, int32_t* out_xyz, int on_device);
+
 /* The whole field as a dense int32 array out[nz][ny][nx] (host or device). */
 vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device);
 

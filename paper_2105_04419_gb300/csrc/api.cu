@@ -577,6 +577,29 @@ vdbedt_status vdbedt_query(vdbedt_handle h, const int32_t* xyz, int64_t n, int32
   return VDBEDT_OK;
 }
 
+vdbedt_status vdbedt_query_nearest(vdbedt_handle h, const int32_t* xyz, int64_t n, int32_t* out_xyz, int on_device) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!xyz || !out_xyz))) return fail(h, VDBEDT_EINVAL, "bad query arguments");
+  if (n == 0) return VDBEDT_OK;
+  DeviceGuard guard(h->device);
+  if (on_device) {
+    CK(h, launch_query_nearest(h->g, xyz, n, out_xyz, h->st), "nearest");
+    return VDBEDT_OK;
+  }
+  size_t bx = ((size_t)n * 12 + 255) & ~(size_t)255;
+  CK(h, ensure_scratch(h->io, 2 * bx), "io alloc");
+  int32_t* dxyz = (int32_t*)h->io.buf;
+  int32_t* dout = (int32_t*)((char*)h->io.buf + bx);
+  CK(h, cudaMemcpyAsync(dxyz, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, h->st), "h2d");
+  CK(h, launch_query_nearest(h->g, dxyz, n, dout, h->st), "nearest");
+  s = device_errors(h);
+  if (s) return s;
+  CK(h, cudaMemcpyAsync(out_xyz, dout, (size_t)n * 12, cudaMemcpyDeviceToHost, h->st), "d2h");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return VDBEDT_OK;
+}
+
 vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device) {
   vdbedt_status s = check_handle(h);
   if (s) return s;

@@ -2,7 +2,8 @@
 //
 // Query: D at voxel coordinates through the two-level interior (hash probe, child table); voxels
 // outside the grid or in unstored bricks return the background dmax^2 (the paper's tile value,
-// Sec. IV-A).
+// Sec. IV-A).  Nearest-obstacle query: the occupied voxel a cell's distance is measured to (the
+// obstacle the paper keeps per cell, Sec. IV-B), found on the lattice sphere of radius^2 D.
 //
 // Clearance cost (Eq. 2, clearance term, as a squared hinge): per point p (metres),
 //   u = p / vs (float32), i0 = floor(u) clamped to [0, n-2], t = u - i0,
@@ -37,6 +38,54 @@ __global__ void k_export_dense(GridView g, int32_t* __restrict__ out) {
     int64_t r = i / g.nx;
     int y = (int)(r % g.ny), z = (int)(r / g.ny);
     out[i] = sqdist_at(g, x, y, z);
+  }
+}
+
+__device__ __forceinline__ bool occupied_at(const GridView& g, int x, int y, int z) {
+  const int s = find_brick(g, x >> 3, y >> 3, z >> 3);
+  return s >= 0 && ((g.occ[(size_t)s * 8 + (z & 7)] >> ((x & 7) + 8 * (y & 7))) & 1ull) != 0ull;
+}
+
+__device__ __forceinline__ int isqrt_floor(int v) {
+  int r = (int)sqrtf((float)v);
+  while (r * r > v) --r;
+  while ((r + 1) * (r + 1) <= v) ++r;
+  return r;
+}
+
+// Nearest occupied voxel of a query voxel: D(v) fixes the squared distance, so the obstacle lies
+// on the lattice sphere |o - v|^2 = D; its points are visited in increasing (z, y, x) and the
+// first occupied one is returned (ties to the smallest (z, y, x)).  (-1, -1, -1) outside the grid
+// or when D = dmax^2 (no obstacle closer than dmax).
+__global__ void k_query_nearest(GridView g, const int32_t* __restrict__ xyz, int64_t n, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    int rx = -1, ry = -1, rz = -1;
+    const int D = sqdist_at(g, x, y, z);
+    if ((unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz && D < g.INF) {
+      bool found = false;
+      const int r = isqrt_floor(D);
+      for (int dz = -r; dz <= r && !found; ++dz) {
+        const int oz = z + dz, rem = D - dz * dz;
+        if ((unsigned)oz >= (unsigned)g.nz || rem < 0) continue;
+        const int r2 = isqrt_floor(rem);
+        for (int dy = -r2; dy <= r2 && !found; ++dy) {
+          const int oy = y + dy, rem2 = rem - dy * dy;
+          if ((unsigned)oy >= (unsigned)g.ny) continue;
+          const int dx = isqrt_floor(rem2);
+          if (dx * dx != rem2) continue;
+          if (x - dx >= 0 && occupied_at(g, x - dx, oy, oz)) {
+            rx = x - dx, ry = oy, rz = oz, found = true;
+          } else if (dx > 0 && x + dx < g.nx && occupied_at(g, x + dx, oy, oz)) {
+            rx = x + dx, ry = oy, rz = oz, found = true;
+          }
+        }
+      }
+      if (!found) set_error(g, kErrInternal);  // a finite D always has an obstacle on its sphere
+    }
+    out[3 * i] = rx;
+    out[3 * i + 1] = ry;
+    out[3 * i + 2] = rz;
   }
 }
 
@@ -163,6 +212,12 @@ unsigned grid_for(int64_t n, int threads) {
 cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   VDB_LAUNCH(k_query, grid_for(n, 256), 256, 0, st, g, xyz, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_query_nearest(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  VDB_LAUNCH(k_query_nearest, grid_for(n, 128), 128, 0, st, g, xyz, n, out);
   return cudaGetLastError();
 }
 

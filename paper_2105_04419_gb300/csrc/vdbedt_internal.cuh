@@ -326,6 +326,8 @@ cudaError_t launch_wait_selftest(const GridView& g, int which, cudaStream_t st);
 
 // queries (query.cu)
 cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st);
+// out[3k .. 3k + 2]: nearest occupied voxel of query k (ties to the smallest (z, y, x)), or -1s
+cudaError_t launch_query_nearest(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st);
 cudaError_t launch_export_dense(const GridView& g, int32_t* out, cudaStream_t st);
 // obstacle and finite brick counts into counters C_OBST and C_FINITE
 cudaError_t launch_count_flags(const GridView& g, cudaStream_t st);

@@ -64,6 +64,7 @@ SIGNATURES = {
     "vdbedt_global": (ctypes.c_int, [_H]),
     "vdbedt_update": (ctypes.c_int, [_H, ctypes.POINTER(UpdateStats)]),
     "vdbedt_query": (ctypes.c_int, [_H, _P, _I64, _P, ctypes.c_int]),
+    "vdbedt_query_nearest": (ctypes.c_int, [_H, _P, _I64, _P, ctypes.c_int]),
     "vdbedt_export_dense": (ctypes.c_int, [_H, _P, ctypes.c_int]),
     "vdbedt_clearance_forward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P]),
     "vdbedt_clearance_backward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P, _P]),
@@ -271,6 +272,25 @@ class Map:
         out = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
         self._enter(x, out)
         _check(lib.vdbedt_query(self._h, x.data_ptr(), x.shape[0], out.data_ptr(), 1), "vdbedt_query", self._h)
+        self._leave()
+        return out
+
+    def query_nearest(self, xyz):
+        """Nearest obstacle (x, y, z) of each voxel of xyz [n, 3] (numpy or CUDA tensor), -1s where
+        none lies closer than dmax; ties to the smallest (z, y, x)."""
+        lib = load()
+        if isinstance(xyz, np.ndarray):
+            x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+            out = np.empty_like(x)
+            _check(lib.vdbedt_query_nearest(self._h, _ptr_host(x), x.shape[0], _ptr_host(out), 0),
+                   "vdbedt_query_nearest", self._h)
+            return out
+        torch = _torch()
+        x = xyz.to(torch.int32).contiguous().view(-1, 3)
+        out = torch.empty_like(x)
+        self._enter(x, out)
+        _check(lib.vdbedt_query_nearest(self._h, x.data_ptr(), x.shape[0], out.data_ptr(), 1), "vdbedt_query_nearest",
+               self._h)
         self._leave()
         return out
 
