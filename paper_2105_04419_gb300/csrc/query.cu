@@ -56,24 +56,27 @@ __device__ __forceinline__ int isqrt_floor(int v) {
 // Nearest occupied voxel of a query voxel: D(v) fixes the squared distance, so the obstacle lies
 // on the lattice sphere |o - v|^2 = D; its points are visited in increasing (z, y, x) and the
 // first occupied one is returned (ties to the smallest (z, y, x)).  (-1, -1, -1) outside the grid
-// or when D = dmax^2 (no obstacle closer than dmax).
+// or when D = dmax^2 (no obstacle closer than dmax).  Integer square roots come from a shared
+// table of floor(sqrt(v)) for v = 0 .. dmax^2 (dynamic shared memory, dmax^2 + 1 bytes).
 __global__ void k_query_nearest(GridView g, const int32_t* __restrict__ xyz, int64_t n, int32_t* __restrict__ out) {
+  extern __shared__ uint8_t isq[];
+  for (int v = threadIdx.x; v <= g.INF; v += blockDim.x) isq[v] = (uint8_t)isqrt_floor(v);
+  __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
     int rx = -1, ry = -1, rz = -1;
     const int D = sqdist_at(g, x, y, z);
     if ((unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz && D < g.INF) {
       bool found = false;
-      const int r = isqrt_floor(D);
+      const int r = isq[D];
       for (int dz = -r; dz <= r && !found; ++dz) {
         const int oz = z + dz, rem = D - dz * dz;
-        if ((unsigned)oz >= (unsigned)g.nz || rem < 0) continue;
-        const int r2 = isqrt_floor(rem);
+        if ((unsigned)oz >= (unsigned)g.nz) continue;
+        const int r2 = isq[rem];
         for (int dy = -r2; dy <= r2 && !found; ++dy) {
           const int oy = y + dy, rem2 = rem - dy * dy;
-          if ((unsigned)oy >= (unsigned)g.ny) continue;
-          const int dx = isqrt_floor(rem2);
-          if (dx * dx != rem2) continue;
+          const int dx = isq[rem2];
+          if (dx * dx != rem2 || (unsigned)oy >= (unsigned)g.ny) continue;
           if (x - dx >= 0 && occupied_at(g, x - dx, oy, oz)) {
             rx = x - dx, ry = oy, rz = oz, found = true;
           } else if (dx > 0 && x + dx < g.nx && occupied_at(g, x + dx, oy, oz)) {
@@ -217,7 +220,8 @@ cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32
 
 cudaError_t launch_query_nearest(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  VDB_LAUNCH(k_query_nearest, grid_for(n, 128), 128, 0, st, g, xyz, n, out);
+  const size_t smem = (size_t)g.INF + 1;  // at most 32,762 bytes (dmax <= 181)
+  VDB_LAUNCH(k_query_nearest, grid_for(n, 128), 128, smem, st, g, xyz, n, out);
   return cudaGetLastError();
 }
 
