@@ -1168,17 +1168,17 @@ __global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* _
       if (c < 0 || c > n_max) atomicOr(&counters[C_ERR], kErrInvalidRecord);
     }
   }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-    int v = occ[i];
-    bool ok = (unsigned)x < (unsigned)nx && (unsigned)y < (unsigned)ny && (unsigned)z < (unsigned)nz && v <= 1;
+  auto put = [&](int64_t i, int x, int y, int z, int v) {
+    const bool ok = (unsigned)x < (unsigned)nx && (unsigned)y < (unsigned)ny && (unsigned)z < (unsigned)nz && v <= 1;
     if (!ok) {
       if (invalid) atomicAdd(invalid, 1);
       dst[i] = pack_rec(kBadCoord, 0, 0, 0);  // skipped (and reported) by the ingest kernels
     } else {
       dst[i] = pack_rec(x, y, z, v);
     }
-  }
+  };
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    put(i, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], occ[i]);
 }
 }  // namespace
 

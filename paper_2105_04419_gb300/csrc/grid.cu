@@ -292,6 +292,24 @@ __global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, 
   }
 }
 
+// A node absent from the table and inserted by exactly one thread, at index idx: its key, then a
+// hash slot claimed with the final word (read by later kernels: the kernel boundary orders both).
+__device__ void insert_new_node(const GridView& g, uint32_t key, int idx) {
+  if (idx >= g.node_cap) {
+    set_error(g, kErrNodeOverflow);
+    return;
+  }
+  g.node_key[idx] = (int32_t)key;
+  const unsigned long long word = ((unsigned long long)key << 32) | (uint32_t)idx;
+  uint32_t h = hash32(key) & g.hmask;
+  bool placed = false;
+  for (uint32_t probe = 0; probe <= g.hmask && !placed; ++probe) {
+    placed = atomicCAS(&g.hslots[h], ~0ull, word) == ~0ull;
+    h = (h + 1) & g.hmask;
+  }
+  if (!placed) set_error(g, kErrNodeOverflow);
+}
+
 // Nodes of the obstacle bricks, created before the bricks so that no brick allocation waits on a
 // node insertion in progress: one thread per flagged node key absent from the table; indices come
 // from one atomic per block, and each key (inserted by exactly one thread) claims an empty hash
@@ -304,21 +322,7 @@ __global__ void k_create_flagged_nodes(GridView g, int32_t* __restrict__ nflag, 
       need = find_node(g, (uint32_t)k) < 0;
     }
     const int idx = block_agg_add(&g.counters[C_NNODES], need, nullptr);
-    if (need) {
-      if (idx >= g.node_cap) {
-        set_error(g, kErrNodeOverflow);
-      } else {
-        g.node_key[idx] = (int32_t)k;
-        const unsigned long long word = ((unsigned long long)(uint32_t)k << 32) | (uint32_t)idx;
-        uint32_t h = hash32((uint32_t)k) & g.hmask;
-        bool placed = false;
-        for (uint32_t probe = 0; probe <= g.hmask && !placed; ++probe) {
-          placed = atomicCAS(&g.hslots[h], ~0ull, word) == ~0ull;
-          h = (h + 1) & g.hmask;
-        }
-        if (!placed) set_error(g, kErrNodeOverflow);
-      }
-    }
+    if (need) insert_new_node(g, (uint32_t)k, idx);
   }
 }
 
@@ -662,21 +666,7 @@ __global__ void __launch_bounds__(256) k_dense_nodes(VS vs, DenseScratch ds) {
       need = find_node(g, (uint32_t)k) < 0;
     }
     const int idx = block_agg_add(&g.counters[C_NNODES], need, nullptr);
-    if (need) {
-      if (idx >= g.node_cap) {
-        set_error(g, kErrNodeOverflow);
-      } else {
-        g.node_key[idx] = (int32_t)k;
-        const unsigned long long word = ((unsigned long long)(uint32_t)k << 32) | (uint32_t)idx;
-        uint32_t h = hash32((uint32_t)k) & g.hmask;
-        bool placed = false;
-        for (uint32_t probe = 0; probe <= g.hmask && !placed; ++probe) {
-          placed = atomicCAS(&g.hslots[h], ~0ull, word) == ~0ull;
-          h = (h + 1) & g.hmask;
-        }
-        if (!placed) set_error(g, kErrNodeOverflow);
-      }
-    }
+    if (need) insert_new_node(g, (uint32_t)k, idx);
   }
 }
 
