@@ -92,22 +92,16 @@ __global__ void k_reset_nodes(VS vs) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   (void)gi;
-  const int nn = min(g.counters[C_NNODES], g.node_cap);
-  const int64_t total = (int64_t)nn * kNodeBricks;
-  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < total; i += (int64_t)nblk * blockDim.x) {
-    g.child[i] = kNoSlot;
-    if ((i & 3) == 0) {
-      int64_t j = i >> 2;  // 3 x 1024 marks per node
-      g.mark[3 * j] = 0;
-      g.mark[3 * j + 1] = 0;
-      g.mark[3 * j + 2] = 0;
-    }
-    if ((i & 31) == 0) g.amask[i >> 5] = 0u;
-    if ((i & 31) < 3) g.mwork[(i >> 5) * 3 + (i & 31)] = 0u;
-  }
-  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i <= (int64_t)g.hmask;
-       i += (int64_t)nblk * blockDim.x)
-    g.hslots[i] = ~0ull;
+  // per used node: 4096 child slots, 3 x 1024 marks, 128 activity words and 384 work words, all
+  // whole 16-byte vectors (the per-node arrays start at multiples of their node strides)
+  const int64_t nn = min(g.counters[C_NNODES], g.node_cap);
+  const int64_t stride = (int64_t)nblk * blockDim.x, t0 = (int64_t)bid * blockDim.x + threadIdx.x;
+  const int4 none = make_int4(kNoSlot, kNoSlot, kNoSlot, kNoSlot), zero = make_int4(0, 0, 0, 0);
+  for (int64_t i = t0; i < nn * (kNodeBricks / 4); i += stride) reinterpret_cast<int4*>(g.child)[i] = none;
+  for (int64_t i = t0; i < nn * (3 * 1024 / 4); i += stride) reinterpret_cast<int4*>(g.mark)[i] = zero;
+  for (int64_t i = t0; i < nn * (128 / 4); i += stride) reinterpret_cast<int4*>(g.amask)[i] = zero;
+  for (int64_t i = t0; i < nn * (384 / 4); i += stride) reinterpret_cast<int4*>(g.mwork)[i] = zero;
+  for (int64_t i = t0; i <= (int64_t)g.hmask; i += stride) g.hslots[i] = ~0ull;
 }
 
 // Start of an incremental update: clear the per-update counters and advance the update epoch
@@ -129,6 +123,12 @@ __global__ void k_begin_update(GridView g) {
 // ---- brick allocation ----
 // Fill a freshly allocated brick: empty occupancy, coordinates, flags; with `init_fields` also
 // g2 and D at dmax^2 (bricks added by an incremental update may be read before a pass writes them).
+__device__ __forceinline__ void init_brick_meta(const GridView& g, int slot, int node, int bx, int by, int bz) {
+  g.bcoord[slot] = make_int4(bx, by, bz, node);
+  g.bflags[slot] = 0u;
+  g.bepoch[slot] = 0;
+}
+
 __device__ void init_brick(const GridView& g, int slot, int node, int bx, int by, int bz, bool init_fields) {
   for (int w = 0; w < 8; ++w) g.occ[(size_t)slot * 8 + w] = 0ull;
   if (init_fields) {
@@ -147,9 +147,7 @@ __device__ void init_brick(const GridView& g, int slot, int node, int bx, int by
     int4* dd = reinterpret_cast<int4*>(g.dist + (size_t)slot * kBrickVox);
     for (int q = 0; q < 128; ++q) dd[q] = make_int4(g.INF, g.INF, g.INF, g.INF);
   }
-  g.bcoord[slot] = make_int4(bx, by, bz, node);
-  g.bflags[slot] = 0u;
-  g.bepoch[slot] = 0;
+  init_brick_meta(g, slot, node, bx, by, bz);
 }
 
 __device__ __forceinline__ bool brick_has_obstacle(const GridView& g, int s) {
@@ -597,8 +595,15 @@ struct DenseScratch {
   }
 };
 
+// Pass 1: one warp per unit (a brick row: by, bz and up to kDenseX bricks along x).  The unit's
+// 64 input rows form eight contiguous stretches (one per plane z); each lane loads 16 bytes (two
+// bricks) of each row, a plane's eight loads issued together, and assembles both bricks' eight
+// mask words in registers -- no shared memory, no block barrier.  A lane then writes its two bricks
+// whole (a warp's stores are one contiguous run) with their flags, and marks their nodes.
+constexpr int kDenseX = 64;
+
 template <class VS, class SRC>
-__global__ void __launch_bounds__(256) k_dense_masks(VS vs, SRC src, DenseScratch ds) {
+__global__ void __launch_bounds__(256, 2) k_dense_masks(VS vs, SRC src, DenseScratch ds) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   const uint8_t* __restrict__ grid = src.get(gi);
@@ -606,43 +611,84 @@ __global__ void __launch_bounds__(256) k_dense_masks(VS vs, SRC src, DenseScratc
   int32_t* flag;
   int32_t* nflag;
   ds.at(gi, dbits, flag, nflag);
-  const int SX = (g.BX + 3) / 4;
-  const int64_t nunits = (int64_t)SX * g.BY * g.BZ;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int b = lane >> 3, z = lane & 7;
-  const bool vec = (g.nx % 8) == 0 && (reinterpret_cast<uintptr_t>(grid) & 7u) == 0;
-  for (int64_t u = (int64_t)bid * nwarps + warp; u < nunits; u += (int64_t)nblk * nwarps) {
-    const int bx = (int)(u % SX) * 4 + b;
-    const int by = (int)((u / SX) % g.BY), bz = (int)(u / ((int64_t)SX * g.BY));
-    const int gz = bz * 8 + z, x0 = bx * 8;
-    unsigned long long word = 0ull;  // bits x + 8 y of depth z
-    if (bx < g.BX && gz < g.nz) {
-      const int nxv = min(8, g.nx - x0);
+  const uint32_t nch = (uint32_t)(g.BX + kDenseX - 1) / kDenseX;
+  const uint32_t nunits = nch * (uint32_t)g.BY * (uint32_t)g.BZ;
+  const int lane = threadIdx.x & 31;
+  const bool v16 = (g.nx % 16) == 0 && (reinterpret_cast<uintptr_t>(grid) & 15u) == 0;
+  const bool v8 = (g.nx % 8) == 0 && (reinterpret_cast<uintptr_t>(grid) & 7u) == 0;
+  const uint32_t nw = (uint32_t)nblk * (blockDim.x >> 5);
+  for (uint32_t u = (uint32_t)bid * (blockDim.x >> 5) + (threadIdx.x >> 5); u < nunits; u += nw) {
+    const int ch = (int)(u % nch);
+    const uint32_t rest = u / nch;
+    const int by = (int)(rest % (uint32_t)g.BY), bz = (int)(rest / (uint32_t)g.BY);
+    const int bx0 = ch * kDenseX, nbx = min(kDenseX, g.BX - bx0);
+    const int j = 2 * lane;  // this lane: bricks j and j + 1 of the chunk
+    if (j >= nbx) continue;  // lanes past the row's end (the warp has no collective below)
+    const bool two = j + 1 < nbx;
+    const int x0 = (bx0 + j) * 8;
+    const int nrow = min(8, g.ny - by * 8), nplane = min(8, g.nz - bz * 8);
+    const uint8_t* base = grid + ((size_t)bz * 8 * g.ny + (size_t)by * 8) * g.nx + x0;
+    const size_t zstride = (size_t)g.ny * g.nx;
+    unsigned long long w0[8], w1[8];  // plane z's mask word of brick j and of brick j + 1
 #pragma unroll
-      for (int y = 0; y < 8; ++y) {
-        const int gy = by * 8 + y;
-        if (gy < g.ny) {
-          const uint8_t* row = grid + ((size_t)gz * g.ny + gy) * g.nx + x0;
-          uint32_t bits;
-          if (vec) {
-            bits = nonzero_bytes(__ldg(reinterpret_cast<const unsigned long long*>(row)));
-          } else {
-            bits = 0u;
-            for (int x = 0; x < nxv; ++x) bits |= (uint32_t)(row[x] != 0) << x;
-          }
-          word |= (unsigned long long)bits << (8 * y);
+    for (int z = 0; z < 8; ++z) {
+      const uint8_t* pl = base + (size_t)z * zstride;
+      const int nr = z < nplane ? nrow : 0;
+      uint32_t m[8];  // row y: bits 0-7 brick j, bits 8-15 brick j + 1
+      if (v16) {  // nx a multiple of 16: bricks come in whole pairs
+        uint4 w[8];
+#pragma unroll
+        for (int y = 0; y < 8; ++y)
+          w[y] = y < nr ? __ldg(reinterpret_cast<const uint4*>(pl + (size_t)y * g.nx)) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int y = 0; y < 8; ++y)
+          m[y] = nonzero_bytes(((unsigned long long)w[y].y << 32) | w[y].x) |
+                 (nonzero_bytes(((unsigned long long)w[y].w << 32) | w[y].z) << 8);
+      } else if (v8) {
+        unsigned long long lo[8], hi[8];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          lo[y] = y < nr ? __ldg(reinterpret_cast<const unsigned long long*>(pl + (size_t)y * g.nx)) : 0ull;
+          hi[y] = y < nr && two ? __ldg(reinterpret_cast<const unsigned long long*>(pl + (size_t)y * g.nx + 8)) : 0ull;
+        }
+#pragma unroll
+        for (int y = 0; y < 8; ++y) m[y] = nonzero_bytes(lo[y]) | (nonzero_bytes(hi[y]) << 8);
+      } else {  // ragged rows: byte loads
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          uint32_t v = 0u;
+          if (y < nr)
+            for (int x = 0; x < 16 && x0 + x < g.nx && (x < 8 || two); ++x) v |= (uint32_t)(pl[(size_t)y * g.nx + x] != 0) << x;
+          m[y] = v;
         }
       }
-    }
-    const int64_t lb = bx + (int64_t)g.BX * (by + (int64_t)g.BY * bz);
-    if (bx < g.BX) dbits[lb * 8 + z] = word;
-    const unsigned nz8 = (__ballot_sync(0xffffffffu, word != 0ull) >> (8 * b)) & 0xFFu;
-    if (z == 0 && bx < g.BX) {
-      flag[lb] = nz8 ? 1 : 0;
-      if (nz8) {
-        const int nk = node_key_of(g, bx, by, bz);
-        if (!nflag[nk]) nflag[nk] = 1;
+      unsigned long long a = 0ull, b = 0ull;
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        a |= (unsigned long long)(m[y] & 0xffu) << (8 * y);
+        b |= (unsigned long long)(m[y] >> 8) << (8 * y);
       }
+      w0[z] = a;
+      w1[z] = b;
+    }
+    const int bx = bx0 + j;
+    const int64_t lb = bx + (int64_t)g.BX * (by + (int64_t)g.BY * bz);
+    unsigned long long any0 = 0ull, any1 = 0ull;
+    ulonglong2* d0 = reinterpret_cast<ulonglong2*>(dbits + lb * 8);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      d0[q] = make_ulonglong2(w0[2 * q], w0[2 * q + 1]);
+      any0 |= w0[2 * q] | w0[2 * q + 1];
+      any1 |= w1[2 * q] | w1[2 * q + 1];
+    }
+    flag[lb] = any0 != 0ull;
+    if (any0) nflag[node_key_of(g, bx, by, bz)] = 1;
+    if (two) {
+      ulonglong2* d1 = d0 + 4;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) d1[q] = make_ulonglong2(w1[2 * q], w1[2 * q + 1]);
+      flag[lb + 1] = any1 != 0ull;
+      if (any1) nflag[node_key_of(g, bx + 1, by, bz)] = 1;
     }
   }
 }
@@ -683,9 +729,10 @@ __global__ void __launch_bounds__(256) k_dense_alloc(VS vs, DenseScratch ds) {
     const int64_t lb = base + threadIdx.x;
     int node = -1, bx = 0, by = 0, bz = 0;
     if (lb < nbr && flag[lb]) {
-      bx = (int)(lb % g.BX);
-      by = (int)((lb / g.BX) % g.BY);
-      bz = (int)(lb / ((int64_t)g.BX * g.BY));
+      const uint32_t l = (uint32_t)lb, r = l / (uint32_t)g.BX;  // bricks < 2^32
+      bx = (int)(l - r * (uint32_t)g.BX);
+      by = (int)(r % (uint32_t)g.BY);
+      bz = (int)(r / (uint32_t)g.BY);
       node = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
     }
     int total = 0;
@@ -694,7 +741,7 @@ __global__ void __launch_bounds__(256) k_dense_alloc(VS vs, DenseScratch ds) {
       if (slot >= g.cap) {
         set_error(g, kErrOverflow);
       } else {
-        init_brick(g, slot, node, bx, by, bz, false);
+        init_brick_meta(g, slot, node, bx, by, bz);
         const ulonglong2* src = reinterpret_cast<const ulonglong2*>(dbits + lb * 8);
         ulonglong2* dst = reinterpret_cast<ulonglong2*>(g.occ + (size_t)slot * 8);
 #pragma unroll
@@ -1403,8 +1450,8 @@ int batch_blocks(const GridView& g, int kind) {
   switch (kind) {
     case BK_RESET: return clamp_blocks(((int64_t)g.node_cap * kNodeBricks + g.hmask + t) / t, 1024);
     case BK_DENSE: {
-      const int64_t units = (int64_t)((g.BX + 3) / 4) * g.BY * g.BZ;  // a warp each
-      return clamp_blocks((units * 32 + t - 1) / t, 152 * 64);
+      const int64_t units = (int64_t)((g.BX + kDenseX - 1) / kDenseX) * g.BY * g.BZ;  // a warp each
+      return clamp_blocks((units * 32 + t - 1) / t, 152 * 16);
     }
     case BK_DNODES: return clamp_blocks(((int64_t)g.NX * g.NY * g.NZ + t - 1) / t, 1024);
     case BK_DALLOC: return clamp_blocks(((int64_t)g.BX * g.BY * g.BZ + t - 1) / t, 152 * 64);

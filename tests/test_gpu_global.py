@@ -114,6 +114,18 @@ def test_dense_ingest_matches_records():
     assert np.array_equal(a, O.edt_factorised(occ, 12))
 
 
+@pytest.mark.parametrize("nx", [200, 520, 1040, 1037])
+def test_dense_ingest_row_widths(nx):
+    """Row widths for each load form of the dense ingest: 16-byte loads (1040, several chunks of
+    64 bricks with a ragged last one), 8-byte loads (200; 520 ends in a lone brick) and byte loads
+    (1037); ny and nz ragged."""
+    occ = W.bernoulli_grid(nx, (21, 19, nx), 0.01)
+    occ[3:9, 0, nx - 5:] = 1
+    a = gpu_global(occ, 9, dense=True).export_dense()
+    assert np.array_equal(a, gpu_global(occ, 9, dense=False).export_dense())
+    assert first_mismatch(a, O.edt_factorised(occ, 9)) is None
+
+
 def test_duplicates_and_clears_last_record_wins():
     import paper_2105_04419_gb300 as V
     rs = np.random.default_rng(5)
