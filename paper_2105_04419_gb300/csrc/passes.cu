@@ -115,11 +115,11 @@ template <int W>
 __device__ __forceinline__ void window_min8(const uint32_t* __restrict__ c, uint32_t (&out)[8], bool prune) {
   static_assert(W % 4 == 0, "window is a multiple of 4 offsets");
   uint32_t v[8 + 2 * W];
-  __half2 acc[8];
+  uint32_t acc[8];  // fp16x2 bits: non-negative halves order as unsigned 16-bit integers
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     v[k + W] = c[(k + W) * 32];
-    acc[k] = u2h(v[k + W]);
+    acc[k] = v[k + W];
   }
   bool live = true;  // warp-uniform
 #pragma unroll
@@ -130,23 +130,24 @@ __device__ __forceinline__ void window_min8(const uint32_t* __restrict__ c, uint
         const int d = 4 * ch + dd;
         v[W - d] = c[(W - d) * 32];
         v[W + 7 + d] = c[(W + 7 + d) * 32];
+        const __half2 sq = u2h(half2_bits(d * d));
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          __half2 m = __hmin2(u2h(v[k + W - d]), u2h(v[k + W + d]));
-          acc[k] = __hmin2(acc[k], __hadd2(m, u2h(half2_bits(d * d))));
+        for (int k = 0; k < 8; ++k) {  // two fp16 adds, one three-way minimum of the bit patterns
+          const uint32_t lo = h2u(__hadd2(u2h(v[k + W - d]), sq)), hi = h2u(__hadd2(u2h(v[k + W + d]), sq));
+          acc[k] = __vimin3_u16x2(acc[k], lo, hi);
         }
       }
       if (prune && ch + 1 < W / 4) {
         const int d1 = 4 * ch + 5;  // the next offset
-        __half2 mx = __hmax2(__hmax2(__hmax2(acc[0], acc[1]), __hmax2(acc[2], acc[3])),
-                             __hmax2(__hmax2(acc[4], acc[5]), __hmax2(acc[6], acc[7])));
-        const bool done = __hbge2(u2h(half2_bits(d1 * d1)), mx);
+        const uint32_t mx = __vimax3_u16x2(__vimax3_u16x2(acc[0], acc[1], acc[2]), __vimax3_u16x2(acc[3], acc[4], acc[5]),
+                                           __vmaxu2(acc[6], acc[7]));
+        const bool done = __hbge2(u2h(half2_bits(d1 * d1)), u2h(mx));
         live = !__all_sync(0xffffffffu, done);
       }
     }
   }
 #pragma unroll
-  for (int k = 0; k < 8; ++k) out[k] = h2u(acc[k]);
+  for (int k = 0; k < 8; ++k) out[k] = acc[k];
 }
 
 // ================================================================================================
