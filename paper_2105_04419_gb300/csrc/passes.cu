@@ -61,6 +61,15 @@ __host__ __device__ constexpr uint32_t half_bits(int n) {
 }
 __host__ __device__ constexpr uint32_t half2_bits(int n) { return half_bits(n) | (half_bits(n) << 16); }
 
+// Sets or clears one bit of a brick's flags with a reduction (no value returned, so the warp does
+// not wait for the word's round trip); each pass owns the bit it writes.
+__device__ __forceinline__ void set_flag_bit(const GridView& g, int slot, uint32_t bit, bool on) {
+  if (on)
+    atomicOr(&g.bflags[slot], bit);
+  else
+    atomicAnd(&g.bflags[slot], ~bit);
+}
+
 // ---- asynchronous bulk copies and mbarriers (inline PTX) ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -286,7 +295,7 @@ __device__ __forceinline__ void x_compute_rows(const GridView& g, const uint32_t
     *reinterpret_cast<uint4*>(g.g1 + (size_t)slot * kBrickVox + (y0 + r) * 64 + z * 8) =
         make_uint4(w[r][0], w[r][1], w[r][2], w[r][3]);
   const unsigned anyfin = __any_sync(0xffffffffu, fin);
-  if (lane == 0) g.bflags[slot] = anyfin ? (g.bflags[slot] | F_G1FIN) : (g.bflags[slot] & ~F_G1FIN);
+  if (lane == 0) set_flag_bit(g, slot, F_G1FIN, anyfin);
 }
 
 // y or z pass of one brick: the staged column holds planes along the pass axis, 32 words each
@@ -333,7 +342,7 @@ __device__ __forceinline__ void window_compute(const GridView& g, const uint32_t
   const unsigned anyfin = __any_sync(0xffffffffu, fin);
   if (lane == 0) {
     const uint32_t bit = AXIS == 1 ? F_G2FIN : F_FINITE;
-    g.bflags[slot] = anyfin ? (g.bflags[slot] | bit) : (g.bflags[slot] & ~bit);
+    set_flag_bit(g, slot, bit, anyfin);
   }
 }
 
@@ -539,7 +548,7 @@ __global__ void __launch_bounds__(kGenThreads) k_xy_generic(GridView g, const un
       bool fin = false;
       for (int v = threadIdx.x; v < 512; v += blockDim.x) fin |= g.g2[(size_t)s * kBrickVox + v] < (uint16_t)g.INF;
       int any = __syncthreads_or(fin);
-      if (threadIdx.x == 0) g.bflags[s] = any ? (g.bflags[s] | F_G2FIN) : (g.bflags[s] & ~F_G2FIN);
+      if (threadIdx.x == 0) set_flag_bit(g, s, F_G2FIN, any);
     }
   }
 }
@@ -574,7 +583,7 @@ __global__ void __launch_bounds__(kGenThreads) k_z_generic(GridView g, const uns
         finite |= best < g.INF;
       }
       int any = __syncthreads_or(finite);
-      if (threadIdx.x == 0) g.bflags[s] = any ? (g.bflags[s] | F_FINITE) : (g.bflags[s] & ~F_FINITE);
+      if (threadIdx.x == 0) set_flag_bit(g, s, F_FINITE, any);
     }
     __syncthreads();
   }
