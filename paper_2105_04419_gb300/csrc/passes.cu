@@ -354,7 +354,7 @@ __device__ __forceinline__ void window_compute(const GridView& g, const uint32_t
 // Resident blocks per SM the window passes ask the register allocator for (at most 80 registers
 // for RUN 4, 72 for RUN 8): enough warps to keep the packed-min pipe busy.
 __host__ __device__ constexpr int pass_min_blocks(int run, int axis) {
-  return axis == 0 ? 1 : (run == 4 ? 5 : (run == 8 ? 3 : 1));
+  return axis == 0 ? (run == 4 ? 10 : (run == 8 ? 7 : 3)) : (run == 4 ? 5 : (run == 8 ? 3 : 1));
 }
 
 template <int R, int RUN, int AXIS>
