@@ -1227,17 +1227,13 @@ cudaError_t launch_reset(const GridView& g, cudaStream_t st) {
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Apply staged records.  Bricks of "set" records are found or created through a stable radix
-// sort of brick keys, a unique pass and a compaction.  Bits: without tracking and when every
-// record sets a voxel, OR them in directly; otherwise (some record clears a voxel, or tracking
-// is on) sort (voxel key, record index) stably and let each voxel's last record decide.  With
-// tracking, each flipped voxel's brick is appended once to `changed`.
-// Apply staged records.  Bricks of "set" records are found or created through a stable radix
-// sort of brick keys, a unique pass and a compaction (few records), or a counting sort through one
-// flag per brick of the grid (many records).  Bits: in the global form the records' bits go to the
-// bricks directly (few records: OR-ed per record; many records: OR-ed into a dense scratch mask in
-// the counting pass and copied whole at allocation); whenever a record clears a voxel, or flips are
-// tracked, a stable sort of (voxel key, record index) lets each voxel's last record decide.  With
+// Apply staged records.  Bricks of "set" records are found or created through a counting sort over
+// one flag per brick of the grid (many records), or a stable radix sort of brick keys, a unique pass
+// and a compaction (few records).  Bits: in the global form, when every record sets a voxel, the
+// records' bits go to the bricks directly (many records: OR-ed into a dense scratch mask during the
+// counting pass and copied whole at allocation; few records: OR-ed per record).  Whenever a record
+// clears a voxel, or flips are tracked, each voxel's last record decides its bit through the
+// per-voxel last-record table (largest record index per voxel, then applied and reset).  With
 // tracking, each flipped voxel's brick is appended once to `changed`.
 static size_t ingest_scratch_bytes(const GridView& g, int64_t n, bool track) {
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
