@@ -23,6 +23,11 @@ RUNS = (4, 8, 16)
 # 1: full window; 3: pruned window; 7: pruned window with the x pass on plain loads (+4)
 VARIANTS = (1, 3, 7)
 X_DIRECT = 4
+# Candidates within TIE of the fastest count as equal, and the first of them in preference order
+# wins (the library defaults first), so that timing noise does not flip the choice between runs.
+TIE = 0.02
+RUN_PREF = (8, 16, 4)
+VARIANT_PREF = (3, 7, 1)
 _lock = threading.Lock()
 
 
@@ -53,23 +58,29 @@ def signature(target) -> str:
     return f"{dev}|R={infos[0]['R']}|grids={len(maps)}|bricks~{_round_sig(bricks)}"
 
 
+def _pick(cands, cost):
+    """The first candidate (in preference order) whose cost is within TIE of the lowest."""
+    best = min(cost(c) for c in cands)
+    return next(c for c in cands if cost(c) <= best * (1.0 + TIE))
+
+
 def choose(table: dict, joint_yz: bool = False) -> dict:
     """Pick the tuning from timed phases.  table[(variant, run)] = {"x_ms", "y_ms", "z_ms"}
     (medians).  The x pass takes its fastest (kernel, run) over every candidate (its time depends
     only on the X_DIRECT bit of the variant and the run); the window variant is the one whose best
     y + z is lowest; then y and z each take their fastest run under it (jointly when the phases are
-    timed together, as for batches)."""
-    xv, x_run = min(((v, r) for v in VARIANTS for r in RUNS), key=lambda vr: table[vr]["x_ms"])
+    timed together, as for batches).  Near-ties (TIE) go to the preferred candidate."""
+    xv, x_run = _pick([(v, r) for v in VARIANT_PREF for r in RUN_PREF], lambda vr: table[vr]["x_ms"])
 
     def yz_best(v):
         if joint_yz:
-            r = min(RUNS, key=lambda r: table[(v, r)]["z_ms"])
+            r = _pick(RUN_PREF, lambda r: table[(v, r)]["z_ms"])
             return table[(v, r)]["z_ms"], r, r
-        ry = min(RUNS, key=lambda r: table[(v, r)]["y_ms"])
-        rz = min(RUNS, key=lambda r: table[(v, r)]["z_ms"])
+        ry = _pick(RUN_PREF, lambda r: table[(v, r)]["y_ms"])
+        rz = _pick(RUN_PREF, lambda r: table[(v, r)]["z_ms"])
         return table[(v, ry)]["y_ms"] + table[(v, rz)]["z_ms"], ry, rz
 
-    window = min(VARIANTS, key=lambda v: yz_best(v)[0])
+    window = _pick(VARIANT_PREF, lambda v: yz_best(v)[0])
     _, y_run, z_run = yz_best(window)
     variant = (window & 3) | (xv & X_DIRECT)
     return {"x_run": x_run, "y_run": y_run, "z_run": z_run, "variant": variant}

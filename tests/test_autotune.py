@@ -26,7 +26,7 @@ def test_choose_x_direct_bit():
     def t(v, r):
         return {"x_ms": 1.0 if (v & 4 and r == 8) else 2.0,
                 "y_ms": 1.0 if v == 1 else 3.0, "z_ms": 1.0 if v == 1 else 3.0}
-    assert A.choose(table_from(t)) == {"x_run": 8, "y_run": 4, "z_run": 4, "variant": 5}
+    assert A.choose(table_from(t)) == {"x_run": 8, "y_run": 8, "z_run": 8, "variant": 5}  # equal runs: run 8
 
 
 def test_choose_variant_by_best_yz_sum():
@@ -37,6 +37,16 @@ def test_choose_variant_by_best_yz_sum():
         return {"x_ms": 1.0, "y_ms": 2.0, "z_ms": {4: 3.0, 8: 2.5, 16: 4.0}[r]}
     got = A.choose(table_from(t))
     assert got["variant"] == 1 and got["z_run"] == 8
+
+
+def test_choose_near_ties_go_to_the_preferred_run():
+    # z at run 16 is 1 % faster than at run 8 (noise-sized): run 8 is kept; y at run 4 is 10 %
+    # faster than at run 8: run 4 wins
+    def t(v, r):
+        return {"x_ms": 1.0 + (v & 4), "y_ms": {4: 0.9, 8: 1.0, 16: 1.2}[r] + (v == 1),
+                "z_ms": {4: 1.5, 8: 1.0, 16: 0.99}[r] + (v == 1)}
+    got = A.choose(table_from(t))
+    assert got == {"x_run": 8, "y_run": 4, "z_run": 8, "variant": 3}
 
 
 def test_choose_joint_yz():
