@@ -101,6 +101,7 @@ __global__ void k_reset_nodes(VS vs) {
   for (int64_t i = t0; i < nn * (3 * 1024 / 4); i += stride) reinterpret_cast<int4*>(g.mark)[i] = zero;
   for (int64_t i = t0; i < nn * (128 / 4); i += stride) reinterpret_cast<int4*>(g.amask)[i] = zero;
   for (int64_t i = t0; i < nn * (384 / 4); i += stride) reinterpret_cast<int4*>(g.mwork)[i] = zero;
+  for (int64_t i = t0; i < nn; i += stride) reinterpret_cast<int4*>(g.afresh)[i] = zero;
   for (int64_t i = t0; i <= (int64_t)g.hmask; i += stride) g.hslots[i] = ~0ull;
 }
 
@@ -116,6 +117,7 @@ __global__ void k_begin_update(GridView g) {
     g.counters[C_NEW_BRICKS] = 0;
     g.counters[C_UNIQUE] = 0;
     g.counters[C_HAS_ZERO] = 0;
+    g.counters[C_FRESH] = 0;
     g.counters[C_EPOCH] += 1;
   }
 }
@@ -960,6 +962,18 @@ __global__ void __launch_bounds__(256) k_dilate_nodes(VS vs) {
 
 // Mark bricks within Chebyshev radius R of brick (bx,by,bz) in amask: one (dy, dz) row (used by the
 // incremental form, where few bricks change).
+// An amask word that an update gives new bits: listed once per update (its fresh bit dedupes), so
+// that the update's allocation visits only those words.
+__device__ __forceinline__ void note_fresh_word(const GridView& g, int node, int word) {
+  const uint32_t b = 1u << (word & 31);
+  if (atomicOr(&g.afresh[(size_t)node * 4 + (word >> 5)], b) & b) return;
+  const int p = atomicAdd(&g.counters[C_FRESH], 1);
+  if (p < g.node_cap * 128)
+    g.flist[p] = node * 128 + word;
+  else
+    set_error(g, kErrOverflow);  // not reached: each word is listed at most once
+}
+
 __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int dy, int dz) {
   const int R = g.R;
   int y = by + dy, z = bz + dz;
@@ -973,7 +987,8 @@ __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int
       uint32_t bitsx = ((1u << (lx1 - lx0 + 1)) - 1u) << lx0;
       int ly = y & 15, lz = z & 15;
       int word = (ly >> 1) + 8 * lz;
-      atomicOr(&g.amask[(size_t)node * 128 + word], bitsx << (16 * (ly & 1)));
+      const uint32_t add = bitsx << (16 * (ly & 1));
+      if (add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add)) note_fresh_word(g, node, word);
     }
     x0 = seg_end + 1;
   }
@@ -1019,6 +1034,40 @@ __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
         }
       }
     }
+  }
+}
+
+// Incremental form: allocate the marked bricks without storage in the words this update marked
+// first (the fresh list), a warp per listed word and a lane per brick of it, fields at dmax^2; then
+// clear the word's fresh bit.  The work follows the update's dilation, not the size of the map.
+__global__ void __launch_bounds__(256) k_alloc_fresh(GridView g) {
+  const int nf = min(g.counters[C_FRESH], g.node_cap * 128);
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
+  for (int i = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); i < nf; i += nw) {
+    const int e = g.flist[i], node = e >> 7, word = e & 127;
+    const int l = word * 32 + lane;  // local brick: lx + 16 ly + 256 lz
+    const bool need = ((g.amask[(size_t)node * 128 + word] >> lane) & 1u) &&
+                      g.child[(size_t)node * kNodeBricks + l] == kNoSlot;
+    const unsigned bal = __ballot_sync(0xffffffffu, need);
+    int base = 0;
+    if (lane == 0 && bal) {
+      base = atomicAdd(&g.counters[C_NBRICKS], __popc(bal));
+      atomicAdd(&g.counters[C_NEW_BRICKS], __popc(bal));
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (need) {
+      const int slot = base + __popc(bal & ((1u << lane) - 1u));
+      if (slot >= g.cap) {
+        set_error(g, kErrOverflow);
+      } else {
+        const int key = g.node_key[node];
+        const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+        init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8), true);
+        g.child[(size_t)node * kNodeBricks + l] = slot;
+      }
+    }
+    if (lane == 0) atomicAnd(&g.afresh[(size_t)node * 4 + (word >> 5)], ~(1u << (word & 31)));
   }
 }
 
@@ -1521,7 +1570,7 @@ cudaError_t launch_build_items_batch(const GridView* views, const BatchShape& b,
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const int32_t* changed, const Items& it,
                                     cudaStream_t st) {
   VDB_LAUNCH(k_changed_flags_dilate, 1024, kT, 0, st, g, changed);
-  VDB_LAUNCH(k_alloc_marked<OneView>, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, OneView{g}, true);
+  VDB_LAUNCH(k_alloc_fresh, g.node_cap < 256 ? g.node_cap : 256, kT, 0, st, g);
   VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }
