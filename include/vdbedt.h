@@ -63,6 +63,7 @@ typedef struct {
   void* stream;        /* cudaStream_t to run on; NULL: the handle creates and owns one */
   uint32_t flags;      /* reserved, 0 */
   int64_t max_bricks;  /* brick capacity; 0: every brick of the grid (always enough) */
+  int64_t max_nodes;   /* interior-node capacity (a node covers 16^3 bricks); 0: every node of the grid */
 } vdbedt_config;
 
 typedef struct {
@@ -87,8 +88,13 @@ typedef struct {
 } vdbedt_update_stats;
 
 /* Create a handle for an nx x ny x nz grid with no obstacles (every D = dmax^2).
- * Allocates the grid's storage for cfg->max_bricks bricks up front; the record stage and the
- * ingest scratch grow on demand (vdbedt_set_occupancy_counted reserves them ahead).
+ * Allocates the grid's storage for cfg->max_bricks bricks (about 4.1 KB each) and cfg->max_nodes
+ * interior nodes (about 31 KB each) up front; the record stage and the ingest scratch grow on
+ * demand (vdbedt_set_occupancy_counted reserves them ahead).  With both capacities set, the memory
+ * follows the mapped part of the grid, not its size: a grid may span up to 2^32 bricks (e.g.
+ * 16384 x 16384 x 8184 voxels) with obstacles in a small part of it.  Record-driven ingest and
+ * updates work at any grid size; the dense entry points and vdbedt_export_dense scale with the grid.
+ * Exceeding a capacity during a transform is EOVERFLOW.
  * EINVAL: a size < 1, dmax outside [1, VDBEDT_DMAX_LIMIT], voxel_size <= 0, bad device.
  * ENOMEM: device allocation failed. */
 vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out);

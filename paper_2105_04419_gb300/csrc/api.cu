@@ -270,7 +270,7 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   const int64_t NX = ceil_div(BX, 16), NY = ceil_div(BY, 16), NZ = ceil_div(BZ, 16);
   int64_t cap = cfg->max_bricks > 0 ? std::min<int64_t>(cfg->max_bricks, BX * BY * BZ) : BX * BY * BZ;
   if (cap * 512 >= (int64_t)0xFFFFFFFFll) return fail(nullptr, VDBEDT_EINVAL, "brick capacity too large (max 8M)");
-  const int64_t node_cap = NX * NY * NZ;
+  const int64_t node_cap = cfg->max_nodes > 0 ? std::min<int64_t>(cfg->max_nodes, NX * NY * NZ) : NX * NY * NZ;
 
   DeviceGuard guard(cfg->device);
   vdbedt_map* h = new vdbedt_map();
@@ -320,6 +320,7 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   AL(g.amask, node_cap * 128);
   AL(g.mwork, node_cap * 384);
   AL(g.afresh, node_cap * 4);
+  AL(g.nclaim, node_cap * 128);
   AL(g.flist, node_cap * 128);
   AL(g.node_key, node_cap);
   AL(g.mark, node_cap * 3 * 1024);
@@ -364,6 +365,7 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   cudaMemsetAsync(g.amask, 0, sizeof(uint32_t) * (size_t)node_cap * 128, h->st);
   cudaMemsetAsync(g.mwork, 0, sizeof(uint32_t) * (size_t)node_cap * 384, h->st);
   cudaMemsetAsync(g.afresh, 0, sizeof(uint32_t) * (size_t)node_cap * 4, h->st);
+  cudaMemsetAsync(g.nclaim, 0, sizeof(uint32_t) * (size_t)node_cap * 128, h->st);
   cudaMemsetAsync(g.mark, 0, sizeof(int32_t) * (size_t)node_cap * 3 * 1024, h->st);
   if (!slice) cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, h->st);
   e = cudaStreamSynchronize(h->st);

@@ -102,6 +102,7 @@ __global__ void k_reset_nodes(VS vs) {
   for (int64_t i = t0; i < nn * (128 / 4); i += stride) reinterpret_cast<int4*>(g.amask)[i] = zero;
   for (int64_t i = t0; i < nn * (384 / 4); i += stride) reinterpret_cast<int4*>(g.mwork)[i] = zero;
   for (int64_t i = t0; i < nn; i += stride) reinterpret_cast<int4*>(g.afresh)[i] = zero;
+  for (int64_t i = t0; i < nn * (128 / 4); i += stride) reinterpret_cast<int4*>(g.nclaim)[i] = zero;
   for (int64_t i = t0; i <= (int64_t)g.hmask; i += stride) g.hslots[i] = ~0ull;
 }
 
@@ -118,6 +119,7 @@ __global__ void k_begin_update(GridView g) {
     g.counters[C_UNIQUE] = 0;
     g.counters[C_HAS_ZERO] = 0;
     g.counters[C_FRESH] = 0;
+    g.counters[C_DEFERRED] = 0;
     g.counters[C_EPOCH] += 1;
   }
 }
@@ -437,13 +439,30 @@ __global__ void k_apply_set_only(GridView g, const rec_t* __restrict__ rec, int6
   }
 }
 
-// Tracked ingest (incremental form): the bricks of "set" records that are not stored yet are
-// appended once each to a list (brick flags dedupe; count in C_UNIQUE, cleared when the update
-// begins), with flags on their node keys; after the nodes are created, the listed bricks are
-// allocated with their fields at dmax^2 and their flags cleared again, so the flag arrays stay
-// zero between updates.  Records of stored bricks need no brick work at all.
+// Tracked ingest (incremental form): each brick of a "set" record that is not stored yet is listed
+// once for allocation (count in C_UNIQUE, cleared when the update begins).  A per-node bit
+// (`nclaim`, the amask layout) dedupes the bricks, so the scratch follows the records and the node
+// capacity, not the size of the grid.  A record whose node does not exist yet flags its node key
+// and the deferral counter; once the flagged nodes are created, a second pass (which returns at
+// once when nothing was deferred) lists those bricks.  The listed bricks are then allocated with
+// their fields at dmax^2 and their bits cleared, so `nclaim` is zero between updates.  Records of
+// stored bricks need no brick work at all.
+__device__ __forceinline__ void list_missing_brick(const GridView& g, int node, int bx, int by, int bz,
+                                                   unsigned long long* list) {
+  const int l = local_brick(bx, by, bz);
+  const uint32_t b = 1u << (l & 31);
+  if (atomicOr(&g.nclaim[(size_t)node * 128 + (l >> 5)], b) & b) return;
+  const int p = atomicAdd(&g.counters[C_UNIQUE], 1);
+  if (p < g.cap)
+    list[p] = pack_brick(bx, by, bz);
+  else
+    set_error(g, kErrOverflow);  // more new bricks than the capacity holds
+}
+
+template <bool DEFERRED>
 __global__ void k_rec_missing(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
-                              int32_t* __restrict__ flag, int32_t* __restrict__ nflag, int32_t* __restrict__ list) {
+                              int32_t* __restrict__ nflag, unsigned long long* __restrict__ list) {
+  if (DEFERRED && g.counters[C_DEFERRED] == 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t n = rec_count(n_max, n_dev);
   GRID_STRIDE(i, n) {
@@ -454,38 +473,39 @@ __global__ void k_rec_missing(GridView g, const rec_t* __restrict__ rec, int64_t
         bad = true;
       } else if (r.w == 1) {
         const int bx = r.x >> 3, by = r.y >> 3, bz = r.z >> 3;
-        if (find_brick(g, bx, by, bz) < 0) {
-          const int64_t lb = bx + (int64_t)g.BX * (by + (int64_t)g.BY * bz);
-          if (atomicCAS(&flag[lb], 0, 1) == 0) {
-            list[atomicAdd(&g.counters[C_UNIQUE], 1)] = (int32_t)lb;
-            const int nk = node_key_of(g, bx, by, bz);
-            if (!nflag[nk]) nflag[nk] = 1;
-          }
+        const int nk = node_key_of(g, bx, by, bz);
+        const int node = find_node(g, (uint32_t)nk);
+        if (node >= 0) {
+          if (g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] < 0)
+            list_missing_brick(g, node, bx, by, bz, list);
+        } else if (!DEFERRED && !nflag[nk]) {
+          nflag[nk] = 1;
+          atomicOr(&g.counters[C_DEFERRED], 1);
         }
       } else {
         zero = true;
       }
     }
-    if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
-    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+    if (!DEFERRED) {
+      if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+      if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+    }
   }
 }
 
-__global__ void k_alloc_listed(GridView g, const int32_t* __restrict__ list, int32_t* __restrict__ flag, int64_t max) {
+__global__ void k_alloc_listed(GridView g, const unsigned long long* __restrict__ list, int64_t max) {
   const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], max);
   GRID_STRIDE(j, cnt) {
     int node = -1, bx = 0, by = 0, bz = 0;
     int* e = nullptr;
     bool need = false;
     if (j < cnt) {
-      const int64_t lb = list[j];
-      flag[lb] = 0;
-      bx = (int)(lb % g.BX);
-      by = (int)((lb / g.BX) % g.BY);
-      bz = (int)(lb / ((int64_t)g.BX * g.BY));
+      unpack_brick(list[j], bx, by, bz);
       node = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
       if (node >= 0) {
-        e = &g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
+        const int l = local_brick(bx, by, bz);
+        atomicAnd(&g.nclaim[(size_t)node * 128 + (l >> 5)], ~(1u << (l & 31)));
+        e = &g.child[(size_t)node * kNodeBricks + l];
         need = *e == kNoSlot;
       }
     }
@@ -795,7 +815,16 @@ __global__ void k_obstacle_flags(VS vs) {
   }
 }
 
-// One warp per node holding obstacle bricks: create the nodes within ceil(R / 16) nodes of it.
+__device__ __forceinline__ uint32_t row16(const uint32_t* m, int y, int z) {
+  return (m[(y >> 1) + 8 * z] >> (16 * (y & 1))) & 0xFFFFu;
+}
+
+// One warp per node holding obstacle bricks: create the neighbouring nodes that hold a brick within
+// R bricks (Chebyshev) of one of its obstacle bricks, the only nodes its dilation reaches.  With
+// R <= 16 the neighbours are the 26 adjacent nodes: neighbour (dx, dy, dz) is needed when one
+// obstacle brick lies within R bricks of the side shared with it along every axis with a nonzero
+// offset.  Each lane classifies 8 of the node's 256 brick rows and the warp ORs the 27-bit set of
+// directions they reach.  (R > 16: every node within ceil(R / 16) nodes.)
 template <class VS>
 __global__ void k_node_halo(VS vs) {
   int bid, nblk, gi;
@@ -810,17 +839,34 @@ __global__ void k_node_halo(VS vs) {
     if (!__any_sync(0xffffffffu, any != 0u)) continue;
     const int key = g.node_key[node];
     const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+    uint32_t dirs = 0xFFFFFFFFu;  // directions o = (dx + 1) + 3 (dy + 1) + 9 (dz + 1) to create
+    if (NR == 1) {
+      const uint32_t lo = g.R >= 16 ? 0xFFFFu : ((1u << g.R) - 1u), hi = (lo << (16 - g.R)) & 0xFFFFu;
+      dirs = 0u;
+      for (int r = lane; r < 256; r += 32) {
+        const int yy = r & 15, zz = r >> 4;
+        const uint32_t row = row16(om, yy, zz);
+        if (!row) continue;
+        // per axis, bit k: offset k - 1 reachable from this row's obstacle bricks
+        const uint32_t ax = ((row & lo) ? 1u : 0u) | 2u | ((row & hi) ? 4u : 0u);
+        const uint32_t ay = (yy < g.R ? 1u : 0u) | 2u | (yy >= 16 - g.R ? 4u : 0u);
+        const uint32_t az = (zz < g.R ? 1u : 0u) | 2u | (zz >= 16 - g.R ? 4u : 0u);
+        for (int kz = 0; kz < 3; ++kz)
+          for (int ky = 0; ky < 3; ++ky)
+            for (int kx = 0; kx < 3; ++kx)
+              if ((az >> kz) & (ay >> ky) & (ax >> kx) & 1u) dirs |= 1u << (kx + 3 * (ky + 3 * kz));
+      }
+      dirs = __reduce_or_sync(0xffffffffu, dirs);
+    }
     for (int o = lane; o < side * side * side; o += 32) {
-      int x = nxn + o % side - NR, y = nyn + (o / side) % side - NR, z = nzn + o / (side * side) - NR;
-      if (x < 0 || y < 0 || z < 0 || x >= g.NX || y >= g.NY || z >= g.NZ) continue;
-      get_or_create_node(g, (uint32_t)(x + g.NX * (y + g.NY * z)));
+      const int dx = o % side - NR, dy = (o / side) % side - NR, dz = o / (side * side) - NR;
+      const int x = nxn + dx, y = nyn + dy, z = nzn + dz;
+      if (x < 0 || y < 0 || z < 0 || x >= g.NX || y >= g.NY || z >= g.NZ || (dx == 0 && dy == 0 && dz == 0)) continue;
+      if (NR > 1 || ((dirs >> o) & 1u)) get_or_create_node(g, (uint32_t)(x + g.NX * (y + g.NY * z)));
     }
   }
 }
 
-__device__ __forceinline__ uint32_t row16(const uint32_t* m, int y, int z) {
-  return (m[(y >> 1) + 8 * z] >> (16 * (y & 1))) & 0xFFFFu;
-}
 
 __device__ __forceinline__ int node_at(const GridView& g, int x, int y, int z) {
   if (x < 0 || y < 0 || z < 0 || x >= g.NX || y >= g.NY || z >= g.NZ) return -1;
@@ -1288,7 +1334,7 @@ static size_t ingest_scratch_bytes(const GridView& g, int64_t n, bool track) {
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
   const bool counting = n >= nbr_all / 4;
   const bool dense_bits = counting && !track && nbr_all * 8 < (int64_t)0xFFFFFFFFll;
-  const int64_t m = n > nbr_all ? n : nbr_all;
+  const int64_t m = counting && nbr_all > n ? nbr_all : n;  // brick flags only on the counting path
   const size_t nb4 = align_up((size_t)m * 4);
   const size_t nkeys_al = ((size_t)g.NX * g.NY * g.NZ + 63) & ~(size_t)63;
   const size_t flags = align_up(((size_t)m + nkeys_al) * 4);  // node flags, then brick flags
@@ -1305,10 +1351,10 @@ static cudaError_t ensure_vlast(const GridView& g, Scratch& vl, cudaStream_t st)
   return cudaMemsetAsync(vl.buf, 0xFF, want, st);
 }
 
-// The tracked ingest's zeroed arrays: brick flags, node-key flags, the list of missing bricks.
+// The tracked ingest's scratch: node-key flags (zero between updates), the list of missing bricks.
 static size_t tracked_bytes(const GridView& g) {
-  const size_t nbr = (size_t)g.BX * g.BY * g.BZ, nkeys = (size_t)g.NX * g.NY * g.NZ;
-  return align_up(nbr * 4) + align_up(nkeys * 4) + align_up(nbr * 4);
+  const size_t nkeys = (size_t)g.NX * g.NY * g.NZ;
+  return align_up(nkeys * 4) + align_up((size_t)g.cap * 8);
 }
 
 static cudaError_t ensure_tracked(const GridView& g, Scratch& miss, cudaStream_t st) {
@@ -1339,17 +1385,17 @@ static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, in
   if (e != cudaSuccess) return e;
   e = ensure_vlast(g, vl, st);
   if (e != cudaSuccess) return e;
-  const size_t nbr = (size_t)g.BX * g.BY * g.BZ, nkeys = (size_t)g.NX * g.NY * g.NZ;
+  const size_t nkeys = (size_t)g.NX * g.NY * g.NZ;
   char* p = (char*)miss.buf;
-  int32_t* flag = (int32_t*)p;
-  int32_t* nflag = (int32_t*)(p + align_up(nbr * 4));
-  int32_t* list = (int32_t*)(p + align_up(nbr * 4) + align_up(nkeys * 4));
+  int32_t* nflag = (int32_t*)p;
+  unsigned long long* list = (unsigned long long*)(p + align_up(nkeys * 4));
   int32_t* vlast = (int32_t*)vl.buf;
   const unsigned nbk = blocks_for(n);
-  VDB_LAUNCH(k_rec_missing, nbk, kT, 0, st, g, rec, n, n_dev, flag, nflag, list);
+  const int64_t nlist = n < (int64_t)g.cap ? n : (int64_t)g.cap;
+  VDB_LAUNCH(k_rec_missing<false>, nbk, kT, 0, st, g, rec, n, n_dev, nflag, list);
   VDB_LAUNCH(k_create_flagged_nodes, blocks_for((int64_t)nkeys), kT, 0, st, g, nflag, (int64_t)nkeys);
-  VDB_LAUNCH(k_alloc_listed, blocks_for(n < (int64_t)nbr ? n : (int64_t)nbr), kT, 0, st, g, list, flag,
-             n < (int64_t)nbr ? n : (int64_t)nbr);
+  VDB_LAUNCH(k_rec_missing<true>, nbk, kT, 0, st, g, rec, n, n_dev, nflag, list);
+  VDB_LAUNCH(k_alloc_listed, blocks_for(nlist), kT, 0, st, g, list, nlist);
   VDB_LAUNCH(k_rec_last, nbk, kT, 0, st, g, rec, n, n_dev, true, vlast);
   VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, n, n_dev, true, true, vlast, changed);
   return cudaGetLastError();
@@ -1363,7 +1409,7 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
   const bool counting = n >= nbr_all / 4;
   // the dense mask is indexed by a 32-bit word number (8 words per brick)
   const bool dense_bits = counting && !track && nbr_all * 8 < (int64_t)0xFFFFFFFFll;
-  const int64_t m = n > nbr_all ? n : nbr_all;
+  const int64_t m = counting && nbr_all > n ? nbr_all : n;  // brick flags only on the counting path
   const size_t nb4 = align_up((size_t)m * 4);
   cudaError_t e = ensure_scratch(scr, ingest_scratch_bytes(g, n, track));
   if (e != cudaSuccess) return e;

@@ -51,7 +51,7 @@ enum Counter : int {
   C_OBST = 12,
   C_FRESH = 13,  // compute-set words first marked by this update (incremental), listed in flist
   C_EPOCH = 14,  // incremental update epoch (run and brick dedupe marks)
-  C_SPARE = 15,
+  C_DEFERRED = 15,  // the tracked ingest met "set" records whose node did not exist yet
   C_NUM = 16
 };
 
@@ -75,6 +75,7 @@ struct GridView {
   uint32_t* mwork;    // [node_cap * 384] obstacle bits and two dilation stages, same layout
   uint32_t* afresh;   // [node_cap * 4] bit w of the node's 4 words: amask word w got bits this update
   int32_t* flist;     // [node_cap * 128] node * 128 + word of those words (C_FRESH of them)
+  uint32_t* nclaim;   // [node_cap * 128] bricks listed for allocation by the running ingest (amask layout)
   int32_t* node_key;  // [node_cap]
   int32_t* mark;      // [node_cap * 3 * 1024] epoch of the last time each run along axis a was queued
   unsigned long long* occ;  // [cap * 8]

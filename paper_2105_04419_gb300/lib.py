@@ -27,7 +27,7 @@ class VdbedtError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("dmax", ctypes.c_int32),
                 ("voxel_size", ctypes.c_float), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("flags", ctypes.c_uint32), ("max_bricks", ctypes.c_int64)]
+                ("flags", ctypes.c_uint32), ("max_bricks", ctypes.c_int64), ("max_nodes", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -132,7 +132,7 @@ class Map:
     """One sparse distance field (a vdbedt handle) on a CUDA device."""
 
     def __init__(self, nx: int, ny: int, nz: int, dmax: int, voxel_size: float = 0.1, device: int = 0,
-                 stream=None, max_bricks: int = 0, _borrow=None):
+                 stream=None, max_bricks: int = 0, max_nodes: int = 0, _borrow=None):
         lib = load()
         torch = _torch()
         if _borrow is not None:
@@ -146,7 +146,8 @@ class Map:
             stream = torch.cuda.Stream(device)
         self.device = device
         self.stream = stream
-        cfg = Config(nx, ny, nz, dmax, voxel_size, device, ctypes.c_void_p(stream.cuda_stream), 0, max_bricks)
+        cfg = Config(nx, ny, nz, dmax, voxel_size, device, ctypes.c_void_p(stream.cuda_stream), 0, max_bricks,
+                     max_nodes)
         h = ctypes.c_void_p()
         _check(lib.vdbedt_create(ctypes.byref(cfg), ctypes.byref(h)), "vdbedt_create")
         self._h = h
