@@ -1235,22 +1235,45 @@ __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int 
 }
 
 // Slots of each queued run's bricks with R bricks of halo on both sides along the axis.
-__global__ void k_item_slots(GridView g, int axis, int run, const unsigned long long* __restrict__ items,
-                             int32_t* __restrict__ out) {
+__global__ void k_item_slots(GridView g, int rx, int ry, int rz, Items it) {
+  // blockIdx.y = axis; a warp per queued run, a lane per slot: a run lies inside one node and its
+  // halo (R <= 6 < 16 bricks) reaches at most the neighbouring node on each side along the axis,
+  // so three node lookups (lanes 0-2) serve the whole slot list, read from the child tables
+  const int axis = (int)blockIdx.y;
+  const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
+  const unsigned long long* __restrict__ items = it.run[axis];
+  int32_t* __restrict__ out = it.slots[axis];
   const int n = min(g.items_ctr[axis], g.item_cap);
   const int nb = run + 2 * g.R;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n * kItemSlots;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int item = (int)(i / kItemSlots), j = (int)(i % kItemSlots);
-    int s = -1;
-    if (j < nb) {
-      int bx, by, bz;
-      unpack_brick(items[item], bx, by, bz);
-      const int off = j - g.R;
-      s = find_brick(g, bx + (axis == 0 ? off : 0), by + (axis == 1 ? off : 0), bz + (axis == 2 ? off : 0));
-      if (s >= 0) s += g.slot_base;
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
+  for (int item = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); item < n; item += nw) {
+    int bx, by, bz;
+    unpack_brick(items[item], bx, by, bz);
+    const int ba = axis == 0 ? bx : (axis == 1 ? by : bz);
+    const int Ba = axis == 0 ? g.BX : (axis == 1 ? g.BY : g.BZ);
+    const int NQa = axis == 0 ? g.NX : (axis == 1 ? g.NY : g.NZ);
+    int nq = -1;
+    if (lane < 3) {
+      const int qa = (ba >> 4) + lane - 1;
+      if (qa >= 0 && qa < NQa) {
+        const int qx = axis == 0 ? qa : bx >> 4, qy = axis == 1 ? qa : by >> 4, qz = axis == 2 ? qa : bz >> 4;
+        nq = find_node(g, (uint32_t)(qx + g.NX * (qy + g.NY * qz)));
+      }
     }
-    out[i] = s;
+    const int n_lo = __shfl_sync(0xffffffffu, nq, 0), n_mid = __shfl_sync(0xffffffffu, nq, 1),
+              n_hi = __shfl_sync(0xffffffffu, nq, 2);
+    int s = -1;
+    const int ca = ba + lane - g.R;  // this slot's brick coordinate along the axis
+    if (lane < nb && ca >= 0 && ca < Ba) {
+      const int node = (ca >> 4) < (ba >> 4) ? n_lo : ((ca >> 4) > (ba >> 4) ? n_hi : n_mid);
+      if (node >= 0) {
+        const int cx = axis == 0 ? ca : bx, cy = axis == 1 ? ca : by, cz = axis == 2 ? ca : bz;
+        s = g.child[(size_t)node * kNodeBricks + local_brick(cx, cy, cz)];
+        if (s >= 0) s += g.slot_base;
+      }
+    }
+    out[(size_t)item * kItemSlots + lane] = s;
   }
 }
 
@@ -1529,7 +1552,7 @@ cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, const It
 }
 
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st) {
-  for (int a = 0; a < 3; ++a) VDB_LAUNCH(k_item_slots, 2048, kT, 0, st, g, a, t.run[a], it.run[a], it.slots[a]);
+  VDB_LAUNCH(k_item_slots, dim3(1024, 3), kT, 0, st, g, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }
 
