@@ -32,9 +32,11 @@
 // such integer exactly, the sum of two is exact whenever it is below 2048 and rounds to a value
 // >= 2048 otherwise, and min is exact, so every minimum below dmax^2 is computed exactly and every
 // candidate at or above it stays at or above it.  Each lane owns 8 consecutive outputs of two
-// neighbouring lines, pairing offsets +d and -d: acc = min(acc, min(v[k-d], v[k+d]) + d^2).  The
-// pruned form stops when (d + 1)^2 reaches every output's current minimum in the warp, and skips
-// windows whose input bricks hold no value below dmax^2.
+// neighbouring lines, pairing offsets +d and -d: acc = min(acc, v[k-d] + d^2, v[k+d] + d^2), two
+// fp16 adds and one three-input minimum taken on the bit patterns as unsigned 16-bit integers
+// (non-negative fp16 values order like their bit patterns).  The pruned form stops when (d + 1)^2
+// reaches every output's current minimum in the warp, and skips windows whose input bricks hold no
+// value below dmax^2.
 //
 // Grids with dmax above 45 (up to 181) take the generic kernels at the end of the file: int32
 // arithmetic read from shared memory with a runtime window.
