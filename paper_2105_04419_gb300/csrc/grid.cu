@@ -581,24 +581,23 @@ __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t 
 }
 
 // ---- dense ingest ----
-// Two streaming passes.  (1) Masks: one warp per 4 consecutive bricks along x; lane (b, z) reads the
-// 8 x-rows (y = 0..7) of brick b at depth z, 8 bytes each (one 8-byte load when rows are 8-byte
-// aligned), so every load instruction covers whole 32-byte sectors and the warp writes its
-// bricks' 64-byte masks as 256 contiguous bytes of a dense per-brick scratch, with one flag per
-// brick and one per node key.  (2) After the flagged nodes are created, one thread per brick of
-// the grid allocates the occupied bricks (slots reserved with one atomic per block) and copies
-// their masks in.  The grid was reset just before, so every brick is new; brick fields are left
-// for the global transform that always follows a dense ingest.
-__device__ __forceinline__ uint32_t nonzero_bytes(unsigned long long w) {
-  // bit i = byte i nonzero: fold each byte onto its low bit, then gather the eight low bits
-  w |= w >> 4;
-  w |= w >> 2;
-  w |= w >> 1;
-  w &= 0x0101010101010101ull;
-  return (uint32_t)((w * 0x0102040810204080ull) >> 56);
+// Two streaming passes.  (1) Masks: one warp per brick row (below) writes each brick's eight mask
+// words into a plane-major scratch, with one flag per brick and one per node key.  (2) After the
+// flagged nodes are created, one thread per brick of the grid allocates the occupied bricks (slots
+// reserved with one atomic per block) and copies their masks in.  The grid was reset just before,
+// so every brick is new; brick fields are left for the global transform that always follows a
+// dense ingest.
+
+// Bit i set when byte i of w is nonzero: the high bit of (low seven bits + 0x7F) | byte marks a
+// nonzero byte, and one multiply gathers the four marks (bits 7, 15, 23, 31 land on 28 .. 31
+// without overlapping any other partial product).
+__device__ __forceinline__ uint32_t nonzero4(uint32_t w) {
+  const uint32_t t = (((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;
+  return (t * 0x00204081u) >> 28;
 }
 
-// Scratch of the dense ingest: masks (8 words per brick of the grid), brick flags, node-key flags.
+// Scratch of the dense ingest: masks (8 words per brick of the grid, plane-major: plane z of brick
+// lb at dbits[z * bricks + lb]), brick flags, node-key flags.
 // A single grid's pointers are its own; grid i of a batch adds off[3i], off[3i + 1], off[3i + 2].
 struct DenseScratch {
   unsigned long long* dbits;
@@ -619,13 +618,14 @@ struct DenseScratch {
 
 // Pass 1: one warp per unit (a brick row: by, bz and up to kDenseX bricks along x).  The unit's
 // 64 input rows form eight contiguous stretches (one per plane z); each lane loads 16 bytes (two
-// bricks) of each row, a plane's eight loads issued together, and assembles both bricks' eight
-// mask words in registers -- no shared memory, no block barrier.  A lane then writes its two bricks
-// whole (a warp's stores are one contiguous run) with their flags, and marks their nodes.
+// bricks) of each row, a plane's eight loads issued together, and assembles both bricks' mask word
+// of that plane in registers -- no shared memory, no block barrier -- and stores it to the
+// plane-major scratch (a warp's stores are one contiguous run).  After the eight planes a lane
+// writes its two bricks' flags and marks their nodes.
 constexpr int kDenseX = 64;
 
 template <class VS, class SRC>
-__global__ void __launch_bounds__(256, 2) k_dense_masks(VS vs, SRC src, DenseScratch ds) {
+__global__ void __launch_bounds__(256, 4) k_dense_masks(VS vs, SRC src, DenseScratch ds) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   const uint8_t* __restrict__ grid = src.get(gi);
@@ -633,6 +633,7 @@ __global__ void __launch_bounds__(256, 2) k_dense_masks(VS vs, SRC src, DenseScr
   int32_t* flag;
   int32_t* nflag;
   ds.at(gi, dbits, flag, nflag);
+  const int64_t nbr = (int64_t)g.BX * g.BY * g.BZ;
   const uint32_t nch = (uint32_t)(g.BX + kDenseX - 1) / kDenseX;
   const uint32_t nunits = nch * (uint32_t)g.BY * (uint32_t)g.BZ;
   const int lane = threadIdx.x & 31;
@@ -651,8 +652,9 @@ __global__ void __launch_bounds__(256, 2) k_dense_masks(VS vs, SRC src, DenseScr
     const int nrow = min(8, g.ny - by * 8), nplane = min(8, g.nz - bz * 8);
     const uint8_t* base = grid + ((size_t)bz * 8 * g.ny + (size_t)by * 8) * g.nx + x0;
     const size_t zstride = (size_t)g.ny * g.nx;
-    unsigned long long w0[8], w1[8];  // plane z's mask word of brick j and of brick j + 1
-#pragma unroll
+    const int64_t lb = (bx0 + j) + (int64_t)g.BX * (by + (int64_t)g.BY * bz);
+    unsigned long long any0 = 0ull, any1 = 0ull;
+#pragma unroll 2
     for (int z = 0; z < 8; ++z) {
       const uint8_t* pl = base + (size_t)z * zstride;
       const int nr = z < nplane ? nrow : 0;
@@ -664,17 +666,17 @@ __global__ void __launch_bounds__(256, 2) k_dense_masks(VS vs, SRC src, DenseScr
           w[y] = y < nr ? __ldg(reinterpret_cast<const uint4*>(pl + (size_t)y * g.nx)) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int y = 0; y < 8; ++y)
-          m[y] = nonzero_bytes(((unsigned long long)w[y].y << 32) | w[y].x) |
-                 (nonzero_bytes(((unsigned long long)w[y].w << 32) | w[y].z) << 8);
+          m[y] = nonzero4(w[y].x) | (nonzero4(w[y].y) << 4) | (nonzero4(w[y].z) << 8) | (nonzero4(w[y].w) << 12);
       } else if (v8) {
-        unsigned long long lo[8], hi[8];
+        uint2 lo[8], hi[8];
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
-          lo[y] = y < nr ? __ldg(reinterpret_cast<const unsigned long long*>(pl + (size_t)y * g.nx)) : 0ull;
-          hi[y] = y < nr && two ? __ldg(reinterpret_cast<const unsigned long long*>(pl + (size_t)y * g.nx + 8)) : 0ull;
+          lo[y] = y < nr ? __ldg(reinterpret_cast<const uint2*>(pl + (size_t)y * g.nx)) : make_uint2(0u, 0u);
+          hi[y] = y < nr && two ? __ldg(reinterpret_cast<const uint2*>(pl + (size_t)y * g.nx + 8)) : make_uint2(0u, 0u);
         }
 #pragma unroll
-        for (int y = 0; y < 8; ++y) m[y] = nonzero_bytes(lo[y]) | (nonzero_bytes(hi[y]) << 8);
+        for (int y = 0; y < 8; ++y)
+          m[y] = nonzero4(lo[y].x) | (nonzero4(lo[y].y) << 4) | (nonzero4(hi[y].x) << 8) | (nonzero4(hi[y].y) << 12);
       } else {  // ragged rows: byte loads
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
@@ -690,25 +692,16 @@ __global__ void __launch_bounds__(256, 2) k_dense_masks(VS vs, SRC src, DenseScr
         a |= (unsigned long long)(m[y] & 0xffu) << (8 * y);
         b |= (unsigned long long)(m[y] >> 8) << (8 * y);
       }
-      w0[z] = a;
-      w1[z] = b;
+      unsigned long long* plane = dbits + (size_t)z * nbr;
+      plane[lb] = a;
+      if (two) plane[lb + 1] = b;
+      any0 |= a;
+      any1 |= b;
     }
     const int bx = bx0 + j;
-    const int64_t lb = bx + (int64_t)g.BX * (by + (int64_t)g.BY * bz);
-    unsigned long long any0 = 0ull, any1 = 0ull;
-    ulonglong2* d0 = reinterpret_cast<ulonglong2*>(dbits + lb * 8);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      d0[q] = make_ulonglong2(w0[2 * q], w0[2 * q + 1]);
-      any0 |= w0[2 * q] | w0[2 * q + 1];
-      any1 |= w1[2 * q] | w1[2 * q + 1];
-    }
     flag[lb] = any0 != 0ull;
     if (any0) nflag[node_key_of(g, bx, by, bz)] = 1;
     if (two) {
-      ulonglong2* d1 = d0 + 4;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) d1[q] = make_ulonglong2(w1[2 * q], w1[2 * q + 1]);
       flag[lb + 1] = any1 != 0ull;
       if (any1) nflag[node_key_of(g, bx + 1, by, bz)] = 1;
     }
@@ -764,10 +757,9 @@ __global__ void __launch_bounds__(256) k_dense_alloc(VS vs, DenseScratch ds) {
         set_error(g, kErrOverflow);
       } else {
         init_brick_meta(g, slot, node, bx, by, bz);
-        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(dbits + lb * 8);
         ulonglong2* dst = reinterpret_cast<ulonglong2*>(g.occ + (size_t)slot * 8);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = src[q];
+        for (int q = 0; q < 4; ++q) dst[q] = make_ulonglong2(dbits[(2 * q) * nbr + lb], dbits[(2 * q + 1) * nbr + lb]);
         g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] = slot;
       }
     }
