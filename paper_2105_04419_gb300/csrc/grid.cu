@@ -1554,7 +1554,7 @@ static int clamp_blocks(int64_t n, int hi) { return (int)(n < 1 ? 1 : (n > hi ? 
 int batch_blocks(const GridView& g, int kind) {
   const int64_t t = kT;
   switch (kind) {
-    case BK_RESET: return clamp_blocks(((int64_t)g.node_cap * kNodeBricks + g.hmask + t) / t, 1024);
+    case BK_RESET: return clamp_blocks(((int64_t)g.node_cap * (kNodeBricks / 4) + g.hmask + t) / t, 1024);  // int4 stores
     case BK_DENSE: {
       const int64_t units = (int64_t)((g.BX + kDenseX - 1) / kDenseX) * g.BY * g.BZ;  // a warp each
       return clamp_blocks((units * 32 + t - 1) / t, 152 * 16);
