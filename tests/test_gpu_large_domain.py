@@ -136,3 +136,39 @@ def test_node_capacity_enough_matches_dense_grid():
     assert m.info()["nodes"] <= 16
     assert np.array_equal(m.export_dense(), O.edt_factorised(occ, 12))
     m.close()
+
+
+def test_graph_replay_on_huge_grid():
+    """The captured update (UpdateGraph) on the 16384 x 16384 x 8184 grid with capacities: its
+    reserved scratch does not scale with the grid, and after each frame it equals the eager
+    update of a twin handle, including frames that create nodes."""
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(77)
+    base = cluster(rs, (4000, 4000, 4000), 40)
+    a = V.Map(*DIMS, DMAX, max_bricks=8000, max_nodes=32)
+    b = V.Map(*DIMS, DMAX, max_bricks=8000, max_nodes=32)
+    for m in (a, b):
+        m.set_occupancy(base, np.ones(len(base), np.uint8))
+        m.global_()
+    g = V.UpdateGraph(a, 20000)
+    boxes = [((4000 - DMAX, 4000 - DMAX, 4000 - DMAX), 40 + 2 * DMAX)]
+    for f, lo in enumerate([(4030, 3990, 4010), (9000, 12000, 600), (9010, 12010, 610)]):
+        add = cluster(rs, lo, 24)
+        rm = base[rs.choice(len(base), 50, replace=False)]
+        rec = np.concatenate([add, rm])
+        val = np.concatenate([np.ones(len(add)), np.zeros(len(rm))]).astype(np.uint8)
+        g.run(rec, val)
+        b.set_occupancy(rec, val)
+        b.update()
+        boxes.append(((lo[0] - DMAX, lo[1] - DMAX, lo[2] - DMAX), 24 + 2 * DMAX))
+        for blo, size in boxes:
+            blo = np.maximum(np.asarray(blo), 0)
+            bhi = np.minimum(blo + size, DIMS)
+            z, y, x = np.meshgrid(np.arange(blo[2], bhi[2]), np.arange(blo[1], bhi[1]), np.arange(blo[0], bhi[0]),
+                                  indexing="ij")
+            xyz = np.stack([x.ravel(), y.ravel(), z.ravel()], 1).astype(np.int32)
+            assert np.array_equal(a.query(xyz), b.query(xyz)), (f, blo)
+    assert a.info()["device_bytes"] < (1 << 30)
+    a.synchronize()
+    a.close()
+    b.close()
