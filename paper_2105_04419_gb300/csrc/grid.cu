@@ -237,60 +237,76 @@ __global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int6
 // With `dbits` (global form), the records' bits are also OR-ed into a dense mask of every brick of
 // the grid (64 B per brick; lanes of one x-row merged by a segmented OR), so that allocation can copy
 // each new brick's mask whole instead of a second pass over the records.
+// One record of the counting-path mark (all lanes of the warp call it together).  The brick flag
+// is only ever set, by the first lane of each run of records in one brick, without reading it
+// first (no dependent load); the node flags follow from the compacted bricks.
+__device__ __forceinline__ void mark_record(const GridView& g, bool have, rec_t packed, int lane,
+                                            int32_t* __restrict__ flag, unsigned long long* __restrict__ dbits) {
+  bool zero = false, bad = false;
+  uint32_t widx = 0xFFFFFFFFu;  // mask word index lb * 8 + z, or none
+  uint32_t blo = 0u, bhi = 0u;  // bit x + 8 y of that word, as two halves
+  long long lb = -1;            // brick of a "set" record
+  if (have) {
+    int4 r = unpack_rec(packed);
+    if (!rec_valid(g, r)) {
+      bad = true;
+    } else if (r.w == 1) {
+      lb = (r.x >> 3) + (int64_t)g.BX * ((r.y >> 3) + (int64_t)g.BY * (r.z >> 3));
+      if (dbits) {
+        widx = (uint32_t)(lb * 8 + (r.z & 7));
+        const int bit = (r.x & 7) + 8 * (r.y & 7);
+        if (bit < 32) blo = 1u << bit; else bhi = 1u << (bit - 32);
+      }
+    } else {
+      zero = true;
+    }
+  }
+  const long long lb_prev = __shfl_up_sync(0xffffffffu, lb, 1);
+  if (lb >= 0 && (lane == 0 || lb_prev != lb)) flag[lb] = 1;
+  if (dbits) {
+    // lanes hitting the same word OR their bits over up to 8 lanes back (runs of equal words are
+    // short: records of one x-row are adjacent); the last lane of each run, and every 8th lane of
+    // a longer run, issues the atomic
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const uint32_t wp = __shfl_up_sync(0xffffffffu, widx, o);
+      const uint32_t lp = __shfl_up_sync(0xffffffffu, blo, o);
+      const uint32_t hp = __shfl_up_sync(0xffffffffu, bhi, o);
+      if (lane >= o && wp == widx) {
+        blo |= lp;
+        bhi |= hp;
+      }
+    }
+    const uint32_t wprev = __shfl_up_sync(0xffffffffu, widx, 1);
+    const uint32_t wnext = __shfl_down_sync(0xffffffffu, widx, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || wprev != widx);
+    const unsigned upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+    const int start = 31 - __clz(heads & upto);
+    const bool run_end = lane == 31 || wnext != widx;
+    if (widx != 0xFFFFFFFFu && (run_end || ((lane - start) & 7) == 7))
+      atomicOr(dbits + widx, ((unsigned long long)bhi << 32) | blo);
+  }
+  if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+}
+
 __global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
-                                     int32_t* __restrict__ flag, unsigned long long* __restrict__ dbits,
-                                     int32_t* __restrict__ nflag) {
+                                     int32_t* __restrict__ flag, unsigned long long* __restrict__ dbits) {
   const int lane = threadIdx.x & 31;
   const int64_t n = rec_count(n_max, n_dev);
-  GRID_STRIDE(i, n) {
-    bool zero = false, bad = false;
-    uint32_t widx = 0xFFFFFFFFu;  // mask word index lb * 8 + z, or none
-    uint32_t blo = 0u, bhi = 0u;  // bit x + 8 y of that word, as two halves
-    if (i < n) {
-      int4 r = unpack_rec(rec[i]);
-      if (!rec_valid(g, r)) {
-        bad = true;
-      } else if (r.w == 1) {
-        int64_t lb = (r.x >> 3) + (int64_t)g.BX * ((r.y >> 3) + (int64_t)g.BY * (r.z >> 3));
-        if (!flag[lb]) {
-          flag[lb] = 1;
-          const int nk = node_key_of(g, r.x >> 3, r.y >> 3, r.z >> 3);
-          if (!nflag[nk]) nflag[nk] = 1;
-        }
-        if (dbits) {
-          widx = (uint32_t)(lb * 8 + (r.z & 7));
-          const int bit = (r.x & 7) + 8 * (r.y & 7);
-          if (bit < 32) blo = 1u << bit; else bhi = 1u << (bit - 32);
-        }
-      } else {
-        zero = true;
-      }
-    }
-    if (dbits) {
-      // lanes hitting the same word OR their bits over up to 8 lanes back (runs of equal words are
-      // short: records of one x-row are adjacent); the last lane of each run, and every 8th lane of
-      // a longer run, issues the atomic
+  // four records per thread and iteration, all loaded before any is used (the loop bounds are
+  // uniform over the grid, so the warp-wide steps see all 32 lanes)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += 4 * stride) {
+    rec_t r[4];
 #pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
-        const uint32_t wp = __shfl_up_sync(0xffffffffu, widx, o);
-        const uint32_t lp = __shfl_up_sync(0xffffffffu, blo, o);
-        const uint32_t hp = __shfl_up_sync(0xffffffffu, bhi, o);
-        if (lane >= o && wp == widx) {
-          blo |= lp;
-          bhi |= hp;
-        }
-      }
-      const uint32_t wprev = __shfl_up_sync(0xffffffffu, widx, 1);
-      const uint32_t wnext = __shfl_down_sync(0xffffffffu, widx, 1);
-      const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || wprev != widx);
-      const unsigned upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
-      const int start = 31 - __clz(heads & upto);
-      const bool run_end = lane == 31 || wnext != widx;
-      if (widx != 0xFFFFFFFFu && (run_end || ((lane - start) & 7) == 7))
-        atomicOr(dbits + widx, ((unsigned long long)bhi << 32) | blo);
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = base + k * stride + threadIdx.x;
+      r[k] = i < n ? __ldg(rec + i) : 0ull;
     }
-    if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
-    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (base + k * stride < n) mark_record(g, base + k * stride + threadIdx.x < n, r[k], lane, flag, dbits);
   }
 }
 
@@ -338,10 +354,23 @@ __global__ void k_flag_key_nodes(GridView g, const uint32_t* __restrict__ uniq, 
   }
 }
 
-__global__ void k_compact_flag_index(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t n,
-                                     uint32_t* __restrict__ out) {
+// Compaction of the flagged bricks (in key order), with the flags of their node keys: consecutive
+// bricks mostly share a node, so only the first flagged lane of each run of one node key in the
+// warp sets it (without reading it first).
+__global__ void k_compact_flag_index(GridView g, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                                     int64_t n, uint32_t* __restrict__ out, int32_t* __restrict__ nflag) {
+  const int lane = threadIdx.x & 31;
   GRID_STRIDE(i, n) {
-    if (i < n && flag[i]) out[pos[i]] = (uint32_t)i;
+    int nk = -1;
+    if (i < n && flag[i]) {
+      out[pos[i]] = (uint32_t)i;
+      const uint32_t lb = (uint32_t)i, rest = lb / (uint32_t)g.BX;
+      nk = node_key_of(g, (int)(lb - rest * (uint32_t)g.BX), (int)(rest % (uint32_t)g.BY), (int)(rest / (uint32_t)g.BY));
+    }
+    const unsigned set = __ballot_sync(0xffffffffu, nk >= 0);
+    const int prev_lane = 31 - __clz(set & ((1u << lane) - 1u));  // previous flagged lane, or -1
+    const int nk_prev = __shfl_sync(0xffffffffu, nk, prev_lane < 0 ? lane : prev_lane);
+    if (nk >= 0 && (prev_lane < 0 || nk_prev != nk)) nflag[nk] = 1;
   }
 }
 
@@ -1460,11 +1489,11 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
       e = cudaMemsetAsync(dbits, 0, (size_t)nbr * 64, st);
       if (e != cudaSuccess) return e;
     }
-    VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, n_dev, flag, dbits, nflag);
-    VDB_LAUNCH(k_create_flagged_nodes, blocks_for(nkeys), kT, 0, st, g, nflag, nkeys);
+    VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, n_dev, flag, dbits);
     e = exclusive_scan_i32(flag, pos, (int64_t)nbr, g.counters + C_UNIQUE, stemp, st);
     if (e != cudaSuccess) return e;
-    VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, flag, pos, (int64_t)nbr, ka);
+    VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, g, flag, pos, (int64_t)nbr, ka, nflag);
+    VDB_LAUNCH(k_create_flagged_nodes, blocks_for(nkeys), kT, 0, st, g, nflag, nkeys);
     VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for((int64_t)nbr), kT, 0, st, g, ka, (int64_t)nbr, track, dbits);
     if (!track && !dbits) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
   } else {
