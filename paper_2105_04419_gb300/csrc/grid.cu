@@ -134,7 +134,9 @@ __device__ __forceinline__ void init_brick_meta(const GridView& g, int slot, int
 }
 
 __device__ void init_brick(const GridView& g, int slot, int node, int bx, int by, int bz, bool init_fields) {
-  for (int w = 0; w < 8; ++w) g.occ[(size_t)slot * 8 + w] = 0ull;
+  ulonglong2* occ = reinterpret_cast<ulonglong2*>(g.occ + (size_t)slot * 8);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) occ[q] = make_ulonglong2(0ull, 0ull);
   if (init_fields) {
     uint16_t inf;
     if (g.dmax <= 45 && g.R <= 6) {
@@ -1061,44 +1063,29 @@ __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int
   }
 }
 
-// Allocate every marked brick without storage: a block per (node, 512-brick chunk), two bricks
-// per thread, one atomic per block for the slot range (block scan of the per-thread counts).
+// Allocate every marked brick without storage: a block per (node, 256-brick chunk), a brick per
+// thread, one atomic per block for the slot range (block scan of the flags).
 template <class VS>
 __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
-  for (int b = bid; b < nn * 8; b += nblk) {
-    const int node = b >> 3, chunk = b & 7;
-    const int l0 = chunk * 512 + threadIdx.x * 2;
-    const uint32_t word = g.amask[(size_t)node * 128 + (l0 >> 5)];
-    bool need[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      need[k] = ((word >> ((l0 + k) & 31)) & 1u) && g.child[(size_t)node * kNodeBricks + l0 + k] == kNoSlot;
-    const int cnt = (int)need[0] + (int)need[1];
-    // block scan of cnt (0..2): two predicates in sequence keep block_agg_add's contract
-    int total0 = 0, total1 = 0;
-    const int s0 = block_agg_add(&g.counters[C_NBRICKS], need[0], &total0);
-    const int s1 = block_agg_add(&g.counters[C_NBRICKS], need[1], &total1);
-    (void)cnt;
-    if (threadIdx.x == 0 && total0 + total1) atomicAdd(&g.counters[C_NEW_BRICKS], total0 + total1);
-    if (need[0] || need[1]) {
-      const int key = g.node_key[node];
-      const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (!need[k]) continue;
-        const int slot = k ? s1 : s0;
-        const int l = l0 + k;
-        if (slot >= g.cap) {
-          set_error(g, kErrOverflow);
-        } else {
-          init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8),
-                     init_fields);
-          g.child[(size_t)node * kNodeBricks + l] = slot;
-        }
+  for (int b = bid; b < nn * 16; b += nblk) {
+    const int node = b >> 4, l = (b & 15) * 256 + threadIdx.x;
+    const bool need = ((g.amask[(size_t)node * 128 + (l >> 5)] >> (l & 31)) & 1u) &&
+                      g.child[(size_t)node * kNodeBricks + l] == kNoSlot;
+    int total = 0;
+    const int slot = block_agg_add(&g.counters[C_NBRICKS], need, &total);
+    if (threadIdx.x == 0 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
+    if (need) {
+      if (slot >= g.cap) {
+        set_error(g, kErrOverflow);
+      } else {
+        const int key = g.node_key[node];
+        const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+        init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8), init_fields);
+        g.child[(size_t)node * kNodeBricks + l] = slot;
       }
     }
   }
@@ -1555,7 +1542,7 @@ cudaError_t launch_activation_full(const GridView& g, cudaStream_t st) {
     VDB_LAUNCH((k_dilate_stage<1, OneView>), 256, kT, 0, st, v);
     VDB_LAUNCH((k_dilate_stage<2, OneView>), 256, kT, 0, st, v);
   }
-  VDB_LAUNCH(k_alloc_marked<OneView>, g.node_cap * 8 < 8192 ? g.node_cap * 8 : 8192, kT, 0, st, v, false);
+  VDB_LAUNCH(k_alloc_marked<OneView>, g.node_cap * 16 < 8192 ? g.node_cap * 16 : 8192, kT, 0, st, v, false);
   return cudaGetLastError();
 }
 
@@ -1594,7 +1581,7 @@ int batch_blocks(const GridView& g, int kind) {
     case BK_OBST: return clamp_blocks(((int64_t)g.cap + t - 1) / t, 1024);
     case BK_HALO: return clamp_blocks(((int64_t)g.node_cap * 32 + t - 1) / t, 64);
     case BK_DILATE: return clamp_blocks(g.node_cap, 1024);
-    case BK_ALLOC: return clamp_blocks((int64_t)g.node_cap * 8, 8192);
+    case BK_ALLOC: return clamp_blocks((int64_t)g.node_cap * 16, 8192);
     case BK_ITEMS: return clamp_blocks((int64_t)g.node_cap * 12, 8192);
   }
   return 1;
