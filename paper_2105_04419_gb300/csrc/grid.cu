@@ -1213,29 +1213,39 @@ __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int 
     }
     __syncthreads();
     if (with_slots) {
-      for (int idx = threadIdx.x; idx < cnt * nb; idx += 256) {
-        const int i = idx / nb, j = idx % nb;
-        const int p = base + i;
-        if (p >= g.item_cap) continue;
-        const int line = lines[i];
-        int l[3];
-        l[a1] = line & 15;
-        l[a2] = line >> 4;
-        int c = r0 + j - R, src = node;
-        if (c < 0) {
-          c += 16;
-          src = nbr_sh[0];
-        } else if (c >= 16) {
-          c -= 16;
-          src = nbr_sh[1];
+      // four slots per thread and round, their child reads issued before any is written
+      const int total = cnt * nb;
+      for (int idx0 = threadIdx.x; idx0 < total; idx0 += 4 * 256) {
+        int sv[4];
+        int64_t dst[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = idx0 + u * 256;
+          sv[u] = -1;
+          dst[u] = -1;
+          if (idx < total) {
+            const int i = idx / nb, j = idx % nb;
+            const int p = base + i;
+            if (p < g.item_cap) {
+              const int line = lines[i];
+              int c = r0 + j - R, src = node;
+              if (c < 0) {
+                c += 16;
+                src = nbr_sh[0];
+              } else if (c >= 16) {
+                c -= 16;
+                src = nbr_sh[1];
+              }
+              dst[u] = (int64_t)p * kItemSlots + j;
+              // local brick: c along the axis, the line's two coordinates across it
+              const int lb = (c << (4 * axis)) | ((line & 15) << (4 * a1)) | ((line >> 4) << (4 * a2));
+              if (src >= 0) sv[u] = g.child[(size_t)src * kNodeBricks + lb];
+            }
+          }
         }
-        l[axis] = c;
-        int sv = -1;
-        if (src >= 0) {
-          sv = g.child[(size_t)src * kNodeBricks + local_brick(l[0], l[1], l[2])];
-          sv = sv >= 0 ? sv + g.slot_base : -1;
-        }
-        it.slots[axis][(size_t)p * kItemSlots + j] = sv;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (dst[u] >= 0) it.slots[axis][dst[u]] = sv[u] >= 0 ? sv[u] + g.slot_base : -1;
       }
     }
     __syncthreads();
