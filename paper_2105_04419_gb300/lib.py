@@ -129,7 +129,11 @@ def _ptr_host(a: np.ndarray) -> int:
 
 
 class Map:
-    """One sparse distance field (a vdbedt handle) on a CUDA device."""
+    """One sparse distance field (a vdbedt handle) on a CUDA device.
+
+    `max_bricks` and `max_nodes` (0: every brick / node of the grid) cap the storage allocated up
+    front, so that a large grid mapped only in part needs memory for the mapped part alone; a
+    transform that needs more reports EOVERFLOW."""
 
     def __init__(self, nx: int, ny: int, nz: int, dmax: int, voxel_size: float = 0.1, device: int = 0,
                  stream=None, max_bricks: int = 0, max_nodes: int = 0, _borrow=None):
