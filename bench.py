@@ -176,6 +176,9 @@ def dist_summary(v):
             "max": v[-1], "min": v[0], "mean": statistics.mean(v)}
 
 
+INCR_RUN = 4
+
+
 def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
     """Per-frame incremental update along the lidar sequence (map starts empty): eager calls and
     the CUDA-graph replay, each frame event-timed on the map's stream with L2 flushed before it,
@@ -193,8 +196,10 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
     val_d = torch.from_numpy(np.concatenate([v for _, v in frames])).cuda()
     sl = [(xyz_d[offs[k]:offs[k + 1]], val_d[offs[k]:offs[k + 1]]) for k in range(nframes)]
 
-    # untimed pass with statistics (records, net flips, dirty runs per frame)
+    # untimed pass with statistics (records, net flips, dirty runs per frame); every incremental
+    # map works on runs of INCR_RUN bricks (the library's default), pruned windows
     ms = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    ms.set_tuning(INCR_RUN, INCR_RUN, INCR_RUN, 3)
     ms.global_()
     ms.set_profiling(True)
     stats, phases = [], []
@@ -219,6 +224,7 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
         return [a.elapsed_time(b) for a, b in ev]
 
     me = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    me.set_tuning(INCR_RUN, INCR_RUN, INCR_RUN, 3)
     me.global_()
     launches0 = V.kernel_launches()
 
@@ -232,6 +238,7 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
     me.close()
 
     mg = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    mg.set_tuning(INCR_RUN, INCR_RUN, INCR_RUN, 3)
     mg.global_()
     graph = V.UpdateGraph(mg, max(counts))
     graph_ms = timed(lambda k: graph.run(*sl[k]))
@@ -259,6 +266,12 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
     mf.close()
     glob = statistics.median(gms)
     g = dist_summary(graph_ms)
+    # algorithmic bytes of a frame: the unfused three-pass model (21 B per voxel) over the bricks the
+    # z pass recomputes (its dirty runs, INCR_RUN bricks each: an upper bound on the influence
+    # region), plus 16 B per record
+    peak, peak_src = peaks()
+    fbytes = [21 * 512 * s["z_items"] * INCR_RUN + 16 * s["records"] for s in stats]
+    fgbs = [b / (t * 1e-3) / 1e9 for b, t in zip(fbytes, graph_ms)]
     return {"frames": nframes, "workload": "lidar sequence along tunnel 0 of the scene, 64 beams x 1024 azimuths, "
                                            "range 400 voxels, 1 % noise; map starts empty",
             "records_per_frame": dist_summary([s["records"] for s in stats]),
@@ -266,6 +279,10 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
             "changed_bricks_per_frame": dist_summary([s["changed_bricks"] for s in stats]),
             "z_runs_per_frame": dist_summary([s["z_items"] for s in stats]),
             "graph_ms_per_frame": g, "eager_ms_per_frame": dist_summary(eager_ms),
+            "roofline_frames": {"model": "21 B x 512 x bricks of the z pass's dirty runs + 16 B x records, per frame",
+                                "bytes_per_frame": dist_summary(fbytes), "achieved_median": statistics.median(fgbs),
+                                "unit": "GB/s", "peak": peak, "peak_source": peak_src,
+                                "frac_median": statistics.median(fgbs) / peak},
             "eager_phase_ms_median": phase_med,
             "eager_launches_per_frame": eager_launches,
             "global_ms_final_occupancy": glob, "global_over_graph_median": glob / g["median"],
