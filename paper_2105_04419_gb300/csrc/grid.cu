@@ -1178,12 +1178,14 @@ __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int 
     }
     const int o1 = threadIdx.x & 15, o2 = threadIdx.x >> 4;
     bool any = false;
-    for (int j = 0; j < run; ++j) {
-      int l[3];
-      l[axis] = r0 + j;
-      l[a1] = o1;
-      l[a2] = o2;
-      any |= ch[local_brick(l[0], l[1], l[2])] >= 0;
+    {
+      // the run's child entries along the line, all read before any is tested
+      const int across = (o1 << (4 * a1)) | (o2 << (4 * a2));
+      int c[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) c[j] = j < run ? ch[across | ((r0 + j) << (4 * axis))] : -1;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) any |= c[j] >= 0;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, any);
     if (lane == 0) wsum[warp] = __popc(bal);
