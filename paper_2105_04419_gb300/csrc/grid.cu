@@ -416,18 +416,24 @@ __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__
     }
     int total = 0;
     const int slot = block_agg_add(&g.counters[C_NBRICKS], need, &total);
+    const ulonglong2* src = dbits ? reinterpret_cast<const ulonglong2*>(dbits + (size_t)lb * 8) : nullptr;
     if (need) {
       if (slot >= g.cap) {
         set_error(g, kErrOverflow);
       } else {
-        init_brick(g, slot, node, bx, by, bz, init);
+        if (dbits) {  // a new brick takes the records' mask as it is (the dense mask path is untracked)
+          init_brick_meta(g, slot, node, bx, by, bz);
+          ulonglong2* dst = reinterpret_cast<ulonglong2*>(g.occ + (size_t)slot * 8);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = src[q];
+        } else {
+          init_brick(g, slot, node, bx, by, bz, init);
+        }
         *e = slot;
       }
-    }
-    if (dbits && j < cnt && e) {
-      const int sl = need ? slot : *e;
+    } else if (dbits && j < cnt && e) {  // a stored brick ORs the records' mask in
+      const int sl = *e;
       if (sl >= 0 && sl < g.cap) {
-        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(dbits + (size_t)lb * 8);
         ulonglong2* dst = reinterpret_cast<ulonglong2*>(g.occ + (size_t)sl * 8);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
