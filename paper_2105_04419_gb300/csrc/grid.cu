@@ -1,8 +1,8 @@
 // Building and maintaining the sparse brick grid on the device.
 //
-//   ingest (global form)  staged occupancy records -> brick keys of "set" records -> sorted unique
-//            list (a counting sort through one flag per brick of the grid when records are many,
-//            an LSD radix sort + unique + compaction when they are few) -> nodes created first
+//   ingest (global form)  staged occupancy records -> brick keys of "set" records -> unique list
+//            (one flag per brick of the grid, compacted with one atomic per warp, when records are
+//            many; an LSD radix sort + unique + compaction when they are few) -> nodes created first
 //            (one thread per flagged node key) -> bricks allocated (slots reserved with one
 //            atomic per block) -> occupancy bits set (OR-ed into a dense mask during the count, or
 //            per record).  Several records for one voxel: the last one wins -- a per-voxel
@@ -234,8 +234,8 @@ __global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int6
   }
 }
 
-// Many records: bucket the brick keys of "set" records through one flag per brick of the grid
-// (a counting sort on the brick key); the compaction of the flags is the sorted unique key list.
+// Many records: bucket the brick keys of "set" records through one flag per brick of the grid; the
+// compaction of the flags is the unique key list.
 // With `dbits` (global form), the records' bits are also OR-ed into a dense mask of every brick of
 // the grid (64 B per brick; lanes of one x-row merged by a segmented OR), so that allocation can copy
 // each new brick's mask whole instead of a second pass over the records.
@@ -357,21 +357,26 @@ __global__ void k_flag_key_nodes(GridView g, const uint32_t* __restrict__ uniq, 
   }
 }
 
-// Compaction of the flagged bricks (in key order), with the flags of their node keys: consecutive
-// bricks mostly share a node, so only the first flagged lane of each run of one node key in the
-// warp sets it (without reading it first).
-__global__ void k_compact_flag_index(GridView g, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
-                                     int64_t n, uint32_t* __restrict__ out, int32_t* __restrict__ nflag) {
+// Compaction of the flagged bricks, one atomic per warp for the list positions (a warp's bricks
+// stay in key order, warps follow in completion order), with the flags of their node keys:
+// consecutive bricks mostly share a node, so only the first flagged lane of each run of one node
+// key in the warp sets it (without reading it first).
+__global__ void k_compact_flag_index(GridView g, const int32_t* __restrict__ flag, int64_t n,
+                                     uint32_t* __restrict__ out, int32_t* __restrict__ nflag) {
   const int lane = threadIdx.x & 31;
   GRID_STRIDE(i, n) {
     int nk = -1;
     if (i < n && flag[i]) {
-      out[pos[i]] = (uint32_t)i;
       const uint32_t lb = (uint32_t)i, rest = lb / (uint32_t)g.BX;
       nk = node_key_of(g, (int)(lb - rest * (uint32_t)g.BX), (int)(rest % (uint32_t)g.BY), (int)(rest / (uint32_t)g.BY));
     }
     const unsigned set = __ballot_sync(0xffffffffu, nk >= 0);
-    const int prev_lane = 31 - __clz(set & ((1u << lane) - 1u));  // previous flagged lane, or -1
+    int base = 0;
+    if (lane == 0 && set) base = atomicAdd(&g.counters[C_UNIQUE], __popc(set));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const unsigned below = set & ((1u << lane) - 1u);
+    if (nk >= 0) out[base + __popc(below)] = (uint32_t)i;
+    const int prev_lane = 31 - __clz(below);  // previous flagged lane, or -1
     const int nk_prev = __shfl_sync(0xffffffffu, nk, prev_lane < 0 ? lane : prev_lane);
     if (nk >= 0 && (prev_lane < 0 || nk_prev != nk)) nflag[nk] = 1;
   }
@@ -1488,7 +1493,7 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
   const unsigned nbk = blocks_for(n);
   const uint64_t nbr = (uint64_t)nbr_all;
   if (counting) {
-    // counting sort of brick keys over the grid's bricks, then compaction
+    // one flag per brick of the grid, then compaction
     e = cudaMemsetAsync(nflag, 0, sizeof(int32_t) * (size_t)(nkeys_al + (int64_t)nbr), st);
     if (e != cudaSuccess) return e;
     if (dbits) {
@@ -1496,9 +1501,9 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
       if (e != cudaSuccess) return e;
     }
     VDB_LAUNCH(k_mark_record_bricks, nbk, kT, 0, st, g, rec, n, n_dev, flag, dbits);
-    e = exclusive_scan_i32(flag, pos, (int64_t)nbr, g.counters + C_UNIQUE, stemp, st);
+    e = cudaMemsetAsync(g.counters + C_UNIQUE, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, g, flag, pos, (int64_t)nbr, ka, nflag);
+    VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, g, flag, (int64_t)nbr, ka, nflag);
     VDB_LAUNCH(k_create_flagged_nodes, blocks_for(nkeys), kT, 0, st, g, nflag, nkeys);
     VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for((int64_t)nbr), kT, 0, st, g, ka, (int64_t)nbr, track, dbits);
     if (!track && !dbits) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
