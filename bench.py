@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work-item tuning")
     ap.add_argument("--frames", type=int, default=300, help="lidar frames of the incremental measurement")
+    ap.add_argument("--incr-run", type=int, default=4, choices=(4, 8, 16),
+                    help="bricks per work item of the incremental maps (default: the library's 4)")
     ap.add_argument("--variant", type=int, default=0, help="pass variant (0 automatic; see vdbedt_set_tuning)")
     ap.add_argument("--x-run", type=int, default=0)
     ap.add_argument("--y-run", type=int, default=0)
@@ -176,10 +178,7 @@ def dist_summary(v):
             "max": v[-1], "min": v[0], "mean": statistics.mean(v)}
 
 
-INCR_RUN = 4
-
-
-def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
+def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4):
     """Per-frame incremental update along the lidar sequence (map starts empty): eager calls and
     the CUDA-graph replay, each frame event-timed on the map's stream with L2 flushed before it,
     against the global transform of the final occupancy."""
@@ -197,7 +196,7 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
     sl = [(xyz_d[offs[k]:offs[k + 1]], val_d[offs[k]:offs[k + 1]]) for k in range(nframes)]
 
     # untimed pass with statistics (records, net flips, dirty runs per frame); every incremental
-    # map works on runs of INCR_RUN bricks (the library's default), pruned windows
+    # map works on runs of INCR_RUN bricks (default: the library's 4), pruned windows
     ms = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
     ms.set_tuning(INCR_RUN, INCR_RUN, INCR_RUN, 3)
     ms.global_()
@@ -278,7 +277,7 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes):
             "net_flips_per_frame": dist_summary([s["net_flips"] for s in stats]),
             "changed_bricks_per_frame": dist_summary([s["changed_bricks"] for s in stats]),
             "z_runs_per_frame": dist_summary([s["z_items"] for s in stats]),
-            "graph_ms_per_frame": g, "eager_ms_per_frame": dist_summary(eager_ms),
+            "runs": INCR_RUN, "graph_ms_per_frame": g, "eager_ms_per_frame": dist_summary(eager_ms),
             "roofline_frames": {"model": "21 B x 512 x bricks of the z pass's dirty runs + 16 B x records, per frame",
                                 "bytes_per_frame": dist_summary(fbytes), "achieved_median": statistics.median(fgbs),
                                 "unit": "GB/s", "peak": peak, "peak_source": peak_src,
@@ -670,7 +669,7 @@ def main():
     if wl["kind"] == "tunnel" and not args.no_batched:
         line["batched"] = bench_batched(V, torch, stream, flush, autotuned=not args.no_autotune)
     if wl["kind"] == "tunnel" and not args.no_incremental:
-        line["incremental"] = bench_incremental(V, torch, wl, occ, stream, flush, args.frames)
+        line["incremental"] = bench_incremental(V, torch, wl, occ, stream, flush, args.frames, args.incr_run)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(occ, dmax)
     if rank == 0:
