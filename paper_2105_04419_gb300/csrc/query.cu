@@ -228,24 +228,38 @@ cudaError_t launch_query_nearest(const GridView& g, const int32_t* xyz, int64_t 
 // Bricks holding an obstacle and bricks holding a finite D, counted on the device (counters
 // C_OBST and C_FINITE, cleared by the caller): one atomic per warp and flag.
 __global__ void k_count_flags(GridView g) {
+  // counts kept per warp over the grid-stride loop, then one atomic per block and counter (the
+  // two counters would otherwise take an atomic from every warp)
+  __shared__ int wobst[32], wfin[32];
   const int nb = min(g.counters[C_NBRICKS], g.cap);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int obst = 0, fin = 0;
   for (int base = blockIdx.x * blockDim.x; base < nb; base += gridDim.x * blockDim.x) {
     const int s = base + threadIdx.x;
     const uint32_t f = s < nb ? g.bflags[s] : 0u;
-    const int obst = __popc(__ballot_sync(0xffffffffu, (f & F_OBST) != 0u));
-    const int fin = __popc(__ballot_sync(0xffffffffu, (f & F_FINITE) != 0u));
-    if (lane == 0) {
-      if (obst) atomicAdd(&g.counters[C_OBST], obst);
-      if (fin) atomicAdd(&g.counters[C_FINITE], fin);
+    obst += __popc(__ballot_sync(0xffffffffu, (f & F_OBST) != 0u));
+    fin += __popc(__ballot_sync(0xffffffffu, (f & F_FINITE) != 0u));
+  }
+  if (lane == 0) {
+    wobst[warp] = obst;
+    wfin[warp] = fin;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int to = 0, tf = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      to += wobst[w];
+      tf += wfin[w];
     }
+    if (to) atomicAdd(&g.counters[C_OBST], to);
+    if (tf) atomicAdd(&g.counters[C_FINITE], tf);
   }
 }
 
 cudaError_t launch_count_flags(const GridView& g, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(g.counters + C_FINITE, 0, 2 * sizeof(int32_t), st);  // C_FINITE, C_OBST
   if (e != cudaSuccess) return e;
-  VDB_LAUNCH(k_count_flags, 1024, 256, 0, st, g);
+  VDB_LAUNCH(k_count_flags, 304, 256, 0, st, g);
   return cudaGetLastError();
 }
 
