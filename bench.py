@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=300, help="lidar frames of the incremental measurement")
     ap.add_argument("--incr-run", type=int, default=4, choices=(4, 8, 16),
                     help="bricks per work item of the incremental maps (default: the library's 4)")
+    ap.add_argument("--alg1-frames", type=int, default=0,
+                    help="also time the paper's Alg. 1 (the oracle's single-threaded transcription) on the "
+                         "first K lidar frames (tens of seconds per frame, about 7 GB of host memory)")
     ap.add_argument("--variant", type=int, default=0, help="pass variant (0 automatic; see vdbedt_set_tuning)")
     ap.add_argument("--x-run", type=int, default=0)
     ap.add_argument("--y-run", type=int, default=0)
@@ -178,7 +181,26 @@ def dist_summary(v):
             "max": v[-1], "min": v[0], "mean": statistics.mean(v)}
 
 
-def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4):
+def alg1_frames(truth, frames, dmax, k):
+    """The paper's Alg. 1 (the oracle's transcription, one thread as in the paper) on the first k
+    frames of the sequence, from the same empty map: milliseconds and queue counters per frame."""
+    import oracle as O
+    a = O.Alg1(truth.shape, dmax)
+    try:
+        a.global_(np.zeros(truth.shape, np.uint8))
+        out = []
+        for xyz, val in frames[:k]:
+            a.reset_counters()
+            t0 = time.perf_counter()
+            a.update(xyz, val)
+            out.append(dict(ms=1e3 * (time.perf_counter() - t0), records=int(len(val)), **a.counters()))
+        return {"frames": out, "threads": 1, "kind": "oracle (Alg. 1)",
+                "note": "the same records as the GPU frames; the GPU's fields equal Eq. 1, Alg. 1 may overshoot it"}
+    finally:
+        a.close()
+
+
+def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, alg1_k=0):
     """Per-frame incremental update along the lidar sequence (map starts empty): eager calls and
     the CUDA-graph replay, each frame event-timed on the map's stream with L2 flushed before it,
     against the global transform of the final occupancy."""
@@ -188,6 +210,7 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4):
     _, lines = W.tunnel_lines(wl["seed"], (nx, ny, nz), ntunnels=wl.get("ntunnels", 40))
     seq = W.LidarSequence(truth, wl["seed"], lines[0], nframes=nframes)
     frames = [seq.next() for _ in range(nframes)]
+    alg1 = alg1_frames(truth, frames, dmax, alg1_k) if alg1_k > 0 else None
     final_occ = seq.map
     counts = [len(v) for _, v in frames]
     offs = np.concatenate([[0], np.cumsum(counts)])
@@ -286,7 +309,8 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4):
             "eager_launches_per_frame": eager_launches,
             "global_ms_final_occupancy": glob, "global_over_graph_median": glob / g["median"],
             "final_map": {"occupied_voxels": int(final_occ.sum()), "allocated_bricks": info_final["allocated_bricks"]},
-            "graph_equals_eager": same, "l2": "flushed before every frame (untimed)"}
+            "graph_equals_eager": same, "l2": "flushed before every frame (untimed)",
+            **({"cpu_alg1": alg1} if alg1 else {})}
 
 
 def bench_clearance(V, torch, m, occ, stream, reps=20):
@@ -669,7 +693,8 @@ def main():
     if wl["kind"] == "tunnel" and not args.no_batched:
         line["batched"] = bench_batched(V, torch, stream, flush, autotuned=not args.no_autotune)
     if wl["kind"] == "tunnel" and not args.no_incremental:
-        line["incremental"] = bench_incremental(V, torch, wl, occ, stream, flush, args.frames, args.incr_run)
+        line["incremental"] = bench_incremental(V, torch, wl, occ, stream, flush, args.frames, args.incr_run,
+                                                args.alg1_frames if rank == 0 else 0)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(occ, dmax)
     if rank == 0:
