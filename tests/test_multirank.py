@@ -72,3 +72,20 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["unit"] == "Mvoxels/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_alg1_frames_helper():
+    """bench.alg1_frames runs the paper's Alg. 1 on the first frames of a lidar sequence (here a
+    small scene) and reports time, record count and queue counters per frame."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    dims = (96, 80, 48)
+    truth = W.tunnel_scene(4, dims, ntunnels=3, rmin=5, rmax=8)
+    _, lines = W.tunnel_lines(4, dims, ntunnels=3, rmin=5, rmax=8)
+    seq = W.LidarSequence(truth, 4, lines[0], nframes=4, nbeams=8, nazim=128, maxrange=80)
+    frames = [seq.next() for _ in range(3)]
+    r = bench.alg1_frames(truth, frames, 12, 2)
+    assert len(r["frames"]) == 2 and r["threads"] == 1
+    for f, (xyz, val) in zip(r["frames"], frames):
+        assert f["records"] == len(val) and f["ms"] > 0 and f["lowered"] >= 0
