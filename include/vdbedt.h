@@ -94,6 +94,7 @@ typedef struct {
  * follows the mapped part of the grid, not its size: a grid may span up to 2^32 bricks (e.g.
  * 16384 x 16384 x 8184 voxels) with obstacles in a small part of it.  Record-driven ingest and
  * updates work at any grid size; the dense entry points and vdbedt_export_dense scale with the grid.
+ * The brick capacity is at most 8,388,607 (max_bricks 0 on a larger grid is EINVAL: set it).
  * Exceeding a capacity during a transform is EOVERFLOW.
  * EINVAL: a size < 1, dmax outside [1, VDBEDT_DMAX_LIMIT], voxel_size <= 0, bad device.
  * ENOMEM: device allocation failed. */
