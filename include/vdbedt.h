@@ -261,12 +261,17 @@ vdbedt_status vdbedt_selftest_wait_timeout(vdbedt_handle h, int32_t which);
  * device and `stream` (cudaStream_t, NULL = legacy default stream).  occ and out are device
  * pointers, owned by the caller.
  * Its two intermediate fields live in a fixed device array of the library (2 x 16 bit x
- * VDBEDT_NOALLOC_MAX_VOXELS = 8 MiB) that every GPU loading the library holds until exit.  The
- * first call on a device looks that array's address up (cudaGetSymbolAddress) while the device is
- * current: make that first call before any stream capture.  All calls on a device share the array:
- * calls whose work overlaps on the GPU race.
+ * VDBEDT_NOALLOC_MAX_VOXELS = 8 MiB) that every GPU loading the library holds until exit.  Host
+ * code needs that array's device address, which the library looks up (cudaGetSymbolAddress) with
+ * the device current: every call whose stream is not being captured looks it up again and caches
+ * it per device, so a context that was torn down and recreated (cudaDeviceReset) is followed by the
+ * next such call; a call made during a stream capture uses the cached address, so make the first
+ * call on each device before any capture (one made during a capture first is ECUDA).  All calls on
+ * a device share the array: calls whose work overlaps on the GPU race.
  * EINVAL: a null pointer, a size < 1, nx * ny * nz > VDBEDT_NOALLOC_MAX_VOXELS, or dmax outside
- * [1, VDBEDT_DMAX_LIMIT].  ECUDA: the address lookup or a launch failed. */
+ * [1, VDBEDT_DMAX_LIMIT].  ECUDA: a CUDA error of earlier work was already pending on this thread
+ * (it is left pending, for its owner to read), the address lookup failed, or a launch failed.
+ * Messages: vdbedt_last_error(NULL). */
 #define VDBEDT_NOALLOC_MAX_VOXELS (1 << 21)
 vdbedt_status vdbedt_edt_dense_noalloc(const uint8_t* occ, int32_t nx, int32_t ny, int32_t nz, int32_t dmax,
                                        int32_t* out, void* stream);

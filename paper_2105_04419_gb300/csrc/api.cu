@@ -16,9 +16,14 @@
 
 using namespace vdbedt;
 
+namespace {
+thread_local std::string g_last_error = "";
+}
+
 namespace vdbedt {
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, const int32_t* n_dev,
                                 int32_t* count_out, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
                                 int32_t* counters, cudaStream_t st);
@@ -60,8 +65,6 @@ struct vdbedt_map {
 };
 
 namespace {
-
-thread_local std::string g_last_error = "";
 
 struct DeviceGuard {
   int prev = -1;

@@ -15,8 +15,11 @@
 // the array.
 //
 // Host code must not pass the array's name to a kernel (in host code it is a host-side stand-in,
-// not a device address): the device address is looked up once per device with
-// cudaGetSymbolAddress, on the first call made while that device is current, and cached.
+// not a device address): the device address comes from cudaGetSymbolAddress, called with the
+// device current.  Each call made while its stream is not being captured looks the address up
+// again and refreshes the per-device cache, so a context torn down and recreated in between (for
+// example by cudaDeviceReset) is followed; a call made during a stream capture uses the cached
+// address, which is why the first call on a device must come before any capture.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,28 +77,60 @@ __global__ void k_dense_win(const uint16_t* __restrict__ in, int nx, int ny, int
 
 }  // namespace
 
+namespace {
+
+vdbedt_status noalloc_fail(vdbedt_status s, const char* msg) {
+  vdbedt::set_last_error(msg);
+  return s;
+}
+
+}  // namespace
+
 extern "C" vdbedt_status vdbedt_edt_dense_noalloc(const uint8_t* occ, int32_t nx, int32_t ny, int32_t nz,
                                                   int32_t dmax, int32_t* out, void* stream) {
-  if (!occ || !out || nx < 1 || ny < 1 || nz < 1 || dmax < 1 || dmax > VDBEDT_DMAX_LIMIT) return VDBEDT_EINVAL;
+  if (!occ || !out) return noalloc_fail(VDBEDT_EINVAL, "vdbedt_edt_dense_noalloc: null pointer");
+  if (nx < 1 || ny < 1 || nz < 1) return noalloc_fail(VDBEDT_EINVAL, "vdbedt_edt_dense_noalloc: size < 1");
+  if (dmax < 1 || dmax > VDBEDT_DMAX_LIMIT)
+    return noalloc_fail(VDBEDT_EINVAL, "vdbedt_edt_dense_noalloc: dmax outside [1, VDBEDT_DMAX_LIMIT]");
   const int64_t n = (int64_t)nx * ny * nz;
-  if (n > kMaxVoxels) return VDBEDT_EINVAL;
+  if (n > kMaxVoxels)
+    return noalloc_fail(VDBEDT_EINVAL, "vdbedt_edt_dense_noalloc: more than VDBEDT_NOALLOC_MAX_VOXELS voxels");
+  // an error left pending by earlier work on this thread is not ours to report or to clear
+  if (cudaPeekAtLastError() != cudaSuccess)
+    return noalloc_fail(VDBEDT_ECUDA, "vdbedt_edt_dense_noalloc: a CUDA error from earlier work is pending "
+                                      "(read it with cudaGetLastError first)");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VDBEDT_ECUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return noalloc_fail(VDBEDT_ECUDA, "vdbedt_edt_dense_noalloc: no current device");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return noalloc_fail(VDBEDT_ECUDA, "vdbedt_edt_dense_noalloc: invalid stream");
+  }
   uint16_t* scratch = g_scratch_ptr[dev].load(std::memory_order_acquire);
-  if (!scratch) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return VDBEDT_ECUDA;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return noalloc_fail(VDBEDT_ECUDA, "vdbedt_edt_dense_noalloc: scratch address lookup failed");
+    }
     scratch = static_cast<uint16_t*>(p);
     g_scratch_ptr[dev].store(scratch, std::memory_order_release);
+  } else if (!scratch) {
+    return noalloc_fail(VDBEDT_ECUDA, "vdbedt_edt_dense_noalloc: first call on this device made during a stream "
+                                      "capture (call it once before capturing)");
   }
-  cudaStream_t st = (cudaStream_t)stream;
   int64_t blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   uint16_t* g1 = scratch;
   uint16_t* g2 = scratch + kMaxVoxels;
   VDB_LAUNCH(k_dense_x, (unsigned)blocks, 256, 0, st, occ, nx, ny, nz, dmax, g1);
+  if (cudaGetLastError() != cudaSuccess) return noalloc_fail(VDBEDT_ECUDA, "vdbedt_edt_dense_noalloc: x launch");
   VDB_LAUNCH(k_dense_win, (unsigned)blocks, 256, 0, st, g1, nx, ny, nz, dmax, 1, g2, (int32_t*)nullptr);
+  if (cudaGetLastError() != cudaSuccess) return noalloc_fail(VDBEDT_ECUDA, "vdbedt_edt_dense_noalloc: y launch");
   VDB_LAUNCH(k_dense_win, (unsigned)blocks, 256, 0, st, g2, nx, ny, nz, dmax, 2, (uint16_t*)nullptr, out);
-  return cudaGetLastError() == cudaSuccess ? VDBEDT_OK : VDBEDT_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return noalloc_fail(VDBEDT_ECUDA, "vdbedt_edt_dense_noalloc: z launch");
+  return VDBEDT_OK;
 }

@@ -215,6 +215,8 @@ namespace vdbedt {
 
 // Process-wide count of kernel launches made by the library (reported by vdbedt_kernel_launches).
 void note_launch();
+// Message returned by vdbedt_last_error(NULL) on this thread (calls that have no handle).
+void set_last_error(const char* msg);
 
 #define VDB_LAUNCH(kernel, grid, block, smem, stream, ...)         \
   do {                                                             \

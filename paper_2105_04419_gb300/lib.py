@@ -427,15 +427,29 @@ NOALLOC_MAX_VOXELS = 1 << 21
 def edt_dense_noalloc(occ, dmax: int, out=None):
     """D of a small dense grid occ [nz, ny, nx] (CUDA tensor) through vdbedt_edt_dense_noalloc, which
     allocates nothing on the device (its scratch is a fixed array of the library); returns int32
-    [nz, ny, nx] on the current torch stream.  `out` (int32 CUDA tensor) may be given preallocated."""
+    [nz, ny, nx] on occ's device and that device's current torch stream.  `out` (a contiguous int32
+    CUDA tensor of shape [nz, ny, nx] on occ's device) may be given preallocated, so that the call
+    itself allocates nothing.  Bad tensors raise TypeError / ValueError before the C call."""
     torch = _torch()
-    o = occ.to(torch.uint8).contiguous()
-    nz, ny, nx = o.shape
-    if out is None:
-        out = torch.empty((nz, ny, nx), dtype=torch.int32, device=o.device)
-    st = torch.cuda.current_stream(o.device).cuda_stream
-    _check(load().vdbedt_edt_dense_noalloc(o.data_ptr(), nx, ny, nz, int(dmax), out.data_ptr(), st),
-           "vdbedt_edt_dense_noalloc")
+    if not isinstance(occ, torch.Tensor) or not occ.is_cuda:
+        raise TypeError("occ must be a CUDA tensor [nz, ny, nx]")
+    if occ.dim() != 3:
+        raise ValueError(f"occ must have 3 dimensions [nz, ny, nx], got shape {tuple(occ.shape)}")
+    if out is not None:
+        if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.int32:
+            raise TypeError("out must be an int32 CUDA tensor")
+        if out.device != occ.device:
+            raise ValueError(f"out is on {out.device}, occ on {occ.device}")
+        if tuple(out.shape) != tuple(occ.shape) or not out.is_contiguous():
+            raise ValueError(f"out must be contiguous with shape {tuple(occ.shape)}")
+    with torch.cuda.device(occ.device):
+        o = occ if (occ.dtype == torch.uint8 and occ.is_contiguous()) else occ.to(torch.uint8).contiguous()
+        nz, ny, nx = o.shape
+        if out is None:
+            out = torch.empty((nz, ny, nx), dtype=torch.int32, device=o.device)
+        st = torch.cuda.current_stream(o.device).cuda_stream
+        _check(load().vdbedt_edt_dense_noalloc(o.data_ptr(), nx, ny, nz, int(dmax), out.data_ptr(), st),
+               "vdbedt_edt_dense_noalloc")
     return out
 
 

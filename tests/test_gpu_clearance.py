@@ -59,6 +59,15 @@ def test_boundary_points_and_clamping():
 
 
 def test_gradient_vs_finite_differences():
+    """Central differences of the float64 oracle at h = 1e-3 m against the GPU gradient, held to the
+    stated gradient tolerance (1e-3 relative, 1e-5 absolute floor where the hinge is inactive).
+
+    The perturbed points are float32 and the cell coordinate u = p / vs is taken in float32 (the
+    precision both sides pick the cell in), so the step actually taken in u differs from 2 h / vs by
+    up to an ulp of u on each side.  Inside a cell the squared hinge of a trilinear distance is
+    exactly quadratic along one axis, so the divided difference over the step actually taken is the
+    derivative at its midpoint; dividing by that step (not by 2 h) removes the rounding of the
+    perturbation from the comparison."""
     import torch
     import paper_2105_04419_gb300 as V
     occ, m, D = setup_field(seed=5)
@@ -73,11 +82,15 @@ def test_gradient_vs_finite_differences():
     keep = ((frac > 2 * h / vs) & (frac < 1 - 2 * h / vs)).all(1) & (np.abs(tau - d[0]) > 2 * h)
     assert keep.sum() > 100
     fd = np.zeros((keep.sum(), 3))
+    vs32 = np.float32(vs)
     for a in range(3):
         e = np.zeros(3)
         e[a] = h
         for j, i in enumerate(np.flatnonzero(keep)):
-            cp = O.clearance(D, 12, vs, tau, (pts[0, i] + e).astype(np.float32)[None, None])[0][0]
-            cm = O.clearance(D, 12, vs, tau, (pts[0, i] - e).astype(np.float32)[None, None])[0][0]
-            fd[j, a] = (cp - cm) / (2 * h)
-    np.testing.assert_allclose(grad[keep], fd, rtol=2e-3, atol=2e-4)
+            pp = (pts[0, i] + e).astype(np.float32)
+            pm = (pts[0, i] - e).astype(np.float32)
+            cp = O.clearance(D, 12, vs, tau, pp[None, None])[0][0]
+            cm = O.clearance(D, 12, vs, tau, pm[None, None])[0][0]
+            step = (float(pp[a] / vs32) - float(pm[a] / vs32)) * vs  # metres, as the oracle sees it
+            fd[j, a] = (cp - cm) / step
+    np.testing.assert_allclose(grad[keep], fd, rtol=GRAD_RTOL, atol=GRAD_ATOL)

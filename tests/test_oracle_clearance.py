@@ -63,14 +63,20 @@ def test_gradient_vs_central_differences():
     frac = u - np.floor(u)
     keep = ((frac > 2 * h / vs) & (frac < 1 - 2 * h / vs)).all(1) & (np.abs(tau - d[0]) > 2 * h)
     assert keep.sum() > 100
+    vs32 = np.float32(vs)
     for a in range(3):
         e = np.zeros(3)
         e[a] = h
-        # finite differences in float64 on the oracle's own value, evaluated point by point
-        cp = [O.clearance(D, dmax, vs, tau, (pts[0, i] + e)[None, None].astype(np.float64).astype(np.float32))[0][0]
-              for i in np.flatnonzero(keep)]
-        cm = [O.clearance(D, dmax, vs, tau, (pts[0, i] - e)[None, None].astype(np.float64).astype(np.float32))[0][0]
-              for i in np.flatnonzero(keep)]
-        fd = (np.array(cp) - np.array(cm)) / (2 * h)
+        # central differences in float64 on the oracle's own value, point by point; the points are
+        # float32 and u = p / vs is taken in float32, so the quotient divides by the step actually
+        # taken in u (the squared hinge of a trilinear distance is exactly quadratic along one axis
+        # inside a cell, so that quotient is the derivative at the step's midpoint)
+        idx = np.flatnonzero(keep)
+        pp = [(pts[0, i] + e).astype(np.float32) for i in idx]
+        pm = [(pts[0, i] - e).astype(np.float32) for i in idx]
+        cp = np.array([O.clearance(D, dmax, vs, tau, q[None, None])[0][0] for q in pp])
+        cm = np.array([O.clearance(D, dmax, vs, tau, q[None, None])[0][0] for q in pm])
+        step = np.array([(float(q[a] / vs32) - float(r[a] / vs32)) * vs for q, r in zip(pp, pm)])
+        fd = (cp - cm) / step
         an = grad[0, keep, a]
-        np.testing.assert_allclose(an, fd, rtol=1e-3, atol=1e-4)
+        np.testing.assert_allclose(an, fd, rtol=1e-3, atol=1e-5)
