@@ -175,7 +175,12 @@ vdbedt_status vdbedt_clearance_backward(vdbedt_handle h, const float* pts, int64
  *   x_run, y_run, z_run: bricks per work item of the pass along that axis (4, 8 or 16);
  *   variant: 0 automatic, 1 full windowed minimum, 3 windowed minimum with early exit and skips
  *            (the default; both exact); adding 4 (5 or 7) runs the x pass with plain loads instead
- *            of the bulk-copy ring.  Other values are EINVAL. */
+ *            of the bulk-copy ring; 8 the lower-envelope form of all three passes (exact, O(1)
+ *            amortised work per voxel whatever the window, runs of 16 bricks: the separable
+ *            transform of Eq. 1 line by line).  Grids with dmax above 45 always take the envelope
+ *            form.  Switching between the windowed and envelope forms changes how intermediate
+ *            fields are stored, so the next vdbedt_update recomputes the whole field (as
+ *            vdbedt_global).  Other values are EINVAL. */
 typedef struct {
   int32_t x_run, y_run, z_run, variant;
 } vdbedt_tuning;
@@ -223,8 +228,9 @@ vdbedt_status vdbedt_batch_map(vdbedt_batch_handle b, int32_t i, vdbedt_handle* 
  * before return).  grids itself is a host array of k pointers. */
 vdbedt_status vdbedt_batch_set_occupancy_dense(vdbedt_batch_handle b, const uint8_t* const* grids, int on_device);
 /* Global transform of every grid of the batch (records staged on a grid are applied first).
- * Bit-identical to vdbedt_global on each grid.  Grids with dmax above 45 are transformed one
- * after the other. */
+ * Bit-identical to vdbedt_global on each grid.  In the lower-envelope form (dmax above 45, or
+ * variant 8) the grids are transformed one after the other, and the batch's phase times put the
+ * whole transform in z_ms. */
 vdbedt_status vdbedt_batch_global(vdbedt_batch_handle b);
 /* vdbedt_set_tuning on every grid of the batch. */
 vdbedt_status vdbedt_batch_set_tuning(vdbedt_batch_handle b, const vdbedt_tuning* t);

@@ -2,15 +2,19 @@
 
 The brick is fixed at 8^3 voxels (the storage layout); what is tuned is the tile each pass works
 on -- the run of bricks one work item covers along the pass axis (4, 8 or 16 bricks: longer runs
-re-read less halo per output brick but give fewer, larger items) -- and the window variant of the
-in-plane and z passes (1: full window; 3: window with early exit and skips of windows without
-finite input).  Every choice computes the same exact field; only the time differs.
+re-read less halo per output brick but give fewer, larger items) -- and the algorithm: the windowed
+minimum of the in-plane and z passes (1: full window; 3: window with early exit and skips of
+windows without finite input) or the lower-envelope form of all three passes (variant 8: O(1)
+amortised work per voxel whatever the window, on runs of 16 bricks; the only form above dmax 45).
+Every choice computes the same exact field; only the time differs.
 
 The tuner times the map's (or batch's) own global transform under each candidate with the
 library's phase events, picks per axis the fastest run, and stores the choice in a JSON cache keyed
 by GPU, brick radius and workload size, so that later maps of the same kind reuse it without
-timing.  The passes are independent per axis, so 3 variants x 3 runs = 9 timed configurations
-cover every combination (the x pass also has two kernels: the bulk-copy ring and plain loads).
+timing.  The windowed passes are independent per axis, so 3 variants x 3 runs = 9 timed
+configurations cover every combination (the x pass also has two kernels: the bulk-copy ring and
+plain loads); the envelope form is one more, compared with the windowed choice on the whole
+transform (x + y + z), since it replaces all three passes.
 """
 from __future__ import annotations
 
@@ -23,6 +27,9 @@ RUNS = (4, 8, 16)
 # 1: full window; 3: pruned window; 7: pruned window with the x pass on plain loads (+4)
 VARIANTS = (1, 3, 7)
 X_DIRECT = 4
+ENVELOPE = 8  # the lower-envelope form (runs of 16 bricks; the run settings do not apply)
+ENVELOPE_KEY = (ENVELOPE, 16)
+WINDOW_DMAX = 45  # above it, the envelope is the only form
 # Candidates within TIE of the fastest count as equal, and the first of them in preference order
 # wins (the library defaults first), so that timing noise does not flip the choice between runs.
 TIE = 0.02
@@ -66,10 +73,16 @@ def _pick(cands, cost):
 
 def choose(table: dict, joint_yz: bool = False) -> dict:
     """Pick the tuning from timed phases.  table[(variant, run)] = {"x_ms", "y_ms", "z_ms"}
-    (medians).  The x pass takes its fastest (kernel, run) over every candidate (its time depends
-    only on the X_DIRECT bit of the variant and the run); the window variant is the one whose best
-    y + z is lowest; then y and z each take their fastest run under it (jointly when the phases are
-    timed together, as for batches).  Near-ties (TIE) go to the preferred candidate."""
+    (medians), with the envelope form at ENVELOPE_KEY when it was timed.  The x pass takes its
+    fastest (kernel, run) over every windowed candidate (its time depends only on the X_DIRECT bit
+    of the variant and the run); the window variant is the one whose best y + z is lowest; then y
+    and z each take their fastest run under it (jointly when the phases are timed together, as for
+    batches).  The envelope form replaces that choice when its whole transform (x + y + z) is
+    faster than the windowed choice's.  Near-ties (TIE) go to the preferred candidate (the windowed
+    form before the envelope)."""
+    env = {"x_run": 16, "y_run": 16, "z_run": 16, "variant": ENVELOPE}
+    if not any(k != ENVELOPE_KEY for k in table):
+        return env
     xv, x_run = _pick([(v, r) for v in VARIANT_PREF for r in RUN_PREF], lambda vr: table[vr]["x_ms"])
 
     def yz_best(v):
@@ -81,8 +94,12 @@ def choose(table: dict, joint_yz: bool = False) -> dict:
         return table[(v, ry)]["y_ms"] + table[(v, rz)]["z_ms"], ry, rz
 
     window = _pick(VARIANT_PREF, lambda v: yz_best(v)[0])
-    _, y_run, z_run = yz_best(window)
+    yz, y_run, z_run = yz_best(window)
     variant = (window & 3) | (xv & X_DIRECT)
+    if ENVELOPE_KEY in table:
+        e = table[ENVELOPE_KEY]
+        if (e["x_ms"] + e["y_ms"] + e["z_ms"]) * (1.0 + TIE) < table[(xv, x_run)]["x_ms"] + yz:
+            return env
     return {"x_run": x_run, "y_run": y_run, "z_run": z_run, "variant": variant}
 
 
@@ -106,19 +123,22 @@ def _store(path: str, key: str, value: dict) -> None:
 
 
 def measure(target, reps: int = 5) -> dict:
-    """Median phase times of target.global_() under each (variant, run) candidate."""
+    """Median phase times of target.global_() under each candidate: every (variant, run) of the
+    windowed form when the target's dmax allows it, and the envelope form."""
+    cands = [ENVELOPE_KEY]
+    if getattr(target, "dmax", 0) <= WINDOW_DMAX:
+        cands = [(v, r) for v in VARIANTS for r in RUNS] + cands
     table = {}
     target.set_profiling(True)
     try:
-        for v in VARIANTS:
-            for r in RUNS:
-                target.set_tuning(r, r, r, v)
-                target.global_()  # warm-up (also applies any staged records)
-                samples = []
-                for _ in range(reps):
-                    target.global_()
-                    samples.append(target.phase_times())
-                table[(v, r)] = {k: statistics.median(s[k] for s in samples) for k in ("x_ms", "y_ms", "z_ms")}
+        for v, r in cands:
+            target.set_tuning(r, r, r, v)
+            target.global_()  # warm-up (also applies any staged records)
+            samples = []
+            for _ in range(reps):
+                target.global_()
+                samples.append(target.phase_times())
+            table[(v, r)] = {k: statistics.median(s[k] for s in samples) for k in ("x_ms", "y_ms", "z_ms")}
     finally:
         target.set_profiling(False)
     return table

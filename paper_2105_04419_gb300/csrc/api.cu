@@ -292,6 +292,7 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   g.dmax = cfg->dmax;
   g.R = (cfg->dmax + 6) / 8;
   g.INF = cfg->dmax * cfg->dmax;
+  g.half = (cfg->dmax <= 45 && g.R >= 1 && g.R <= 6) ? 1 : 0;  // fp16 fields unless the envelope form is chosen
   uint32_t hcap = 64;
   while ((int64_t)hcap < 2 * node_cap) hcap <<= 1;
   g.hmask = hcap - 1;
@@ -655,14 +656,22 @@ vdbedt_status vdbedt_set_tuning(vdbedt_handle h, const vdbedt_tuning* t) {
   if (s) return s;
   if (!t) return fail(h, VDBEDT_EINVAL, "null tuning");
   auto ok_run = [](int r) { return r == 0 || r == 4 || r == 8 || r == 16; };
+  const int v = t->variant;
   if (!ok_run(t->x_run) || !ok_run(t->y_run) || !ok_run(t->z_run) ||
-      !(t->variant == 0 || t->variant == 1 || t->variant == 3 || t->variant == 5 || t->variant == 7))
+      !(v == 0 || v == 1 || v == 3 || v == 5 || v == 7 || v == kVariantEnvelope))
     return fail(h, VDBEDT_EINVAL, "bad tuning");
   const Tuning d;
   h->tune.run[0] = t->x_run ? t->x_run : d.run[0];
   h->tune.run[1] = t->y_run ? t->y_run : d.run[1];
   h->tune.run[2] = t->z_run ? t->z_run : d.run[2];
-  h->tune.variant = t->variant ? t->variant : d.variant;
+  h->tune.variant = v ? v : d.variant;
+  // the windowed kernels keep fp16 fields, the envelope kernels 16-bit integers: a change of form
+  // makes the stored intermediates unusable, so the next update recomputes the whole field
+  const int half = (h->cfg.dmax <= 45 && h->g.R >= 1 && h->g.R <= 6 && h->tune.variant != kVariantEnvelope) ? 1 : 0;
+  if (half != h->g.half) {
+    h->g.half = half;
+    h->computed = false;
+  }
   return VDBEDT_OK;
 }
 
@@ -817,11 +826,15 @@ vdbedt_status batch_global(vdbedt_batch* b) {
   DeviceGuard guard(b->device);
   const GridView& g0 = b->maps[0]->g;
   if (!half_path(g0)) {
-    // dmax above 45: the generic kernels find bricks through each grid's own tables; grid by grid
+    // the envelope kernels find bricks through each grid's own tables: grid by grid (the phase
+    // events then put the whole transform in the last phase)
+    for (int i = 0; i < 5; ++i) bmark(b, i);
     for (vdbedt_map* m : b->maps) {
       s = do_global(m);
       if (s) return bfail(b, s, m->err);
     }
+    bmark(b, 5);
+    b->ev_recorded = b->profiling;
     return VDBEDT_OK;
   }
   Tuning t = b->tune;
@@ -1084,6 +1097,16 @@ vdbedt_status vdbedt_batch_set_tuning(vdbedt_batch_handle b, const vdbedt_tuning
     if (s) return bfail(b, s, m->err);
   }
   b->tune = b->maps[0]->tune;
+  if (b->pool.half != b->maps[0]->g.half) {
+    // the field form changed: the device copy of the grids' views follows
+    DeviceGuard guard(b->device);
+    std::vector<GridView> views;
+    for (vdbedt_map* m : b->maps) views.push_back(m->g);
+    BCK(b, cudaMemcpyAsync(b->d_views, views.data(), sizeof(GridView) * views.size(), cudaMemcpyHostToDevice, b->st),
+        "views");
+    BCK(b, cudaStreamSynchronize(b->st), "views");
+    b->pool.half = b->maps[0]->g.half;
+  }
   return VDBEDT_OK;
 }
 

@@ -125,8 +125,9 @@ __global__ void k_begin_update(GridView g) {
 }
 
 // ---- brick allocation ----
-// Fill a freshly allocated brick: empty occupancy, coordinates, flags; with `init_fields` also
-// g2 and D at dmax^2 (bricks added by an incremental update may be read before a pass writes them).
+// Fill a freshly allocated brick: empty occupancy, coordinates, flags (no plane holds a value below
+// dmax^2); with `init_fields` also g1, g2 and D at dmax^2 (bricks added by an incremental update may
+// be read before a pass writes them).
 __device__ __forceinline__ void init_brick_meta(const GridView& g, int slot, int node, int bx, int by, int bz) {
   g.bcoord[slot] = make_int4(bx, by, bz, node);
   g.bflags[slot] = 0u;
@@ -139,7 +140,7 @@ __device__ void init_brick(const GridView& g, int slot, int node, int bx, int by
   for (int q = 0; q < 4; ++q) occ[q] = make_ulonglong2(0ull, 0ull);
   if (init_fields) {
     uint16_t inf;
-    if (g.dmax <= 45 && g.R <= 6) {
+    if (g.half) {
       __half h = __int2half_rn(g.INF);
       inf = *reinterpret_cast<uint16_t*>(&h);
     } else {

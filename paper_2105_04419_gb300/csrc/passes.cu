@@ -38,8 +38,8 @@
 // reaches every output's current minimum in the warp, and skips windows whose input bricks hold no
 // value below dmax^2.
 //
-// Grids with dmax above 45 (up to 181) take the generic kernels at the end of the file: int32
-// arithmetic read from shared memory with a runtime window.
+// Grids with dmax above 45 (up to 181), and any grid tuned to variant 8, take the lower-envelope
+// kernels at the end of the file: O(1) amortised work per voxel, whatever the window.
 #include <cuda_fp16.h>
 
 #include "vdbedt_internal.cuh"
@@ -495,99 +495,184 @@ __global__ void __launch_bounds__(256) k_x_direct(GridView g, const int32_t* __r
 }
 
 // ------------------------------------------------------------------------------------------------
-// Generic kernels (any dmax up to 181): int32 from shared memory, runtime window W = 8R.
+// Lower-envelope kernels (any dmax up to 181; the only form above 45, variant 8 below it).
+//
+// Fields hold plain 16-bit integers (g1 y-major, g2 z-major, as in the windowed kernels).  A work
+// item is a run of kEnvRun bricks along the pass axis (a node's length); each kernel finds the
+// run's bricks and their R bricks of halo on each side through the node tables.
+//   x: the distance to the nearest occupied voxel of an x-line, from the line's bits: within the
+//      output brick's own byte with one count of leading / trailing zeros, beyond it by scanning
+//      the neighbouring bricks' bytes outward until one holds a set bit (a warp per output brick,
+//      a lane per two x-rows).
+//   y, z: for one line f(0 .. n-1) along the axis (the run and its halo, n = 8 (kEnvRun + 2R)),
+//      every output x needs min over q of (x - q)^2 + f(q), the lower envelope of the parabolas
+//      rooted at (q, f(q)) evaluated at x (the separable exact transform of Felzenszwalb and
+//      Huttenlocher, "Distance Transforms of Sampled Functions", 2012, restated here for integers
+//      and a streaming deque).  A thread owns a line.  Input q enters as the parabola with
+//      h = f(q) + q^2 (inputs at dmax^2 are left out: they cannot bring an output below dmax^2);
+//      the back of the deque is dropped while it is nowhere strictly below both its predecessor and
+//      the new parabola -- (h_q - h_b)(v_b - v_a) <= (h_b - h_a)(q - v_b), the intersection test
+//      with the denominators multiplied out (no division, exact in int32).  Once q = x + W, output x
+//      has seen every input within W (any farther one costs at least (W + 1)^2 >= dmax^2):
+//      parabolas rooted more than W before x are dropped from the front, the front is dropped while
+//      its successor is at least as low at x (h_b - h_a <= 2x (v_b - v_a)), and the front gives
+//      min(dmax^2, h - 2xv + x^2).  Queries advance monotonically, so every parabola enters and
+//      leaves once: O(1) amortised per voxel, independent of the window.  The deque holds at most
+//      2W + 2 entries (a ring in the thread's local memory, one packed word h << 9 | v each).
 // ------------------------------------------------------------------------------------------------
-constexpr int kGenRun = 4;
-constexpr int kGenThreads = 256;
+constexpr int kEnvRun = 16;
+constexpr int kEnvThreads = 64;  // y, z: one line of an item per thread (8 x 8 lines)
 
-__global__ void __launch_bounds__(kGenThreads) k_xy_generic(GridView g, const unsigned long long* __restrict__ items,
-                                                            int max_items) {
-  const int R = g.R, W = 8 * R, NBX = 2 * R + 1, NBY = kGenRun + 2 * R, NYR = 8 * NBY;
-  extern __shared__ __align__(16) unsigned char smem[];
-  int* slots = reinterpret_cast<int*>(smem);                        // [NBY][NBX]
-  int* g1 = slots + NBX * NBY;                                      // [z][row][x]
-  const int nitems = min(g.items_ctr[1], max_items);
+__device__ __forceinline__ int occ_byte(const GridView& g, int slot, int row) {
+  return slot >= 0 ? (int)reinterpret_cast<const uint8_t*>(g.occ)[(size_t)slot * 64 + row] : 0;
+}
+
+// x pass (lower envelope of a binary line = nearest set bit).  Block = 8 warps; per item the
+// slots of the run and its halo along x are looked up once.
+__global__ void __launch_bounds__(256) k_env_x(GridView g, const unsigned long long* __restrict__ items, int max_items) {
+  __shared__ int slots[kEnvRun + 2 * 23];
+  const int R = g.R, NB = kEnvRun + 2 * R, INF = g.INF, dmax = g.dmax;
+  const int nitems = min(g.items_ctr[0], max_items);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    int bx, by0, bz;
-    unpack_brick(items[it], bx, by0, bz);
-    for (int i = threadIdx.x; i < NBX * NBY; i += blockDim.x)
-      slots[i] = find_brick(g, bx - R + i % NBX, by0 - R + i / NBX, bz);
+    int bx0, by, bz;
+    unpack_brick(items[it], bx0, by, bz);
     __syncthreads();
-    // x pass straight from the bit masks: scan outward along the line
-    for (int i = threadIdx.x; i < 8 * NYR * 8; i += blockDim.x) {
-      int x = i & 7, row = (i >> 3) % NYR, z = (i >> 3) / NYR;
-      int byi = row >> 3, y = row & 7;
-      int best = g.INF;
-      for (int d = 0; d <= W && d * d < best; ++d) {
-        for (int sgn = -1; sgn <= 1; sgn += 2) {
-          if (d == 0 && sgn > 0) continue;
-          int xx = 8 * R + x + sgn * d;  // position in the line of 8 * NBX voxels
-          if (xx < 0 || xx >= 8 * NBX) continue;
-          int s = slots[byi * NBX + (xx >> 3)];
-          if (s < 0) continue;
-          uint8_t rowbits = reinterpret_cast<const uint8_t*>(g.occ)[(size_t)s * 64 + y + 8 * z];
-          if ((rowbits >> (xx & 7)) & 1) best = min(best, d * d);
-        }
-      }
-      g1[(z * NYR + row) * 8 + x] = best;
-    }
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) slots[i] = find_brick(g, bx0 - R + i, by, bz);
     __syncthreads();
-    for (int i = threadIdx.x; i < kGenRun * 512; i += blockDim.x) {
-      int b = i >> 9, v = i & 511;
-      int x = v & 7, y = (v >> 3) & 7, z = v >> 6;
-      int s = slots[(b + R) * NBX + R];
-      if (s < 0) continue;
-      int row = (b + R) * 8 + y;
-      int best = g.INF;
-      for (int d = -W; d <= W; ++d) best = min(best, d * d + g1[(z * NYR + row + d) * 8 + x]);
-      g.g2[(size_t)s * kBrickVox + v] = (uint16_t)best;
-    }
-    __syncthreads();
-    // in-plane finite flags of the run's bricks
-    for (int b = 0; b < kGenRun; ++b) {
-      int s = slots[(b + R) * NBX + R];
-      if (s < 0) continue;
+    for (int b = warp; b < kEnvRun; b += 8) {
+      const int slot = slots[b + R];
+      if (slot < 0) continue;  // warp-uniform
       bool fin = false;
-      for (int v = threadIdx.x; v < 512; v += blockDim.x) fin |= g.g2[(size_t)s * kBrickVox + v] < (uint16_t)g.INF;
-      int any = __syncthreads_or(fin);
-      if (threadIdx.x == 0) set_flag_bit(g, s, F_G2FIN, any);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = lane + 32 * h;  // y + 8 z: byte of the brick masks
+        const int y = row & 7, z = row >> 3;
+        const int own = occ_byte(g, slots[b + R], row);
+        // distance from the brick's first voxel to the nearest set bit before it, and from its last
+        // voxel to the nearest one after it (beyond dmax - 1 counts as none)
+        int left = 1 << 20, right = 1 << 20;
+        for (int j = 1; j <= R && 8 * j - 7 < dmax; ++j) {
+          const int m = occ_byte(g, slots[b + R - j], row);
+          if (m) {
+            left = 8 * j - (31 - __clz(m));
+            break;
+          }
+        }
+        for (int j = 1; j <= R && 8 * j - 7 < dmax; ++j) {
+          const int m = occ_byte(g, slots[b + R + j], row);
+          if (m) {
+            right = 8 * j - 7 + (__ffs(m) - 1);
+            break;
+          }
+        }
+        uint16_t v[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          const int lm = own & ((2 << x) - 1), rm = own >> x;
+          const int dl = lm ? x - (31 - __clz(lm)) : x + left;
+          const int dr = rm ? __ffs(rm) - 1 : (7 - x) + right;
+          const int d = min(dl, dr);
+          const int val = d < dmax ? d * d : INF;
+          fin |= val < INF;
+          v[x] = (uint16_t)val;
+        }
+        // g1 is y-major: voxel x + 8 z + 64 y
+        uint4 pk;
+        pk.x = v[0] | ((uint32_t)v[1] << 16);
+        pk.y = v[2] | ((uint32_t)v[3] << 16);
+        pk.z = v[4] | ((uint32_t)v[5] << 16);
+        pk.w = v[6] | ((uint32_t)v[7] << 16);
+        *reinterpret_cast<uint4*>(g.g1 + (size_t)slot * kBrickVox + 64 * y + 8 * z) = pk;
+      }
+      const unsigned anyfin = __any_sync(0xffffffffu, fin);
+      if (lane == 0) set_flag_bit(g, slot, F_G1FIN, anyfin);
     }
   }
 }
 
-__global__ void __launch_bounds__(kGenThreads) k_z_generic(GridView g, const unsigned long long* __restrict__ items,
-                                                           int max_items) {
-  const int R = g.R, W = 8 * R, NB = kGenRun + 2 * R;
-  extern __shared__ __align__(16) unsigned char smem[];
-  int* slots = reinterpret_cast<int*>(smem);
-  uint16_t* col = reinterpret_cast<uint16_t*>(slots + NB + 3);  // [brick][512]
-  const int nitems = min(g.items_ctr[2], max_items);
+// y (AXIS 1: g1 -> g2) or z (AXIS 2: g2 -> D) pass by the lower envelope.  Block = one item at a
+// time, thread t = the line (t & 7, t >> 3) across the axis.  RING >= 2W + 2.
+template <int AXIS, int RING>
+__global__ void __launch_bounds__(kEnvThreads) k_env_yz(GridView g, const unsigned long long* __restrict__ items,
+                                                        int max_items) {
+  __shared__ int slots[kEnvRun + 2 * 23];  // stored bricks of the run and its halo (-1: none)
+  __shared__ int inslot[kEnvRun + 2 * 23];  // the same, -1 also where the brick's input is all dmax^2
+  __shared__ __align__(16) uint16_t tile[kBrickVox];  // y pass: one output brick, transposed to z-major
+  const int R = g.R, W = 8 * R, NB = kEnvRun + 2 * R, n = 8 * NB, INF = g.INF;
+  const int nitems = min(g.items_ctr[AXIS], max_items);
+  const int t = threadIdx.x;
+  const int c0 = t & 7, c1 = t >> 3;  // y pass: (x, z); z pass: (x, y)
+  const uint16_t* __restrict__ src = AXIS == 1 ? g.g1 : g.g2;
+  const uint32_t in_fin = AXIS == 1 ? F_G1FIN : F_G2FIN;
+  int ring[RING];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    int bx, by, bz0;
-    unpack_brick(items[it], bx, by, bz0);
-    for (int i = threadIdx.x; i < NB; i += blockDim.x) slots[i] = find_brick(g, bx, by, bz0 - R + i);
-    __syncthreads();
-    for (int i = threadIdx.x; i < NB * 512; i += blockDim.x) {
-      int s = slots[i >> 9];
-      col[i] = s >= 0 ? g.g2[(size_t)s * kBrickVox + (i & 511)] : (uint16_t)g.INF;
+    int bx, by, bz;
+    unpack_brick(items[it], bx, by, bz);
+    __syncthreads();  // the previous item's slots are no longer read
+    for (int i = t; i < NB; i += blockDim.x) {
+      const int s = AXIS == 1 ? find_brick(g, bx, by - R + i, bz) : find_brick(g, bx, by, bz - R + i);
+      slots[i] = s;
+      inslot[i] = (s >= 0 && (g.bflags[s] & in_fin)) ? s : -1;
     }
     __syncthreads();
-    for (int b = 0; b < kGenRun; ++b) {
-      int s = slots[b + R];
-      if (s < 0) continue;
-      bool finite = false;
-      for (int v = threadIdx.x; v < 512; v += blockDim.x) {
-        int z = v >> 6, xy = v & 63;
-        int plane = (b + R) * 8 + z;
-        int best = g.INF;
-        for (int d = -W; d <= W; ++d) best = min(best, d * d + (int)col[(plane + d) * 64 + xy]);
-        g.dist[(size_t)s * kBrickVox + v] = best;
-        finite |= best < g.INF;
+    int head = 0, tail = 0, cnt = 0;
+    bool fin = false;
+    for (int q = 0; q < n; ++q) {
+      const int sq = inslot[q >> 3];
+      // input (c0, c1) at position q & 7 along the axis: g1 y-major x + 8z + 64y, g2 z-major x + 8y + 64z
+      const int f = sq >= 0 ? (int)src[(size_t)sq * kBrickVox + 64 * (q & 7) + 8 * c1 + c0] : INF;
+      if (f < INF) {
+        const int hq = f + q * q;
+        while (cnt >= 2) {
+          const int ib = tail == 0 ? RING - 1 : tail - 1, ia = ib == 0 ? RING - 1 : ib - 1;
+          const int b = ring[ib], a = ring[ia];
+          const int vb = b & 511, hb = b >> 9, va = a & 511, ha = a >> 9;
+          if ((hq - hb) * (vb - va) > (hb - ha) * (q - vb)) break;
+          tail = ib;
+          --cnt;
+        }
+        ring[tail] = (hq << 9) | q;
+        tail = tail + 1 == RING ? 0 : tail + 1;
+        ++cnt;
       }
-      int any = __syncthreads_or(finite);
-      if (threadIdx.x == 0) set_flag_bit(g, s, F_FINITE, any);
+      const int x = q - W;  // output position, once every input within W of it is in
+      if (x < W) continue;  // block-uniform
+      while (cnt > 0 && (ring[head] & 511) < x - W) {
+        head = head + 1 == RING ? 0 : head + 1;
+        --cnt;
+      }
+      while (cnt >= 2) {
+        const int ib = head + 1 == RING ? 0 : head + 1;
+        const int a = ring[head], b = ring[ib];
+        if ((b >> 9) - (a >> 9) > 2 * x * ((b & 511) - (a & 511))) break;
+        head = ib;
+        --cnt;
+      }
+      int res = INF;
+      if (cnt > 0) {
+        const int a = ring[head];
+        res = min(INF, (a >> 9) - 2 * x * (a & 511) + x * x);
+      }
+      fin |= res < INF;
+      const int oslot = slots[x >> 3];  // block-uniform
+      const int k = x & 7;
+      if (AXIS == 1)
+        tile[c0 + 8 * k + 64 * c1] = (uint16_t)res;  // g2 z-major: x + 8 y + 64 z
+      else if (oslot >= 0)
+        g.dist[(size_t)oslot * kBrickVox + 64 * k + 8 * c1 + c0] = res;  // D z-major: x + 8 y + 64 z
+      if (k == 7) {  // block-uniform: the output brick is complete
+        const int any = __syncthreads_or(fin);
+        fin = false;
+        if (oslot >= 0) {
+          if (AXIS == 1)
+            for (int i = t; i < kBrickVox / 8; i += blockDim.x)
+              reinterpret_cast<uint4*>(g.g2 + (size_t)oslot * kBrickVox)[i] = reinterpret_cast<const uint4*>(tile)[i];
+          if (t == 0) set_flag_bit(g, oslot, AXIS == 1 ? F_G2FIN : F_FINITE, any != 0);
+        }
+        if (AXIS == 1) __syncthreads();  // the tile is read before the next brick overwrites it
+      }
     }
-    __syncthreads();
   }
 }
 
@@ -602,20 +687,34 @@ int num_sms() {
   return g_num_sms;
 }
 
-template <typename K, typename... Extra>
-cudaError_t launch_persistent(K kernel, int threads, size_t smem, const GridView& g, const unsigned long long* items,
-                              int max_items, cudaStream_t st, Extra... extra) {
-  if (max_items <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+// Persistent launch of an envelope kernel: as many blocks as fit on the GPU at once (items are
+// taken grid-stride; blocks beyond the queued count exit at once).
+template <typename K>
+cudaError_t launch_env_kernel(K kernel, int threads, const GridView& g, const unsigned long long* items,
+                              cudaStream_t st) {
+  if (g.item_cap <= 0) return cudaSuccess;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = num_sms() * per_sm;
-  if (grid > max_items) grid = max_items;
-  VDB_LAUNCH(kernel, grid, threads, smem, st, g, items, max_items, extra...);
+  if (grid > g.item_cap) grid = g.item_cap;
+  VDB_LAUNCH(kernel, grid, threads, 0, st, g, items, g.item_cap);
   return cudaGetLastError();
+}
+
+// Envelope pass along `axis`; the deque ring is sized for the grid's window (2W + 2 entries).
+cudaError_t launch_env(const GridView& g, int axis, const Items& it, cudaStream_t st) {
+  if (axis == 0) return launch_env_kernel(k_env_x, 256, g, it.run[0], st);
+  const int need = 2 * 8 * g.R + 2;
+  if (axis == 1) {
+    if (need <= 130) return launch_env_kernel(k_env_yz<1, 130>, kEnvThreads, g, it.run[1], st);
+    if (need <= 258) return launch_env_kernel(k_env_yz<1, 258>, kEnvThreads, g, it.run[1], st);
+    return launch_env_kernel(k_env_yz<1, 370>, kEnvThreads, g, it.run[1], st);
+  }
+  if (need <= 130) return launch_env_kernel(k_env_yz<2, 130>, kEnvThreads, g, it.run[2], st);
+  if (need <= 258) return launch_env_kernel(k_env_yz<2, 258>, kEnvThreads, g, it.run[2], st);
+  return launch_env_kernel(k_env_yz<2, 370>, kEnvThreads, g, it.run[2], st);
 }
 
 template <int R, int RUN, int AXIS>
@@ -709,9 +808,9 @@ cudaError_t launch_wait_selftest(const GridView& g, int which, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-bool half_path(const GridView& g) { return g.dmax <= 45 && g.R >= 1 && g.R <= 6; }
+bool half_path(const GridView& g) { return g.half != 0; }
 
-int effective_run(const GridView& g, const Tuning& t, int axis) { return half_path(g) ? t.run[axis] : kGenRun; }
+int effective_run(const GridView& g, const Tuning& t, int axis) { return half_path(g) ? t.run[axis] : kEnvRun; }
 
 // The half kernels address bricks by pool slot (the slot lists hold local slot + slot_base):
 // their view has the per-brick pointers moved back to the first slot of the pool.
@@ -738,16 +837,8 @@ cudaError_t launch_pass(const GridView& g, const Tuning& t, int axis, const Item
     if (axis == 1) return pass_half_run<1>(p, t.run[1], it.slots[1], g.item_cap, st, prune);
     return pass_half_run<2>(p, t.run[2], it.slots[2], g.item_cap, st, prune);
   }
-  // the generic kernels find bricks through the grid's own tables (local slots)
-  if (axis == 0) return cudaSuccess;  // the generic in-plane kernel reads the masks itself
-  if (axis == 1) {
-    const int R = g.R, NBX = 2 * R + 1, NBY = kGenRun + 2 * R;
-    size_t smem = (size_t)NBX * NBY * 4 + (size_t)8 * 8 * NBY * 8 * 4 + 64;
-    return launch_persistent(k_xy_generic, kGenThreads, smem, g, it.run[1], g.item_cap, st);
-  }
-  const int NB = kGenRun + 2 * g.R;
-  size_t smem = (size_t)(NB + 3) * 4 + (size_t)NB * 512 * 2 + 64;
-  return launch_persistent(k_z_generic, kGenThreads, smem, g, it.run[2], g.item_cap, st);
+  // the envelope kernels find bricks through the grid's own tables (local slots)
+  return launch_env(g, axis, it, st);
 }
 
 }  // namespace vdbedt

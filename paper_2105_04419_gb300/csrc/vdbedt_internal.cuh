@@ -66,6 +66,8 @@ struct GridView {
   int BX, BY, BZ;     // bricks per axis
   int NX, NY, NZ;     // nodes per axis
   int dmax, R, INF;   // truncation, brick radius of influence, dmax^2
+  int half;           // 1: g1 / g2 hold fp16 bit patterns (windowed kernels, dmax <= 45); 0: 16-bit
+                      // integers (lower-envelope kernels)
   uint32_t hmask;     // hash capacity - 1
   int cap;            // brick capacity
   int node_cap;       // node capacity
@@ -228,8 +230,10 @@ constexpr int kItemSlots = 32;  // slot list entries per work item (run + 2R <= 
 constexpr int kBatchMax = 1024;  // grids per batch (the dense-ingest source table is a kernel parameter)
 
 // Tuning.variant: low bits 1 = full windowed minimum, 3 = windowed minimum with early exit and
-// skips (y and z passes); + kVariantXDirect = x pass with plain loads instead of the copy ring.
+// skips (y and z passes); + kVariantXDirect = x pass with plain loads instead of the copy ring;
+// kVariantEnvelope = the lower-envelope kernels for all three passes (16-bit integer fields).
 constexpr int kVariantXDirect = 4;
+constexpr int kVariantEnvelope = 8;
 struct Tuning {
   int run[3] = {4, 4, 4};  // bricks per work item along x, y, z
   int variant = 3;

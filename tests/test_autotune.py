@@ -8,8 +8,28 @@ import pytest
 from paper_2105_04419_gb300 import autotune as A
 
 
-def table_from(fn):
-    return {(v, r): fn(v, r) for v in A.VARIANTS for r in A.RUNS}
+def table_from(fn, envelope=None):
+    t = {(v, r): fn(v, r) for v in A.VARIANTS for r in A.RUNS}
+    if envelope is not None:
+        t[A.ENVELOPE_KEY] = envelope
+    return t
+
+
+def test_choose_envelope_only_when_faster_overall():
+    # windowed best: x 1.0 (run 16) + y 4.0 (run 8) + z 4.0 (run 4) = 9.0
+    def t(v, r):
+        return {"x_ms": {4: 3.0, 8: 2.0, 16: 1.0}[r] + (0.5 if v & 4 else 0.0),
+                "y_ms": {4: 5.0, 8: 4.0, 16: 6.0}[r] * (2.0 if v == 1 else 1.0),
+                "z_ms": {4: 4.0, 8: 5.0, 16: 7.0}[r] * (2.0 if v == 1 else 1.0)}
+    slower = {"x_ms": 1.0, "y_ms": 4.0, "z_ms": 4.1}       # 9.1: the windowed choice stays
+    tie = {"x_ms": 1.0, "y_ms": 3.9, "z_ms": 3.95}          # 8.85, within 2 %: the windowed choice stays
+    faster = {"x_ms": 0.5, "y_ms": 2.0, "z_ms": 2.0}       # 4.5: the envelope form wins
+    win = {"x_run": 16, "y_run": 8, "z_run": 4, "variant": 3}
+    assert A.choose(table_from(t, slower)) == win
+    assert A.choose(table_from(t, tie)) == win
+    assert A.choose(table_from(t, faster)) == {"x_run": 16, "y_run": 16, "z_run": 16, "variant": 8}
+    # above dmax 45 only the envelope is timed
+    assert A.choose({A.ENVELOPE_KEY: faster})["variant"] == 8
 
 
 def test_choose_per_axis_minimum():
@@ -57,9 +77,11 @@ def test_choose_joint_yz():
 
 
 class FakeTarget:
-    """Records calls; phase times depend on the tuning like a pass that prefers run 8."""
+    """Records calls; phase times depend on the tuning like a pass that prefers run 8 (the
+    envelope form, variant 8, is slower overall)."""
 
     device = 0
+    dmax = 32
 
     def __init__(self):
         self.tuning = None
@@ -77,6 +99,8 @@ class FakeTarget:
 
     def phase_times(self):
         x, y, z, v = self.tuning
+        if v == A.ENVELOPE:
+            return {"x_ms": 1.0, "y_ms": 2.0, "z_ms": 2.0}
         cost = {4: 2.0, 8: 1.0, 16: 3.0}
         return {"x_ms": cost[x] + (v & 4), "y_ms": cost[y] + (v == 1), "z_ms": cost[z] + (v == 1)}
 
@@ -110,7 +134,7 @@ def test_autotuned_map_is_exact(tmp_path):
     m = V.Map(192, 160, 64, 20)
     m.set_occupancy_dense(occ)
     got = A.autotune(m, reps=2, cache_path=str(tmp_path / "t.json"))
-    assert got["source"] == "measured" and got["variant"] in (1, 3, 5, 7)
+    assert got["source"] == "measured" and got["variant"] in (1, 3, 5, 7, 8)
     assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 20)) is None
     again = A.autotune(m, reps=2, cache_path=str(tmp_path / "t.json"))
     assert again["source"] == "cache"

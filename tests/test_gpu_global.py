@@ -2,7 +2,7 @@
 
 Covers: the dense 64^3 Bernoulli(0.02) workload at dmax 16 (five seeds); ragged grids that are not
 multiples of the 8^3 brick and span several 16^3-brick interior nodes; every dmax class (the half
-kernels for dmax <= 45 with brick radius R = 1..6, the generic kernels above); empty, full,
+kernels for dmax <= 45 with brick radius R = 1..6, the lower-envelope kernels above); empty, full,
 single-obstacle and corner cases; the dense and the record ingest; every tuning of the work-item
 runs; duplicate and clearing records (last record wins); and the counters of the grid.
 """
@@ -95,10 +95,10 @@ def test_tunings(runs, variant):
     assert first_mismatch(got, ref) is None, first_mismatch(got, ref)
 
 
-@pytest.mark.parametrize("variant", [1, 3, 7])
+@pytest.mark.parametrize("variant", [1, 3, 7, 8])
 @pytest.mark.parametrize("dmax", [2, 12, 20, 28, 36, 44])
 def test_variants_every_radius(variant, dmax):
-    """Brick radius R = 1..6 for both window variants."""
+    """Brick radius R = 1..6 for both window variants and the lower-envelope form (8)."""
     rs = np.random.default_rng(100 + dmax)
     occ = (rs.random((44, 57, 66)) < 0.002).astype(np.uint8)
     ref = O.edt_factorised(occ, dmax)
