@@ -232,6 +232,19 @@ vdbedt_status vdbedt_batch_set_occupancy_dense(vdbedt_batch_handle b, const uint
  * variant 8) the grids are transformed one after the other, and the batch's phase times put the
  * whole transform in z_ms. */
 vdbedt_status vdbedt_batch_global(vdbedt_batch_handle b);
+/* Incremental transform of every grid of the batch (Alg. 1's edits followed by DistanceTransform,
+ * Sec. IV-B, for k maps at once): the records staged on each grid (vdbedt_set_occupancy or
+ * vdbedt_set_occupancy_counted on its handle) are applied, the changed bricks of every grid are
+ * dilated by R bricks and their dirty runs recomputed, each step launched once for all grids, the
+ * runs of every grid in one shared work queue.  Bit-identical to vdbedt_update on each grid.  A grid
+ * without a field yet (no transform since its occupancy was set) makes the call a
+ * vdbedt_batch_global.  In the lower-envelope form the grids are updated one after the other.
+ * Capturable into a CUDA graph after one uncaptured call with the same staging (counted staging on
+ * each grid, so that nothing reallocates): the grids' arguments live in device memory and are
+ * uploaded only when their staging changes, which is EINVAL during a capture.  stats (nullable): an
+ * array of k entries, filled after a stream synchronisation; the run counts (x/y/z_items) are the
+ * shared queue's, the same on every entry. */
+vdbedt_status vdbedt_batch_update(vdbedt_batch_handle b, vdbedt_update_stats* stats);
 /* vdbedt_set_tuning on every grid of the batch. */
 vdbedt_status vdbedt_batch_set_tuning(vdbedt_batch_handle b, const vdbedt_tuning* t);
 /* Report device-side errors of any grid (vdbedt_synchronize on each). */

@@ -16,6 +16,7 @@ over the library's forward and backward kernels).
 """
 from .lib import (  # noqa: F401
     Batch,
+    BatchUpdateGraph,
     GlobalGraph,
     VDBEDT_DMAX_LIMIT,
     Map,

@@ -775,6 +775,8 @@ struct vdbedt_batch {
   bool profiling = false;
   cudaEvent_t ev[6] = {};
   bool ev_recorded = false;
+  UpdArgs* d_upd = nullptr;  // the grids' update arguments in device memory
+  UpdArgs* h_upd = nullptr;  // and their page-locked host copy
 };
 
 namespace {
@@ -796,6 +798,7 @@ void destroy_batch(vdbedt_batch* b) {
   if (b->scr.buf) cudaFree(b->scr.buf);
   for (int i = 0; i < 6; ++i)
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  if (b->h_upd) cudaFreeHost(b->h_upd);
   if (b->own_stream && b->st) cudaStreamDestroy(b->st);
   delete b;
 }
@@ -868,9 +871,118 @@ vdbedt_status batch_global(vdbedt_batch* b) {
   return VDBEDT_OK;
 }
 
+// Incremental update of every grid of a batch: each step (begin, tracked ingest, marking, slot
+// lists, the three passes) is one launch for all grids; the dirty runs of every grid go to the
+// batch's shared work queue, tagged with their grid.
+vdbedt_status batch_update(vdbedt_batch* b, vdbedt_update_stats* stats) {
+  vdbedt_status s = batch_members_ok(b);
+  if (s) return s;
+  DeviceGuard guard(b->device);
+  const GridView& g0 = b->maps[0]->g;
+  bool fresh = true;
+  for (vdbedt_map* m : b->maps) fresh &= m->computed && !m->dense_pending;
+  std::vector<int64_t> nrec((size_t)b->k);
+  std::vector<char> counted((size_t)b->k);
+  for (int i = 0; i < b->k; ++i) {
+    nrec[(size_t)i] = b->maps[(size_t)i]->stage_n;
+    counted[(size_t)i] = b->maps[(size_t)i]->stage_counted;
+  }
+  if (!fresh) {
+    // a grid without a field yet: the global transform of the whole batch (applies the records)
+    s = batch_global(b);
+    if (s) return s;
+  } else if (!half_path(g0)) {
+    // the envelope form: grid by grid
+    for (vdbedt_map* m : b->maps) {
+      s = vdbedt_update(m, nullptr);
+      if (s) return bfail(b, s, m->err);
+    }
+  } else {
+    Tuning t = b->tune;
+    for (int a = 0; a < 3; ++a) t.run[a] = effective_run(g0, b->tune, a);
+    // The grids' arguments in device memory stay fixed while staging does not reallocate (every
+    // grid reads its record count from its device count word), so a captured update replays with
+    // the same arguments; they are uploaded again only when they change, outside a capture.
+    BatchUpdShape shape{b->k, 0, 0, 0, 0};
+    BatchCounts counts{};
+    std::vector<UpdArgs> args((size_t)b->k);
+    for (int i = 0; i < b->k; ++i) {
+      vdbedt_map* m = b->maps[(size_t)i];
+      UpdArgs& a = args[(size_t)i];
+      a.g = m->g;
+      a.rec = m->stage;
+      a.n = m->stage_cap;
+      a.n_dev = m->d_count;
+      a.changed = m->changed;
+      BCK(b, prepare_update_args(m->g, m->vlast, m->miss, a, b->st), "update scratch");
+      counts.c[i] = m->stage_counted ? -1 : (int32_t)m->stage_n;  // -1: the counted staging wrote it
+      shape.max_n = std::max<int64_t>(shape.max_n, m->stage_cap);
+      shape.max_nkeys = std::max<int64_t>(shape.max_nkeys, (int64_t)m->g.NX * m->g.NY * m->g.NZ);
+      shape.max_cap = std::max<int64_t>(shape.max_cap, m->g.cap);
+      shape.max_node_cap = std::max<int64_t>(shape.max_node_cap, m->g.node_cap);
+    }
+    if (memcmp(args.data(), b->h_upd, sizeof(UpdArgs) * (size_t)b->k) != 0) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(b->st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return bfail(b, VDBEDT_EINVAL, "batch update captured before an uncaptured call with the same staging");
+      BCK(b, cudaStreamSynchronize(b->st), "sync");  // earlier updates may still read the old arguments
+      memcpy(b->h_upd, args.data(), sizeof(UpdArgs) * (size_t)b->k);
+      BCK(b, cudaMemcpyAsync(b->d_upd, b->h_upd, sizeof(UpdArgs) * (size_t)b->k, cudaMemcpyHostToDevice, b->st),
+          "update arguments");
+      BCK(b, cudaStreamSynchronize(b->st), "sync");
+    }
+    bmark(b, 0);
+    BCK(b, launch_update_batch_ingest(b->d_upd, shape, counts, b->st), "ingest");
+    for (vdbedt_map* m : b->maps) clear_stage(m);
+    bmark(b, 1);
+    BCK(b, launch_update_batch_mark(b->d_upd, shape, t, b->items, b->st), "mark");
+    bmark(b, 2);
+    BCK(b, launch_item_slots_batch(b->d_views, t, b->items, b->pool.items_ctr, b->pool.item_cap, b->st), "item slots");
+    bmark(b, 3);
+    BCK(b, launch_pass(b->pool, t, 0, b->items, b->st), "x pass");
+    bmark(b, 4);
+    BCK(b, launch_pass(b->pool, t, 1, b->items, b->st), "y pass");
+    BCK(b, launch_pass(b->pool, t, 2, b->items, b->st), "z pass");
+    bmark(b, 5);
+    b->ev_recorded = b->profiling;
+  }
+  if (stats) {
+    for (int i = 0; i < b->k; ++i) {
+      vdbedt_map* m = b->maps[(size_t)i];
+      BCK(b, cudaMemcpyAsync(m->h_pinned, m->g.counters, sizeof(int32_t) * C_NUM, cudaMemcpyDeviceToHost, b->st), "d2h");
+      if (counted[(size_t)i])
+        BCK(b, cudaMemcpyAsync(m->h_pinned + 40, m->d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, b->st), "d2h");
+    }
+    BCK(b, cudaMemcpyAsync(b->maps[0]->h_pinned + 44, b->pool.items_ctr, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost,
+                           b->st), "d2h");
+    BCK(b, cudaStreamSynchronize(b->st), "sync");
+    for (int i = 0; i < b->k; ++i) {
+      vdbedt_map* m = b->maps[(size_t)i];
+      s = device_errors(m);
+      if (s) return bfail(b, s, m->err);
+      const int32_t* c = m->h_pinned;
+      vdbedt_update_stats& o = stats[i];
+      o.records = counted[(size_t)i] ? c[40] : nrec[(size_t)i];
+      o.net_flips = c[C_FLIPS];
+      o.changed_bricks = c[C_CHANGED];
+      // the work queue is shared: its run counts are the batch's, reported on every grid
+      o.x_items = b->maps[0]->h_pinned[44];
+      o.y_items = b->maps[0]->h_pinned[45];
+      o.z_items = b->maps[0]->h_pinned[46];
+      o.new_bricks = c[C_NEW_BRICKS];
+    }
+  }
+  return VDBEDT_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+vdbedt_status vdbedt_batch_update(vdbedt_batch_handle b, vdbedt_update_stats* stats) {
+  if (!b) return bfail(nullptr, VDBEDT_EINVAL, "null batch");
+  return batch_update(b, stats);
+}
 
 vdbedt_status vdbedt_batch_create(const vdbedt_config* cfgs, int32_t k, vdbedt_batch_handle* out) {
   if (!cfgs || !out || k < 1 || k > kBatchMax) return bfail(nullptr, VDBEDT_EINVAL, "need 1 <= k <= VDBEDT_BATCH_MAX configs");
@@ -929,9 +1041,14 @@ vdbedt_status vdbedt_batch_create(const vdbedt_config* cfgs, int32_t k, vdbedt_b
   for (int a = 0; a < 3; ++a) {
     BAL(b->items.run[a], total);
     BAL(b->items.slots[a], total * kItemSlots);
+    BAL(b->items.igrid[a], total);
   }
   BAL(b->d_views, k);
+  BAL(b->d_upd, k);
 #undef BAL
+  e = cudaMallocHost((void**)&b->h_upd, sizeof(UpdArgs) * (size_t)k);
+  if (e != cudaSuccess) return bail(e, "pinned alloc");
+  memset(b->h_upd, 0, sizeof(UpdArgs) * (size_t)k);
   e = cudaMemsetAsync(b->counters, 0, sizeof(int32_t) * (size_t)(k + 1) * C_NUM, b->st);
   if (e != cudaSuccess) return bail(e, "memset");
   int32_t* bctr = b->counters + (size_t)k * C_NUM;

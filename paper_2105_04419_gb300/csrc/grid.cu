@@ -85,6 +85,15 @@ struct BatchSrc {
   const uint8_t* p[kBatchMax];
   __device__ __forceinline__ const uint8_t* get(int grid) const { return p[grid]; }
 };
+// Argument sources of the incremental update's kernels: one grid, or the grid blockIdx.y of a batch.
+struct UpdOne {
+  UpdArgs a;
+  __device__ __forceinline__ UpdArgs get() const { return a; }
+};
+struct UpdBatch {
+  const UpdArgs* a;
+  __device__ __forceinline__ UpdArgs get() const { return a[blockIdx.y]; }
+};
 
 // ---- reset ----
 template <class VS>
@@ -107,9 +116,33 @@ __global__ void k_reset_nodes(VS vs) {
 }
 
 // Start of an incremental update: clear the per-update counters and advance the update epoch
-// (kept on the device, so that a captured update replays with a fresh epoch each time).
-__global__ void k_begin_update(GridView g) {
+// (kept on the device, so that a captured update replays with a fresh epoch each time).  In a batch
+// every grid's block clears the shared run counters (all store 0).
+template <class US>
+__global__ void k_begin_update(US us) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const GridView g = us.get().g;
+    g.items_ctr[0] = 0;
+    g.items_ctr[1] = 0;
+    g.items_ctr[2] = 0;
+    g.counters[C_CHANGED] = 0;
+    g.counters[C_FLIPS] = 0;
+    g.counters[C_NEW_BRICKS] = 0;
+    g.counters[C_UNIQUE] = 0;
+    g.counters[C_HAS_ZERO] = 0;
+    g.counters[C_FRESH] = 0;
+    g.counters[C_DEFERRED] = 0;
+    g.counters[C_EPOCH] += 1;
+  }
+}
+
+// Batched form: the same, plus the record count of grids staged without a device count.
+__global__ void k_begin_batch_update(const UpdArgs* __restrict__ args, BatchCounts counts) {
   if (threadIdx.x == 0) {
+    const int i = (int)blockIdx.y;
+    const UpdArgs a = args[i];
+    if (counts.c[i] >= 0) *const_cast<int32_t*>(a.n_dev) = counts.c[i];
+    const GridView& g = a.g;
     g.items_ctr[0] = 0;
     g.items_ctr[1] = 0;
     g.items_ctr[2] = 0;
@@ -336,7 +369,7 @@ __device__ void insert_new_node(const GridView& g, uint32_t key, int idx) {
 // node insertion in progress: one thread per flagged node key absent from the table; indices come
 // from one atomic per block, and each key (inserted by exactly one thread) claims an empty hash
 // slot with its final word.  Later kernels read the nodes (the kernel boundary orders them).
-__global__ void k_create_flagged_nodes(GridView g, int32_t* __restrict__ nflag, int64_t nkeys) {
+__device__ __forceinline__ void create_flagged_nodes(const GridView& g, int32_t* __restrict__ nflag, int64_t nkeys) {
   GRID_STRIDE(k, nkeys) {
     bool need = false;
     if (k < nkeys && nflag[k]) {
@@ -346,6 +379,10 @@ __global__ void k_create_flagged_nodes(GridView g, int32_t* __restrict__ nflag, 
     const int idx = block_agg_add(&g.counters[C_NNODES], need, nullptr);
     if (need) insert_new_node(g, (uint32_t)k, idx);
   }
+}
+
+__global__ void k_create_flagged_nodes(GridView g, int32_t* __restrict__ nflag, int64_t nkeys) {
+  create_flagged_nodes(g, nflag, nkeys);
 }
 
 // Node flags of the unique brick keys (radix path).
@@ -503,12 +540,14 @@ __device__ __forceinline__ void list_missing_brick(const GridView& g, int node, 
     set_error(g, kErrOverflow);  // more new bricks than the capacity holds
 }
 
-template <bool DEFERRED>
-__global__ void k_rec_missing(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
-                              int32_t* __restrict__ nflag, unsigned long long* __restrict__ list) {
+template <bool DEFERRED, class US>
+__global__ void k_rec_missing(US us) {
+  const UpdArgs A = us.get();
+  const GridView& g = A.g;
   if (DEFERRED && g.counters[C_DEFERRED] == 0) return;
   const int lane = threadIdx.x & 31;
-  const int64_t n = rec_count(n_max, n_dev);
+  const int64_t n = rec_count(A.n, A.n_dev);
+  const rec_t* __restrict__ rec = A.rec;
   GRID_STRIDE(i, n) {
     bool zero = false, bad = false;
     if (i < n) {
@@ -521,9 +560,9 @@ __global__ void k_rec_missing(GridView g, const rec_t* __restrict__ rec, int64_t
         const int node = find_node(g, (uint32_t)nk);
         if (node >= 0) {
           if (g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] < 0)
-            list_missing_brick(g, node, bx, by, bz, list);
-        } else if (!DEFERRED && !nflag[nk]) {
-          nflag[nk] = 1;
+            list_missing_brick(g, node, bx, by, bz, A.list);
+        } else if (!DEFERRED && !A.nflag[nk]) {
+          A.nflag[nk] = 1;
           atomicOr(&g.counters[C_DEFERRED], 1);
         }
       } else {
@@ -537,8 +576,20 @@ __global__ void k_rec_missing(GridView g, const rec_t* __restrict__ rec, int64_t
   }
 }
 
-__global__ void k_alloc_listed(GridView g, const unsigned long long* __restrict__ list, int64_t max) {
-  const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], max);
+// Nodes flagged by the tracked ingest (node keys of "set" records whose node did not exist).
+template <class US>
+__global__ void k_upd_nodes(US us) {
+  const UpdArgs A = us.get();
+  if (A.g.counters[C_DEFERRED] == 0) return;
+  create_flagged_nodes(A.g, A.nflag, (int64_t)A.g.NX * A.g.NY * A.g.NZ);
+}
+
+template <class US>
+__global__ void k_alloc_listed(US us) {
+  const UpdArgs A = us.get();
+  const GridView& g = A.g;
+  const unsigned long long* __restrict__ list = A.list;
+  const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], min(A.n, (int64_t)g.cap));
   GRID_STRIDE(j, cnt) {
     int node = -1, bx = 0, by = 0, bz = 0;
     int* e = nullptr;
@@ -580,8 +631,8 @@ __device__ __forceinline__ int64_t rec_voxel(const GridView& g, rec_t packed) {
   return (int64_t)s * 512 + ((r.x & 7) + 8 * (r.y & 7) + 64 * (r.z & 7));
 }
 
-__global__ void k_rec_last(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev, bool force,
-                           int32_t* __restrict__ vlast) {
+__device__ __forceinline__ void rec_last(const GridView& g, const rec_t* __restrict__ rec, int64_t n_max,
+                                         const int32_t* n_dev, bool force, int32_t* __restrict__ vlast) {
   if (!force && !g.counters[C_HAS_ZERO]) return;
   const int64_t n = rec_count(n_max, n_dev);
   GRID_STRIDE(i, n) {
@@ -593,8 +644,9 @@ __global__ void k_rec_last(GridView g, const rec_t* __restrict__ rec, int64_t n_
 }
 
 // Flips are counted; with `track` the brick is appended once per epoch to the changed list.
-__global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
-                             bool force, bool track, int32_t* __restrict__ vlast, int32_t* __restrict__ changed) {
+__device__ __forceinline__ void apply_last(const GridView& g, const rec_t* __restrict__ rec, int64_t n_max,
+                                           const int32_t* n_dev, bool force, bool track, int32_t* __restrict__ vlast,
+                                           int32_t* __restrict__ changed) {
   if (!force && !g.counters[C_HAS_ZERO]) return;
   const int64_t n = rec_count(n_max, n_dev);
   const int epoch = g.counters[C_EPOCH];
@@ -622,6 +674,29 @@ __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t 
     unsigned m = __ballot_sync(0xffffffffu, flip);
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(&g.counters[C_FLIPS], __popc(m));
   }
+}
+
+__global__ void k_rec_last(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev, bool force,
+                           int32_t* __restrict__ vlast) {
+  rec_last(g, rec, n_max, n_dev, force, vlast);
+}
+
+__global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
+                             bool force, bool track, int32_t* __restrict__ vlast, int32_t* __restrict__ changed) {
+  apply_last(g, rec, n_max, n_dev, force, track, vlast, changed);
+}
+
+// The tracked forms (incremental update): every record, flips tracked.
+template <class US>
+__global__ void k_upd_rec_last(US us) {
+  const UpdArgs A = us.get();
+  rec_last(A.g, A.rec, A.n, A.n_dev, true, A.vlast);
+}
+
+template <class US>
+__global__ void k_upd_apply_last(US us) {
+  const UpdArgs A = us.get();
+  apply_last(A.g, A.rec, A.n, A.n_dev, true, true, A.vlast, A.changed);
 }
 
 // ---- dense ingest ----
@@ -1107,7 +1182,9 @@ __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
 // Incremental form: allocate the marked bricks without storage in the words this update marked
 // first (the fresh list), a warp per listed word and a lane per brick of it, fields at dmax^2; then
 // clear the word's fresh bit.  The work follows the update's dilation, not the size of the map.
-__global__ void __launch_bounds__(256) k_alloc_fresh(GridView g) {
+template <class US>
+__global__ void __launch_bounds__(256) k_alloc_fresh(US us) {
+  const GridView g = us.get().g;
   const int nf = min(g.counters[C_FRESH], g.node_cap * 128);
   const int lane = threadIdx.x & 31;
   const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
@@ -1140,17 +1217,19 @@ __global__ void __launch_bounds__(256) k_alloc_fresh(GridView g) {
 
 // ---- work items ----
 // Queue the run along `axis` that holds brick (bx, by, bz) (runs are aligned to `run` bricks
-// inside the node), once per epoch.
+// inside the node), once per epoch; in a batch, igrid records the run's grid.
 __device__ __forceinline__ void queue_run(const GridView& g, int axis, int bx, int by, int bz, int node, int run,
-                                          int epoch, unsigned long long* items) {
+                                          int epoch, unsigned long long* items, int32_t* igrid, int grid) {
   const int l[3] = {bx & 15, by & 15, bz & 15};
   const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
   const int id = l[a1] + 16 * (l[a2] + 16 * (l[axis] / run));
   if (atomicExch(&g.mark[((size_t)node * 3 + axis) * 1024 + id], epoch) != epoch) {
     const int p = atomicAdd(&g.items_ctr[axis], 1);
     const int back = l[axis] % run;
-    if (p < g.item_cap)
+    if (p < g.item_cap) {
       items[p] = pack_brick(bx - (axis == 0 ? back : 0), by - (axis == 1 ? back : 0), bz - (axis == 2 ? back : 0));
+      if (igrid) igrid[p] = grid;
+    }
   }
 }
 
@@ -1267,52 +1346,72 @@ __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int 
   }
 }
 
-// Slots of each queued run's bricks with R bricks of halo on both sides along the axis.
-__global__ void k_item_slots(GridView g, int rx, int ry, int rz, Items it) {
-  // blockIdx.y = axis; a warp per queued run, a lane per slot: a run lies inside one node and its
-  // halo (R <= 6 < 16 bricks) reaches at most the neighbouring node on each side along the axis,
-  // so three node lookups (lanes 0-2) serve the whole slot list, read from the child tables
-  const int axis = (int)blockIdx.y;
-  const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
-  const unsigned long long* __restrict__ items = it.run[axis];
-  int32_t* __restrict__ out = it.slots[axis];
-  const int n = min(g.items_ctr[axis], g.item_cap);
+// Slots of each queued run's bricks with R bricks of halo on both sides along the axis: a warp per
+// queued run, a lane per slot.  A run lies inside one node and its halo (R <= 6 < 16 bricks)
+// reaches at most the neighbouring node on each side along the axis, so three node lookups (lanes
+// 0-2) serve the whole slot list, read from the child tables.
+__device__ __forceinline__ void run_slots(const GridView& g, int axis, int run, unsigned long long packed,
+                                          int32_t* __restrict__ dst) {
   const int nb = run + 2 * g.R;
   const int lane = threadIdx.x & 31;
+  int bx, by, bz;
+  unpack_brick(packed, bx, by, bz);
+  const int ba = axis == 0 ? bx : (axis == 1 ? by : bz);
+  const int Ba = axis == 0 ? g.BX : (axis == 1 ? g.BY : g.BZ);
+  const int NQa = axis == 0 ? g.NX : (axis == 1 ? g.NY : g.NZ);
+  int nq = -1;
+  if (lane < 3) {
+    const int qa = (ba >> 4) + lane - 1;
+    if (qa >= 0 && qa < NQa) {
+      const int qx = axis == 0 ? qa : bx >> 4, qy = axis == 1 ? qa : by >> 4, qz = axis == 2 ? qa : bz >> 4;
+      nq = find_node(g, (uint32_t)(qx + g.NX * (qy + g.NY * qz)));
+    }
+  }
+  const int n_lo = __shfl_sync(0xffffffffu, nq, 0), n_mid = __shfl_sync(0xffffffffu, nq, 1),
+            n_hi = __shfl_sync(0xffffffffu, nq, 2);
+  int s = -1;
+  const int ca = ba + lane - g.R;  // this slot's brick coordinate along the axis
+  if (lane < nb && ca >= 0 && ca < Ba) {
+    const int node = (ca >> 4) < (ba >> 4) ? n_lo : ((ca >> 4) > (ba >> 4) ? n_hi : n_mid);
+    if (node >= 0) {
+      const int cx = axis == 0 ? ca : bx, cy = axis == 1 ? ca : by, cz = axis == 2 ? ca : bz;
+      s = g.child[(size_t)node * kNodeBricks + local_brick(cx, cy, cz)];
+      if (s >= 0) s += g.slot_base;
+    }
+  }
+  dst[lane] = s;
+}
+
+// blockIdx.y = axis
+__global__ void k_item_slots(GridView g, int rx, int ry, int rz, Items it) {
+  const int axis = (int)blockIdx.y;
+  const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
+  const int n = min(g.items_ctr[axis], g.item_cap);
+  const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
+  for (int item = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); item < n; item += nw)
+    run_slots(g, axis, run, it.run[axis][item], it.slots[axis] + (size_t)item * kItemSlots);
+}
+
+// The same for a batch's shared queue: each run's grid comes from it.igrid.
+__global__ void k_item_slots_batch(const GridView* __restrict__ views, const int32_t* __restrict__ items_ctr,
+                                   int item_cap, int rx, int ry, int rz, Items it) {
+  const int axis = (int)blockIdx.y;
+  const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
+  const int n = min(items_ctr[axis], item_cap);
   const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
   for (int item = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); item < n; item += nw) {
-    int bx, by, bz;
-    unpack_brick(items[item], bx, by, bz);
-    const int ba = axis == 0 ? bx : (axis == 1 ? by : bz);
-    const int Ba = axis == 0 ? g.BX : (axis == 1 ? g.BY : g.BZ);
-    const int NQa = axis == 0 ? g.NX : (axis == 1 ? g.NY : g.NZ);
-    int nq = -1;
-    if (lane < 3) {
-      const int qa = (ba >> 4) + lane - 1;
-      if (qa >= 0 && qa < NQa) {
-        const int qx = axis == 0 ? qa : bx >> 4, qy = axis == 1 ? qa : by >> 4, qz = axis == 2 ? qa : bz >> 4;
-        nq = find_node(g, (uint32_t)(qx + g.NX * (qy + g.NY * qz)));
-      }
-    }
-    const int n_lo = __shfl_sync(0xffffffffu, nq, 0), n_mid = __shfl_sync(0xffffffffu, nq, 1),
-              n_hi = __shfl_sync(0xffffffffu, nq, 2);
-    int s = -1;
-    const int ca = ba + lane - g.R;  // this slot's brick coordinate along the axis
-    if (lane < nb && ca >= 0 && ca < Ba) {
-      const int node = (ca >> 4) < (ba >> 4) ? n_lo : ((ca >> 4) > (ba >> 4) ? n_hi : n_mid);
-      if (node >= 0) {
-        const int cx = axis == 0 ? ca : bx, cy = axis == 1 ? ca : by, cz = axis == 2 ? ca : bz;
-        s = g.child[(size_t)node * kNodeBricks + local_brick(cx, cy, cz)];
-        if (s >= 0) s += g.slot_base;
-      }
-    }
-    out[(size_t)item * kItemSlots + lane] = s;
+    const GridView g = views[it.igrid[axis][item]];
+    run_slots(g, axis, run, it.run[axis][item], it.slots[axis] + (size_t)item * kItemSlots);
   }
 }
 
 // ---- incremental ----
 // For every changed brick: refresh its obstacle flag; if it holds obstacles, mark its dilation.
-__global__ void k_changed_flags_dilate(GridView g, const int32_t* __restrict__ changed) {
+template <class US>
+__global__ void k_changed_flags_dilate(US us) {
+  const UpdArgs A = us.get();
+  const GridView& g = A.g;
+  const int32_t* __restrict__ changed = A.changed;
   const int nc = min(g.counters[C_CHANGED], g.cap);
   const int side = 2 * g.R + 1, rows = side * side;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nc * rows;
@@ -1332,7 +1431,12 @@ __global__ void k_changed_flags_dilate(GridView g, const int32_t* __restrict__ c
 
 // Dirty sets of an update: every stored brick within R (Chebyshev) of a changed brick needs its z
 // pass; those in the changed brick's z layer also need the in-plane pass.
-__global__ void k_mark_dirty(GridView g, const int32_t* __restrict__ changed, int rx, int ry, int rz, Items it) {
+template <class US>
+__global__ void k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
+  const UpdArgs A = us.get();
+  const GridView& g = A.g;
+  const int32_t* __restrict__ changed = A.changed;
+  const int grid = (int)blockIdx.y;
   const int nc = min(g.counters[C_CHANGED], g.cap);
   const int epoch = g.counters[C_EPOCH];
   const int side = 2 * g.R + 1, vol = side * side * side;
@@ -1349,10 +1453,39 @@ __global__ void k_mark_dirty(GridView g, const int32_t* __restrict__ changed, in
     if (slot < 0) continue;
     // x-lines change only within R bricks along x of a changed brick, in-plane values within R in
     // x and y, D within R in all three
-    if (dy == 0 && dz == 0) queue_run(g, 0, bx, by, bz, node, rx, epoch, it.run[0]);
-    if (dz == 0) queue_run(g, 1, bx, by, bz, node, ry, epoch, it.run[1]);
-    queue_run(g, 2, bx, by, bz, node, rz, epoch, it.run[2]);
+    if (dy == 0 && dz == 0) queue_run(g, 0, bx, by, bz, node, rx, epoch, it.run[0], it.igrid[0], grid);
+    if (dz == 0) queue_run(g, 1, bx, by, bz, node, ry, epoch, it.run[1], it.igrid[1], grid);
+    queue_run(g, 2, bx, by, bz, node, rz, epoch, it.run[2], it.igrid[2], grid);
   }
+}
+
+// The incremental update's kernels for one grid or all grids of a batch (k = gridDim.y).
+template <class US>
+cudaError_t update_ingest_kernels(US us, int k, int64_t n, int64_t nkeys, int64_t cap, cudaStream_t st) {
+  const int div = k > 1 ? k : 1;
+  auto bx = [&](int64_t work, int hi) {
+    int64_t b = (work + kT - 1) / kT;
+    const int64_t lim = k > 1 ? (hi / div > 16 ? hi / div : 16) : hi;
+    return (unsigned)(b < 1 ? 1 : (b > lim ? lim : b));
+  };
+  const dim3 gr(bx(n, 152 * 16), k), gk(bx(nkeys, 152 * 16), k), gl(bx(n < cap ? n : cap, 152 * 16), k);
+  VDB_LAUNCH((k_rec_missing<false, US>), gr, kT, 0, st, us);
+  VDB_LAUNCH(k_upd_nodes<US>, gk, kT, 0, st, us);
+  VDB_LAUNCH((k_rec_missing<true, US>), gr, kT, 0, st, us);
+  VDB_LAUNCH(k_alloc_listed<US>, gl, kT, 0, st, us);
+  VDB_LAUNCH(k_upd_rec_last<US>, gr, kT, 0, st, us);
+  VDB_LAUNCH(k_upd_apply_last<US>, gr, kT, 0, st, us);
+  return cudaGetLastError();
+}
+
+template <class US>
+cudaError_t update_mark_kernels(US us, int k, int node_cap, const Tuning& t, const Items& it, cudaStream_t st) {
+  const unsigned div = k > 1 ? (unsigned)k : 1u;
+  auto share = [&](unsigned single) { return k > 1 ? (single / div > 16 ? single / div : 16u) : single; };
+  VDB_LAUNCH(k_changed_flags_dilate<US>, dim3(share(1024), k), kT, 0, st, us);
+  VDB_LAUNCH(k_alloc_fresh<US>, dim3(share(node_cap < 256 ? (unsigned)node_cap : 256u), k), kT, 0, st, us);
+  VDB_LAUNCH(k_mark_dirty<US>, dim3(share(2048), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -1431,30 +1564,36 @@ cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& 
 }
 
 cudaError_t launch_begin_update(const GridView& g, cudaStream_t st) {
-  VDB_LAUNCH(k_begin_update, 1, 32, 0, st, g);
+  UpdArgs a{};
+  a.g = g;
+  VDB_LAUNCH(k_begin_update<UpdOne>, 1, 32, 0, st, UpdOne{a});
   return cudaGetLastError();
 }
 
-static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev,
-                                         int32_t* changed, Scratch& vl, Scratch& miss, cudaStream_t st) {
+cudaError_t prepare_update_args(const GridView& g, Scratch& vl, Scratch& miss, UpdArgs& a, cudaStream_t st) {
   cudaError_t e = ensure_tracked(g, miss, st);
   if (e != cudaSuccess) return e;
   e = ensure_vlast(g, vl, st);
   if (e != cudaSuccess) return e;
   const size_t nkeys = (size_t)g.NX * g.NY * g.NZ;
   char* p = (char*)miss.buf;
-  int32_t* nflag = (int32_t*)p;
-  unsigned long long* list = (unsigned long long*)(p + align_up(nkeys * 4));
-  int32_t* vlast = (int32_t*)vl.buf;
-  const unsigned nbk = blocks_for(n);
-  const int64_t nlist = n < (int64_t)g.cap ? n : (int64_t)g.cap;
-  VDB_LAUNCH(k_rec_missing<false>, nbk, kT, 0, st, g, rec, n, n_dev, nflag, list);
-  VDB_LAUNCH(k_create_flagged_nodes, blocks_for((int64_t)nkeys), kT, 0, st, g, nflag, (int64_t)nkeys);
-  VDB_LAUNCH(k_rec_missing<true>, nbk, kT, 0, st, g, rec, n, n_dev, nflag, list);
-  VDB_LAUNCH(k_alloc_listed, blocks_for(nlist), kT, 0, st, g, list, nlist);
-  VDB_LAUNCH(k_rec_last, nbk, kT, 0, st, g, rec, n, n_dev, true, vlast);
-  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, n, n_dev, true, true, vlast, changed);
-  return cudaGetLastError();
+  a.nflag = (int32_t*)p;
+  a.list = (unsigned long long*)(p + align_up(nkeys * 4));
+  a.vlast = (int32_t*)vl.buf;
+  return cudaSuccess;
+}
+
+static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev,
+                                         int32_t* changed, Scratch& vl, Scratch& miss, cudaStream_t st) {
+  UpdArgs a{};
+  a.g = g;
+  a.rec = rec;
+  a.n = n;
+  a.n_dev = n_dev;
+  a.changed = changed;
+  cudaError_t e = prepare_update_args(g, vl, miss, a, st);
+  if (e != cudaSuccess) return e;
+  return update_ingest_kernels(UpdOne{a}, 1, n, (int64_t)g.NX * g.NY * g.NZ, g.cap, st);
 }
 
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
@@ -1589,6 +1728,13 @@ cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& i
   return cudaGetLastError();
 }
 
+cudaError_t launch_item_slots_batch(const GridView* views, const Tuning& t, const Items& it, int32_t* items_ctr,
+                                    int item_cap, cudaStream_t st) {
+  VDB_LAUNCH(k_item_slots_batch, dim3(1024, 3), kT, 0, st, views, items_ctr, item_cap, t.run[0], t.run[1], t.run[2],
+             it);
+  return cudaGetLastError();
+}
+
 // ---- batches ----
 static int clamp_blocks(int64_t n, int hi) { return (int)(n < 1 ? 1 : (n > hi ? hi : n)); }
 
@@ -1671,10 +1817,26 @@ cudaError_t launch_build_items_batch(const GridView* views, const BatchShape& b,
 // (the item counters were cleared when the update began)
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const int32_t* changed, const Items& it,
                                     cudaStream_t st) {
-  VDB_LAUNCH(k_changed_flags_dilate, 1024, kT, 0, st, g, changed);
-  VDB_LAUNCH(k_alloc_fresh, g.node_cap < 256 ? g.node_cap : 256, kT, 0, st, g);
-  VDB_LAUNCH(k_mark_dirty, 2048, kT, 0, st, g, changed, t.run[0], t.run[1], t.run[2], it);
-  return cudaGetLastError();
+  UpdArgs a{};
+  a.g = g;
+  a.changed = const_cast<int32_t*>(changed);
+  return update_mark_kernels(UpdOne{a}, 1, g.node_cap, t, it, st);
+}
+
+// Batched update: begin + tracked ingest of every grid, then the marking (one launch per step).
+cudaError_t launch_update_batch_ingest(const UpdArgs* d_args, const BatchUpdShape& s, const BatchCounts& counts,
+                                       cudaStream_t st) {
+  if (s.k <= 0) return cudaSuccess;
+  VDB_LAUNCH(k_begin_batch_update, dim3(1, s.k), 32, 0, st, d_args, counts);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return update_ingest_kernels(UpdBatch{d_args}, s.k, s.max_n, s.max_nkeys, s.max_cap, st);
+}
+
+cudaError_t launch_update_batch_mark(const UpdArgs* d_args, const BatchUpdShape& s, const Tuning& t, const Items& it,
+                                     cudaStream_t st) {
+  if (s.k <= 0) return cudaSuccess;
+  return update_mark_kernels(UpdBatch{d_args}, s.k, (int)s.max_node_cap, t, it, st);
 }
 
 }  // namespace vdbedt

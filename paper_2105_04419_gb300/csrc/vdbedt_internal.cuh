@@ -244,6 +244,7 @@ struct Tuning {
 struct Items {
   unsigned long long* run[3];  // packed brick coordinates of the first brick of each run
   int32_t* slots[3];           // [cap * kItemSlots]
+  int32_t* igrid[3];           // batches: the grid of each queued run (null for a single grid)
 };
 
 // primitives (prims.cu)
@@ -274,6 +275,20 @@ struct Scratch {
   void* buf = nullptr;
   size_t bytes = 0;
 };
+
+// Per-grid arguments of the incremental update's kernels: the same kernels serve one grid (the
+// arguments are a kernel parameter) or every grid of a batch at once (an array in device memory;
+// blockIdx.y picks the grid, blockIdx.x strides over that grid's work).
+struct UpdArgs {
+  GridView g;
+  const rec_t* rec;          // staged records
+  int64_t n;                 // staged records (upper bound when counted)
+  const int32_t* n_dev;      // device-side count (counted staging) or null
+  int32_t* changed;          // bricks holding a flipped voxel (cap entries)
+  int32_t* vlast;            // per-voxel last-record table (cap * 512 words, all -1 between ingests)
+  int32_t* nflag;            // node-key flags of the tracked ingest (zero between updates)
+  unsigned long long* list;  // bricks the tracked ingest allocates (cap entries)
+};
 cudaError_t ensure_scratch(Scratch& s, size_t bytes);
 
 cudaError_t launch_reset(const GridView& g, cudaStream_t st);
@@ -296,6 +311,28 @@ cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, const It
                                     cudaStream_t st);
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const int32_t* changed, const Items& it,
                                     cudaStream_t st);
+// The tracked scratch of one grid (node-key flags, missing-brick list) and its last-record table,
+// allocated on first use; fills a's vlast / nflag / list.
+cudaError_t prepare_update_args(const GridView& g, Scratch& vl, Scratch& miss, UpdArgs& a, cudaStream_t st);
+// Batched incremental update of k grids (d_args: their arguments in device memory): the same
+// kernels as one grid's update, each launched once for all grids.  max_*: the largest staged
+// count, node-key count, brick and node capacity over the grids (launch shapes).
+struct BatchUpdShape {
+  int k;
+  int64_t max_n, max_nkeys, max_cap, max_node_cap;
+};
+// record counts of the grids staged without a device count (-1: the grid's count word is already
+// written), passed by value to the first kernel
+struct BatchCounts {
+  int32_t c[kBatchMax];
+};
+cudaError_t launch_update_batch_ingest(const UpdArgs* d_args, const BatchUpdShape& s, const BatchCounts& counts,
+                                       cudaStream_t st);
+cudaError_t launch_update_batch_mark(const UpdArgs* d_args, const BatchUpdShape& s, const Tuning& t, const Items& it,
+                                     cudaStream_t st);
+// slot lists of every queued run of a batch (each run's grid from it.igrid)
+cudaError_t launch_item_slots_batch(const GridView* views, const Tuning& t, const Items& it, int32_t* items_ctr,
+                                    int item_cap, cudaStream_t st);
 // slot lists of every queued run (half path)
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st);
 

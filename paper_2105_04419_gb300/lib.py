@@ -74,6 +74,7 @@ SIGNATURES = {
     "vdbedt_batch_map": (ctypes.c_int, [_H, _I32, ctypes.POINTER(ctypes.c_void_p)]),
     "vdbedt_batch_set_occupancy_dense": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
     "vdbedt_batch_global": (ctypes.c_int, [_H]),
+    "vdbedt_batch_update": (ctypes.c_int, [_H, ctypes.POINTER(UpdateStats)]),
     "vdbedt_batch_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(Tuning)]),
     "vdbedt_batch_synchronize": (ctypes.c_int, [_H]),
     "vdbedt_batch_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
@@ -421,6 +422,66 @@ class UpdateGraph(_CapturedStep):
         _check(lib.vdbedt_update(h, None), "vdbedt_update", h)
 
 
+class BatchUpdateGraph:
+    """One incremental update of every grid of a Batch -- counted staging of up to max_records
+    device records per grid, then vdbedt_batch_update -- captured once into a CUDA graph.
+    run(frames) takes one (xyz [n, 3] int32, occ [n] uint8) pair per grid (CUDA tensors or numpy),
+    writes them into the graph's fixed input buffers and replays the graph on the batch's stream;
+    the result equals set_occupancy on each grid + Batch.update() bit for bit."""
+
+    def __init__(self, batch: "Batch", max_records: int):
+        torch = _torch()
+        self.b = batch
+        self.max_records = int(max_records)
+        k = len(batch.maps)
+        dev = f"cuda:{batch.device}"
+        self.xyz = torch.zeros((k, self.max_records, 3), dtype=torch.int32, device=dev)
+        self.occ = torch.zeros((k, self.max_records), dtype=torch.uint8, device=dev)
+        self.count = torch.zeros(k, dtype=torch.int32, device=dev)
+        m0 = batch.maps[0]
+        m0._enter()
+        with torch.cuda.stream(batch.stream):
+            # one uncaptured run with empty frames: reserves every grid's stage and scratch and
+            # uploads the grids' update arguments
+            self._body()
+            batch.stream.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=batch.stream):
+                self._body()
+        batch.synchronize()
+
+    def _body(self):
+        lib = load()
+        for i, m in enumerate(self.b.maps):
+            _check(lib.vdbedt_set_occupancy_counted(m._h, self.xyz[i].data_ptr(), self.occ[i].data_ptr(),
+                                                    self.count[i:i + 1].data_ptr(), self.max_records),
+                   "vdbedt_set_occupancy_counted", m._h)
+        self.b._chk(lib.vdbedt_batch_update(self.b._b, None), "vdbedt_batch_update")
+
+    def run(self, frames):
+        torch = _torch()
+        if len(frames) != len(self.b.maps):
+            raise ValueError("one (xyz, occ) pair per grid")
+        counts = []
+        m0 = self.b.maps[0]
+        m0._enter()
+        with torch.cuda.stream(self.b.stream):
+            for i, (xyz, occ) in enumerate(frames):
+                n = int(occ.shape[0])
+                if n > self.max_records:
+                    raise ValueError(f"{n} records exceed the captured maximum {self.max_records}")
+                if isinstance(xyz, np.ndarray):
+                    xyz = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3))
+                    occ = torch.from_numpy(np.ascontiguousarray(occ, dtype=np.uint8).reshape(-1))
+                if n:
+                    self.xyz[i, :n].copy_(xyz.view(-1, 3), non_blocking=True)
+                    self.occ[i, :n].copy_(occ.view(-1), non_blocking=True)
+                counts.append(n)
+            self.count.copy_(torch.tensor(counts, dtype=torch.int32), non_blocking=True)
+            self.graph.replay()
+        m0._leave()
+
+
 NOALLOC_MAX_VOXELS = 1 << 21
 
 
@@ -526,6 +587,16 @@ class Batch:
 
     def global_(self):
         self._chk(load().vdbedt_batch_global(self._b), "vdbedt_batch_global")
+
+    def update(self, stats: bool = False):
+        """vdbedt_batch_update: every grid applies its staged records incrementally, each step
+        launched once for the whole batch; with stats, one dict per grid."""
+        k = len(self.maps)
+        st = (UpdateStats * k)() if stats else None
+        self._chk(load().vdbedt_batch_update(self._b, st), "vdbedt_batch_update")
+        if st is not None:
+            return [{f: getattr(st[i], f) for f, _ in UpdateStats._fields_} for i in range(k)]
+        return None
 
     def set_tuning(self, x_run: int = 0, y_run: int = 0, z_run: int = 0, variant: int = 0):
         t = Tuning(x_run, y_run, z_run, variant)
