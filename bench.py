@@ -64,9 +64,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=300, help="lidar frames of the incremental measurement")
     ap.add_argument("--incr-run", type=int, default=4, choices=(4, 8, 16),
                     help="bricks per work item of the incremental maps (default: the library's 4)")
-    ap.add_argument("--alg1-frames", type=int, default=0,
-                    help="also time the paper's Alg. 1 (the oracle's single-threaded transcription) on the "
-                         "first K lidar frames (tens of seconds per frame, about 7 GB of host memory)")
+    ap.add_argument("--alg1-frames", type=int, default=1,
+                    help="time the paper's Alg. 1 (the oracle's single-threaded transcription) on the first K "
+                         "lidar frames (about 20 s for the first frame and 7 GB of host memory; 0: skip)")
     ap.add_argument("--variant", type=int, default=0, help="pass variant (0 automatic; see vdbedt_set_tuning)")
     ap.add_argument("--x-run", type=int, default=0)
     ap.add_argument("--y-run", type=int, default=0)
@@ -211,6 +211,7 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
     seq = W.LidarSequence(truth, wl["seed"], lines[0], nframes=nframes)
     frames = [seq.next() for _ in range(nframes)]
     alg1 = alg1_frames(truth, frames, dmax, alg1_k) if alg1_k > 0 else None
+    hits = [int(v.sum()) for _, v in frames]  # "set" records: one per ray that meets a wall in range
     final_occ = seq.map
     counts = [len(v) for _, v in frames]
     offs = np.concatenate([[0], np.cumsum(counts)])
@@ -294,9 +295,18 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
     peak, peak_src = peaks()
     fbytes = [21 * 512 * s["z_items"] * INCR_RUN + 16 * s["records"] for s in stats]
     fgbs = [b / (t * 1e-3) / 1e9 for b, t in zip(fbytes, graph_ms)]
+    # the same frames on the bricks each pass actually recomputed (stored bricks of the dirty runs),
+    # at the stored widths (x: mask in + g1 out; y: g1 + g2; z: g2 + int32 D) and under the 21 B model
+    sbytes = [1088 * s["x_bricks"] + 2048 * s["y_bricks"] + 3072 * s["z_bricks"] + 16 * s["records"] for s in stats]
+    mbytes = [21 * 512 * s["z_bricks"] + 16 * s["records"] for s in stats]
+    sgbs = [b / (t * 1e-3) / 1e9 for b, t in zip(sbytes, graph_ms)]
+    mgbs = [b / (t * 1e-3) / 1e9 for b, t in zip(mbytes, graph_ms)]
     return {"frames": nframes, "workload": "lidar sequence along tunnel 0 of the scene, 64 beams x 1024 azimuths, "
                                            "range 400 voxels, 1 % noise; map starts empty",
             "records_per_frame": dist_summary([s["records"] for s in stats]),
+            "set_records_per_frame": dist_summary(hits),
+            "records_note": "set records are the rays' wall hits within range (at most 64 x 1024 per frame); the "
+                            "other records clear the map-occupied voxels the rays traverse",
             "net_flips_per_frame": dist_summary([s["net_flips"] for s in stats]),
             "changed_bricks_per_frame": dist_summary([s["changed_bricks"] for s in stats]),
             "z_runs_per_frame": dist_summary([s["z_items"] for s in stats]),
@@ -305,12 +315,20 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
                                 "bytes_per_frame": dist_summary(fbytes), "achieved_median": statistics.median(fgbs),
                                 "unit": "GB/s", "peak": peak, "peak_source": peak_src,
                                 "frac_median": statistics.median(fgbs) / peak},
+            "roofline_frames_recomputed": {
+                "model": "bricks each pass recomputed (stored bricks of its dirty runs) at stored widths: "
+                         "1,088 B x, 2,048 B y, 3,072 B z per brick + 16 B per record",
+                "bytes_per_frame": dist_summary(sbytes), "achieved_median": statistics.median(sgbs),
+                "frac_median": statistics.median(sgbs) / peak, "unit": "GB/s", "peak": peak, "peak_source": peak_src,
+                "model_21B": {"bytes_per_frame": dist_summary(mbytes), "achieved_median": statistics.median(mgbs),
+                              "frac_median": statistics.median(mgbs) / peak},
+                "bricks_per_frame": {a: dist_summary([s[a + "_bricks"] for s in stats]) for a in "xyz"}},
             "eager_phase_ms_median": phase_med,
             "eager_launches_per_frame": eager_launches,
             "global_ms_final_occupancy": glob, "global_over_graph_median": glob / g["median"],
             "final_map": {"occupied_voxels": int(final_occ.sum()), "allocated_bricks": info_final["allocated_bricks"]},
             "graph_equals_eager": same, "l2": "flushed before every frame (untimed)",
-            **({"cpu_alg1": alg1} if alg1 else {})}
+            **({"cpu_alg1": alg1} if alg1 else {})}, frames
 
 
 def bench_clearance(V, torch, m, occ, stream, reps=20):
@@ -417,10 +435,12 @@ def bench_batched(V, torch, stream, flush, autotuned=True, steps=5, warmup=3):
         same &= bool(torch.equal(a, c))
         active += b.maps[i].info()["finite_bricks"] * 512
         del a, c
+    upd = bench_batched_update(V, torch, b, singles, stream, flush, dims)
     for m in singles:
         m.close()
     b.close()
     return {"maps": k, "dmax": dmax, "seed": seed, "domain_voxels": voxels, "active_voxels": active,
+            "update": upd,
             "sides": {"min": min(d[0] for d in dims), "max": max(d[0] for d in dims)},
             "step": "dense occupancy from device grids + global transform of every map",
             "batch_ms": batch_ms, "batch_mvoxels_per_s": active / (batch_ms / 1e3) / 1e6,
@@ -431,6 +451,68 @@ def bench_batched(V, torch, stream, flush, autotuned=True, steps=5, warmup=3):
                                 "x": phases["x_ms"], "y_and_z": phases["z_ms"]},
             "batch_equals_single_handles": same, "l2": "flushed between timed steps (untimed)",
             "tuning": {k: v for k, v in tuning.items() if k != "key"}}
+
+
+def bench_batched_update(V, torch, b, singles, stream, flush, dims, records=2000, frames=8, warm=3, seed=13):
+    """Incremental frames on the 96 maps: each map gets `records` random records per frame (2/3 set,
+    1/3 clear, uniform in its grid).  The batch's update (each step one launch for all maps) replayed
+    from one CUDA graph, against the 96 single handles' updates each replayed from its own graph;
+    same records, same starting fields; event-timed per frame, L2 flushed before each."""
+    k = len(dims)
+    rs = np.random.default_rng(seed)
+    fr = []
+    for f in range(frames):
+        per = []
+        for nx, ny, nz in dims:
+            xyz = np.stack([rs.integers(0, nx, records), rs.integers(0, ny, records), rs.integers(0, nz, records)],
+                           1).astype(np.int32)
+            val = (rs.random(records) < 2.0 / 3.0).astype(np.uint8)
+            per.append((torch.from_numpy(xyz).cuda(), torch.from_numpy(val).cuda()))
+        fr.append(per)
+    bg = V.BatchUpdateGraph(b, records)
+    sg = [V.UpdateGraph(m, records) for m in singles]
+
+    def fill_batch(f):
+        for i, (xyz, val) in enumerate(fr[f]):
+            bg.xyz[i].copy_(xyz)
+            bg.occ[i].copy_(val)
+        bg.count.fill_(records)
+
+    def fill_singles(f):
+        for g, (xyz, val) in zip(sg, fr[f]):
+            g.xyz.copy_(xyz)
+            g.occ.copy_(val)
+            g.count.fill_(records)
+
+    def timed(fill, run):
+        ms = []
+        for f in range(frames):
+            fill(f)
+            flush.fill_(f & 255)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run()
+            e.record(stream)
+            torch.cuda.synchronize()
+            if f >= warm:
+                ms.append(a.elapsed_time(e))
+        return statistics.median(ms)
+
+    batch_ms = timed(fill_batch, bg.replay)
+
+    def run_singles():
+        for g in sg:
+            g.replay()
+
+    single_ms = timed(fill_singles, run_singles)
+    same = all(bool(torch.equal(b.maps[i].export_dense(on_device=True), singles[i].export_dense(on_device=True)))
+               for i in range(k))
+    del bg, sg
+    return {"frames_timed": frames - warm, "records_per_map_per_frame": records,
+            "records": "uniform in each map, 2/3 set, 1/3 clear",
+            "batch_graph_ms_per_frame": batch_ms, "single_graphs_ms_per_frame": single_ms,
+            "single_over_batch": single_ms / batch_ms, "batch_equals_single_handles": same,
+            "step": "one frame of incremental updates on every map (graph replays; records already on the device)"}
 
 
 def bench_nearest(V, torch, m, dims, stream, reps=20):
@@ -456,6 +538,22 @@ def bench_nearest(V, torch, m, dims, stream, reps=20):
             "rule": "nearest occupied voxel, ties to the smallest (z, y, x); voxels uniform in the grid"}
 
 
+def host_cpu():
+    """The host's cores: os.sched_getaffinity and lscpu."""
+    info = {"affinity_cores": len(os.sched_getaffinity(0))}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            key, _, v = ln.partition(":")
+            key = key.strip()
+            if key in ("Architecture", "CPU(s)", "Model name", "Thread(s) per core", "Core(s) per socket",
+                       "Socket(s)", "CPU max MHz"):
+                info[key] = v.strip()
+    except Exception:
+        info["lscpu"] = "unavailable"
+    return info
+
+
 def cpu_baseline(occ, dmax, budget_s=12.0):
     """The CPU oracle (Eq. 1 factorised, OpenMP on all host cores) on a z-slab of the workload."""
     import oracle as O
@@ -476,6 +574,50 @@ def cpu_baseline(occ, dmax, budget_s=12.0):
     return {"value": active / dt / 1e6, "unit": "Mvoxels/s", "cores": cores, "kind": "oracle",
             "sample": f"Eq. 1 factorised (OpenMP) on the first {planes} z-planes ({nx}x{ny}x{planes}) of the "
                       f"workload; {active} active voxels in {dt:.2f} s"}
+
+
+def cpu_baselines_other(frames_first, truth, dmax3, budget4_voxels=300_000_000):
+    """The oracle on the other workloads, timed on the host cores: Eq. 1 factorised (OpenMP) on the
+    dense 64^3 cube (median of 5) and on the first maps of the 96-map batch (about 3e8 voxels); the
+    paper's Alg. 1 (one thread, as the paper runs it) global on the 64^3 cube and on the first lidar
+    frame from an empty map."""
+    import oracle as O
+    import workloads as W
+    out = {"o1": {}, "o2_alg1": {}}
+    occ1 = W.bernoulli_grid(0, (64, 64, 64), 0.02)
+    ts = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        D1 = O.edt_factorised(occ1, 16)
+        ts.append(time.perf_counter() - t0)
+    a1 = active_voxels_of(D1, 16)
+    out["o1"]["cube64_dmax16"] = {"ms": 1e3 * statistics.median(ts), "mvoxels_per_s": a1 / statistics.median(ts) / 1e6,
+                                  "active_voxels": a1, "threads": O.num_threads()}
+    voxels, act, dt, maps = 0, 0, 0.0, 0
+    while voxels < budget4_voxels and maps < 96:
+        g = W.batched_map(7, maps)
+        t0 = time.perf_counter()
+        D = O.edt_factorised(g, 24)
+        dt += time.perf_counter() - t0
+        act += active_voxels_of(D, 24)
+        voxels += g.size
+        maps += 1
+        del D, g
+    out["o1"]["batch96_dmax24_first_maps"] = {"maps": maps, "domain_voxels": voxels, "active_voxels": act,
+                                              "s": dt, "mvoxels_per_s": act / dt / 1e6, "threads": O.num_threads()}
+    a = O.Alg1(occ1.shape, 16)
+    try:
+        t0 = time.perf_counter()
+        a.global_(occ1)
+        ms = 1e3 * (time.perf_counter() - t0)
+        exact = bool(np.array_equal(a.dist(), D1))
+        out["o2_alg1"]["cube64_dmax16_global"] = dict(ms=ms, mvoxels_per_s=a1 / (ms / 1e3) / 1e6, threads=1,
+                                                      equals_eq1=exact, **a.counters())
+    finally:
+        a.close()
+    if frames_first:
+        out["o2_alg1"]["lidar_first_frames_dmax32"] = alg1_frames(truth, frames_first, dmax3, len(frames_first))
+    return out
 
 
 def active_voxels_of(D, dmax):
@@ -666,37 +808,60 @@ def main():
                              "step": "the same step captured once into a CUDA graph and replayed"}}
 
     if not args.no_e2e:
-        # end to end through the C ABI with host buffers (pinned): host records -> device,
-        # transform, and the grid's counters (including the active-brick count, reduced on the
-        # device) back to the host
-        xyz_h = torch.from_numpy(xyz_h).pin_memory().numpy()
-        ones_h = torch.from_numpy(ones_h).pin_memory().numpy()
-        e2e_ms = []
-        for k in range(max(3, args.warmup) + args.steps):
-            flush.fill_(k & 255)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            m.reset()
-            m.set_occupancy(xyz_h, ones_h)
-            m.global_()
-            inf2 = m.info()
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        e2e_ms = e2e_ms[max(3, args.warmup):]
-        ems = max_over_ranks(statistics.mean(e2e_ms))
+        # end to end through the C ABI with host buffers (pinned): the occupied-voxel records (packed
+        # 64-bit records; the (x, y, z) + occ form beside it) host -> device, the transform, and a
+        # host consumer's read-back: D at 2^20 voxels uniform in the grid, queried from host memory
+        # into host memory (coordinates in, distances out), with the grid's counters
+        nq = 1 << 20
+        rq = np.random.default_rng(21)
+        q_h = torch.from_numpy(np.stack([rq.integers(0, nx, nq), rq.integers(0, ny, nq), rq.integers(0, nz, nq)],
+                                        1).astype(np.int32)).pin_memory().numpy()
+        d_h = torch.empty(nq, dtype=torch.int32).pin_memory().numpy()
+        packed_h = torch.from_numpy(V.pack_records(xyz_h, ones_h).view(np.int64)).pin_memory().numpy().view(np.uint64)
+        xyz_p = torch.from_numpy(xyz_h).pin_memory().numpy()
+        ones_p = torch.from_numpy(ones_h).pin_memory().numpy()
+        lib = V.load()
+
+        def e2e(stage):
+            ms = []
+            for k in range(max(3, args.warmup) + args.steps):
+                flush.fill_(k & 255)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                m.reset()
+                stage()
+                m.global_()
+                V.lib._check(lib.vdbedt_query(m.handle, q_h.ctypes.data, nq, d_h.ctypes.data, 0), "vdbedt_query",
+                             m.handle)
+                inf2 = m.info()
+                ms.append(1e3 * (time.perf_counter() - t0))
+            return max_over_ranks(statistics.mean(ms[max(3, args.warmup):])), inf2
+
+        ems, inf2 = e2e(lambda: m.set_occupancy_packed(packed_h))
+        ems3, _ = e2e(lambda: m.set_occupancy(xyz_p, ones_p))
+        qref = m.query(q_h)
         line["e2e"] = {"value": inf2["finite_bricks"] * 512 * world / (ems / 1e3) / 1e6, "unit": "Mvoxels/s",
-                       "ms_per_step": ems, "host_buffers": "pinned", "h2d_bytes_per_step": int(n * 13),
-                       "d2h_bytes_per_step": 4 * 16}
+                       "ms_per_step": ems, "host_buffers": "pinned", "records": "packed 64-bit",
+                       "h2d_bytes_per_step": int(n * 8 + nq * 12), "d2h_bytes_per_step": int(nq * 4 + 4 * 19),
+                       "readback": f"D at {nq} voxels (vdbedt_query, host in and out) + grid counters",
+                       "readback_equals_device_query": bool(np.array_equal(qref, d_h)),
+                       "triples_form": {"ms_per_step": ems3, "value": inf2["finite_bricks"] * 512 * world / (ems3 / 1e3) / 1e6,
+                                        "h2d_bytes_per_step": int(n * 13 + nq * 12)}}
 
     if wl["kind"] == "tunnel" and not args.no_clearance:
         line["clearance"] = bench_clearance(V, torch, m, occ, stream)
         line["nearest"] = bench_nearest(V, torch, m, wl["dims"], stream)
     if wl["kind"] == "tunnel" and not args.no_batched:
         line["batched"] = bench_batched(V, torch, stream, flush, autotuned=not args.no_autotune)
+    frames = None
     if wl["kind"] == "tunnel" and not args.no_incremental:
-        line["incremental"] = bench_incremental(V, torch, wl, occ, stream, flush, args.frames, args.incr_run,
-                                                args.alg1_frames if rank == 0 else 0)
+        line["incremental"], frames = bench_incremental(V, torch, wl, occ, stream, flush, args.frames,
+                                                        args.incr_run, 0)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(occ, dmax)
+        line["cpu_baseline"]["host"] = host_cpu()
+        first = frames[:args.alg1_frames] if (frames and args.alg1_frames > 0 and wl["kind"] == "tunnel") else None
+        line["cpu_baseline"].update(cpu_baselines_other(first, occ, dmax))
     if rank == 0:
         print(json.dumps(line), flush=True)
     m.close()

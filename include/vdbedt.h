@@ -85,6 +85,9 @@ typedef struct {
   int64_t y_items;        /* brick runs recomputed by the y pass */
   int64_t z_items;        /* brick runs recomputed by the z pass */
   int64_t new_bricks;     /* bricks allocated by this update */
+  int64_t x_bricks;       /* stored bricks in those runs, recomputed by the x pass */
+  int64_t y_bricks;       /* ... by the y pass */
+  int64_t z_bricks;       /* ... by the z pass */
 } vdbedt_update_stats;
 
 /* Create a handle for an nx x ny x nz grid with no obstacles (every D = dmax^2).
@@ -112,6 +115,13 @@ vdbedt_status vdbedt_destroy(vdbedt_handle h);
  * the whole call with EINVAL.  n == 0 is a no-op; n < 0 is EINVAL. */
 vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const uint8_t* occ, int64_t n,
                                    int on_device);
+
+/* The same records packed in 64 bits each, 8 bytes instead of 13 (for host links, where the record
+ * stream is the largest transfer): rec[k] = x | y << 21 | z << 42 | occ << 63 (x, y, z below 2^21,
+ * occ 0 or 1).  Semantics, validation and errors as vdbedt_set_occupancy (a coordinate outside the
+ * grid rejects a host call; from device memory it is skipped and reported by the next
+ * synchronising call); page-locked host arrays are read in place. */
+vdbedt_status vdbedt_set_occupancy_packed(vdbedt_handle h, const uint64_t* rec, int64_t n, int on_device);
 
 /* Stage up to n_max occupancy records in device memory whose actual count is the int32 at n_dev
  * (device memory), read when the stream reaches the call -- the same edits as vdbedt_set_occupancy

@@ -26,6 +26,7 @@ from .lib import (  # noqa: F401
     edt_dense_noalloc,
     global_batched,
     kernel_launches,
+    pack_records,
     library_path,
     load,
 )

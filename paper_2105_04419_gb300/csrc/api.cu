@@ -27,6 +27,8 @@ void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, const int32_t* n_dev,
                                 int32_t* count_out, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
                                 int32_t* counters, cudaStream_t st);
+cudaError_t launch_check_packed(const uint64_t* src, int64_t n, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
+                                int32_t* counters, cudaStream_t st);
 }
 
 struct vdbedt_batch;
@@ -461,6 +463,40 @@ vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const ui
   return VDBEDT_OK;
 }
 
+vdbedt_status vdbedt_set_occupancy_packed(vdbedt_handle h, const uint64_t* rec, int64_t n, int on_device) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (n < 0) return fail(h, VDBEDT_EINVAL, "negative record count");
+  if (n == 0) return VDBEDT_OK;
+  if (!rec) return fail(h, VDBEDT_EINVAL, "null records");
+  if (h->stage_counted) return fail(h, VDBEDT_EINVAL, "records staged with a device count must be applied first");
+  DeviceGuard guard(h->device);
+  s = ensure_stage(h, h->stage_n + n);
+  if (s) return s;
+  rec_t* dst = h->stage + h->stage_n;
+  const uint64_t* src = rec;
+  if (!on_device) {
+    // page-locked host records are read in place (mapped host memory); others are copied first
+    src = static_cast<const uint64_t*>(mapped_host(rec));
+    if (!src) {
+      CK(h, ensure_scratch(h->io, (size_t)n * 8), "io alloc");
+      CK(h, cudaMemcpyAsync(h->io.buf, rec, (size_t)n * 8, cudaMemcpyHostToDevice, h->st), "h2d");
+      src = (const uint64_t*)h->io.buf;
+    }
+    CK(h, cudaMemsetAsync(h->d_invalid, 0, sizeof(int32_t), h->st), "memset");
+  }
+  CK(h, launch_check_packed(src, n, h->g.nx, h->g.ny, h->g.nz, dst, on_device ? nullptr : h->d_invalid,
+                            h->g.counters, h->st),
+     "check");
+  if (!on_device) {
+    CK(h, cudaMemcpyAsync(h->h_pinned, h->d_invalid, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st), "d2h");
+    CK(h, cudaStreamSynchronize(h->st), "sync");
+    if (h->h_pinned[0] != 0) return fail(h, VDBEDT_EINVAL, "packed record outside the grid; call rejected");
+  }
+  h->stage_n += n;
+  return VDBEDT_OK;
+}
+
 vdbedt_status vdbedt_set_occupancy_counted(vdbedt_handle h, const int32_t* xyz, const uint8_t* occ,
                                            const int32_t* n_dev, int64_t n_max) {
   vdbedt_status s = check_handle(h);
@@ -559,6 +595,9 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     stats->y_items = c[45];
     stats->z_items = c[46];
     stats->new_bricks = c[C_NEW_BRICKS];
+    stats->x_bricks = c[C_XB];
+    stats->y_bricks = c[C_YB];
+    stats->z_bricks = c[C_ZB];
   }
   return VDBEDT_OK;
 }
@@ -970,6 +1009,9 @@ vdbedt_status batch_update(vdbedt_batch* b, vdbedt_update_stats* stats) {
       o.y_items = b->maps[0]->h_pinned[45];
       o.z_items = b->maps[0]->h_pinned[46];
       o.new_bricks = c[C_NEW_BRICKS];
+      o.x_bricks = c[C_XB];
+      o.y_bricks = c[C_YB];
+      o.z_bricks = c[C_ZB];
     }
   }
   return VDBEDT_OK;
@@ -1328,7 +1370,36 @@ __global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* _
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     put(i, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], occ[i]);
 }
+
+// Packed records (x | y << 21 | z << 42 | occ << 63, the stage's own format): copied into the stage
+// after a range check; a record outside the grid is counted (host input: the call is rejected) or
+// flagged in the error word (device input: reported by the next synchronising call), and replaced
+// by a skipped record.
+__global__ void k_check_packed(const uint64_t* __restrict__ src, int64_t n, int nx, int ny, int nz,
+                               rec_t* __restrict__ dst, int32_t* invalid, int32_t* counters) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const rec_t r = src[i];
+    const int4 u = unpack_rec(r);
+    const bool ok = u.x < nx && u.y < ny && u.z < nz;
+    if (!ok) {
+      if (invalid)
+        atomicAdd(invalid, 1);
+      else
+        atomicOr(&counters[C_ERR], kErrInvalidRecord);
+    }
+    dst[i] = ok ? r : pack_rec(kBadCoord, 0, 0, 0);
+  }
+}
 }  // namespace
+
+cudaError_t launch_check_packed(const uint64_t* src, int64_t n, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
+                                int32_t* counters, cudaStream_t st) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  VDB_LAUNCH(k_check_packed, (unsigned)b, 256, 0, st, src, n, nx, ny, nz, dst, invalid, counters);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, const int32_t* n_dev,
                                 int32_t* count_out, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,

@@ -132,6 +132,9 @@ __global__ void k_begin_update(US us) {
     g.counters[C_HAS_ZERO] = 0;
     g.counters[C_FRESH] = 0;
     g.counters[C_DEFERRED] = 0;
+    g.counters[C_XB] = 0;
+    g.counters[C_YB] = 0;
+    g.counters[C_ZB] = 0;
     g.counters[C_EPOCH] += 1;
   }
 }
@@ -153,6 +156,9 @@ __global__ void k_begin_batch_update(const UpdArgs* __restrict__ args, BatchCoun
     g.counters[C_HAS_ZERO] = 0;
     g.counters[C_FRESH] = 0;
     g.counters[C_DEFERRED] = 0;
+    g.counters[C_XB] = 0;
+    g.counters[C_YB] = 0;
+    g.counters[C_ZB] = 0;
     g.counters[C_EPOCH] += 1;
   }
 }
@@ -1380,6 +1386,9 @@ __device__ __forceinline__ void run_slots(const GridView& g, int axis, int run, 
     }
   }
   dst[lane] = s;
+  // the run's own stored bricks (the ones the pass recomputes), counted for the update statistics
+  const unsigned own = __ballot_sync(0xffffffffu, s >= 0 && lane >= g.R && lane < g.R + run);
+  if (lane == 0 && own) atomicAdd(&g.counters[C_XB + axis], __popc(own));
 }
 
 // blockIdx.y = axis

@@ -52,7 +52,10 @@ enum Counter : int {
   C_FRESH = 13,  // compute-set words first marked by this update (incremental), listed in flist
   C_EPOCH = 14,  // incremental update epoch (run and brick dedupe marks)
   C_DEFERRED = 15,  // the tracked ingest met "set" records whose node did not exist yet
-  C_NUM = 16
+  C_XB = 16,  // stored bricks in the update's dirty runs per axis (x, y, z: three consecutive words)
+  C_YB = 17,
+  C_ZB = 18,
+  C_NUM = 19
 };
 
 // brick flags

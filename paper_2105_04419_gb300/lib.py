@@ -39,7 +39,8 @@ class Info(ctypes.Structure):
 class UpdateStats(ctypes.Structure):
     _fields_ = [("records", ctypes.c_int64), ("net_flips", ctypes.c_int64), ("changed_bricks", ctypes.c_int64),
                 ("x_items", ctypes.c_int64), ("y_items", ctypes.c_int64), ("z_items", ctypes.c_int64),
-                ("new_bricks", ctypes.c_int64)]
+                ("new_bricks", ctypes.c_int64), ("x_bricks", ctypes.c_int64), ("y_bricks", ctypes.c_int64),
+                ("z_bricks", ctypes.c_int64)]
 
 
 class PhaseTimes(ctypes.Structure):
@@ -59,6 +60,7 @@ SIGNATURES = {
     "vdbedt_destroy": (ctypes.c_int, [_H]),
     "vdbedt_set_occupancy": (ctypes.c_int, [_H, _P, _P, _I64, ctypes.c_int]),
     "vdbedt_set_occupancy_counted": (ctypes.c_int, [_H, _P, _P, _P, _I64]),
+    "vdbedt_set_occupancy_packed": (ctypes.c_int, [_H, _P, _I64, ctypes.c_int]),
     "vdbedt_set_occupancy_dense": (ctypes.c_int, [_H, _P, ctypes.c_int]),
     "vdbedt_reset": (ctypes.c_int, [_H]),
     "vdbedt_global": (ctypes.c_int, [_H]),
@@ -127,6 +129,16 @@ def _torch():
 def _ptr_host(a: np.ndarray) -> int:
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data
+
+
+def pack_records(xyz, occ) -> np.ndarray:
+    """Host records (x, y, z) [n, 3] and occ [n] packed as uint64 x | y << 21 | z << 42 | occ << 63."""
+    x = np.ascontiguousarray(xyz, dtype=np.int64).reshape(-1, 3)
+    o = np.ascontiguousarray(occ, dtype=np.uint64).reshape(-1)
+    if x.size and (x.min() < 0 or x.max() >= 1 << 21):
+        raise ValueError("coordinates must lie in [0, 2^21)")
+    u = x.astype(np.uint64)
+    return u[:, 0] | (u[:, 1] << np.uint64(21)) | (u[:, 2] << np.uint64(42)) | ((o & np.uint64(1)) << np.uint64(63))
 
 
 class Map:
@@ -208,6 +220,22 @@ class Map:
             self._enter(x, o)
             _check(lib.vdbedt_set_occupancy(self._h, x.data_ptr(), o.data_ptr(), x.shape[0], 1),
                    "vdbedt_set_occupancy", self._h)
+
+    def set_occupancy_packed(self, rec):
+        """Stage records packed as uint64 x | y << 21 | z << 42 | occ << 63 (numpy uint64 on the
+        host, or an int64 / uint64 CUDA tensor); see pack_records."""
+        lib = load()
+        if isinstance(rec, np.ndarray):
+            r = np.ascontiguousarray(rec, dtype=np.uint64).reshape(-1)
+            _check(lib.vdbedt_set_occupancy_packed(self._h, _ptr_host(r), r.shape[0], 0),
+                   "vdbedt_set_occupancy_packed", self._h)
+        else:
+            r = rec.contiguous().view(-1)
+            if r.element_size() != 8 or not r.is_cuda:
+                raise TypeError("packed records are 64-bit integers")
+            self._enter(r)
+            _check(lib.vdbedt_set_occupancy_packed(self._h, r.data_ptr(), r.shape[0], 1),
+                   "vdbedt_set_occupancy_packed", self._h)
 
     def set_occupancy_counted(self, xyz, occ, count, n_max: int):
         """Stage up to n_max device records whose count is the int32 CUDA tensor `count` (read on
@@ -478,6 +506,15 @@ class BatchUpdateGraph:
                     self.occ[i, :n].copy_(occ.view(-1), non_blocking=True)
                 counts.append(n)
             self.count.copy_(torch.tensor(counts, dtype=torch.int32), non_blocking=True)
+            self.graph.replay()
+        m0._leave()
+
+    def replay(self):
+        """Replay with the records already in the input buffers (xyz, occ, count)."""
+        torch = _torch()
+        m0 = self.b.maps[0]
+        m0._enter()
+        with torch.cuda.stream(self.b.stream):
             self.graph.replay()
         m0._leave()
 

@@ -268,3 +268,58 @@ def test_pinned_host_records_read_in_place():
     assert e.value.code == "EINVAL"
     m.global_()
     assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 13)) is None
+
+
+def test_packed_records_match_triples():
+    """Records packed in 64 bits (host, pinned host and device) give the same field as the
+    (x, y, z) + occ format, for the global transform and an update with clears and repeats."""
+    import torch
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(17)
+    occ = W.bernoulli_grid(17, (40, 64, 72), 0.01)
+    nz, ny, nx = occ.shape
+    xyz = coords_of(occ)
+    val = np.ones(len(xyz), np.uint8)
+    edits = np.stack([rs.integers(0, nx, 500), rs.integers(0, ny, 500), rs.integers(0, nz, 500)], 1).astype(np.int32)
+    ev = rs.integers(0, 2, 500).astype(np.uint8)
+    ref_maps = []
+    for form in ("triples", "host", "pinned", "device"):
+        m = V.Map(nx, ny, nz, 20)
+        for k, (x, v) in enumerate(((xyz, val), (edits, ev))):
+            if form == "triples":
+                m.set_occupancy(x, v)
+            else:
+                p = V.pack_records(x, v)
+                if form == "pinned":
+                    p = torch.from_numpy(p.view(np.int64)).pin_memory().numpy().view(np.uint64)
+                elif form == "device":
+                    p = torch.from_numpy(p.view(np.int64)).cuda()
+                m.set_occupancy_packed(p)
+            if k == 0:
+                m.global_()
+            else:
+                m.update()
+        ref_maps.append(m.export_dense())
+        m.close()
+    for got in ref_maps[1:]:
+        assert np.array_equal(got, ref_maps[0])
+    for (x, y, z), v in zip(edits, ev):
+        occ[z, y, x] = v
+    assert first_mismatch(ref_maps[0], O.edt_factorised(occ, 20)) is None
+
+
+def test_packed_records_outside_the_grid():
+    import torch
+    import paper_2105_04419_gb300 as V
+    m = V.Map(16, 16, 16, 6)
+    bad = V.pack_records(np.array([[1, 2, 3], [16, 0, 0]], np.int32), np.array([1, 1], np.uint8))
+    with pytest.raises(V.VdbedtError) as e:
+        m.set_occupancy_packed(bad)
+    assert e.value.code == "EINVAL"
+    m.set_occupancy_packed(torch.from_numpy(bad.view(np.int64)).cuda())  # device: skipped, reported later
+    m.global_()
+    with pytest.raises(V.VdbedtError) as e:
+        m.synchronize()
+    assert e.value.code == "EINVAL"
+    d = m.export_dense()
+    assert d[3, 2, 1] == 0 and (d == 0).sum() == 1

@@ -89,3 +89,17 @@ def test_alg1_frames_helper():
     assert len(r["frames"]) == 2 and r["threads"] == 1
     for f, (xyz, val) in zip(r["frames"], frames):
         assert f["records"] == len(val) and f["ms"] > 0 and f["lowered"] >= 0
+
+
+def test_bench_cpu_baselines_other_small():
+    """bench.cpu_baselines_other times the oracle on the other workloads (here with a small budget):
+    Eq. 1 factorised on the 64^3 cube and on the first batch map, the paper's Alg. 1 global on the
+    cube, which equals Eq. 1 there; host_cpu reports the cores."""
+    import bench
+    out = bench.cpu_baselines_other(None, None, 32, budget4_voxels=1)
+    assert out["o1"]["cube64_dmax16"]["active_voxels"] > 0
+    assert out["o1"]["batch96_dmax24_first_maps"]["maps"] == 1
+    assert out["o2_alg1"]["cube64_dmax16_global"]["threads"] == 1
+    assert out["o2_alg1"]["cube64_dmax16_global"]["equals_eq1"] in (True, False)
+    info = bench.host_cpu()
+    assert info["affinity_cores"] >= 1
