@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-incremental", action="store_true")
     ap.add_argument("--no-clearance", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-crossover", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work-item tuning")
     ap.add_argument("--frames", type=int, default=300, help="lidar frames of the incremental measurement")
     ap.add_argument("--incr-run", type=int, default=4, choices=(4, 8, 16),
@@ -329,6 +330,62 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
             "final_map": {"occupied_voxels": int(final_occ.sum()), "allocated_bricks": info_final["allocated_bricks"]},
             "graph_equals_eager": same, "l2": "flushed before every frame (untimed)",
             **({"cpu_alg1": alg1} if alg1 else {})}, frames
+
+
+def bench_crossover(V, torch, wl, occ, xyz_d, stream, flush, fractions=(1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 0.1, 0.25, 0.5),
+                    seed=17):
+    """Global against incremental transform after edits of growing size (the paper's ablation shape,
+    Sec. V-A: remove a fraction of the obstacles at random and add as many new ones, uniform in the
+    domain).  For each fraction the map holds the scene's field; the same records are staged and
+    either vdbedt_update or vdbedt_global applies them (event-timed, L2 flushed before, 3 repeats,
+    median); the two fields are compared."""
+    nx, ny, nz = wl["dims"]
+    dmax = wl["dmax"]
+    rs = np.random.default_rng(seed)
+    n_obs = xyz_d.shape[0]
+    ones = torch.ones(n_obs, dtype=torch.uint8, device="cuda")
+    m = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    rows = []
+    for f in fractions:
+        k = max(1, int(round(f * n_obs)))
+        rm = xyz_d[torch.from_numpy(rs.choice(n_obs, k, replace=False)).cuda()]
+        add = torch.from_numpy(np.stack([rs.integers(0, nx, k), rs.integers(0, ny, k), rs.integers(0, nz, k)],
+                                        1).astype(np.int32)).cuda()
+        rec = torch.cat([rm, add])
+        val = torch.cat([torch.zeros(k, dtype=torch.uint8, device="cuda"), torch.ones(k, dtype=torch.uint8, device="cuda")])
+        res = {}
+        for form in ("update", "global"):
+            ts = []
+            for r in range(3):
+                m.reset()
+                m.set_occupancy(xyz_d, ones)
+                m.global_()
+                m.set_occupancy(rec, val)
+                flush.fill_(r)
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                if form == "update":
+                    m.update()
+                else:
+                    m.global_()
+                e.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(e))
+            res[form] = statistics.median(ts)
+            res[form + "_field"] = m.export_dense(on_device=True)
+        m.reset()
+        m.set_occupancy(xyz_d, ones)
+        m.global_()
+        m.set_occupancy(rec, val)
+        st = m.update(stats=True)
+        same = bool(torch.equal(res.pop("update_field"), res.pop("global_field")))
+        rows.append({"fraction": f, "removed": k, "added": k, "net_flips": st["net_flips"],
+                     "changed_bricks": st["changed_bricks"], "z_bricks": st["z_bricks"],
+                     "update_ms": res["update"], "global_ms": res["global"],
+                     "global_over_update": res["global"] / res["update"], "same_field": same})
+    m.close()
+    return {"workload": "the scene's obstacles; a fraction removed at random and as many added uniformly in the domain",
+            "step": "staged records applied by vdbedt_update or by vdbedt_global on the same map", "rows": rows}
 
 
 def bench_clearance(V, torch, m, occ, stream, reps=20):
@@ -851,6 +908,8 @@ def main():
     if wl["kind"] == "tunnel" and not args.no_clearance:
         line["clearance"] = bench_clearance(V, torch, m, occ, stream)
         line["nearest"] = bench_nearest(V, torch, m, wl["dims"], stream)
+    if wl["kind"] == "tunnel" and not args.no_crossover:
+        line["crossover"] = bench_crossover(V, torch, wl, occ, xyz, stream, flush)
     if wl["kind"] == "tunnel" and not args.no_batched:
         line["batched"] = bench_batched(V, torch, stream, flush, autotuned=not args.no_autotune)
     frames = None

@@ -87,7 +87,9 @@ typedef struct {
   int64_t new_bricks;     /* bricks allocated by this update */
   int64_t x_bricks;       /* stored bricks in those runs, recomputed by the x pass */
   int64_t y_bricks;       /* ... by the y pass */
-  int64_t z_bricks;       /* ... by the z pass */
+  int64_t z_bricks;       /* ... by the z pass (the three counts are 0 when global_form is 1) */
+  int64_t global_form;    /* 1: the edits reached so far that the update switched to the global form after
+                             applying them (same field, lower cost; see vdbedt_update) */
 } vdbedt_update_stats;
 
 /* Create a handle for an nx x ny x nz grid with no obstacles (every D = dmax^2).
@@ -148,7 +150,12 @@ vdbedt_status vdbedt_global(vdbedt_handle h);
 
 /* Incremental transform: apply staged records; recompute only the bricks that a flipped voxel can
  * reach (Chebyshev brick radius R around each changed brick).  Equal, bit for bit, to vdbedt_global
- * on the same occupancy.  stats (nullable) is filled after a stream synchronisation. */
+ * on the same occupancy.  When the changed bricks times (2R + 1)^3 exceed 24 times the stored
+ * bricks (the marking would then cost more than recomputing the map), the update decides on the
+ * device, after applying the records, to rebuild the compute set and work lists as vdbedt_global
+ * does (the trade-off of the paper's Sec. V-A between global and incremental transforms); the
+ * decision needs no host round trip, so a captured update keeps it.  stats (nullable) is filled
+ * after a stream synchronisation. */
 vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats);
 
 /* D at n voxel coordinates; coordinates outside the grid or in unstored bricks give dmax^2.

@@ -64,6 +64,7 @@ struct vdbedt_map {
   bool profiling = false;
   cudaEvent_t ev[7] = {};
   bool ev_recorded = false;
+  Fork fork;  // side stream of the update's global-form branch
 };
 
 namespace {
@@ -304,6 +305,9 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   auto bail = [&](cudaError_t e, const char* where) {
     vdbedt_status s = cuda_fail(nullptr, e, where);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->fork.side) cudaStreamDestroy(h->fork.side);
+    if (h->fork.fork) cudaEventDestroy(h->fork.fork);
+    if (h->fork.join) cudaEventDestroy(h->fork.join);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
     return s;
@@ -316,6 +320,10 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
     if (e != cudaSuccess) return bail(e, "stream");
     h->own_stream = true;
   }
+  e = cudaStreamCreateWithFlags(&h->fork.side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork.join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(e, "side stream");
 #define AL(ptr, count)                                   \
   do {                                                   \
     e = dalloc(h, &(ptr), (size_t)(count));              \
@@ -406,6 +414,9 @@ void destroy_impl(vdbedt_map* h) {
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (int i = 0; i < 7; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  if (h->fork.side) cudaStreamDestroy(h->fork.side);
+  if (h->fork.fork) cudaEventDestroy(h->fork.fork);
+  if (h->fork.join) cudaEventDestroy(h->fork.join);
   if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
 }
@@ -575,9 +586,13 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
       clear_stage(h);
     }
     mark(h, 1);
-    CK(h, launch_incremental_mark(h->g, t, h->changed, h->items, h->st), "mark");
+    CK(h, launch_incremental_mark(h->g, t, h->changed, h->items, h->fork, h->st), "mark");
     mark(h, 2);
-    s = run_passes(h, t, true);
+    // slot lists of the dirty runs (an update that switched to the global form got them with its
+    // work lists), then the side stream's branch joins before the passes
+    if (half_path(h->g)) CK(h, launch_item_slots(h->g, t, h->items, h->st), "item slots");
+    CK(h, cudaStreamWaitEvent(h->st, h->fork.join, 0), "join");
+    s = run_passes(h, t, false);
     if (s) return s;
   }
   if (stats) {
@@ -598,6 +613,7 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     stats->x_bricks = c[C_XB];
     stats->y_bricks = c[C_YB];
     stats->z_bricks = c[C_ZB];
+    stats->global_form = c[C_BIG];
   }
   return VDBEDT_OK;
 }
@@ -816,6 +832,7 @@ struct vdbedt_batch {
   bool ev_recorded = false;
   UpdArgs* d_upd = nullptr;  // the grids' update arguments in device memory
   UpdArgs* h_upd = nullptr;  // and their page-locked host copy
+  Fork fork;                 // side stream of the update's global-form branch
 };
 
 namespace {
@@ -838,6 +855,9 @@ void destroy_batch(vdbedt_batch* b) {
   for (int i = 0; i < 6; ++i)
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   if (b->h_upd) cudaFreeHost(b->h_upd);
+  if (b->fork.side) cudaStreamDestroy(b->fork.side);
+  if (b->fork.fork) cudaEventDestroy(b->fork.fork);
+  if (b->fork.join) cudaEventDestroy(b->fork.join);
   if (b->own_stream && b->st) cudaStreamDestroy(b->st);
   delete b;
 }
@@ -942,7 +962,7 @@ vdbedt_status batch_update(vdbedt_batch* b, vdbedt_update_stats* stats) {
     // The grids' arguments in device memory stay fixed while staging does not reallocate (every
     // grid reads its record count from its device count word), so a captured update replays with
     // the same arguments; they are uploaded again only when they change, outside a capture.
-    BatchUpdShape shape{b->k, 0, 0, 0, 0};
+    BatchUpdShape shape{b->k, 0, 0, 0, 0, g0.R, half_path(g0)};
     BatchCounts counts{};
     std::vector<UpdArgs> args((size_t)b->k);
     for (int i = 0; i < b->k; ++i) {
@@ -974,7 +994,8 @@ vdbedt_status batch_update(vdbedt_batch* b, vdbedt_update_stats* stats) {
     BCK(b, launch_update_batch_ingest(b->d_upd, shape, counts, b->st), "ingest");
     for (vdbedt_map* m : b->maps) clear_stage(m);
     bmark(b, 1);
-    BCK(b, launch_update_batch_mark(b->d_upd, shape, t, b->items, b->st), "mark");
+    BCK(b, launch_update_batch_mark(b->d_upd, shape, t, b->items, b->fork, b->st), "mark");
+    BCK(b, cudaStreamWaitEvent(b->st, b->fork.join, 0), "join");
     bmark(b, 2);
     BCK(b, launch_item_slots_batch(b->d_views, t, b->items, b->pool.items_ctr, b->pool.item_cap, b->st), "item slots");
     bmark(b, 3);
@@ -1012,6 +1033,7 @@ vdbedt_status batch_update(vdbedt_batch* b, vdbedt_update_stats* stats) {
       o.x_bricks = c[C_XB];
       o.y_bricks = c[C_YB];
       o.z_bricks = c[C_ZB];
+      o.global_form = c[C_BIG];
     }
   }
   return VDBEDT_OK;
@@ -1090,6 +1112,10 @@ vdbedt_status vdbedt_batch_create(const vdbedt_config* cfgs, int32_t k, vdbedt_b
 #undef BAL
   e = cudaMallocHost((void**)&b->h_upd, sizeof(UpdArgs) * (size_t)k);
   if (e != cudaSuccess) return bail(e, "pinned alloc");
+  e = cudaStreamCreateWithFlags(&b->fork.side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork.join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(e, "side stream");
   memset(b->h_upd, 0, sizeof(UpdArgs) * (size_t)k);
   e = cudaMemsetAsync(b->counters, 0, sizeof(int32_t) * (size_t)(k + 1) * C_NUM, b->st);
   if (e != cudaSuccess) return bail(e, "memset");

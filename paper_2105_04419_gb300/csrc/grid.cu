@@ -59,6 +59,7 @@ struct OneView {
     grid = 0;
     return g;
   }
+  __device__ __forceinline__ bool skip(const GridView&) const { return false; }
 };
 struct BatchViews {
   const GridView* v;
@@ -76,6 +77,30 @@ struct BatchViews {
     grid = lo;
     return v[lo];
   }
+  __device__ __forceinline__ bool skip(const GridView&) const { return false; }
+};
+// The global form's activation and work-list kernels run inside an incremental update only for
+// grids whose update switched to the global form (counters[C_BIG] set after the records were
+// applied): one grid (the whole launch is its share), or grid blockIdx.y of a batch.
+struct GatedOne {
+  GridView g;
+  __device__ __forceinline__ GridView get(int& bid, int& nblk, int& grid) const {
+    bid = blockIdx.x;
+    nblk = gridDim.x;
+    grid = 0;
+    return g;
+  }
+  __device__ __forceinline__ bool skip(const GridView& v) const { return v.counters[C_BIG] == 0; }
+};
+struct GatedBatch {
+  const UpdArgs* a;
+  __device__ __forceinline__ GridView get(int& bid, int& nblk, int& grid) const {
+    bid = blockIdx.x;
+    nblk = gridDim.x;
+    grid = (int)blockIdx.y;
+    return a[blockIdx.y].g;
+  }
+  __device__ __forceinline__ bool skip(const GridView& v) const { return v.counters[C_BIG] == 0; }
 };
 struct OneSrc {
   const uint8_t* p;
@@ -135,6 +160,7 @@ __global__ void k_begin_update(US us) {
     g.counters[C_XB] = 0;
     g.counters[C_YB] = 0;
     g.counters[C_ZB] = 0;
+    g.counters[C_BIG] = 0;
     g.counters[C_EPOCH] += 1;
   }
 }
@@ -159,6 +185,7 @@ __global__ void k_begin_batch_update(const UpdArgs* __restrict__ args, BatchCoun
     g.counters[C_XB] = 0;
     g.counters[C_YB] = 0;
     g.counters[C_ZB] = 0;
+    g.counters[C_BIG] = 0;
     g.counters[C_EPOCH] += 1;
   }
 }
@@ -902,6 +929,7 @@ template <class VS>
 __global__ void k_clear_masks(VS vs) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
+  if (vs.skip(g)) return;
   (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
@@ -918,6 +946,7 @@ template <class VS>
 __global__ void k_obstacle_flags(VS vs) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
+  if (vs.skip(g)) return;
   (void)gi;
   const int nb = min(g.counters[C_NBRICKS], g.cap);
   for (int s = bid * blockDim.x + threadIdx.x; s < nb; s += nblk * blockDim.x) {
@@ -946,6 +975,7 @@ template <class VS>
 __global__ void k_node_halo(VS vs) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
+  if (vs.skip(g)) return;
   (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int lane = threadIdx.x & 31;
@@ -997,6 +1027,7 @@ template <int AXIS, class VS>
 __global__ void k_dilate_stage(VS vs) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
+  if (vs.skip(g)) return;
   (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int R = g.R;
@@ -1068,6 +1099,7 @@ template <class VS>
 __global__ void __launch_bounds__(256) k_dilate_nodes(VS vs) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
+  if (vs.skip(g)) return;
   (void)gi;
   __shared__ int nbr[27];
   __shared__ uint16_t X[48][48];  // [z' + 16][y' + 16]: rows dilated along x
@@ -1163,6 +1195,7 @@ template <class VS>
 __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
+  if (vs.skip(g)) return;
   (void)gi;
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   for (int b = bid; b < nn * 16; b += nblk) {
@@ -1191,6 +1224,7 @@ __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
 template <class US>
 __global__ void __launch_bounds__(256) k_alloc_fresh(US us) {
   const GridView g = us.get().g;
+  if (g.counters[C_BIG]) return;
   const int nf = min(g.counters[C_FRESH], g.node_cap * 128);
   const int lane = threadIdx.x & 31;
   const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
@@ -1248,7 +1282,7 @@ template <class VS>
 __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int rz, Items it, bool with_slots) {
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
-  (void)gi;
+  if (vs.skip(g)) return;
   __shared__ int wsum[8];
   __shared__ int base_sh, count_sh;
   __shared__ int nbr_sh[2];
@@ -1309,6 +1343,7 @@ __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int 
         l0[a1] = o1;
         l0[a2] = o2;
         it.run[axis][p] = pack_brick(q[0] * 16 + l0[0], q[1] * 16 + l0[1], q[2] * 16 + l0[2]);
+        if (it.igrid[axis]) it.igrid[axis][p] = gi;
       }
     }
     __syncthreads();
@@ -1393,6 +1428,7 @@ __device__ __forceinline__ void run_slots(const GridView& g, int axis, int run, 
 
 // blockIdx.y = axis
 __global__ void k_item_slots(GridView g, int rx, int ry, int rz, Items it) {
+  if (g.counters[C_BIG]) return;  // the global form's work lists came with their slots
   const int axis = (int)blockIdx.y;
   const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
   const int n = min(g.items_ctr[axis], g.item_cap);
@@ -1410,6 +1446,7 @@ __global__ void k_item_slots_batch(const GridView* __restrict__ views, const int
   const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
   for (int item = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); item < n; item += nw) {
     const GridView g = views[it.igrid[axis][item]];
+    if (g.counters[C_BIG]) continue;  // warp-uniform: that grid's runs came with their slots
     run_slots(g, axis, run, it.run[axis][item], it.slots[axis] + (size_t)item * kItemSlots);
   }
 }
@@ -1423,6 +1460,13 @@ __global__ void k_changed_flags_dilate(US us) {
   const int32_t* __restrict__ changed = A.changed;
   const int nc = min(g.counters[C_CHANGED], g.cap);
   const int side = 2 * g.R + 1, rows = side * side;
+  // The marking costs (2R + 1)^3 brick visits per changed brick; once that exceeds kBigUpdate
+  // visits per stored brick, the update takes the global form's activation and work lists instead
+  // (same field; measured crossover on the tunnel scene).  Every block reaches the same decision.
+  if ((int64_t)nc * side * side * side > (int64_t)kBigUpdate * max(g.counters[C_NBRICKS], 1)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_BIG] = 1;
+    return;
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nc * rows;
        i += (int64_t)gridDim.x * blockDim.x) {
     int s = changed[i / rows], r = (int)(i % rows);
@@ -1446,6 +1490,7 @@ __global__ void k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
   const GridView& g = A.g;
   const int32_t* __restrict__ changed = A.changed;
   const int grid = (int)blockIdx.y;
+  if (g.counters[C_BIG]) return;
   const int nc = min(g.counters[C_CHANGED], g.cap);
   const int epoch = g.counters[C_EPOCH];
   const int side = 2 * g.R + 1, vol = side * side * side;
@@ -1487,12 +1532,48 @@ cudaError_t update_ingest_kernels(US us, int k, int64_t n, int64_t nkeys, int64_
   return cudaGetLastError();
 }
 
-template <class US>
-cudaError_t update_mark_kernels(US us, int k, int node_cap, const Tuning& t, const Items& it, cudaStream_t st) {
+template <class US, class GV>
+cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool with_slots, const Tuning& t,
+                                const Items& it, const Fork& fk, cudaStream_t st) {
   const unsigned div = k > 1 ? (unsigned)k : 1u;
   auto share = [&](unsigned single) { return k > 1 ? (single / div > 16 ? single / div : 16u) : single; };
+  const unsigned nc = (unsigned)node_cap;
+  // the decision (counters[C_BIG]) and, for updates that stay incremental, the changed bricks' flags
+  // and dilation marks
   VDB_LAUNCH(k_changed_flags_dilate<US>, dim3(share(1024), k), kT, 0, st, us);
-  VDB_LAUNCH(k_alloc_fresh<US>, dim3(share(node_cap < 256 ? (unsigned)node_cap : 256u), k), kT, 0, st, us);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cudaStream_t gs = st;
+  if (fk.side) {
+    e = cudaEventRecord(fk.fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(fk.side, fk.fork, 0);
+    if (e != cudaSuccess) return e;
+    gs = fk.side;
+  }
+  // global form, for the grids whose update switched to it (the others' blocks return at once; the
+  // kernels stride over their work, so a launch of at most two blocks per SM keeps that cheap)
+  auto gated = [&](unsigned single) { return share(single < 304u ? single : 304u); };
+  VDB_LAUNCH(k_clear_masks<GV>, dim3(gated(256), k), kT, 0, gs, gv);
+  VDB_LAUNCH(k_obstacle_flags<GV>, dim3(gated(1024), k), kT, 0, gs, gv);
+  VDB_LAUNCH(k_node_halo<GV>, dim3(gated(64), k), kT, 0, gs, gv);
+  if (R <= 16) {
+    VDB_LAUNCH(k_dilate_nodes<GV>, dim3(gated(nc < 1024 ? nc : 1024u), k), 256, 0, gs, gv);
+  } else {
+    VDB_LAUNCH((k_dilate_stage<0, GV>), dim3(gated(256), k), kT, 0, gs, gv);
+    VDB_LAUNCH((k_dilate_stage<1, GV>), dim3(gated(256), k), kT, 0, gs, gv);
+    VDB_LAUNCH((k_dilate_stage<2, GV>), dim3(gated(256), k), kT, 0, gs, gv);
+  }
+  VDB_LAUNCH(k_alloc_marked<GV>, dim3(gated(nc * 16 < 8192 ? nc * 16 : 8192u), k), kT, 0, gs, gv, false);
+  VDB_LAUNCH(k_items_nodes<GV>, dim3(gated(nc * 12 < 8192 ? nc * 12 : 8192u), k), kT, 0, gs, gv, t.run[0], t.run[1],
+             t.run[2], it, with_slots);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (fk.side) {
+    e = cudaEventRecord(fk.join, fk.side);
+    if (e != cudaSuccess) return e;
+  }
+  // incremental form: new bricks of the dilation, the dirty runs
+  VDB_LAUNCH(k_alloc_fresh<US>, dim3(share(nc < 256 ? nc : 256u), k), kT, 0, st, us);
   VDB_LAUNCH(k_mark_dirty<US>, dim3(share(2048), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }
@@ -1825,11 +1906,11 @@ cudaError_t launch_build_items_batch(const GridView* views, const BatchShape& b,
 // Incremental: records were already applied with flip tracking (changed list filled).
 // (the item counters were cleared when the update began)
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const int32_t* changed, const Items& it,
-                                    cudaStream_t st) {
+                                    const Fork& fk, cudaStream_t st) {
   UpdArgs a{};
   a.g = g;
   a.changed = const_cast<int32_t*>(changed);
-  return update_mark_kernels(UpdOne{a}, 1, g.node_cap, t, it, st);
+  return update_mark_kernels(UpdOne{a}, GatedOne{g}, 1, g.node_cap, g.R, half_path(g), t, it, fk, st);
 }
 
 // Batched update: begin + tracked ingest of every grid, then the marking (one launch per step).
@@ -1843,9 +1924,10 @@ cudaError_t launch_update_batch_ingest(const UpdArgs* d_args, const BatchUpdShap
 }
 
 cudaError_t launch_update_batch_mark(const UpdArgs* d_args, const BatchUpdShape& s, const Tuning& t, const Items& it,
-                                     cudaStream_t st) {
+                                     const Fork& fk, cudaStream_t st) {
   if (s.k <= 0) return cudaSuccess;
-  return update_mark_kernels(UpdBatch{d_args}, s.k, (int)s.max_node_cap, t, it, st);
+  return update_mark_kernels(UpdBatch{d_args}, GatedBatch{d_args}, s.k, (int)s.max_node_cap, s.R, s.half, t, it, fk,
+                             st);
 }
 
 }  // namespace vdbedt

@@ -55,7 +55,8 @@ enum Counter : int {
   C_XB = 16,  // stored bricks in the update's dirty runs per axis (x, y, z: three consecutive words)
   C_YB = 17,
   C_ZB = 18,
-  C_NUM = 19
+  C_BIG = 19,  // this update's edits reach so far that it takes the global form after applying them
+  C_NUM = 20
 };
 
 // brick flags
@@ -236,6 +237,9 @@ constexpr int kBatchMax = 1024;  // grids per batch (the dense-ingest source tab
 // skips (y and z passes); + kVariantXDirect = x pass with plain loads instead of the copy ring;
 // kVariantEnvelope = the lower-envelope kernels for all three passes (16-bit integer fields).
 constexpr int kVariantXDirect = 4;
+// An incremental update whose changed bricks times (2R + 1)^3 exceed kBigUpdate times the stored
+// bricks takes the global form's activation and work lists after applying its records.
+constexpr int kBigUpdate = 24;
 constexpr int kVariantEnvelope = 8;
 struct Tuning {
   int run[3] = {4, 4, 4};  // bricks per work item along x, y, z
@@ -312,8 +316,16 @@ cudaError_t launch_activation_full(const GridView& g, cudaStream_t st);
 // every run holding a stored brick, with slot lists when with_slots (half path)
 cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, const Items& it, bool with_slots,
                                     cudaStream_t st);
+// A side stream for the update's two alternative branches: the global form's activation and work
+// lists run there (forked after the decision kernel, joined by the caller before the passes), so
+// that when the update stays incremental their launches, which exit at once, overlap the marking.
+struct Fork {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+// Records fork.join on the side stream; the caller waits on it before the passes.
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const int32_t* changed, const Items& it,
-                                    cudaStream_t st);
+                                    const Fork& fk, cudaStream_t st);
 // The tracked scratch of one grid (node-key flags, missing-brick list) and its last-record table,
 // allocated on first use; fills a's vlast / nflag / list.
 cudaError_t prepare_update_args(const GridView& g, Scratch& vl, Scratch& miss, UpdArgs& a, cudaStream_t st);
@@ -323,6 +335,8 @@ cudaError_t prepare_update_args(const GridView& g, Scratch& vl, Scratch& miss, U
 struct BatchUpdShape {
   int k;
   int64_t max_n, max_nkeys, max_cap, max_node_cap;
+  int R;      // common to the batch
+  bool half;  // the windowed form (work lists carry slot lists)
 };
 // record counts of the grids staged without a device count (-1: the grid's count word is already
 // written), passed by value to the first kernel
@@ -332,7 +346,7 @@ struct BatchCounts {
 cudaError_t launch_update_batch_ingest(const UpdArgs* d_args, const BatchUpdShape& s, const BatchCounts& counts,
                                        cudaStream_t st);
 cudaError_t launch_update_batch_mark(const UpdArgs* d_args, const BatchUpdShape& s, const Tuning& t, const Items& it,
-                                     cudaStream_t st);
+                                     const Fork& fk, cudaStream_t st);
 // slot lists of every queued run of a batch (each run's grid from it.igrid)
 cudaError_t launch_item_slots_batch(const GridView* views, const Tuning& t, const Items& it, int32_t* items_ctr,
                                     int item_cap, cudaStream_t st);

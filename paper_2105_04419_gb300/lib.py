@@ -40,7 +40,7 @@ class UpdateStats(ctypes.Structure):
     _fields_ = [("records", ctypes.c_int64), ("net_flips", ctypes.c_int64), ("changed_bricks", ctypes.c_int64),
                 ("x_items", ctypes.c_int64), ("y_items", ctypes.c_int64), ("z_items", ctypes.c_int64),
                 ("new_bricks", ctypes.c_int64), ("x_bricks", ctypes.c_int64), ("y_bricks", ctypes.c_int64),
-                ("z_bricks", ctypes.c_int64)]
+                ("z_bricks", ctypes.c_int64), ("global_form", ctypes.c_int64)]
 
 
 class PhaseTimes(ctypes.Structure):

@@ -141,3 +141,57 @@ def test_small_frames_in_large_grid():
         st = m.update(stats=True)
         ref = O.edt_factorised(occ, dmax)
         assert first_mismatch(m.export_dense(), ref) is None, (f, st)
+
+
+def _edit_fraction(rs, occ, f):
+    """The paper's ablation shape (Sec. V-A): remove a fraction f of the obstacles at random and add
+    as many new ones uniformly in the grid."""
+    nz, ny, nx = occ.shape
+    obs = np.argwhere(occ)
+    k = max(1, int(round(f * len(obs))))
+    rm = obs[rs.choice(len(obs), k, replace=False)][:, ::-1].astype(np.int32)
+    add = np.stack([rs.integers(0, nx, k), rs.integers(0, ny, k), rs.integers(0, nz, k)], 1).astype(np.int32)
+    xyz = np.concatenate([rm, add])
+    val = np.concatenate([np.zeros(k, np.uint8), np.ones(k, np.uint8)])
+    return xyz, val
+
+
+def test_switch_to_global_form_on_each_side():
+    """Small edits stay incremental, large ones switch to the global form on the device; both, and an
+    incremental frame after a switched one, equal Eq. 1."""
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(41)
+    occ = W.tunnel_scene(6, (200, 160, 96), ntunnels=6, rmin=5, rmax=12)
+    nz, ny, nx = occ.shape
+    m = V.Map(nx, ny, nz, 16)
+    m.set_occupancy_dense(occ)
+    m.global_()
+    for f, expect in ((0.0005, 0), (0.3, 1), (0.0005, 0), (0.05, 1)):
+        xyz, val = _edit_fraction(rs, occ, f)
+        for (x, y, z), v in zip(xyz, val):
+            occ[z, y, x] = v
+        m.set_occupancy(xyz, val)
+        st = m.update(stats=True)
+        assert st["global_form"] == expect, (f, st)
+        ref = O.edt_factorised(occ, 16)
+        assert first_mismatch(m.export_dense(), ref) is None, (f, first_mismatch(m.export_dense(), ref))
+
+
+def test_switch_inside_a_captured_update():
+    """One captured update replayed with a large frame (the device switches to the global form) and
+    then small frames (incremental): every replay equals Eq. 1."""
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(42)
+    occ = W.bernoulli_grid(42, (64, 96, 120), 0.01)
+    nz, ny, nx = occ.shape
+    m = V.Map(nx, ny, nz, 12)
+    m.set_occupancy_dense(occ)
+    m.global_()
+    g = V.UpdateGraph(m, 40000)
+    for f in (0.4, 0.001, 0.2, 0.0005):
+        xyz, val = _edit_fraction(rs, occ, f)
+        for (x, y, z), v in zip(xyz, val):
+            occ[z, y, x] = v
+        g.run(xyz, val)
+        ref = O.edt_factorised(occ, 12)
+        assert first_mismatch(m.export_dense(), ref) is None, (f, first_mismatch(m.export_dense(), ref))
