@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-clearance", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-crossover", action="store_true")
+    ap.add_argument("--shard", choices=["replicas", "slabs"], default="replicas",
+                    help="replicas: every rank transforms the whole scene; slabs: the scene's grid is split "
+                         "into z-slabs over the ranks (sparse halo exchange of band records)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work-item tuning")
     ap.add_argument("--frames", type=int, default=300, help="lidar frames of the incremental measurement")
     ap.add_argument("--incr-run", type=int, default=4, choices=(4, 8, 16),
@@ -724,6 +727,80 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_shard_slabs(args, wl, V, torch, dist, rank, world, local):
+    """One grid over the ranks: z-slabs (paper_2105_04419_gb300.slabs.SlabMap).  One step = every
+    rank's own global transform, export of its halo bands, the record exchange with its neighbours
+    (NCCL point-to-point), the staging of the neighbours' records and an incremental update.
+    value = active voxels of the whole grid / the slowest rank's step time (L2 flushed between
+    steps); bytes exchanged are reported per rank."""
+    import workloads as W
+    from paper_2105_04419_gb300 import slabs as S
+    nx, ny, nz = wl["dims"]
+    dmax = wl["dmax"]
+    occ = make_occupancy(wl)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sm = S.SlabMap(nx, ny, nz, dmax, rank, world, device=local, stream=stream)
+    z, y, x = np.nonzero(occ[sm.z0:sm.z1])
+    own = torch.from_numpy(np.stack([x, y, z + (sm.z0 - sm.h0)], 1).astype(np.int32)).cuda()
+    ones = torch.ones(own.shape[0], dtype=torch.uint8, device="cuda")
+    del occ
+    group = dist.group.WORLD if world > 1 else None
+
+    def step():
+        if world > 1:
+            sm.global_(own, ones, group=group)
+        else:
+            sm.finish(sm.begin_global(own, ones))
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = []
+    b0 = sm.bytes_sent
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(e))
+    if world > 1:
+        dist.barrier()
+    step_ms = max_over_ranks(statistics.mean(ms))
+    sent = (sm.bytes_sent - b0) / max(1, args.steps)
+    d = sm.owned_field()
+    nzo = d.shape[0]
+    bz, by, bx = -(-nzo // 8), -(-ny // 8), -(-nx // 8)
+    pad = torch.full((bz * 8, by * 8, bx * 8), dmax * dmax, dtype=torch.int32, device="cuda")
+    pad[:nzo, :ny, :nx] = d
+    act = torch.tensor([float((pad < dmax * dmax).view(bz, 8, by, 8, bx, 8).any(5).any(3).any(1).sum().item()) * 512],
+                       dtype=torch.float64, device="cuda")
+    per_rank = torch.tensor([float(sent), float(sm.h1 - sm.h0)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(act)
+        allr = [torch.zeros_like(per_rank) for _ in range(world)]
+        dist.all_gather(allr, per_rank)
+    else:
+        allr = [per_rank]
+    sm.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": act.item() / (step_ms / 1e3) / 1e6, "unit": "Mvoxels/s", "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": wl["name"], "parallelism": f"z-slabs x{world}",
+                           "step": "own global + band export + record exchange + incremental update of the halos",
+                           "l2": "flushed between timed steps (256 MiB write, untimed)"},
+                "shard": {"bytes_sent_per_step_per_rank": [r[0].item() for r in allr],
+                          "extended_planes_per_rank": [int(r[1].item()) for r in allr],
+                          "halo_planes": S.halo_planes(dmax)}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
@@ -746,6 +823,11 @@ def main():
             dist.barrier()
     import paper_2105_04419_gb300 as V
 
+    if args.shard == "slabs":
+        run_shard_slabs(args, wl, V, torch, dist, rank, world, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     occ = make_occupancy(wl)
     nx, ny, nz = wl["dims"]
     dmax = wl["dmax"]

@@ -173,6 +173,18 @@ vdbedt_status vdbedt_query_nearest(vdbedt_handle h, const int32_t* xyz, int64_t 
 /* The whole field as a dense int32 array out[nz][ny][nx] (host or device). */
 vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device);
 
+/* The occupancy of planes z_lo <= z < z_hi as packed records (the format of
+ * vdbedt_set_occupancy_packed) with z shifted by dz, into out (device, up to max_n records):
+ * mode 0: every occupied voxel (occ = 1); mode 1: every voxel, occupied or free, of the bricks that
+ * the last vdbedt_update changed (the bricks holding one of its flipped voxels).  Staged on another
+ * handle whose grid covers the shifted planes, they reproduce those planes' occupancy (mode 0 on an
+ * empty grid; mode 1 replays the update's changes).  This is how one grid split into z-slabs over
+ * several GPUs exchanges only the occupied voxels (or the changed bricks) of each slab's halo band.
+ * Synchronises; *n_out (host) receives the number of records; more than max_n is EOVERFLOW (the
+ * first max_n are written, *n_out holds the full count).  Record order is unspecified. */
+vdbedt_status vdbedt_export_occupancy(vdbedt_handle h, int32_t z_lo, int32_t z_hi, int32_t dz, int32_t mode,
+                                      uint64_t* out, int64_t max_n, int64_t* n_out);
+
 /* Clearance cost of Eq. 2 (second term) as a squared hinge, for T trajectories of P points.
  * pts: device float [T][P][3], metres; voxel centre (i, j, k) sits at (i, j, k) * voxel_size.
  * Per point: u = p / voxel_size (float32), cell i0 = floor(u) clamped to [0, n - 2] per axis,

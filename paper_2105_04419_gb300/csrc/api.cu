@@ -683,6 +683,36 @@ vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device) 
   return VDBEDT_OK;
 }
 
+vdbedt_status vdbedt_export_occupancy(vdbedt_handle h, int32_t z_lo, int32_t z_hi, int32_t dz, int32_t mode,
+                                      uint64_t* out, int64_t max_n, int64_t* n_out) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (!n_out || (max_n > 0 && !out) || max_n < 0 || (mode != 0 && mode != 1))
+    return fail(h, VDBEDT_EINVAL, "bad export arguments");
+  z_lo = std::max(z_lo, 0);
+  z_hi = std::min(z_hi, h->g.nz);
+  if (z_hi <= z_lo) {
+    *n_out = 0;
+    return VDBEDT_OK;
+  }
+  if ((int64_t)z_lo + dz < 0 || (int64_t)z_hi + dz > (int64_t)kBadCoord)
+    return fail(h, VDBEDT_EINVAL, "shifted z outside [0, 2^21 - 1)");
+  DeviceGuard guard(h->device);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(h->d_invalid + 2);
+  CK(h, launch_export_occupancy(h->g, h->changed, z_lo, z_hi, dz, mode, reinterpret_cast<unsigned long long*>(out),
+                                max_n, cnt, h->st),
+     "export occupancy");
+  s = device_errors(h);
+  if (s) return s;
+  CK(h, cudaMemcpyAsync(h->h_pinned + 48, cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->st), "d2h");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  unsigned long long c = 0;
+  memcpy(&c, h->h_pinned + 48, sizeof(c));
+  *n_out = (int64_t)c;
+  if ((int64_t)c > max_n) return fail(h, VDBEDT_EOVERFLOW, "more records than max_n (the count is in *n_out)");
+  return VDBEDT_OK;
+}
+
 vdbedt_status vdbedt_clearance_forward(vdbedt_handle h, const float* pts, int64_t T, int64_t P, float tau,
                                        float* cost) {
   vdbedt_status s = check_handle(h);

@@ -263,6 +263,66 @@ cudaError_t launch_count_flags(const GridView& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+namespace {
+// Occupancy of a z-range as packed records (x | y << 21 | (z + dz) << 42 | occ << 63): a warp per
+// brick (stored bricks, or the bricks the last update changed), a lane per two voxel rows of one
+// z-plane pair; records are appended with one atomic per warp per plane pair.  mode 0: occupied
+// voxels only (occ = 1); mode 1: every voxel of the brick in the range, occupied or not.
+__global__ void k_export_occupancy(GridView g, const int32_t* __restrict__ changed, int z_lo, int z_hi, int dz,
+                                   int mode, unsigned long long* __restrict__ out, int64_t max_n,
+                                   unsigned long long* __restrict__ count) {
+  const int nb = mode == 0 ? min(g.counters[C_NBRICKS], g.cap) : min(g.counters[C_CHANGED], g.cap);
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
+  for (int i = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); i < nb; i += nw) {
+    const int slot = mode == 0 ? i : changed[i];
+    const int4 c = g.bcoord[slot];
+    const int bz0 = 8 * c.z;
+    if (bz0 + 8 <= z_lo || bz0 >= z_hi) continue;  // warp-uniform
+    for (int zz = 0; zz < 8; ++zz) {
+      const int z = bz0 + zz;
+      if (z < z_lo || z >= z_hi) continue;  // warp-uniform
+      const unsigned long long word = g.occ[(size_t)slot * 8 + zz];  // bit x + 8 y
+      // lane: bits 2 lane, 2 lane + 1 of the plane
+      const int b0 = 2 * lane;
+      const int e0 = (int)((word >> b0) & 1ull), e1 = (int)((word >> (b0 + 1)) & 1ull);
+      // voxels of a brick that hangs over the grid's edge are not part of the grid
+      const int y = 8 * c.y + (b0 >> 3), x0 = 8 * c.x + (b0 & 7);
+      const bool in0 = x0 < g.nx && y < g.ny, in1 = x0 + 1 < g.nx && y < g.ny;
+      const int k0 = (mode == 0 ? e0 : 1) & (int)in0, k1 = (mode == 0 ? e1 : 1) & (int)in1;
+      const int mine = k0 + k1;
+      int incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total == 0) continue;
+      unsigned long long base = 0;
+      if (lane == 31) base = atomicAdd(count, (unsigned long long)total);
+      base = __shfl_sync(0xffffffffu, base, 31);
+      unsigned long long p = base + (unsigned long long)(incl - mine);
+      for (int q = 0; q < 2; ++q) {
+        if (!(q ? k1 : k0)) continue;
+        if ((int64_t)p < max_n)
+          out[p] = pack_rec(x0 + q, y, z + dz, q ? e1 : e0);
+        ++p;
+      }
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_export_occupancy(const GridView& g, const int32_t* changed, int z_lo, int z_hi, int dz, int mode,
+                                    unsigned long long* out, int64_t max_n, unsigned long long* count,
+                                    cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  VDB_LAUNCH(k_export_occupancy, 152 * 8, 256, 0, st, g, changed, z_lo, z_hi, dz, mode, out, max_n, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_export_dense(const GridView& g, int32_t* out, cudaStream_t st) {
   int64_t n = (int64_t)g.nx * g.ny * g.nz;
   VDB_LAUNCH(k_export_dense, grid_for(n, 256), 256, 0, st, g, out);

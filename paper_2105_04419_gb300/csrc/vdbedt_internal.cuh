@@ -392,6 +392,12 @@ cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32
 // out[3k .. 3k + 2]: nearest occupied voxel of query k (ties to the smallest (z, y, x)), or -1s
 cudaError_t launch_query_nearest(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st);
 cudaError_t launch_export_dense(const GridView& g, int32_t* out, cudaStream_t st);
+// occupancy of planes [z_lo, z_hi) as packed records with z shifted by dz (mode 0: occupied voxels
+// of every stored brick; mode 1: every voxel of the bricks in `changed`); *count = records found
+// (only the first max_n are written)
+cudaError_t launch_export_occupancy(const GridView& g, const int32_t* changed, int z_lo, int z_hi, int dz, int mode,
+                                    unsigned long long* out, int64_t max_n, unsigned long long* count,
+                                    cudaStream_t st);
 // obstacle and finite brick counts into counters C_OBST and C_FINITE
 cudaError_t launch_count_flags(const GridView& g, cudaStream_t st);
 cudaError_t launch_clearance_fwd(const GridView& g, float vs, const float* pts, int64_t T, int64_t P, float tau,

@@ -68,6 +68,7 @@ SIGNATURES = {
     "vdbedt_query": (ctypes.c_int, [_H, _P, _I64, _P, ctypes.c_int]),
     "vdbedt_query_nearest": (ctypes.c_int, [_H, _P, _I64, _P, ctypes.c_int]),
     "vdbedt_export_dense": (ctypes.c_int, [_H, _P, ctypes.c_int]),
+    "vdbedt_export_occupancy": (ctypes.c_int, [_H, _I32, _I32, _I32, _I32, _P, _I64, ctypes.POINTER(ctypes.c_int64)]),
     "vdbedt_clearance_forward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P]),
     "vdbedt_clearance_backward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P, _P]),
     "vdbedt_global_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _I32]),
@@ -341,6 +342,26 @@ class Map:
         _check(lib.vdbedt_export_dense(self._h, out.data_ptr(), 1), "vdbedt_export_dense", self._h)
         self._leave()
         return out
+
+    def export_occupancy(self, z_lo: int, z_hi: int, dz: int = 0, changed_only: bool = False, max_n: int = 0):
+        """Occupancy of planes [z_lo, z_hi) as packed 64-bit records (int64 CUDA tensor) with z
+        shifted by dz: every occupied voxel, or (changed_only) every voxel of the bricks the last
+        update changed.  Grows its buffer and retries once when max_n is too small."""
+        torch = _torch()
+        lib = load()
+        n = ctypes.c_int64(0)
+        cap = int(max_n) if max_n > 0 else 1 << 16
+        for _ in range(2):
+            out = torch.empty(cap, dtype=torch.int64, device=f"cuda:{self.device}")
+            self._enter(out)
+            st = lib.vdbedt_export_occupancy(self._h, int(z_lo), int(z_hi), int(dz), int(bool(changed_only)),
+                                             out.data_ptr(), cap, ctypes.byref(n))
+            if st == 5 and n.value > cap:  # EOVERFLOW: retry with room for every record
+                cap = int(n.value)
+                continue
+            _check(st, "vdbedt_export_occupancy", self._h)
+            return out[: n.value]
+        raise VdbedtError(5, "vdbedt_export_occupancy", "record count changed between attempts")
 
     def clearance_forward(self, pts, tau: float):
         torch = _torch()

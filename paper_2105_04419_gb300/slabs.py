@@ -9,6 +9,16 @@ one exchange no rank needs anything from another: there is no exchange of distan
 
 Only a neighbour's own planes are exchanged, so every owned slab must be at least H planes thick
 (slab_bounds checks this).
+
+Two forms of the exchange:
+  * dense (exchange_halos, sharded_global): uint8 planes, then a dense transform of the slab;
+  * sparse (SlabMap): each rank's map covers its extended slab; only records cross between ranks --
+    the occupied voxels of the H planes a neighbour holds as halo (global form: the rank transforms
+    its own obstacles, exports that band with vdbedt_export_occupancy, receives its neighbours'
+    bands and applies them with an incremental update), or every voxel of the bricks its last update
+    changed inside that band (incremental form: own edits -> update -> exchange -> a second, small
+    update).  The bytes exchanged follow the obstacles (or the changes) near the slab ends, not the
+    slab's volume, and the grid stays sparse on every rank.
 """
 from __future__ import annotations
 
@@ -96,3 +106,120 @@ def sharded_global(owned, rank: int, world: int, nz: int, dmax: int, group=None,
         return owned_part(m.export_dense(on_device=True), bounds, rank, dmax).clone()
     finally:
         m.close()
+
+
+def band_ranges(bounds: list, rank: int, dmax: int) -> dict:
+    """The planes of this rank's own range that each neighbour holds in its halo: {peer: (z_lo,
+    z_hi)} in grid z."""
+    h = halo_planes(dmax)
+    z0, z1 = bounds[rank]
+    out = {}
+    if rank > 0:
+        out[rank - 1] = (z0, min(z1, z0 + h))
+    if rank < len(bounds) - 1:
+        out[rank + 1] = (max(z0, z1 - h), z1)
+    return out
+
+
+def exchange_records(send: dict, rank: int, world: int, group=None) -> dict:
+    """Variable-length point-to-point exchange with the neighbours: send[peer] is a 1-D int64 tensor
+    (packed records) for each neighbour; returns {peer: received tensor}.  Counts go first, then the
+    payloads that are not empty.  CPU tensors for gloo, CUDA tensors for NCCL."""
+    import torch
+    import torch.distributed as dist
+    peers = [p for p in (rank - 1, rank + 1) if 0 <= p < world]
+    if not peers:
+        return {}
+    dev = next(iter(send.values())).device if send else torch.device("cpu")
+    n_out = {p: torch.tensor([int(send[p].numel())], dtype=torch.int64, device=dev) for p in peers}
+    n_in = {p: torch.zeros(1, dtype=torch.int64, device=dev) for p in peers}
+    ops = []
+    for p in peers:
+        ops.append(dist.P2POp(dist.isend, n_out[p], p, group))
+        ops.append(dist.P2POp(dist.irecv, n_in[p], p, group))
+    for req in dist.batch_isend_irecv(ops):
+        req.wait()
+    recv = {p: torch.empty(int(n_in[p].item()), dtype=torch.int64, device=dev) for p in peers}
+    ops = []
+    for p in peers:
+        if send[p].numel():
+            ops.append(dist.P2POp(dist.isend, send[p].contiguous(), p, group))
+        if recv[p].numel():
+            ops.append(dist.P2POp(dist.irecv, recv[p], p, group))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    return recv
+
+
+class SlabMap:
+    """One rank's share of a grid split into z-slabs, kept sparse: a Map of the rank's extended slab
+    (its own planes and H planes of halo each side; local z = grid z - h0).  The exchange is split
+    into begin_* (returns the records to send to each neighbour) and finish (applies the records
+    received), so that ranks can be emulated in one process; global_() / update() do both around a
+    torch.distributed exchange.  Records passed in are in local coordinates and must lie in the
+    rank's own planes; bytes_sent / bytes_received count the records exchanged."""
+
+    def __init__(self, nx: int, ny: int, nz: int, dmax: int, rank: int, world: int, device: int = 0, stream=None,
+                 max_bricks: int = 0, max_nodes: int = 0):
+        from .lib import Map
+        self.nz, self.dmax, self.rank, self.world = nz, dmax, rank, world
+        self.bounds = slab_bounds(nz, world, dmax)
+        self.h0, self.h1 = extended_range(self.bounds, rank, dmax)
+        self.z0, self.z1 = self.bounds[rank]
+        self.map = Map(nx, ny, self.h1 - self.h0, dmax, device=device, stream=stream, max_bricks=max_bricks,
+                       max_nodes=max_nodes)
+        self.bytes_sent = 0
+        self.bytes_received = 0
+
+    def close(self):
+        self.map.close()
+
+    def _stage(self, xyz=None, occ=None, packed=None):
+        if packed is not None:
+            self.map.set_occupancy_packed(packed)
+        if xyz is not None and len(xyz):
+            self.map.set_occupancy(xyz, occ)
+
+    def _sends(self, changed_only: bool) -> dict:
+        out = {}
+        for peer, (z_lo, z_hi) in band_ranges(self.bounds, self.rank, self.dmax).items():
+            peer_h0, _ = extended_range(self.bounds, peer, self.dmax)
+            out[peer] = self.map.export_occupancy(z_lo - self.h0, z_hi - self.h0, dz=self.h0 - peer_h0,
+                                                  changed_only=changed_only)
+            self.bytes_sent += 8 * out[peer].numel()
+        return out
+
+    def begin_global(self, xyz=None, occ=None, packed=None) -> dict:
+        """The rank's own occupancy (records in local coordinates) -> its own global transform; returns
+        the occupied voxels of each neighbour's halo band, in that neighbour's local coordinates."""
+        self.map.reset()
+        self._stage(xyz, occ, packed)
+        self.map.global_()
+        return self._sends(False)
+
+    def begin_update(self, xyz=None, occ=None, packed=None) -> dict:
+        """The rank's own edits (local coordinates) -> incremental update; returns every voxel of the
+        bricks that update changed inside each neighbour's halo band."""
+        self._stage(xyz, occ, packed)
+        self.map.update()
+        return self._sends(True)
+
+    def finish(self, received: dict):
+        """Apply the neighbours' records (halo planes) with an incremental update."""
+        for rec in received.values():
+            self.bytes_received += 8 * rec.numel()
+            if rec.numel():
+                self.map.set_occupancy_packed(rec)
+        self.map.update()
+
+    def global_(self, xyz=None, occ=None, packed=None, group=None):
+        self.finish(exchange_records(self.begin_global(xyz, occ, packed), self.rank, self.world, group))
+
+    def update(self, xyz=None, occ=None, packed=None, group=None):
+        self.finish(exchange_records(self.begin_update(xyz, occ, packed), self.rank, self.world, group))
+
+    def owned_field(self):
+        """D of the rank's own planes ([z1 - z0, ny, nx] int32 CUDA tensor)."""
+        d = self.map.export_dense(on_device=True)
+        return d[self.z0 - self.h0: self.z1 - self.h0]

@@ -116,3 +116,78 @@ def test_exchange_halos_gloo(world, shape, dmax):
     assert all(exact for _, exact, _ in got)
     occ = scene(world * 100 + dmax, shape)
     assert np.array_equal(np.concatenate([part for _, _, part in got], 0), O.edt_factorised(occ, dmax))
+
+
+def test_band_ranges_match_neighbour_halos():
+    for nz, world, dmax in ((256, 4, 32), (131, 3, 24), (72, 9, 5)):
+        b = S.slab_bounds(nz, world, dmax)
+        for r in range(world):
+            for peer, (z_lo, z_hi) in S.band_ranges(b, r, dmax).items():
+                h0, h1 = S.extended_range(b, peer, dmax)
+                z0, z1 = b[r]
+                # exactly the planes of this rank's own range that lie in the peer's extended slab
+                assert (z_lo, z_hi) == (max(z0, h0), min(z1, h1))
+
+
+def _exchange_main(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_2105_04419_gb300 import slabs as S_
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        def payload(src, dst):  # deterministic, of a size that may be 0
+            n = (7 * src + 3 * dst) % 5 * 1000
+            return torch.arange(n, dtype=torch.int64) * (src + 1) + dst
+        send = {p: payload(rank, p) for p in (rank - 1, rank + 1) if 0 <= p < world}
+        got = S_.exchange_records(send, rank, world)
+        ok = all(torch.equal(got[p], payload(p, rank)) for p in got) and set(got) == set(send)
+        q.put((rank, ok))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
+def test_exchange_records_gloo(world):
+    """Variable-length record exchange between neighbours (some payloads empty) over gloo ranks."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_exchange_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=180) for _ in range(world))
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert all(ok for _, ok in got)
+
+
+def test_sparse_protocol_oracle_emulation():
+    """The sparse slab protocol's arithmetic on CPU with the oracle: each rank holds its own obstacles
+    plus the neighbours' band obstacles (as the record exchange delivers them) in its extended slab;
+    after edits, each rank replays the neighbours' changed band voxels.  The owned parts, stacked,
+    equal the oracle on the whole grid, before and after the edits."""
+    rs = np.random.default_rng(5)
+    nz, ny, nx, world, dmax = 96, 20, 24, 3, 12
+    b = S.slab_bounds(nz, world, dmax)
+    occ = scene(77, (nz, ny, nx))
+    for frame in range(3):
+        if frame:
+            k = 400
+            pts = np.stack([rs.integers(0, nz, k), rs.integers(0, ny, k), rs.integers(0, nx, k)], 1)
+            occ[pts[:, 0], pts[:, 1], pts[:, 2]] = rs.integers(0, 2, k)
+        parts = []
+        for r in range(world):
+            h0, h1 = S.extended_range(b, r, dmax)
+            ext = np.zeros((h1 - h0, ny, nx), np.uint8)
+            z0, z1 = b[r]
+            ext[z0 - h0: z1 - h0] = occ[z0:z1]  # own planes
+            for peer in (r - 1, r + 1):
+                if 0 <= peer < world:
+                    lo, hi = S.band_ranges(b, peer, dmax)[r]  # what the peer sends to r
+                    ext[lo - h0: hi - h0] = occ[lo:hi]
+            parts.append(S.owned_part(O.edt_factorised(ext, dmax), b, r, dmax))
+        assert np.array_equal(np.concatenate(parts, 0), O.edt_factorised(occ, dmax)), frame
