@@ -55,15 +55,32 @@ typedef enum {
 /* Largest supported truncation: keeps dmax^2 = 32761 < 2^15 so stored intermediates fit 16 bits. */
 #define VDBEDT_DMAX_LIMIT 181
 
+/* Flags of vdbedt_config.
+ * VDBEDT_FLAG_UNBOUNDED: a grid without a fixed size that grows where records fall (the paper's
+ * motivation for a VDB-style tree, Sec. I and Sec. IV-A): nx, ny, nz are ignored; coordinates are
+ * signed, VDBEDT_UNBOUNDED_MIN <= x, y, z < VDBEDT_UNBOUNDED_MAX on every axis (about +-10^6
+ * voxels, +-105 km at 0.1 m), and interior nodes and bricks are created only where obstacles and
+ * their dilation reach, so max_bricks and max_nodes (both required) bound the memory.  Queries
+ * anywhere in that range answer dmax^2 where nothing is mapped.  Not available: the dense entry
+ * points (vdbedt_set_occupancy_dense, vdbedt_export_dense) and batches.  Packed records
+ * (vdbedt_set_occupancy_packed, vdbedt_export_occupancy) hold each coordinate plus
+ * VDBEDT_UNBOUNDED_OFFSET (non-negative).  The clearance query takes points in metres as usual
+ * (cells are found in float32: far from the origin the in-cell position is coarser). */
+#define VDBEDT_FLAG_UNBOUNDED 1u
+#define VDBEDT_UNBOUNDED_OFFSET (1 << 20)
+#define VDBEDT_UNBOUNDED_MIN (-(1 << 20))
+#define VDBEDT_UNBOUNDED_MAX ((1 << 20) - 128)
+
 typedef struct {
-  int32_t nx, ny, nz;  /* grid size in voxels, each >= 1 */
+  int32_t nx, ny, nz;  /* grid size in voxels, each >= 1 (at most 2^21 - 128; ignored when unbounded) */
   int32_t dmax;        /* truncation distance in voxels, 1 <= dmax <= VDBEDT_DMAX_LIMIT */
   float voxel_size;    /* metres per voxel (used by the clearance query), > 0 */
   int32_t device;      /* CUDA device ordinal */
   void* stream;        /* cudaStream_t to run on; NULL: the handle creates and owns one */
-  uint32_t flags;      /* reserved, 0 */
+  uint32_t flags;      /* 0 or VDBEDT_FLAG_UNBOUNDED */
   int64_t max_bricks;  /* brick capacity; 0: every brick of the grid (always enough) */
-  int64_t max_nodes;   /* interior-node capacity (a node covers 16^3 bricks); 0: every node of the grid */
+  int64_t max_nodes;   /* interior-node capacity (a node covers 16^3 bricks); 0: every node of the grid;
+                          at most 4,194,302 */
 } vdbedt_config;
 
 typedef struct {

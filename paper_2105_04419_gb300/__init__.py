@@ -27,6 +27,9 @@ from .lib import (  # noqa: F401
     global_batched,
     kernel_launches,
     pack_records,
+    UNBOUNDED_MAX,
+    UNBOUNDED_MIN,
+    UNBOUNDED_OFFSET,
     library_path,
     load,
 )

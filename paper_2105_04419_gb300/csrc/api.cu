@@ -25,7 +25,7 @@ static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, const int32_t* n_dev,
-                                int32_t* count_out, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
+                                int32_t* count_out, int nx, int ny, int nz, int off, rec_t* dst, int32_t* invalid,
                                 int32_t* counters, cudaStream_t st);
 cudaError_t launch_check_packed(const uint64_t* src, int64_t n, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
                                 int32_t* counters, cudaStream_t st);
@@ -222,7 +222,7 @@ vdbedt_status do_global(vdbedt_map* h) {
   CK(h, cudaMemsetAsync(h->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), h->st), "memset");
   if (h->stage_n > 0) {
     CK(h,
-       launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, nullptr, h->scr, h->vlast, h->miss,
+       launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, h->changed, h->scr, h->vlast, h->miss,
                              h->st),
        "ingest");
     clear_stage(h);
@@ -262,7 +262,14 @@ int64_t config_cap(const vdbedt_config* cfg) {
 
 vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbedt_map** out) {
   if (!cfg || !out) return fail(nullptr, VDBEDT_EINVAL, "null argument");
-  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, VDBEDT_EINVAL, "grid size must be >= 1");
+  const bool unbounded = (cfg->flags & VDBEDT_FLAG_UNBOUNDED) != 0;
+  if (cfg->flags & ~(uint32_t)VDBEDT_FLAG_UNBOUNDED) return fail(nullptr, VDBEDT_EINVAL, "unknown flags");
+  if (unbounded && slice) return fail(nullptr, VDBEDT_EINVAL, "a batch grid cannot be unbounded");
+  if (unbounded && (cfg->max_bricks <= 0 || cfg->max_nodes <= 0))
+    return fail(nullptr, VDBEDT_EINVAL, "an unbounded grid needs max_bricks and max_nodes");
+  const int64_t nx = unbounded ? kUnboundedSize : cfg->nx, ny = unbounded ? kUnboundedSize : cfg->ny,
+                nz = unbounded ? kUnboundedSize : cfg->nz;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, VDBEDT_EINVAL, "grid size must be >= 1");
   if (cfg->dmax < 1 || cfg->dmax > VDBEDT_DMAX_LIMIT) return fail(nullptr, VDBEDT_EINVAL, "dmax out of range");
   if (!(cfg->voxel_size > 0.f)) return fail(nullptr, VDBEDT_EINVAL, "voxel_size must be > 0");
   int ndev = 0;
@@ -270,22 +277,28 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
     cudaGetLastError();
     return fail(nullptr, VDBEDT_EINVAL, "no such CUDA device");
   }
-  const int64_t BX = ceil_div(cfg->nx, 8), BY = ceil_div(cfg->ny, 8), BZ = ceil_div(cfg->nz, 8);
-  if (cfg->nx >= kBadCoord || cfg->ny >= kBadCoord || cfg->nz >= kBadCoord || BX * BY * BZ >= (int64_t)0xFFFFFFFFll)
+  const int64_t BX = ceil_div(nx, 8), BY = ceil_div(ny, 8), BZ = ceil_div(nz, 8);
+  // node keys stay below 2^42 - 1 (16,383 nodes per axis at most) and brick keys of bounded grids
+  // fit 32 bits
+  if (nx > kUnboundedSize || ny > kUnboundedSize || nz > kUnboundedSize ||
+      (!unbounded && BX * BY * BZ >= (int64_t)0xFFFFFFFFll))
     return fail(nullptr, VDBEDT_EINVAL, "grid too large");
   const int64_t NX = ceil_div(BX, 16), NY = ceil_div(BY, 16), NZ = ceil_div(BZ, 16);
   int64_t cap = cfg->max_bricks > 0 ? std::min<int64_t>(cfg->max_bricks, BX * BY * BZ) : BX * BY * BZ;
   if (cap * 512 >= (int64_t)0xFFFFFFFFll) return fail(nullptr, VDBEDT_EINVAL, "brick capacity too large (max 8M)");
   const int64_t node_cap = cfg->max_nodes > 0 ? std::min<int64_t>(cfg->max_nodes, NX * NY * NZ) : NX * NY * NZ;
+  if (node_cap > kMaxNodes) return fail(nullptr, VDBEDT_EINVAL, "node capacity too large (max 4,194,302)");
 
   DeviceGuard guard(cfg->device);
   vdbedt_map* h = new vdbedt_map();
   h->cfg = *cfg;
   h->device = cfg->device;
   GridView& g = h->g;
-  g.nx = cfg->nx;
-  g.ny = cfg->ny;
-  g.nz = cfg->nz;
+  g.nx = (int)nx;
+  g.ny = (int)ny;
+  g.nz = (int)nz;
+  g.unbounded = unbounded ? 1 : 0;
+  g.off = unbounded ? kUnboundedOffset : 0;
   g.BX = (int)BX;
   g.BY = (int)BY;
   g.BZ = (int)BZ;
@@ -444,7 +457,7 @@ vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const ui
   if (s) return s;
   rec_t* dst = h->stage + h->stage_n;
   if (on_device) {
-    CK(h, launch_pack_records(xyz, occ, n, nullptr, nullptr, h->g.nx, h->g.ny, h->g.nz, dst, nullptr, h->g.counters,
+    CK(h, launch_pack_records(xyz, occ, n, nullptr, nullptr, h->g.nx, h->g.ny, h->g.nz, h->g.off, dst, nullptr, h->g.counters,
                               h->st), "pack");
   } else {
     // pack and validate on the device, then check before accepting.  Page-locked host arrays are
@@ -462,7 +475,7 @@ vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const ui
       docc = cocc;
     }
     CK(h, cudaMemsetAsync(h->d_invalid, 0, sizeof(int32_t), h->st), "memset");
-    CK(h, launch_pack_records(dxyz, docc, n, nullptr, nullptr, h->g.nx, h->g.ny, h->g.nz, dst, h->d_invalid,
+    CK(h, launch_pack_records(dxyz, docc, n, nullptr, nullptr, h->g.nx, h->g.ny, h->g.nz, h->g.off, dst, h->d_invalid,
                               h->g.counters, h->st),
        "pack");
     CK(h, cudaMemcpyAsync(h->h_pinned, h->d_invalid, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st), "d2h");
@@ -519,7 +532,7 @@ vdbedt_status vdbedt_set_occupancy_counted(vdbedt_handle h, const int32_t* xyz, 
   s = ensure_stage(h, n_max);
   if (s) return s;
   CK(h, reserve_ingest(h->g, n_max, h->scr, h->vlast, h->miss, h->st), "ingest scratch");
-  CK(h, launch_pack_records(xyz, occ, n_max, n_dev, h->d_count, h->g.nx, h->g.ny, h->g.nz, h->stage, nullptr,
+  CK(h, launch_pack_records(xyz, occ, n_max, n_dev, h->d_count, h->g.nx, h->g.ny, h->g.nz, h->g.off, h->stage, nullptr,
                               h->g.counters, h->st),
      "pack");
   h->stage_n = n_max;
@@ -531,6 +544,7 @@ vdbedt_status vdbedt_set_occupancy_dense(vdbedt_handle h, const uint8_t* grid, i
   vdbedt_status s = check_handle(h);
   if (s) return s;
   if (!grid) return fail(h, VDBEDT_EINVAL, "null grid");
+  if (h->g.unbounded) return fail(h, VDBEDT_EINVAL, "an unbounded grid has no dense form");
   DeviceGuard guard(h->device);
   s = vdbedt_reset(h);
   if (s) return s;
@@ -668,6 +682,7 @@ vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device) 
   vdbedt_status s = check_handle(h);
   if (s) return s;
   if (!out) return fail(h, VDBEDT_EINVAL, "null output");
+  if (h->g.unbounded) return fail(h, VDBEDT_EINVAL, "an unbounded grid has no dense form");
   DeviceGuard guard(h->device);
   size_t bytes = (size_t)h->g.nx * h->g.ny * h->g.nz * 4;
   if (on_device) {
@@ -689,8 +704,10 @@ vdbedt_status vdbedt_export_occupancy(vdbedt_handle h, int32_t z_lo, int32_t z_h
   if (s) return s;
   if (!n_out || (max_n > 0 && !out) || max_n < 0 || (mode != 0 && mode != 1))
     return fail(h, VDBEDT_EINVAL, "bad export arguments");
-  z_lo = std::max(z_lo, 0);
-  z_hi = std::min(z_hi, h->g.nz);
+  // caller z -> stored z (an unbounded grid's coordinates are stored shifted)
+  const int64_t zl = std::max<int64_t>((int64_t)z_lo + h->g.off, 0), zh = std::min<int64_t>((int64_t)z_hi + h->g.off, h->g.nz);
+  z_lo = (int32_t)zl;
+  z_hi = (int32_t)std::max<int64_t>(zh, zl);
   if (z_hi <= z_lo) {
     *n_out = 0;
     return VDBEDT_OK;
@@ -1403,7 +1420,7 @@ namespace {
 // count, clamped to [0, n], is copied to count_out for the ingest kernels, and a count outside that
 // range sets the invalid-record error bit.
 __global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* __restrict__ occ, int64_t n_max,
-                               const int32_t* n_dev, int32_t* count_out, int nx, int ny, int nz,
+                               const int32_t* n_dev, int32_t* count_out, int nx, int ny, int nz, int off,
                                rec_t* __restrict__ dst, int32_t* invalid, int32_t* counters) {
   int64_t n = n_max;
   if (n_dev) {
@@ -1424,7 +1441,7 @@ __global__ void k_pack_records(const int32_t* __restrict__ xyz, const uint8_t* _
     }
   };
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    put(i, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], occ[i]);
+    put(i, xyz[3 * i] + off, xyz[3 * i + 1] + off, xyz[3 * i + 2] + off, occ[i]);
 }
 
 // Packed records (x | y << 21 | z << 42 | occ << 63, the stage's own format): copied into the stage
@@ -1458,12 +1475,12 @@ cudaError_t launch_check_packed(const uint64_t* src, int64_t n, int nx, int ny, 
 }
 
 cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t n, const int32_t* n_dev,
-                                int32_t* count_out, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
+                                int32_t* count_out, int nx, int ny, int nz, int off, rec_t* dst, int32_t* invalid,
                                 int32_t* counters, cudaStream_t st) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
   if (b < 1) b = 1;
-  VDB_LAUNCH(k_pack_records, (unsigned)b, 256, 0, st, xyz, occ, n, n_dev, count_out, nx, ny, nz, dst, invalid,
+  VDB_LAUNCH(k_pack_records, (unsigned)b, 256, 0, st, xyz, occ, n, n_dev, count_out, nx, ny, nz, off, dst, invalid,
              counters);
   return cudaGetLastError();
 }

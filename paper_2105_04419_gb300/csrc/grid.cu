@@ -382,17 +382,17 @@ __global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, 
 
 // A node absent from the table and inserted by exactly one thread, at index idx: its key, then a
 // hash slot claimed with the final word (read by later kernels: the kernel boundary orders both).
-__device__ void insert_new_node(const GridView& g, uint32_t key, int idx) {
+__device__ void insert_new_node(const GridView& g, unsigned long long key, int idx) {
   if (idx >= g.node_cap) {
     set_error(g, kErrNodeOverflow);
     return;
   }
-  g.node_key[idx] = (int32_t)key;
-  const unsigned long long word = ((unsigned long long)key << 32) | (uint32_t)idx;
-  uint32_t h = hash32(key) & g.hmask;
+  g.node_key[idx] = (long long)key;
+  const unsigned long long word = (key << kIndexBits) | (uint32_t)idx;
+  uint32_t h = hash_key(key) & g.hmask;
   bool placed = false;
   for (uint32_t probe = 0; probe <= g.hmask && !placed; ++probe) {
-    placed = atomicCAS(&g.hslots[h], ~0ull, word) == ~0ull;
+    placed = atomicCAS(&g.hslots[h], kEmptySlot, word) == kEmptySlot;
     h = (h + 1) & g.hmask;
   }
   if (!placed) set_error(g, kErrNodeOverflow);
@@ -407,10 +407,10 @@ __device__ __forceinline__ void create_flagged_nodes(const GridView& g, int32_t*
     bool need = false;
     if (k < nkeys && nflag[k]) {
       nflag[k] = 0;
-      need = find_node(g, (uint32_t)k) < 0;
+      need = find_node(g, (unsigned long long)k) < 0;
     }
     const int idx = block_agg_add(&g.counters[C_NNODES], need, nullptr);
-    if (need) insert_new_node(g, (uint32_t)k, idx);
+    if (need) insert_new_node(g, (unsigned long long)k, idx);
   }
 }
 
@@ -439,7 +439,8 @@ __global__ void k_compact_flag_index(GridView g, const int32_t* __restrict__ fla
     int nk = -1;
     if (i < n && flag[i]) {
       const uint32_t lb = (uint32_t)i, rest = lb / (uint32_t)g.BX;
-      nk = node_key_of(g, (int)(lb - rest * (uint32_t)g.BX), (int)(rest % (uint32_t)g.BY), (int)(rest / (uint32_t)g.BY));
+      nk = (int)node_key_of(g, (int)(lb - rest * (uint32_t)g.BX), (int)(rest % (uint32_t)g.BY),
+                            (int)(rest / (uint32_t)g.BY));
     }
     const unsigned set = __ballot_sync(0xffffffffu, nk >= 0);
     int base = 0;
@@ -484,7 +485,7 @@ __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__
       int rest = (int)(lb / (uint32_t)g.BX);
       by = rest % g.BY;
       bz = rest / g.BY;
-      node = get_or_create_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+      node = get_or_create_node(g, node_key_of(g, bx, by, bz));
       if (node >= 0) {
         e = &g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
         need = *e == kNoSlot;
@@ -589,12 +590,13 @@ __global__ void k_rec_missing(US us) {
         bad = true;
       } else if (r.w == 1) {
         const int bx = r.x >> 3, by = r.y >> 3, bz = r.z >> 3;
-        const int nk = node_key_of(g, bx, by, bz);
-        const int node = find_node(g, (uint32_t)nk);
+        const unsigned long long nk = node_key_of(g, bx, by, bz);
+        // an unbounded grid has no per-key flags: its nodes are created here, by the records
+        const int node = A.nflag ? find_node(g, nk) : get_or_create_node(g, nk);
         if (node >= 0) {
           if (g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] < 0)
             list_missing_brick(g, node, bx, by, bz, A.list);
-        } else if (!DEFERRED && !A.nflag[nk]) {
+        } else if (!DEFERRED && A.nflag && !A.nflag[nk]) {
           A.nflag[nk] = 1;
           atomicOr(&g.counters[C_DEFERRED], 1);
         }
@@ -629,7 +631,7 @@ __global__ void k_alloc_listed(US us) {
     bool need = false;
     if (j < cnt) {
       unpack_brick(list[j], bx, by, bz);
-      node = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+      node = find_node(g, node_key_of(g, bx, by, bz));
       if (node >= 0) {
         const int l = local_brick(bx, by, bz);
         atomicAnd(&g.nclaim[(size_t)node * 128 + (l >> 5)], ~(1u << (l & 31)));
@@ -876,10 +878,10 @@ __global__ void __launch_bounds__(256) k_dense_nodes(VS vs, DenseScratch ds) {
     bool need = false;
     if (k < nkeys && nflag[k]) {
       nflag[k] = 0;
-      need = find_node(g, (uint32_t)k) < 0;
+      need = find_node(g, (unsigned long long)k) < 0;
     }
     const int idx = block_agg_add(&g.counters[C_NNODES], need, nullptr);
-    if (need) insert_new_node(g, (uint32_t)k, idx);
+    if (need) insert_new_node(g, (unsigned long long)k, idx);
   }
 }
 
@@ -900,7 +902,7 @@ __global__ void __launch_bounds__(256) k_dense_alloc(VS vs, DenseScratch ds) {
       bx = (int)(l - r * (uint32_t)g.BX);
       by = (int)(r % (uint32_t)g.BY);
       bz = (int)(r / (uint32_t)g.BY);
-      node = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+      node = find_node(g, node_key_of(g, bx, by, bz));
     }
     int total = 0;
     const int slot = block_agg_add(&g.counters[C_NBRICKS], node >= 0, &total);
@@ -984,8 +986,8 @@ __global__ void k_node_halo(VS vs) {
     const uint32_t* om = g.mwork + (size_t)node * 384;
     uint32_t any = om[lane] | om[lane + 32] | om[lane + 64] | om[lane + 96];
     if (!__any_sync(0xffffffffu, any != 0u)) continue;
-    const int key = g.node_key[node];
-    const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+    int nxn, nyn, nzn;
+    node_coords(g, (unsigned long long)g.node_key[node], nxn, nyn, nzn);
     uint32_t dirs = 0xFFFFFFFFu;  // directions o = (dx + 1) + 3 (dy + 1) + 9 (dz + 1) to create
     if (NR == 1) {
       const uint32_t lo = g.R >= 16 ? 0xFFFFu : ((1u << g.R) - 1u), hi = (lo << (16 - g.R)) & 0xFFFFu;
@@ -1009,7 +1011,7 @@ __global__ void k_node_halo(VS vs) {
       const int dx = o % side - NR, dy = (o / side) % side - NR, dz = o / (side * side) - NR;
       const int x = nxn + dx, y = nyn + dy, z = nzn + dz;
       if (x < 0 || y < 0 || z < 0 || x >= g.NX || y >= g.NY || z >= g.NZ || (dx == 0 && dy == 0 && dz == 0)) continue;
-      if (NR > 1 || ((dirs >> o) & 1u)) get_or_create_node(g, (uint32_t)(x + g.NX * (y + g.NY * z)));
+      if (NR > 1 || ((dirs >> o) & 1u)) get_or_create_node(g, node_key_at(g, x, y, z));
     }
   }
 }
@@ -1017,7 +1019,7 @@ __global__ void k_node_halo(VS vs) {
 
 __device__ __forceinline__ int node_at(const GridView& g, int x, int y, int z) {
   if (x < 0 || y < 0 || z < 0 || x >= g.NX || y >= g.NY || z >= g.NZ) return -1;
-  return find_node(g, (uint32_t)(x + g.NX * (y + g.NY * z)));
+  return find_node(g, node_key_at(g, x, y, z));
 }
 
 // Stage 0 -> 1: dilate each x-row by R across the neighbouring nodes along x.
@@ -1035,8 +1037,8 @@ __global__ void k_dilate_stage(VS vs) {
   for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < (int64_t)nn * 128;
        i += (int64_t)nblk * blockDim.x) {
     const int node = (int)(i >> 7), w = (int)(i & 127);
-    const int key = g.node_key[node];
-    const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+    int nxn, nyn, nzn;
+    node_coords(g, (unsigned long long)g.node_key[node], nxn, nyn, nzn);
     const int z = w >> 3;
     uint32_t out = 0u;
     for (int half = 0; half < 2; ++half) {
@@ -1107,8 +1109,8 @@ __global__ void __launch_bounds__(256) k_dilate_nodes(VS vs) {
   const int nn = min(g.counters[C_NNODES], g.node_cap);
   const int R = g.R;
   for (int node = bid; node < nn; node += nblk) {
-    const int key = g.node_key[node];
-    const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+    int nxn, nyn, nzn;
+    node_coords(g, (unsigned long long)g.node_key[node], nxn, nyn, nzn);
     if (threadIdx.x < 27) {
       const int t = threadIdx.x, dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
       nbr[t] = (dx | dy | dz) == 0 ? node : node_at(g, nxn + dx, nyn + dy, nzn + dz);
@@ -1176,7 +1178,7 @@ __device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int
   int x0 = max(bx - R, 0), x1 = min(bx + R, g.BX - 1);
   while (x0 <= x1) {
     int seg_end = min(x1, (x0 | 15));
-    int node = get_or_create_node(g, (uint32_t)node_key_of(g, x0, y, z));
+    int node = get_or_create_node(g, node_key_of(g, x0, y, z));
     if (node >= 0) {
       int lx0 = x0 & 15, lx1 = seg_end & 15;
       uint32_t bitsx = ((1u << (lx1 - lx0 + 1)) - 1u) << lx0;
@@ -1209,8 +1211,8 @@ __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
       if (slot >= g.cap) {
         set_error(g, kErrOverflow);
       } else {
-        const int key = g.node_key[node];
-        const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+        int nxn, nyn, nzn;
+        node_coords(g, (unsigned long long)g.node_key[node], nxn, nyn, nzn);
         init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8), init_fields);
         g.child[(size_t)node * kNodeBricks + l] = slot;
       }
@@ -1245,8 +1247,8 @@ __global__ void __launch_bounds__(256) k_alloc_fresh(US us) {
       if (slot >= g.cap) {
         set_error(g, kErrOverflow);
       } else {
-        const int key = g.node_key[node];
-        const int nxn = key % g.NX, nyn = (key / g.NX) % g.NY, nzn = key / (g.NX * g.NY);
+        int nxn, nyn, nzn;
+        node_coords(g, (unsigned long long)g.node_key[node], nxn, nyn, nzn);
         init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8), true);
         g.child[(size_t)node * kNodeBricks + l] = slot;
       }
@@ -1294,8 +1296,8 @@ __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int 
     const int node = b / 12, axis = (b % 12) / 4, qrun = b % 4;
     const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
     if (qrun >= 16 / run) continue;  // block-uniform
-    const int key = g.node_key[node];
-    const int q[3] = {key % g.NX, (key / g.NX) % g.NY, key / (g.NX * g.NY)};
+    int q[3];
+    node_coords(g, (unsigned long long)g.node_key[node], q[0], q[1], q[2]);
     const int32_t* ch = g.child + (size_t)node * kNodeBricks;
     const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
     const int r0 = qrun * run, nb = run + 2 * R;
@@ -1304,7 +1306,7 @@ __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int 
       qq[axis] += threadIdx.x == 0 ? -1 : 1;
       int n2 = -1;
       if (qq[0] >= 0 && qq[1] >= 0 && qq[2] >= 0 && qq[0] < g.NX && qq[1] < g.NY && qq[2] < g.NZ)
-        n2 = find_node(g, (uint32_t)(qq[0] + g.NX * (qq[1] + g.NY * qq[2])));
+        n2 = find_node(g, node_key_at(g, qq[0], qq[1], qq[2]));
       nbr_sh[threadIdx.x] = n2;
     }
     const int o1 = threadIdx.x & 15, o2 = threadIdx.x >> 4;
@@ -1405,7 +1407,7 @@ __device__ __forceinline__ void run_slots(const GridView& g, int axis, int run, 
     const int qa = (ba >> 4) + lane - 1;
     if (qa >= 0 && qa < NQa) {
       const int qx = axis == 0 ? qa : bx >> 4, qy = axis == 1 ? qa : by >> 4, qz = axis == 2 ? qa : bz >> 4;
-      nq = find_node(g, (uint32_t)(qx + g.NX * (qy + g.NY * qz)));
+      nq = find_node(g, node_key_at(g, qx, qy, qz));
     }
   }
   const int n_lo = __shfl_sync(0xffffffffu, nq, 0), n_mid = __shfl_sync(0xffffffffu, nq, 1),
@@ -1501,7 +1503,7 @@ __global__ void k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
     int4 c = g.bcoord[s];
     int bx = c.x + dx, by = c.y + dy, bz = c.z + dz;
     if ((unsigned)bx >= (unsigned)g.BX || (unsigned)by >= (unsigned)g.BY || (unsigned)bz >= (unsigned)g.BZ) continue;
-    int node = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+    int node = find_node(g, node_key_of(g, bx, by, bz));
     if (node < 0) continue;
     const int slot = g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
     if (slot < 0) continue;
@@ -1631,10 +1633,11 @@ static cudaError_t ensure_vlast(const GridView& g, Scratch& vl, cudaStream_t st)
 }
 
 // The tracked ingest's scratch: node-key flags (zero between updates), the list of missing bricks.
-static size_t tracked_bytes(const GridView& g) {
-  const size_t nkeys = (size_t)g.NX * g.NY * g.NZ;
-  return align_up(nkeys * 4) + align_up((size_t)g.cap * 8);
+// node-key flags (none for an unbounded grid), then the missing-brick list
+static size_t tracked_flag_bytes(const GridView& g) {
+  return g.unbounded ? 0 : align_up((size_t)g.NX * g.NY * g.NZ * 4);
 }
+static size_t tracked_bytes(const GridView& g) { return tracked_flag_bytes(g) + align_up((size_t)g.cap * 8); }
 
 static cudaError_t ensure_tracked(const GridView& g, Scratch& miss, cudaStream_t st) {
   const size_t want = tracked_bytes(g);
@@ -1646,7 +1649,7 @@ static cudaError_t ensure_tracked(const GridView& g, Scratch& miss, cudaStream_t
 
 cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  cudaError_t e = ensure_scratch(scr, ingest_scratch_bytes(g, n, false));
+  cudaError_t e = g.unbounded ? cudaSuccess : ensure_scratch(scr, ingest_scratch_bytes(g, n, false));
   if (e != cudaSuccess) return e;
   e = ensure_tracked(g, miss, st);
   if (e != cudaSuccess) return e;
@@ -1665,14 +1668,15 @@ cudaError_t prepare_update_args(const GridView& g, Scratch& vl, Scratch& miss, U
   if (e != cudaSuccess) return e;
   e = ensure_vlast(g, vl, st);
   if (e != cudaSuccess) return e;
-  const size_t nkeys = (size_t)g.NX * g.NY * g.NZ;
   char* p = (char*)miss.buf;
-  a.nflag = (int32_t*)p;
-  a.list = (unsigned long long*)(p + align_up(nkeys * 4));
+  a.nflag = g.unbounded ? nullptr : (int32_t*)p;
+  a.list = (unsigned long long*)(p + tracked_flag_bytes(g));
   a.vlast = (int32_t*)vl.buf;
   return cudaSuccess;
 }
 
+// The tracked ingest: with `track` (an incremental update) each flipped voxel's brick joins the
+// changed list once; unbounded grids take this path for the global form too (no brick-key sort).
 static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev,
                                          int32_t* changed, Scratch& vl, Scratch& miss, cudaStream_t st) {
   UpdArgs a{};
@@ -1683,13 +1687,13 @@ static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, in
   a.changed = changed;
   cudaError_t e = prepare_update_args(g, vl, miss, a, st);
   if (e != cudaSuccess) return e;
-  return update_ingest_kernels(UpdOne{a}, 1, n, (int64_t)g.NX * g.NY * g.NZ, g.cap, st);
+  return update_ingest_kernels(UpdOne{a}, 1, n, g.unbounded ? 1 : (int64_t)g.NX * g.NY * g.NZ, g.cap, st);
 }
 
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
                                   int32_t* changed, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  if (track) return launch_ingest_tracked(g, rec, n, n_dev, changed, vl, miss, st);
+  if (track || g.unbounded) return launch_ingest_tracked(g, rec, n, n_dev, changed, vl, miss, st);
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
   const bool counting = n >= nbr_all / 4;
   // the dense mask is indexed by a 32-bit word number (8 words per brick)

@@ -771,8 +771,8 @@ __global__ void k_wait_selftest(GridView g, int which) {
     mbar_init(&bar, 1);
     mbar_wait_bounded(g, &bar, 0);
   } else {
-    const uint32_t key = 0;
-    g.hslots[hash32(key) & g.hmask] = ((unsigned long long)key << 32) | kPending;
+    const unsigned long long key = 0;
+    g.hslots[hash_key(key) & g.hmask] = (key << kIndexBits) | kPending;
     get_or_create_node(g, key);
   }
 }

@@ -25,9 +25,10 @@ __device__ __forceinline__ int sqdist_at(const GridView& g, int x, int y, int z)
   return g.dist[(size_t)s * kBrickVox + (x & 7) + 8 * (y & 7) + 64 * (z & 7)];
 }
 
+// caller coordinates are stored shifted by g.off (an unbounded grid's signed coordinates)
 __global__ void k_query(GridView g, const int32_t* __restrict__ xyz, int64_t n, int32_t* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = sqdist_at(g, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
+    out[i] = sqdist_at(g, xyz[3 * i] + g.off, xyz[3 * i + 1] + g.off, xyz[3 * i + 2] + g.off);
 }
 
 // One warp per x-row of a brick-aligned 8-voxel segment: lanes cover 32 consecutive x.
@@ -63,8 +64,8 @@ __global__ void k_query_nearest(GridView g, const int32_t* __restrict__ xyz, int
   for (int v = threadIdx.x; v <= g.INF; v += blockDim.x) isq[v] = (uint8_t)isqrt_floor(v);
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-    int rx = -1, ry = -1, rz = -1;
+    const int x = xyz[3 * i] + g.off, y = xyz[3 * i + 1] + g.off, z = xyz[3 * i + 2] + g.off;
+    int rx = -1 + g.off, ry = -1 + g.off, rz = -1 + g.off;
     const int D = sqdist_at(g, x, y, z);
     if ((unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz && D < g.INF) {
       bool found = false;
@@ -86,9 +87,9 @@ __global__ void k_query_nearest(GridView g, const int32_t* __restrict__ xyz, int
       }
       if (!found) set_error(g, kErrInternal);  // a finite D always has an obstacle on its sphere
     }
-    out[3 * i] = rx;
-    out[3 * i + 1] = ry;
-    out[3 * i + 2] = rz;
+    out[3 * i] = rx - g.off;  // (-1, -1, -1) when there is none
+    out[3 * i + 1] = ry - g.off;
+    out[3 * i + 2] = rz - g.off;
   }
 }
 
@@ -101,12 +102,14 @@ __device__ __forceinline__ void cell_of(const GridView& g, float vs, float px, f
                                         int& k0, float& tx, float& ty, float& tz) {
   float ux = px / vs, uy = py / vs, uz = pz / vs;
   float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
-  i0 = (int)fminf(fmaxf(fx, 0.f), (float)(g.nx - 2));
-  j0 = (int)fminf(fmaxf(fy, 0.f), (float)(g.ny - 2));
-  k0 = (int)fminf(fmaxf(fz, 0.f), (float)(g.nz - 2));
-  tx = ux - (float)i0;
-  ty = uy - (float)j0;
-  tz = uz - (float)k0;
+  // cells in stored coordinates (shifted by g.off); t measured from the cell in caller coordinates
+  const float o = (float)g.off;
+  i0 = (int)fminf(fmaxf(fx + o, 0.f), (float)(g.nx - 2));
+  j0 = (int)fminf(fmaxf(fy + o, 0.f), (float)(g.ny - 2));
+  k0 = (int)fminf(fmaxf(fz + o, 0.f), (float)(g.nz - 2));
+  tx = ux - (float)(i0 - g.off);
+  ty = uy - (float)(j0 - g.off);
+  tz = uz - (float)(k0 - g.off);
 }
 
 __device__ __forceinline__ void corners(const GridView& g, float vs, int i0, int j0, int k0, Corner8& c) {

@@ -3,7 +3,8 @@
 // Sparse grid layout in device memory (paper Sec. IV-A: a shallow, wide tree with a hashed top
 // level, directly indexed lower levels and a background tile value):
 //   level 1  hash table of interior nodes (open addressing, linear probing); a node covers
-//            16^3 bricks = 128^3 voxels; slot word = (node key << 32) | node index
+//            16^3 bricks = 128^3 voxels; node key = nx + NX (ny + NY nz) of the node's coordinates
+//            (below 2^42); slot word = (node key << 22) | node index (all ones: empty)
 //   level 2  per node a dense table of 4096 child slots (int32; -1 = background tile dmax^2)
 //            plus a 4096-bit mask of bricks in the compute set
 //   leaves   8^3-voxel bricks in a pool indexed by slot:
@@ -17,14 +18,22 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/vdbedt.h"
+
 namespace vdbedt {
 
 constexpr int kBrick = 8;
 constexpr int kBrickVox = 512;
 constexpr int kNodeB = 16;  // bricks per node edge
 constexpr int kNodeBricks = kNodeB * kNodeB * kNodeB;
-constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
-constexpr uint32_t kPending = 0xFFFFFFFFu;
+constexpr unsigned long long kEmptySlot = ~0ull;
+constexpr int kIndexBits = 22;
+constexpr uint32_t kPending = (1u << kIndexBits) - 1u;  // index field of a claimed, unpublished slot
+constexpr int kMaxNodes = (1 << kIndexBits) - 2;
+// Unbounded grids: coordinates in [-kUnboundedOffset, kUnboundedOffset - 128) on every axis, stored
+// shifted by kUnboundedOffset (node coordinates 0 .. 16382, keys below 2^42 - 1).
+constexpr int kUnboundedOffset = VDBEDT_UNBOUNDED_OFFSET;
+constexpr int kUnboundedSize = VDBEDT_UNBOUNDED_MAX + VDBEDT_UNBOUNDED_OFFSET;
 constexpr int32_t kNoSlot = -1;
 
 // device error bits
@@ -72,6 +81,8 @@ struct GridView {
   int dmax, R, INF;   // truncation, brick radius of influence, dmax^2
   int half;           // 1: g1 / g2 hold fp16 bit patterns (windowed kernels, dmax <= 45); 0: 16-bit
                       // integers (lower-envelope kernels)
+  int off;            // added to caller coordinates (0; kUnboundedOffset for an unbounded grid)
+  int unbounded;      // 1: no per-node-key arrays (nodes are created where records fall)
   uint32_t hmask;     // hash capacity - 1
   int cap;            // brick capacity
   int node_cap;       // node capacity
@@ -82,7 +93,7 @@ struct GridView {
   uint32_t* afresh;   // [node_cap * 4] bit w of the node's 4 words: amask word w got bits this update
   int32_t* flist;     // [node_cap * 128] node * 128 + word of those words (C_FRESH of them)
   uint32_t* nclaim;   // [node_cap * 128] bricks listed for allocation by the running ingest (amask layout)
-  int32_t* node_key;  // [node_cap]
+  long long* node_key;  // [node_cap]
   int32_t* mark;      // [node_cap * 3 * 1024] epoch of the last time each run along axis a was queued
   unsigned long long* occ;  // [cap * 8]
   uint16_t* g1;       // [cap * 512]
@@ -101,8 +112,19 @@ struct GridView {
   int32_t* items_ctr; // [3] items queued along x, y, z (the grid's counters, or the batch's)
 };
 
-__host__ __device__ inline int node_key_of(const GridView& g, int bx, int by, int bz) {
-  return (bx >> 4) + g.NX * ((by >> 4) + g.NY * (bz >> 4));
+__host__ __device__ inline unsigned long long node_key_of(const GridView& g, int bx, int by, int bz) {
+  return (unsigned long long)(bx >> 4) +
+         (unsigned long long)g.NX * ((unsigned long long)(by >> 4) + (unsigned long long)g.NY * (unsigned long long)(bz >> 4));
+}
+// node coordinates of a key
+__host__ __device__ inline void node_coords(const GridView& g, unsigned long long key, int& x, int& y, int& z) {
+  x = (int)(key % (unsigned long long)g.NX);
+  const unsigned long long r = key / (unsigned long long)g.NX;
+  y = (int)(r % (unsigned long long)g.NY);
+  z = (int)(r / (unsigned long long)g.NY);
+}
+__host__ __device__ inline unsigned long long node_key_at(const GridView& g, int x, int y, int z) {
+  return (unsigned long long)x + (unsigned long long)g.NX * ((unsigned long long)y + (unsigned long long)g.NY * (unsigned long long)z);
 }
 
 __device__ __forceinline__ uint32_t hash32(uint32_t k) {
@@ -112,6 +134,10 @@ __device__ __forceinline__ uint32_t hash32(uint32_t k) {
   k *= 0x846ca68bu;
   k ^= k >> 16;
   return k;
+}
+// slot of a 64-bit node key: the high word folded into the low one before the 32-bit mix
+__device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
+  return hash32((uint32_t)k ^ hash32((uint32_t)(k >> 32) + 0x9e3779b9u));
 }
 
 __device__ __forceinline__ void set_error(const GridView& g, int bits) { atomicOr(&g.counters[C_ERR], bits); }
@@ -129,16 +155,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Node index for node key, or -1 when the node is absent.  Readers never wait: a node whose
 // insertion is still pending is absent for them (inserts happen in kernels that do not read the
 // node's bricks).
-__device__ __forceinline__ int find_node(const GridView& g, uint32_t key) {
-  uint32_t h = hash32(key) & g.hmask;
+__device__ __forceinline__ int find_node(const GridView& g, unsigned long long key) {
+  uint32_t h = hash_key(key) & g.hmask;
   for (uint32_t probe = 0; probe <= g.hmask; ++probe) {
-    unsigned long long w = g.hslots[h];
-    uint32_t k = (uint32_t)(w >> 32);
-    if (k == key) {
-      uint32_t v = (uint32_t)w;
+    const unsigned long long w = g.hslots[h];
+    if (w == kEmptySlot) return -1;
+    if ((w >> kIndexBits) == key) {
+      const uint32_t v = (uint32_t)(w & kPending);
       return v == kPending ? -1 : (int)v;
     }
-    if (k == kEmptyKey) return -1;
     h = (h + 1) & g.hmask;
   }
   return -1;
@@ -147,35 +172,33 @@ __device__ __forceinline__ int find_node(const GridView& g, uint32_t key) {
 // Find or insert the node with this key.  The inserting thread claims the hash slot with a
 // pending marker, allocates the node index, then publishes it; other inserters of the same key
 // wait for publication with a bounded spin (error bit on give-up).
-__device__ inline int get_or_create_node(const GridView& g, uint32_t key) {
-  uint32_t h = hash32(key) & g.hmask;
+__device__ inline int get_or_create_node(const GridView& g, unsigned long long key) {
+  uint32_t h = hash_key(key) & g.hmask;
   for (uint32_t probe = 0; probe <= g.hmask; ++probe) {
     unsigned long long w = g.hslots[h];
-    uint32_t k = (uint32_t)(w >> 32);
-    if (k == kEmptyKey) {
-      unsigned long long want = ((unsigned long long)key << 32) | kPending;
-      unsigned long long old = atomicCAS(&g.hslots[h], w, want);
+    if (w == kEmptySlot) {
+      const unsigned long long want = (key << kIndexBits) | kPending;
+      const unsigned long long old = atomicCAS(&g.hslots[h], w, want);
       if (old == w) {
         int idx = atomicAdd(&g.counters[C_NNODES], 1);
         if (idx >= g.node_cap) {
           set_error(g, kErrNodeOverflow);
           return -1;
         }
-        g.node_key[idx] = (int32_t)key;
+        g.node_key[idx] = (long long)key;
         __threadfence();
-        atomicExch(&g.hslots[h], ((unsigned long long)key << 32) | (uint32_t)idx);
+        atomicExch(&g.hslots[h], (key << kIndexBits) | (uint32_t)idx);
         return idx;
       }
       w = old;
-      k = (uint32_t)(w >> 32);
     }
-    if (k == key) {
-      if ((uint32_t)w != kPending) return (int)(uint32_t)w;  // published: no atomic needed
+    if ((w >> kIndexBits) == key) {
+      if ((uint32_t)(w & kPending) != kPending) return (int)(w & kPending);  // published: no atomic needed
       const unsigned long long t0 = global_ns();
       for (uint32_t spin = 0; spin < kWaitMaxPolls; ++spin) {
         // plain (volatile) reads while waiting: they do not queue behind the publishing exchange
-        unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&g.hslots[h]);
-        uint32_t v = (uint32_t)cur;
+        const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&g.hslots[h]);
+        const uint32_t v = (uint32_t)(cur & kPending);
         if (v != kPending) return (int)v;
         if ((spin & 63u) == 63u && global_ns() - t0 > kWaitLimitNs) break;
         __nanosleep(64);
@@ -196,7 +219,7 @@ __device__ __forceinline__ int local_brick(int bx, int by, int bz) {
 // Slot of brick (bx, by, bz), or -1 when it is outside the grid or not stored.
 __device__ __forceinline__ int find_brick(const GridView& g, int bx, int by, int bz) {
   if ((unsigned)bx >= (unsigned)g.BX || (unsigned)by >= (unsigned)g.BY || (unsigned)bz >= (unsigned)g.BZ) return -1;
-  int n = find_node(g, (uint32_t)node_key_of(g, bx, by, bz));
+  int n = find_node(g, node_key_of(g, bx, by, bz));
   if (n < 0) return -1;
   int s = g.child[(size_t)n * kNodeBricks + local_brick(bx, by, bz)];
   return s >= 0 ? s : -1;

@@ -132,9 +132,14 @@ def _ptr_host(a: np.ndarray) -> int:
     return a.ctypes.data
 
 
-def pack_records(xyz, occ) -> np.ndarray:
-    """Host records (x, y, z) [n, 3] and occ [n] packed as uint64 x | y << 21 | z << 42 | occ << 63."""
-    x = np.ascontiguousarray(xyz, dtype=np.int64).reshape(-1, 3)
+UNBOUNDED_OFFSET = 1 << 20
+UNBOUNDED_MIN, UNBOUNDED_MAX = -(1 << 20), (1 << 20) - 128
+
+
+def pack_records(xyz, occ, offset: int = 0) -> np.ndarray:
+    """Host records (x, y, z) [n, 3] and occ [n] packed as uint64 x | y << 21 | z << 42 | occ << 63
+    (coordinates plus `offset`: UNBOUNDED_OFFSET for an unbounded map)."""
+    x = np.ascontiguousarray(xyz, dtype=np.int64).reshape(-1, 3) + int(offset)
     o = np.ascontiguousarray(occ, dtype=np.uint64).reshape(-1)
     if x.size and (x.min() < 0 or x.max() >= 1 << 21):
         raise ValueError("coordinates must lie in [0, 2^21)")
@@ -147,10 +152,12 @@ class Map:
 
     `max_bricks` and `max_nodes` (0: every brick / node of the grid) cap the storage allocated up
     front, so that a large grid mapped only in part needs memory for the mapped part alone; a
-    transform that needs more reports EOVERFLOW."""
+    transform that needs more reports EOVERFLOW.  With `unbounded`, nx, ny, nz are ignored and
+    coordinates are signed in [UNBOUNDED_MIN, UNBOUNDED_MAX) on every axis (both capacities are
+    then required; no dense entry points)."""
 
     def __init__(self, nx: int, ny: int, nz: int, dmax: int, voxel_size: float = 0.1, device: int = 0,
-                 stream=None, max_bricks: int = 0, max_nodes: int = 0, _borrow=None):
+                 stream=None, max_bricks: int = 0, max_nodes: int = 0, unbounded: bool = False, _borrow=None):
         lib = load()
         torch = _torch()
         if _borrow is not None:
@@ -164,12 +171,13 @@ class Map:
             stream = torch.cuda.Stream(device)
         self.device = device
         self.stream = stream
-        cfg = Config(nx, ny, nz, dmax, voxel_size, device, ctypes.c_void_p(stream.cuda_stream), 0, max_bricks,
-                     max_nodes)
+        cfg = Config(nx, ny, nz, dmax, voxel_size, device, ctypes.c_void_p(stream.cuda_stream), 1 if unbounded else 0,
+                     max_bricks, max_nodes)
         h = ctypes.c_void_p()
         _check(lib.vdbedt_create(ctypes.byref(cfg), ctypes.byref(h)), "vdbedt_create")
         self._h = h
-        self.shape_xyz = (nx, ny, nz)
+        self.shape_xyz = None if unbounded else (nx, ny, nz)
+        self.unbounded = unbounded
         self.dmax = dmax
         self.voxel_size = voxel_size
 
