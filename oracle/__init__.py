@@ -13,6 +13,7 @@ Functions (each cites the passage it follows; the exact rules are in the C heade
                             global (Lower only, Sec. V-A) and incremental.
 * :func:`clearance`       -- the clearance term of Eq. 2 as a squared hinge on a trilinear
                             distance, its sum per trajectory and its gradient, in float64.
+* :func:`distance_at`     -- that trilinear distance and its gradient at points (float64).
 * :func:`nearest_obstacle` -- the nearest occupied voxel of sampled voxels (the obstacle a cell
                             records with its distance, Sec. IV-B), ties to the smallest (z, y, x).
 
@@ -199,6 +200,38 @@ class Alg1:
 
     def reset_counters(self):
         _L().alg1_reset_counters(self._h)
+
+
+def distance_at(D_zyx: np.ndarray, dmax: int, vs: float, pts: np.ndarray):
+    """The trilinear distance field of Eq. 2's clearance term and its gradient, in float64: for
+    points p [..., 3] (metres, float32), u = p / vs in float32 (the precision in which the GPU picks
+    the cell), cell i0 = floor(u) clamped to [0, n - 2], t = u - i0; corner distance
+    d_c = vs * sqrt(min(D_c, dmax^2)); d = trilinear interpolation of the eight corners at t; and
+    dd/dp = (1 / vs) * grad_t(trilinear) (inside a cell; one-sided at faces by the floor).
+    Returns (d [...], grad [..., 3]).  The same interpolation the clearance cost uses."""
+    D = np.asarray(D_zyx)
+    nz, ny, nx = D.shape
+    p32 = np.asarray(pts, dtype=np.float32)
+    u32 = p32 / np.float32(vs)
+    dims = np.array([nx, ny, nz])
+    i0 = np.clip(np.floor(u32).astype(np.int64), 0, dims - 2)
+    t = u32.astype(np.float64) - i0
+    dc = float(vs) * np.sqrt(np.minimum(D.astype(np.float64), float(dmax) ** 2))
+    x0, y0, z0 = i0[..., 0], i0[..., 1], i0[..., 2]
+    tx, ty, tz = t[..., 0], t[..., 1], t[..., 2]
+    c = {}
+    for a in (0, 1):
+        for b in (0, 1):
+            for e in (0, 1):
+                c[a, b, e] = dc[z0 + e, y0 + b, x0 + a]
+    wx = (1 - tx, tx)
+    wy = (1 - ty, ty)
+    wz = (1 - tz, tz)
+    d = sum(wx[a] * wy[b] * wz[e] * c[a, b, e] for a in (0, 1) for b in (0, 1) for e in (0, 1))
+    gx = sum((c[1, b, e] - c[0, b, e]) * wy[b] * wz[e] for b in (0, 1) for e in (0, 1))
+    gy = sum((c[a, 1, e] - c[a, 0, e]) * wx[a] * wz[e] for a in (0, 1) for e in (0, 1))
+    gz = sum((c[a, b, 1] - c[a, b, 0]) * wx[a] * wy[b] for a in (0, 1) for b in (0, 1))
+    return d, np.stack([gx, gy, gz], axis=-1) / float(vs)
 
 
 def clearance(D_zyx: np.ndarray, dmax: int, vs: float, tau: float, pts: np.ndarray):

@@ -80,3 +80,46 @@ def test_gradient_vs_central_differences():
         fd = (cp - cm) / step
         an = grad[0, keep, a]
         np.testing.assert_allclose(an, fd, rtol=1e-3, atol=1e-5)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_distance_at_plane_closed_form(axis):
+    """Obstacles on the plane (axis) = 0: d = vs * coordinate along the axis (linear, so trilinear
+    interpolation reproduces it exactly) and its gradient is the axis' unit vector."""
+    vs, dmax = 0.1, 8
+    occ, D = plane_field(axis, dmax=dmax)
+    rs = np.random.default_rng(10 + axis)
+    nz, ny, nx = D.shape
+    hi = np.array([nx - 1, ny - 1, nz - 1]) * vs
+    pts = (rs.random((300, 3)) * hi).astype(np.float32)
+    pts[:, axis] = np.minimum(pts[:, axis], np.float32((dmax - 1) * vs))
+    d, g = O.distance_at(D, dmax, vs, pts)
+    np.testing.assert_allclose(d, pts[:, axis].astype(np.float64), rtol=0, atol=1e-6)
+    expect = np.zeros_like(g)
+    expect[:, axis] = 1.0
+    np.testing.assert_allclose(g, expect, rtol=0, atol=1e-9)
+
+
+def test_distance_at_matches_clearance_and_differences():
+    """distance_at's d is the clearance's d; its gradient matches central differences divided by
+    the step taken in the float32 cell coordinate (exact for a trilinear function inside a cell)."""
+    occ = W.bernoulli_grid(21, (20, 22, 24), 0.01)
+    dmax, vs, h = 8, 0.1, 1e-3
+    D = O.edt_factorised(occ, dmax)
+    pts = W.free_points(5, occ, vs, 300)
+    d, g = O.distance_at(D, dmax, vs, pts)
+    _, _, dc = O.clearance(D, dmax, vs, 10.0, pts[None])
+    np.testing.assert_allclose(d, dc[0], rtol=0, atol=1e-12)
+    u = pts.astype(np.float64) / vs
+    frac = u - np.floor(u)
+    keep = ((frac > 2 * h / vs) & (frac < 1 - 2 * h / vs)).all(1)
+    vs32 = np.float32(vs)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        for i in np.flatnonzero(keep):
+            pp = (pts[i] + e).astype(np.float32)
+            pm = (pts[i] - e).astype(np.float32)
+            step = (float(pp[a] / vs32) - float(pm[a] / vs32)) * vs
+            fd = (O.distance_at(D, dmax, vs, pp[None])[0][0] - O.distance_at(D, dmax, vs, pm[None])[0][0]) / step
+            assert abs(fd - g[i, a]) <= 1e-6 * max(1.0, abs(g[i, a])), (i, a, fd, g[i, a])
