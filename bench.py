@@ -420,6 +420,7 @@ def bench_clearance(V, torch, m, occ, stream, reps=20):
         return p.grad
 
     ag = time_it(autograd)
+    dg = time_it(lambda: m.distance_at(pts, with_grad=True))
     gr = m.clearance_backward(pts, tau, ones)
     active = float((gr.abs().sum(-1) > 0).float().mean().item())
     q = T * P
@@ -427,6 +428,7 @@ def bench_clearance(V, torch, m, occ, stream, reps=20):
             "fwd_ms": fwd, "fwd_queries_per_s": q / (fwd / 1e3),
             "fwd_bwd_ms": fb, "fwd_bwd_queries_per_s": q / (fb / 1e3),
             "autograd_fwd_bwd_ms": ag, "autograd_overhead_ms": ag - fb,
+            "distance_gradient_ms": dg, "distance_gradient_queries_per_s": q / (dg / 1e3),
             "hinge_active_fraction": active,
             "hinge_active_rule": "points with a nonzero gradient (d < tau and a nonzero distance gradient)"}
 

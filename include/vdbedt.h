@@ -202,6 +202,13 @@ vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device);
 vdbedt_status vdbedt_export_occupancy(vdbedt_handle h, int32_t z_lo, int32_t z_hi, int32_t dz, int32_t mode,
                                       uint64_t* out, int64_t max_n, int64_t* n_out);
 
+/* Distance field for planners: at n points pts[n][3] (metres; device pointers), dist[k] = the
+ * trilinear distance d of the clearance cost below (same cell choice and corner values) and, when
+ * grad is not NULL, grad[k][0..2] = dd/dp = (1 / voxel_size) * d(trilinear)/dt, the gradient of the
+ * distance field a planner follows away from obstacles (the paper's trajectory optimisation pushes
+ * trajectories along it, Sec. I, Eq. 2).  Grids with a size < 2 along any axis are EINVAL. */
+vdbedt_status vdbedt_distance_at(vdbedt_handle h, const float* pts, int64_t n, float* dist, float* grad);
+
 /* Clearance cost of Eq. 2 (second term) as a squared hinge, for T trajectories of P points.
  * pts: device float [T][P][3], metres; voxel centre (i, j, k) sits at (i, j, k) * voxel_size.
  * Per point: u = p / voxel_size (float32), cell i0 = floor(u) clamped to [0, n - 2] per axis,

@@ -730,6 +730,16 @@ vdbedt_status vdbedt_export_occupancy(vdbedt_handle h, int32_t z_lo, int32_t z_h
   return VDBEDT_OK;
 }
 
+vdbedt_status vdbedt_distance_at(vdbedt_handle h, const float* pts, int64_t n, float* dist, float* grad) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!pts || !dist))) return fail(h, VDBEDT_EINVAL, "bad distance arguments");
+  if (h->g.nx < 2 || h->g.ny < 2 || h->g.nz < 2) return fail(h, VDBEDT_EINVAL, "grid needs >= 2 voxels per axis");
+  DeviceGuard guard(h->device);
+  CK(h, launch_distance_at(h->g, h->cfg.voxel_size, pts, n, dist, grad, h->st), "distance");
+  return VDBEDT_OK;
+}
+
 vdbedt_status vdbedt_clearance_forward(vdbedt_handle h, const float* pts, int64_t T, int64_t P, float tau,
                                        float* cost) {
   vdbedt_status s = check_handle(h);

@@ -206,6 +206,36 @@ __global__ void k_clearance_bwd(GridView g, float vs, const float* __restrict__ 
   }
 }
 
+// Distance and its gradient at points (planners): d = trilinear(vs sqrt(D)) as in the clearance
+// cost, grad = (1 / vs) grad_t(trilinear), a thread per point.
+__global__ void k_distance_at(GridView g, float vs, const float* __restrict__ pts, int64_t n, float* __restrict__ dist,
+                              float* __restrict__ grad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float* q = pts + i * 3;
+    int i0, j0, k0;
+    float tx, ty, tz;
+    cell_of(g, vs, q[0], q[1], q[2], i0, j0, k0, tx, ty, tz);
+    Corner8 c;
+    corners(g, vs, i0, j0, k0, c);
+    dist[i] = trilinear(c, tx, ty, tz);
+    if (grad) {
+      float gx = 0.f, gy = 0.f, gz = 0.f;
+      const float wx[2] = {1.f - tx, tx}, wy[2] = {1.f - ty, ty}, wz[2] = {1.f - tz, tz};
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          gx += (c.d[1 + 2 * b + 4 * e] - c.d[2 * b + 4 * e]) * wy[b] * wz[e];
+          gy += (c.d[2 + b + 4 * e] - c.d[b + 4 * e]) * wx[b] * wz[e];
+          gz += (c.d[4 + b + 2 * e] - c.d[b + 2 * e]) * wx[b] * wy[e];
+        }
+      grad[i * 3] = gx / vs;
+      grad[i * 3 + 1] = gy / vs;
+      grad[i * 3 + 2] = gz / vs;
+    }
+  }
+}
+
 unsigned grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -218,6 +248,13 @@ unsigned grid_for(int64_t n, int threads) {
 cudaError_t launch_query(const GridView& g, const int32_t* xyz, int64_t n, int32_t* out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   VDB_LAUNCH(k_query, grid_for(n, 256), 256, 0, st, g, xyz, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_distance_at(const GridView& g, float vs, const float* pts, int64_t n, float* dist, float* grad,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  VDB_LAUNCH(k_distance_at, grid_for(n, 256), 256, 0, st, g, vs, pts, n, dist, grad);
   return cudaGetLastError();
 }
 

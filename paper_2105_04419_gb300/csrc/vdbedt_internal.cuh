@@ -423,6 +423,9 @@ cudaError_t launch_export_occupancy(const GridView& g, const int32_t* changed, i
                                     cudaStream_t st);
 // obstacle and finite brick counts into counters C_OBST and C_FINITE
 cudaError_t launch_count_flags(const GridView& g, cudaStream_t st);
+// d (metres) and, when grad is not null, dd/dp at n points (the clearance cost's interpolation)
+cudaError_t launch_distance_at(const GridView& g, float vs, const float* pts, int64_t n, float* dist, float* grad,
+                               cudaStream_t st);
 cudaError_t launch_clearance_fwd(const GridView& g, float vs, const float* pts, int64_t T, int64_t P, float tau,
                                  float* cost, cudaStream_t st);
 cudaError_t launch_clearance_bwd(const GridView& g, float vs, const float* pts, int64_t T, int64_t P, float tau,

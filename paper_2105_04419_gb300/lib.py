@@ -70,6 +70,7 @@ SIGNATURES = {
     "vdbedt_export_dense": (ctypes.c_int, [_H, _P, ctypes.c_int]),
     "vdbedt_export_occupancy": (ctypes.c_int, [_H, _I32, _I32, _I32, _I32, _P, _I64, ctypes.POINTER(ctypes.c_int64)]),
     "vdbedt_clearance_forward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P]),
+    "vdbedt_distance_at": (ctypes.c_int, [_H, _P, _I64, _P, _P]),
     "vdbedt_clearance_backward": (ctypes.c_int, [_H, _P, _I64, _I64, _F, _P, _P]),
     "vdbedt_global_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _I32]),
     "vdbedt_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), _I32, ctypes.POINTER(ctypes.c_void_p)]),
@@ -370,6 +371,22 @@ class Map:
             _check(st, "vdbedt_export_occupancy", self._h)
             return out[: n.value]
         raise VdbedtError(5, "vdbedt_export_occupancy", "record count changed between attempts")
+
+    def distance_at(self, pts, with_grad: bool = True):
+        """Trilinear distance (metres) at points [..., 3] (float32 CUDA tensor, metres) and, with
+        with_grad, its gradient [..., 3] (the field a planner descends away from obstacles)."""
+        torch = _torch()
+        p = pts.contiguous().view(-1, 3)
+        if p.dtype != torch.float32 or not p.is_cuda:
+            raise TypeError("pts must be a float32 CUDA tensor [..., 3]")
+        d = torch.empty(p.shape[0], dtype=torch.float32, device=p.device)
+        g = torch.empty_like(p) if with_grad else None
+        self._enter(p, d, *([g] if with_grad else []))
+        _check(load().vdbedt_distance_at(self._h, p.data_ptr(), p.shape[0], d.data_ptr(),
+                                         g.data_ptr() if with_grad else None), "vdbedt_distance_at", self._h)
+        self._leave()
+        shape = pts.shape[:-1]
+        return (d.view(shape), g.view(*shape, 3)) if with_grad else d.view(shape)
 
     def clearance_forward(self, pts, tau: float):
         torch = _torch()

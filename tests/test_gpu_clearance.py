@@ -94,3 +94,21 @@ def test_gradient_vs_finite_differences():
             step = (float(pp[a] / vs32) - float(pm[a] / vs32)) * vs  # metres, as the oracle sees it
             fd[j, a] = (cp - cm) / step
     np.testing.assert_allclose(grad[keep], fd, rtol=GRAD_RTOL, atol=GRAD_ATOL)
+
+
+def test_distance_and_gradient_at_points():
+    """vdbedt_distance_at against the float64 oracle: the trilinear distance within 1e-4 relative
+    and its gradient within 1e-3 relative (the stated tolerances), on points in free space, on cell
+    faces and at the grid's last face."""
+    import torch
+    occ, m, D = setup_field(seed=6)
+    vs = 0.1
+    nz, ny, nx = occ.shape
+    pts = W.free_points(9, occ, vs, 2000).reshape(-1, 3)
+    extra = np.array([[0, 0, 0], [(nx - 1) * vs, (ny - 1) * vs, (nz - 1) * vs], [1.0, 1.2, 0.5]], np.float32)
+    pts = np.concatenate([pts, extra]).astype(np.float32)
+    d_o, g_o = O.distance_at(D, 12, vs, pts)
+    d, g = m.distance_at(torch.from_numpy(pts).cuda())
+    np.testing.assert_allclose(d.cpu().numpy(), d_o, rtol=VAL_RTOL, atol=VAL_ATOL)
+    np.testing.assert_allclose(g.cpu().numpy(), g_o, rtol=GRAD_RTOL, atol=GRAD_ATOL)
+    assert np.abs(g_o).max() > 0.5
