@@ -104,7 +104,8 @@ typedef struct {
   int64_t new_bricks;     /* bricks allocated by this update */
   int64_t x_bricks;       /* stored bricks in those runs, recomputed by the x pass */
   int64_t y_bricks;       /* ... by the y pass */
-  int64_t z_bricks;       /* ... by the z pass (the three counts are 0 when global_form is 1) */
+  int64_t z_bricks;       /* ... by the z pass (global_form 1: every stored brick; the three counts are 0
+                             in the envelope form, variant 8 or dmax > 45) */
   int64_t global_form;    /* 1: the edits reached so far that the update switched to the global form after
                              applying them (same field, lower cost; see vdbedt_update) */
 } vdbedt_update_stats;

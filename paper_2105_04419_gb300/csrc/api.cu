@@ -608,6 +608,8 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     CK(h, cudaStreamWaitEvent(h->st, h->fork.join, 0), "join");
     s = run_passes(h, t, false);
     if (s) return s;
+    if (stats && half_path(h->g))
+      CK(h, launch_count_run_bricks(nullptr, h->g, h->g.items_ctr, h->g.item_cap, t, h->items, h->st), "count");
   }
   if (stats) {
     CK(h, cudaMemcpyAsync(h->h_pinned, h->g.counters, sizeof(int32_t) * C_NUM, cudaMemcpyDeviceToHost, h->st), "d2h");
@@ -1062,6 +1064,8 @@ vdbedt_status batch_update(vdbedt_batch* b, vdbedt_update_stats* stats) {
     BCK(b, launch_pass(b->pool, t, 2, b->items, b->st), "z pass");
     bmark(b, 5);
     b->ev_recorded = b->profiling;
+    if (stats)
+      BCK(b, launch_count_run_bricks(b->d_views, g0, b->pool.items_ctr, b->pool.item_cap, t, b->items, b->st), "count");
   }
   if (stats) {
     for (int i = 0; i < b->k; ++i) {

@@ -145,6 +145,7 @@ __global__ void k_reset_nodes(VS vs) {
 // every grid's block clears the shared run counters (all store 0).
 template <class US>
 __global__ void k_begin_update(US us) {
+  pdl_enter();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     const GridView g = us.get().g;
     g.items_ctr[0] = 0;
@@ -167,6 +168,7 @@ __global__ void k_begin_update(US us) {
 
 // Batched form: the same, plus the record count of grids staged without a device count.
 __global__ void k_begin_batch_update(const UpdArgs* __restrict__ args, BatchCounts counts) {
+  pdl_enter();
   if (threadIdx.x == 0) {
     const int i = (int)blockIdx.y;
     const UpdArgs a = args[i];
@@ -200,19 +202,52 @@ __device__ __forceinline__ void init_brick_meta(const GridView& g, int slot, int
   g.bepoch[slot] = 0;
 }
 
+// dmax^2 twice in the 16-bit encoding of g1 / g2 (fp16 bits in the windowed form, integers else)
+__device__ __forceinline__ uint32_t field_inf2(const GridView& g) {
+  uint16_t inf;
+  if (g.half) {
+    __half h = __int2half_rn(g.INF);
+    inf = *reinterpret_cast<uint16_t*>(&h);
+  } else {
+    inf = (uint16_t)g.INF;
+  }
+  return (uint32_t)inf | ((uint32_t)inf << 16);
+}
+
+// g1, g2 and D of `slot` at dmax^2, written by a whole warp (every lane passes the same slot): each
+// store instruction covers 512 contiguous bytes.
+__device__ __forceinline__ void init_fields_warp(const GridView& g, int slot, int lane) {
+  const uint32_t p = field_inf2(g);
+  const uint4 v = make_uint4(p, p, p, p);
+  uint4* d1 = reinterpret_cast<uint4*>(g.g1 + (size_t)slot * kBrickVox);
+  uint4* d2 = reinterpret_cast<uint4*>(g.g2 + (size_t)slot * kBrickVox);
+  d1[lane] = v;
+  d1[lane + 32] = v;
+  d2[lane] = v;
+  d2[lane + 32] = v;
+  int4* dd = reinterpret_cast<int4*>(g.dist + (size_t)slot * kBrickVox);
+  const int4 w = make_int4(g.INF, g.INF, g.INF, g.INF);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dd[lane + 32 * q] = w;
+}
+
+// The fields of the slots `ok` lanes hold, a brick at a time by the whole warp (warp-uniform call).
+__device__ __forceinline__ void init_fields_ballot(const GridView& g, bool ok, int slot) {
+  const int lane = threadIdx.x & 31;
+  unsigned todo = __ballot_sync(0xffffffffu, ok);
+  while (todo) {
+    const int b = __ffs(todo) - 1;
+    todo &= todo - 1u;
+    init_fields_warp(g, __shfl_sync(0xffffffffu, slot, b), lane);
+  }
+}
+
 __device__ void init_brick(const GridView& g, int slot, int node, int bx, int by, int bz, bool init_fields) {
   ulonglong2* occ = reinterpret_cast<ulonglong2*>(g.occ + (size_t)slot * 8);
 #pragma unroll
   for (int q = 0; q < 4; ++q) occ[q] = make_ulonglong2(0ull, 0ull);
   if (init_fields) {
-    uint16_t inf;
-    if (g.half) {
-      __half h = __int2half_rn(g.INF);
-      inf = *reinterpret_cast<uint16_t*>(&h);
-    } else {
-      inf = (uint16_t)g.INF;
-    }
-    uint32_t p = (uint32_t)inf | ((uint32_t)inf << 16);
+    const uint32_t p = field_inf2(g);
     uint4* dst = reinterpret_cast<uint4*>(g.g2 + (size_t)slot * kBrickVox);
     for (int q = 0; q < 64; ++q) dst[q] = make_uint4(p, p, p, p);
     uint4* d1 = reinterpret_cast<uint4*>(g.g1 + (size_t)slot * kBrickVox);
@@ -274,6 +309,18 @@ __device__ __forceinline__ int64_t rec_count(int64_t n, const int32_t* n_dev) {
 #define GRID_STRIDE(i, n)                                                                              \
   for (int64_t i##_base = (int64_t)blockIdx.x * blockDim.x, i = i##_base + threadIdx.x; i##_base < (n); \
        i##_base += (int64_t)gridDim.x * blockDim.x, i = i##_base + threadIdx.x)
+
+// Places for the lanes with `want` in a list counted by *ctr: one atomic per warp (warp-uniform
+// call); returns the lane's place (meaningful where want).
+__device__ __forceinline__ int warp_reserve(int32_t* ctr, bool want) {
+  const unsigned m = __ballot_sync(0xffffffffu, want);
+  if (!m) return 0;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(ctr, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + __popc(m & ((1u << lane) - 1u));
+}
 
 __global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int64_t n, const int32_t* n_dev,
                                  uint32_t* __restrict__ keys) {
@@ -576,6 +623,7 @@ __device__ __forceinline__ void list_missing_brick(const GridView& g, int node, 
 
 template <bool DEFERRED, class US>
 __global__ void k_rec_missing(US us) {
+  pdl_enter();
   const UpdArgs A = us.get();
   const GridView& g = A.g;
   if (DEFERRED && g.counters[C_DEFERRED] == 0) return;
@@ -614,6 +662,7 @@ __global__ void k_rec_missing(US us) {
 // Nodes flagged by the tracked ingest (node keys of "set" records whose node did not exist).
 template <class US>
 __global__ void k_upd_nodes(US us) {
+  pdl_enter();
   const UpdArgs A = us.get();
   if (A.g.counters[C_DEFERRED] == 0) return;
   create_flagged_nodes(A.g, A.nflag, (int64_t)A.g.NX * A.g.NY * A.g.NZ);
@@ -621,6 +670,7 @@ __global__ void k_upd_nodes(US us) {
 
 template <class US>
 __global__ void k_alloc_listed(US us) {
+  pdl_enter();
   const UpdArgs A = us.get();
   const GridView& g = A.g;
   const unsigned long long* __restrict__ list = A.list;
@@ -641,14 +691,11 @@ __global__ void k_alloc_listed(US us) {
     }
     int total = 0;
     const int slot = block_agg_add(&g.counters[C_NBRICKS], need, &total);
-    if (need) {
-      if (slot >= g.cap) {
-        set_error(g, kErrOverflow);
-      } else {
-        init_brick(g, slot, node, bx, by, bz, true);
-        *e = slot;
-      }
-    }
+    const bool ok = need && slot < g.cap;
+    if (need && !ok) set_error(g, kErrOverflow);
+    if (ok) init_brick(g, slot, node, bx, by, bz, false);
+    init_fields_ballot(g, ok, slot);
+    if (ok) *e = slot;
     if (threadIdx.x == 0 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
   }
 }
@@ -686,7 +733,8 @@ __device__ __forceinline__ void apply_last(const GridView& g, const rec_t* __res
   const int64_t n = rec_count(n_max, n_dev);
   const int epoch = g.counters[C_EPOCH];
   GRID_STRIDE(j, n) {
-    bool flip = false;
+    bool flip = false, first = false;
+    int slot = 0;
     if (j < n) {
       const rec_t packed = rec[j];
       const int64_t key = rec_voxel(g, packed);
@@ -699,13 +747,14 @@ __device__ __forceinline__ void apply_last(const GridView& g, const rec_t* __res
         if (cur != ((packed >> 63) != 0ull)) {
           atomicXor(word, bit);
           flip = true;
-          if (track && atomicExch(&g.bepoch[s], epoch) != epoch) {
-            int p = atomicAdd(&g.counters[C_CHANGED], 1);
-            changed[p] = s;
-          }
+          first = track && atomicExch(&g.bepoch[s], epoch) != epoch;
+          slot = s;
         }
       }
     }
+    // the changed list: each brick once per epoch, a warp's bricks with one atomic
+    const int p = warp_reserve(&g.counters[C_CHANGED], first);
+    if (first) changed[p] = slot;
     unsigned m = __ballot_sync(0xffffffffu, flip);
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(&g.counters[C_FLIPS], __popc(m));
   }
@@ -724,12 +773,14 @@ __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t 
 // The tracked forms (incremental update): every record, flips tracked.
 template <class US>
 __global__ void k_upd_rec_last(US us) {
+  pdl_enter();
   const UpdArgs A = us.get();
   rec_last(A.g, A.rec, A.n, A.n_dev, true, A.vlast);
 }
 
 template <class US>
 __global__ void k_upd_apply_last(US us) {
+  pdl_enter();
   const UpdArgs A = us.get();
   apply_last(A.g, A.rec, A.n, A.n_dev, true, true, A.vlast, A.changed);
 }
@@ -929,6 +980,7 @@ __global__ void __launch_bounds__(256) k_dense_alloc(VS vs, DenseScratch ds) {
 
 template <class VS>
 __global__ void k_clear_masks(VS vs) {
+  pdl_enter();
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   if (vs.skip(g)) return;
@@ -946,6 +998,7 @@ __global__ void k_clear_masks(VS vs) {
 
 template <class VS>
 __global__ void k_obstacle_flags(VS vs) {
+  pdl_enter();
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   if (vs.skip(g)) return;
@@ -975,6 +1028,7 @@ __device__ __forceinline__ uint32_t row16(const uint32_t* m, int y, int z) {
 // directions they reach.  (R > 16: every node within ceil(R / 16) nodes.)
 template <class VS>
 __global__ void k_node_halo(VS vs) {
+  pdl_enter();
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   if (vs.skip(g)) return;
@@ -1027,6 +1081,7 @@ __device__ __forceinline__ int node_at(const GridView& g, int x, int y, int z) {
 // to the grid.  One thread per (node, mask word), i.e. two rows.
 template <int AXIS, class VS>
 __global__ void k_dilate_stage(VS vs) {
+  pdl_enter();
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   if (vs.skip(g)) return;
@@ -1099,6 +1154,7 @@ __global__ void k_dilate_stage(VS vs) {
 // stage launches.
 template <class VS>
 __global__ void __launch_bounds__(256) k_dilate_nodes(VS vs) {
+  pdl_enter();
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   if (vs.skip(g)) return;
@@ -1159,42 +1215,28 @@ __global__ void __launch_bounds__(256) k_dilate_nodes(VS vs) {
 
 // Mark bricks within Chebyshev radius R of brick (bx,by,bz) in amask: one (dy, dz) row (used by the
 // incremental form, where few bricks change).
-// An amask word that an update gives new bits: listed once per update (its fresh bit dedupes), so
-// that the update's allocation visits only those words.
-__device__ __forceinline__ void note_fresh_word(const GridView& g, int node, int word) {
+// An amask word that an update gives new bits is listed once per update (its fresh bit dedupes),
+// so that the update's allocation visits only those words: claim_fresh_word tells the one caller
+// that lists it, list_fresh_words appends a warp's words with one atomic (warp-uniform call).
+__device__ __forceinline__ bool claim_fresh_word(const GridView& g, int node, int word) {
   const uint32_t b = 1u << (word & 31);
-  if (atomicOr(&g.afresh[(size_t)node * 4 + (word >> 5)], b) & b) return;
-  const int p = atomicAdd(&g.counters[C_FRESH], 1);
-  if (p < g.node_cap * 128)
-    g.flist[p] = node * 128 + word;
-  else
-    set_error(g, kErrOverflow);  // not reached: each word is listed at most once
+  return !(atomicOr(&g.afresh[(size_t)node * 4 + (word >> 5)], b) & b);
 }
 
-__device__ void mark_dilation_row(const GridView& g, int bx, int by, int bz, int dy, int dz) {
-  const int R = g.R;
-  int y = by + dy, z = bz + dz;
-  if ((unsigned)y >= (unsigned)g.BY || (unsigned)z >= (unsigned)g.BZ) return;
-  int x0 = max(bx - R, 0), x1 = min(bx + R, g.BX - 1);
-  while (x0 <= x1) {
-    int seg_end = min(x1, (x0 | 15));
-    int node = get_or_create_node(g, node_key_of(g, x0, y, z));
-    if (node >= 0) {
-      int lx0 = x0 & 15, lx1 = seg_end & 15;
-      uint32_t bitsx = ((1u << (lx1 - lx0 + 1)) - 1u) << lx0;
-      int ly = y & 15, lz = z & 15;
-      int word = (ly >> 1) + 8 * lz;
-      const uint32_t add = bitsx << (16 * (ly & 1));
-      if (add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add)) note_fresh_word(g, node, word);
-    }
-    x0 = seg_end + 1;
-  }
+__device__ __forceinline__ void list_fresh_words(const GridView& g, bool want, int entry) {
+  const int p = warp_reserve(&g.counters[C_FRESH], want);
+  if (!want) return;
+  if (p < g.node_cap * 128)
+    g.flist[p] = entry;
+  else
+    set_error(g, kErrOverflow);  // not reached: each word is listed at most once
 }
 
 // Allocate every marked brick without storage: a block per (node, 256-brick chunk), a brick per
 // thread, one atomic per block for the slot range (block scan of the flags).
 template <class VS>
 __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
+  pdl_enter();
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   if (vs.skip(g)) return;
@@ -1225,6 +1267,7 @@ __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
 // clear the word's fresh bit.  The work follows the update's dilation, not the size of the map.
 template <class US>
 __global__ void __launch_bounds__(256) k_alloc_fresh(US us) {
+  pdl_enter();
   const GridView g = us.get().g;
   if (g.counters[C_BIG]) return;
   const int nf = min(g.counters[C_FRESH], g.node_cap * 128);
@@ -1242,36 +1285,44 @@ __global__ void __launch_bounds__(256) k_alloc_fresh(US us) {
       atomicAdd(&g.counters[C_NEW_BRICKS], __popc(bal));
     }
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (need) {
-      const int slot = base + __popc(bal & ((1u << lane) - 1u));
-      if (slot >= g.cap) {
-        set_error(g, kErrOverflow);
-      } else {
-        int nxn, nyn, nzn;
-        node_coords(g, (unsigned long long)g.node_key[node], nxn, nyn, nzn);
-        init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8), true);
-        g.child[(size_t)node * kNodeBricks + l] = slot;
-      }
+    const int slot = base + __popc(bal & ((1u << lane) - 1u));
+    const bool ok = need && slot < g.cap;
+    if (need && !ok) set_error(g, kErrOverflow);
+    if (ok) {
+      int nxn, nyn, nzn;
+      node_coords(g, (unsigned long long)g.node_key[node], nxn, nyn, nzn);
+      init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8), false);
     }
+    init_fields_ballot(g, ok, slot);
+    if (ok) g.child[(size_t)node * kNodeBricks + l] = slot;
     if (lane == 0) atomicAnd(&g.afresh[(size_t)node * 4 + (word >> 5)], ~(1u << (word & 31)));
   }
 }
 
 // ---- work items ----
-// Queue the run along `axis` that holds brick (bx, by, bz) (runs are aligned to `run` bricks
-// inside the node), once per epoch; in a batch, igrid records the run's grid.
-__device__ __forceinline__ void queue_run(const GridView& g, int axis, int bx, int by, int bz, int node, int run,
-                                          int epoch, unsigned long long* items, int32_t* igrid, int grid) {
-  const int l[3] = {bx & 15, by & 15, bz & 15};
-  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
-  const int id = l[a1] + 16 * (l[a2] + 16 * (l[axis] / run));
-  if (atomicExch(&g.mark[((size_t)node * 3 + axis) * 1024 + id], epoch) != epoch) {
-    const int p = atomicAdd(&g.items_ctr[axis], 1);
-    const int back = l[axis] % run;
-    if (p < g.item_cap) {
-      items[p] = pack_brick(bx - (axis == 0 ? back : 0), by - (axis == 1 ? back : 0), bz - (axis == 2 ? back : 0));
-      if (igrid) igrid[p] = grid;
-    }
+// Claim the run along `axis` that holds brick (bx, by, bz) (runs are aligned to `run` bricks inside
+// the node) for this epoch: true for the one caller that queues it, with the run's first brick in
+// `packed`.  A plain read first lets runs already claimed in this epoch skip the exchange (a value
+// read before another thread's exchange only leads to the exchange).
+__device__ __forceinline__ bool claim_run(const GridView& g, int axis, int bx, int by, int bz, int node, int run,
+                                          int epoch, unsigned long long& packed) {
+  const int la = axis == 0 ? bx & 15 : (axis == 1 ? by & 15 : bz & 15);
+  const int l1 = axis == 0 ? by & 15 : bx & 15, l2 = axis == 2 ? by & 15 : bz & 15;
+  int* mk = &g.mark[((size_t)node * 3 + axis) * 1024 + l1 + 16 * (l2 + 16 * (la / run))];
+  if (__ldcg(mk) == epoch || atomicExch(mk, epoch) == epoch) return false;
+  const int back = la % run;
+  packed = pack_brick(bx - (axis == 0 ? back : 0), by - (axis == 1 ? back : 0), bz - (axis == 2 ? back : 0));
+  return true;
+}
+
+// Append the claimed runs of a warp to the axis's work list (warp-uniform call); in a batch, igrid
+// records each run's grid.
+__device__ __forceinline__ void emit_runs(const GridView& g, int axis, bool won, unsigned long long packed,
+                                          unsigned long long* items, int32_t* igrid, int grid) {
+  const int p = warp_reserve(&g.items_ctr[axis], won);
+  if (won && p < g.item_cap) {
+    items[p] = packed;
+    if (igrid) igrid[p] = grid;
   }
 }
 
@@ -1282,6 +1333,7 @@ __device__ __forceinline__ void queue_run(const GridView& g, int axis, int bx, i
 // (R <= 6 < 16, so the halo reaches at most one node each way), one slot per thread.
 template <class VS>
 __global__ void __launch_bounds__(256) k_items_nodes(VS vs, int rx, int ry, int rz, Items it, bool with_slots) {
+  pdl_enter();
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   if (vs.skip(g)) return;
@@ -1423,13 +1475,11 @@ __device__ __forceinline__ void run_slots(const GridView& g, int axis, int run, 
     }
   }
   dst[lane] = s;
-  // the run's own stored bricks (the ones the pass recomputes), counted for the update statistics
-  const unsigned own = __ballot_sync(0xffffffffu, s >= 0 && lane >= g.R && lane < g.R + run);
-  if (lane == 0 && own) atomicAdd(&g.counters[C_XB + axis], __popc(own));
 }
 
 // blockIdx.y = axis
 __global__ void k_item_slots(GridView g, int rx, int ry, int rz, Items it) {
+  pdl_enter();
   if (g.counters[C_BIG]) return;  // the global form's work lists came with their slots
   const int axis = (int)blockIdx.y;
   const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
@@ -1442,6 +1492,7 @@ __global__ void k_item_slots(GridView g, int rx, int ry, int rz, Items it) {
 // The same for a batch's shared queue: each run's grid comes from it.igrid.
 __global__ void k_item_slots_batch(const GridView* __restrict__ views, const int32_t* __restrict__ items_ctr,
                                    int item_cap, int rx, int ry, int rz, Items it) {
+  pdl_enter();
   const int axis = (int)blockIdx.y;
   const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
   const int n = min(items_ctr[axis], item_cap);
@@ -1453,15 +1504,39 @@ __global__ void k_item_slots_batch(const GridView* __restrict__ views, const int
   }
 }
 
+// Update statistics only (launched when they are asked for): the stored bricks each pass
+// recomputes, i.e. the own entries (R .. R + run - 1) of every run's slot list that hold a slot,
+// added to the counters of the run's grid (views == nullptr: every run is grid `one`'s).
+// blockIdx.y = axis, a thread per run.
+__global__ void k_count_run_bricks(const GridView* __restrict__ views, GridView one, const int32_t* __restrict__ items_ctr,
+                                   int item_cap, int rx, int ry, int rz, Items it) {
+  const int axis = (int)blockIdx.y;
+  const int run = axis == 0 ? rx : (axis == 1 ? ry : rz);
+  const int n = min(items_ctr[axis], item_cap);
+  for (int item = (int)(blockIdx.x * blockDim.x + threadIdx.x); item < n; item += (int)(gridDim.x * blockDim.x)) {
+    const int32_t* sl = it.slots[axis] + (size_t)item * kItemSlots + one.R;
+    int own = 0;
+    for (int j = 0; j < run; ++j) own += sl[j] >= 0;
+    int32_t* ctr = views ? views[it.igrid[axis][item]].counters : one.counters;
+    if (own) atomicAdd(&ctr[C_XB + axis], own);
+  }
+}
+
 // ---- incremental ----
 // For every changed brick: refresh its obstacle flag; if it holds obstacles, mark its dilation.
+// A block per changed brick: its first threads find or create the interior nodes the brick's cube
+// spans (at most 4 per axis), then a thread per row (y, z) of the cube sets the row's x extent in
+// the allocation masks of one or two nodes.
 template <class US>
-__global__ void k_changed_flags_dilate(US us) {
+__global__ void __launch_bounds__(256) k_changed_flags_dilate(US us) {
+  pdl_enter();
+  __shared__ int nodes[64];
+  __shared__ int obst_sh;
   const UpdArgs A = us.get();
   const GridView& g = A.g;
   const int32_t* __restrict__ changed = A.changed;
   const int nc = min(g.counters[C_CHANGED], g.cap);
-  const int side = 2 * g.R + 1, rows = side * side;
+  const int R = g.R, side = 2 * R + 1;
   // The marking costs (2R + 1)^3 brick visits per changed brick; once that exceeds kBigUpdate
   // visits per stored brick, the update takes the global form's activation and work lists instead
   // (same field; measured crossover on the tunnel scene).  Every block reaches the same decision.
@@ -1469,25 +1544,64 @@ __global__ void k_changed_flags_dilate(US us) {
     if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_BIG] = 1;
     return;
   }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nc * rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int s = changed[i / rows], r = (int)(i % rows);
-    bool obst = brick_has_obstacle(g, s);
-    if (r == 0) {
-      uint32_t f = g.bflags[s];
+  for (int i = (int)blockIdx.x; i < nc; i += (int)gridDim.x) {
+    const int s = changed[i];
+    __syncthreads();  // the table of the block's previous brick is no longer read
+    if (threadIdx.x == 0) {
+      const bool obst = brick_has_obstacle(g, s);
+      const uint32_t f = g.bflags[s];
       g.bflags[s] = obst ? (f | F_OBST) : (f & ~F_OBST);
+      obst_sh = obst;
     }
-    if (obst) {
-      int4 c = g.bcoord[s];
-      mark_dilation_row(g, c.x, c.y, c.z, r % side - g.R, r / side - g.R);
+    __syncthreads();
+    if (!obst_sh) continue;
+    const int4 c = g.bcoord[s];
+    const int x0 = max(c.x - R, 0), x1 = min(c.x + R, g.BX - 1);
+    const int y0 = max(c.y - R, 0), y1 = min(c.y + R, g.BY - 1);
+    const int z0 = max(c.z - R, 0), z1 = min(c.z + R, g.BZ - 1);
+    const int qx0 = x0 >> 4, qy0 = y0 >> 4, qz0 = z0 >> 4;
+    const int nqx = (x1 >> 4) - qx0 + 1, nqy = (y1 >> 4) - qy0 + 1, nqz = (z1 >> 4) - qz0 + 1;
+    if ((int)threadIdx.x < nqx * nqy * nqz) {
+      const int q = (int)threadIdx.x;
+      nodes[q] = get_or_create_node(g, node_key_at(g, qx0 + q % nqx, qy0 + (q / nqx) % nqy, qz0 + q / (nqx * nqy)));
+    }
+    __syncthreads();
+    const int nyr = y1 - y0 + 1, rows = nyr * (z1 - z0 + 1);
+    // a row's x extent is split at node boundaries (the same segments on every lane); the rounds are
+    // block-uniform so that the fresh list is appended a warp at a time
+    for (int r0 = 0; r0 < rows; r0 += (int)blockDim.x) {
+      const int r = r0 + (int)threadIdx.x;
+      const bool live = r < rows;
+      const int y = y0 + (live ? r % nyr : 0), z = z0 + (live ? r / nyr : 0);
+      const int ly = y & 15, lz = z & 15, word = (ly >> 1) + 8 * lz;
+      const int nrow = nqx * (((y >> 4) - qy0) + nqy * ((z >> 4) - qz0));
+      for (int xa = x0; xa <= x1;) {  // the same segments on every lane
+        const int xe = min(x1, xa | 15);
+        const int node = live ? nodes[nrow + (xa >> 4) - qx0] : -1;
+        bool fresh = false;
+        if (node >= 0) {
+          const uint32_t bitsx = ((1u << ((xe & 15) - (xa & 15) + 1)) - 1u) << (xa & 15);
+          const uint32_t add = bitsx << (16 * (ly & 1));
+          fresh = (add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add)) && claim_fresh_word(g, node, word);
+        }
+        list_fresh_words(g, fresh, node * 128 + word);
+        xa = xe + 1;
+      }
     }
   }
 }
 
 // Dirty sets of an update: every stored brick within R (Chebyshev) of a changed brick needs its z
-// pass; those in the changed brick's z layer also need the in-plane pass.
+// pass; those in the changed brick's z layer also need the in-plane pass, those in its x row the x
+// pass.  A block per changed brick: its first threads look up the interior nodes the brick's cube
+// spans (at most 4 per axis: 2R + 1 <= 47 bricks), then a thread per (column, z run) of the cube
+// reads the run's bricks inside the cube and queues the run once if one is stored, and for the
+// changed brick's z layer that brick's y run and x run.  Runs are aligned to their length (4, 8
+// or 16) inside nodes, hence at multiples of it in grid coordinates.
 template <class US>
-__global__ void k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
+__global__ void __launch_bounds__(256) k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
+  pdl_enter();
+  __shared__ int nodes[64];
   const UpdArgs A = us.get();
   const GridView& g = A.g;
   const int32_t* __restrict__ changed = A.changed;
@@ -1495,23 +1609,49 @@ __global__ void k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
   if (g.counters[C_BIG]) return;
   const int nc = min(g.counters[C_CHANGED], g.cap);
   const int epoch = g.counters[C_EPOCH];
-  const int side = 2 * g.R + 1, vol = side * side * side;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nc * vol;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int s = changed[i / vol], r = (int)(i % vol);
-    int dx = r % side - g.R, dy = (r / side) % side - g.R, dz = r / (side * side) - g.R;
-    int4 c = g.bcoord[s];
-    int bx = c.x + dx, by = c.y + dy, bz = c.z + dz;
-    if ((unsigned)bx >= (unsigned)g.BX || (unsigned)by >= (unsigned)g.BY || (unsigned)bz >= (unsigned)g.BZ) continue;
-    int node = find_node(g, node_key_of(g, bx, by, bz));
-    if (node < 0) continue;
-    const int slot = g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
-    if (slot < 0) continue;
-    // x-lines change only within R bricks along x of a changed brick, in-plane values within R in
-    // x and y, D within R in all three
-    if (dy == 0 && dz == 0) queue_run(g, 0, bx, by, bz, node, rx, epoch, it.run[0], it.igrid[0], grid);
-    if (dz == 0) queue_run(g, 1, bx, by, bz, node, ry, epoch, it.run[1], it.igrid[1], grid);
-    queue_run(g, 2, bx, by, bz, node, rz, epoch, it.run[2], it.igrid[2], grid);
+  const int R = g.R;
+  for (int i = (int)blockIdx.x; i < nc; i += (int)gridDim.x) {
+    const int4 c = g.bcoord[changed[i]];
+    const int x0 = max(c.x - R, 0), x1 = min(c.x + R, g.BX - 1);
+    const int y0 = max(c.y - R, 0), y1 = min(c.y + R, g.BY - 1);
+    const int z0 = max(c.z - R, 0), z1 = min(c.z + R, g.BZ - 1);
+    const int qx0 = x0 >> 4, qy0 = y0 >> 4, qz0 = z0 >> 4;
+    const int nqx = (x1 >> 4) - qx0 + 1, nqy = (y1 >> 4) - qy0 + 1, nqz = (z1 >> 4) - qz0 + 1;
+    __syncthreads();  // the table of the block's previous brick is no longer read
+    if ((int)threadIdx.x < nqx * nqy * nqz) {
+      const int q = (int)threadIdx.x;
+      nodes[q] = find_node(g, node_key_at(g, qx0 + q % nqx, qy0 + (q / nqx) % nqy, qz0 + q / (nqx * nqy)));
+    }
+    __syncthreads();
+    const int r0 = z0 - z0 % rz, nruns = (z1 - r0) / rz + 1;
+    const int ncx = x1 - x0 + 1, ncol = ncx * (y1 - y0 + 1), total = ncol * nruns;
+    for (int u0 = 0; u0 < total; u0 += (int)blockDim.x) {  // block-uniform rounds: the lists' places are
+      const int u = u0 + (int)threadIdx.x;                 // reserved a warp at a time
+      bool wx = false, wy = false, wz = false;
+      unsigned long long px = 0, py = 0, pz = 0;
+      if (u < total) {
+        const int col = u % ncol, zr = u / ncol;
+        const int bx = x0 + col % ncx, by = y0 + col / ncx;
+        const int zs = max(r0 + zr * rz, z0), ze = min(r0 + zr * rz + rz - 1, z1);
+        const int node = nodes[((bx >> 4) - qx0) + nqx * (((by >> 4) - qy0) + nqy * ((zs >> 4) - qz0))];
+        if (node >= 0) {
+          const int32_t* ch = g.child + (size_t)node * kNodeBricks;
+          bool any = false;
+          for (int bz = zs; bz <= ze; ++bz) {
+            const bool stored = ch[local_brick(bx, by, bz)] >= 0;
+            any |= stored;
+            if (bz == c.z && stored) {
+              if (by == c.y) wx = claim_run(g, 0, bx, by, bz, node, rx, epoch, px);
+              wy = claim_run(g, 1, bx, by, bz, node, ry, epoch, py);
+            }
+          }
+          if (any) wz = claim_run(g, 2, bx, by, zs, node, rz, epoch, pz);
+        }
+      }
+      emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
+      emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
+      emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
+    }
   }
 }
 
@@ -1525,12 +1665,12 @@ cudaError_t update_ingest_kernels(US us, int k, int64_t n, int64_t nkeys, int64_
     return (unsigned)(b < 1 ? 1 : (b > lim ? lim : b));
   };
   const dim3 gr(bx(n, 152 * 16), k), gk(bx(nkeys, 152 * 16), k), gl(bx(n < cap ? n : cap, 152 * 16), k);
-  VDB_LAUNCH((k_rec_missing<false, US>), gr, kT, 0, st, us);
-  VDB_LAUNCH(k_upd_nodes<US>, gk, kT, 0, st, us);
-  VDB_LAUNCH((k_rec_missing<true, US>), gr, kT, 0, st, us);
-  VDB_LAUNCH(k_alloc_listed<US>, gl, kT, 0, st, us);
-  VDB_LAUNCH(k_upd_rec_last<US>, gr, kT, 0, st, us);
-  VDB_LAUNCH(k_upd_apply_last<US>, gr, kT, 0, st, us);
+  VDB_LAUNCH_PDL((k_rec_missing<false, US>), gr, kT, 0, st, us);
+  VDB_LAUNCH_PDL(k_upd_nodes<US>, gk, kT, 0, st, us);
+  VDB_LAUNCH_PDL((k_rec_missing<true, US>), gr, kT, 0, st, us);
+  VDB_LAUNCH_PDL(k_alloc_listed<US>, gl, kT, 0, st, us);
+  VDB_LAUNCH_PDL(k_upd_rec_last<US>, gr, kT, 0, st, us);
+  VDB_LAUNCH_PDL(k_upd_apply_last<US>, gr, kT, 0, st, us);
   return cudaGetLastError();
 }
 
@@ -1542,7 +1682,7 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
   const unsigned nc = (unsigned)node_cap;
   // the decision (counters[C_BIG]) and, for updates that stay incremental, the changed bricks' flags
   // and dilation marks
-  VDB_LAUNCH(k_changed_flags_dilate<US>, dim3(share(1024), k), kT, 0, st, us);
+  VDB_LAUNCH_PDL(k_changed_flags_dilate<US>, dim3(share(1216), k), kT, 0, st, us);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   cudaStream_t gs = st;
@@ -1556,17 +1696,17 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
   // kernels stride over their work, so a launch of at most two blocks per SM keeps that cheap)
   auto gated = [&](unsigned single) { return share(single < 304u ? single : 304u); };
   VDB_LAUNCH(k_clear_masks<GV>, dim3(gated(256), k), kT, 0, gs, gv);
-  VDB_LAUNCH(k_obstacle_flags<GV>, dim3(gated(1024), k), kT, 0, gs, gv);
-  VDB_LAUNCH(k_node_halo<GV>, dim3(gated(64), k), kT, 0, gs, gv);
+  VDB_LAUNCH_PDL(k_obstacle_flags<GV>, dim3(gated(1024), k), kT, 0, gs, gv);
+  VDB_LAUNCH_PDL(k_node_halo<GV>, dim3(gated(64), k), kT, 0, gs, gv);
   if (R <= 16) {
-    VDB_LAUNCH(k_dilate_nodes<GV>, dim3(gated(nc < 1024 ? nc : 1024u), k), 256, 0, gs, gv);
+    VDB_LAUNCH_PDL(k_dilate_nodes<GV>, dim3(gated(nc < 1024 ? nc : 1024u), k), 256, 0, gs, gv);
   } else {
-    VDB_LAUNCH((k_dilate_stage<0, GV>), dim3(gated(256), k), kT, 0, gs, gv);
-    VDB_LAUNCH((k_dilate_stage<1, GV>), dim3(gated(256), k), kT, 0, gs, gv);
-    VDB_LAUNCH((k_dilate_stage<2, GV>), dim3(gated(256), k), kT, 0, gs, gv);
+    VDB_LAUNCH_PDL((k_dilate_stage<0, GV>), dim3(gated(256), k), kT, 0, gs, gv);
+    VDB_LAUNCH_PDL((k_dilate_stage<1, GV>), dim3(gated(256), k), kT, 0, gs, gv);
+    VDB_LAUNCH_PDL((k_dilate_stage<2, GV>), dim3(gated(256), k), kT, 0, gs, gv);
   }
-  VDB_LAUNCH(k_alloc_marked<GV>, dim3(gated(nc * 16 < 8192 ? nc * 16 : 8192u), k), kT, 0, gs, gv, false);
-  VDB_LAUNCH(k_items_nodes<GV>, dim3(gated(nc * 12 < 8192 ? nc * 12 : 8192u), k), kT, 0, gs, gv, t.run[0], t.run[1],
+  VDB_LAUNCH_PDL(k_alloc_marked<GV>, dim3(gated(nc * 16 < 8192 ? nc * 16 : 8192u), k), kT, 0, gs, gv, false);
+  VDB_LAUNCH_PDL(k_items_nodes<GV>, dim3(gated(nc * 12 < 8192 ? nc * 12 : 8192u), k), kT, 0, gs, gv, t.run[0], t.run[1],
              t.run[2], it, with_slots);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1576,7 +1716,7 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
   }
   // incremental form: new bricks of the dilation, the dirty runs
   VDB_LAUNCH(k_alloc_fresh<US>, dim3(share(nc < 256 ? nc : 256u), k), kT, 0, st, us);
-  VDB_LAUNCH(k_mark_dirty<US>, dim3(share(2048), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
+  VDB_LAUNCH_PDL(k_mark_dirty<US>, dim3(share(1216), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }
 
@@ -1819,6 +1959,13 @@ cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, const It
 
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st) {
   VDB_LAUNCH(k_item_slots, dim3(1024, 3), kT, 0, st, g, t.run[0], t.run[1], t.run[2], it);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_run_bricks(const GridView* views, const GridView& one, const int32_t* items_ctr, int item_cap,
+                                   const Tuning& t, const Items& it, cudaStream_t st) {
+  VDB_LAUNCH(k_count_run_bricks, dim3(152, 3), kT, 0, st, views, one, items_ctr, item_cap, t.run[0], t.run[1], t.run[2],
+             it);
   return cudaGetLastError();
 }
 

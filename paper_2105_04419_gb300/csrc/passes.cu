@@ -362,6 +362,7 @@ __host__ __device__ constexpr int pass_min_blocks(int run, int axis) {
 template <int R, int RUN, int AXIS>
 __global__ void __launch_bounds__(32 * (RUN + 1), pass_min_blocks(RUN, AXIS))
     k_pass(GridView g, const int32_t* __restrict__ islots, int max_items, bool prune) {
+  pdl_enter();
   using S = ColShape<R, RUN, AXIS>;
   constexpr int NB = S::NB, NS = S::NS;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -463,6 +464,7 @@ __global__ void __launch_bounds__(32 * (RUN + 1), pass_min_blocks(RUN, AXIS))
 template <int R>
 __global__ void __launch_bounds__(256) k_x_direct(GridView g, const int32_t* __restrict__ islots, int max_items,
                                                   int run) {
+  pdl_enter();
   constexpr int NBX = 2 * R + 1;
   const int nitems = min(g.items_ctr[0], max_items);
   const int lane = threadIdx.x & 31;
@@ -722,17 +724,29 @@ cudaError_t pass_half(const GridView& g, const int32_t* islots, int max_items, c
   using S = ColShape<R, RUN, AXIS>;
   auto kernel = k_pass<R, RUN, AXIS>;
   if (max_items <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+  // attributes and resident blocks per SM, set up once per device (0: not yet)
+  static int per_sm_dev[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, S::THREADS, S::SMEM);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  int per_sm = dev >= 0 && dev < 64 ? per_sm_dev[dev] : 0;
+  if (per_sm == 0) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, S::THREADS, S::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (dev >= 0 && dev < 64) per_sm_dev[dev] = per_sm;
+  }
   int grid = num_sms() * per_sm;
   if (grid > max_items) grid = max_items;
-  VDB_LAUNCH(kernel, grid, S::THREADS, S::SMEM, st, g, islots, max_items, prune);
+  // the y and z passes follow the previous pass directly: their launch overlaps its tail
+  if (AXIS > 0)
+    VDB_LAUNCH_PDL(kernel, grid, S::THREADS, S::SMEM, st, g, islots, max_items, prune);
+  else
+    VDB_LAUNCH(kernel, grid, S::THREADS, S::SMEM, st, g, islots, max_items, prune);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/vdbedt.h"
 
 namespace vdbedt {
@@ -142,6 +144,14 @@ __device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
 
 __device__ __forceinline__ void set_error(const GridView& g, int bits) { atomicOr(&g.counters[C_ERR], bits); }
 
+// First statement of a kernel that may be launched with VDB_LAUNCH_PDL: wait until the previous
+// kernel of the stream has finished and its writes are visible (returns at once for a kernel
+// launched without the attribute), then let the next kernel of the stream begin launching.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Device-side waits give up after kWaitLimitNs of global time (or kWaitMaxPolls polls, whichever
 // comes first), set the error word and let the kernel return.
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // one second
@@ -251,6 +261,32 @@ void set_last_error(const char* msg);
   do {                                                             \
     ::vdbedt::note_launch();                                       \
     kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);    \
+  } while (0)
+
+// Launch with programmatic stream serialization: the kernel may be scheduled before the previous
+// kernel of the stream has finished, so its launch and block scheduling overlap that kernel's
+// tail.  Only for kernels that call pdl_enter() before their first memory access.  Errors are
+// left for cudaGetLastError like those of VDB_LAUNCH.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+#define VDB_LAUNCH_PDL(kernel, grid, block, smem, stream, ...)                         \
+  do {                                                                                 \
+    ::vdbedt::note_launch();                                                           \
+    ::vdbedt::launch_pdl(kernel, dim3(grid), dim3(block), (smem), (stream), __VA_ARGS__); \
   } while (0)
 
 constexpr int kItemSlots = 32;  // slot list entries per work item (run + 2R <= 28 on the half path)
@@ -373,6 +409,10 @@ cudaError_t launch_update_batch_mark(const UpdArgs* d_args, const BatchUpdShape&
 // slot lists of every queued run of a batch (each run's grid from it.igrid)
 cudaError_t launch_item_slots_batch(const GridView* views, const Tuning& t, const Items& it, int32_t* items_ctr,
                                     int item_cap, cudaStream_t st);
+// Update statistics: stored bricks of every run's slot list per axis into each grid's C_XB .. C_ZB
+// (views == nullptr: a single grid `one`).
+cudaError_t launch_count_run_bricks(const GridView* views, const GridView& one, const int32_t* items_ctr, int item_cap,
+                                   const Tuning& t, const Items& it, cudaStream_t st);
 // slot lists of every queued run (half path)
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st);
 

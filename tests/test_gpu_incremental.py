@@ -173,6 +173,14 @@ def test_switch_to_global_form_on_each_side():
         m.set_occupancy(xyz, val)
         st = m.update(stats=True)
         assert st["global_form"] == expect, (f, st)
+        # recomputed bricks: the global form's runs hold every stored brick once per axis; an
+        # incremental update's z runs hold at least its changed bricks
+        nb = m.info()["allocated_bricks"]
+        if expect:
+            assert st["x_bricks"] == st["y_bricks"] == st["z_bricks"] == nb, (st, nb)
+        else:
+            assert st["changed_bricks"] <= st["z_bricks"] <= nb and 0 < st["x_bricks"] <= nb, (st, nb)
+            assert 0 < st["y_bricks"] <= nb, (st, nb)
         ref = O.edt_factorised(occ, 16)
         assert first_mismatch(m.export_dense(), ref) is None, (f, first_mismatch(m.export_dense(), ref))
 
