@@ -1599,7 +1599,7 @@ __global__ void __launch_bounds__(256) k_changed_flags_dilate(US us) {
 // changed brick's z layer that brick's y run and x run.  Runs are aligned to their length (4, 8
 // or 16) inside nodes, hence at multiples of it in grid coordinates.
 template <class US>
-__global__ void __launch_bounds__(256) k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
+__global__ void __launch_bounds__(256, 8) k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
   pdl_enter();
   __shared__ int nodes[64];
   const UpdArgs A = us.get();
@@ -1715,7 +1715,8 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
     if (e != cudaSuccess) return e;
   }
   // incremental form: new bricks of the dilation, the dirty runs
-  VDB_LAUNCH(k_alloc_fresh<US>, dim3(share(nc < 256 ? nc : 256u), k), kT, 0, st, us);
+  // a warp per fresh word (the count is on the device): one wave of 8 warps per block on every SM
+  VDB_LAUNCH(k_alloc_fresh<US>, dim3(share(1216), k), kT, 0, st, us);
   VDB_LAUNCH_PDL(k_mark_dirty<US>, dim3(share(1216), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }
@@ -1958,7 +1959,7 @@ cudaError_t launch_build_items_full(const GridView& g, const Tuning& t, const It
 }
 
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st) {
-  VDB_LAUNCH(k_item_slots, dim3(1024, 3), kT, 0, st, g, t.run[0], t.run[1], t.run[2], it);
+  VDB_LAUNCH(k_item_slots, dim3(405, 3), kT, 0, st, g, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }
 
@@ -1971,7 +1972,7 @@ cudaError_t launch_count_run_bricks(const GridView* views, const GridView& one, 
 
 cudaError_t launch_item_slots_batch(const GridView* views, const Tuning& t, const Items& it, int32_t* items_ctr,
                                     int item_cap, cudaStream_t st) {
-  VDB_LAUNCH(k_item_slots_batch, dim3(1024, 3), kT, 0, st, views, items_ctr, item_cap, t.run[0], t.run[1], t.run[2],
+  VDB_LAUNCH(k_item_slots_batch, dim3(405, 3), kT, 0, st, views, items_ctr, item_cap, t.run[0], t.run[1], t.run[2],
              it);
   return cudaGetLastError();
 }
