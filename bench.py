@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-clearance", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-crossover", action="store_true")
+    ap.add_argument("--no-untruncated", action="store_true")
     ap.add_argument("--shard", choices=["replicas", "slabs"], default="replicas",
                     help="replicas: every rank transforms the whole scene; slabs: the scene's grid is split "
                          "into z-slabs over the ranks (sparse halo exchange of band records)")
@@ -577,6 +578,53 @@ def bench_batched_update(V, torch, b, singles, stream, flush, dims, records=2000
             "step": "one frame of incremental updates on every map (graph replays; records already on the device)"}
 
 
+def bench_untruncated(V, torch, wl, xyz, ones, stream, flush, steps=5, warm=3):
+    """The same scene with no truncation (the paper's dmax = infinity runs, Table II): reset + stage
+    device records + global transform over whole lines of the grid, event-timed with the L2
+    flushed before each step.  Bytes per voxel of the line passes (model, every value finite): x
+    12 (g1 written, read back, written), y and z 24 each (input 4, stack pushed and read 8 + 8,
+    output 4)."""
+    nx, ny, nz = wl["dims"]
+    m = V.Map(nx, ny, nz, None, voxel_size=0.1, stream=stream)
+
+    def step():
+        m.reset()
+        m.set_occupancy(xyz, ones)
+        m.global_()
+
+    for _ in range(warm):
+        step()
+    m.set_profiling(True)
+    ms, ph = [], {"ingest_ms": [], "x_ms": [], "y_ms": [], "z_ms": []}
+    for k in range(steps):
+        flush.fill_(k & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        pt = m.phase_times()
+        for key in ph:
+            ph[key].append(pt[key])
+    m.set_profiling(False)
+    info = m.info()
+    probe = m.query(np.array([[nx // 2, ny // 2, nz // 2]], np.int32))
+    m.close()
+    vox = nx * ny * nz
+    t = statistics.mean(ms)
+    phm = {k: statistics.mean(v) for k, v in ph.items()}
+    peak, peak_src = peaks()
+    per_vox = {"x_ms": 12, "y_ms": 24, "z_ms": 24}
+    return {"workload": wl["name"].replace(", dmax 32", "") + ", no truncation", "dmax": "none (untruncated)",
+            "ms_per_step": t, "value": vox / (t / 1e3) / 1e6, "unit": "Mvoxels/s (every voxel of the grid)",
+            "phases_ms": phm, "stored_bricks": info["allocated_bricks"], "finite_bricks": info["finite_bricks"],
+            "centre_voxel_D": int(probe[0]),
+            "passes_gbs_model": {k: vox * per_vox[k] / (phm[k] / 1e3) / 1e9 for k in per_vox},
+            "bytes_per_voxel_model": per_vox, "peak": peak, "peak_source": peak_src,
+            "l2": "flushed before every step (untimed)", "steps": steps}
+
+
 def bench_nearest(V, torch, m, dims, stream, reps=20):
     """Nearest-obstacle query of 2^20 voxels uniform in the grid, device in and out, event-timed."""
     nx, ny, nz = dims
@@ -992,6 +1040,8 @@ def main():
     if wl["kind"] == "tunnel" and not args.no_clearance:
         line["clearance"] = bench_clearance(V, torch, m, occ, stream)
         line["nearest"] = bench_nearest(V, torch, m, wl["dims"], stream)
+    if wl["kind"] == "tunnel" and not args.no_untruncated:
+        line["untruncated"] = bench_untruncated(V, torch, wl, xyz, ones, stream, flush)
     if wl["kind"] == "tunnel" and not args.no_crossover:
         line["crossover"] = bench_crossover(V, torch, wl, occ, xyz, stream, flush)
     if wl["kind"] == "tunnel" and not args.no_batched:

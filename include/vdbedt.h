@@ -71,13 +71,26 @@ typedef enum {
 #define VDBEDT_UNBOUNDED_MIN (-(1 << 20))
 #define VDBEDT_UNBOUNDED_MAX ((1 << 20) - 128)
 
+/* VDBEDT_FLAG_UNTRUNCATED: no truncation (the paper's dmax = infinity runs, Table II): D is Eq. 1's
+ * exact squared distance to the nearest occupied voxel anywhere in the grid, and VDBEDT_D_NONE at
+ * every voxel while the grid holds no obstacle (and for queries outside the grid).  dmax must be 0.
+ * A bounded grid only, with (nx-1)^2 + (ny-1)^2 + (nz-1)^2 < 2^31 - 1 so that every distance fits
+ * int32, and every brick stored from creation (max_bricks and max_nodes 0 or at least the grid's):
+ * about 6.2 KB per 8^3 brick (32-bit intermediates) plus, from the first transform, 8 bytes per
+ * voxel of line scratch.  The transform runs whole lines of the grid (x: nearest occupied voxel of
+ * the row; y, z: lower envelope of the parabolas rooted at the line's values); vdbedt_update applies
+ * the staged records and recomputes the field (global form).  Not available: batches,
+ * vdbedt_set_tuning, vdbedt_query_nearest and the unbounded flag. */
+#define VDBEDT_FLAG_UNTRUNCATED 2u
+#define VDBEDT_D_NONE 2147483647
+
 typedef struct {
   int32_t nx, ny, nz;  /* grid size in voxels, each >= 1 (at most 2^21 - 128; ignored when unbounded) */
-  int32_t dmax;        /* truncation distance in voxels, 1 <= dmax <= VDBEDT_DMAX_LIMIT */
+  int32_t dmax;        /* truncation distance in voxels, 1 <= dmax <= VDBEDT_DMAX_LIMIT (0 when untruncated) */
   float voxel_size;    /* metres per voxel (used by the clearance query), > 0 */
   int32_t device;      /* CUDA device ordinal */
   void* stream;        /* cudaStream_t to run on; NULL: the handle creates and owns one */
-  uint32_t flags;      /* 0 or VDBEDT_FLAG_UNBOUNDED */
+  uint32_t flags;      /* 0, VDBEDT_FLAG_UNBOUNDED or VDBEDT_FLAG_UNTRUNCATED */
   int64_t max_bricks;  /* brick capacity; 0: every brick of the grid (always enough) */
   int64_t max_nodes;   /* interior-node capacity (a node covers 16^3 bricks); 0: every node of the grid;
                           at most 4,194,302 */
@@ -110,7 +123,8 @@ typedef struct {
                              applying them (same field, lower cost; see vdbedt_update) */
 } vdbedt_update_stats;
 
-/* Create a handle for an nx x ny x nz grid with no obstacles (every D = dmax^2).
+/* Create a handle for an nx x ny x nz grid with no obstacles (every D = dmax^2; VDBEDT_D_NONE when
+ * untruncated).
  * Allocates the grid's storage for cfg->max_bricks bricks (about 4.1 KB each) and cfg->max_nodes
  * interior nodes (about 31 KB each) up front; the record stage and the ingest scratch grow on
  * demand (vdbedt_set_occupancy_counted reserves them ahead).  With both capacities set, the memory
@@ -119,7 +133,8 @@ typedef struct {
  * updates work at any grid size; the dense entry points and vdbedt_export_dense scale with the grid.
  * The brick capacity is at most 8,388,607 (max_bricks 0 on a larger grid is EINVAL: set it).
  * Exceeding a capacity during a transform is EOVERFLOW.
- * EINVAL: a size < 1, dmax outside [1, VDBEDT_DMAX_LIMIT], voxel_size <= 0, bad device.
+ * EINVAL: a size < 1, dmax outside [1, VDBEDT_DMAX_LIMIT] (not 0 with VDBEDT_FLAG_UNTRUNCATED, or a
+ * grid or capacities outside that flag's limits), voxel_size <= 0, unknown flags, bad device.
  * ENOMEM: device allocation failed. */
 vdbedt_status vdbedt_create(const vdbedt_config* cfg, vdbedt_handle* out);
 
@@ -176,7 +191,8 @@ vdbedt_status vdbedt_global(vdbedt_handle h);
  * after a stream synchronisation. */
 vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats);
 
-/* D at n voxel coordinates; coordinates outside the grid or in unstored bricks give dmax^2.
+/* D at n voxel coordinates; coordinates outside the grid or in unstored bricks give dmax^2
+ * (VDBEDT_D_NONE when untruncated).
  * on_device != 0: xyz and out_sqdist are device pointers; otherwise host pointers (the call waits). */
 vdbedt_status vdbedt_query(vdbedt_handle h, const int32_t* xyz, int64_t n, int32_t* out_sqdist, int on_device);
 
@@ -185,7 +201,7 @@ vdbedt_status vdbedt_query(vdbedt_handle h, const int32_t* xyz, int64_t n, int32
  * the lattice points with |o - v|^2 = D(v) in increasing (z, y, x) order, so ties go to the
  * smallest (z, y, x).  (-1, -1, -1) for voxels outside the grid or with D = dmax^2 (no obstacle
  * closer than dmax).  Reads the current field (after vdbedt_global / vdbedt_update).  on_device
- * as for vdbedt_query. */
+ * as for vdbedt_query.  EINVAL on an untruncated grid. */
 vdbedt_status vdbedt_query_nearest(vdbedt_handle h, const int32_t* xyz, int64_t n, int32_t* out_xyz, int on_device);
 
 /* The whole field as a dense int32 array out[nz][ny][nx] (host or device). */
@@ -199,7 +215,8 @@ vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device);
  * empty grid; mode 1 replays the update's changes).  This is how one grid split into z-slabs over
  * several GPUs exchanges only the occupied voxels (or the changed bricks) of each slab's halo band.
  * Synchronises; *n_out (host) receives the number of records; more than max_n is EOVERFLOW (the
- * first max_n are written, *n_out holds the full count).  Record order is unspecified. */
+ * first max_n are written, *n_out holds the full count).  Record order is unspecified.  Mode 1 is
+ * EINVAL on an untruncated grid (its updates recompute the field without a changed-brick list). */
 vdbedt_status vdbedt_export_occupancy(vdbedt_handle h, int32_t z_lo, int32_t z_hi, int32_t dz, int32_t mode,
                                       uint64_t* out, int64_t max_n, int64_t* n_out);
 
@@ -234,7 +251,7 @@ vdbedt_status vdbedt_clearance_backward(vdbedt_handle h, const float* pts, int64
  *            transform of Eq. 1 line by line).  Grids with dmax above 45 always take the envelope
  *            form.  Switching between the windowed and envelope forms changes how intermediate
  *            fields are stored, so the next vdbedt_update recomputes the whole field (as
- *            vdbedt_global).  Other values are EINVAL. */
+ *            vdbedt_global).  Other values are EINVAL, and so is any call on an untruncated grid. */
 typedef struct {
   int32_t x_run, y_run, z_run, variant;
 } vdbedt_tuning;

@@ -9,6 +9,9 @@ Functions (each cites the passage it follows; the exact rules are in the C heade
 * :func:`edt_naive`       -- Eq. 1 written out (every obstacle), truncated at dmax^2 (Sec. III).
 * :func:`edt_factorised`  -- Eq. 1 minimised one axis at a time (exact; min distributes over +).
 * :func:`edt_at`          -- Eq. 1 at sampled voxels, offsets scanned in increasing length.
+* :func:`edt_untruncated` -- Eq. 1 with no truncation (the paper's dmax = infinity runs, Table II):
+                            the factorised minimum with a cap beyond every distance in the grid;
+                            :func:`edt_untruncated_at` the same at sampled voxels, by brute force.
 * :class:`Alg1`           -- the paper's priority-queue raise/lower transform (Alg. 1, Sec. IV-B),
                             global (Lower only, Sec. V-A) and incremental.
 * :func:`clearance`       -- the clearance term of Eq. 2 as a squared hinge on a trilinear
@@ -102,6 +105,36 @@ def edt_factorised(occ_zyx: np.ndarray, dmax: int, threads: int = 0) -> np.ndarr
     if rc:
         raise ValueError(f"oracle_edt_factorised failed ({rc})")
     return out
+
+
+NONE = 2147483647  # untruncated: no occupied voxel anywhere in the grid
+
+
+def edt_untruncated(occ_zyx: np.ndarray, threads: int = 0) -> np.ndarray:
+    """Eq. 1 without the truncation (the paper's dmax = infinity, Table II): at every voxel the
+    squared distance to the nearest occupied voxel anywhere in the grid; NONE at every voxel of a
+    grid without one.  Any two voxels lie less than nx + ny + nz apart, so the factorised minimum
+    with that cap takes each whole line as its window and no value reaches the cap."""
+    occ = np.asarray(occ_zyx)
+    if not occ.any():
+        return np.full(occ.shape, NONE, dtype=np.int32)
+    nz, ny, nx = occ.shape
+    return edt_factorised(occ, nx + ny + nz, threads)
+
+
+def edt_untruncated_at(occ_zyx: np.ndarray, xyz: np.ndarray) -> np.ndarray:
+    """Eq. 1 without truncation at the voxels ``xyz`` [m, 3] (x, y, z), written out: the least
+    squared distance to every occupied voxel of the grid (brute force); NONE when it holds none."""
+    occ = np.asarray(occ_zyx)
+    oz, oy, ox = np.nonzero(occ)
+    obs = np.stack([ox, oy, oz], 1).astype(np.int32)
+    pts = np.asarray(xyz, dtype=np.int32).reshape(-1, 3)
+    out = np.full(pts.shape[0], NONE, dtype=np.int64)
+    if len(obs):
+        for i, p in enumerate(pts):
+            d = obs - p  # coordinates below 2^15: every square and sum fits int32
+            out[i] = np.min(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2])
+    return out.astype(np.int32)
 
 
 def edt_at(occ_zyx: np.ndarray, dmax: int, xyz: np.ndarray, threads: int = 0) -> np.ndarray:

@@ -17,6 +17,7 @@ over the library's forward and backward kernels).
 from .lib import (  # noqa: F401
     Batch,
     BatchUpdateGraph,
+    D_NONE,
     GlobalGraph,
     VDBEDT_DMAX_LIMIT,
     Map,

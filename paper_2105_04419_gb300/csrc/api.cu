@@ -55,6 +55,7 @@ struct vdbedt_map {
   Scratch vlast;  // per-voxel last-record table of the ordered ingest
   Scratch miss;   // flags and missing-brick list of the tracked (incremental) ingest
   Scratch io;  // host-input staging on the device
+  Scratch uts;  // line stacks of the untruncated transform
   Items items{};
   int32_t* changed = nullptr;
   Tuning tune;
@@ -228,6 +229,22 @@ vdbedt_status do_global(vdbedt_map* h) {
     clear_stage(h);
   }
   h->dense_pending = false;
+  if (h->g.untrunc) {
+    // every brick is stored: no activation or work lists, three whole-line passes
+    CK(h, ensure_scratch(h->uts, ut_scratch_bytes(h->g)), "untruncated scratch");
+    mark(h, 1);
+    mark(h, 2);
+    mark(h, 3);
+    CK(h, launch_ut_pass(h->g, 0, h->uts.buf, h->st), "x pass");
+    mark(h, 4);
+    CK(h, launch_ut_pass(h->g, 1, h->uts.buf, h->st), "y pass");
+    mark(h, 5);
+    CK(h, launch_ut_pass(h->g, 2, h->uts.buf, h->st), "z pass");
+    mark(h, 6);
+    h->ev_recorded = h->profiling && !capturing(h);
+    h->computed = true;
+    return VDBEDT_OK;
+  }
   mark(h, 1);
   CK(h, launch_activation_full(h->g, h->st), "activation");
   mark(h, 2);
@@ -263,14 +280,22 @@ int64_t config_cap(const vdbedt_config* cfg) {
 vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbedt_map** out) {
   if (!cfg || !out) return fail(nullptr, VDBEDT_EINVAL, "null argument");
   const bool unbounded = (cfg->flags & VDBEDT_FLAG_UNBOUNDED) != 0;
-  if (cfg->flags & ~(uint32_t)VDBEDT_FLAG_UNBOUNDED) return fail(nullptr, VDBEDT_EINVAL, "unknown flags");
+  const bool untrunc = (cfg->flags & VDBEDT_FLAG_UNTRUNCATED) != 0;
+  if (cfg->flags & ~(uint32_t)(VDBEDT_FLAG_UNBOUNDED | VDBEDT_FLAG_UNTRUNCATED))
+    return fail(nullptr, VDBEDT_EINVAL, "unknown flags");
   if (unbounded && slice) return fail(nullptr, VDBEDT_EINVAL, "a batch grid cannot be unbounded");
+  if (untrunc && (slice || unbounded))
+    return fail(nullptr, VDBEDT_EINVAL, "an untruncated grid is bounded and not part of a batch");
   if (unbounded && (cfg->max_bricks <= 0 || cfg->max_nodes <= 0))
     return fail(nullptr, VDBEDT_EINVAL, "an unbounded grid needs max_bricks and max_nodes");
   const int64_t nx = unbounded ? kUnboundedSize : cfg->nx, ny = unbounded ? kUnboundedSize : cfg->ny,
                 nz = unbounded ? kUnboundedSize : cfg->nz;
   if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, VDBEDT_EINVAL, "grid size must be >= 1");
-  if (cfg->dmax < 1 || cfg->dmax > VDBEDT_DMAX_LIMIT) return fail(nullptr, VDBEDT_EINVAL, "dmax out of range");
+  if (untrunc ? cfg->dmax != 0 : (cfg->dmax < 1 || cfg->dmax > VDBEDT_DMAX_LIMIT))
+    return fail(nullptr, VDBEDT_EINVAL, untrunc ? "an untruncated grid takes dmax 0" : "dmax out of range");
+  // untruncated: every squared distance of the grid below VDBEDT_D_NONE
+  if (untrunc && (nx - 1) * (nx - 1) + (ny - 1) * (ny - 1) + (nz - 1) * (nz - 1) >= (int64_t)VDBEDT_D_NONE)
+    return fail(nullptr, VDBEDT_EINVAL, "untruncated grid too large for int32 distances");
   if (!(cfg->voxel_size > 0.f)) return fail(nullptr, VDBEDT_EINVAL, "voxel_size must be > 0");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
@@ -287,6 +312,8 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   int64_t cap = cfg->max_bricks > 0 ? std::min<int64_t>(cfg->max_bricks, BX * BY * BZ) : BX * BY * BZ;
   if (cap * 512 >= (int64_t)0xFFFFFFFFll) return fail(nullptr, VDBEDT_EINVAL, "brick capacity too large (max 8M)");
   const int64_t node_cap = cfg->max_nodes > 0 ? std::min<int64_t>(cfg->max_nodes, NX * NY * NZ) : NX * NY * NZ;
+  if (untrunc && (cap < BX * BY * BZ || node_cap < NX * NY * NZ))
+    return fail(nullptr, VDBEDT_EINVAL, "an untruncated grid stores every brick (max_bricks, max_nodes 0)");
   if (node_cap > kMaxNodes) return fail(nullptr, VDBEDT_EINVAL, "node capacity too large (max 4,194,302)");
 
   DeviceGuard guard(cfg->device);
@@ -307,8 +334,9 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   g.NZ = (int)NZ;
   g.dmax = cfg->dmax;
   g.R = (cfg->dmax + 6) / 8;
-  g.INF = cfg->dmax * cfg->dmax;
-  g.half = (cfg->dmax <= 45 && g.R >= 1 && g.R <= 6) ? 1 : 0;  // fp16 fields unless the envelope form is chosen
+  g.INF = untrunc ? kNone : cfg->dmax * cfg->dmax;
+  g.half = (!untrunc && cfg->dmax <= 45 && g.R >= 1 && g.R <= 6) ? 1 : 0;  // fp16 fields unless the envelope form is chosen
+  g.untrunc = untrunc ? 1 : 0;
   uint32_t hcap = 64;
   while ((int64_t)hcap < 2 * node_cap) hcap <<= 1;
   g.hmask = hcap - 1;
@@ -366,8 +394,8 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
     h->items = slice->items;
   } else {
     AL(g.occ, cap * 8);
-    AL(g.g1, cap * kBrickVox);
-    AL(g.g2, cap * kBrickVox);
+    AL(g.g1, cap * kBrickVox * (untrunc ? 2 : 1));  // int32 intermediates when untruncated
+    AL(g.g2, cap * kBrickVox * (untrunc ? 2 : 1));
     AL(g.dist, cap * kBrickVox);
     AL(g.bcoord, cap);
     AL(g.bflags, cap);
@@ -395,6 +423,10 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   cudaMemsetAsync(g.nclaim, 0, sizeof(uint32_t) * (size_t)node_cap * 128, h->st);
   cudaMemsetAsync(g.mark, 0, sizeof(int32_t) * (size_t)node_cap * 3 * 1024, h->st);
   if (!slice) cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, h->st);
+  if (untrunc) {
+    e = launch_ut_init(g, h->st);
+    if (e != cudaSuccess) return bail(e, "untruncated init");
+  }
   e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return bail(e, "init");
   *out = h;
@@ -424,6 +456,7 @@ void destroy_impl(vdbedt_map* h) {
   if (h->vlast.buf) cudaFree(h->vlast.buf);
   if (h->miss.buf) cudaFree(h->miss.buf);
   if (h->io.buf) cudaFree(h->io.buf);
+  if (h->uts.buf) cudaFree(h->uts.buf);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (int i = 0; i < 7; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -555,7 +588,8 @@ vdbedt_status vdbedt_set_occupancy_dense(vdbedt_handle h, const uint8_t* grid, i
     CK(h, cudaMemcpyAsync(h->io.buf, grid, bytes, cudaMemcpyHostToDevice, h->st), "h2d");
     src = (const uint8_t*)h->io.buf;
   }
-  CK(h, launch_ingest_dense(h->g, src, h->scr, h->st), "dense ingest");
+  CK(h, h->g.untrunc ? launch_ut_dense(h->g, src, h->st) : launch_ingest_dense(h->g, src, h->scr, h->st),
+     "dense ingest");
   if (!on_device) CK(h, cudaStreamSynchronize(h->st), "sync");
   h->dense_pending = true;
   return VDBEDT_OK;
@@ -565,7 +599,7 @@ vdbedt_status vdbedt_reset(vdbedt_handle h) {
   vdbedt_status s = check_handle(h);
   if (s) return s;
   DeviceGuard guard(h->device);
-  CK(h, launch_reset(h->g, h->st), "reset");
+  CK(h, h->g.untrunc ? launch_ut_reset(h->g, h->st) : launch_reset(h->g, h->st), "reset");
   clear_stage(h);
   h->computed = false;
   h->dense_pending = false;
@@ -585,7 +619,7 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
   DeviceGuard guard(h->device);
   const int64_t nrec = h->stage_n;
   const bool counted = h->stage_counted;
-  if (!h->computed || h->dense_pending) {
+  if (!h->computed || h->dense_pending || h->g.untrunc) {  // untruncated: always the global form
     s = do_global(h);
     if (s) return s;
   } else {
@@ -629,7 +663,7 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     stats->x_bricks = c[C_XB];
     stats->y_bricks = c[C_YB];
     stats->z_bricks = c[C_ZB];
-    stats->global_form = c[C_BIG];
+    stats->global_form = h->g.untrunc ? 1 : c[C_BIG];
   }
   return VDBEDT_OK;
 }
@@ -661,6 +695,7 @@ vdbedt_status vdbedt_query_nearest(vdbedt_handle h, const int32_t* xyz, int64_t 
   vdbedt_status s = check_handle(h);
   if (s) return s;
   if (n < 0 || (n > 0 && (!xyz || !out_xyz))) return fail(h, VDBEDT_EINVAL, "bad query arguments");
+  if (h->g.untrunc) return fail(h, VDBEDT_EINVAL, "no nearest-obstacle query on an untruncated grid");
   if (n == 0) return VDBEDT_OK;
   DeviceGuard guard(h->device);
   if (on_device) {
@@ -704,7 +739,7 @@ vdbedt_status vdbedt_export_occupancy(vdbedt_handle h, int32_t z_lo, int32_t z_h
                                       uint64_t* out, int64_t max_n, int64_t* n_out) {
   vdbedt_status s = check_handle(h);
   if (s) return s;
-  if (!n_out || (max_n > 0 && !out) || max_n < 0 || (mode != 0 && mode != 1))
+  if (!n_out || (max_n > 0 && !out) || max_n < 0 || (mode != 0 && mode != 1) || (mode == 1 && h->g.untrunc))
     return fail(h, VDBEDT_EINVAL, "bad export arguments");
   // caller z -> stored z (an unbounded grid's coordinates are stored shifted)
   const int64_t zl = std::max<int64_t>((int64_t)z_lo + h->g.off, 0), zh = std::min<int64_t>((int64_t)z_hi + h->g.off, h->g.nz);
@@ -769,6 +804,7 @@ vdbedt_status vdbedt_set_tuning(vdbedt_handle h, const vdbedt_tuning* t) {
   vdbedt_status s = check_handle(h);
   if (s) return s;
   if (!t) return fail(h, VDBEDT_EINVAL, "null tuning");
+  if (h->g.untrunc) return fail(h, VDBEDT_EINVAL, "an untruncated grid has no tuning");
   auto ok_run = [](int r) { return r == 0 || r == 4 || r == 8 || r == 16; };
   const int v = t->variant;
   if (!ok_run(t->x_run) || !ok_run(t->y_run) || !ok_run(t->z_run) ||

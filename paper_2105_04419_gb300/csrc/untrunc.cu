@@ -1,0 +1,261 @@
+// Untruncated transform (VDBEDT_FLAG_UNTRUNCATED): Eq. 1 without the truncation, i.e. the exact
+// squared distance to the nearest occupied voxel anywhere in a bounded grid (the paper's
+// dmax = infinity runs, Table II).  With no truncation every voxel is in reach of every obstacle,
+// so every brick is stored, brick (bx, by, bz) at slot bx + BX (by + BY bz), and the transform runs
+// over whole lines of the grid, one axis after the other (Eq. 1's minimum taken per axis):
+//   x: per row, the distance to the nearest occupied voxel on either side (a forward and a
+//      backward sweep), g1 = dx^2;
+//   y, z: per line, the lower envelope of the parabolas f(i) + (t - i)^2 rooted at the line's
+//      finite values (g1, then g2): built on a stack in one sweep, read back in a second.  Two
+//      parabolas are compared through their intersection with the denominators multiplied out,
+//      exactly, in 64-bit integers (the grid's size limit keeps every product below 2^50).
+// kNone marks a row, plane or grid without an obstacle.  Only voxels inside the grid are read or
+// written; g1 and g2 hold int32 here (their arrays are allocated twice as large).
+#include "vdbedt_internal.cuh"
+
+namespace vdbedt {
+namespace {
+
+constexpr int kUT = 256;
+
+__device__ __forceinline__ int ut_slot(const GridView& g, int bx, int by, int bz) {
+  return bx + g.BX * (by + g.BY * bz);
+}
+
+__device__ __forceinline__ int ut_vox(int x, int y, int z) { return (x & 7) + 8 * (y & 7) + 64 * (z & 7); }
+
+unsigned ut_blocks(int64_t threads) {
+  const int64_t b = (threads + kUT - 1) / kUT;
+  return (unsigned)(b < 1 ? 1 : (b > 152 * 64 ? 152 * 64 : b));
+}
+
+// Interior nodes of every key of the grid (node indices in creation order).
+__global__ void k_ut_nodes(GridView g) {
+  const int64_t nk = (int64_t)g.NX * g.NY * g.NZ;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nk; k += (int64_t)gridDim.x * blockDim.x)
+    get_or_create_node(g, (unsigned long long)k);
+}
+
+// Every brick of the grid at its fixed slot, with an empty occupancy.
+__global__ void k_ut_bricks(GridView g) {
+  const int64_t nb = (int64_t)g.BX * g.BY * g.BZ;
+  if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_NBRICKS] = (int)nb;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    const int bx = (int)(b % g.BX), r = (int)(b / g.BX), by = r % g.BY, bz = r / g.BY;
+    const int node = find_node(g, node_key_of(g, bx, by, bz));
+    if (node < 0) {
+      set_error(g, kErrInternal);
+      continue;
+    }
+    g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] = (int)b;
+    g.bcoord[b] = make_int4(bx, by, bz, node);
+    g.bflags[b] = 0u;
+    g.bepoch[b] = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) g.occ[(size_t)b * 8 + q] = 0ull;
+  }
+}
+
+// Empty occupancy and flags; the counters start over except the stored bricks and nodes.
+__global__ void k_ut_reset(GridView g) {
+  const int64_t nb = (int64_t)g.BX * g.BY * g.BZ;
+  if (blockIdx.x == 0 && (int)threadIdx.x < C_NUM && threadIdx.x != C_NBRICKS && threadIdx.x != C_NNODES)
+    g.counters[threadIdx.x] = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb * 8; i += (int64_t)gridDim.x * blockDim.x) {
+    g.occ[i] = 0ull;
+    if ((i & 7) == 0) g.bflags[i >> 3] = 0u;
+  }
+}
+
+// Occupancy from a dense uint8 grid [nz][ny][nx] (nonzero = occupied): a thread per (brick,
+// plane) assembles the plane's 64-bit word (bit x + 8 y) from eight rows of eight bytes.
+__global__ void k_ut_dense(GridView g, const uint8_t* __restrict__ grid) {
+  const int64_t nw = (int64_t)g.BX * g.BY * g.BZ * 8;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (int64_t)gridDim.x * blockDim.x) {
+    // i = bx + BX (pz + 8 (by + BY bz)): neighbouring threads read neighbouring 8-byte row pieces
+    const int bx = (int)(i % g.BX);
+    const int64_t r = i / g.BX;
+    const int pz = (int)(r & 7);
+    const int64_t rb = r >> 3;
+    const int by = (int)(rb % g.BY), bz = (int)(rb / g.BY);
+    const int z = 8 * bz + pz;
+    unsigned long long w = 0ull;
+    if (z < g.nz) {
+      for (int py = 0; py < 8; ++py) {
+        const int y = 8 * by + py;
+        if (y >= g.ny) break;
+        const uint8_t* row = grid + ((size_t)z * g.ny + y) * g.nx;
+        for (int px = 0; px < 8; ++px) {
+          const int x = 8 * bx + px;
+          if (x < g.nx && row[x]) w |= 1ull << (px + 8 * py);
+        }
+      }
+    }
+    g.occ[(size_t)ut_slot(g, bx, by, bz) * 8 + pz] = w;
+  }
+}
+
+// x pass: a thread per voxel row (64 rows of a brick line on consecutive threads).  The forward
+// sweep stores the distance to the last occupied voxel at or before x (-1: none); the backward
+// sweep combines it with the distance to the next one and stores g1 = d^2 (kNone: empty row).
+__global__ void k_ut_x(GridView g) {
+  int32_t* __restrict__ g1 = reinterpret_cast<int32_t*>(g.g1);
+  const int64_t nrows = (int64_t)g.BY * g.BZ * 64;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nrows; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t line = t >> 6;
+    const int q = (int)(t & 63);
+    const int by = (int)(line % g.BY), bz = (int)(line / g.BY);
+    const int y = 8 * by + (q & 7), z = 8 * bz + (q >> 3);
+    if (y >= g.ny || z >= g.nz) continue;
+    const int shift = 8 * (y & 7);
+    const size_t row = (size_t)(8 * (y & 7) + 64 * (z & 7));
+    int last = -1;
+    for (int bx = 0; bx < g.BX; ++bx) {
+      const int s = ut_slot(g, bx, by, bz);
+      const uint32_t byte = (uint32_t)(g.occ[(size_t)s * 8 + (z & 7)] >> shift) & 0xFFu;
+      int v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int x = 8 * bx + i;
+        if ((byte >> i) & 1u) last = x;
+        v[i] = last < 0 ? -1 : x - last;
+      }
+      int4* dst = reinterpret_cast<int4*>(g1 + (size_t)s * kBrickVox + row);
+      dst[0] = make_int4(v[0], v[1], v[2], v[3]);
+      dst[1] = make_int4(v[4], v[5], v[6], v[7]);
+    }
+    int next = -1;
+    for (int bx = g.BX - 1; bx >= 0; --bx) {
+      const int s = ut_slot(g, bx, by, bz);
+      const uint32_t byte = (uint32_t)(g.occ[(size_t)s * 8 + (z & 7)] >> shift) & 0xFFu;
+      int4* dst = reinterpret_cast<int4*>(g1 + (size_t)s * kBrickVox + row);
+      const int4 a = dst[0], b = dst[1];
+      int v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 7; i >= 0; --i) {
+        const int x = 8 * bx + i;
+        if (x >= g.nx) continue;  // padding of the last brick: never read
+        if ((byte >> i) & 1u) next = x;
+        int d = v[i];
+        if (next >= 0 && (d < 0 || next - x < d)) d = next - x;
+        v[i] = d < 0 ? kNone : d * d;
+      }
+      dst[0] = make_int4(v[0], v[1], v[2], v[3]);
+      dst[1] = make_int4(v[4], v[5], v[6], v[7]);
+    }
+  }
+}
+
+// y (AXIS 1: g1 -> g2) or z (AXIS 2: g2 -> D) pass: a thread per line, lines (x, z) or (x, y)
+// with x fastest.  The line's stack (position, value) lives in `stack`, n entries per line.
+template <int AXIS>
+__global__ void k_ut_env(GridView g, const int32_t* __restrict__ in, int32_t* __restrict__ out, int2* __restrict__ stack) {
+  const int n = AXIS == 1 ? g.ny : g.nz;
+  const int64_t nlines = (int64_t)g.nx * (AXIS == 1 ? g.nz : g.ny);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nlines; t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % g.nx), c = (int)(t / g.nx);  // c: z (AXIS 1) or y (AXIS 2)
+    auto at = [&](int i) -> size_t {
+      return AXIS == 1 ? (size_t)ut_slot(g, x >> 3, i >> 3, c >> 3) * kBrickVox + ut_vox(x, i, c)
+                       : (size_t)ut_slot(g, x >> 3, c >> 3, i >> 3) * kBrickVox + ut_vox(x, c, i);
+    };
+    int2* st = stack + (size_t)t * n;
+    // build: the top two entries stay in registers (p1 top, p0 below it)
+    int m = 0, p0 = 0, f0 = 0, p1 = 0, f1 = 0;
+    for (int i = 0; i < n; ++i) {
+      const int fi = in[at(i)];
+      if (fi == kNone) continue;
+      const long long Fi = (long long)fi + (long long)i * i;
+      while (m >= 2) {
+        // drop the top when the new parabola undercuts it no later than the top undercuts the one
+        // below: (Fi - F1) / (i - p1) <= (F1 - F0) / (p1 - p0)
+        const long long F1 = (long long)f1 + (long long)p1 * p1, F0 = (long long)f0 + (long long)p0 * p0;
+        if ((Fi - F1) * (long long)(p1 - p0) > (F1 - F0) * (long long)(i - p1)) break;
+        --m;
+        p1 = p0;
+        f1 = f0;
+        if (m >= 2) {
+          const int2 e = st[m - 2];
+          p0 = e.x;
+          f0 = e.y;
+        }
+      }
+      st[m] = make_int2(i, fi);
+      p0 = p1;
+      f0 = f1;
+      p1 = i;
+      f1 = fi;
+      ++m;
+    }
+    // read back: the envelope's parabola moves forward with the position
+    if (m == 0) {
+      for (int i = 0; i < n; ++i) out[at(i)] = kNone;
+      continue;
+    }
+    int k = 0;
+    int2 cur = st[0], nxt = m > 1 ? st[1] : cur;
+    for (int i = 0; i < n; ++i) {
+      while (k + 1 < m) {
+        // the next parabola is no higher at i: F(nxt) - F(cur) <= 2 i (nxt - cur)
+        const long long Fc = (long long)cur.y + (long long)cur.x * cur.x;
+        const long long Fn = (long long)nxt.y + (long long)nxt.x * nxt.x;
+        if (Fn - Fc > 2ll * i * (long long)(nxt.x - cur.x)) break;
+        ++k;
+        cur = nxt;
+        if (k + 1 < m) nxt = st[k + 1];
+      }
+      const int d = i - cur.x;
+      out[at(i)] = cur.y + d * d;
+    }
+  }
+}
+
+// Brick flags after the transform: obstacle bits, and finite D (voxel (0, 0, 0) of every brick lies
+// inside the grid; with an obstacle anywhere every voxel is finite).
+__global__ void k_ut_flags(GridView g) {
+  const int64_t nb = (int64_t)g.BX * g.BY * g.BZ;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long any = 0ull;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) any |= g.occ[(size_t)b * 8 + q];
+    uint32_t f = any ? F_OBST : 0u;
+    if (g.dist[(size_t)b * kBrickVox] != kNone) f |= F_FINITE | F_G2FIN | F_G1FIN;
+    g.bflags[b] = f;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ut_init(const GridView& g, cudaStream_t st) {
+  VDB_LAUNCH(k_ut_nodes, ut_blocks((int64_t)g.NX * g.NY * g.NZ), kUT, 0, st, g);
+  VDB_LAUNCH(k_ut_bricks, ut_blocks((int64_t)g.BX * g.BY * g.BZ), kUT, 0, st, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ut_reset(const GridView& g, cudaStream_t st) {
+  VDB_LAUNCH(k_ut_reset, ut_blocks((int64_t)g.BX * g.BY * g.BZ * 8), kUT, 0, st, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ut_dense(const GridView& g, const uint8_t* grid, cudaStream_t st) {
+  VDB_LAUNCH(k_ut_dense, ut_blocks((int64_t)g.BX * g.BY * g.BZ * 8), kUT, 0, st, g, grid);
+  return cudaGetLastError();
+}
+
+size_t ut_scratch_bytes(const GridView& g) { return (size_t)g.nx * g.ny * g.nz * sizeof(int2); }
+
+cudaError_t launch_ut_pass(const GridView& g, int axis, void* scratch, cudaStream_t st) {
+  int32_t* g1 = reinterpret_cast<int32_t*>(g.g1);
+  int32_t* g2 = reinterpret_cast<int32_t*>(g.g2);
+  int2* stack = static_cast<int2*>(scratch);
+  if (axis == 0) {
+    VDB_LAUNCH(k_ut_x, ut_blocks((int64_t)g.BY * g.BZ * 64), kUT, 0, st, g);
+  } else if (axis == 1) {
+    VDB_LAUNCH(k_ut_env<1>, ut_blocks((int64_t)g.nx * g.nz), kUT, 0, st, g, g1, g2, stack);
+  } else {
+    VDB_LAUNCH(k_ut_env<2>, ut_blocks((int64_t)g.nx * g.ny), kUT, 0, st, g, g2, g.dist, stack);
+    VDB_LAUNCH(k_ut_flags, ut_blocks((int64_t)g.BX * g.BY * g.BZ), kUT, 0, st, g);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace vdbedt

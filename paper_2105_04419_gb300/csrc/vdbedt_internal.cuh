@@ -37,6 +37,7 @@ constexpr int kMaxNodes = (1 << kIndexBits) - 2;
 constexpr int kUnboundedOffset = VDBEDT_UNBOUNDED_OFFSET;
 constexpr int kUnboundedSize = VDBEDT_UNBOUNDED_MAX + VDBEDT_UNBOUNDED_OFFSET;
 constexpr int32_t kNoSlot = -1;
+constexpr int32_t kNone = VDBEDT_D_NONE;  // untruncated grids: no obstacle on the line / in the grid
 
 // device error bits
 constexpr int kErrOverflow = 1;
@@ -85,6 +86,8 @@ struct GridView {
                       // integers (lower-envelope kernels)
   int off;            // added to caller coordinates (0; kUnboundedOffset for an unbounded grid)
   int unbounded;      // 1: no per-node-key arrays (nodes are created where records fall)
+  int untrunc;        // 1: no truncation; every brick stored at slot bx + BX (by + BY bz), g1 / g2 hold
+                      // int32 (their arrays are twice as large), INF = kNone
   uint32_t hmask;     // hash capacity - 1
   int cap;            // brick capacity
   int node_cap;       // node capacity
@@ -413,6 +416,13 @@ cudaError_t launch_item_slots_batch(const GridView* views, const Tuning& t, cons
 // (views == nullptr: a single grid `one`).
 cudaError_t launch_count_run_bricks(const GridView* views, const GridView& one, const int32_t* items_ctr, int item_cap,
                                    const Tuning& t, const Items& it, cudaStream_t st);
+// Untruncated grids: store every brick (at creation), clear the occupancy (reset), take a dense
+// uint8 grid, and the transform proper (three whole-line passes; `scratch` holds 8 bytes per voxel).
+cudaError_t launch_ut_init(const GridView& g, cudaStream_t st);
+cudaError_t launch_ut_reset(const GridView& g, cudaStream_t st);
+cudaError_t launch_ut_dense(const GridView& g, const uint8_t* grid, cudaStream_t st);
+size_t ut_scratch_bytes(const GridView& g);
+cudaError_t launch_ut_pass(const GridView& g, int axis, void* scratch, cudaStream_t st);
 // slot lists of every queued run (half path)
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st);
 

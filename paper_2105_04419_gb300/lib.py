@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 
@@ -135,6 +136,8 @@ def _ptr_host(a: np.ndarray) -> int:
 
 UNBOUNDED_OFFSET = 1 << 20
 UNBOUNDED_MIN, UNBOUNDED_MAX = -(1 << 20), (1 << 20) - 128
+FLAG_UNBOUNDED, FLAG_UNTRUNCATED = 1, 2
+D_NONE = 2147483647  # untruncated grids: no obstacle anywhere (VDBEDT_D_NONE)
 
 
 def pack_records(xyz, occ, offset: int = 0) -> np.ndarray:
@@ -155,7 +158,9 @@ class Map:
     front, so that a large grid mapped only in part needs memory for the mapped part alone; a
     transform that needs more reports EOVERFLOW.  With `unbounded`, nx, ny, nz are ignored and
     coordinates are signed in [UNBOUNDED_MIN, UNBOUNDED_MAX) on every axis (both capacities are
-    then required; no dense entry points)."""
+    then required; no dense entry points).  `dmax=None` (or ``math.inf``) asks for no truncation:
+    D is the exact squared distance to the nearest obstacle anywhere in the grid, D_NONE while the
+    grid holds none (every brick stored; no batches, tuning or nearest-obstacle query)."""
 
     def __init__(self, nx: int, ny: int, nz: int, dmax: int, voxel_size: float = 0.1, device: int = 0,
                  stream=None, max_bricks: int = 0, max_nodes: int = 0, unbounded: bool = False, _borrow=None):
@@ -167,19 +172,22 @@ class Map:
             self.device, self.shape_xyz, self.dmax, self.voxel_size = device, (nx, ny, nz), dmax, voxel_size
             return
         self._owned = True
+        untruncated = dmax is None or (isinstance(dmax, float) and math.isinf(dmax))
         if stream is None:
             # a stream of its own: the library would otherwise create one that torch cannot see
             stream = torch.cuda.Stream(device)
         self.device = device
         self.stream = stream
-        cfg = Config(nx, ny, nz, dmax, voxel_size, device, ctypes.c_void_p(stream.cuda_stream), 1 if unbounded else 0,
-                     max_bricks, max_nodes)
+        flags = (FLAG_UNBOUNDED if unbounded else 0) | (FLAG_UNTRUNCATED if untruncated else 0)
+        cfg = Config(nx, ny, nz, 0 if untruncated else dmax, voxel_size, device, ctypes.c_void_p(stream.cuda_stream),
+                     flags, max_bricks, max_nodes)
         h = ctypes.c_void_p()
         _check(lib.vdbedt_create(ctypes.byref(cfg), ctypes.byref(h)), "vdbedt_create")
         self._h = h
         self.shape_xyz = None if unbounded else (nx, ny, nz)
         self.unbounded = unbounded
-        self.dmax = dmax
+        self.untruncated = untruncated
+        self.dmax = None if untruncated else dmax
         self.voxel_size = voxel_size
 
     # -- lifetime --

@@ -79,3 +79,22 @@ def test_create_without_device_is_einval(lib):
     assert lb.vdbedt_destroy(None) == 0
     bad = L.Config(0, 8, 8, 4, 0.1, 0, None, 0, 0)
     assert lb.vdbedt_create(ctypes.byref(bad), ctypes.byref(h)) == 1
+
+
+def test_header_constants_match_binding(tmp_path):
+    """The binding's copies of the header's macros (flags, sentinels, limits) hold the same values."""
+    import subprocess
+    from paper_2105_04419_gb300 import lib as L
+    pairs = {"VDBEDT_FLAG_UNBOUNDED": L.FLAG_UNBOUNDED, "VDBEDT_FLAG_UNTRUNCATED": L.FLAG_UNTRUNCATED,
+             "VDBEDT_D_NONE": L.D_NONE, "VDBEDT_UNBOUNDED_OFFSET": L.UNBOUNDED_OFFSET,
+             "VDBEDT_UNBOUNDED_MIN": L.UNBOUNDED_MIN, "VDBEDT_UNBOUNDED_MAX": L.UNBOUNDED_MAX,
+             "VDBEDT_DMAX_LIMIT": L.VDBEDT_DMAX_LIMIT}
+    lines = ['#include <stdio.h>', '#include "vdbedt.h"', "int main(void) {"]
+    lines += [f'printf("{k} %lld\\n", (long long)({k}));' for k in pairs]
+    lines.append("return 0; }")
+    c = tmp_path / "consts.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)])
+    got = {l.split()[0]: int(l.split()[1]) for l in subprocess.check_output([str(exe)], text=True).split("\n") if l}
+    assert got == pairs
