@@ -159,40 +159,48 @@ __global__ void k_ut_env(GridView g, const int32_t* __restrict__ in, int32_t* __
                        : (size_t)ut_slot(g, x >> 3, c >> 3, i >> 3) * kBrickVox + ut_vox(x, c, i);
     };
     int2* st = stack + (size_t)t * n;
-    // build: the top two entries stay in registers (p1 top, p0 below it)
+    // build: the top two entries stay in registers (p1 top, p0 below it); the inputs are loaded a
+    // brick (8 positions) at a time, all eight before any is used
     int m = 0, p0 = 0, f0 = 0, p1 = 0, f1 = 0;
-    for (int i = 0; i < n; ++i) {
-      const int fi = in[at(i)];
-      if (fi == kNone) continue;
-      const long long Fi = (long long)fi + (long long)i * i;
-      while (m >= 2) {
-        // drop the top when the new parabola undercuts it no later than the top undercuts the one
-        // below: (Fi - F1) / (i - p1) <= (F1 - F0) / (p1 - p0)
-        const long long F1 = (long long)f1 + (long long)p1 * p1, F0 = (long long)f0 + (long long)p0 * p0;
-        if ((Fi - F1) * (long long)(p1 - p0) > (F1 - F0) * (long long)(i - p1)) break;
-        --m;
-        p1 = p0;
-        f1 = f0;
-        if (m >= 2) {
-          const int2 e = st[m - 2];
-          p0 = e.x;
-          f0 = e.y;
+    for (int i0 = 0; i0 < n; i0 += 8) {
+      int fv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) fv[j] = i0 + j < n ? in[at(i0 + j)] : kNone;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int i = i0 + j, fi = fv[j];
+        if (fi == kNone) continue;
+        const long long Fi = (long long)fi + (long long)i * i;
+        while (m >= 2) {
+          // drop the top when the new parabola undercuts it no later than the top undercuts the one
+          // below: (Fi - F1) / (i - p1) <= (F1 - F0) / (p1 - p0)
+          const long long F1 = (long long)f1 + (long long)p1 * p1, F0 = (long long)f0 + (long long)p0 * p0;
+          if ((Fi - F1) * (long long)(p1 - p0) > (F1 - F0) * (long long)(i - p1)) break;
+          --m;
+          p1 = p0;
+          f1 = f0;
+          if (m >= 2) {
+            const int2 e = st[m - 2];
+            p0 = e.x;
+            f0 = e.y;
+          }
         }
+        st[m] = make_int2(i, fi);
+        p0 = p1;
+        f0 = f1;
+        p1 = i;
+        f1 = fi;
+        ++m;
       }
-      st[m] = make_int2(i, fi);
-      p0 = p1;
-      f0 = f1;
-      p1 = i;
-      f1 = fi;
-      ++m;
     }
     // read back: the envelope's parabola moves forward with the position
     if (m == 0) {
       for (int i = 0; i < n; ++i) out[at(i)] = kNone;
       continue;
     }
+    // entries k, k + 1 and (loaded ahead) k + 2 in registers
     int k = 0;
-    int2 cur = st[0], nxt = m > 1 ? st[1] : cur;
+    int2 cur = st[0], nxt = m > 1 ? st[1] : cur, ahead = m > 2 ? st[2] : cur;
     for (int i = 0; i < n; ++i) {
       while (k + 1 < m) {
         // the next parabola is no higher at i: F(nxt) - F(cur) <= 2 i (nxt - cur)
@@ -201,7 +209,8 @@ __global__ void k_ut_env(GridView g, const int32_t* __restrict__ in, int32_t* __
         if (Fn - Fc > 2ll * i * (long long)(nxt.x - cur.x)) break;
         ++k;
         cur = nxt;
-        if (k + 1 < m) nxt = st[k + 1];
+        nxt = ahead;
+        if (k + 2 < m) ahead = st[k + 2];
       }
       const int d = i - cur.x;
       out[at(i)] = cur.y + d * d;
