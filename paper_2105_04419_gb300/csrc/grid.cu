@@ -1524,9 +1524,12 @@ __global__ void k_count_run_bricks(const GridView* __restrict__ views, GridView 
 
 // ---- incremental ----
 // For every changed brick: refresh its obstacle flag; if it holds obstacles, mark its dilation.
-// A block per changed brick: its first threads find or create the interior nodes the brick's cube
-// spans (at most 4 per axis), then a thread per row (y, z) of the cube sets the row's x extent in
-// the allocation masks of one or two nodes.
+// With at most two changed bricks per block, a block per changed brick: its first threads find or
+// create the interior nodes the brick's cube spans (at most 4 per axis), then a thread per row
+// (y, z) of the cube sets the row's x extent in the allocation masks of its nodes (short dependent
+// chains for the few-brick updates of a single map).  With more (a batch's share of the launch, a
+// large update), a thread per (changed brick, row) with its own node lookups keeps every thread of
+// the GPU busy instead.
 template <class US>
 __global__ void __launch_bounds__(256) k_changed_flags_dilate(US us) {
   pdl_enter();
@@ -1542,6 +1545,49 @@ __global__ void __launch_bounds__(256) k_changed_flags_dilate(US us) {
   // (same field; measured crossover on the tunnel scene).  Every block reaches the same decision.
   if ((int64_t)nc * side * side * side > (int64_t)kBigUpdate * max(g.counters[C_NBRICKS], 1)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_BIG] = 1;
+    return;
+  }
+  if (nc > 2 * (int)gridDim.x) {
+    // many changed bricks per block (a batch's share of the grid, or a large update): a thread per
+    // (changed brick, row), each row's nodes looked up on its own, the rounds block-uniform
+    const int rows = side * side, nseg = (side + 15) / 16 + 1;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < (int64_t)nc * rows;
+         base += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = base + threadIdx.x;
+      int s = -1, r = 0;
+      bool obst = false;
+      if (i < (int64_t)nc * rows) {
+        s = changed[i / rows];
+        r = (int)(i % rows);
+        obst = brick_has_obstacle(g, s);
+        if (r == 0) {
+          const uint32_t f = g.bflags[s];
+          g.bflags[s] = obst ? (f | F_OBST) : (f & ~F_OBST);
+        }
+      }
+      int4 c = make_int4(0, 0, 0, 0);
+      if (obst) c = g.bcoord[s];
+      const int y = c.y + r % side - R, z = c.z + r / side - R;
+      const bool live = obst && (unsigned)y < (unsigned)g.BY && (unsigned)z < (unsigned)g.BZ;
+      const int x0 = max(c.x - R, 0), x1 = min(c.x + R, g.BX - 1);
+      const int ly = y & 15, lz = z & 15, word = (ly >> 1) + 8 * lz;
+      int xa = x0;
+      for (int k = 0; k < nseg; ++k) {  // the row's segments, one node each (same count on every lane)
+        bool fresh = false;
+        int node = -1;
+        if (live && xa <= x1) {
+          const int xe = min(x1, xa | 15);
+          node = get_or_create_node(g, node_key_of(g, xa, y, z));
+          if (node >= 0) {
+            const uint32_t bitsx = ((1u << ((xe & 15) - (xa & 15) + 1)) - 1u) << (xa & 15);
+            const uint32_t add = bitsx << (16 * (ly & 1));
+            fresh = (add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add)) && claim_fresh_word(g, node, word);
+          }
+          xa = xe + 1;
+        }
+        list_fresh_words(g, fresh, node * 128 + word);
+      }
+    }
     return;
   }
   for (int i = (int)blockIdx.x; i < nc; i += (int)gridDim.x) {
@@ -1597,7 +1643,8 @@ __global__ void __launch_bounds__(256) k_changed_flags_dilate(US us) {
 // spans (at most 4 per axis: 2R + 1 <= 47 bricks), then a thread per (column, z run) of the cube
 // reads the run's bricks inside the cube and queues the run once if one is stored, and for the
 // changed brick's z layer that brick's y run and x run.  Runs are aligned to their length (4, 8
-// or 16) inside nodes, hence at multiples of it in grid coordinates.
+// or 16) inside nodes, hence at multiples of it in grid coordinates.  With more than two changed
+// bricks per block, a thread per (changed brick, offset in its cube) instead, as for the dilation.
 template <class US>
 __global__ void __launch_bounds__(256, 8) k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
   pdl_enter();
@@ -1610,6 +1657,35 @@ __global__ void __launch_bounds__(256, 8) k_mark_dirty(US us, int rx, int ry, in
   const int nc = min(g.counters[C_CHANGED], g.cap);
   const int epoch = g.counters[C_EPOCH];
   const int R = g.R;
+  if (nc > 2 * (int)gridDim.x) {
+    // many changed bricks per block: a thread per (changed brick, offset in its cube), each brick's
+    // node looked up on its own, the rounds block-uniform
+    const int side = 2 * R + 1, vol = side * side * side;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < (int64_t)nc * vol;
+         base += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = base + threadIdx.x;
+      bool wx = false, wy = false, wz = false;
+      unsigned long long px = 0, py = 0, pz = 0;
+      if (i < (int64_t)nc * vol) {
+        const int r = (int)(i % vol);
+        const int dx = r % side - R, dy = (r / side) % side - R, dz = r / (side * side) - R;
+        const int4 c = g.bcoord[changed[i / vol]];
+        const int bx = c.x + dx, by = c.y + dy, bz = c.z + dz;
+        if ((unsigned)bx < (unsigned)g.BX && (unsigned)by < (unsigned)g.BY && (unsigned)bz < (unsigned)g.BZ) {
+          const int node = find_node(g, node_key_of(g, bx, by, bz));
+          if (node >= 0 && g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] >= 0) {
+            if (dy == 0 && dz == 0) wx = claim_run(g, 0, bx, by, bz, node, rx, epoch, px);
+            if (dz == 0) wy = claim_run(g, 1, bx, by, bz, node, ry, epoch, py);
+            wz = claim_run(g, 2, bx, by, bz, node, rz, epoch, pz);
+          }
+        }
+      }
+      emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
+      emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
+      emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
+    }
+    return;
+  }
   for (int i = (int)blockIdx.x; i < nc; i += (int)gridDim.x) {
     const int4 c = g.bcoord[changed[i]];
     const int x0 = max(c.x - R, 0), x1 = min(c.x + R, g.BX - 1);
@@ -1717,7 +1793,7 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
   // incremental form: new bricks of the dilation, the dirty runs
   // a warp per fresh word (the count is on the device): one wave of 8 warps per block on every SM
   VDB_LAUNCH(k_alloc_fresh<US>, dim3(share(1216), k), kT, 0, st, us);
-  VDB_LAUNCH_PDL(k_mark_dirty<US>, dim3(share(1216), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
+  VDB_LAUNCH_PDL(k_mark_dirty<US>, dim3(share(2432), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }
 
@@ -1972,7 +2048,7 @@ cudaError_t launch_count_run_bricks(const GridView* views, const GridView& one, 
 
 cudaError_t launch_item_slots_batch(const GridView* views, const Tuning& t, const Items& it, int32_t* items_ctr,
                                     int item_cap, cudaStream_t st) {
-  VDB_LAUNCH(k_item_slots_batch, dim3(405, 3), kT, 0, st, views, items_ctr, item_cap, t.run[0], t.run[1], t.run[2],
+  VDB_LAUNCH(k_item_slots_batch, dim3(1216, 3), kT, 0, st, views, items_ctr, item_cap, t.run[0], t.run[1], t.run[2],
              it);
   return cudaGetLastError();
 }
