@@ -997,10 +997,11 @@ def main():
                              "step": "the same step captured once into a CUDA graph and replayed"}}
 
     if not args.no_e2e:
-        # end to end through the C ABI with host buffers (pinned): the occupied-voxel records (packed
-        # 64-bit records; the (x, y, z) + occ form beside it) host -> device, the transform, and a
-        # host consumer's read-back: D at 2^20 voxels uniform in the grid, queried from host memory
-        # into host memory (coordinates in, distances out), with the grid's counters
+        # end to end through the C ABI with host buffers (pinned): the occupancy host -> device (the
+        # occupied bricks as 64-byte masks; packed 64-bit records and the (x, y, z) + occ form
+        # beside it), the transform, and a host consumer's read-back: D at 2^20 voxels uniform in the
+        # grid, queried from host memory into host memory (coordinates in, distances out), with the
+        # grid's counters
         nq = 1 << 20
         rq = np.random.default_rng(21)
         q_h = torch.from_numpy(np.stack([rq.integers(0, nx, nq), rq.integers(0, ny, nq), rq.integers(0, nz, nq)],
@@ -1009,6 +1010,10 @@ def main():
         packed_h = torch.from_numpy(V.pack_records(xyz_h, ones_h).view(np.int64)).pin_memory().numpy().view(np.uint64)
         xyz_p = torch.from_numpy(xyz_h).pin_memory().numpy()
         ones_p = torch.from_numpy(ones_h).pin_memory().numpy()
+        bk_h, bm_h = V.brick_masks(occ)
+        nb = len(bk_h)
+        bk_p = torch.from_numpy(bk_h).pin_memory().numpy()
+        bm_p = torch.from_numpy(bm_h.view(np.int64)).pin_memory().numpy().view(np.uint64)
         lib = V.load()
 
         def e2e(stage):
@@ -1026,15 +1031,21 @@ def main():
                 ms.append(1e3 * (time.perf_counter() - t0))
             return max_over_ranks(statistics.mean(ms[max(3, args.warmup):])), inf2
 
-        ems, inf2 = e2e(lambda: m.set_occupancy_packed(packed_h))
-        ems3, _ = e2e(lambda: m.set_occupancy(xyz_p, ones_p))
+        emsb, inf2 = e2e(lambda: m.set_occupancy_bricks(bk_p, bm_p))
         qref = m.query(q_h)
-        line["e2e"] = {"value": inf2["finite_bricks"] * 512 * world / (ems / 1e3) / 1e6, "unit": "Mvoxels/s",
-                       "ms_per_step": ems, "host_buffers": "pinned", "records": "packed 64-bit",
-                       "h2d_bytes_per_step": int(n * 8 + nq * 12), "d2h_bytes_per_step": int(nq * 4 + 4 * 19),
+        same_b = bool(np.array_equal(qref, d_h))
+        ems, _ = e2e(lambda: m.set_occupancy_packed(packed_h))
+        ems3, _ = e2e(lambda: m.set_occupancy(xyz_p, ones_p))
+        act = inf2["finite_bricks"] * 512 * world
+        line["e2e"] = {"value": act / (emsb / 1e3) / 1e6, "unit": "Mvoxels/s",
+                       "ms_per_step": emsb, "host_buffers": "pinned",
+                       "records": f"occupied bricks as 64-byte masks + brick coordinates ({nb} bricks)",
+                       "h2d_bytes_per_step": int(nb * 76 + nq * 12), "d2h_bytes_per_step": int(nq * 4 + 4 * 19 + 16),
                        "readback": f"D at {nq} voxels (vdbedt_query, host in and out) + grid counters",
-                       "readback_equals_device_query": bool(np.array_equal(qref, d_h)),
-                       "triples_form": {"ms_per_step": ems3, "value": inf2["finite_bricks"] * 512 * world / (ems3 / 1e3) / 1e6,
+                       "readback_equals_device_query": same_b,
+                       "packed_form": {"ms_per_step": ems, "value": act / (ems / 1e3) / 1e6,
+                                       "h2d_bytes_per_step": int(n * 8 + nq * 12)},
+                       "triples_form": {"ms_per_step": ems3, "value": act / (ems3 / 1e3) / 1e6,
                                         "h2d_bytes_per_step": int(n * 13 + nq * 12)}}
 
     if wl["kind"] == "tunnel" and not args.no_clearance:

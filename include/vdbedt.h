@@ -158,6 +158,18 @@ vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const ui
  * synchronising call); page-locked host arrays are read in place. */
 vdbedt_status vdbedt_set_occupancy_packed(vdbedt_handle h, const uint64_t* rec, int64_t n, int on_device);
 
+/* Occupied voxels given brick by brick (Sec. IV-A's 8^3 leaves), 76 bytes per brick however many of
+ * its voxels are occupied -- a fraction of the record stream over a host link when obstacles fill
+ * bricks densely: bxyz[3k .. 3k + 2] is a brick (bx, by, bz) (caller voxel coordinates divided by 8,
+ * rounded down: signed on an unbounded grid) and masks[8k + z] its plane z, bit x + 8 y marking
+ * voxel (8 bx + x, 8 by + y, 8 bz + z) occupied.  Equivalent to one "set" record (occ 1) per bit,
+ * staged after the records already staged; bits at 0 stage nothing.  The records are written into
+ * the stage on the device (a bit count sizes it first, so the call waits for the device, also
+ * with on_device != 0).  EINVAL (whole call rejected): a brick outside the grid, a bit for a voxel
+ * outside the grid, n < 0; records staged with vdbedt_set_occupancy_counted and not yet applied. */
+vdbedt_status vdbedt_set_occupancy_bricks(vdbedt_handle h, const int32_t* bxyz, const uint64_t* masks, int64_t n,
+                                          int on_device);
+
 /* Stage up to n_max occupancy records in device memory whose actual count is the int32 at n_dev
  * (device memory), read when the stream reaches the call -- the same edits as vdbedt_set_occupancy
  * with on_device = 1, in a form whose launches do not depend on the count, so that a staging call

@@ -23,6 +23,7 @@ from .lib import (  # noqa: F401
     Map,
     UpdateGraph,
     VdbedtError,
+    brick_masks,
     clearance_cost,
     edt_dense_noalloc,
     global_batched,

@@ -29,6 +29,10 @@ cudaError_t launch_pack_records(const int32_t* xyz, const uint8_t* occ, int64_t 
                                 int32_t* counters, cudaStream_t st);
 cudaError_t launch_check_packed(const uint64_t* src, int64_t n, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
                                 int32_t* counters, cudaStream_t st);
+cudaError_t launch_check_bricks(const int32_t* bxyz, const uint64_t* masks, int64_t n, const GridView& g,
+                                int32_t* invalid, unsigned long long* count, cudaStream_t st);
+cudaError_t launch_expand_bricks(const int32_t* bxyz, const uint64_t* masks, int64_t n, const GridView& g, rec_t* dst,
+                                 unsigned long long* cursor, cudaStream_t st);
 }
 
 struct vdbedt_batch;
@@ -551,6 +555,46 @@ vdbedt_status vdbedt_set_occupancy_packed(vdbedt_handle h, const uint64_t* rec, 
     if (h->h_pinned[0] != 0) return fail(h, VDBEDT_EINVAL, "packed record outside the grid; call rejected");
   }
   h->stage_n += n;
+  return VDBEDT_OK;
+}
+
+vdbedt_status vdbedt_set_occupancy_bricks(vdbedt_handle h, const int32_t* bxyz, const uint64_t* masks, int64_t n,
+                                          int on_device) {
+  vdbedt_status s = check_handle(h);
+  if (s) return s;
+  if (n < 0) return fail(h, VDBEDT_EINVAL, "negative brick count");
+  if (n == 0) return VDBEDT_OK;
+  if (!bxyz || !masks) return fail(h, VDBEDT_EINVAL, "null bricks");
+  if (h->stage_counted) return fail(h, VDBEDT_EINVAL, "records staged with a device count must be applied first");
+  DeviceGuard guard(h->device);
+  // the bricks on the device (host arrays copied once: both passes read them), two counter words
+  // (invalid bricks, then the 64-bit bit count / write cursor) after them
+  const size_t bk = ((size_t)n * 12 + 255) & ~(size_t)255, bm = ((size_t)n * 64 + 255) & ~(size_t)255;
+  CK(h, ensure_scratch(h->io, (on_device ? 0 : bk + bm) + 256), "io alloc");
+  const int32_t* dk = bxyz;
+  const uint64_t* dm = masks;
+  char* ctr = (char*)h->io.buf + (on_device ? 0 : bk + bm);
+  if (!on_device) {
+    CK(h, cudaMemcpyAsync(h->io.buf, bxyz, (size_t)n * 12, cudaMemcpyHostToDevice, h->st), "h2d");
+    CK(h, cudaMemcpyAsync((char*)h->io.buf + bk, masks, (size_t)n * 64, cudaMemcpyHostToDevice, h->st), "h2d");
+    dk = (const int32_t*)h->io.buf;
+    dm = (const uint64_t*)((char*)h->io.buf + bk);
+  }
+  int32_t* invalid = (int32_t*)ctr;
+  unsigned long long* count = (unsigned long long*)(ctr + 8);
+  CK(h, cudaMemsetAsync(ctr, 0, 16, h->st), "memset");
+  CK(h, launch_check_bricks(dk, dm, n, h->g, invalid, count, h->st), "check bricks");
+  CK(h, cudaMemcpyAsync(h->h_pinned + 48, ctr, 16, cudaMemcpyDeviceToHost, h->st), "d2h");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  if (h->h_pinned[48] != 0) return fail(h, VDBEDT_EINVAL, "brick outside the grid or bit for a voxel outside it; call rejected");
+  unsigned long long bits = 0;
+  memcpy(&bits, h->h_pinned + 50, sizeof(bits));
+  if (bits == 0) return VDBEDT_OK;
+  s = ensure_stage(h, h->stage_n + (int64_t)bits);
+  if (s) return s;
+  CK(h, cudaMemsetAsync(count, 0, 8, h->st), "memset");
+  CK(h, launch_expand_bricks(dk, dm, n, h->g, h->stage + h->stage_n, count, h->st), "expand bricks");
+  h->stage_n += (int64_t)bits;
   return VDBEDT_OK;
 }
 
@@ -1515,12 +1559,97 @@ __global__ void k_check_packed(const uint64_t* __restrict__ src, int64_t n, int 
 }
 }  // namespace
 
+// Brick masks: a thread per (brick, plane).  The check pass validates the brick and the plane's
+// bits against the grid (ragged edges included) and counts the set bits; the expansion pass writes
+// one "set" record per bit, places reserved a warp at a time.
+__global__ void k_check_bricks(const int32_t* __restrict__ bxyz, const uint64_t* __restrict__ masks, int64_t n,
+                               GridView g, int32_t* invalid, unsigned long long* count) {
+  const int64_t nw = n * 8;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nw; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int bits = 0;
+    if (i < nw) {
+      const int64_t k = i >> 3;
+      const int pz = (int)(i & 7);
+      const unsigned long long m = masks[i];
+      const int bx = bxyz[3 * k] + (g.off >> 3), by = bxyz[3 * k + 1] + (g.off >> 3), bz = bxyz[3 * k + 2] + (g.off >> 3);
+      bool ok = (unsigned)bx < (unsigned)g.BX && (unsigned)by < (unsigned)g.BY && (unsigned)bz < (unsigned)g.BZ;
+      if (ok && m) {
+        // bits past the grid's last voxel on each axis (a ragged last brick)
+        const int ex = min(8, g.nx - 8 * bx), ey = min(8, g.ny - 8 * by);
+        const unsigned long long row = ex >= 8 ? 0xFFull : ((1ull << ex) - 1ull);
+        unsigned long long inside = 0ull;
+        for (int y = 0; y < ey; ++y) inside |= row << (8 * y);
+        ok = 8 * bz + pz < g.nz ? (m & ~inside) == 0ull : false;
+      }
+      if (!ok) atomicAdd(invalid, 1);
+      bits = ok ? __popcll(m) : 0;
+    }
+    // one atomic per warp for the count
+    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+    if ((threadIdx.x & 31) == 0 && bits) atomicAdd(count, (unsigned long long)bits);
+  }
+}
+
+__global__ void k_expand_bricks(const int32_t* __restrict__ bxyz, const uint64_t* __restrict__ masks, int64_t n,
+                                GridView g, rec_t* __restrict__ dst, unsigned long long* cursor) {
+  const int64_t nw = n * 8;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nw; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    unsigned long long m = 0ull;
+    int bx = 0, by = 0, z = 0;
+    if (i < nw) {
+      const int64_t k = i >> 3;
+      m = masks[i];
+      bx = bxyz[3 * k] + (g.off >> 3);
+      by = bxyz[3 * k + 1] + (g.off >> 3);
+      z = 8 * (bxyz[3 * k + 2] + (g.off >> 3)) + (int)(i & 7);
+    }
+    const int bits = __popcll(m);
+    // the warp's places: an inclusive scan of the bit counts, one atomic
+    int incl = bits;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long first = 0ull;
+    if (lane == 31 && total) first = atomicAdd(cursor, (unsigned long long)total);
+    first = __shfl_sync(0xffffffffu, first, 31);
+    unsigned long long p = first + (unsigned long long)(incl - bits);
+    while (m) {
+      const int b = __ffsll((long long)m) - 1;
+      m &= m - 1ull;
+      dst[p++] = pack_rec(8 * bx + (b & 7), 8 * by + (b >> 3), z, 1);
+    }
+  }
+}
+
 cudaError_t launch_check_packed(const uint64_t* src, int64_t n, int nx, int ny, int nz, rec_t* dst, int32_t* invalid,
                                 int32_t* counters, cudaStream_t st) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
   if (b < 1) b = 1;
   VDB_LAUNCH(k_check_packed, (unsigned)b, 256, 0, st, src, n, nx, ny, nz, dst, invalid, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_bricks(const int32_t* bxyz, const uint64_t* masks, int64_t n, const GridView& g,
+                                int32_t* invalid, unsigned long long* count, cudaStream_t st) {
+  int64_t b = (n * 8 + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  VDB_LAUNCH(k_check_bricks, (unsigned)b, 256, 0, st, bxyz, masks, n, g, invalid, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_bricks(const int32_t* bxyz, const uint64_t* masks, int64_t n, const GridView& g, rec_t* dst,
+                                 unsigned long long* cursor, cudaStream_t st) {
+  int64_t b = (n * 8 + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  VDB_LAUNCH(k_expand_bricks, (unsigned)b, 256, 0, st, bxyz, masks, n, g, dst, cursor);
   return cudaGetLastError();
 }
 

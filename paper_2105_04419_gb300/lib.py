@@ -62,6 +62,7 @@ SIGNATURES = {
     "vdbedt_set_occupancy": (ctypes.c_int, [_H, _P, _P, _I64, ctypes.c_int]),
     "vdbedt_set_occupancy_counted": (ctypes.c_int, [_H, _P, _P, _P, _I64]),
     "vdbedt_set_occupancy_packed": (ctypes.c_int, [_H, _P, _I64, ctypes.c_int]),
+    "vdbedt_set_occupancy_bricks": (ctypes.c_int, [_H, _P, _P, _I64, ctypes.c_int]),
     "vdbedt_set_occupancy_dense": (ctypes.c_int, [_H, _P, ctypes.c_int]),
     "vdbedt_reset": (ctypes.c_int, [_H]),
     "vdbedt_global": (ctypes.c_int, [_H]),
@@ -149,6 +150,28 @@ def pack_records(xyz, occ, offset: int = 0) -> np.ndarray:
         raise ValueError("coordinates must lie in [0, 2^21)")
     u = x.astype(np.uint64)
     return u[:, 0] | (u[:, 1] << np.uint64(21)) | (u[:, 2] << np.uint64(42)) | ((o & np.uint64(1)) << np.uint64(63))
+
+
+def brick_masks(occ_zyx, origin_xyz=(0, 0, 0)):
+    """The occupied bricks of a dense uint8 grid [nz, ny, nx] whose voxel (0, 0, 0) sits at
+    `origin_xyz` (multiples of 8): brick coordinates [n, 3] int32 and their masks [n, 8] uint64
+    (plane z of the brick, bit x + 8 y), for Map.set_occupancy_bricks."""
+    occ = np.asarray(occ_zyx) != 0
+    if any(int(o) % 8 for o in origin_xyz):
+        raise ValueError("the origin must be a multiple of 8 on every axis")
+    nz, ny, nx = occ.shape
+    pz, py, px = -nz % 8, -ny % 8, -nx % 8
+    g = np.pad(occ, ((0, pz), (0, py), (0, px)))
+    bz, by, bx = g.shape[0] // 8, g.shape[1] // 8, g.shape[2] // 8
+    # [bz, z, by, y, bx, x] -> [bz, by, bx, z, y, x]: per brick, plane z, row y, column x
+    t = g.reshape(bz, 8, by, 8, bx, 8).transpose(0, 2, 4, 1, 3, 5)
+    bits = np.packbits(t.reshape(bz, by, bx, 8, 64), axis=-1, bitorder="little")  # 8 bytes per plane
+    words = bits.view(np.uint64).reshape(bz, by, bx, 8)
+    keep = words.any(axis=-1)
+    iz, iy, ix = np.nonzero(keep)
+    o = [int(v) // 8 for v in origin_xyz]
+    bxyz = np.stack([ix + o[0], iy + o[1], iz + o[2]], 1).astype(np.int32)
+    return bxyz, np.ascontiguousarray(words[keep])
 
 
 class Map:
@@ -254,6 +277,28 @@ class Map:
             self._enter(r)
             _check(lib.vdbedt_set_occupancy_packed(self._h, r.data_ptr(), r.shape[0], 1),
                    "vdbedt_set_occupancy_packed", self._h)
+
+    def set_occupancy_bricks(self, bxyz, masks):
+        """Stage occupied voxels brick by brick: bxyz [n, 3] int32 brick coordinates (voxel // 8),
+        masks [n, 8] uint64 (plane z, bit x + 8 y); numpy arrays (host) or CUDA tensors (device).
+        One "set" record per bit; see brick_masks."""
+        lib = load()
+        if isinstance(bxyz, np.ndarray):
+            k = np.ascontiguousarray(bxyz, dtype=np.int32).reshape(-1, 3)
+            m = np.ascontiguousarray(masks, dtype=np.uint64).reshape(-1, 8)
+            if k.shape[0] != m.shape[0]:
+                raise ValueError("one 8-word mask per brick")
+            _check(lib.vdbedt_set_occupancy_bricks(self._h, _ptr_host(k), _ptr_host(m), k.shape[0], 0),
+                   "vdbedt_set_occupancy_bricks", self._h)
+        else:
+            torch = _torch()
+            k = bxyz.to(torch.int32).contiguous().view(-1, 3)
+            m = masks.contiguous().view(-1, 8)
+            if m.element_size() != 8 or not m.is_cuda or k.shape[0] != m.shape[0]:
+                raise TypeError("masks are 64-bit integers, one 8-word mask per brick, on the device")
+            self._enter(k, m)
+            _check(lib.vdbedt_set_occupancy_bricks(self._h, k.data_ptr(), m.data_ptr(), k.shape[0], 1),
+                   "vdbedt_set_occupancy_bricks", self._h)
 
     def set_occupancy_counted(self, xyz, occ, count, n_max: int):
         """Stage up to n_max device records whose count is the int32 CUDA tensor `count` (read on
