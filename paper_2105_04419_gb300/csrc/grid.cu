@@ -123,6 +123,7 @@ struct UpdBatch {
 // ---- reset ----
 template <class VS>
 __global__ void k_reset_nodes(VS vs) {
+  pdl_enter();
   int bid, nblk, gi;
   const GridView g = vs.get(bid, nblk, gi);
   (void)gi;
@@ -324,6 +325,7 @@ __device__ __forceinline__ int warp_reserve(int32_t* ctr, bool want) {
 
 __global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int64_t n, const int32_t* n_dev,
                                  uint32_t* __restrict__ keys) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int64_t ne = rec_count(n, n_dev);  // keys past the count are the sentinel
   GRID_STRIDE(i, n) {
@@ -408,6 +410,7 @@ __device__ __forceinline__ void mark_record(const GridView& g, bool have, rec_t 
 
 __global__ void k_mark_record_bricks(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
                                      int32_t* __restrict__ flag, unsigned long long* __restrict__ dbits) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int64_t n = rec_count(n_max, n_dev);
   // kMarkRecs records per thread and iteration, all loaded before any is used (the loop bounds are
@@ -462,11 +465,13 @@ __device__ __forceinline__ void create_flagged_nodes(const GridView& g, int32_t*
 }
 
 __global__ void k_create_flagged_nodes(GridView g, int32_t* __restrict__ nflag, int64_t nkeys) {
+  pdl_enter();
   create_flagged_nodes(g, nflag, nkeys);
 }
 
 // Node flags of the unique brick keys (radix path).
 __global__ void k_flag_key_nodes(GridView g, const uint32_t* __restrict__ uniq, int64_t n, int32_t* __restrict__ nflag) {
+  pdl_enter();
   const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], n);
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t lb = uniq[j];
@@ -481,6 +486,7 @@ __global__ void k_flag_key_nodes(GridView g, const uint32_t* __restrict__ uniq, 
 // key in the warp sets it (without reading it first).
 __global__ void k_compact_flag_index(GridView g, const int32_t* __restrict__ flag, int64_t n,
                                      uint32_t* __restrict__ out, int32_t* __restrict__ nflag) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   GRID_STRIDE(i, n) {
     int nk = -1;
@@ -502,6 +508,7 @@ __global__ void k_compact_flag_index(GridView g, const int32_t* __restrict__ fla
 }
 
 __global__ void k_head_flags(const uint32_t* __restrict__ keys, int64_t n, uint32_t limit, int32_t* __restrict__ flag) {
+  pdl_enter();
   GRID_STRIDE(i, n) {
     if (i < n) {
       uint32_t k = keys[i];
@@ -512,6 +519,7 @@ __global__ void k_head_flags(const uint32_t* __restrict__ keys, int64_t n, uint3
 
 __global__ void k_compact_keys(const uint32_t* __restrict__ keys, const int32_t* __restrict__ flag,
                                const int32_t* __restrict__ pos, int64_t n, uint32_t* __restrict__ out) {
+  pdl_enter();
   GRID_STRIDE(i, n) {
     if (i < n && flag[i]) out[pos[i]] = keys[i];
   }
@@ -520,6 +528,7 @@ __global__ void k_compact_keys(const uint32_t* __restrict__ keys, const int32_t*
 // Bricks of the unique keys: node found or inserted, slot reserved with one atomic per block.
 __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__ uniq, int64_t n, bool init,
                                         const unsigned long long* __restrict__ dbits) {
+  pdl_enter();
   const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], n);
   GRID_STRIDE(j, cnt) {
     int bx = 0, by = 0, bz = 0, node = -1;
@@ -574,6 +583,7 @@ __global__ void k_alloc_obstacle_bricks(GridView g, const uint32_t* __restrict__
 // of one x-row usually sit next to each other) are merged by a segmented OR over the warp, and the
 // last lane of each segment issues the atomic.
 __global__ void k_apply_set_only(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev) {
+  pdl_enter();
   if (g.counters[C_HAS_ZERO]) return;
   const int lane = threadIdx.x & 31;
   const int64_t n = rec_count(n_max, n_dev);
@@ -762,11 +772,13 @@ __device__ __forceinline__ void apply_last(const GridView& g, const rec_t* __res
 
 __global__ void k_rec_last(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev, bool force,
                            int32_t* __restrict__ vlast) {
+  pdl_enter();
   rec_last(g, rec, n_max, n_dev, force, vlast);
 }
 
 __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t n_max, const int32_t* n_dev,
                              bool force, bool track, int32_t* __restrict__ vlast, int32_t* __restrict__ changed) {
+  pdl_enter();
   apply_last(g, rec, n_max, n_dev, force, track, vlast, changed);
 }
 
@@ -1955,9 +1967,9 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
     e = cudaMemsetAsync(g.counters + C_UNIQUE, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_compact_flag_index, blocks_for((int64_t)nbr), kT, 0, st, g, flag, (int64_t)nbr, ka, nflag);
-    VDB_LAUNCH(k_create_flagged_nodes, blocks_for(nkeys), kT, 0, st, g, nflag, nkeys);
-    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for((int64_t)nbr), kT, 0, st, g, ka, (int64_t)nbr, track, dbits);
-    if (!track && !dbits) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
+    VDB_LAUNCH_PDL(k_create_flagged_nodes, blocks_for(nkeys), kT, 0, st, g, nflag, nkeys);
+    VDB_LAUNCH_PDL(k_alloc_obstacle_bricks, blocks_for((int64_t)nbr), kT, 0, st, g, ka, (int64_t)nbr, track, dbits);
+    if (!track && !dbits) VDB_LAUNCH_PDL(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
   } else {
     // LSD radix sort of the brick keys, unique, compaction
     VDB_LAUNCH(k_rec_brick_keys, nbk, kT, 0, st, g, rec, n, n_dev, ka);
@@ -1974,13 +1986,13 @@ cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n
     e = cudaMemsetAsync(nflag, 0, sizeof(int32_t) * (size_t)nkeys, st);
     if (e != cudaSuccess) return e;
     VDB_LAUNCH(k_flag_key_nodes, blocks_for(n), kT, 0, st, g, uniq, n, nflag);
-    VDB_LAUNCH(k_create_flagged_nodes, blocks_for(nkeys), kT, 0, st, g, nflag, nkeys);
-    VDB_LAUNCH(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, uniq, n, track, nullptr);
-    if (!track) VDB_LAUNCH(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
+    VDB_LAUNCH_PDL(k_create_flagged_nodes, blocks_for(nkeys), kT, 0, st, g, nflag, nkeys);
+    VDB_LAUNCH_PDL(k_alloc_obstacle_bricks, blocks_for(n), kT, 0, st, g, uniq, n, track, nullptr);
+    if (!track) VDB_LAUNCH_PDL(k_apply_set_only, nbk, kT, 0, st, g, rec, n, n_dev);
   }
   // ordered path (its kernels return at once when no record clears a voxel and flips are untracked)
-  VDB_LAUNCH(k_rec_last, nbk, kT, 0, st, g, rec, n, n_dev, track, vlast);
-  VDB_LAUNCH(k_apply_last, nbk, kT, 0, st, g, rec, n, n_dev, track, track, vlast, changed);
+  VDB_LAUNCH_PDL(k_rec_last, nbk, kT, 0, st, g, rec, n, n_dev, track, vlast);
+  VDB_LAUNCH_PDL(k_apply_last, nbk, kT, 0, st, g, rec, n, n_dev, track, track, vlast, changed);
   return cudaGetLastError();
 }
 
@@ -2007,17 +2019,17 @@ cudaError_t launch_ingest_dense(const GridView& g, const uint8_t* grid, Scratch&
 
 cudaError_t launch_activation_full(const GridView& g, cudaStream_t st) {
   const OneView v{g};
-  VDB_LAUNCH(k_clear_masks<OneView>, 256, kT, 0, st, v);
-  VDB_LAUNCH(k_obstacle_flags<OneView>, 1024, kT, 0, st, v);
-  VDB_LAUNCH(k_node_halo<OneView>, 64, kT, 0, st, v);
+  VDB_LAUNCH_PDL(k_clear_masks<OneView>, 256, kT, 0, st, v);
+  VDB_LAUNCH_PDL(k_obstacle_flags<OneView>, 1024, kT, 0, st, v);
+  VDB_LAUNCH_PDL(k_node_halo<OneView>, 64, kT, 0, st, v);
   if (g.R <= 16) {
-    VDB_LAUNCH(k_dilate_nodes<OneView>, g.node_cap < 1024 ? g.node_cap : 1024, 256, 0, st, v);
+    VDB_LAUNCH_PDL(k_dilate_nodes<OneView>, g.node_cap < 1024 ? g.node_cap : 1024, 256, 0, st, v);
   } else {
-    VDB_LAUNCH((k_dilate_stage<0, OneView>), 256, kT, 0, st, v);
-    VDB_LAUNCH((k_dilate_stage<1, OneView>), 256, kT, 0, st, v);
-    VDB_LAUNCH((k_dilate_stage<2, OneView>), 256, kT, 0, st, v);
+    VDB_LAUNCH_PDL((k_dilate_stage<0, OneView>), 256, kT, 0, st, v);
+    VDB_LAUNCH_PDL((k_dilate_stage<1, OneView>), 256, kT, 0, st, v);
+    VDB_LAUNCH_PDL((k_dilate_stage<2, OneView>), 256, kT, 0, st, v);
   }
-  VDB_LAUNCH(k_alloc_marked<OneView>, g.node_cap * 16 < 8192 ? g.node_cap * 16 : 8192, kT, 0, st, v, false);
+  VDB_LAUNCH_PDL(k_alloc_marked<OneView>, g.node_cap * 16 < 8192 ? g.node_cap * 16 : 8192, kT, 0, st, v, false);
   return cudaGetLastError();
 }
 
