@@ -241,14 +241,17 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
     # dilation and the dirty runs, items = slot lists of the dirty runs
     phase_med = {k: statistics.median(p[k] for p in phases) for k in phases[0]}
 
-    def timed(run_frame):
+    def timed(run_frame, label):
+        # an NVTX range per timed sequence, so that a profiler can take just these frames
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nframes)]
+        torch.cuda.nvtx.range_push(label)
         for k in range(nframes):
             flush.fill_(k & 255)
             ev[k][0].record(stream)
             run_frame(k)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         return [a.elapsed_time(b) for a, b in ev]
 
     me = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
@@ -260,7 +263,7 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
         me.set_occupancy(*sl[k])
         me.update()
 
-    eager_ms = timed(eager)
+    eager_ms = timed(eager, "incremental_eager_frames")
     eager_launches = (V.kernel_launches() - launches0) / nframes
     D_eager = me.export_dense(on_device=True)
     me.close()
@@ -269,7 +272,7 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
     mg.set_tuning(INCR_RUN, INCR_RUN, INCR_RUN, 3)
     mg.global_()
     graph = V.UpdateGraph(mg, max(counts))
-    graph_ms = timed(lambda k: graph.run(*sl[k]))
+    graph_ms = timed(lambda k: graph.run(*sl[k]), "incremental_graph_frames")
     D_graph = mg.export_dense(on_device=True)
     same = bool(torch.equal(D_eager, D_graph))
     del D_eager, D_graph

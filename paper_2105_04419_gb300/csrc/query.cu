@@ -42,8 +42,18 @@ __global__ void k_export_dense(GridView g, int32_t* __restrict__ out) {
   }
 }
 
-__device__ __forceinline__ bool occupied_at(const GridView& g, int x, int y, int z) {
-  const int s = find_brick(g, x >> 3, y >> 3, z >> 3);
+// Occupancy bit of voxel (x, y, z) (inside the grid), keeping the thread's last node lookup (key,
+// node): the candidates of one sphere walk mostly fall in one interior node, so most lookups skip
+// the hash table.
+__device__ __forceinline__ bool occupied_at_cached(const GridView& g, int x, int y, int z, unsigned long long& key,
+                                                   int& node) {
+  const unsigned long long k = node_key_of(g, x >> 3, y >> 3, z >> 3);
+  if (k != key) {
+    key = k;
+    node = find_node(g, k);
+  }
+  if (node < 0) return false;
+  const int s = g.child[(size_t)node * kNodeBricks + local_brick(x >> 3, y >> 3, z >> 3)];
   return s >= 0 && ((g.occ[(size_t)s * 8 + (z & 7)] >> ((x & 7) + 8 * (y & 7))) & 1ull) != 0ull;
 }
 
@@ -69,6 +79,8 @@ __global__ void k_query_nearest(GridView g, const int32_t* __restrict__ xyz, int
     const int D = sqdist_at(g, x, y, z);
     if ((unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz && D < g.INF) {
       bool found = false;
+      unsigned long long ckey = ~0ull;  // no node looked up yet
+      int cnode = -1;
       const int r = isq[D];
       for (int dz = -r; dz <= r && !found; ++dz) {
         const int oz = z + dz, rem = D - dz * dz;
@@ -78,9 +90,9 @@ __global__ void k_query_nearest(GridView g, const int32_t* __restrict__ xyz, int
           const int oy = y + dy, rem2 = rem - dy * dy;
           const int dx = isq[rem2];
           if (dx * dx != rem2 || (unsigned)oy >= (unsigned)g.ny) continue;
-          if (x - dx >= 0 && occupied_at(g, x - dx, oy, oz)) {
+          if (x - dx >= 0 && occupied_at_cached(g, x - dx, oy, oz, ckey, cnode)) {
             rx = x - dx, ry = oy, rz = oz, found = true;
-          } else if (dx > 0 && x + dx < g.nx && occupied_at(g, x + dx, oy, oz)) {
+          } else if (dx > 0 && x + dx < g.nx && occupied_at_cached(g, x + dx, oy, oz, ckey, cnode)) {
             rx = x + dx, ry = oy, rz = oz, found = true;
           }
         }

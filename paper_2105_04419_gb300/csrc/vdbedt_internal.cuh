@@ -132,7 +132,7 @@ __host__ __device__ inline unsigned long long node_key_at(const GridView& g, int
   return (unsigned long long)x + (unsigned long long)g.NX * ((unsigned long long)y + (unsigned long long)g.NY * (unsigned long long)z);
 }
 
-__device__ __forceinline__ uint32_t hash32(uint32_t k) {
+__host__ __device__ constexpr uint32_t hash32(uint32_t k) {
   k ^= k >> 16;
   k *= 0x7feb352du;
   k ^= k >> 15;
@@ -140,9 +140,12 @@ __device__ __forceinline__ uint32_t hash32(uint32_t k) {
   k ^= k >> 16;
   return k;
 }
-// slot of a 64-bit node key: the high word folded into the low one before the 32-bit mix
+// slot of a 64-bit node key: the high word folded into the low one before the 32-bit mix (a
+// bounded grid's keys have a zero high word, whose fold is the constant kHashFold0)
+constexpr uint32_t kHashFold0 = hash32(0x9e3779b9u);
 __device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
-  return hash32((uint32_t)k ^ hash32((uint32_t)(k >> 32) + 0x9e3779b9u));
+  const uint32_t hi = (uint32_t)(k >> 32);
+  return hash32((uint32_t)k ^ (hi == 0u ? kHashFold0 : hash32(hi + 0x9e3779b9u)));
 }
 
 __device__ __forceinline__ void set_error(const GridView& g, int bits) { atomicOr(&g.counters[C_ERR], bits); }

@@ -203,3 +203,28 @@ def test_switch_inside_a_captured_update():
         g.run(xyz, val)
         ref = O.edt_factorised(occ, 12)
         assert first_mismatch(m.export_dense(), ref) is None, (f, first_mismatch(m.export_dense(), ref))
+
+
+def test_profiled_transforms_equal_the_oracle():
+    """With phase events recorded between the kernels of a transform (profiling on), global and
+    incremental fields still equal Eq. 1: the events do not reorder the kernels that start early."""
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(77)
+    occ = W.tunnel_scene(5, (160, 128, 64), ntunnels=5, rmin=5, rmax=10)
+    nz, ny, nx = occ.shape
+    m = V.Map(nx, ny, nz, 16)
+    m.set_profiling(True)
+    xyz = W.occupied_coords(occ)
+    m.set_occupancy(xyz, np.ones(len(xyz), np.uint8))
+    m.global_()
+    assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 16)) is None
+    assert m.phase_times()["z_ms"] > 0
+    for f in range(4):
+        xyz, val = _edit_fraction(rs, occ, 0.002)
+        for (x, y, z), v in zip(xyz, val):
+            occ[z, y, x] = v
+        m.set_occupancy(xyz, val)
+        m.update()
+        assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 16)) is None, f
+        m.phase_times()
+    m.close()
