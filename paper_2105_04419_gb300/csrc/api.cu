@@ -350,6 +350,8 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   auto bail = [&](cudaError_t e, const char* where) {
     vdbedt_status s = cuda_fail(nullptr, e, where);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->uts.buf) cudaFree(h->uts.buf);
+    if (h->h_pinned) cudaFreeHost(h->h_pinned);
     if (h->fork.side) cudaStreamDestroy(h->fork.side);
     if (h->fork.fork) cudaEventDestroy(h->fork.fork);
     if (h->fork.join) cudaEventDestroy(h->fork.join);
@@ -428,6 +430,9 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   cudaMemsetAsync(g.mark, 0, sizeof(int32_t) * (size_t)node_cap * 3 * 1024, h->st);
   if (!slice) cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, h->st);
   if (untrunc) {
+    // the line stacks too, so that a transform allocates nothing (and can be captured)
+    e = ensure_scratch(h->uts, ut_scratch_bytes(g));
+    if (e != cudaSuccess) return bail(e, "untruncated scratch");
     e = launch_ut_init(g, h->st);
     if (e != cudaSuccess) return bail(e, "untruncated init");
   }

@@ -167,3 +167,26 @@ def test_full_size_tunnel_scene_sampled():
     assert ref.max() > 32 * 32  # samples beyond the headline truncation
     assert np.array_equal(got, ref), np.nonzero(got != ref)[0][:5]
     m.close()
+
+
+def test_captured_update():
+    """An untruncated map's update captured once (UpdateGraph) and replayed per frame: the transform
+    allocates nothing, so it captures; every replay equals the oracle."""
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(31)
+    nx, ny, nz = 48, 40, 36
+    occ = W.bernoulli_grid(31, (nz, ny, nx), 0.001)
+    occ[1, 2, 3] = 1
+    m = untrunc_map(nx, ny, nz)
+    m.set_occupancy_dense(occ)
+    m.global_()
+    g = V.UpdateGraph(m, 256)
+    for f in range(3):
+        k = 120
+        xyz = np.stack([rs.integers(0, nx, k), rs.integers(0, ny, k), rs.integers(0, nz, k)], 1).astype(np.int32)
+        val = rs.integers(0, 2, k).astype(np.uint8)
+        for (x, y, z), v in zip(xyz, val):
+            occ[z, y, x] = v
+        g.run(xyz, val)
+        assert first_mismatch(m.export_dense(), O.edt_untruncated(occ)) is None, f
+    m.close()
