@@ -1,7 +1,7 @@
 """GPU parity of the sparse z-slab protocol (paper_2105_04419_gb300.slabs.SlabMap) and of the
 occupancy export it is built on, against the CPU oracle, bit-exact.
 
-Ranks are emulated in one process on one GPU (every call of this build runs on one GPU): each
+Ranks are emulated in one process on one GPU: each
 rank's SlabMap returns the records for its neighbours, which are handed over directly, so the
 library side of the protocol -- own transform, band export, staging of the neighbours' records,
 the incremental updates -- runs exactly as on separate GPUs.  The owned fields, stacked, equal the
