@@ -1649,12 +1649,23 @@ __global__ void __launch_bounds__(256) k_changed_flags_dilate(US us) {
   }
 }
 
-// Dirty sets of an update: every stored brick within R (Chebyshev) of a changed brick needs its z
-// pass; those in the changed brick's z layer also need the in-plane pass, those in its x row the x
-// pass.  A block per changed brick: its first threads look up the interior nodes the brick's cube
-// spans (at most 4 per axis: 2R + 1 <= 47 bricks), then a thread per (column, z run) of the cube
-// reads the run's bricks inside the cube and queues the run once if one is stored, and for the
-// changed brick's z layer that brick's y run and x run.  Runs are aligned to their length (4, 8
+// Voxel gap between two bricks d apart along an axis: the nearest voxels of bricks 0 and d are
+// 8 |d| - 7 apart (0 for the same brick).
+__device__ __forceinline__ int brick_gap(int d) {
+  d = abs(d);
+  return d == 0 ? 0 : 8 * d - 7;
+}
+
+// Dirty sets of an update.  D(v) depends only on obstacles closer than dmax (Eq. 1 with the
+// truncation), so a flip in brick c can change D only in bricks whose nearest voxels lie closer
+// than dmax to c's: the ball of radius dmax around c at brick granularity, about half the cube of R
+// bricks.  Such a stored brick needs its z pass.  The in-plane values g2 change only in c's z
+// layer, within dmax in the plane (a disk): those bricks also need the in-plane pass; the x-line
+// values g1 change only in c's x row: those bricks also need the x pass.
+// A block per changed brick: its first threads look up the interior nodes the brick's cube spans
+// (at most 4 per axis: 2R + 1 <= 47 bricks), then a thread per (column, z run) of the cube reads
+// the run's bricks and queues the run once if one of them is stored and inside the ball, and for
+// the changed brick's z layer that brick's y run and x run.  Runs are aligned to their length (4, 8
 // or 16) inside nodes, hence at multiples of it in grid coordinates.  With more than two changed
 // bricks per block, a thread per (changed brick, offset in its cube) instead, as for the dilation.
 template <class US>
@@ -1683,7 +1694,9 @@ __global__ void __launch_bounds__(256, 8) k_mark_dirty(US us, int rx, int ry, in
         const int dx = r % side - R, dy = (r / side) % side - R, dz = r / (side * side) - R;
         const int4 c = g.bcoord[changed[i / vol]];
         const int bx = c.x + dx, by = c.y + dy, bz = c.z + dz;
-        if ((unsigned)bx < (unsigned)g.BX && (unsigned)by < (unsigned)g.BY && (unsigned)bz < (unsigned)g.BZ) {
+        const int gx = brick_gap(dx), gy = brick_gap(dy), gz = brick_gap(dz);
+        if ((unsigned)bx < (unsigned)g.BX && (unsigned)by < (unsigned)g.BY && (unsigned)bz < (unsigned)g.BZ &&
+            gx * gx + gy * gy + gz * gz < g.INF) {
           const int node = find_node(g, node_key_of(g, bx, by, bz));
           if (node >= 0 && g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] >= 0) {
             if (dy == 0 && dz == 0) wx = claim_run(g, 0, bx, by, bz, node, rx, epoch, px);
@@ -1722,12 +1735,14 @@ __global__ void __launch_bounds__(256, 8) k_mark_dirty(US us, int rx, int ry, in
         const int bx = x0 + col % ncx, by = y0 + col / ncx;
         const int zs = max(r0 + zr * rz, z0), ze = min(r0 + zr * rz + rz - 1, z1);
         const int node = nodes[((bx >> 4) - qx0) + nqx * (((by >> 4) - qy0) + nqy * ((zs >> 4) - qz0))];
-        if (node >= 0) {
+        const int gx = brick_gap(bx - c.x), gy = brick_gap(by - c.y), in_plane = gx * gx + gy * gy;
+        if (node >= 0 && in_plane < g.INF) {
           const int32_t* ch = g.child + (size_t)node * kNodeBricks;
           bool any = false;
           for (int bz = zs; bz <= ze; ++bz) {
             const bool stored = ch[local_brick(bx, by, bz)] >= 0;
-            any |= stored;
+            const int gz = brick_gap(bz - c.z);
+            any |= stored && in_plane + gz * gz < g.INF;
             if (bz == c.z && stored) {
               if (by == c.y) wx = claim_run(g, 0, bx, by, bz, node, rx, epoch, px);
               wy = claim_run(g, 1, bx, by, bz, node, ry, epoch, py);
