@@ -1535,21 +1535,41 @@ __global__ void k_count_run_bricks(const GridView* __restrict__ views, GridView 
 }
 
 // ---- incremental ----
-// For every changed brick: refresh its obstacle flag; if it holds obstacles, mark its dilation.
-// With at most two changed bricks per block, a block per changed brick: its first threads find or
-// create the interior nodes the brick's cube spans (at most 4 per axis), then a thread per row
-// (y, z) of the cube sets the row's x extent in the allocation masks of its nodes (short dependent
-// chains for the few-brick updates of a single map).  With more (a batch's share of the launch, a
-// large update), a thread per (changed brick, row) with its own node lookups keeps every thread of
-// the GPU busy instead.
+// Voxel gap between two bricks d apart along an axis: the nearest voxels of bricks 0 and d are
+// 8 |d| - 7 apart (0 for the same brick).
+__device__ __forceinline__ int brick_gap(int d) {
+  d = abs(d);
+  return d == 0 ? 0 : 8 * d - 7;
+}
+
+// For every changed brick c: refresh its obstacle flag; if it holds obstacles, mark its dilation
+// (the bricks within R that must be stored); and queue its dirty runs.
+// Dirty sets: D(v) depends only on obstacles closer than dmax (Eq. 1 with the truncation), so a
+// flip in c can change D only in bricks whose nearest voxels lie closer than dmax to c's -- the
+// ball of radius dmax around c at brick granularity, about half the cube of R bricks.  Such a brick
+// needs its z pass if it is stored or about to be (every brick of the cube of an obstacle-holding
+// c is: the dilation just marked it, and the allocation of the marked bricks runs before the
+// passes).  The in-plane values g2 change only in c's z layer, within dmax in the plane (a disk):
+// those bricks also need the in-plane pass; the x-line values g1 change only in c's x row: those
+// bricks also need the x pass.
+// With at most two changed bricks per block, a block per changed brick: its first threads find
+// (or, for an obstacle-holding c, create) the interior nodes c's cube spans (at most 4 per axis:
+// 2R + 1 <= 47 bricks), then a thread per row (y, z) of the cube sets the row's x extent in the
+// allocation masks, and a thread per (column, z run) of the cube queues the run once if one of its
+// bricks is in the ball (and c's y run and x run in c's layer).  Runs are aligned to their length
+// (4, 8 or 16) inside nodes, hence at multiples of it in grid coordinates.  With more changed bricks
+// per block (a batch's share of the launch, a large update), a thread per (changed brick, row) and
+// then per (changed brick, offset in its cube), each with its own node lookups, keeps every thread
+// of the GPU busy instead.
 template <class US>
-__global__ void __launch_bounds__(256) k_changed_flags_dilate(US us) {
+__global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, int rz, Items it, bool mark) {
   pdl_enter();
   __shared__ int nodes[64];
   __shared__ int obst_sh;
   const UpdArgs A = us.get();
   const GridView& g = A.g;
   const int32_t* __restrict__ changed = A.changed;
+  const int grid = (int)blockIdx.y;
   const int nc = min(g.counters[C_CHANGED], g.cap);
   const int R = g.R, side = 2 * R + 1;
   // The marking costs (2R + 1)^3 brick visits per changed brick; once that exceeds kBigUpdate
@@ -1559,9 +1579,9 @@ __global__ void __launch_bounds__(256) k_changed_flags_dilate(US us) {
     if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_BIG] = 1;
     return;
   }
+  const int epoch = g.counters[C_EPOCH];
   if (nc > 2 * (int)gridDim.x) {
-    // many changed bricks per block (a batch's share of the grid, or a large update): a thread per
-    // (changed brick, row), each row's nodes looked up on its own, the rounds block-uniform
+    // dilation: a thread per (changed brick, row), the rounds block-uniform
     const int rows = side * side, nseg = (side + 15) / 16 + 1;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < (int64_t)nc * rows;
          base += (int64_t)gridDim.x * blockDim.x) {
@@ -1600,105 +1620,35 @@ __global__ void __launch_bounds__(256) k_changed_flags_dilate(US us) {
         list_fresh_words(g, fresh, node * 128 + word);
       }
     }
-    return;
-  }
-  for (int i = (int)blockIdx.x; i < nc; i += (int)gridDim.x) {
-    const int s = changed[i];
-    __syncthreads();  // the table of the block's previous brick is no longer read
-    if (threadIdx.x == 0) {
-      const bool obst = brick_has_obstacle(g, s);
-      const uint32_t f = g.bflags[s];
-      g.bflags[s] = obst ? (f | F_OBST) : (f & ~F_OBST);
-      obst_sh = obst;
-    }
-    __syncthreads();
-    if (!obst_sh) continue;
-    const int4 c = g.bcoord[s];
-    const int x0 = max(c.x - R, 0), x1 = min(c.x + R, g.BX - 1);
-    const int y0 = max(c.y - R, 0), y1 = min(c.y + R, g.BY - 1);
-    const int z0 = max(c.z - R, 0), z1 = min(c.z + R, g.BZ - 1);
-    const int qx0 = x0 >> 4, qy0 = y0 >> 4, qz0 = z0 >> 4;
-    const int nqx = (x1 >> 4) - qx0 + 1, nqy = (y1 >> 4) - qy0 + 1, nqz = (z1 >> 4) - qz0 + 1;
-    if ((int)threadIdx.x < nqx * nqy * nqz) {
-      const int q = (int)threadIdx.x;
-      nodes[q] = get_or_create_node(g, node_key_at(g, qx0 + q % nqx, qy0 + (q / nqx) % nqy, qz0 + q / (nqx * nqy)));
-    }
-    __syncthreads();
-    const int nyr = y1 - y0 + 1, rows = nyr * (z1 - z0 + 1);
-    // a row's x extent is split at node boundaries (the same segments on every lane); the rounds are
-    // block-uniform so that the fresh list is appended a warp at a time
-    for (int r0 = 0; r0 < rows; r0 += (int)blockDim.x) {
-      const int r = r0 + (int)threadIdx.x;
-      const bool live = r < rows;
-      const int y = y0 + (live ? r % nyr : 0), z = z0 + (live ? r / nyr : 0);
-      const int ly = y & 15, lz = z & 15, word = (ly >> 1) + 8 * lz;
-      const int nrow = nqx * (((y >> 4) - qy0) + nqy * ((z >> 4) - qz0));
-      for (int xa = x0; xa <= x1;) {  // the same segments on every lane
-        const int xe = min(x1, xa | 15);
-        const int node = live ? nodes[nrow + (xa >> 4) - qx0] : -1;
-        bool fresh = false;
-        if (node >= 0) {
-          const uint32_t bitsx = ((1u << ((xe & 15) - (xa & 15) + 1)) - 1u) << (xa & 15);
-          const uint32_t add = bitsx << (16 * (ly & 1));
-          fresh = (add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add)) && claim_fresh_word(g, node, word);
-        }
-        list_fresh_words(g, fresh, node * 128 + word);
-        xa = xe + 1;
-      }
-    }
-  }
-}
-
-// Voxel gap between two bricks d apart along an axis: the nearest voxels of bricks 0 and d are
-// 8 |d| - 7 apart (0 for the same brick).
-__device__ __forceinline__ int brick_gap(int d) {
-  d = abs(d);
-  return d == 0 ? 0 : 8 * d - 7;
-}
-
-// Dirty sets of an update.  D(v) depends only on obstacles closer than dmax (Eq. 1 with the
-// truncation), so a flip in brick c can change D only in bricks whose nearest voxels lie closer
-// than dmax to c's: the ball of radius dmax around c at brick granularity, about half the cube of R
-// bricks.  Such a stored brick needs its z pass.  The in-plane values g2 change only in c's z
-// layer, within dmax in the plane (a disk): those bricks also need the in-plane pass; the x-line
-// values g1 change only in c's x row: those bricks also need the x pass.
-// A block per changed brick: its first threads look up the interior nodes the brick's cube spans
-// (at most 4 per axis: 2R + 1 <= 47 bricks), then a thread per (column, z run) of the cube reads
-// the run's bricks and queues the run once if one of them is stored and inside the ball, and for
-// the changed brick's z layer that brick's y run and x run.  Runs are aligned to their length (4, 8
-// or 16) inside nodes, hence at multiples of it in grid coordinates.  With more than two changed
-// bricks per block, a thread per (changed brick, offset in its cube) instead, as for the dilation.
-template <class US>
-__global__ void __launch_bounds__(256, 8) k_mark_dirty(US us, int rx, int ry, int rz, Items it) {
-  pdl_enter();
-  __shared__ int nodes[64];
-  const UpdArgs A = us.get();
-  const GridView& g = A.g;
-  const int32_t* __restrict__ changed = A.changed;
-  const int grid = (int)blockIdx.y;
-  if (g.counters[C_BIG]) return;
-  const int nc = min(g.counters[C_CHANGED], g.cap);
-  const int epoch = g.counters[C_EPOCH];
-  const int R = g.R;
-  if (nc > 2 * (int)gridDim.x) {
-    // many changed bricks per block: a thread per (changed brick, offset in its cube), each brick's
-    // node looked up on its own, the rounds block-uniform
-    const int side = 2 * R + 1, vol = side * side * side;
+    if (!mark) return;
+    // dirty runs: a thread per (changed brick, offset in its cube); a warp spans at most two changed
+    // bricks (a cube has at least 27 offsets), whose obstacle bits its first and last lanes read
+    const int vol = side * side * side;
+    const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < (int64_t)nc * vol;
          base += (int64_t)gridDim.x * blockDim.x) {
       const int64_t i = base + threadIdx.x;
+      const long long bi = i < (int64_t)nc * vol ? (long long)(i / vol) : -1ll;
+      const long long b0 = __shfl_sync(0xffffffffu, bi, 0), b31 = __shfl_sync(0xffffffffu, bi, 31);
+      bool o = false;
+      if (lane == 0 && b0 >= 0) o = brick_has_obstacle(g, changed[b0]);
+      if (lane == 31 && b31 >= 0) o = brick_has_obstacle(g, changed[b31]);
+      const bool o0 = __shfl_sync(0xffffffffu, o, 0), o31 = __shfl_sync(0xffffffffu, o, 31);
       bool wx = false, wy = false, wz = false;
       unsigned long long px = 0, py = 0, pz = 0;
-      if (i < (int64_t)nc * vol) {
+      if (bi >= 0) {
         const int r = (int)(i % vol);
         const int dx = r % side - R, dy = (r / side) % side - R, dz = r / (side * side) - R;
-        const int4 c = g.bcoord[changed[i / vol]];
+        const int s = changed[bi];
+        const int4 c = g.bcoord[s];
         const int bx = c.x + dx, by = c.y + dy, bz = c.z + dz;
         const int gx = brick_gap(dx), gy = brick_gap(dy), gz = brick_gap(dz);
         if ((unsigned)bx < (unsigned)g.BX && (unsigned)by < (unsigned)g.BY && (unsigned)bz < (unsigned)g.BZ &&
             gx * gx + gy * gy + gz * gz < g.INF) {
-          const int node = find_node(g, node_key_of(g, bx, by, bz));
-          if (node >= 0 && g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] >= 0) {
+          const bool obst = bi == b0 ? o0 : o31;
+          const unsigned long long key = node_key_of(g, bx, by, bz);
+          const int node = obst ? get_or_create_node(g, key) : find_node(g, key);
+          if (node >= 0 && (obst || g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] >= 0)) {
             if (dy == 0 && dz == 0) wx = claim_run(g, 0, bx, by, bz, node, rx, epoch, px);
             if (dz == 0) wy = claim_run(g, 1, bx, by, bz, node, ry, epoch, py);
             wz = claim_run(g, 2, bx, by, bz, node, rz, epoch, pz);
@@ -1712,22 +1662,59 @@ __global__ void __launch_bounds__(256, 8) k_mark_dirty(US us, int rx, int ry, in
     return;
   }
   for (int i = (int)blockIdx.x; i < nc; i += (int)gridDim.x) {
-    const int4 c = g.bcoord[changed[i]];
+    const int s = changed[i];
+    __syncthreads();  // the table of the block's previous brick is no longer read
+    if (threadIdx.x == 0) {
+      const bool obst = brick_has_obstacle(g, s);
+      const uint32_t f = g.bflags[s];
+      g.bflags[s] = obst ? (f | F_OBST) : (f & ~F_OBST);
+      obst_sh = obst;
+    }
+    const int4 c = g.bcoord[s];
     const int x0 = max(c.x - R, 0), x1 = min(c.x + R, g.BX - 1);
     const int y0 = max(c.y - R, 0), y1 = min(c.y + R, g.BY - 1);
     const int z0 = max(c.z - R, 0), z1 = min(c.z + R, g.BZ - 1);
     const int qx0 = x0 >> 4, qy0 = y0 >> 4, qz0 = z0 >> 4;
     const int nqx = (x1 >> 4) - qx0 + 1, nqy = (y1 >> 4) - qy0 + 1, nqz = (z1 >> 4) - qz0 + 1;
-    __syncthreads();  // the table of the block's previous brick is no longer read
+    __syncthreads();
+    const bool obst = obst_sh != 0;  // block-uniform
     if ((int)threadIdx.x < nqx * nqy * nqz) {
       const int q = (int)threadIdx.x;
-      nodes[q] = find_node(g, node_key_at(g, qx0 + q % nqx, qy0 + (q / nqx) % nqy, qz0 + q / (nqx * nqy)));
+      const unsigned long long key = node_key_at(g, qx0 + q % nqx, qy0 + (q / nqx) % nqy, qz0 + q / (nqx * nqy));
+      nodes[q] = obst ? get_or_create_node(g, key) : find_node(g, key);
     }
     __syncthreads();
+    if (obst) {
+      // dilation: a row's x extent is split at node boundaries (the same segments on every lane);
+      // the rounds are block-uniform so that the fresh list is appended a warp at a time
+      const int nyr = y1 - y0 + 1, rows = nyr * (z1 - z0 + 1);
+      for (int rb = 0; rb < rows; rb += (int)blockDim.x) {
+        const int r = rb + (int)threadIdx.x;
+        const bool live = r < rows;
+        const int y = y0 + (live ? r % nyr : 0), z = z0 + (live ? r / nyr : 0);
+        const int ly = y & 15, lz = z & 15, word = (ly >> 1) + 8 * lz;
+        const int nrow = nqx * (((y >> 4) - qy0) + nqy * ((z >> 4) - qz0));
+        for (int xa = x0; xa <= x1;) {
+          const int xe = min(x1, xa | 15);
+          const int node = live ? nodes[nrow + (xa >> 4) - qx0] : -1;
+          bool fresh = false;
+          if (node >= 0) {
+            const uint32_t bitsx = ((1u << ((xe & 15) - (xa & 15) + 1)) - 1u) << (xa & 15);
+            const uint32_t add = bitsx << (16 * (ly & 1));
+            fresh = (add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add)) && claim_fresh_word(g, node, word);
+          }
+          list_fresh_words(g, fresh, node * 128 + word);
+          xa = xe + 1;
+        }
+      }
+    }
+    if (!mark) continue;  // block-uniform
+    // dirty runs: a thread per (column, z run) of the cube, block-uniform rounds (the lists' places
+    // are reserved a warp at a time)
     const int r0 = z0 - z0 % rz, nruns = (z1 - r0) / rz + 1;
     const int ncx = x1 - x0 + 1, ncol = ncx * (y1 - y0 + 1), total = ncol * nruns;
-    for (int u0 = 0; u0 < total; u0 += (int)blockDim.x) {  // block-uniform rounds: the lists' places are
-      const int u = u0 + (int)threadIdx.x;                 // reserved a warp at a time
+    for (int u0 = 0; u0 < total; u0 += (int)blockDim.x) {
+      const int u = u0 + (int)threadIdx.x;
       bool wx = false, wy = false, wz = false;
       unsigned long long px = 0, py = 0, pz = 0;
       if (u < total) {
@@ -1740,7 +1727,7 @@ __global__ void __launch_bounds__(256, 8) k_mark_dirty(US us, int rx, int ry, in
           const int32_t* ch = g.child + (size_t)node * kNodeBricks;
           bool any = false;
           for (int bz = zs; bz <= ze; ++bz) {
-            const bool stored = ch[local_brick(bx, by, bz)] >= 0;
+            const bool stored = obst || ch[local_brick(bx, by, bz)] >= 0;
             const int gz = brick_gap(bz - c.z);
             any |= stored && in_plane + gz * gz < g.INF;
             if (bz == c.z && stored) {
@@ -1755,6 +1742,48 @@ __global__ void __launch_bounds__(256, 8) k_mark_dirty(US us, int rx, int ry, in
       emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
       emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
     }
+  }
+}
+
+// Dirty runs of a batch's update, queued after the bricks the dilation added are stored (so that
+// the marking overlaps the batch's gated global-form branch instead of preceding it): a thread per
+// (changed brick, offset in its cube), the ball and disk rules of k_changed_mark, stored bricks
+// read from the child tables.
+template <class US>
+__global__ void __launch_bounds__(256) k_mark_runs(US us, int rx, int ry, int rz, Items it) {
+  pdl_enter();
+  const UpdArgs A = us.get();
+  const GridView& g = A.g;
+  const int32_t* __restrict__ changed = A.changed;
+  const int grid = (int)blockIdx.y;
+  if (g.counters[C_BIG]) return;
+  const int nc = min(g.counters[C_CHANGED], g.cap);
+  const int epoch = g.counters[C_EPOCH];
+  const int R = g.R, side = 2 * R + 1, vol = side * side * side;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < (int64_t)nc * vol;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool wx = false, wy = false, wz = false;
+    unsigned long long px = 0, py = 0, pz = 0;
+    if (i < (int64_t)nc * vol) {
+      const int r = (int)(i % vol);
+      const int dx = r % side - R, dy = (r / side) % side - R, dz = r / (side * side) - R;
+      const int4 c = g.bcoord[changed[i / vol]];
+      const int bx = c.x + dx, by = c.y + dy, bz = c.z + dz;
+      const int gx = brick_gap(dx), gy = brick_gap(dy), gz = brick_gap(dz);
+      if ((unsigned)bx < (unsigned)g.BX && (unsigned)by < (unsigned)g.BY && (unsigned)bz < (unsigned)g.BZ &&
+          gx * gx + gy * gy + gz * gz < g.INF) {
+        const int node = find_node(g, node_key_of(g, bx, by, bz));
+        if (node >= 0 && g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] >= 0) {
+          if (dy == 0 && dz == 0) wx = claim_run(g, 0, bx, by, bz, node, rx, epoch, px);
+          if (dz == 0) wy = claim_run(g, 1, bx, by, bz, node, ry, epoch, py);
+          wz = claim_run(g, 2, bx, by, bz, node, rz, epoch, pz);
+        }
+      }
+    }
+    emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
+    emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
+    emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
   }
 }
 
@@ -1783,9 +1812,9 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
   const unsigned div = k > 1 ? (unsigned)k : 1u;
   auto share = [&](unsigned single) { return k > 1 ? (single / div > 16 ? single / div : 16u) : single; };
   const unsigned nc = (unsigned)node_cap;
-  // the decision (counters[C_BIG]) and, for updates that stay incremental, the changed bricks' flags
-  // and dilation marks
-  VDB_LAUNCH_PDL(k_changed_flags_dilate<US>, dim3(share(1216), k), kT, 0, st, us);
+  // the decision (counters[C_BIG]) and, for updates that stay incremental, the changed bricks' flags,
+  // their dilation marks and their dirty runs
+  VDB_LAUNCH_PDL(k_changed_mark<US>, dim3(share(2432), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it, k == 1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   cudaStream_t gs = st;
@@ -1817,10 +1846,10 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
     e = cudaEventRecord(fk.join, fk.side);
     if (e != cudaSuccess) return e;
   }
-  // incremental form: new bricks of the dilation, the dirty runs
-  // a warp per fresh word (the count is on the device): one wave of 8 warps per block on every SM
+  // incremental form: storage for the bricks the dilation added (a warp per fresh word, the count on
+  // the device: one wave of 8 warps per block on every SM); a batch's dirty runs after it
   VDB_LAUNCH(k_alloc_fresh<US>, dim3(share(1216), k), kT, 0, st, us);
-  VDB_LAUNCH_PDL(k_mark_dirty<US>, dim3(share(2432), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
+  if (k > 1) VDB_LAUNCH_PDL(k_mark_runs<US>, dim3(share(2432), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }
 
