@@ -380,9 +380,7 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   AL(g.child, node_cap * kNodeBricks);
   AL(g.amask, node_cap * 128);
   AL(g.mwork, node_cap * 384);
-  AL(g.afresh, node_cap * 4);
   AL(g.nclaim, node_cap * 128);
-  AL(g.flist, node_cap * 128);
   AL(g.node_key, node_cap);
   AL(g.mark, node_cap * 3 * 1024);
   if (slice) {
@@ -425,7 +423,6 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   cudaMemsetAsync(g.child, 0xFF, sizeof(int32_t) * (size_t)node_cap * kNodeBricks, h->st);
   cudaMemsetAsync(g.amask, 0, sizeof(uint32_t) * (size_t)node_cap * 128, h->st);
   cudaMemsetAsync(g.mwork, 0, sizeof(uint32_t) * (size_t)node_cap * 384, h->st);
-  cudaMemsetAsync(g.afresh, 0, sizeof(uint32_t) * (size_t)node_cap * 4, h->st);
   cudaMemsetAsync(g.nclaim, 0, sizeof(uint32_t) * (size_t)node_cap * 128, h->st);
   cudaMemsetAsync(g.mark, 0, sizeof(int32_t) * (size_t)node_cap * 3 * 1024, h->st);
   if (!slice) cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, h->st);

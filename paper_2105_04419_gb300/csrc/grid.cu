@@ -82,6 +82,16 @@ struct BatchViews {
 // The global form's activation and work-list kernels run inside an incremental update only for
 // grids whose update switched to the global form (counters[C_BIG] set after the records were
 // applied): one grid (the whole launch is its share), or grid blockIdx.y of a batch.
+// An update's choice between its incremental and its global form (the marking would cost (2R + 1)^3
+// brick visits per changed brick; beyond kBigUpdate visits per stored brick the global form's
+// activation and work lists are cheaper -- measured crossover on the tunnel scene).  Taken from the
+// changed-brick count, final once the records are applied, and the stored bricks when the update
+// began, so that every kernel of the update, on either stream and at any time, decides alike.
+__device__ __forceinline__ bool big_update(const GridView& g) {
+  const int64_t nc = min(g.counters[C_CHANGED], g.cap), side = 2 * g.R + 1;
+  return nc * side * side * side > (int64_t)kBigUpdate * max(g.counters[C_NB_START], 1);
+}
+
 struct GatedOne {
   GridView g;
   __device__ __forceinline__ GridView get(int& bid, int& nblk, int& grid) const {
@@ -90,7 +100,7 @@ struct GatedOne {
     grid = 0;
     return g;
   }
-  __device__ __forceinline__ bool skip(const GridView& v) const { return v.counters[C_BIG] == 0; }
+  __device__ __forceinline__ bool skip(const GridView& v) const { return !big_update(v); }
 };
 struct GatedBatch {
   const UpdArgs* a;
@@ -100,7 +110,7 @@ struct GatedBatch {
     grid = (int)blockIdx.y;
     return a[blockIdx.y].g;
   }
-  __device__ __forceinline__ bool skip(const GridView& v) const { return v.counters[C_BIG] == 0; }
+  __device__ __forceinline__ bool skip(const GridView& v) const { return !big_update(v); }
 };
 struct OneSrc {
   const uint8_t* p;
@@ -136,7 +146,6 @@ __global__ void k_reset_nodes(VS vs) {
   for (int64_t i = t0; i < nn * (3 * 1024 / 4); i += stride) reinterpret_cast<int4*>(g.mark)[i] = zero;
   for (int64_t i = t0; i < nn * (128 / 4); i += stride) reinterpret_cast<int4*>(g.amask)[i] = zero;
   for (int64_t i = t0; i < nn * (384 / 4); i += stride) reinterpret_cast<int4*>(g.mwork)[i] = zero;
-  for (int64_t i = t0; i < nn; i += stride) reinterpret_cast<int4*>(g.afresh)[i] = zero;
   for (int64_t i = t0; i < nn * (128 / 4); i += stride) reinterpret_cast<int4*>(g.nclaim)[i] = zero;
   for (int64_t i = t0; i <= (int64_t)g.hmask; i += stride) g.hslots[i] = ~0ull;
 }
@@ -157,12 +166,12 @@ __global__ void k_begin_update(US us) {
     g.counters[C_NEW_BRICKS] = 0;
     g.counters[C_UNIQUE] = 0;
     g.counters[C_HAS_ZERO] = 0;
-    g.counters[C_FRESH] = 0;
     g.counters[C_DEFERRED] = 0;
     g.counters[C_XB] = 0;
     g.counters[C_YB] = 0;
     g.counters[C_ZB] = 0;
     g.counters[C_BIG] = 0;
+    g.counters[C_NB_START] = g.counters[C_NBRICKS];
     g.counters[C_EPOCH] += 1;
   }
 }
@@ -183,12 +192,12 @@ __global__ void k_begin_batch_update(const UpdArgs* __restrict__ args, BatchCoun
     g.counters[C_NEW_BRICKS] = 0;
     g.counters[C_UNIQUE] = 0;
     g.counters[C_HAS_ZERO] = 0;
-    g.counters[C_FRESH] = 0;
     g.counters[C_DEFERRED] = 0;
     g.counters[C_XB] = 0;
     g.counters[C_YB] = 0;
     g.counters[C_ZB] = 0;
     g.counters[C_BIG] = 0;
+    g.counters[C_NB_START] = g.counters[C_NBRICKS];
     g.counters[C_EPOCH] += 1;
   }
 }
@@ -1227,21 +1236,51 @@ __global__ void __launch_bounds__(256) k_dilate_nodes(VS vs) {
 
 // Mark bricks within Chebyshev radius R of brick (bx,by,bz) in amask: one (dy, dz) row (used by the
 // incremental form, where few bricks change).
-// An amask word that an update gives new bits is listed once per update (its fresh bit dedupes),
-// so that the update's allocation visits only those words: claim_fresh_word tells the one caller
-// that lists it, list_fresh_words appends a warp's words with one atomic (warp-uniform call).
-__device__ __forceinline__ bool claim_fresh_word(const GridView& g, int node, int word) {
-  const uint32_t b = 1u << (word & 31);
-  return !(atomicOr(&g.afresh[(size_t)node * 4 + (word >> 5)], b) & b);
+// Places for `cnt` items of each lane in a list counted by *ctr: one atomic per warp (warp-uniform
+// call); returns the lane's first place.  *total receives the warp's sum.
+__device__ __forceinline__ int warp_reserve_count(int32_t* ctr, int cnt, int* total) {
+  const int lane = threadIdx.x & 31;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  *total = __shfl_sync(0xffffffffu, incl, 31);
+  int base = 0;
+  if (lane == 31 && *total) base = atomicAdd(ctr, *total);
+  return __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
 }
 
-__device__ __forceinline__ void list_fresh_words(const GridView& g, bool want, int entry) {
-  const int p = warp_reserve(&g.counters[C_FRESH], want);
-  if (!want) return;
-  if (p < g.node_cap * 128)
-    g.flist[p] = entry;
-  else
-    set_error(g, kErrOverflow);  // not reached: each word is listed at most once
+// Storage for the bricks of a row segment whose compute-set bits (`bits` of amask word `word` of
+// `node`; bit b is the brick at x = x16 + (b & 15) of row (y, z)) this thread set first, so that
+// exactly one thread handles each: the ones without storage get slots (places reserved a warp at
+// a time), their metadata from the thread, their fields at dmax^2 from the whole warp
+// (warp-uniform call).
+__device__ void alloc_new_bits(const GridView& g, int node, int word, uint32_t bits, int x16, int y, int z) {
+  uint32_t need = 0u;
+  if (node >= 0)
+    for (uint32_t b = bits; b; b &= b - 1u) {
+      const int bit = __ffs(b) - 1;
+      if (g.child[(size_t)node * kNodeBricks + word * 32 + bit] == kNoSlot) need |= 1u << bit;
+    }
+  const int cnt = __popc(need);
+  int total = 0;
+  const int base = warp_reserve_count(&g.counters[C_NBRICKS], cnt, &total);
+  if ((threadIdx.x & 31) == 31 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
+  int k = 0;
+  for (uint32_t b = need; b; b &= b - 1u, ++k) {
+    const int bit = __ffs(b) - 1, slot = base + k;
+    if (slot >= g.cap) {
+      set_error(g, kErrOverflow);
+      continue;
+    }
+    init_brick(g, slot, node, x16 + (bit & 15), y, z, false);
+    g.child[(size_t)node * kNodeBricks + word * 32 + bit] = slot;
+  }
+  // fields: round r takes each lane's r-th new brick, a brick at a time by the whole warp
+  const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+  for (int r = 0; r < rounds; ++r) init_fields_ballot(g, r < cnt && base + r < g.cap, base + r);
 }
 
 // Allocate every marked brick without storage: a block per (node, 256-brick chunk), a brick per
@@ -1271,43 +1310,6 @@ __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
         g.child[(size_t)node * kNodeBricks + l] = slot;
       }
     }
-  }
-}
-
-// Incremental form: allocate the marked bricks without storage in the words this update marked
-// first (the fresh list), a warp per listed word and a lane per brick of it, fields at dmax^2; then
-// clear the word's fresh bit.  The work follows the update's dilation, not the size of the map.
-template <class US>
-__global__ void __launch_bounds__(256) k_alloc_fresh(US us) {
-  pdl_enter();
-  const GridView g = us.get().g;
-  if (g.counters[C_BIG]) return;
-  const int nf = min(g.counters[C_FRESH], g.node_cap * 128);
-  const int lane = threadIdx.x & 31;
-  const int nw = (int)gridDim.x * (int)(blockDim.x >> 5);
-  for (int i = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); i < nf; i += nw) {
-    const int e = g.flist[i], node = e >> 7, word = e & 127;
-    const int l = word * 32 + lane;  // local brick: lx + 16 ly + 256 lz
-    const bool need = ((g.amask[(size_t)node * 128 + word] >> lane) & 1u) &&
-                      g.child[(size_t)node * kNodeBricks + l] == kNoSlot;
-    const unsigned bal = __ballot_sync(0xffffffffu, need);
-    int base = 0;
-    if (lane == 0 && bal) {
-      base = atomicAdd(&g.counters[C_NBRICKS], __popc(bal));
-      atomicAdd(&g.counters[C_NEW_BRICKS], __popc(bal));
-    }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    const int slot = base + __popc(bal & ((1u << lane) - 1u));
-    const bool ok = need && slot < g.cap;
-    if (need && !ok) set_error(g, kErrOverflow);
-    if (ok) {
-      int nxn, nyn, nzn;
-      node_coords(g, (unsigned long long)g.node_key[node], nxn, nyn, nzn);
-      init_brick(g, slot, node, nxn * 16 + (l & 15), nyn * 16 + ((l >> 4) & 15), nzn * 16 + (l >> 8), false);
-    }
-    init_fields_ballot(g, ok, slot);
-    if (ok) g.child[(size_t)node * kNodeBricks + l] = slot;
-    if (lane == 0) atomicAnd(&g.afresh[(size_t)node * 4 + (word >> 5)], ~(1u << (word & 31)));
   }
 }
 
@@ -1572,10 +1574,8 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
   const int grid = (int)blockIdx.y;
   const int nc = min(g.counters[C_CHANGED], g.cap);
   const int R = g.R, side = 2 * R + 1;
-  // The marking costs (2R + 1)^3 brick visits per changed brick; once that exceeds kBigUpdate
-  // visits per stored brick, the update takes the global form's activation and work lists instead
-  // (same field; measured crossover on the tunnel scene).  Every block reaches the same decision.
-  if ((int64_t)nc * side * side * side > (int64_t)kBigUpdate * max(g.counters[C_NBRICKS], 1)) {
+  // an update that takes the global form leaves all this to the gated kernels of the side stream
+  if (big_update(g)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) g.counters[C_BIG] = 1;
     return;
   }
@@ -1605,19 +1605,20 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
       const int ly = y & 15, lz = z & 15, word = (ly >> 1) + 8 * lz;
       int xa = x0;
       for (int k = 0; k < nseg; ++k) {  // the row's segments, one node each (same count on every lane)
-        bool fresh = false;
+        uint32_t added = 0u;
         int node = -1;
+        const int x16 = xa & ~15;
         if (live && xa <= x1) {
           const int xe = min(x1, xa | 15);
           node = get_or_create_node(g, node_key_of(g, xa, y, z));
           if (node >= 0) {
             const uint32_t bitsx = ((1u << ((xe & 15) - (xa & 15) + 1)) - 1u) << (xa & 15);
             const uint32_t add = bitsx << (16 * (ly & 1));
-            fresh = (add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add)) && claim_fresh_word(g, node, word);
+            added = add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add);
           }
           xa = xe + 1;
         }
-        list_fresh_words(g, fresh, node * 128 + word);
+        alloc_new_bits(g, node, word, added, x16, y, z);
       }
     }
     if (!mark) return;
@@ -1697,13 +1698,13 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
         for (int xa = x0; xa <= x1;) {
           const int xe = min(x1, xa | 15);
           const int node = live ? nodes[nrow + (xa >> 4) - qx0] : -1;
-          bool fresh = false;
+          uint32_t added = 0u;
           if (node >= 0) {
             const uint32_t bitsx = ((1u << ((xe & 15) - (xa & 15) + 1)) - 1u) << (xa & 15);
             const uint32_t add = bitsx << (16 * (ly & 1));
-            fresh = (add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add)) && claim_fresh_word(g, node, word);
+            added = add & ~atomicOr(&g.amask[(size_t)node * 128 + word], add);
           }
-          list_fresh_words(g, fresh, node * 128 + word);
+          alloc_new_bits(g, node, word, added, xa & ~15, y, z);
           xa = xe + 1;
         }
       }
@@ -1812,11 +1813,7 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
   const unsigned div = k > 1 ? (unsigned)k : 1u;
   auto share = [&](unsigned single) { return k > 1 ? (single / div > 16 ? single / div : 16u) : single; };
   const unsigned nc = (unsigned)node_cap;
-  // the decision (counters[C_BIG]) and, for updates that stay incremental, the changed bricks' flags,
-  // their dilation marks and their dirty runs
-  VDB_LAUNCH_PDL(k_changed_mark<US>, dim3(share(2432), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it, k == 1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   cudaStream_t gs = st;
   if (fk.side) {
     e = cudaEventRecord(fk.fork, st);
@@ -1824,8 +1821,10 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
     if (e != cudaSuccess) return e;
     gs = fk.side;
   }
-  // global form, for the grids whose update switched to it (the others' blocks return at once; the
-  // kernels stride over their work, so a launch of at most two blocks per SM keeps that cheap)
+  // global form, for the grids whose update takes it (each kernel decides for itself; the others'
+  // blocks return at once, and the kernels stride over their work, so a launch of at most two
+  // blocks per SM keeps that cheap), on the side stream from the end of the ingest on, beside the
+  // incremental marking
   auto gated = [&](unsigned single) { return share(single < 304u ? single : 304u); };
   VDB_LAUNCH(k_clear_masks<GV>, dim3(gated(256), k), kT, 0, gs, gv);
   VDB_LAUNCH_PDL(k_obstacle_flags<GV>, dim3(gated(1024), k), kT, 0, gs, gv);
@@ -1846,9 +1845,9 @@ cudaError_t update_mark_kernels(US us, GV gv, int k, int node_cap, int R, bool w
     e = cudaEventRecord(fk.join, fk.side);
     if (e != cudaSuccess) return e;
   }
-  // incremental form: storage for the bricks the dilation added (a warp per fresh word, the count on
-  // the device: one wave of 8 warps per block on every SM); a batch's dirty runs after it
-  VDB_LAUNCH(k_alloc_fresh<US>, dim3(share(1216), k), kT, 0, st, us);
+  // incremental form, for the others: the changed bricks' flags, their dilation (with storage for
+  // the bricks it adds) and, for a single grid, their dirty runs; a batch's dirty runs after that
+  VDB_LAUNCH_PDL(k_changed_mark<US>, dim3(share(2432), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it, k == 1);
   if (k > 1) VDB_LAUNCH_PDL(k_mark_runs<US>, dim3(share(2432), k), kT, 0, st, us, t.run[0], t.run[1], t.run[2], it);
   return cudaGetLastError();
 }

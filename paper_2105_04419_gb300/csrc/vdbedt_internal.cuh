@@ -61,7 +61,7 @@ enum Counter : int {
   C_HAS_ZERO = 10,
   C_FINITE = 11,
   C_OBST = 12,
-  C_FRESH = 13,  // compute-set words first marked by this update (incremental), listed in flist
+  C_NB_START = 13,  // stored bricks when the running update began (its global-vs-incremental choice)
   C_EPOCH = 14,  // incremental update epoch (run and brick dedupe marks)
   C_DEFERRED = 15,  // the tracked ingest met "set" records whose node did not exist yet
   C_XB = 16,  // stored bricks in the update's dirty runs per axis (x, y, z: three consecutive words)
@@ -95,8 +95,6 @@ struct GridView {
   int32_t* child;     // [node_cap * 4096]
   uint32_t* amask;    // [node_cap * 128] compute-set bits: bit l = bx + 16 by + 256 bz (local)
   uint32_t* mwork;    // [node_cap * 384] obstacle bits and two dilation stages, same layout
-  uint32_t* afresh;   // [node_cap * 4] bit w of the node's 4 words: amask word w got bits this update
-  int32_t* flist;     // [node_cap * 128] node * 128 + word of those words (C_FRESH of them)
   uint32_t* nclaim;   // [node_cap * 128] bricks listed for allocation by the running ingest (amask layout)
   long long* node_key;  // [node_cap]
   int32_t* mark;      // [node_cap * 3 * 1024] epoch of the last time each run along axis a was queued
