@@ -194,13 +194,13 @@ vdbedt_status vdbedt_reset(vdbedt_handle h);
 vdbedt_status vdbedt_global(vdbedt_handle h);
 
 /* Incremental transform: apply staged records; recompute only the bricks that a flipped voxel can
- * reach (Chebyshev brick radius R around each changed brick).  Equal, bit for bit, to vdbedt_global
- * on the same occupancy.  When the changed bricks times (2R + 1)^3 exceed 24 times the stored
- * bricks (the marking would then cost more than recomputing the map), the update decides on the
- * device, after applying the records, to rebuild the compute set and work lists as vdbedt_global
- * does (the trade-off of the paper's Sec. V-A between global and incremental transforms); the
- * decision needs no host round trip, so a captured update keeps it.  stats (nullable) is filled
- * after a stream synchronisation. */
+ * reach (bricks whose nearest voxels lie closer than dmax to a changed brick's).  Equal, bit for
+ * bit, to vdbedt_global on the same occupancy.  When the changed bricks times (2R + 1)^3 exceed 24
+ * times the bricks stored when the update began (the marking would then cost more than
+ * recomputing the map), the update decides on the device, after applying the records, to rebuild
+ * the compute set and work lists as vdbedt_global does (the trade-off of the paper's Sec. V-A
+ * between global and incremental transforms); the decision needs no host round trip, so a
+ * captured update keeps it.  stats (nullable) is filled after a stream synchronisation. */
 vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats);
 
 /* D at n voxel coordinates; coordinates outside the grid or in unstored bricks give dmax^2
