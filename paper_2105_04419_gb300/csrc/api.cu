@@ -48,6 +48,7 @@ struct vdbedt_map {
   size_t device_bytes = 0;
   // staged records
   rec_t* stage = nullptr;
+  int32_t* stage_slot = nullptr;  // one word per staged record (the tracked ingest's brick slots)
   int64_t stage_n = 0, stage_cap = 0;
   bool stage_counted = false;  // the stage holds up to stage_n records, *d_count of them valid
   int32_t* d_count = nullptr;
@@ -170,8 +171,14 @@ vdbedt_status ensure_stage(vdbedt_map* h, int64_t need) {
   if (need <= h->stage_cap) return VDBEDT_OK;
   int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
   rec_t* p = nullptr;
+  int32_t* q = nullptr;
   cudaError_t e = cudaMalloc((void**)&p, sizeof(rec_t) * (size_t)cap);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage alloc");
+  e = cudaMalloc((void**)&q, sizeof(int32_t) * (size_t)cap);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    return cuda_fail(h, e, "stage alloc");
+  }
   if (h->stage_n > 0) {
     e = cudaMemcpyAsync(p, h->stage, sizeof(rec_t) * (size_t)h->stage_n, cudaMemcpyDeviceToDevice, h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "stage copy");
@@ -179,8 +186,10 @@ vdbedt_status ensure_stage(vdbedt_map* h, int64_t need) {
   if (h->stage) {
     cudaStreamSynchronize(h->st);
     cudaFree(h->stage);
+    cudaFree(h->stage_slot);
   }
   h->stage = p;
+  h->stage_slot = q;
   h->stage_cap = cap;
   return VDBEDT_OK;
 }
@@ -227,7 +236,8 @@ vdbedt_status do_global(vdbedt_map* h) {
   CK(h, cudaMemsetAsync(h->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), h->st), "memset");
   if (h->stage_n > 0) {
     CK(h,
-       launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, h->changed, h->scr, h->vlast, h->miss,
+       launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, h->changed, h->stage_slot, h->scr,
+                             h->vlast, h->miss,
                              h->st),
        "ingest");
     clear_stage(h);
@@ -458,6 +468,7 @@ void destroy_impl(vdbedt_map* h) {
   cudaStreamSynchronize(h->st);
   for (void* p : h->allocs) cudaFree(p);
   if (h->stage) cudaFree(h->stage);
+  if (h->stage_slot) cudaFree(h->stage_slot);
   if (h->scr.buf) cudaFree(h->scr.buf);
   if (h->vlast.buf) cudaFree(h->vlast.buf);
   if (h->miss.buf) cudaFree(h->miss.buf);
@@ -674,7 +685,8 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     CK(h, launch_begin_update(h->g, h->st), "begin update");
     if (h->stage_n > 0) {
       CK(h,
-         launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->scr, h->vlast,
+         launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->stage_slot, h->scr,
+                               h->vlast,
                                h->miss, h->st),
          "ingest");
       clear_stage(h);
@@ -895,7 +907,7 @@ vdbedt_status vdbedt_get_info(vdbedt_handle h, vdbedt_info* info) {
   info->nodes = h->h_pinned[C_NNODES];
   info->device_bytes =
       (int64_t)(h->device_bytes + h->scr.bytes + h->vlast.bytes + h->miss.bytes + h->io.bytes +
-                sizeof(rec_t) * h->stage_cap);
+                (sizeof(rec_t) + sizeof(int32_t)) * h->stage_cap);
   info->R = h->g.R;
   info->error_bits = h->h_pinned[C_ERR];
   return VDBEDT_OK;
@@ -1048,7 +1060,8 @@ vdbedt_status batch_global(vdbedt_batch* b) {
     if (m->stage_n <= 0) continue;
     BCK(b, cudaMemsetAsync(m->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), b->st), "memset");
     BCK(b,
-        launch_ingest_records(m->g, m->stage, m->stage_n, stage_count(m), false, nullptr, m->scr, m->vlast, m->miss,
+        launch_ingest_records(m->g, m->stage, m->stage_n, stage_count(m), false, nullptr, m->stage_slot, m->scr,
+                              m->vlast, m->miss,
                               b->st),
         "ingest");
     clear_stage(m);
@@ -1114,6 +1127,7 @@ vdbedt_status batch_update(vdbedt_batch* b, vdbedt_update_stats* stats) {
       a.n = m->stage_cap;
       a.n_dev = m->d_count;
       a.changed = m->changed;
+      a.rslot = m->stage_slot;
       BCK(b, prepare_update_args(m->g, m->vlast, m->miss, a, b->st), "update scratch");
       counts.c[i] = m->stage_counted ? -1 : (int32_t)m->stage_n;  // -1: the counted staging wrote it
       shape.max_n = std::max<int64_t>(shape.max_n, m->stage_cap);

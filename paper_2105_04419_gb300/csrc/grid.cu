@@ -653,6 +653,7 @@ __global__ void k_rec_missing(US us) {
     bool zero = false, bad = false;
     if (i < n) {
       int4 r = unpack_rec(rec[i]);
+      int rs = -1;  // the record's brick slot, for the ordered kernels (-2: once allocated)
       if (!rec_valid(g, r)) {
         bad = true;
       } else if (r.w == 1) {
@@ -660,16 +661,27 @@ __global__ void k_rec_missing(US us) {
         const unsigned long long nk = node_key_of(g, bx, by, bz);
         // an unbounded grid has no per-key flags: its nodes are created here, by the records
         const int node = A.nflag ? find_node(g, nk) : get_or_create_node(g, nk);
+        rs = -2;
         if (node >= 0) {
-          if (g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] < 0)
+          const int sl = g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
+          if (sl < 0)
             list_missing_brick(g, node, bx, by, bz, A.list);
+          else
+            rs = sl;
         } else if (!DEFERRED && A.nflag && !A.nflag[nk]) {
           A.nflag[nk] = 1;
           atomicOr(&g.counters[C_DEFERRED], 1);
         }
       } else {
         zero = true;
+        // a cleared voxel matters only in a stored brick: one stored now, or one a "set" record of
+        // the same ingest adds (looked up again once those are allocated)
+        if (!DEFERRED) {
+          rs = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
+          if (rs < 0) rs = -2;
+        }
       }
+      if (!DEFERRED && A.rslot) A.rslot[i] = rs;
     }
     if (!DEFERRED) {
       if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
@@ -724,6 +736,12 @@ __global__ void k_alloc_listed(US us) {
 // first kernel raises it with atomicMax, the second applies each voxel's winning record and puts
 // the entry back to -1, so vlast is all -1 between ingests.  Both run only when some record
 // clears a voxel, or when flips are tracked.
+// voxel index of a record inside its brick
+__device__ __forceinline__ int rec_in_brick(rec_t packed) {
+  const int4 r = unpack_rec(packed);
+  return (r.x & 7) + 8 * (r.y & 7) + 64 * (r.z & 7);
+}
+
 __device__ __forceinline__ int64_t rec_voxel(const GridView& g, rec_t packed) {
   const int4 r = unpack_rec(packed);
   if (!rec_valid(g, r)) return -1;
@@ -747,7 +765,7 @@ __device__ __forceinline__ void rec_last(const GridView& g, const rec_t* __restr
 // Flips are counted; with `track` the brick is appended once per epoch to the changed list.
 __device__ __forceinline__ void apply_last(const GridView& g, const rec_t* __restrict__ rec, int64_t n_max,
                                            const int32_t* n_dev, bool force, bool track, int32_t* __restrict__ vlast,
-                                           int32_t* __restrict__ changed) {
+                                           int32_t* __restrict__ changed, const int32_t* __restrict__ rslot = nullptr) {
   if (!force && !g.counters[C_HAS_ZERO]) return;
   const int64_t n = rec_count(n_max, n_dev);
   const int epoch = g.counters[C_EPOCH];
@@ -756,7 +774,13 @@ __device__ __forceinline__ void apply_last(const GridView& g, const rec_t* __res
     int slot = 0;
     if (j < n) {
       const rec_t packed = rec[j];
-      const int64_t key = rec_voxel(g, packed);
+      int64_t key;
+      if (rslot) {
+        const int sl = rslot[j];
+        key = sl >= 0 ? (int64_t)sl * 512 + rec_in_brick(packed) : -1;
+      } else {
+        key = rec_voxel(g, packed);
+      }
       if (key >= 0 && vlast[key] == (int)j) {
         vlast[key] = -1;
         const int s = (int)(key >> 9), v = (int)(key & 511);
@@ -791,19 +815,33 @@ __global__ void k_apply_last(GridView g, const rec_t* __restrict__ rec, int64_t 
   apply_last(g, rec, n_max, n_dev, force, track, vlast, changed);
 }
 
-// The tracked forms (incremental update): every record, flips tracked.
+// The tracked forms (incremental update): every record, flips tracked, each record's brick slot
+// taken from the first ingest kernel (looked up here only for bricks allocated since).
 template <class US>
 __global__ void k_upd_rec_last(US us) {
   pdl_enter();
   const UpdArgs A = us.get();
-  rec_last(A.g, A.rec, A.n, A.n_dev, true, A.vlast);
+  const GridView& g = A.g;
+  const int64_t n = rec_count(A.n, A.n_dev);
+  GRID_STRIDE(i, n) {
+    if (i < n) {
+      const rec_t packed = A.rec[i];
+      int s = A.rslot[i];
+      if (s == -2) {
+        const int4 r = unpack_rec(packed);
+        s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
+        A.rslot[i] = s;
+      }
+      if (s >= 0) atomicMax(&A.vlast[(int64_t)s * 512 + rec_in_brick(packed)], (int)i);
+    }
+  }
 }
 
 template <class US>
 __global__ void k_upd_apply_last(US us) {
   pdl_enter();
   const UpdArgs A = us.get();
-  apply_last(A.g, A.rec, A.n, A.n_dev, true, true, A.vlast, A.changed);
+  apply_last(A.g, A.rec, A.n, A.n_dev, true, true, A.vlast, A.changed, A.rslot);
 }
 
 // ---- dense ingest ----
@@ -1950,22 +1988,25 @@ cudaError_t prepare_update_args(const GridView& g, Scratch& vl, Scratch& miss, U
 // The tracked ingest: with `track` (an incremental update) each flipped voxel's brick joins the
 // changed list once; unbounded grids take this path for the global form too (no brick-key sort).
 static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev,
-                                         int32_t* changed, Scratch& vl, Scratch& miss, cudaStream_t st) {
+                                         int32_t* changed, int32_t* rslot, Scratch& vl, Scratch& miss,
+                                         cudaStream_t st) {
   UpdArgs a{};
   a.g = g;
   a.rec = rec;
   a.n = n;
   a.n_dev = n_dev;
   a.changed = changed;
+  a.rslot = rslot;
   cudaError_t e = prepare_update_args(g, vl, miss, a, st);
   if (e != cudaSuccess) return e;
   return update_ingest_kernels(UpdOne{a}, 1, n, g.unbounded ? 1 : (int64_t)g.NX * g.NY * g.NZ, g.cap, st);
 }
 
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
-                                  int32_t* changed, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st) {
+                                  int32_t* changed, int32_t* rslot, Scratch& scr, Scratch& vl, Scratch& miss,
+                                  cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  if (track || g.unbounded) return launch_ingest_tracked(g, rec, n, n_dev, changed, vl, miss, st);
+  if (track || g.unbounded) return launch_ingest_tracked(g, rec, n, n_dev, changed, rslot, vl, miss, st);
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
   const bool counting = n >= nbr_all / 4;
   // the dense mask is indexed by a 32-bit word number (8 words per brick)

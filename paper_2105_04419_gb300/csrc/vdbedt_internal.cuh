@@ -358,6 +358,7 @@ struct UpdArgs {
   int32_t* vlast;            // per-voxel last-record table (cap * 512 words, all -1 between ingests)
   int32_t* nflag;            // node-key flags of the tracked ingest (zero between updates)
   unsigned long long* list;  // bricks the tracked ingest allocates (cap entries)
+  int32_t* rslot;            // per staged record: its brick's slot (-1: none, -2: looked up once allocated)
 };
 cudaError_t ensure_scratch(Scratch& s, size_t bytes);
 
@@ -365,9 +366,11 @@ cudaError_t launch_reset(const GridView& g, cudaStream_t st);
 // n records at rec; with n_dev (nullable) only the first *n_dev of them (clamped to [0, n]).
 // scr: sort / scan scratch of the global form; vl: the per-voxel last-record table (allocated and
 // set to -1 on first use, cap * 512 words); miss: the tracked form's flag and list arrays
-// (allocated zeroed on first use and kept zero).
+// (allocated zeroed on first use and kept zero); rslot: one word per record (n entries) for the
+// tracked form's brick slots.
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
-                                  int32_t* changed, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st);
+                                  int32_t* changed, int32_t* rslot, Scratch& scr, Scratch& vl, Scratch& miss,
+                                  cudaStream_t st);
 // size the ingest scratch, the tracked arrays and the last-record table for up to n records
 cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st);
 // clear the per-update counters and advance the device-side update epoch

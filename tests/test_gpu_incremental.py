@@ -228,3 +228,34 @@ def test_profiled_transforms_equal_the_oracle():
         assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 16)) is None, f
         m.phase_times()
     m.close()
+
+
+def test_clears_in_bricks_added_by_the_same_frame():
+    """A frame that sets voxels in bricks not stored yet and clears some of them again (the clear
+    last): the bricks are added by the frame's own set records, and the later clears must still win
+    (last record of a voxel), with or without a capture."""
+    import paper_2105_04419_gb300 as V
+    nx, ny, nz = 96, 80, 64
+    occ = np.zeros((nz, ny, nx), np.uint8)
+    occ[5:9, 5:9, 5:9] = 1  # something stored far from the edits
+    for captured in (False, True):
+        m = V.Map(nx, ny, nz, 12)
+        m.set_occupancy_dense(occ)
+        m.global_()
+        cur = occ.copy()
+        g = V.UpdateGraph(m, 64) if captured else None
+        rs = np.random.default_rng(3 + captured)
+        for f in range(3):
+            base = np.array([60 + 4 * f, 50, 40], np.int32)
+            pts = base + rs.integers(0, 8, (6, 3)).astype(np.int32)
+            # set all six, then clear the first three again, then set the first once more and clear it
+            xyz = np.concatenate([pts, pts[:3], pts[:1], pts[:1]])
+            val = np.array([1] * 6 + [0] * 3 + [1, 0], np.uint8)
+            apply_records(cur, xyz, val)
+            if captured:
+                g.run(xyz, val)
+            else:
+                m.set_occupancy(xyz, val)
+                m.update()
+            assert first_mismatch(m.export_dense(), O.edt_factorised(cur, 12)) is None, (captured, f)
+        m.close()
