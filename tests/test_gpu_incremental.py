@@ -259,3 +259,26 @@ def test_clears_in_bricks_added_by_the_same_frame():
                 m.update()
             assert first_mismatch(m.export_dense(), O.edt_factorised(cur, 12)) is None, (captured, f)
         m.close()
+
+
+def test_many_changed_bricks_without_the_switch():
+    """An update whose changed bricks outnumber twice the marking launch's blocks (the kernel then
+    takes a thread per (changed brick, row / cube offset)) while staying incremental: small dmax,
+    every brick stored, random edits over the whole grid; several frames, each equal to Eq. 1."""
+    import paper_2105_04419_gb300 as V
+    rs = np.random.default_rng(19)
+    nx, ny, nz = 256, 256, 128
+    occ = (rs.random((nz, ny, nx)) < 0.01).astype(np.uint8)
+    m = V.Map(nx, ny, nz, 3)
+    m.set_occupancy_dense(occ)
+    m.global_()
+    for f in range(3):
+        k = 16000  # mostly sets of free voxels: about 8,000 changed bricks of the 16,384
+        xyz = np.stack([rs.integers(0, nx, k), rs.integers(0, ny, k), rs.integers(0, nz, k)], 1).astype(np.int32)
+        val = (rs.random(k) < 0.9).astype(np.uint8)
+        apply_records(occ, xyz, val)
+        m.set_occupancy(xyz, val)
+        st = m.update(stats=True)
+        assert st["global_form"] == 0 and st["changed_bricks"] > 2 * 2432, st
+        assert first_mismatch(m.export_dense(), O.edt_factorised(occ, 3)) is None, f
+    m.close()
