@@ -126,7 +126,7 @@ typedef struct {
 /* Create a handle for an nx x ny x nz grid with no obstacles (every D = dmax^2; VDBEDT_D_NONE when
  * untruncated).
  * Allocates the grid's storage for cfg->max_bricks bricks (about 4.1 KB each) and cfg->max_nodes
- * interior nodes (about 31 KB each) up front; the record stage and the ingest scratch grow on
+ * interior nodes (about 30 KB each) up front; the record stage and the ingest scratch grow on
  * demand (vdbedt_set_occupancy_counted reserves them ahead).  With both capacities set, the memory
  * follows the mapped part of the grid, not its size: a grid may span up to 2^32 bricks (e.g.
  * 16384 x 16384 x 8184 voxels) with obstacles in a small part of it.  Record-driven ingest and
