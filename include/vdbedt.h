@@ -147,7 +147,8 @@ vdbedt_status vdbedt_destroy(vdbedt_handle h);
  * more than once, its last record wins.  on_device != 0: xyz and occ are device pointers (read on
  * the stream; an invalid record is skipped and reported as EINVAL by the next synchronising call);
  * otherwise host pointers, validated here: any coordinate outside the grid or occ[k] > 1 rejects
- * the whole call with EINVAL.  n == 0 is a no-op; n < 0 is EINVAL. */
+ * the whole call with EINVAL.  n == 0 is a no-op; n < 0 is EINVAL; at most 2^31 - 1 records can be
+ * staged at a time (more: EINVAL). */
 vdbedt_status vdbedt_set_occupancy(vdbedt_handle h, const int32_t* xyz, const uint8_t* occ, int64_t n,
                                    int on_device);
 

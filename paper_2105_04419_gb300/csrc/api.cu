@@ -169,6 +169,8 @@ const void* mapped_host(const void* p) {
 
 vdbedt_status ensure_stage(vdbedt_map* h, int64_t need) {
   if (need <= h->stage_cap) return VDBEDT_OK;
+  // records are indexed by int32 in the ordered ingest
+  if (need > (int64_t)INT32_MAX) return fail(h, VDBEDT_EINVAL, "more than 2^31 - 1 records staged");
   int64_t cap = std::max<int64_t>(need + need / 2, 1 << 16);
   rec_t* p = nullptr;
   int32_t* q = nullptr;
