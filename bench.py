@@ -241,12 +241,15 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
     # dilation and the dirty runs, items = slot lists of the dirty runs
     phase_med = {k: statistics.median(p[k] for p in phases) for k in phases[0]}
 
-    def timed(run_frame, label):
-        # an NVTX range per timed sequence, so that a profiler can take just these frames
+    def timed(run_frame, label, before=None):
+        # an NVTX range per timed sequence, so that a profiler can take just these frames; `before`
+        # runs ahead of each frame's first event (stream-ordered, untimed)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nframes)]
         torch.cuda.nvtx.range_push(label)
         for k in range(nframes):
             flush.fill_(k & 255)
+            if before is not None:
+                before(k)
             ev[k][0].record(stream)
             run_frame(k)
             ev[k][1].record(stream)
@@ -272,11 +275,20 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
     mg.set_tuning(INCR_RUN, INCR_RUN, INCR_RUN, 3)
     mg.global_()
     graph = V.UpdateGraph(mg, max(counts))
-    graph_ms = timed(lambda k: graph.run(*sl[k]), "incremental_graph_frames")
+    # the frame's records written into the graph's input buffers before the frame (as a producer
+    # writing there would), then the replay timed: staging, ingest and transform
+    graph_ms = timed(lambda k: graph.replay(), "incremental_graph_frames", before=lambda k: graph.load(*sl[k]))
     D_graph = mg.export_dense(on_device=True)
     same = bool(torch.equal(D_eager, D_graph))
     del D_eager, D_graph
     mg.close()
+    # UpdateGraph.run on the same frames: the copies into the input buffers inside each frame
+    mr = V.Map(nx, ny, nz, dmax, voxel_size=0.1, stream=stream)
+    mr.set_tuning(INCR_RUN, INCR_RUN, INCR_RUN, 3)
+    mr.global_()
+    graph_r = V.UpdateGraph(mr, max(counts))
+    graph_run_ms = timed(lambda k: graph_r.run(*sl[k]), "incremental_graph_run_frames")
+    mr.close()
 
     # global transform of the final occupancy (same step as the headline: reset + records + global)
     fx = torch.from_numpy(W.occupied_coords(final_occ)).cuda()
@@ -319,6 +331,9 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
             "changed_bricks_per_frame": dist_summary([s["changed_bricks"] for s in stats]),
             "z_runs_per_frame": dist_summary([s["z_items"] for s in stats]),
             "runs": INCR_RUN, "graph_ms_per_frame": g, "eager_ms_per_frame": dist_summary(eager_ms),
+            "graph_run_ms_per_frame": dist_summary(graph_run_ms),
+            "graph_note": "graph: replay with the frame's records already in the graph's input buffers; graph_run: "
+                          "UpdateGraph.run, which copies them there inside the frame (two device copies, one fill)",
             "roofline_frames": {"model": "21 B x 512 x bricks of the z pass's dirty runs + 16 B x records, per frame",
                                 "bytes_per_frame": dist_summary(fbytes), "achieved_median": statistics.median(fgbs),
                                 "unit": "GB/s", "peak": peak, "peak_source": peak_src,

@@ -493,8 +493,10 @@ class _CapturedStep:
         _check(lib.vdbedt_set_occupancy_counted(h, self.xyz.data_ptr(), self.occ.data_ptr(), self.count.data_ptr(),
                                                 self.max_records), "vdbedt_set_occupancy_counted", h)
 
-    def run(self, xyz, occ):
-        """Replay for one set of records; xyz [n, 3] int32 and occ [n] uint8, CUDA tensors or numpy."""
+    def load(self, xyz, occ):
+        """Writes one set of records into the input buffers (stream-ordered on the map's stream)
+        without replaying; xyz [n, 3] int32 and occ [n] uint8, CUDA tensors or numpy.  A producer
+        may instead write xyz[:n], occ[:n] and count[0] itself."""
         torch = _torch()
         n = int(occ.shape[0])
         if n > self.max_records:
@@ -508,8 +510,12 @@ class _CapturedStep:
                 self.xyz[:n].copy_(xyz.view(-1, 3), non_blocking=True)
                 self.occ[:n].copy_(occ.view(-1), non_blocking=True)
             self.count.fill_(n)
-            self.graph.replay()
         self.m._leave()
+
+    def run(self, xyz, occ):
+        """Replay for one set of records; xyz [n, 3] int32 and occ [n] uint8, CUDA tensors or numpy."""
+        self.load(xyz, occ)
+        self.replay()
 
     def replay(self):
         """Replay with the records already in the input buffers (xyz, occ, count)."""

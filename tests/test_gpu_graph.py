@@ -99,7 +99,15 @@ def test_graph_replay_random_records_device_inputs():
         val = np.concatenate([rs.integers(0, 2, k), np.zeros(len(pick), np.int64)]).astype(np.uint8)
         for r in range(len(val)):
             occ[xyz[r, 2], xyz[r, 1], xyz[r, 0]] = val[r]
-        g.run(torch.from_numpy(xyz).cuda(), torch.from_numpy(val).cuda())
+        if f % 2:
+            g.run(torch.from_numpy(xyz).cuda(), torch.from_numpy(val).cuda())
+        else:  # a producer writing the input buffers itself, then a bare replay
+            n = len(val)
+            with torch.cuda.stream(m.stream):
+                g.xyz[:n].copy_(torch.from_numpy(xyz).cuda())
+                g.occ[:n].copy_(torch.from_numpy(val).cuda())
+                g.count.fill_(n)
+            g.replay()
         assert first_mismatch(m.export_dense(), O.edt_factorised(occ, dmax)) is None, f
 
 
