@@ -355,14 +355,14 @@ def bench_incremental(V, torch, wl, truth, stream, flush, nframes, INCR_RUN=4, a
 
 
 def bench_crossover(V, torch, wl, occ, xyz_d, stream, flush, fractions=(1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 0.1, 0.25, 0.5),
-                    seed=17):
+                    seed=17, untruncated=False):
     """Global against incremental transform after edits of growing size (the paper's ablation shape,
     Sec. V-A: remove a fraction of the obstacles at random and add as many new ones, uniform in the
     domain).  For each fraction the map holds the scene's field; the same records are staged and
     either vdbedt_update or vdbedt_global applies them (event-timed, L2 flushed before, 3 repeats,
-    median); the two fields are compared."""
+    median); the two fields are compared.  untruncated: the same on the map without truncation."""
     nx, ny, nz = wl["dims"]
-    dmax = wl["dmax"]
+    dmax = None if untruncated else wl["dmax"]
     rs = np.random.default_rng(seed)
     n_obs = xyz_d.shape[0]
     ones = torch.ones(n_obs, dtype=torch.uint8, device="cuda")
@@ -401,10 +401,14 @@ def bench_crossover(V, torch, wl, occ, xyz_d, stream, flush, fractions=(1e-4, 3e
         m.set_occupancy(rec, val)
         st = m.update(stats=True)
         same = bool(torch.equal(res.pop("update_field"), res.pop("global_field")))
-        rows.append({"fraction": f, "removed": k, "added": k, "net_flips": st["net_flips"],
-                     "changed_bricks": st["changed_bricks"], "z_bricks": st["z_bricks"],
-                     "update_ms": res["update"], "global_ms": res["global"],
-                     "global_over_update": res["global"] / res["update"], "same_field": same})
+        row = {"fraction": f, "removed": k, "added": k, "net_flips": st["net_flips"],
+               "changed_bricks": st["changed_bricks"], "z_bricks": st["z_bricks"],
+               "update_ms": res["update"], "global_ms": res["global"],
+               "global_over_update": res["global"] / res["update"], "same_field": same}
+        if untruncated:
+            del row["z_bricks"]
+            row.update(x_rows=st["x_items"], y_lines=st["y_items"], z_lines=st["z_items"])
+        rows.append(row)
     m.close()
     return {"workload": "the scene's obstacles; a fraction removed at random and as many added uniformly in the domain",
             "step": "staged records applied by vdbedt_update or by vdbedt_global on the same map", "rows": rows}
@@ -641,6 +645,94 @@ def bench_untruncated(V, torch, wl, xyz, ones, stream, flush, steps=5, warm=3):
             "passes_gbs_model": {k: vox * per_vox[k] / (phm[k] / 1e3) / 1e9 for k in per_vox},
             "bytes_per_voxel_model": per_vox, "peak": peak, "peak_source": peak_src,
             "l2": "flushed before every step (untimed)", "steps": steps}
+
+
+def bench_untruncated_frames(V, torch, wl, frames, stream, flush):
+    """The lidar frames of the incremental measurement on the untruncated map (the paper's Table II
+    setting: per-frame updates with dmax = infinity), map starting empty: an untimed pass with
+    statistics (lines each pass recomputes), the eager frames and the captured update's replays
+    (records placed in its input buffers before each frame), each frame event-timed with the L2
+    flushed before it; then the field against a global transform of the final occupancy."""
+    nx, ny, nz = wl["dims"]
+    nframes = len(frames)
+    counts = [len(v) for _, v in frames]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    xyz_d = torch.from_numpy(np.concatenate([x for x, _ in frames])).cuda()
+    val_d = torch.from_numpy(np.concatenate([v for _, v in frames])).cuda()
+    sl = [(xyz_d[offs[k]:offs[k + 1]], val_d[offs[k]:offs[k + 1]]) for k in range(nframes)]
+
+    def fresh():
+        m = V.Map(nx, ny, nz, None, voxel_size=0.1, stream=stream)
+        m.global_()
+        return m
+
+    m = fresh()
+    stats = []
+    for x, v in sl:
+        m.set_occupancy(x, v)
+        stats.append(m.update(stats=True))
+    m.close()
+
+    def timed(run_frame, before=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nframes)]
+        for k in range(nframes):
+            flush.fill_(k & 255)
+            if before is not None:
+                before(k)
+            ev[k][0].record(stream)
+            run_frame(k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    m = fresh()
+
+    def eager(k):
+        m.set_occupancy(*sl[k])
+        m.update()
+
+    eager_ms = timed(eager)
+    D_eager = m.export_dense(on_device=True)
+    # the global transform of the final occupancy on the same map, timed (reset + records + global)
+    final = m.export_occupancy(0, nz)
+    u = final.view(torch.int64)
+    fx = torch.stack([u & ((1 << 21) - 1), (u >> 21) & ((1 << 21) - 1), (u >> 42) & ((1 << 21) - 1)], 1)
+    fx = fx.to(torch.int32).contiguous()
+    fo = torch.ones(fx.shape[0], dtype=torch.uint8, device="cuda")
+    gms = []
+    for k in range(4):
+        flush.fill_(k & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.reset()
+        m.set_occupancy(fx, fo)
+        m.global_()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k >= 1:
+            gms.append(a.elapsed_time(b))
+    same_global = bool(torch.equal(D_eager, m.export_dense(on_device=True)))
+    m.close()
+    mg = fresh()
+    graph = V.UpdateGraph(mg, max(counts))
+    graph_ms = timed(lambda k: graph.replay(), before=lambda k: graph.load(*sl[k]))
+    same_graph = bool(torch.equal(D_eager, mg.export_dense(on_device=True)))
+    mg.close()
+    del D_eager
+    glob = statistics.median(gms)
+    g = dist_summary(graph_ms)
+    return {"frames": nframes, "workload": "the incremental measurement's lidar frames on the untruncated map "
+                                           "(map starts empty)",
+            "net_flips_per_frame": dist_summary([s["net_flips"] for s in stats]),
+            "lines_per_frame": {"x_rows": dist_summary([s["x_items"] for s in stats]),
+                                "y_lines": dist_summary([s["y_items"] for s in stats]),
+                                "z_lines": dist_summary([s["z_items"] for s in stats]),
+                                "of": {"x_rows": ny * nz, "y_lines": nx * nz, "z_lines": nx * ny}},
+            "global_form_frames": int(sum(s["global_form"] for s in stats)),
+            "graph_ms_per_frame": g, "eager_ms_per_frame": dist_summary(eager_ms),
+            "global_ms_final_occupancy": glob, "global_over_graph_median": glob / g["median"],
+            "equals_global_of_final_occupancy": same_global, "graph_equals_eager": same_graph,
+            "l2": "flushed before every frame (untimed)"}
 
 
 def bench_nearest(V, torch, m, dims, stream, reps=20):
@@ -1069,8 +1161,6 @@ def main():
     if wl["kind"] == "tunnel" and not args.no_clearance:
         line["clearance"] = bench_clearance(V, torch, m, occ, stream)
         line["nearest"] = bench_nearest(V, torch, m, wl["dims"], stream)
-    if wl["kind"] == "tunnel" and not args.no_untruncated:
-        line["untruncated"] = bench_untruncated(V, torch, wl, xyz, ones, stream, flush)
     if wl["kind"] == "tunnel" and not args.no_crossover:
         line["crossover"] = bench_crossover(V, torch, wl, occ, xyz, stream, flush)
     if wl["kind"] == "tunnel" and not args.no_batched:
@@ -1079,6 +1169,13 @@ def main():
     if wl["kind"] == "tunnel" and not args.no_incremental:
         line["incremental"], frames = bench_incremental(V, torch, wl, occ, stream, flush, args.frames,
                                                         args.incr_run, 0)
+    if wl["kind"] == "tunnel" and not args.no_untruncated:
+        line["untruncated"] = bench_untruncated(V, torch, wl, xyz, ones, stream, flush)
+        if frames:
+            line["untruncated"]["incremental"] = bench_untruncated_frames(V, torch, wl, frames, stream, flush)
+        if not args.no_crossover:
+            line["untruncated"]["crossover"] = bench_crossover(V, torch, wl, occ, xyz, stream, flush,
+                                                               fractions=(1e-4, 1e-3, 1e-2, 0.1), untruncated=True)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(occ, dmax)
         line["cpu_baseline"]["host"] = host_cpu()

@@ -78,8 +78,10 @@ typedef enum {
  * int32, and every brick stored from creation (max_bricks and max_nodes 0 or at least the grid's):
  * about 6.2 KB per 8^3 brick (32-bit intermediates) plus 8 bytes per voxel of line scratch, all
  * allocated at creation.  The transform runs whole lines of the grid (x: nearest occupied voxel of
- * the row; y, z: lower envelope of the parabolas rooted at the line's values); vdbedt_update applies
- * the staged records and recomputes the field (global form).  Not available: batches,
+ * the row; y, z: lower envelope of the parabolas rooted at the line's values).  vdbedt_update
+ * applies the staged records and recomputes only the lines they reach, exactly: the x rows holding
+ * a flipped voxel, then the y lines on which g1 changed, then the z lines on which g2 changed (each
+ * pass's output on a line depends only on its input along that line).  Not available: batches,
  * vdbedt_set_tuning, vdbedt_query_nearest and the unbounded flag. */
 #define VDBEDT_FLAG_UNTRUNCATED 2u
 #define VDBEDT_D_NONE 2147483647
@@ -111,16 +113,17 @@ typedef struct {
   int64_t records;        /* staged records consumed */
   int64_t net_flips;      /* voxels whose occupancy changed */
   int64_t changed_bricks; /* bricks holding a flipped voxel */
-  int64_t x_items;        /* brick runs recomputed by the x pass */
-  int64_t y_items;        /* brick runs recomputed by the y pass */
-  int64_t z_items;        /* brick runs recomputed by the z pass */
+  int64_t x_items;        /* brick runs recomputed by the x pass (untruncated grid: voxel rows) */
+  int64_t y_items;        /* brick runs recomputed by the y pass (untruncated grid: y lines) */
+  int64_t z_items;        /* brick runs recomputed by the z pass (untruncated grid: z lines) */
   int64_t new_bricks;     /* bricks allocated by this update */
   int64_t x_bricks;       /* stored bricks in those runs, recomputed by the x pass */
   int64_t y_bricks;       /* ... by the y pass */
   int64_t z_bricks;       /* ... by the z pass (global_form 1: every stored brick; the three counts are 0
                              in the envelope form, variant 8 or dmax > 45) */
   int64_t global_form;    /* 1: the edits reached so far that the update switched to the global form after
-                             applying them (same field, lower cost; see vdbedt_update) */
+                             applying them (same field, lower cost; see vdbedt_update), or the grid had no
+                             transform yet (or a new dense grid), which the update then computes whole */
 } vdbedt_update_stats;
 
 /* Create a handle for an nx x ny x nz grid with no obstacles (every D = dmax^2; VDBEDT_D_NONE when
@@ -201,7 +204,9 @@ vdbedt_status vdbedt_global(vdbedt_handle h);
  * recomputing the map), the update decides on the device, after applying the records, to rebuild
  * the compute set and work lists as vdbedt_global does (the trade-off of the paper's Sec. V-A
  * between global and incremental transforms); the decision needs no host round trip, so a
- * captured update keeps it.  stats (nullable) is filled after a stream synchronisation. */
+ * captured update keeps it.  On an untruncated grid the update recomputes the lines the flips reach
+ * (VDBEDT_FLAG_UNTRUNCATED), and its stats count lines (x rows, y lines, z lines) in x_items,
+ * y_items and z_items.  stats (nullable) is filled after a stream synchronisation. */
 vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats);
 
 /* D at n voxel coordinates; coordinates outside the grid or in unstored bricks give dmax^2
@@ -228,8 +233,7 @@ vdbedt_status vdbedt_export_dense(vdbedt_handle h, int32_t* out, int on_device);
  * empty grid; mode 1 replays the update's changes).  This is how one grid split into z-slabs over
  * several GPUs exchanges only the occupied voxels (or the changed bricks) of each slab's halo band.
  * Synchronises; *n_out (host) receives the number of records; more than max_n is EOVERFLOW (the
- * first max_n are written, *n_out holds the full count).  Record order is unspecified.  Mode 1 is
- * EINVAL on an untruncated grid (its updates recompute the field without a changed-brick list). */
+ * first max_n are written, *n_out holds the full count).  Record order is unspecified. */
 vdbedt_status vdbedt_export_occupancy(vdbedt_handle h, int32_t z_lo, int32_t z_hi, int32_t dz, int32_t mode,
                                       uint64_t* out, int64_t max_n, int64_t* n_out);
 

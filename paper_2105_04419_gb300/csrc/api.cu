@@ -427,6 +427,7 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   }
   AL(h->changed, cap);
   AL(h->d_invalid, 4);
+  if (untrunc) AL(g.ut_bits, ut_bits_words(g));
   h->d_count = h->d_invalid + 1;
 #undef AL
   e = cudaMallocHost((void**)&h->h_pinned, 64 * sizeof(int32_t));
@@ -439,6 +440,7 @@ vdbedt_status create_impl(const vdbedt_config* cfg, const PoolSlice* slice, vdbe
   cudaMemsetAsync(g.mark, 0, sizeof(int32_t) * (size_t)node_cap * 3 * 1024, h->st);
   if (!slice) cudaMemsetAsync(g.counters, 0, sizeof(int32_t) * C_NUM, h->st);
   if (untrunc) {
+    cudaMemsetAsync(g.ut_bits, 0, sizeof(uint32_t) * (size_t)ut_bits_words(g), h->st);
     // the line stacks too, so that a transform allocates nothing (and can be captured)
     e = ensure_scratch(h->uts, ut_scratch_bytes(g));
     if (e != cudaSuccess) return bail(e, "untruncated scratch");
@@ -659,6 +661,8 @@ vdbedt_status vdbedt_reset(vdbedt_handle h) {
   if (s) return s;
   DeviceGuard guard(h->device);
   CK(h, h->g.untrunc ? launch_ut_reset(h->g, h->st) : launch_reset(h->g, h->st), "reset");
+  if (h->g.untrunc)
+    CK(h, cudaMemsetAsync(h->g.ut_bits, 0, sizeof(uint32_t) * (size_t)ut_bits_words(h->g), h->st), "memset");
   clear_stage(h);
   h->computed = false;
   h->dense_pending = false;
@@ -678,9 +682,32 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
   DeviceGuard guard(h->device);
   const int64_t nrec = h->stage_n;
   const bool counted = h->stage_counted;
-  if (!h->computed || h->dense_pending || h->g.untrunc) {  // untruncated: always the global form
+  const bool whole = !h->computed || h->dense_pending;
+  if (whole) {
     s = do_global(h);
     if (s) return s;
+  } else if (h->g.untrunc) {
+    // untruncated: the tracked ingest marks the rows of the flipped voxels; each pass recomputes
+    // the lines whose input changed and marks the next axis's lines where its output changed
+    mark(h, 0);
+    CK(h, launch_begin_update(h->g, h->st), "begin update");
+    if (h->stage_n > 0) {
+      CK(h,
+         launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->stage_slot, h->scr,
+                               h->vlast, h->miss, h->st),
+         "ingest");
+      clear_stage(h);
+    }
+    mark(h, 1);
+    mark(h, 2);
+    mark(h, 3);
+    CK(h, launch_ut_update_pass(h->g, 0, h->uts.buf, h->st), "x pass");
+    mark(h, 4);
+    CK(h, launch_ut_update_pass(h->g, 1, h->uts.buf, h->st), "y pass");
+    mark(h, 5);
+    CK(h, launch_ut_update_pass(h->g, 2, h->uts.buf, h->st), "z pass");
+    mark(h, 6);
+    h->ev_recorded = h->profiling && !capturing(h);
   } else {
     const Tuning t = effective_tuning(h);
     mark(h, 0);
@@ -723,7 +750,7 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     stats->x_bricks = c[C_XB];
     stats->y_bricks = c[C_YB];
     stats->z_bricks = c[C_ZB];
-    stats->global_form = h->g.untrunc ? 1 : c[C_BIG];
+    stats->global_form = whole ? 1 : c[C_BIG];
   }
   return VDBEDT_OK;
 }
@@ -799,7 +826,7 @@ vdbedt_status vdbedt_export_occupancy(vdbedt_handle h, int32_t z_lo, int32_t z_h
                                       uint64_t* out, int64_t max_n, int64_t* n_out) {
   vdbedt_status s = check_handle(h);
   if (s) return s;
-  if (!n_out || (max_n > 0 && !out) || max_n < 0 || (mode != 0 && mode != 1) || (mode == 1 && h->g.untrunc))
+  if (!n_out || (max_n > 0 && !out) || max_n < 0 || (mode != 0 && mode != 1))
     return fail(h, VDBEDT_EINVAL, "bad export arguments");
   // caller z -> stored z (an unbounded grid's coordinates are stored shifted)
   const int64_t zl = std::max<int64_t>((int64_t)z_lo + h->g.off, 0), zh = std::min<int64_t>((int64_t)z_hi + h->g.off, h->g.nz);

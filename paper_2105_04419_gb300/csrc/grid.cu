@@ -792,6 +792,11 @@ __device__ __forceinline__ void apply_last(const GridView& g, const rec_t* __res
           flip = true;
           first = track && atomicExch(&g.bepoch[s], epoch) != epoch;
           slot = s;
+          if (track && g.ut_bits) {
+            // untruncated grid (brick s at bx + BX (by + BY bz)): the voxel's x row is dirty
+            const int64_t row = (int64_t)(s / g.BX) * 64 + (v >> 3);
+            atomicOr(&g.ut_bits[row >> 5], 1u << (row & 31));
+          }
         }
       }
     }

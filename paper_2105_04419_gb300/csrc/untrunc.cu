@@ -11,6 +11,8 @@
 //      exactly, in 64-bit integers (the grid's size limit keeps every product below 2^50).
 // kNone marks a row, plane or grid without an obstacle.  Only voxels inside the grid are read or
 // written; g1 and g2 hold int32 here (their arrays are allocated twice as large).
+#include <algorithm>
+
 #include "vdbedt_internal.cuh"
 
 namespace vdbedt {
@@ -56,14 +58,18 @@ __global__ void k_ut_bricks(GridView g) {
   }
 }
 
-// Empty occupancy and flags; the counters start over except the stored bricks and nodes.
+// Empty occupancy, flags and brick epochs; the counters start over except the stored bricks and
+// nodes.
 __global__ void k_ut_reset(GridView g) {
   const int64_t nb = (int64_t)g.BX * g.BY * g.BZ;
   if (blockIdx.x == 0 && (int)threadIdx.x < C_NUM && threadIdx.x != C_NBRICKS && threadIdx.x != C_NNODES)
     g.counters[threadIdx.x] = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb * 8; i += (int64_t)gridDim.x * blockDim.x) {
     g.occ[i] = 0ull;
-    if ((i & 7) == 0) g.bflags[i >> 3] = 0u;
+    if ((i & 7) == 0) {
+      g.bflags[i >> 3] = 0u;
+      g.bepoch[i >> 3] = 0;  // the update epoch starts over with the counters
+    }
   }
 }
 
@@ -98,10 +104,28 @@ __global__ void k_ut_dense(GridView g, const uint8_t* __restrict__ grid) {
 // x pass: a thread per voxel row (64 rows of a brick line on consecutive threads).  The forward
 // sweep stores the distance to the last occupied voxel at or before x (-1: none); the backward
 // sweep combines it with the distance to the next one and stores g1 = d^2 (kNone: empty row).
-__global__ void k_ut_x(GridView g) {
+// INCR (an update): only the rows whose dirty bit is set, each warp taking and clearing its word;
+// the forward sweep goes to `fwd` (row stride 8 BX), and the backward sweep compares each g1 with
+// the stored one, writes the bricks' row pieces that changed and sets the y-line bit (x, z) of
+// every changed voxel, a 32-bit word at a time.
+template <bool INCR>
+__global__ void k_ut_x(GridView g, int32_t* __restrict__ fwd) {
   int32_t* __restrict__ g1 = reinterpret_cast<int32_t*>(g.g1);
-  const int64_t nrows = (int64_t)g.BY * g.BZ * 64;
+  const int64_t nrows = (int64_t)g.BY * g.BZ * 64;  // a multiple of 64: every warp is whole
+  const int lane = threadIdx.x & 31;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nrows; t += (int64_t)gridDim.x * blockDim.x) {
+    if (INCR) {
+      uint32_t w = 0u;
+      if (lane == 0) {
+        w = g.ut_bits[t >> 5];
+        if (w) {
+          g.ut_bits[t >> 5] = 0u;
+          atomicAdd(&g.items_ctr[0], __popc(w));
+        }
+      }
+      w = __shfl_sync(0xffffffffu, w, 0);
+      if (!((w >> lane) & 1u)) continue;
+    }
     const int64_t line = t >> 6;
     const int q = (int)(t & 63);
     const int by = (int)(line % g.BY), bz = (int)(line / g.BY);
@@ -109,6 +133,7 @@ __global__ void k_ut_x(GridView g) {
     if (y >= g.ny || z >= g.nz) continue;
     const int shift = 8 * (y & 7);
     const size_t row = (size_t)(8 * (y & 7) + 64 * (z & 7));
+    int32_t* fw = INCR ? fwd + ((size_t)z * g.ny + y) * (size_t)(8 * g.BX) : nullptr;
     int last = -1;
     for (int bx = 0; bx < g.BX; ++bx) {
       const int s = ut_slot(g, bx, by, bz);
@@ -120,16 +145,19 @@ __global__ void k_ut_x(GridView g) {
         if ((byte >> i) & 1u) last = x;
         v[i] = last < 0 ? -1 : x - last;
       }
-      int4* dst = reinterpret_cast<int4*>(g1 + (size_t)s * kBrickVox + row);
+      int4* dst = reinterpret_cast<int4*>(INCR ? fw + 8 * bx : g1 + (size_t)s * kBrickVox + row);
       dst[0] = make_int4(v[0], v[1], v[2], v[3]);
       dst[1] = make_int4(v[4], v[5], v[6], v[7]);
     }
     int next = -1;
+    uint32_t* ybits = INCR ? g.ut_bits + ut_row_words(g) + (size_t)(ut_nxp(g) >> 5) * z : nullptr;
+    uint32_t acc = 0u;  // changed voxels of the current 32-voxel word of the row
     for (int bx = g.BX - 1; bx >= 0; --bx) {
       const int s = ut_slot(g, bx, by, bz);
       const uint32_t byte = (uint32_t)(g.occ[(size_t)s * 8 + (z & 7)] >> shift) & 0xFFu;
       int4* dst = reinterpret_cast<int4*>(g1 + (size_t)s * kBrickVox + row);
-      const int4 a = dst[0], b = dst[1];
+      const int4* src = reinterpret_cast<const int4*>(INCR ? fw + 8 * bx : g1 + (size_t)s * kBrickVox + row);
+      const int4 a = src[0], b = src[1];
       int v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int i = 7; i >= 0; --i) {
@@ -140,8 +168,26 @@ __global__ void k_ut_x(GridView g) {
         if (next >= 0 && (d < 0 || next - x < d)) d = next - x;
         v[i] = d < 0 ? kNone : d * d;
       }
-      dst[0] = make_int4(v[0], v[1], v[2], v[3]);
-      dst[1] = make_int4(v[4], v[5], v[6], v[7]);
+      if (INCR) {
+        const int4 oa = dst[0], ob = dst[1];
+        const int old[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+        uint32_t ch = 0u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (8 * bx + i < g.nx && v[i] != old[i]) ch |= 1u << i;
+        if (ch) {
+          dst[0] = make_int4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_int4(v[4], v[5], v[6], v[7]);
+          acc |= ch << ((8 * bx) & 31);
+        }
+        if (((8 * bx) & 31) == 0 && acc) {  // the word's first brick: flush its bits
+          atomicOr(&ybits[(8 * bx) >> 5], acc);
+          acc = 0u;
+        }
+      } else {
+        dst[0] = make_int4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_int4(v[4], v[5], v[6], v[7]);
+      }
     }
   }
 }
@@ -218,6 +264,114 @@ __global__ void k_ut_env(GridView g, const int32_t* __restrict__ in, int32_t* __
   }
 }
 
+// The update's y (AXIS 1) or z (AXIS 2) pass over the lines whose dirty bit is set: lines (x, c)
+// with x padded to NXP, so that a warp's 32 lanes are 32 lines along x at one c and take one word
+// of dirty bits (then cleared).  Each dirty lane builds its line's envelope as k_ut_env does; the
+// read-back runs on every lane of the warp in step, so that the y pass can gather the voxels whose
+// g2 changed into the z-line bits (x, y) with one ballot and one OR per position.  The z pass
+// writes D on its dirty lines.
+template <int AXIS>
+__global__ void k_ut_env_upd(GridView g, const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                             int2* __restrict__ stack) {
+  const int n = AXIS == 1 ? g.ny : g.nz;
+  const int nxp = ut_nxp(g);
+  const int64_t nlines = (int64_t)nxp * (AXIS == 1 ? g.nz : g.ny);  // a multiple of 32
+  uint32_t* bits = g.ut_bits + ut_row_words(g) + (AXIS == 1 ? 0 : ut_yline_words(g));
+  uint32_t* zbits = g.ut_bits + ut_row_words(g) + ut_yline_words(g);
+  const int lane = threadIdx.x & 31;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nlines; t += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t w = 0u;
+    if (lane == 0) {
+      w = bits[t >> 5];
+      if (w) {
+        bits[t >> 5] = 0u;
+        atomicAdd(&g.items_ctr[AXIS], __popc(w));
+      }
+    }
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (!w) continue;  // warp-uniform
+    const int x = (int)(t % nxp), c = (int)(t / nxp);  // c: z (AXIS 1) or y (AXIS 2)
+    const bool dirty = (w >> lane) & 1u;                 // set only for x < nx
+    auto at = [&](int i) -> size_t {
+      return AXIS == 1 ? (size_t)ut_slot(g, x >> 3, i >> 3, c >> 3) * kBrickVox + ut_vox(x, i, c)
+                       : (size_t)ut_slot(g, x >> 3, c >> 3, i >> 3) * kBrickVox + ut_vox(x, c, i);
+    };
+    int2* st = stack + ((size_t)c * g.nx + x) * n;
+    int m = 0;
+    if (dirty) {
+      int p0 = 0, f0 = 0, p1 = 0, f1 = 0;
+      for (int i0 = 0; i0 < n; i0 += 8) {
+        int fv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) fv[j] = i0 + j < n ? in[at(i0 + j)] : kNone;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int i = i0 + j, fi = fv[j];
+          if (fi == kNone) continue;
+          const long long Fi = (long long)fi + (long long)i * i;
+          while (m >= 2) {
+            const long long F1 = (long long)f1 + (long long)p1 * p1, F0 = (long long)f0 + (long long)p0 * p0;
+            if ((Fi - F1) * (long long)(p1 - p0) > (F1 - F0) * (long long)(i - p1)) break;
+            --m;
+            p1 = p0;
+            f1 = f0;
+            if (m >= 2) {
+              const int2 e = st[m - 2];
+              p0 = e.x;
+              f0 = e.y;
+            }
+          }
+          st[m] = make_int2(i, fi);
+          p0 = p1;
+          f0 = f1;
+          p1 = i;
+          f1 = fi;
+          ++m;
+        }
+      }
+    }
+    int k = 0;
+    int2 cur = make_int2(0, 0), nxt = cur, ahead = cur;
+    if (m > 0) {
+      cur = st[0];
+      nxt = m > 1 ? st[1] : cur;
+      ahead = m > 2 ? st[2] : cur;
+    }
+    for (int i = 0; i < n; ++i) {
+      bool changed = false;
+      if (dirty) {
+        int val = kNone;
+        if (m > 0) {
+          while (k + 1 < m) {
+            const long long Fc = (long long)cur.y + (long long)cur.x * cur.x;
+            const long long Fn = (long long)nxt.y + (long long)nxt.x * nxt.x;
+            if (Fn - Fc > 2ll * i * (long long)(nxt.x - cur.x)) break;
+            ++k;
+            cur = nxt;
+            nxt = ahead;
+            if (k + 2 < m) ahead = st[k + 2];
+          }
+          const int d = i - cur.x;
+          val = cur.y + d * d;
+        }
+        const size_t a = at(i);
+        if (AXIS == 1) {
+          if (out[a] != val) {
+            out[a] = val;
+            changed = true;
+          }
+        } else {
+          out[a] = val;
+        }
+      }
+      if (AXIS == 1) {
+        const uint32_t b = __ballot_sync(0xffffffffu, changed);
+        if (lane == 0 && b) atomicOr(&zbits[((int64_t)nxp * i + (x - lane)) >> 5], b);
+      }
+    }
+  }
+}
+
 // Brick flags after the transform: obstacle bits, and finite D (voxel (0, 0, 0) of every brick lies
 // inside the grid; with an obstacle anywhere every voxel is finite).
 __global__ void k_ut_flags(GridView g) {
@@ -250,18 +404,37 @@ cudaError_t launch_ut_dense(const GridView& g, const uint8_t* grid, cudaStream_t
   return cudaGetLastError();
 }
 
-size_t ut_scratch_bytes(const GridView& g) { return (size_t)g.nx * g.ny * g.nz * sizeof(int2); }
+// The line stacks (8 bytes per voxel), or the x rows of an update's forward sweep (4 bytes per
+// voxel of rows padded to 8 BX), whichever is larger.
+size_t ut_scratch_bytes(const GridView& g) {
+  return std::max((size_t)g.nx * g.ny * g.nz * sizeof(int2), (size_t)8 * g.BX * g.ny * g.nz * sizeof(int32_t));
+}
 
 cudaError_t launch_ut_pass(const GridView& g, int axis, void* scratch, cudaStream_t st) {
   int32_t* g1 = reinterpret_cast<int32_t*>(g.g1);
   int32_t* g2 = reinterpret_cast<int32_t*>(g.g2);
   int2* stack = static_cast<int2*>(scratch);
   if (axis == 0) {
-    VDB_LAUNCH(k_ut_x, ut_blocks((int64_t)g.BY * g.BZ * 64), kUT, 0, st, g);
+    VDB_LAUNCH(k_ut_x<false>, ut_blocks((int64_t)g.BY * g.BZ * 64), kUT, 0, st, g, nullptr);
   } else if (axis == 1) {
     VDB_LAUNCH(k_ut_env<1>, ut_blocks((int64_t)g.nx * g.nz), kUT, 0, st, g, g1, g2, stack);
   } else {
     VDB_LAUNCH(k_ut_env<2>, ut_blocks((int64_t)g.nx * g.ny), kUT, 0, st, g, g2, g.dist, stack);
+    VDB_LAUNCH(k_ut_flags, ut_blocks((int64_t)g.BX * g.BY * g.BZ), kUT, 0, st, g);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ut_update_pass(const GridView& g, int axis, void* scratch, cudaStream_t st) {
+  int32_t* g1 = reinterpret_cast<int32_t*>(g.g1);
+  int32_t* g2 = reinterpret_cast<int32_t*>(g.g2);
+  if (axis == 0) {
+    VDB_LAUNCH(k_ut_x<true>, ut_blocks((int64_t)g.BY * g.BZ * 64), kUT, 0, st, g, static_cast<int32_t*>(scratch));
+  } else if (axis == 1) {
+    VDB_LAUNCH(k_ut_env_upd<1>, ut_blocks((int64_t)ut_nxp(g) * g.nz), kUT, 0, st, g, g1, g2, static_cast<int2*>(scratch));
+  } else {
+    VDB_LAUNCH(k_ut_env_upd<2>, ut_blocks((int64_t)ut_nxp(g) * g.ny), kUT, 0, st, g, g2, g.dist,
+               static_cast<int2*>(scratch));
     VDB_LAUNCH(k_ut_flags, ut_blocks((int64_t)g.BX * g.BY * g.BZ), kUT, 0, st, g);
   }
   return cudaGetLastError();

@@ -113,7 +113,21 @@ struct GridView {
   int slot_base;
   int item_cap;       // capacity of the work lists (items per axis)
   int32_t* items_ctr; // [3] items queued along x, y, z (the grid's counters, or the batch's)
+  // Untruncated grids: dirty-line bits of an update (null otherwise), three bitmaps back to back,
+  // each cleared by the pass that reads it: x rows (bit (by + BY bz) * 64 + (y & 7) + 8 (z & 7), set
+  // by the tracked ingest at each flipped voxel), y lines (bit x + NXP z, set where the x pass
+  // changed g1) and z lines (bit x + NXP y, set where the y pass changed g2); NXP = nx rounded up
+  // to 32, so that a warp's 32 lines along x share one word.
+  uint32_t* ut_bits;
 };
+
+__host__ __device__ inline int ut_nxp(const GridView& g) { return (g.nx + 31) & ~31; }
+__host__ __device__ inline int64_t ut_row_words(const GridView& g) { return (int64_t)g.BY * g.BZ * 2; }
+__host__ __device__ inline int64_t ut_yline_words(const GridView& g) { return (int64_t)(ut_nxp(g) >> 5) * g.nz; }
+__host__ __device__ inline int64_t ut_zline_words(const GridView& g) { return (int64_t)(ut_nxp(g) >> 5) * g.ny; }
+__host__ __device__ inline int64_t ut_bits_words(const GridView& g) {
+  return ut_row_words(g) + ut_yline_words(g) + ut_zline_words(g);
+}
 
 __host__ __device__ inline unsigned long long node_key_of(const GridView& g, int bx, int by, int bz) {
   return (unsigned long long)(bx >> 4) +
@@ -427,6 +441,10 @@ cudaError_t launch_ut_reset(const GridView& g, cudaStream_t st);
 cudaError_t launch_ut_dense(const GridView& g, const uint8_t* grid, cudaStream_t st);
 size_t ut_scratch_bytes(const GridView& g);
 cudaError_t launch_ut_pass(const GridView& g, int axis, void* scratch, cudaStream_t st);
+// The update's pass along `axis` over the lines its dirty bits name (x: rows holding a flipped
+// voxel; y, z: lines whose input changed), marking the next axis's lines where its output changed;
+// lines recomputed are counted in items_ctr[axis].  The z pass also refreshes the brick flags.
+cudaError_t launch_ut_update_pass(const GridView& g, int axis, void* scratch, cudaStream_t st);
 // slot lists of every queued run (half path)
 cudaError_t launch_item_slots(const GridView& g, const Tuning& t, const Items& it, cudaStream_t st);
 
