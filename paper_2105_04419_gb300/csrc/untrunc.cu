@@ -8,7 +8,8 @@
 //   y, z: per line, the lower envelope of the parabolas f(i) + (t - i)^2 rooted at the line's
 //      finite values (g1, then g2): built on a stack in one sweep, read back in a second.  Two
 //      parabolas are compared through their intersection with the denominators multiplied out,
-//      exactly, in 64-bit integers (the grid's size limit keeps every product below 2^50).
+//      exactly: the grid's size limit keeps every f(p) + p^2 below 2^31, so the differences are
+//      int32 and each product one widening multiply (below 2^48).
 // kNone marks a row, plane or grid without an obstacle.  Only voxels inside the grid are read or
 // written; g1 and g2 hold int32 here (their arrays are allocated twice as large).
 #include <algorithm>
@@ -25,6 +26,16 @@ __device__ __forceinline__ int ut_slot(const GridView& g, int bx, int by, int bz
 }
 
 __device__ __forceinline__ int ut_vox(int x, int y, int z) { return (x & 7) + 8 * (y & 7) + 64 * (z & 7); }
+
+// A line's stack in the scratch, interleaved with the other 31 lines of its group of 32 (entry m
+// of line t at ((t >> 5) n + m) 32 + (t & 31)): lanes of a warp that push or pop at similar depths
+// touch the same 32-byte sectors instead of 32 separate regions.
+struct LineStack {
+  int2* p;
+  __device__ __forceinline__ LineStack(int2* stack, int64_t t, int n)
+      : p(stack + (size_t)(t >> 5) * 32 * n + (size_t)(t & 31)) {}
+  __device__ __forceinline__ int2& operator[](int m) const { return p[(size_t)m * 32]; }
+};
 
 unsigned ut_blocks(int64_t threads) {
   const int64_t b = (threads + kUT - 1) / kUT;
@@ -192,75 +203,105 @@ __global__ void k_ut_x(GridView g, int32_t* __restrict__ fwd) {
   }
 }
 
+// Voxel i of line (x, c) along AXIS (1: y, c = z; 2: z, c = y) in a pool of bricks at fixed slots:
+// base + (i >> 3) * brick stride + (i & 7) * voxel stride.
+template <int AXIS>
+struct LineAt {
+  size_t base, bstride;
+  __device__ __forceinline__ LineAt(const GridView& g, int x, int c) {
+    base = AXIS == 1 ? (size_t)ut_slot(g, x >> 3, 0, c >> 3) * kBrickVox + ut_vox(x, 0, c)
+                     : (size_t)ut_slot(g, x >> 3, c >> 3, 0) * kBrickVox + ut_vox(x, c, 0);
+    bstride = (size_t)kBrickVox * (AXIS == 1 ? g.BX : (size_t)g.BX * g.BY);
+  }
+  __device__ __forceinline__ size_t operator()(int i) const {
+    return base + (size_t)(i >> 3) * bstride + (size_t)((i & 7) * (AXIS == 1 ? 8 : 64));
+  }
+};
+
+// Lower envelope of the parabolas f(i) + (t - i)^2 over the line's finite values, built on the
+// line's stack: entries (p, F = f(p) + p^2), the top two also in registers.  The grid's size limit
+// keeps every F below 2^31, so differences of F are int32 and each intersection test compares two
+// widening 32 x 32 -> 64-bit products exactly.  The inputs are loaded a brick (8 positions) at a
+// time, all eight before any is used.  Returns the entry count.
+template <int AXIS>
+__device__ __forceinline__ int env_build(const LineStack& st, const LineAt<AXIS>& at, const int32_t* __restrict__ in,
+                                         int n) {
+  int m = 0, p0 = 0, F0 = 0, p1 = 0, F1 = 0;
+  for (int i0 = 0; i0 < n; i0 += 8) {
+    int fv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) fv[j] = i0 + j < n ? in[at(i0 + j)] : kNone;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + j;
+      if (fv[j] == kNone) continue;
+      const int Fi = fv[j] + i * i;
+      while (m >= 2) {
+        // drop the top when the new parabola undercuts it no later than the top undercuts the one
+        // below: (Fi - F1) / (i - p1) <= (F1 - F0) / (p1 - p0)
+        if ((long long)(Fi - F1) * (p1 - p0) > (long long)(F1 - F0) * (i - p1)) break;
+        --m;
+        p1 = p0;
+        F1 = F0;
+        if (m >= 2) {
+          const int2 e = st[m - 2];
+          p0 = e.x;
+          F0 = e.y;
+        }
+      }
+      st[m] = make_int2(i, Fi);
+      p0 = p1;
+      F0 = F1;
+      p1 = i;
+      F1 = Fi;
+      ++m;
+    }
+  }
+  return m;
+}
+
+// Reading an envelope back in increasing position: the lowest parabola only moves forward.
+// Entries k, k + 1 and (loaded ahead) k + 2 in registers.
+struct EnvRead {
+  const LineStack& st;
+  int m, k;
+  int2 cur, nxt, ahead;
+  __device__ __forceinline__ EnvRead(const LineStack& s, int count) : st(s), m(count), k(0) {
+    cur = nxt = ahead = make_int2(0, 0);
+    if (m > 0) {
+      cur = st[0];
+      nxt = m > 1 ? st[1] : cur;
+      ahead = m > 2 ? st[2] : cur;
+    }
+  }
+  // the envelope at i (i non-decreasing between calls); kNone for an empty envelope
+  __device__ __forceinline__ int at(int i) {
+    if (m == 0) return kNone;
+    while (k + 1 < m) {
+      // the next parabola is no higher at i: F(nxt) - F(cur) <= 2 i (nxt - cur)
+      if ((long long)(nxt.y - cur.y) > (long long)(2 * i) * (nxt.x - cur.x)) break;
+      ++k;
+      cur = nxt;
+      nxt = ahead;
+      if (k + 2 < m) ahead = st[k + 2];
+    }
+    const int d = i - cur.x;
+    return (cur.y - cur.x * cur.x) + d * d;  // f(p) + (i - p)^2
+  }
+};
+
 // y (AXIS 1: g1 -> g2) or z (AXIS 2: g2 -> D) pass: a thread per line, lines (x, z) or (x, y)
-// with x fastest.  The line's stack (position, value) lives in `stack`, n entries per line.
+// with x fastest, the line's stack in `stack` (LineStack).
 template <int AXIS>
 __global__ void k_ut_env(GridView g, const int32_t* __restrict__ in, int32_t* __restrict__ out, int2* __restrict__ stack) {
   const int n = AXIS == 1 ? g.ny : g.nz;
   const int64_t nlines = (int64_t)g.nx * (AXIS == 1 ? g.nz : g.ny);
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nlines; t += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(t % g.nx), c = (int)(t / g.nx);  // c: z (AXIS 1) or y (AXIS 2)
-    auto at = [&](int i) -> size_t {
-      return AXIS == 1 ? (size_t)ut_slot(g, x >> 3, i >> 3, c >> 3) * kBrickVox + ut_vox(x, i, c)
-                       : (size_t)ut_slot(g, x >> 3, c >> 3, i >> 3) * kBrickVox + ut_vox(x, c, i);
-    };
-    int2* st = stack + (size_t)t * n;
-    // build: the top two entries stay in registers (p1 top, p0 below it); the inputs are loaded a
-    // brick (8 positions) at a time, all eight before any is used
-    int m = 0, p0 = 0, f0 = 0, p1 = 0, f1 = 0;
-    for (int i0 = 0; i0 < n; i0 += 8) {
-      int fv[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) fv[j] = i0 + j < n ? in[at(i0 + j)] : kNone;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int i = i0 + j, fi = fv[j];
-        if (fi == kNone) continue;
-        const long long Fi = (long long)fi + (long long)i * i;
-        while (m >= 2) {
-          // drop the top when the new parabola undercuts it no later than the top undercuts the one
-          // below: (Fi - F1) / (i - p1) <= (F1 - F0) / (p1 - p0)
-          const long long F1 = (long long)f1 + (long long)p1 * p1, F0 = (long long)f0 + (long long)p0 * p0;
-          if ((Fi - F1) * (long long)(p1 - p0) > (F1 - F0) * (long long)(i - p1)) break;
-          --m;
-          p1 = p0;
-          f1 = f0;
-          if (m >= 2) {
-            const int2 e = st[m - 2];
-            p0 = e.x;
-            f0 = e.y;
-          }
-        }
-        st[m] = make_int2(i, fi);
-        p0 = p1;
-        f0 = f1;
-        p1 = i;
-        f1 = fi;
-        ++m;
-      }
-    }
-    // read back: the envelope's parabola moves forward with the position
-    if (m == 0) {
-      for (int i = 0; i < n; ++i) out[at(i)] = kNone;
-      continue;
-    }
-    // entries k, k + 1 and (loaded ahead) k + 2 in registers
-    int k = 0;
-    int2 cur = st[0], nxt = m > 1 ? st[1] : cur, ahead = m > 2 ? st[2] : cur;
-    for (int i = 0; i < n; ++i) {
-      while (k + 1 < m) {
-        // the next parabola is no higher at i: F(nxt) - F(cur) <= 2 i (nxt - cur)
-        const long long Fc = (long long)cur.y + (long long)cur.x * cur.x;
-        const long long Fn = (long long)nxt.y + (long long)nxt.x * nxt.x;
-        if (Fn - Fc > 2ll * i * (long long)(nxt.x - cur.x)) break;
-        ++k;
-        cur = nxt;
-        nxt = ahead;
-        if (k + 2 < m) ahead = st[k + 2];
-      }
-      const int d = i - cur.x;
-      out[at(i)] = cur.y + d * d;
-    }
+    const LineAt<AXIS> at(g, x, c);
+    const LineStack st(stack, t, n);
+    EnvRead env(st, env_build<AXIS>(st, at, in, n));
+    for (int i = 0; i < n; ++i) out[at(i)] = env.at(i);
   }
 }
 
@@ -292,68 +333,13 @@ __global__ void k_ut_env_upd(GridView g, const int32_t* __restrict__ in, int32_t
     if (!w) continue;  // warp-uniform
     const int x = (int)(t % nxp), c = (int)(t / nxp);  // c: z (AXIS 1) or y (AXIS 2)
     const bool dirty = (w >> lane) & 1u;                 // set only for x < nx
-    auto at = [&](int i) -> size_t {
-      return AXIS == 1 ? (size_t)ut_slot(g, x >> 3, i >> 3, c >> 3) * kBrickVox + ut_vox(x, i, c)
-                       : (size_t)ut_slot(g, x >> 3, c >> 3, i >> 3) * kBrickVox + ut_vox(x, c, i);
-    };
-    int2* st = stack + ((size_t)c * g.nx + x) * n;
-    int m = 0;
-    if (dirty) {
-      int p0 = 0, f0 = 0, p1 = 0, f1 = 0;
-      for (int i0 = 0; i0 < n; i0 += 8) {
-        int fv[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) fv[j] = i0 + j < n ? in[at(i0 + j)] : kNone;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int i = i0 + j, fi = fv[j];
-          if (fi == kNone) continue;
-          const long long Fi = (long long)fi + (long long)i * i;
-          while (m >= 2) {
-            const long long F1 = (long long)f1 + (long long)p1 * p1, F0 = (long long)f0 + (long long)p0 * p0;
-            if ((Fi - F1) * (long long)(p1 - p0) > (F1 - F0) * (long long)(i - p1)) break;
-            --m;
-            p1 = p0;
-            f1 = f0;
-            if (m >= 2) {
-              const int2 e = st[m - 2];
-              p0 = e.x;
-              f0 = e.y;
-            }
-          }
-          st[m] = make_int2(i, fi);
-          p0 = p1;
-          f0 = f1;
-          p1 = i;
-          f1 = fi;
-          ++m;
-        }
-      }
-    }
-    int k = 0;
-    int2 cur = make_int2(0, 0), nxt = cur, ahead = cur;
-    if (m > 0) {
-      cur = st[0];
-      nxt = m > 1 ? st[1] : cur;
-      ahead = m > 2 ? st[2] : cur;
-    }
+    const LineAt<AXIS> at(g, x, c);
+    const LineStack st(stack, t, n);
+    EnvRead env(st, dirty ? env_build<AXIS>(st, at, in, n) : 0);
     for (int i = 0; i < n; ++i) {
       bool changed = false;
       if (dirty) {
-        int val = kNone;
-        if (m > 0) {
-          while (k + 1 < m) {
-            const long long Fc = (long long)cur.y + (long long)cur.x * cur.x;
-            const long long Fn = (long long)nxt.y + (long long)nxt.x * nxt.x;
-            if (Fn - Fc > 2ll * i * (long long)(nxt.x - cur.x)) break;
-            ++k;
-            cur = nxt;
-            nxt = ahead;
-            if (k + 2 < m) ahead = st[k + 2];
-          }
-          const int d = i - cur.x;
-          val = cur.y + d * d;
-        }
+        const int val = env.at(i);
         const size_t a = at(i);
         if (AXIS == 1) {
           if (out[a] != val) {
@@ -404,10 +390,10 @@ cudaError_t launch_ut_dense(const GridView& g, const uint8_t* grid, cudaStream_t
   return cudaGetLastError();
 }
 
-// The line stacks (8 bytes per voxel), or the x rows of an update's forward sweep (4 bytes per
-// voxel of rows padded to 8 BX), whichever is larger.
+// The line stacks (8 bytes per voxel of lines padded along x to a multiple of 32), or the x rows
+// of an update's forward sweep (4 bytes per voxel of rows padded to 8 BX), whichever is larger.
 size_t ut_scratch_bytes(const GridView& g) {
-  return std::max((size_t)g.nx * g.ny * g.nz * sizeof(int2), (size_t)8 * g.BX * g.ny * g.nz * sizeof(int32_t));
+  return std::max((size_t)ut_nxp(g) * g.ny * g.nz * sizeof(int2), (size_t)8 * g.BX * g.ny * g.nz * sizeof(int32_t));
 }
 
 cudaError_t launch_ut_pass(const GridView& g, int axis, void* scratch, cudaStream_t st) {
