@@ -1363,11 +1363,12 @@ __global__ void __launch_bounds__(256) k_alloc_marked(VS vs, bool init_fields) {
 // read before another thread's exchange only leads to the exchange).
 __device__ __forceinline__ bool claim_run(const GridView& g, int axis, int bx, int by, int bz, int node, int run,
                                           int epoch, unsigned long long& packed) {
+  // run is 4, 8 or 16: a shift and a mask instead of a division
   const int la = axis == 0 ? bx & 15 : (axis == 1 ? by & 15 : bz & 15);
   const int l1 = axis == 0 ? by & 15 : bx & 15, l2 = axis == 2 ? by & 15 : bz & 15;
-  int* mk = &g.mark[((size_t)node * 3 + axis) * 1024 + l1 + 16 * (l2 + 16 * (la / run))];
+  int* mk = &g.mark[((size_t)node * 3 + axis) * 1024 + l1 + 16 * (l2 + 16 * (la >> (__ffs(run) - 1)))];
   if (__ldcg(mk) == epoch || atomicExch(mk, epoch) == epoch) return false;
-  const int back = la % run;
+  const int back = la & (run - 1);
   packed = pack_brick(bx - (axis == 0 ? back : 0), by - (axis == 1 ? back : 0), bz - (axis == 2 ? back : 0));
   return true;
 }
@@ -1753,21 +1754,25 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
       }
     }
     if (!mark) continue;  // block-uniform
-    // dirty runs: a thread per (column, z run) of the cube, block-uniform rounds (the lists' places
-    // are reserved a warp at a time)
-    const int r0 = z0 - z0 % rz, nruns = (z1 - r0) / rz + 1;
-    const int ncx = x1 - x0 + 1, ncol = ncx * (y1 - y0 + 1), total = ncol * nruns;
-    for (int u0 = 0; u0 < total; u0 += (int)blockDim.x) {
-      const int u = u0 + (int)threadIdx.x;
-      bool wx = false, wy = false, wz = false;
-      unsigned long long px = 0, py = 0, pz = 0;
-      if (u < total) {
-        const int col = u % ncol, zr = u / ncol;
-        const int bx = x0 + col % ncx, by = y0 + col / ncx;
+    // dirty runs: a thread per column (x, y) of the cube, looping over the cube's z runs (runs of
+    // 4, 8 or 16: shifts, not divisions); the rounds and the loop are block-uniform, and a warp
+    // past the last column skips both (the lists' places are reserved a warp at a time)
+    const int r0 = z0 & ~(rz - 1), nruns = ((z1 - r0) >> (__ffs(rz) - 1)) + 1;
+    const int ncx = x1 - x0 + 1, ncol = ncx * (y1 - y0 + 1);
+    for (int c0 = 0; c0 < ncol; c0 += (int)blockDim.x) {
+      if (c0 + ((int)threadIdx.x & ~31) >= ncol) continue;  // warp-uniform
+      const int col = c0 + (int)threadIdx.x;
+      const int cy = col / ncx;
+      const int bx = x0 + (col - cy * ncx), by = y0 + cy;
+      const int gx = brick_gap(bx - c.x), gy = brick_gap(by - c.y), in_plane = gx * gx + gy * gy;
+      const bool col_live = col < ncol && in_plane < g.INF;
+      const int nxy = ((bx >> 4) - qx0) + nqx * ((by >> 4) - qy0);
+      for (int zr = 0; zr < nruns; ++zr) {
+        bool wx = false, wy = false, wz = false;
+        unsigned long long px = 0, py = 0, pz = 0;
         const int zs = max(r0 + zr * rz, z0), ze = min(r0 + zr * rz + rz - 1, z1);
-        const int node = nodes[((bx >> 4) - qx0) + nqx * (((by >> 4) - qy0) + nqy * ((zs >> 4) - qz0))];
-        const int gx = brick_gap(bx - c.x), gy = brick_gap(by - c.y), in_plane = gx * gx + gy * gy;
-        if (node >= 0 && in_plane < g.INF) {
+        const int node = col_live ? nodes[nxy + nqx * nqy * ((zs >> 4) - qz0)] : -1;
+        if (node >= 0) {
           const int32_t* ch = g.child + (size_t)node * kNodeBricks;
           bool any = false;
           for (int bz = zs; bz <= ze; ++bz) {
@@ -1781,10 +1786,10 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
           }
           if (any) wz = claim_run(g, 2, bx, by, zs, node, rz, epoch, pz);
         }
+        emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
+        emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
+        emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
       }
-      emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
-      emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
-      emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
     }
   }
 }
