@@ -1754,25 +1754,22 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
       }
     }
     if (!mark) continue;  // block-uniform
-    // dirty runs: a thread per column (x, y) of the cube, looping over the cube's z runs (runs of
-    // 4, 8 or 16: shifts, not divisions); the rounds and the loop are block-uniform, and a warp
-    // past the last column skips both (the lists' places are reserved a warp at a time)
+    // dirty runs: a thread per (column, z run) of the cube, block-uniform rounds (the lists' places
+    // are reserved a warp at a time); runs are 4, 8 or 16 bricks (shifts, not divisions)
     const int r0 = z0 & ~(rz - 1), nruns = ((z1 - r0) >> (__ffs(rz) - 1)) + 1;
-    const int ncx = x1 - x0 + 1, ncol = ncx * (y1 - y0 + 1);
-    for (int c0 = 0; c0 < ncol; c0 += (int)blockDim.x) {
-      if (c0 + ((int)threadIdx.x & ~31) >= ncol) continue;  // warp-uniform
-      const int col = c0 + (int)threadIdx.x;
-      const int cy = col / ncx;
-      const int bx = x0 + (col - cy * ncx), by = y0 + cy;
-      const int gx = brick_gap(bx - c.x), gy = brick_gap(by - c.y), in_plane = gx * gx + gy * gy;
-      const bool col_live = col < ncol && in_plane < g.INF;
-      const int nxy = ((bx >> 4) - qx0) + nqx * ((by >> 4) - qy0);
-      for (int zr = 0; zr < nruns; ++zr) {
-        bool wx = false, wy = false, wz = false;
-        unsigned long long px = 0, py = 0, pz = 0;
+    const int ncx = x1 - x0 + 1, ncol = ncx * (y1 - y0 + 1), total = ncol * nruns;
+    for (int u0 = 0; u0 < total; u0 += (int)blockDim.x) {
+      const int u = u0 + (int)threadIdx.x;
+      bool wx = false, wy = false, wz = false;
+      unsigned long long px = 0, py = 0, pz = 0;
+      if (u < total) {
+        const int zr = u / ncol, col = u - zr * ncol;
+        const int cy = col / ncx;
+        const int bx = x0 + (col - cy * ncx), by = y0 + cy;
         const int zs = max(r0 + zr * rz, z0), ze = min(r0 + zr * rz + rz - 1, z1);
-        const int node = col_live ? nodes[nxy + nqx * nqy * ((zs >> 4) - qz0)] : -1;
-        if (node >= 0) {
+        const int node = nodes[((bx >> 4) - qx0) + nqx * (((by >> 4) - qy0) + nqy * ((zs >> 4) - qz0))];
+        const int gx = brick_gap(bx - c.x), gy = brick_gap(by - c.y), in_plane = gx * gx + gy * gy;
+        if (node >= 0 && in_plane < g.INF) {
           const int32_t* ch = g.child + (size_t)node * kNodeBricks;
           bool any = false;
           for (int bz = zs; bz <= ze; ++bz) {
@@ -1786,10 +1783,10 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
           }
           if (any) wz = claim_run(g, 2, bx, by, zs, node, rz, epoch, pz);
         }
-        emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
-        emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
-        emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
       }
+      emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
+      emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
+      emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
     }
   }
 }
