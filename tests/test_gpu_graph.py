@@ -99,8 +99,11 @@ def test_graph_replay_random_records_device_inputs():
         val = np.concatenate([rs.integers(0, 2, k), np.zeros(len(pick), np.int64)]).astype(np.uint8)
         for r in range(len(val)):
             occ[xyz[r, 2], xyz[r, 1], xyz[r, 0]] = val[r]
-        if f % 2:
+        if f % 3 == 1:
             g.run(torch.from_numpy(xyz).cuda(), torch.from_numpy(val).cuda())
+        elif f % 3 == 2:  # the records loaded ahead, then a bare replay
+            g.load(xyz, val)
+            g.replay()
         else:  # a producer writing the input buffers itself, then a bare replay
             n = len(val)
             with torch.cuda.stream(m.stream):
