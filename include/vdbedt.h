@@ -77,12 +77,13 @@ typedef enum {
  * A bounded grid only, with (nx-1)^2 + (ny-1)^2 + (nz-1)^2 < 2^31 - 1 so that every distance fits
  * int32, and every brick stored from creation (max_bricks and max_nodes 0 or at least the grid's):
  * about 6.2 KB per 8^3 brick (32-bit intermediates) plus 8 bytes per voxel of line scratch (nx
- * rounded up to 32) and three bitmaps of dirty lines, all allocated at creation.  The transform runs whole lines of the grid (x: nearest occupied voxel of
- * the row; y, z: lower envelope of the parabolas rooted at the line's values).  vdbedt_update
- * applies the staged records and recomputes only the lines they reach, exactly: the x rows holding
- * a flipped voxel, then the y lines on which g1 changed, then the z lines on which g2 changed (each
- * pass's output on a line depends only on its input along that line).  Not available: batches,
- * vdbedt_set_tuning, vdbedt_query_nearest and the unbounded flag. */
+ * rounded up to 32) and three bitmaps of dirty lines, all allocated at creation.  The transform
+ * runs whole lines of the grid (x: nearest occupied voxel of the row; y, z: lower envelope of the
+ * parabolas rooted at the line's values).  vdbedt_update applies the staged records and recomputes
+ * only the lines they reach, exactly: the x rows holding a flipped voxel, then the y lines on which
+ * g1 changed, then the z lines on which g2 changed (each pass's output on a line depends only on
+ * its input along that line).  Not available: batches, vdbedt_set_tuning, vdbedt_query_nearest and
+ * the unbounded flag. */
 #define VDBEDT_FLAG_UNTRUNCATED 2u
 #define VDBEDT_D_NONE 2147483647
 
