@@ -620,114 +620,73 @@ __global__ void k_apply_set_only(GridView g, const rec_t* __restrict__ rec, int6
   }
 }
 
-// Tracked ingest (incremental form): each brick of a "set" record that is not stored yet is listed
-// once for allocation (count in C_UNIQUE, cleared when the update begins).  A per-node bit
-// (`nclaim`, the amask layout) dedupes the bricks, so the scratch follows the records and the node
-// capacity, not the size of the grid.  A record whose node does not exist yet flags its node key
-// and the deferral counter; once the flagged nodes are created, a second pass (which returns at
-// once when nothing was deferred) lists those bricks.  The listed bricks are then allocated with
-// their fields at dmax^2 and their bits cleared, so `nclaim` is zero between updates.  Records of
-// stored bricks need no brick work at all.
-__device__ __forceinline__ void list_missing_brick(const GridView& g, int node, int bx, int by, int bz,
-                                                   unsigned long long* list) {
-  const int l = local_brick(bx, by, bz);
-  const uint32_t b = 1u << (l & 31);
-  if (atomicOr(&g.nclaim[(size_t)node * 128 + (l >> 5)], b) & b) return;
-  const int p = atomicAdd(&g.counters[C_UNIQUE], 1);
-  if (p < g.cap)
-    list[p] = pack_brick(bx, by, bz);
-  else
-    set_error(g, kErrOverflow);  // more new bricks than the capacity holds
-}
-
-template <bool DEFERRED, class US>
-__global__ void k_rec_missing(US us) {
+// Tracked ingest (incremental form), first kernel: each record's brick slot for the ordered
+// kernels (rslot).  A "set" record whose brick is not stored yet creates the brick's interior node
+// when it is missing (inline, as the marking kernel does) and claims the brick with a per-node bit
+// (`nclaim`, the amask layout); the claiming thread allocates the brick (slots reserved a warp at a
+// time, fields at dmax^2 written by the whole warp) and publishes its slot in the child table.
+// Records that lose the claim, or read the child table before the claimer publishes, look the
+// brick up again in the next kernel (rslot -2).  The claimer's record keeps -3 - slot, so that the
+// next kernel, when no record of this ingest tests the bit any more, clears it: `nclaim` is zero
+// between updates.  Records of stored bricks need no brick work at all.
+template <class US>
+__global__ void k_rec_slots(US us) {
   pdl_enter();
   const UpdArgs A = us.get();
   const GridView& g = A.g;
-  if (DEFERRED && g.counters[C_DEFERRED] == 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t n = rec_count(A.n, A.n_dev);
   const rec_t* __restrict__ rec = A.rec;
-  GRID_STRIDE(i, n) {
-    bool zero = false, bad = false;
+  GRID_STRIDE(i, n) {  // block-uniform rounds: the warp-wide steps below see all 32 lanes
+    bool zero = false, bad = false, claim = false;
+    int rs = -1;  // the record's brick slot (-2: looked up once allocated)
+    int node = -1, bx = 0, by = 0, bz = 0;
     if (i < n) {
       int4 r = unpack_rec(rec[i]);
-      int rs = -1;  // the record's brick slot, for the ordered kernels (-2: once allocated)
       if (!rec_valid(g, r)) {
         bad = true;
       } else if (r.w == 1) {
-        const int bx = r.x >> 3, by = r.y >> 3, bz = r.z >> 3;
-        const unsigned long long nk = node_key_of(g, bx, by, bz);
-        // an unbounded grid has no per-key flags: its nodes are created here, by the records
-        const int node = A.nflag ? find_node(g, nk) : get_or_create_node(g, nk);
+        bx = r.x >> 3;
+        by = r.y >> 3;
+        bz = r.z >> 3;
+        node = get_or_create_node(g, node_key_of(g, bx, by, bz));
         rs = -2;
         if (node >= 0) {
-          const int sl = g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)];
-          if (sl < 0)
-            list_missing_brick(g, node, bx, by, bz, A.list);
-          else
+          const int l = local_brick(bx, by, bz);
+          const int sl = g.child[(size_t)node * kNodeBricks + l];
+          if (sl >= 0) {
             rs = sl;
-        } else if (!DEFERRED && A.nflag && !A.nflag[nk]) {
-          A.nflag[nk] = 1;
-          atomicOr(&g.counters[C_DEFERRED], 1);
+          } else {
+            const uint32_t b = 1u << (l & 31);
+            claim = (atomicOr(&g.nclaim[(size_t)node * 128 + (l >> 5)], b) & b) == 0u;
+          }
         }
       } else {
         zero = true;
         // a cleared voxel matters only in a stored brick: one stored now, or one a "set" record of
-        // the same ingest adds (looked up again once those are allocated)
-        if (!DEFERRED) {
-          rs = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
-          if (rs < 0) rs = -2;
-        }
-      }
-      if (!DEFERRED && A.rslot) A.rslot[i] = rs;
-    }
-    if (!DEFERRED) {
-      if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
-      if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
-    }
-  }
-}
-
-// Nodes flagged by the tracked ingest (node keys of "set" records whose node did not exist).
-template <class US>
-__global__ void k_upd_nodes(US us) {
-  pdl_enter();
-  const UpdArgs A = us.get();
-  if (A.g.counters[C_DEFERRED] == 0) return;
-  create_flagged_nodes(A.g, A.nflag, (int64_t)A.g.NX * A.g.NY * A.g.NZ);
-}
-
-template <class US>
-__global__ void k_alloc_listed(US us) {
-  pdl_enter();
-  const UpdArgs A = us.get();
-  const GridView& g = A.g;
-  const unsigned long long* __restrict__ list = A.list;
-  const int64_t cnt = min((int64_t)g.counters[C_UNIQUE], min(A.n, (int64_t)g.cap));
-  GRID_STRIDE(j, cnt) {
-    int node = -1, bx = 0, by = 0, bz = 0;
-    int* e = nullptr;
-    bool need = false;
-    if (j < cnt) {
-      unpack_brick(list[j], bx, by, bz);
-      node = find_node(g, node_key_of(g, bx, by, bz));
-      if (node >= 0) {
-        const int l = local_brick(bx, by, bz);
-        atomicAnd(&g.nclaim[(size_t)node * 128 + (l >> 5)], ~(1u << (l & 31)));
-        e = &g.child[(size_t)node * kNodeBricks + l];
-        need = *e == kNoSlot;
+        // the same ingest adds (looked up again once it is published)
+        rs = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
+        if (rs < 0) rs = -2;
       }
     }
-    int total = 0;
-    const int slot = block_agg_add(&g.counters[C_NBRICKS], need, &total);
-    const bool ok = need && slot < g.cap;
-    if (need && !ok) set_error(g, kErrOverflow);
+    const int slot = warp_reserve(&g.counters[C_NBRICKS], claim);
+    const bool ok = claim && slot < g.cap;
+    if (claim && !ok) {
+      set_error(g, kErrOverflow);  // more bricks than the capacity holds: give the claim back
+      const int l = local_brick(bx, by, bz);
+      atomicAnd(&g.nclaim[(size_t)node * 128 + (l >> 5)], ~(1u << (l & 31)));
+    }
     if (ok) init_brick(g, slot, node, bx, by, bz, false);
     init_fields_ballot(g, ok, slot);
-    if (ok) *e = slot;
-    if (threadIdx.x == 0 && total) atomicAdd(&g.counters[C_NEW_BRICKS], total);
+    if (ok) {
+      g.child[(size_t)node * kNodeBricks + local_brick(bx, by, bz)] = slot;
+      rs = -3 - slot;
+    }
+    const unsigned made = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0 && made) atomicAdd(&g.counters[C_NEW_BRICKS], __popc(made));
+    if (i < n) A.rslot[i] = rs;
+    if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
   }
 }
 
@@ -832,7 +791,14 @@ __global__ void k_upd_rec_last(US us) {
     if (i < n) {
       const rec_t packed = A.rec[i];
       int s = A.rslot[i];
-      if (s == -2) {
+      if (s <= -3) {
+        // the record that allocated its brick: the claim bit goes back to zero
+        s = -3 - s;
+        const int4 c = g.bcoord[s];
+        const int l = local_brick(c.x, c.y, c.z);
+        atomicAnd(&g.nclaim[(size_t)c.w * 128 + (l >> 5)], ~(1u << (l & 31)));
+        A.rslot[i] = s;
+      } else if (s == -2) {
         const int4 r = unpack_rec(packed);
         s = find_brick(g, r.x >> 3, r.y >> 3, r.z >> 3);
         A.rslot[i] = s;
@@ -1835,18 +1801,15 @@ __global__ void __launch_bounds__(256) k_mark_runs(US us, int rx, int ry, int rz
 
 // The incremental update's kernels for one grid or all grids of a batch (k = gridDim.y).
 template <class US>
-cudaError_t update_ingest_kernels(US us, int k, int64_t n, int64_t nkeys, int64_t cap, cudaStream_t st) {
+cudaError_t update_ingest_kernels(US us, int k, int64_t n, cudaStream_t st) {
   const int div = k > 1 ? k : 1;
   auto bx = [&](int64_t work, int hi) {
     int64_t b = (work + kT - 1) / kT;
     const int64_t lim = k > 1 ? (hi / div > 16 ? hi / div : 16) : hi;
     return (unsigned)(b < 1 ? 1 : (b > lim ? lim : b));
   };
-  const dim3 gr(bx(n, 152 * 16), k), gk(bx(nkeys, 152 * 16), k), gl(bx(n < cap ? n : cap, 152 * 16), k);
-  VDB_LAUNCH_PDL((k_rec_missing<false, US>), gr, kT, 0, st, us);
-  VDB_LAUNCH_PDL(k_upd_nodes<US>, gk, kT, 0, st, us);
-  VDB_LAUNCH_PDL((k_rec_missing<true, US>), gr, kT, 0, st, us);
-  VDB_LAUNCH_PDL(k_alloc_listed<US>, gl, kT, 0, st, us);
+  const dim3 gr(bx(n, 152 * 16), k);
+  VDB_LAUNCH_PDL(k_rec_slots<US>, gr, kT, 0, st, us);
   VDB_LAUNCH_PDL(k_upd_rec_last<US>, gr, kT, 0, st, us);
   VDB_LAUNCH_PDL(k_upd_apply_last<US>, gr, kT, 0, st, us);
   return cudaGetLastError();
@@ -2006,7 +1969,7 @@ static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, in
   a.rslot = rslot;
   cudaError_t e = prepare_update_args(g, vl, miss, a, st);
   if (e != cudaSuccess) return e;
-  return update_ingest_kernels(UpdOne{a}, 1, n, g.unbounded ? 1 : (int64_t)g.NX * g.NY * g.NZ, g.cap, st);
+  return update_ingest_kernels(UpdOne{a}, 1, n, st);
 }
 
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
@@ -2251,7 +2214,7 @@ cudaError_t launch_update_batch_ingest(const UpdArgs* d_args, const BatchUpdShap
   VDB_LAUNCH(k_begin_batch_update, dim3(1, s.k), 32, 0, st, d_args, counts);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return update_ingest_kernels(UpdBatch{d_args}, s.k, s.max_n, s.max_nkeys, s.max_cap, st);
+  return update_ingest_kernels(UpdBatch{d_args}, s.k, s.max_n, st);
 }
 
 cudaError_t launch_update_batch_mark(const UpdArgs* d_args, const BatchUpdShape& s, const Tuning& t, const Items& it,
