@@ -58,7 +58,6 @@ struct vdbedt_map {
   int32_t* h_pinned = nullptr;  // pinned host words for small readbacks
   Scratch scr;
   Scratch vlast;  // per-voxel last-record table of the ordered ingest
-  Scratch miss;   // flags and missing-brick list of the tracked (incremental) ingest
   Scratch io;  // host-input staging on the device
   Scratch uts;  // line stacks of the untruncated transform
   Items items{};
@@ -239,8 +238,7 @@ vdbedt_status do_global(vdbedt_map* h) {
   if (h->stage_n > 0) {
     CK(h,
        launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), false, h->changed, h->stage_slot, h->scr,
-                             h->vlast, h->miss,
-                             h->st),
+                             h->vlast, h->st),
        "ingest");
     clear_stage(h);
   }
@@ -475,7 +473,6 @@ void destroy_impl(vdbedt_map* h) {
   if (h->stage_slot) cudaFree(h->stage_slot);
   if (h->scr.buf) cudaFree(h->scr.buf);
   if (h->vlast.buf) cudaFree(h->vlast.buf);
-  if (h->miss.buf) cudaFree(h->miss.buf);
   if (h->io.buf) cudaFree(h->io.buf);
   if (h->uts.buf) cudaFree(h->uts.buf);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -625,7 +622,7 @@ vdbedt_status vdbedt_set_occupancy_counted(vdbedt_handle h, const int32_t* xyz, 
   DeviceGuard guard(h->device);
   s = ensure_stage(h, n_max);
   if (s) return s;
-  CK(h, reserve_ingest(h->g, n_max, h->scr, h->vlast, h->miss, h->st), "ingest scratch");
+  CK(h, reserve_ingest(h->g, n_max, h->scr, h->vlast, h->st), "ingest scratch");
   CK(h, launch_pack_records(xyz, occ, n_max, n_dev, h->d_count, h->g.nx, h->g.ny, h->g.nz, h->g.off, h->stage, nullptr,
                               h->g.counters, h->st),
      "pack");
@@ -694,7 +691,7 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     if (h->stage_n > 0) {
       CK(h,
          launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->stage_slot, h->scr,
-                               h->vlast, h->miss, h->st),
+                               h->vlast, h->st),
          "ingest");
       clear_stage(h);
     }
@@ -715,8 +712,7 @@ vdbedt_status vdbedt_update(vdbedt_handle h, vdbedt_update_stats* stats) {
     if (h->stage_n > 0) {
       CK(h,
          launch_ingest_records(h->g, h->stage, h->stage_n, stage_count(h), true, h->changed, h->stage_slot, h->scr,
-                               h->vlast,
-                               h->miss, h->st),
+                               h->vlast, h->st),
          "ingest");
       clear_stage(h);
     }
@@ -935,7 +931,7 @@ vdbedt_status vdbedt_get_info(vdbedt_handle h, vdbedt_info* info) {
   info->capacity_bricks = h->g.cap;
   info->nodes = h->h_pinned[C_NNODES];
   info->device_bytes =
-      (int64_t)(h->device_bytes + h->scr.bytes + h->vlast.bytes + h->miss.bytes + h->io.bytes +
+      (int64_t)(h->device_bytes + h->scr.bytes + h->vlast.bytes + h->io.bytes +
                 (sizeof(rec_t) + sizeof(int32_t)) * h->stage_cap);
   info->R = h->g.R;
   info->error_bits = h->h_pinned[C_ERR];
@@ -1090,8 +1086,7 @@ vdbedt_status batch_global(vdbedt_batch* b) {
     BCK(b, cudaMemsetAsync(m->g.counters + C_HAS_ZERO, 0, sizeof(int32_t), b->st), "memset");
     BCK(b,
         launch_ingest_records(m->g, m->stage, m->stage_n, stage_count(m), false, nullptr, m->stage_slot, m->scr,
-                              m->vlast, m->miss,
-                              b->st),
+                              m->vlast, b->st),
         "ingest");
     clear_stage(m);
   }
@@ -1145,7 +1140,7 @@ vdbedt_status batch_update(vdbedt_batch* b, vdbedt_update_stats* stats) {
     // The grids' arguments in device memory stay fixed while staging does not reallocate (every
     // grid reads its record count from its device count word), so a captured update replays with
     // the same arguments; they are uploaded again only when they change, outside a capture.
-    BatchUpdShape shape{b->k, 0, 0, 0, 0, g0.R, half_path(g0)};
+    BatchUpdShape shape{b->k, 0, 0, g0.R, half_path(g0)};
     BatchCounts counts{};
     std::vector<UpdArgs> args((size_t)b->k);
     for (int i = 0; i < b->k; ++i) {
@@ -1157,11 +1152,9 @@ vdbedt_status batch_update(vdbedt_batch* b, vdbedt_update_stats* stats) {
       a.n_dev = m->d_count;
       a.changed = m->changed;
       a.rslot = m->stage_slot;
-      BCK(b, prepare_update_args(m->g, m->vlast, m->miss, a, b->st), "update scratch");
+      BCK(b, prepare_update_args(m->g, m->vlast, a, b->st), "update scratch");
       counts.c[i] = m->stage_counted ? -1 : (int32_t)m->stage_n;  // -1: the counted staging wrote it
       shape.max_n = std::max<int64_t>(shape.max_n, m->stage_cap);
-      shape.max_nkeys = std::max<int64_t>(shape.max_nkeys, (int64_t)m->g.NX * m->g.NY * m->g.NZ);
-      shape.max_cap = std::max<int64_t>(shape.max_cap, m->g.cap);
       shape.max_node_cap = std::max<int64_t>(shape.max_node_cap, m->g.node_cap);
     }
     if (memcmp(args.data(), b->h_upd, sizeof(UpdArgs) * (size_t)b->k) != 0) {

@@ -166,7 +166,6 @@ __global__ void k_begin_update(US us) {
     g.counters[C_NEW_BRICKS] = 0;
     g.counters[C_UNIQUE] = 0;
     g.counters[C_HAS_ZERO] = 0;
-    g.counters[C_DEFERRED] = 0;
     g.counters[C_XB] = 0;
     g.counters[C_YB] = 0;
     g.counters[C_ZB] = 0;
@@ -192,7 +191,6 @@ __global__ void k_begin_batch_update(const UpdArgs* __restrict__ args, BatchCoun
     g.counters[C_NEW_BRICKS] = 0;
     g.counters[C_UNIQUE] = 0;
     g.counters[C_HAS_ZERO] = 0;
-    g.counters[C_DEFERRED] = 0;
     g.counters[C_XB] = 0;
     g.counters[C_YB] = 0;
     g.counters[C_ZB] = 0;
@@ -1912,26 +1910,9 @@ static cudaError_t ensure_vlast(const GridView& g, Scratch& vl, cudaStream_t st)
   return cudaMemsetAsync(vl.buf, 0xFF, want, st);
 }
 
-// The tracked ingest's scratch: node-key flags (zero between updates), the list of missing bricks.
-// node-key flags (none for an unbounded grid), then the missing-brick list
-static size_t tracked_flag_bytes(const GridView& g) {
-  return g.unbounded ? 0 : align_up((size_t)g.NX * g.NY * g.NZ * 4);
-}
-static size_t tracked_bytes(const GridView& g) { return tracked_flag_bytes(g) + align_up((size_t)g.cap * 8); }
-
-static cudaError_t ensure_tracked(const GridView& g, Scratch& miss, cudaStream_t st) {
-  const size_t want = tracked_bytes(g);
-  if (miss.bytes >= want) return cudaSuccess;
-  cudaError_t e = ensure_scratch(miss, want);
-  if (e != cudaSuccess) return e;
-  return cudaMemsetAsync(miss.buf, 0, miss.bytes, st);
-}
-
-cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st) {
+cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e = g.unbounded ? cudaSuccess : ensure_scratch(scr, ingest_scratch_bytes(g, n, false));
-  if (e != cudaSuccess) return e;
-  e = ensure_tracked(g, miss, st);
   if (e != cudaSuccess) return e;
   return ensure_vlast(g, vl, st);
 }
@@ -1943,14 +1924,9 @@ cudaError_t launch_begin_update(const GridView& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t prepare_update_args(const GridView& g, Scratch& vl, Scratch& miss, UpdArgs& a, cudaStream_t st) {
-  cudaError_t e = ensure_tracked(g, miss, st);
+cudaError_t prepare_update_args(const GridView& g, Scratch& vl, UpdArgs& a, cudaStream_t st) {
+  cudaError_t e = ensure_vlast(g, vl, st);
   if (e != cudaSuccess) return e;
-  e = ensure_vlast(g, vl, st);
-  if (e != cudaSuccess) return e;
-  char* p = (char*)miss.buf;
-  a.nflag = g.unbounded ? nullptr : (int32_t*)p;
-  a.list = (unsigned long long*)(p + tracked_flag_bytes(g));
   a.vlast = (int32_t*)vl.buf;
   return cudaSuccess;
 }
@@ -1958,8 +1934,7 @@ cudaError_t prepare_update_args(const GridView& g, Scratch& vl, Scratch& miss, U
 // The tracked ingest: with `track` (an incremental update) each flipped voxel's brick joins the
 // changed list once; unbounded grids take this path for the global form too (no brick-key sort).
 static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev,
-                                         int32_t* changed, int32_t* rslot, Scratch& vl, Scratch& miss,
-                                         cudaStream_t st) {
+                                         int32_t* changed, int32_t* rslot, Scratch& vl, cudaStream_t st) {
   UpdArgs a{};
   a.g = g;
   a.rec = rec;
@@ -1967,16 +1942,15 @@ static cudaError_t launch_ingest_tracked(const GridView& g, const rec_t* rec, in
   a.n_dev = n_dev;
   a.changed = changed;
   a.rslot = rslot;
-  cudaError_t e = prepare_update_args(g, vl, miss, a, st);
+  cudaError_t e = prepare_update_args(g, vl, a, st);
   if (e != cudaSuccess) return e;
   return update_ingest_kernels(UpdOne{a}, 1, n, st);
 }
 
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
-                                  int32_t* changed, int32_t* rslot, Scratch& scr, Scratch& vl, Scratch& miss,
-                                  cudaStream_t st) {
+                                  int32_t* changed, int32_t* rslot, Scratch& scr, Scratch& vl, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  if (track || g.unbounded) return launch_ingest_tracked(g, rec, n, n_dev, changed, rslot, vl, miss, st);
+  if (track || g.unbounded) return launch_ingest_tracked(g, rec, n, n_dev, changed, rslot, vl, st);
   const int64_t nbr_all = (int64_t)g.BX * g.BY * g.BZ;
   const bool counting = n >= nbr_all / 4;
   // the dense mask is indexed by a 32-bit word number (8 words per brick)

@@ -63,7 +63,7 @@ enum Counter : int {
   C_OBST = 12,
   C_NB_START = 13,  // stored bricks when the running update began (its global-vs-incremental choice)
   C_EPOCH = 14,  // incremental update epoch (run and brick dedupe marks)
-  C_DEFERRED = 15,  // the tracked ingest met "set" records whose node did not exist yet
+  C_SPARE = 15,  // unused
   C_XB = 16,  // stored bricks in the update's dirty runs per axis (x, y, z: three consecutive words)
   C_YB = 17,
   C_ZB = 18,
@@ -370,23 +370,20 @@ struct UpdArgs {
   const int32_t* n_dev;      // device-side count (counted staging) or null
   int32_t* changed;          // bricks holding a flipped voxel (cap entries)
   int32_t* vlast;            // per-voxel last-record table (cap * 512 words, all -1 between ingests)
-  int32_t* nflag;            // node-key flags of the tracked ingest (zero between updates)
-  unsigned long long* list;  // bricks the tracked ingest allocates (cap entries)
-  int32_t* rslot;            // per staged record: its brick's slot (-1: none, -2: looked up once allocated)
+  int32_t* rslot;            // per staged record: its brick's slot (-1: none, -2: looked up once allocated,
+                             // -3 - slot: the brick this record allocated)
 };
 cudaError_t ensure_scratch(Scratch& s, size_t bytes);
 
 cudaError_t launch_reset(const GridView& g, cudaStream_t st);
 // n records at rec; with n_dev (nullable) only the first *n_dev of them (clamped to [0, n]).
 // scr: sort / scan scratch of the global form; vl: the per-voxel last-record table (allocated and
-// set to -1 on first use, cap * 512 words); miss: the tracked form's flag and list arrays
-// (allocated zeroed on first use and kept zero); rslot: one word per record (n entries) for the
-// tracked form's brick slots.
+// set to -1 on first use, cap * 512 words); rslot: one word per record (n entries) for the tracked
+// form's brick slots.
 cudaError_t launch_ingest_records(const GridView& g, const rec_t* rec, int64_t n, const int32_t* n_dev, bool track,
-                                  int32_t* changed, int32_t* rslot, Scratch& scr, Scratch& vl, Scratch& miss,
-                                  cudaStream_t st);
-// size the ingest scratch, the tracked arrays and the last-record table for up to n records
-cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, Scratch& miss, cudaStream_t st);
+                                  int32_t* changed, int32_t* rslot, Scratch& scr, Scratch& vl, cudaStream_t st);
+// size the ingest scratch and the last-record table for up to n records
+cudaError_t reserve_ingest(const GridView& g, int64_t n, Scratch& scr, Scratch& vl, cudaStream_t st);
 // clear the per-update counters and advance the device-side update epoch
 cudaError_t launch_begin_update(const GridView& g, cudaStream_t st);
 // dense grid -> bricks (scratch: dense_scratch_bytes(g))
@@ -406,15 +403,14 @@ struct Fork {
 // Records fork.join on the side stream; the caller waits on it before the passes.
 cudaError_t launch_incremental_mark(const GridView& g, const Tuning& t, const int32_t* changed, const Items& it,
                                     const Fork& fk, cudaStream_t st);
-// The tracked scratch of one grid (node-key flags, missing-brick list) and its last-record table,
-// allocated on first use; fills a's vlast / nflag / list.
-cudaError_t prepare_update_args(const GridView& g, Scratch& vl, Scratch& miss, UpdArgs& a, cudaStream_t st);
+// The last-record table of one grid, allocated on first use; fills a's vlast.
+cudaError_t prepare_update_args(const GridView& g, Scratch& vl, UpdArgs& a, cudaStream_t st);
 // Batched incremental update of k grids (d_args: their arguments in device memory): the same
 // kernels as one grid's update, each launched once for all grids.  max_*: the largest staged
-// count, node-key count, brick and node capacity over the grids (launch shapes).
+// count and node capacity over the grids (launch shapes).
 struct BatchUpdShape {
   int k;
-  int64_t max_n, max_nkeys, max_cap, max_node_cap;
+  int64_t max_n, max_node_cap;
   int R;      // common to the batch
   bool half;  // the windowed form (work lists carry slot lists)
 };
