@@ -172,3 +172,21 @@ def test_graph_replay_on_huge_grid():
     a.synchronize()
     a.close()
     b.close()
+
+
+def test_brick_capacity_overflow_in_update_reported():
+    """An update whose new obstacle bricks exceed the brick capacity: the bricks that fit are
+    stored, the rest are refused, and the next synchronising call reports EOVERFLOW."""
+    import paper_2105_04419_gb300 as V
+    m = V.Map(256, 256, 64, 2, max_bricks=30)  # R = 1: an obstacle brick's cube is 27 bricks
+    m.set_occupancy(np.array([[100, 100, 30]], np.int32), np.ones(1, np.uint8))
+    m.global_()
+    m.synchronize()
+    assert m.info()["allocated_bricks"] == 27
+    far = np.array([[8 + 40 * k, 8, 8] for k in range(5)], np.int32)  # five new bricks, far apart
+    m.set_occupancy(far, np.ones(len(far), np.uint8))
+    m.update()
+    with pytest.raises(V.VdbedtError) as e:
+        m.synchronize()
+    assert e.value.code == "EOVERFLOW"
+    m.close()
