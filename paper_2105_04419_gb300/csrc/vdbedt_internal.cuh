@@ -95,7 +95,7 @@ struct GridView {
   int32_t* child;     // [node_cap * 4096]
   uint32_t* amask;    // [node_cap * 128] compute-set bits: bit l = bx + 16 by + 256 bz (local)
   uint32_t* mwork;    // [node_cap * 384] obstacle bits and two dilation stages, same layout
-  uint32_t* nclaim;   // [node_cap * 128] bricks listed for allocation by the running ingest (amask layout)
+  uint32_t* nclaim;   // [node_cap * 128] bricks claimed for allocation by the running ingest (amask layout)
   long long* node_key;  // [node_cap]
   int32_t* mark;      // [node_cap * 3 * 1024] epoch of the last time each run along axis a was queued
   unsigned long long* occ;  // [cap * 8]
