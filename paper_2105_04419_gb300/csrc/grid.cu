@@ -1695,7 +1695,7 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
     __syncthreads();
     if (obst) {
       // dilation: a row's x extent is split at node boundaries (the same segments on every lane);
-      // the rounds are block-uniform so that the fresh list is appended a warp at a time
+      // the rounds are block-uniform so that new bricks' slots are reserved a warp at a time
       const int nyr = y1 - y0 + 1, rows = nyr * (z1 - z0 + 1);
       for (int rb = 0; rb < rows; rb += (int)blockDim.x) {
         const int r = rb + (int)threadIdx.x;
