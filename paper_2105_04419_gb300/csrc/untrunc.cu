@@ -3,8 +3,8 @@
 // dmax = infinity runs, Table II).  With no truncation every voxel is in reach of every obstacle,
 // so every brick is stored, brick (bx, by, bz) at slot bx + BX (by + BY bz), and the transform runs
 // over whole lines of the grid, one axis after the other (Eq. 1's minimum taken per axis):
-//   x: per row, the distance to the nearest occupied voxel on either side (a forward and a
-//      backward sweep), g1 = dx^2;
+//   x: per row, the distance to the nearest occupied voxel on either side (a forward sweep that
+//      keeps one carry per brick, and a backward sweep that writes g1 = dx^2);
 //   y, z: per line, the lower envelope of the parabolas f(i) + (t - i)^2 rooted at the line's
 //      finite values (g1, then g2): built on a stack in one sweep, read back in a second.  Two
 //      parabolas are compared through their intersection with the denominators multiplied out,
@@ -112,15 +112,17 @@ __global__ void k_ut_dense(GridView g, const uint8_t* __restrict__ grid) {
   }
 }
 
-// x pass: a thread per voxel row (64 rows of a brick line on consecutive threads).  The forward
-// sweep stores the distance to the last occupied voxel at or before x (-1: none); the backward
-// sweep combines it with the distance to the next one and stores g1 = d^2 (kNone: empty row).
+// x pass: a thread per voxel row (the 64 rows of a brick line on consecutive threads).  A forward
+// sweep over the row's occupancy bytes stores, per brick, the last occupied voxel before the brick
+// (-1: none) in `carry` (entry bx * rows + t, so that a warp's 32 rows share a 128-byte line); the
+// backward sweep then knows, inside each brick, the nearest occupied voxel on the left (the
+// brick's own bits at or below the voxel, else the carry) and on the right (followed as it goes),
+// and writes g1 = d^2 (kNone: empty row) once per voxel.
 // INCR (an update): only the rows whose dirty bit is set, each warp taking and clearing its word;
-// the forward sweep goes to `fwd` (row stride 8 BX), and the backward sweep compares each g1 with
-// the stored one, writes the bricks' row pieces that changed and sets the y-line bit (x, z) of
-// every changed voxel, a 32-bit word at a time.
+// the backward sweep compares each g1 with the stored one, writes the bricks' row pieces that
+// changed and sets the y-line bit (x, z) of every changed voxel, a 32-bit word at a time.
 template <bool INCR>
-__global__ void k_ut_x(GridView g, int32_t* __restrict__ fwd) {
+__global__ void k_ut_x(GridView g, int32_t* __restrict__ carry) {
   int32_t* __restrict__ g1 = reinterpret_cast<int32_t*>(g.g1);
   const int64_t nrows = (int64_t)g.BY * g.BZ * 64;  // a multiple of 64: every warp is whole
   const int lane = threadIdx.x & 31;
@@ -144,21 +146,11 @@ __global__ void k_ut_x(GridView g, int32_t* __restrict__ fwd) {
     if (y >= g.ny || z >= g.nz) continue;
     const int shift = 8 * (y & 7);
     const size_t row = (size_t)(8 * (y & 7) + 64 * (z & 7));
-    int32_t* fw = INCR ? fwd + ((size_t)z * g.ny + y) * (size_t)(8 * g.BX) : nullptr;
     int last = -1;
     for (int bx = 0; bx < g.BX; ++bx) {
-      const int s = ut_slot(g, bx, by, bz);
-      const uint32_t byte = (uint32_t)(g.occ[(size_t)s * 8 + (z & 7)] >> shift) & 0xFFu;
-      int v[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int x = 8 * bx + i;
-        if ((byte >> i) & 1u) last = x;
-        v[i] = last < 0 ? -1 : x - last;
-      }
-      int4* dst = reinterpret_cast<int4*>(INCR ? fw + 8 * bx : g1 + (size_t)s * kBrickVox + row);
-      dst[0] = make_int4(v[0], v[1], v[2], v[3]);
-      dst[1] = make_int4(v[4], v[5], v[6], v[7]);
+      carry[(size_t)bx * nrows + t] = last;
+      const uint32_t byte = (uint32_t)(g.occ[(size_t)ut_slot(g, bx, by, bz) * 8 + (z & 7)] >> shift) & 0xFFu;
+      if (byte) last = 8 * bx + 31 - __clz(byte);
     }
     int next = -1;
     uint32_t* ybits = INCR ? g.ut_bits + ut_row_words(g) + (size_t)(ut_nxp(g) >> 5) * z : nullptr;
@@ -166,18 +158,18 @@ __global__ void k_ut_x(GridView g, int32_t* __restrict__ fwd) {
     for (int bx = g.BX - 1; bx >= 0; --bx) {
       const int s = ut_slot(g, bx, by, bz);
       const uint32_t byte = (uint32_t)(g.occ[(size_t)s * 8 + (z & 7)] >> shift) & 0xFFu;
+      const int left_in = carry[(size_t)bx * nrows + t];
       int4* dst = reinterpret_cast<int4*>(g1 + (size_t)s * kBrickVox + row);
-      const int4* src = reinterpret_cast<const int4*>(INCR ? fw + 8 * bx : g1 + (size_t)s * kBrickVox + row);
-      const int4 a = src[0], b = src[1];
-      int v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+      int v[8];
 #pragma unroll
       for (int i = 7; i >= 0; --i) {
         const int x = 8 * bx + i;
-        if (x >= g.nx) continue;  // padding of the last brick: never read
         if ((byte >> i) & 1u) next = x;
-        int d = v[i];
+        const uint32_t below = byte & ((2u << i) - 1u);  // occupied voxels of the brick at or left of x
+        const int lpos = below ? 8 * bx + 31 - __clz(below) : left_in;
+        int d = lpos >= 0 ? x - lpos : -1;
         if (next >= 0 && (d < 0 || next - x < d)) d = next - x;
-        v[i] = d < 0 ? kNone : d * d;
+        v[i] = (d < 0 || x >= g.nx) ? kNone : d * d;  // the last brick's padding holds kNone
       }
       if (INCR) {
         const int4 oa = dst[0], ob = dst[1];
@@ -390,10 +382,10 @@ cudaError_t launch_ut_dense(const GridView& g, const uint8_t* grid, cudaStream_t
   return cudaGetLastError();
 }
 
-// The line stacks (8 bytes per voxel of lines padded along x to a multiple of 32), or the x rows
-// of an update's forward sweep (4 bytes per voxel of rows padded to 8 BX), whichever is larger.
+// The line stacks (8 bytes per voxel of lines padded along x to a multiple of 32), or the x pass's
+// carries (4 bytes per row and brick), whichever is larger.
 size_t ut_scratch_bytes(const GridView& g) {
-  return std::max((size_t)ut_nxp(g) * g.ny * g.nz * sizeof(int2), (size_t)8 * g.BX * g.ny * g.nz * sizeof(int32_t));
+  return std::max((size_t)ut_nxp(g) * g.ny * g.nz * sizeof(int2), (size_t)g.BX * g.BY * g.BZ * 64 * sizeof(int32_t));
 }
 
 cudaError_t launch_ut_pass(const GridView& g, int axis, void* scratch, cudaStream_t st) {
@@ -401,7 +393,7 @@ cudaError_t launch_ut_pass(const GridView& g, int axis, void* scratch, cudaStrea
   int32_t* g2 = reinterpret_cast<int32_t*>(g.g2);
   int2* stack = static_cast<int2*>(scratch);
   if (axis == 0) {
-    VDB_LAUNCH(k_ut_x<false>, ut_blocks((int64_t)g.BY * g.BZ * 64), kUT, 0, st, g, nullptr);
+    VDB_LAUNCH(k_ut_x<false>, ut_blocks((int64_t)g.BY * g.BZ * 64), kUT, 0, st, g, static_cast<int32_t*>(scratch));
   } else if (axis == 1) {
     VDB_LAUNCH(k_ut_env<1>, ut_blocks((int64_t)g.nx * g.nz), kUT, 0, st, g, g1, g2, stack);
   } else {
