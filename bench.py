@@ -514,12 +514,30 @@ def bench_batched(V, torch, stream, flush, autotuned=True, steps=5, warmup=3):
     b.set_profiling(False)
     same = True
     active = 0
+    allocated = 0
     for i in range(k):
         a = b.maps[i].export_dense(on_device=True)
         c = singles[i].export_dense(on_device=True)
         same &= bool(torch.equal(a, c))
-        active += b.maps[i].info()["finite_bricks"] * 512
+        inf_i = b.maps[i].info()
+        active += inf_i["finite_bricks"] * 512
+        allocated += inf_i["allocated_bricks"]
         del a, c
+    # bytes of the step: the unfused three-pass model (21 B per active voxel), and the stored widths
+    # (dense uint8 grids in; per allocated brick 1,088 B x, 2,048 B y, 3,072 B z); the passes alone
+    # against their phase times
+    peak, peak_src = peaks()
+    stored = voxels + 6208 * allocated
+    pass_bytes = {"x": 1088 * allocated, "y_and_z": 5120 * allocated}
+    roof = {"model_21B": {"bytes": 21 * active, "achieved": 21 * active / (batch_ms * 1e-3) / 1e9,
+                          "frac": 21 * active / (batch_ms * 1e-3) / 1e9 / peak},
+            "stored_widths": {"bytes": stored, "achieved": stored / (batch_ms * 1e-3) / 1e9,
+                              "frac": stored / (batch_ms * 1e-3) / 1e9 / peak},
+            "passes_stored_widths": {
+                key: {"bytes": v, "achieved": v / (ph * 1e-3) / 1e9, "frac": v / (ph * 1e-3) / 1e9 / peak}
+                for key, v, ph in (("x", pass_bytes["x"], phases["x_ms"]),
+                                   ("y_and_z", pass_bytes["y_and_z"], phases["z_ms"]))},
+            "allocated_bricks": allocated, "unit": "GB/s", "peak": peak, "peak_source": peak_src}
     upd = bench_batched_update(V, torch, b, singles, stream, flush, dims)
     for m in singles:
         m.close()
@@ -535,7 +553,7 @@ def bench_batched(V, torch, stream, flush, autotuned=True, steps=5, warmup=3):
             "batch_phases_ms": {"reset_and_dense_ingest": dense_ms, "activation": phases["activation_ms"], "items": phases["items_ms"],
                                 "x": phases["x_ms"], "y_and_z": phases["z_ms"]},
             "batch_equals_single_handles": same, "l2": "flushed between timed steps (untimed)",
-            "tuning": {k: v for k, v in tuning.items() if k != "key"}}
+            "roofline": roof, "tuning": {k: v for k, v in tuning.items() if k != "key"}}
 
 
 def bench_batched_update(V, torch, b, singles, stream, flush, dims, records=2000, frames=8, warm=3, seed=13):
