@@ -19,7 +19,8 @@ def _apply(occ, xyz, val):
 
 
 @pytest.mark.parametrize("seed,shape_xyz,dmax", [(1, (40, 36, 28), 7), (2, (70, 20, 33), 12), (3, (17, 64, 50), 24),
-                                                 (4, (33, 33, 33), 3), (5, (29, 41, 23), None)])
+                                                 (4, (33, 33, 33), 3), (5, (29, 41, 23), None),
+                                                 (6, (1, 37, 9), None), (7, (45, 1, 40), None)])
 def test_random_operation_sequences(seed, shape_xyz, dmax):
     import torch
 
