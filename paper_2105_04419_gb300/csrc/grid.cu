@@ -487,8 +487,9 @@ __global__ void k_flag_key_nodes(GridView g, const uint32_t* __restrict__ uniq, 
   }
 }
 
-// Compaction of the flagged bricks, one atomic per warp for the list positions (a warp's bricks
-// stay in key order, warps follow in completion order), with the flags of their node keys:
+// Compaction of the flagged bricks, one atomic per block for the list positions (a block's bricks
+// stay in key order, blocks follow in completion order; one counter word takes about a thousand
+// atomics instead of one per warp holding a flagged brick), with the flags of their node keys:
 // consecutive bricks mostly share a node, so only the first flagged lane of each run of one node
 // key in the warp sets it (without reading it first).
 __global__ void k_compact_flag_index(GridView g, const int32_t* __restrict__ flag, int64_t n,
@@ -503,11 +504,9 @@ __global__ void k_compact_flag_index(GridView g, const int32_t* __restrict__ fla
                             (int)(rest / (uint32_t)g.BY));
     }
     const unsigned set = __ballot_sync(0xffffffffu, nk >= 0);
-    int base = 0;
-    if (lane == 0 && set) base = atomicAdd(&g.counters[C_UNIQUE], __popc(set));
-    base = __shfl_sync(0xffffffffu, base, 0);
+    const int pos = block_agg_add(&g.counters[C_UNIQUE], nk >= 0, nullptr);  // block-uniform call
     const unsigned below = set & ((1u << lane) - 1u);
-    if (nk >= 0) out[base + __popc(below)] = (uint32_t)i;
+    if (nk >= 0) out[pos] = (uint32_t)i;
     const int prev_lane = 31 - __clz(below);  // previous flagged lane, or -1
     const int nk_prev = __shfl_sync(0xffffffffu, nk, prev_lane < 0 ? lane : prev_lane);
     if (nk >= 0 && (prev_lane < 0 || nk_prev != nk)) nflag[nk] = 1;
@@ -757,11 +756,11 @@ __device__ __forceinline__ void apply_last(const GridView& g, const rec_t* __res
         }
       }
     }
-    // the changed list: each brick once per epoch, a warp's bricks with one atomic
-    const int p = warp_reserve(&g.counters[C_CHANGED], first);
+    // the changed list: each brick once per epoch, a block's bricks with one atomic (as the flip
+    // count): the counter words see one atomic per block, not one per warp
+    const int p = block_agg_add(&g.counters[C_CHANGED], first, nullptr);
     if (first) changed[p] = slot;
-    unsigned m = __ballot_sync(0xffffffffu, flip);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&g.counters[C_FLIPS], __popc(m));
+    block_agg_add(&g.counters[C_FLIPS], flip, nullptr);
   }
 }
 
