@@ -1336,14 +1336,34 @@ __device__ __forceinline__ bool claim_run(const GridView& g, int axis, int bx, i
   return true;
 }
 
-// Append the claimed runs of a warp to the axis's work list (warp-uniform call); in a batch, igrid
-// records each run's grid.
-__device__ __forceinline__ void emit_runs(const GridView& g, int axis, bool won, unsigned long long packed,
-                                          unsigned long long* items, int32_t* igrid, int grid) {
-  const int p = warp_reserve(&g.items_ctr[axis], won);
-  if (won && p < g.item_cap) {
-    items[p] = packed;
-    if (igrid) igrid[p] = grid;
+// Append the claimed runs (won[a]: this thread's run along axis a) to the three axes' work lists
+// (block-uniform call; in a batch, igrid records each run's grid): the warps' counts are summed in
+// shared memory and each list's counter word takes one atomic per block -- one per warp would
+// queue thousands of atomics on the same word in a frame's marking.
+__device__ __forceinline__ void emit_runs3(const GridView& g, const bool (&won)[3], const unsigned long long (&packed)[3],
+                                           const Items& it, int grid) {
+  __shared__ int cnt[3], base[3];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int off[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const unsigned m = __ballot_sync(0xffffffffu, won[a]);
+    int wb = 0;
+    if (lane == 0 && m) wb = atomicAdd(&cnt[a], __popc(m));
+    off[a] = __shfl_sync(0xffffffffu, wb, 0) + __popc(m & ((1u << lane) - 1u));
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&g.items_ctr[threadIdx.x], cnt[threadIdx.x]) : 0;
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int p = base[a] + off[a];
+    if (won[a] && p < g.item_cap) {
+      it.run[a][p] = packed[a];
+      if (it.igrid[a]) it.igrid[a][p] = grid;
+    }
   }
 }
 
@@ -1663,9 +1683,7 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
           }
         }
       }
-      emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
-      emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
-      emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
+      emit_runs3(g, {wx, wy, wz}, {px, py, pz}, it, grid);
     }
     return;
   }
@@ -1747,9 +1765,7 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
           if (any) wz = claim_run(g, 2, bx, by, zs, node, rz, epoch, pz);
         }
       }
-      emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
-      emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
-      emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
+      emit_runs3(g, {wx, wy, wz}, {px, py, pz}, it, grid);
     }
   }
 }
@@ -1790,9 +1806,7 @@ __global__ void __launch_bounds__(256) k_mark_runs(US us, int rx, int ry, int rz
         }
       }
     }
-    emit_runs(g, 0, wx, px, it.run[0], it.igrid[0], grid);
-    emit_runs(g, 1, wy, py, it.run[1], it.igrid[1], grid);
-    emit_runs(g, 2, wz, pz, it.run[2], it.igrid[2], grid);
+    emit_runs3(g, {wx, wy, wz}, {px, py, pz}, it, grid);
   }
 }
 
