@@ -1690,26 +1690,36 @@ __global__ void __launch_bounds__(256, 6) k_changed_mark(US us, int rx, int ry, 
   for (int i = (int)blockIdx.x; i < nc; i += (int)gridDim.x) {
     const int s = changed[i];
     __syncthreads();  // the table of the block's previous brick is no longer read
-    if (threadIdx.x == 0) {
-      const bool obst = brick_has_obstacle(g, s);
-      const uint32_t f = g.bflags[s];
-      g.bflags[s] = obst ? (f | F_OBST) : (f & ~F_OBST);
-      obst_sh = obst;
-    }
     const int4 c = g.bcoord[s];
     const int x0 = max(c.x - R, 0), x1 = min(c.x + R, g.BX - 1);
     const int y0 = max(c.y - R, 0), y1 = min(c.y + R, g.BY - 1);
     const int z0 = max(c.z - R, 0), z1 = min(c.z + R, g.BZ - 1);
     const int qx0 = x0 >> 4, qy0 = y0 >> 4, qz0 = z0 >> 4;
     const int nqx = (x1 >> 4) - qx0 + 1, nqy = (y1 >> 4) - qy0 + 1, nqz = (z1 >> 4) - qz0 + 1;
-    __syncthreads();
-    const bool obst = obst_sh != 0;  // block-uniform
-    if ((int)threadIdx.x < nqx * nqy * nqz) {
-      const int q = (int)threadIdx.x;
-      const unsigned long long key = node_key_at(g, qx0 + q % nqx, qy0 + (q / nqx) % nqy, qz0 + q / (nqx * nqy));
-      nodes[q] = obst ? get_or_create_node(g, key) : find_node(g, key);
+    const int nq = nqx * nqy * nqz;  // at most 4^3
+    // at once: the brick's obstacle bit (lanes 0-7 of warp 0, a mask word each) and the lookups of
+    // the nodes its cube spans (threads 32 .. 32 + nq - 1); nodes an obstacle brick's dilation
+    // needs and that do not exist yet are created after the barrier
+    if (threadIdx.x < 8) {
+      const bool any = __any_sync(0xffu, g.occ[(size_t)s * 8 + threadIdx.x] != 0ull);
+      if (threadIdx.x == 0) {
+        const uint32_t f = g.bflags[s];
+        g.bflags[s] = any ? (f | F_OBST) : (f & ~F_OBST);
+        obst_sh = any;
+      }
+    } else if ((int)threadIdx.x >= 32 && (int)threadIdx.x < 32 + nq) {
+      const int q = (int)threadIdx.x - 32;
+      nodes[q] = find_node(g, node_key_at(g, qx0 + q % nqx, qy0 + (q / nqx) % nqy, qz0 + q / (nqx * nqy)));
     }
     __syncthreads();
+    const bool obst = obst_sh != 0;  // block-uniform
+    if (obst) {
+      if ((int)threadIdx.x < nq && nodes[threadIdx.x] < 0) {
+        const int q = (int)threadIdx.x;
+        nodes[q] = get_or_create_node(g, node_key_at(g, qx0 + q % nqx, qy0 + (q / nqx) % nqy, qz0 + q / (nqx * nqy)));
+      }
+      __syncthreads();
+    }
     if (obst) {
       // dilation: a row's x extent is split at node boundaries (the same segments on every lane);
       // the rounds are block-uniform so that new bricks' slots are reserved a warp at a time
