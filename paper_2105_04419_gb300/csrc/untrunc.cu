@@ -37,16 +37,6 @@ struct LineStack {
   __device__ __forceinline__ int2& operator[](int m) const { return p[(size_t)m * 32]; }
 };
 
-// Adds each thread's `n` to *ctr with one atomic per block (every thread of the block calls it).
-__device__ __forceinline__ void block_count(int32_t* ctr, int n) {
-  __shared__ int sum;
-  if (threadIdx.x == 0) sum = 0;
-  __syncthreads();
-  if (n) atomicAdd(&sum, n);
-  __syncthreads();
-  if (threadIdx.x == 0 && sum) atomicAdd(ctr, sum);
-}
-
 unsigned ut_blocks(int64_t threads) {
   const int64_t b = (threads + kUT - 1) / kUT;
   return (unsigned)(b < 1 ? 1 : (b > 152 * 64 ? 152 * 64 : b));
@@ -136,7 +126,6 @@ __global__ void k_ut_x(GridView g, int32_t* __restrict__ carry) {
   int32_t* __restrict__ g1 = reinterpret_cast<int32_t*>(g.g1);
   const int64_t nrows = (int64_t)g.BY * g.BZ * 64;  // a multiple of 64: every warp is whole
   const int lane = threadIdx.x & 31;
-  int rows = 0;  // rows recomputed (lane 0 of each warp), counted once per block at the end
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nrows; t += (int64_t)gridDim.x * blockDim.x) {
     if (INCR) {
       uint32_t w = 0u;
@@ -144,7 +133,7 @@ __global__ void k_ut_x(GridView g, int32_t* __restrict__ carry) {
         w = g.ut_bits[t >> 5];
         if (w) {
           g.ut_bits[t >> 5] = 0u;
-          rows += __popc(w);
+          atomicAdd(&g.items_ctr[0], __popc(w));
         }
       }
       w = __shfl_sync(0xffffffffu, w, 0);
@@ -204,7 +193,6 @@ __global__ void k_ut_x(GridView g, int32_t* __restrict__ carry) {
       }
     }
   }
-  if (INCR) block_count(&g.items_ctr[0], rows);
 }
 
 // Voxel i of line (x, c) along AXIS (1: y, c = z; 2: z, c = y) in a pool of bricks at fixed slots:
@@ -324,14 +312,13 @@ __global__ void k_ut_env_upd(GridView g, const int32_t* __restrict__ in, int32_t
   uint32_t* bits = g.ut_bits + ut_row_words(g) + (AXIS == 1 ? 0 : ut_yline_words(g));
   uint32_t* zbits = g.ut_bits + ut_row_words(g) + ut_yline_words(g);
   const int lane = threadIdx.x & 31;
-  int lines = 0;  // lines recomputed (lane 0 of each warp), counted once per block at the end
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nlines; t += (int64_t)gridDim.x * blockDim.x) {
     uint32_t w = 0u;
     if (lane == 0) {
       w = bits[t >> 5];
       if (w) {
         bits[t >> 5] = 0u;
-        lines += __popc(w);
+        atomicAdd(&g.items_ctr[AXIS], __popc(w));
       }
     }
     w = __shfl_sync(0xffffffffu, w, 0);
@@ -361,7 +348,6 @@ __global__ void k_ut_env_upd(GridView g, const int32_t* __restrict__ in, int32_t
       }
     }
   }
-  block_count(&g.items_ctr[AXIS], lines);
 }
 
 // Brick flags after the transform: obstacle bits, and finite D (voxel (0, 0, 0) of every brick lies
