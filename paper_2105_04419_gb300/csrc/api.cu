@@ -1603,6 +1603,9 @@ __global__ void k_check_packed(const uint64_t* __restrict__ src, int64_t n, int 
 __global__ void k_check_bricks(const int32_t* __restrict__ bxyz, const uint64_t* __restrict__ masks, int64_t n,
                                GridView g, int32_t* invalid, unsigned long long* count) {
   const int64_t nw = n * 8;
+  __shared__ unsigned long long bsum;  // the block's bit count: one atomic on *count per block
+  if (threadIdx.x == 0) bsum = 0ull;
+  __syncthreads();
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nw; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
     int bits = 0;
@@ -1623,16 +1626,19 @@ __global__ void k_check_bricks(const int32_t* __restrict__ bxyz, const uint64_t*
       if (!ok) atomicAdd(invalid, 1);
       bits = ok ? __popcll(m) : 0;
     }
-    // one atomic per warp for the count
     for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
-    if ((threadIdx.x & 31) == 0 && bits) atomicAdd(count, (unsigned long long)bits);
+    if ((threadIdx.x & 31) == 0 && bits) atomicAdd(&bsum, (unsigned long long)bits);
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && bsum) atomicAdd(count, bsum);
 }
 
 __global__ void k_expand_bricks(const int32_t* __restrict__ bxyz, const uint64_t* __restrict__ masks, int64_t n,
                                 GridView g, rec_t* __restrict__ dst, unsigned long long* cursor) {
   const int64_t nw = n * 8;
   const int lane = threadIdx.x & 31;
+  __shared__ int wtot[32];
+  __shared__ unsigned long long woff[32], bbase;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nw; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
     unsigned long long m = 0ull;
@@ -1645,17 +1651,28 @@ __global__ void k_expand_bricks(const int32_t* __restrict__ bxyz, const uint64_t
       z = 8 * (bxyz[3 * k + 2] + (g.off >> 3)) + (int)(i & 7);
     }
     const int bits = __popcll(m);
-    // the warp's places: an inclusive scan of the bit counts, one atomic
+    // the block's places: an inclusive scan of the bit counts in each warp, the warps' totals
+    // scanned by thread 0, one atomic on the cursor per block
     int incl = bits;
     for (int o = 1; o < 32; o <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += v;
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long first = 0ull;
-    if (lane == 31 && total) first = atomicAdd(cursor, (unsigned long long)total);
-    first = __shfl_sync(0xffffffffu, first, 31);
-    unsigned long long p = first + (unsigned long long)(incl - bits);
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0ull;
+      for (int w = 0; w < nwarps; ++w) {
+        const unsigned long long c = (unsigned long long)wtot[w];
+        woff[w] = t;
+        t += c;
+      }
+      bbase = t ? atomicAdd(cursor, t) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long p = bbase + woff[warp] + (unsigned long long)(incl - bits);
+    __syncthreads();  // the block's next round rewrites wtot / woff / bbase
     while (m) {
       const int b = __ffsll((long long)m) - 1;
       m &= m - 1ull;
