@@ -297,54 +297,51 @@ __global__ void k_ut_env(GridView g, const int32_t* __restrict__ in, int32_t* __
   }
 }
 
-// The update's y (AXIS 1) or z (AXIS 2) pass over the lines whose dirty bit is set: lines (x, c)
-// with x padded to NXP, so that a warp's 32 lanes are 32 lines along x at one c and take one word
-// of dirty bits (then cleared).  Each dirty lane builds its line's envelope as k_ut_env does; the
-// read-back runs on every lane of the warp in step, so that the y pass can gather the voxels whose
-// g2 changed into the z-line bits (x, y) with one ballot and one OR per position.  The z pass
-// writes D on its dirty lines.
+// The update's y (AXIS 1) or z (AXIS 2) pass over the dirty lines: lines (x, c) with x padded to
+// NXP, so that a warp's 32 lanes are 32 lines along x at one c and take one word of dirty bits
+// (y) or 32 dirty bytes (z), cleared once read.  Each dirty lane builds its line's envelope as
+// k_ut_env does and reads it back; the y pass writes the g2 values that changed and sets the
+// z-line byte (x, y) of each.  The z pass writes D on its dirty lines.
 template <int AXIS>
 __global__ void k_ut_env_upd(GridView g, const int32_t* __restrict__ in, int32_t* __restrict__ out,
                              int2* __restrict__ stack) {
   const int n = AXIS == 1 ? g.ny : g.nz;
   const int nxp = ut_nxp(g);
   const int64_t nlines = (int64_t)nxp * (AXIS == 1 ? g.nz : g.ny);  // a multiple of 32
-  uint32_t* bits = g.ut_bits + ut_row_words(g) + (AXIS == 1 ? 0 : ut_yline_words(g));
-  uint32_t* zbits = g.ut_bits + ut_row_words(g) + ut_yline_words(g);
+  uint32_t* ybits = g.ut_bits + ut_row_words(g);
+  uint8_t* zflag = reinterpret_cast<uint8_t*>(g.ut_bits + ut_row_words(g) + ut_yline_words(g));
   const int lane = threadIdx.x & 31;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nlines; t += (int64_t)gridDim.x * blockDim.x) {
     uint32_t w = 0u;
-    if (lane == 0) {
-      w = bits[t >> 5];
-      if (w) {
-        bits[t >> 5] = 0u;
-        atomicAdd(&g.items_ctr[AXIS], __popc(w));
+    if (AXIS == 1) {
+      if (lane == 0) {
+        w = ybits[t >> 5];
+        if (w) ybits[t >> 5] = 0u;
       }
+      w = __shfl_sync(0xffffffffu, w, 0);
+    } else {
+      const bool f = zflag[t] != 0;
+      w = __ballot_sync(0xffffffffu, f);
+      if (f) zflag[t] = 0;
     }
-    w = __shfl_sync(0xffffffffu, w, 0);
     if (!w) continue;  // warp-uniform
+    if (lane == 0) atomicAdd(&g.items_ctr[AXIS], __popc(w));
+    const bool dirty = (w >> lane) & 1u;  // set only for x < nx
+    if (!dirty) continue;
     const int x = (int)(t % nxp), c = (int)(t / nxp);  // c: z (AXIS 1) or y (AXIS 2)
-    const bool dirty = (w >> lane) & 1u;                 // set only for x < nx
     const LineAt<AXIS> at(g, x, c);
     const LineStack st(stack, t, n);
-    EnvRead env(st, dirty ? env_build<AXIS>(st, at, in, n) : 0);
+    EnvRead env(st, env_build<AXIS>(st, at, in, n));
     for (int i = 0; i < n; ++i) {
-      bool changed = false;
-      if (dirty) {
-        const int val = env.at(i);
-        const size_t a = at(i);
-        if (AXIS == 1) {
-          if (out[a] != val) {
-            out[a] = val;
-            changed = true;
-          }
-        } else {
-          out[a] = val;
-        }
-      }
+      const int val = env.at(i);
+      const size_t a = at(i);
       if (AXIS == 1) {
-        const uint32_t b = __ballot_sync(0xffffffffu, changed);
-        if (lane == 0 && b) atomicOr(&zbits[((int64_t)nxp * i + (x - lane)) >> 5], b);
+        if (out[a] != val) {
+          out[a] = val;
+          zflag[(size_t)nxp * i + x] = 1;
+        }
+      } else {
+        out[a] = val;
       }
     }
   }
