@@ -77,7 +77,7 @@ typedef enum {
  * A bounded grid only, with (nx-1)^2 + (ny-1)^2 + (nz-1)^2 < 2^31 - 1 so that every distance fits
  * int32, and every brick stored from creation (max_bricks and max_nodes 0 or at least the grid's):
  * about 6.2 KB per 8^3 brick (32-bit intermediates) plus 8 bytes per voxel of line scratch (nx
- * rounded up to 32) and three bitmaps of dirty lines, all allocated at creation.  The transform
+ * rounded up to 32) and three sets of dirty lines, all allocated at creation.  The transform
  * runs whole lines of the grid (x: nearest occupied voxel of the row; y, z: lower envelope of the
  * parabolas rooted at the line's values).  vdbedt_update applies the staged records and recomputes
  * only the lines they reach, exactly: the x rows holding a flipped voxel, then the y lines on which
