@@ -120,7 +120,7 @@ __global__ void k_ut_dense(GridView g, const uint8_t* __restrict__ grid) {
 // and writes g1 = d^2 (kNone: empty row) once per voxel.
 // INCR (an update): only the rows whose dirty bit is set, each warp taking and clearing its word;
 // the backward sweep compares each g1 with the stored one, writes the bricks' row pieces that
-// changed and sets the y-line bit (x, z) of every changed voxel, a 32-bit word at a time.
+// changed and sets the y-line byte (x, z) of every changed voxel with a plain store.
 template <bool INCR>
 __global__ void k_ut_x(GridView g, int32_t* __restrict__ carry) {
   int32_t* __restrict__ g1 = reinterpret_cast<int32_t*>(g.g1);
@@ -153,8 +153,7 @@ __global__ void k_ut_x(GridView g, int32_t* __restrict__ carry) {
       if (byte) last = 8 * bx + 31 - __clz(byte);
     }
     int next = -1;
-    uint32_t* ybits = INCR ? g.ut_bits + ut_row_words(g) + (size_t)(ut_nxp(g) >> 5) * z : nullptr;
-    uint32_t acc = 0u;  // changed voxels of the current 32-voxel word of the row
+    uint8_t* yflag = INCR ? reinterpret_cast<uint8_t*>(g.ut_bits + ut_row_words(g)) + (size_t)ut_nxp(g) * z : nullptr;
     for (int bx = g.BX - 1; bx >= 0; --bx) {
       const int s = ut_slot(g, bx, by, bz);
       const uint32_t byte = (uint32_t)(g.occ[(size_t)s * 8 + (z & 7)] >> shift) & 0xFFu;
@@ -181,11 +180,9 @@ __global__ void k_ut_x(GridView g, int32_t* __restrict__ carry) {
         if (ch) {
           dst[0] = make_int4(v[0], v[1], v[2], v[3]);
           dst[1] = make_int4(v[4], v[5], v[6], v[7]);
-          acc |= ch << ((8 * bx) & 31);
-        }
-        if (((8 * bx) & 31) == 0 && acc) {  // the word's first brick: flush its bits
-          atomicOr(&ybits[(8 * bx) >> 5], acc);
-          acc = 0u;
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if ((ch >> i) & 1u) yflag[8 * bx + i] = 1;  // the rows of every y write the same y lines
         }
       } else {
         dst[0] = make_int4(v[0], v[1], v[2], v[3]);
@@ -298,32 +295,24 @@ __global__ void k_ut_env(GridView g, const int32_t* __restrict__ in, int32_t* __
 }
 
 // The update's y (AXIS 1) or z (AXIS 2) pass over the dirty lines: lines (x, c) with x padded to
-// NXP, so that a warp's 32 lanes are 32 lines along x at one c and take one word of dirty bits
-// (y) or 32 dirty bytes (z), cleared once read.  Each dirty lane builds its line's envelope as
-// k_ut_env does and reads it back; the y pass writes the g2 values that changed and sets the
-// z-line byte (x, y) of each.  The z pass writes D on its dirty lines.
+// NXP, so that a warp's 32 lanes are 32 lines along x at one c and read 32 dirty-line bytes,
+// cleared once read.  Each dirty lane builds its line's envelope as k_ut_env does and reads it
+// back; the y pass writes the g2 values that changed and sets the z-line byte (x, y) of each.
+// The z pass writes D on its dirty lines.
 template <int AXIS>
 __global__ void k_ut_env_upd(GridView g, const int32_t* __restrict__ in, int32_t* __restrict__ out,
                              int2* __restrict__ stack) {
   const int n = AXIS == 1 ? g.ny : g.nz;
   const int nxp = ut_nxp(g);
   const int64_t nlines = (int64_t)nxp * (AXIS == 1 ? g.nz : g.ny);  // a multiple of 32
-  uint32_t* ybits = g.ut_bits + ut_row_words(g);
+  uint8_t* yflag = reinterpret_cast<uint8_t*>(g.ut_bits + ut_row_words(g));
   uint8_t* zflag = reinterpret_cast<uint8_t*>(g.ut_bits + ut_row_words(g) + ut_yline_words(g));
+  uint8_t* flag = AXIS == 1 ? yflag : zflag;  // this pass's dirty lines
   const int lane = threadIdx.x & 31;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nlines; t += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t w = 0u;
-    if (AXIS == 1) {
-      if (lane == 0) {
-        w = ybits[t >> 5];
-        if (w) ybits[t >> 5] = 0u;
-      }
-      w = __shfl_sync(0xffffffffu, w, 0);
-    } else {
-      const bool f = zflag[t] != 0;
-      w = __ballot_sync(0xffffffffu, f);
-      if (f) zflag[t] = 0;
-    }
+    const bool f = flag[t] != 0;
+    const uint32_t w = __ballot_sync(0xffffffffu, f);
+    if (f) flag[t] = 0;
     if (!w) continue;  // warp-uniform
     if (lane == 0) atomicAdd(&g.items_ctr[AXIS], __popc(w));
     const bool dirty = (w >> lane) & 1u;  // set only for x < nx

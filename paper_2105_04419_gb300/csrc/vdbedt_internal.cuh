@@ -115,16 +115,17 @@ struct GridView {
   int32_t* items_ctr; // [3] items queued along x, y, z (the grid's counters, or the batch's)
   // Untruncated grids: the dirty lines of an update (null otherwise), three sets back to back,
   // each cleared by the pass that reads it: x rows (bit (by + BY bz) * 64 + (y & 7) + 8 (z & 7), set
-  // by the tracked ingest at each flipped voxel), y lines (bit x + NXP z, set where the x pass
-  // changed g1) and z lines (a byte per line x + NXP y, set with plain stores where the y pass
-  // changed g2: the y lines of every z plane write them, and bytes need no atomics); NXP = nx
-  // rounded up to 32, so that a warp's 32 lines along x share one word (32 bytes for z lines).
+  // by the tracked ingest at each flipped voxel), y lines (a byte per line x + NXP z, set where the
+  // x pass changed g1) and z lines (a byte per line x + NXP y, set where the y pass changed g2); the
+  // bytes are set with plain stores -- the rows of every y (the y lines of every z) write the same
+  // lines, and bytes need no atomics; NXP = nx rounded up to 32, so that a warp's 32 lines along x
+  // read 32 consecutive bytes.
   uint32_t* ut_bits;
 };
 
 __host__ __device__ inline int ut_nxp(const GridView& g) { return (g.nx + 31) & ~31; }
 __host__ __device__ inline int64_t ut_row_words(const GridView& g) { return (int64_t)g.BY * g.BZ * 2; }
-__host__ __device__ inline int64_t ut_yline_words(const GridView& g) { return (int64_t)(ut_nxp(g) >> 5) * g.nz; }
+__host__ __device__ inline int64_t ut_yline_words(const GridView& g) { return (int64_t)(ut_nxp(g) >> 2) * g.nz; }
 __host__ __device__ inline int64_t ut_zline_words(const GridView& g) { return (int64_t)(ut_nxp(g) >> 2) * g.ny; }
 __host__ __device__ inline int64_t ut_bits_words(const GridView& g) {
   return ut_row_words(g) + ut_yline_words(g) + ut_zline_words(g);
