@@ -24,8 +24,12 @@ from __future__ import annotations
 
 
 def halo_planes(dmax: int) -> int:
-    """Planes of occupancy needed beyond each end of a slab: 8R, R = floor((dmax + 6) / 8)."""
-    return 8 * ((dmax + 6) // 8)
+    """Planes of occupancy needed beyond each end of a slab: 8R, R = floor((dmax + 6) / 8).  An
+    untruncated grid (dmax None) has no finite halo -- any obstacle can be a voxel's nearest -- so
+    it cannot be split into slabs."""
+    if dmax is None or isinstance(dmax, float) or int(dmax) < 1:
+        raise ValueError("z-slabs need a finite truncation dmax >= 1 (an untruncated grid has no finite halo)")
+    return 8 * ((int(dmax) + 6) // 8)
 
 
 def slab_bounds(nz: int, world: int, dmax: int) -> list:

@@ -191,3 +191,14 @@ def test_sparse_protocol_oracle_emulation():
                     ext[lo - h0: hi - h0] = occ[lo:hi]
             parts.append(S.owned_part(O.edt_factorised(ext, dmax), b, r, dmax))
         assert np.array_equal(np.concatenate(parts, 0), O.edt_factorised(occ, dmax)), frame
+
+
+def test_untruncated_grid_has_no_slabs():
+    """Without a truncation every obstacle can be a voxel's nearest: no finite halo, so the slab
+    split is refused with a clear error."""
+    import paper_2105_04419_gb300.slabs as S
+    with pytest.raises(ValueError):
+        S.slab_bounds(256, 2, None)
+    with pytest.raises(ValueError):
+        S.halo_planes(0)
+    assert S.halo_planes(32) == 32 and S.halo_planes(2) == 8 and S.halo_planes(1) == 0
