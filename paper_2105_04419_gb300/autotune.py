@@ -148,6 +148,8 @@ def autotune(target, reps: int = 5, cache_path: str | None = None, use_cache: bo
     """Tune a Map or Batch on its current occupancy; applies and returns the tuning
     {"x_run", "y_run", "z_run", "variant", "source": "cache" | "measured"}.  The field is left
     recomputed (global transform) under the chosen tuning."""
+    if getattr(target, "untruncated", False):
+        raise ValueError("an untruncated grid has no tuning: its whole-line passes take no work-item shapes")
     path = cache_path or default_cache_path()
     target.global_()
     key = signature(target)
