@@ -320,6 +320,12 @@ __device__ __forceinline__ int64_t rec_count(int64_t n, const int32_t* n_dev) {
 
 // Places for the lanes with `want` in a list counted by *ctr: one atomic per warp (warp-uniform
 // call); returns the lane's place (meaningful where want).
+// Sets a flag word that only ever goes from 0 to 1, reading it first (L2): once one warp has set
+// it the others find it set and issue no atomic on the shared word.
+__device__ __forceinline__ void set_once(int32_t* flag) {
+  if (!__ldcg(flag)) atomicOr(flag, 1);
+}
+
 __device__ __forceinline__ int warp_reserve(int32_t* ctr, bool want) {
   const unsigned m = __ballot_sync(0xffffffffu, want);
   if (!m) return 0;
@@ -352,7 +358,7 @@ __global__ void k_rec_brick_keys(GridView g, const rec_t* __restrict__ rec, int6
     uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
     if (lane > 0 && prev == key) key = 0xFFFFFFFFu;
     if (i < n) keys[i] = key;
-    if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+    if (__any_sync(0xffffffffu, zero) && lane == 0) set_once(&g.counters[C_HAS_ZERO]);
     if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
   }
 }
@@ -411,7 +417,7 @@ __device__ __forceinline__ void mark_record(const GridView& g, bool have, rec_t 
     if (widx != 0xFFFFFFFFu && (run_end || ((lane - start) & 7) == 7))
       atomicOr(dbits + widx, ((unsigned long long)bhi << 32) | blo);
   }
-  if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+  if (__any_sync(0xffffffffu, zero) && lane == 0) set_once(&g.counters[C_HAS_ZERO]);
   if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
 }
 
@@ -682,7 +688,7 @@ __global__ void k_rec_slots(US us) {
     const unsigned made = __ballot_sync(0xffffffffu, ok);
     if (lane == 0 && made) atomicAdd(&g.counters[C_NEW_BRICKS], __popc(made));
     if (i < n) A.rslot[i] = rs;
-    if (__any_sync(0xffffffffu, zero) && lane == 0) atomicOr(&g.counters[C_HAS_ZERO], 1);
+    if (__any_sync(0xffffffffu, zero) && lane == 0) set_once(&g.counters[C_HAS_ZERO]);
     if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(g, kErrInvalidRecord);
   }
 }
