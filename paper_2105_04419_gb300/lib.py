@@ -233,6 +233,10 @@ class Map:
     # stream ordering between the caller's current torch stream and the handle's stream
     def _enter(self, *tensors):
         torch = _torch()
+        for t in tensors:  # device pointers go to the library: CPU tensors or another GPU's are refused
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != self.device:
+                where = t.device if isinstance(t, torch.Tensor) else type(t).__name__
+                raise ValueError(f"expected a CUDA tensor on cuda:{self.device}, got {where}")
         cur = torch.cuda.current_stream(self.device)
         if cur.cuda_stream != self.stream.cuda_stream:
             self.stream.wait_stream(cur)
@@ -252,12 +256,16 @@ class Map:
         if isinstance(xyz, np.ndarray):
             x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
             o = np.ascontiguousarray(occ, dtype=np.uint8).reshape(-1)
+            if x.shape[0] != o.shape[0]:
+                raise ValueError(f"{x.shape[0]} coordinates but {o.shape[0]} occupancy values")
             _check(lib.vdbedt_set_occupancy(self._h, _ptr_host(x), _ptr_host(o), x.shape[0], 0),
                    "vdbedt_set_occupancy", self._h)
         else:
             torch = _torch()
             x = xyz.to(torch.int32).contiguous().view(-1, 3)
             o = occ.to(torch.uint8).contiguous().view(-1)
+            if x.shape[0] != o.shape[0]:
+                raise ValueError(f"{x.shape[0]} coordinates but {o.shape[0]} occupancy values")
             self._enter(x, o)
             _check(lib.vdbedt_set_occupancy(self._h, x.data_ptr(), o.data_ptr(), x.shape[0], 1),
                    "vdbedt_set_occupancy", self._h)
@@ -304,9 +312,10 @@ class Map:
         """Stage up to n_max device records whose count is the int32 CUDA tensor `count` (read on
         the stream); see UpdateGraph for the captured form."""
         torch = _torch()
-        assert xyz.is_cuda and occ.is_cuda and count.is_cuda and count.dtype == torch.int32
-        assert xyz.dtype == torch.int32 and occ.dtype == torch.uint8 and xyz.is_contiguous() and occ.is_contiguous()
-        assert xyz.shape[0] >= n_max and occ.shape[0] >= n_max
+        if count.dtype != torch.int32 or xyz.dtype != torch.int32 or occ.dtype != torch.uint8:
+            raise TypeError("xyz int32, occ uint8, count int32 (CUDA tensors)")
+        if not (xyz.is_contiguous() and occ.is_contiguous()) or xyz.shape[0] < n_max or occ.shape[0] < n_max:
+            raise ValueError(f"contiguous xyz [>= {n_max}, 3] and occ [>= {n_max}] needed")
         self._enter(xyz, occ, count)
         _check(load().vdbedt_set_occupancy_counted(self._h, xyz.data_ptr(), occ.data_ptr(), count.data_ptr(),
                                                    int(n_max)), "vdbedt_set_occupancy_counted", self._h)
